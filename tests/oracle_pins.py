@@ -1,0 +1,234 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each ``pin_*`` takes an ``oracle.Oracle`` and raises AssertionError when the
+oracle disagrees with something other than itself: exact rational arithmetic
+of the definition (brute force with ``fractions.Fraction``), a hand-worked
+example, closed forms (identity, diagonal), an exact integer library routine,
+the invariants (AB)^T = B^T A^T and (AB)x = A(Bx), and rounding-error bounds.
+The definition pinned is the Cauchy product of the paper's Section
+"Implementacje algorytmow" (c_ij = sum_r a_ir b_rj), in the order of Listing 1.
+
+The same pins run against builds of the oracle with one planted mistake each
+(tests/test_oracle_mutants.py) to show that every such mistake is caught.
+"""
+from __future__ import annotations
+
+from fractions import Fraction
+
+import numpy as np
+
+import synth
+
+U64 = 2.0 ** -53  # unit roundoff of binary64
+
+
+def _exact_product(A, B):
+    """Definition of the Cauchy product in exact rationals (tiny inputs)."""
+    n, m = A.shape
+    p = B.shape[1]
+    C = [[Fraction(0)] * p for _ in range(n)]
+    S = [[Fraction(0)] * p for _ in range(n)]
+    for i in range(n):
+        for j in range(p):
+            c = Fraction(0)
+            s = Fraction(0)
+            for r in range(m):
+                a = Fraction(float(A[i, r]))
+                b = Fraction(float(B[r, j]))
+                c += a * b
+                s += abs(a) * abs(b)
+            C[i][j] = c
+            S[i][j] = s
+    return C, S
+
+
+TINY_SHAPES = [(1, 1, 1), (2, 3, 4), (3, 3, 3), (4, 1, 5), (5, 7, 2), (7, 5, 3),
+               (17, 5, 3), (3, 17, 7), (4, 4, 17)]
+
+
+def pin_bruteforce_definition(orc):
+    """FP64 oracle vs exact rationals: |c - c_exact| <= (m-1) u (|A||B|)_ij,
+    the textbook bound for recursive summation of exact products."""
+    for t, (n, m, p) in enumerate(TINY_SHAPES):
+        A = synth.uniform_pm1(100 + t, (n, m))
+        B = synth.uniform_pm1(200 + t, (m, p))
+        C, absC = orc.gemm(A, B, with_abs=True)
+        Cx, Sx = _exact_product(A, B)
+        for i in range(n):
+            for j in range(p):
+                bound = (m - 1) * U64 * float(Sx[i][j]) * (1 + 1e-12)
+                err = abs(Fraction(float(C[i, j])) - Cx[i][j])
+                assert float(err) <= bound, (n, m, p, i, j, float(err), bound)
+                errs = abs(Fraction(float(absC[i, j])) - Sx[i][j])
+                assert float(errs) <= bound + 1e-300, ("abs", n, m, p, i, j)
+
+
+def pin_small_ints_exact(orc):
+    """Integer entries in [-8, 8]: every partial sum is an integer below 2^53,
+    so the oracle must equal the exact integer product (numpy int64 matmul)."""
+    for t, (n, m, p) in enumerate([(1, 1, 1), (33, 64, 17), (8, 4096, 5), (64, 64, 64)]):
+        A = synth.small_ints(300 + t, (n, m))
+        B = synth.small_ints(400 + t, (m, p))
+        C, absC = orc.gemm(A, B, with_abs=True)
+        Ci = A.astype(np.int64) @ B.astype(np.int64)
+        Si = np.abs(A).astype(np.int64) @ np.abs(B).astype(np.int64)
+        assert np.array_equal(C, Ci.astype(np.float64)), (n, m, p)
+        assert np.array_equal(absC, Si.astype(np.float64)), (n, m, p)
+
+
+def pin_hand_example(orc):
+    """Worked by hand from the definition.
+
+    3x3 (the size of the paper's walk-through before Listing 2):
+      A = [[1,2,3],[4,5,6],[7,8,9]], B = [[9,8,7],[6,5,4],[3,2,1]]
+      c_11 = 1*9 + 2*6 + 3*3 = 30, c_12 = 1*8 + 2*5 + 3*2 = 24, ...
+      C = [[30,24,18],[84,69,54],[138,114,90]].
+    In Listing 2 the thread with thread_x = 0, thread_y = 1 reads row
+    thread_y of A and column thread_x of B, i.e. it computes C[1][0] = 84.
+    2x3 by 3x2 (non-square, catches a swapped operand or index):
+      A = [[1,0,-2],[3,1,0]], B = [[2,1],[0,-1],[1,4]]
+      C = [[1*2 + 0*0 + (-2)*1, 1*1 + 0*(-1) + (-2)*4], [3*2 + 1*0 + 0*1, 3*1 + 1*(-1) + 0*4]]
+        = [[0, -7], [6, 2]].
+    """
+    A = np.array([[1, 2, 3], [4, 5, 6], [7, 8, 9]], np.float32)
+    B = np.array([[9, 8, 7], [6, 5, 4], [3, 2, 1]], np.float32)
+    C = orc.gemm(A, B)
+    assert np.array_equal(C, np.array([[30, 24, 18], [84, 69, 54], [138, 114, 90]], np.float64))
+    assert C[1, 0] == 84.0
+    A2 = np.array([[1, 0, -2], [3, 1, 0]], np.float32)
+    B2 = np.array([[2, 1], [0, -1], [1, 4]], np.float32)
+    C2, S2 = orc.gemm(A2, B2, with_abs=True)
+    assert np.array_equal(C2, np.array([[0, -7], [6, 2]], np.float64))
+    # |A||B|: [[1*2+0+2*1, 1*1+0+2*4],[3*2+0+0, 3*1+1*1+0]] = [[4, 9], [6, 4]]
+    assert np.array_equal(S2, np.array([[4, 9], [6, 4]], np.float64))
+
+
+def pin_identity(orc):
+    """A.I = A and I.B = B exactly (one non-zero product per entry)."""
+    A = synth.uniform_pm1(500, (37, 23))
+    C = orc.gemm(A, synth.identity(23))
+    assert np.array_equal(C, A.astype(np.float64))
+    B = synth.uniform_pm1(501, (19, 41))
+    C = orc.gemm(synth.identity(19), B)
+    assert np.array_equal(C, B.astype(np.float64))
+
+
+def pin_diagonal(orc):
+    """Paper's special case of diagonal matrices: A.diag(d) has c_ij = a_ij d_j
+    and diag(d).B has c_ij = d_i b_ij, exactly (products of two float32 values
+    are exact in binary64)."""
+    A = synth.uniform_pm1(600, (29, 31))
+    d = synth.uniform_pm1(601, 31)
+    C = orc.gemm(A, synth.diag_matrix(601, 31))
+    assert np.array_equal(C, A.astype(np.float64) * d.astype(np.float64)[None, :])
+    B = synth.uniform_pm1(602, (31, 13))
+    C = orc.gemm(synth.diag_matrix(601, 31), B)
+    assert np.array_equal(C, d.astype(np.float64)[:, None] * B.astype(np.float64))
+
+
+def pin_transpose(orc):
+    """(AB)^T = B^T A^T: each entry sums the same products in the same order,
+    so the oracle must agree bit for bit."""
+    A = synth.uniform_pm1(700, (23, 45))
+    B = synth.uniform_pm1(701, (45, 31))
+    C = orc.gemm(A, B)
+    Ct = orc.gemm(B.T.copy(), A.T.copy())
+    assert np.array_equal(C.T, Ct)
+
+
+def pin_freivalds(orc):
+    """(AB)x = A(Bx) within the rounding of both sides."""
+    n, m, p = 40, 300, 50
+    A = synth.uniform_pm1(800, (n, m))
+    B = synth.uniform_pm1(801, (m, p))
+    x = synth.freivalds_vector(802, p)
+    C, absC = orc.gemm(A, B, with_abs=True)
+    y, ya = orc.gemv(C, x)
+    z, za = orc.freivalds_rhs(A, B, x)
+    bound = 4 * (m + p) * U64 * za
+    assert np.all(np.abs(y - z) <= bound), float(np.max(np.abs(y - z) / za))
+    # a result with one wrong row must be caught
+    Cb = C.copy()
+    Cb[7, :] += 1e-6 * absC[7, :]
+    yb, _ = orc.gemv(Cb, x)
+    assert np.abs(yb[7] - z[7]) > bound[7]
+
+
+def pin_threads_invariant(orc):
+    """Rows are split over threads; the result must not depend on the split."""
+    A = synth.uniform_pm1(900, (53, 77))
+    B = synth.uniform_pm1(901, (77, 29))
+    ref = orc.gemm(A, B, threads=1)
+    for t in (2, 3, 8, 64):
+        assert np.array_equal(orc.gemm(A, B, threads=t), ref)
+
+
+def pin_empty_dims(orc):
+    """m = 0 gives the empty sum (C = 0); n = 0 or p = 0 gives an empty C."""
+    C = orc.gemm(np.zeros((4, 0), np.float32), np.zeros((0, 5), np.float32))
+    assert C.shape == (4, 5) and np.all(C == 0)
+    assert orc.gemm(np.zeros((0, 3), np.float32), np.ones((3, 2), np.float32)).shape == (0, 2)
+    assert orc.gemm(np.ones((2, 3), np.float32), np.ones((3, 0), np.float32)).shape == (2, 0)
+
+
+def _exact_dot(x, y):
+    return sum((Fraction(float(a)) * Fraction(float(b)) for a, b in zip(x, y)), Fraction(0))
+
+
+def pin_dot2_and_long_double(orc):
+    """Dot2 error <= u|s| + gamma_{n}^2 sum|ab| (Ogita-Rump-Oishi, Prop. 5.5
+    style bound, taken loosely with factor 2); long double error <=
+    (m-1) 2^-LDBL_MANT_DIG sum|ab| + u|s| after rounding to double.  The data
+    are ill-conditioned on purpose: the second half of the products cancels
+    the first half up to a small remainder."""
+    m = 200
+    a = synth.uniform_pm1_f64(1000, m)
+    b = synth.uniform_pm1_f64(1001, m)
+    # y2 chosen so that a2*b2 nearly cancels a1*b1 (condition number ~1e15)
+    A = np.concatenate([a, a]).reshape(1, 2 * m)
+    B = np.concatenate([b, -b * (1 + 2.0 ** -40)]).reshape(2 * m, 1)
+    ex = _exact_dot(A[0], B[:, 0])
+    s_abs = float(sum(abs(Fraction(float(x)) * Fraction(float(y))) for x, y in zip(A[0], B[:, 0])))
+    hi, lo, ab = orc.entries(A, B, np.array([0]), np.array([0]), "dot2")
+    n2 = 2 * m
+    gam = n2 * U64 / (1 - n2 * U64)
+    bound = U64 * abs(float(ex)) + 2 * gam * gam * s_abs
+    assert abs(float(Fraction(float(hi[0])) - ex)) <= bound, (float(hi[0]), float(ex))
+    assert abs(ab[0] - s_abs) <= n2 * U64 * s_abs
+    hl, ll, _ = orc.entries(A, B, np.array([0]), np.array([0]), "ld")
+    ul = 2.0 ** -orc.ldbl_mant_dig()
+    bound_ld = U64 * abs(float(ex)) + (n2 - 1) * ul * s_abs * 1.01
+    assert abs(float(Fraction(float(hl[0])) - ex)) <= bound_ld
+    # plain FP64 cannot meet the Dot2 bound on this data (shows the test bites)
+    plain = orc.gemm(A, B)[0, 0]
+    assert abs(float(Fraction(float(plain)) - ex)) > bound
+
+
+def pin_gemv(orc):
+    """gemv via Dot2 against exact rationals."""
+    X = synth.uniform_pm1_f64(1100, (6, 25))
+    v = synth.uniform_pm1_f64(1101, 25)
+    y, ya = orc.gemv(X, v)
+    for i in range(6):
+        ex = _exact_dot(X[i], v)
+        assert abs(float(Fraction(float(y[i])) - ex)) <= 2 * U64 * abs(float(ex)) + 1e-300
+
+
+def pin_pow2_exact(orc):
+    """Exact fixed-point sum for +-2^k inputs against exact rationals."""
+    A = synth.pow2_int(1200, (5, 37))
+    B = synth.pow2_int(1201, (37, 4))
+    hi, lo = orc.pow2_exact(A, B, shift=50)
+    Cx, _ = _exact_product(A, B)
+    for i in range(5):
+        for j in range(4):
+            got = Fraction(float(hi[i, j])) + Fraction(float(lo[i, j]))
+            assert got == Cx[i][j], (i, j)
+
+
+ALL_PINS = [
+    pin_bruteforce_definition, pin_small_ints_exact, pin_hand_example,
+    pin_identity, pin_diagonal, pin_transpose, pin_freivalds,
+    pin_threads_invariant, pin_empty_dims, pin_dot2_and_long_double,
+    pin_gemv, pin_pow2_exact,
+]
