@@ -1,0 +1,362 @@
+"""Benchmark of the dense product C = A.B on GB300.
+
+One step = one split-BF16x3 product (operand scaling + hi/lo packing +
+tcgen05 tensor-core GEMM) of the square FP32 workload n = m = p = 8192,
+entries uniform[-1,1) from seeds 0 (A) and 1 (B), through the C ABI on
+device-resident operands (inputs larger than L2: 268 MB per operand and per
+packed operand).  Metric: useful TFLOP/s = 2 n m p / time.
+
+Also reported on the same line: the plain SIMT FP32 and FP64 paths at the
+same size (the split path's target is >= 3x the SIMT rate), the dominant
+kernel's roofline, the end-to-end rate through mm_gemm with pinned host
+buffers, the CPU oracle's rate on a bounded sample, clocks during the timed
+region, and the count of library kernel launches.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+
+--impl reference times the CPU oracle (the FP64 evaluation of the definition
+in Listing 1's order) on a bounded sample of the same workload: there is no
+reference implementation of this GPU path to run.
+Multi-GPU (torchrun): every rank runs its own product (independent problems,
+weak scaling); no collective touches the data, only a barrier and a max of
+the times.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_DEFAULT = 8192
+WORKLOAD = "square FP32 GEMM n=m=p=8192, uniform[-1,1) seeds 0/1, split-BF16x3 tcgen05"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.path or not os.path.exists(self.path):
+            return out
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[4:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return out
+        loaded = [r for r in rows if r[2] > 300.0] or rows
+        out["sm_mhz"] = statistics.median(r[0] for r in loaded)
+        out["sm_max_mhz"] = max(r[1] for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        seen = set()
+        for r in loaded:
+            for name, v in zip(names, r[3][1:]):
+                if v.lower().startswith("active"):
+                    seen.add(name)
+        out["reasons"] = sorted(seen)
+        out["samples"] = len(loaded)
+        out["power_w_max"] = max(r[2] for r in rows)
+        return out
+
+
+def oracle_sample_rate(n: int, target_s: float = 12.0, cap_rows: int = 4096):
+    """FP64 oracle (all host cores) on a block of rows of the n^3 workload:
+    returns (TFLOP/s, cores, rows, seconds)."""
+    import numpy as np
+
+    import oracle
+    import synth
+    orc = oracle.default()
+    cores = orc.default_threads()
+    B = synth.uniform_pm1(1, (n, n)).astype(np.float64)
+
+    def run(rows):
+        A = synth.uniform_pm1(0, (rows, n)).astype(np.float64)
+        t0 = time.perf_counter()
+        orc.gemm(A, B, threads=cores)
+        return time.perf_counter() - t0
+
+    rows = max(cores, 8)
+    t = run(rows)
+    while t < 1.0 and rows < cap_rows:
+        rows = min(cap_rows, rows * 4)
+        t = run(rows)
+    if t < target_s and rows < cap_rows:
+        rows = min(cap_rows, max(rows, int(rows * target_s / max(t, 1e-3))))
+        t = run(rows)
+    return 2.0 * rows * n * n / t / 1e12, cores, rows, t
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    n = args.size
+    import oracle
+    orc = oracle.default()
+    cores = orc.default_threads()
+    rates = []
+    rows_used = 0
+    for _ in range(args.warmup):
+        oracle_sample_rate(n, target_s=2.0, cap_rows=256)
+    for _ in range(args.steps):
+        r, cores, rows_used, _ = oracle_sample_rate(n, target_s=6.0, cap_rows=1024)
+        rates.append(r)
+    value = statistics.median(rates)
+    sample = "%d of %d rows of C (FP64 oracle, Listing 1 order, %d threads)" % (rows_used, n, cores)
+    line = {
+        "impl": "reference", "metric": "GEMM TFLOP/s", "value": value, "unit": "TFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 2.0 * n ** 3 / (value * 1e12) * 1e3 if value > 0 else None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD.replace("split-BF16x3 tcgen05", "CPU FP64 oracle"),
+                   "n": n, "m": n, "p": n},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def _traffic_from_profiles(name: str):
+    """DRAM bytes per launch of a kernel from its committed ncu summary
+    (a line 'dram_bytes_per_launch: <int>' with the command that made it)."""
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        for line in open(path):
+            if line.startswith("dram_bytes_per_launch:"):
+                return float(line.split(":", 1)[1].split()[0])
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def run_mine(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1306_6192_gb300 as mm
+    import synth
+
+    mm.check_status(mm.mm_init(device=local), "mm_init")
+    n = args.size
+    flops = 2.0 * n * n * n
+    # every rank multiplies its own operands (independent problems)
+    A = torch.from_numpy(synth.uniform_pm1(0 + 2 * rank, (n, n))).cuda()
+    B = torch.from_numpy(synth.uniform_pm1(1 + 2 * rank, (n, n))).cuda()
+    C = torch.empty((n, n), device="cuda")
+    stream = torch.cuda.Stream()
+    mode = {"split": mm.MM_MODE_SPLIT_BF16X3, "simt": mm.MM_MODE_SIMT}[args.mode]
+
+    def step(md=mode, a=A, b=B, c=C, dt=mm.MM_F32):
+        st = mm.mm_gemm_async(n, n, n, a, b, c, dt, md, stream)
+        if st != mm.MM_OK:
+            raise mm.MMError(st, "mm_gemm_async")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def timed(fn, steps, warmup, trace=False):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        mm.check_status(mm.mm_sync(stream), "warmup")
+        barrier()
+        torch.cuda.synchronize()
+        if trace:
+            mm.mm_trace_reset()
+            mm.mm_trace_enable(True)
+        l0 = mm.mm_launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches = mm.mm_launch_count() - l0
+        barrier()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if trace:
+            mm.mm_trace_enable(False)
+        mm.check_status(mm.mm_sync(stream), "timed")
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, launches
+
+    with Clocks(local) as clk:
+        ms, launches = timed(step, args.steps, args.warmup, trace=True)
+    clocks = clk.summary()
+    per_kernel = {}
+    for k in ("split_scale", "split_pack", "split_tc", "simt_f32"):
+        st, cnt, kms = mm.mm_trace_read(k)
+        if cnt:
+            per_kernel[k] = {"launches": cnt, "avg_ms": kms / cnt}
+    mm.mm_trace_reset()
+    ms_step = ms / args.steps
+    value = world * flops / (ms_step * 1e-3) / 1e12
+
+    peaks, peak_src = _peaks()
+    line = {
+        "metric": "GEMM TFLOP/s", "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3->f32" if args.mode == "split" else "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.mode == "split" else WORKLOAD.replace(
+                       "split-BF16x3 tcgen05", "SIMT FP32"),
+                   "n": n, "m": n, "p": n, "mode": args.mode,
+                   "l2": "inputs larger than L2 (268 MB per operand)",
+                   "parallelism": "replicas x%d" % world},
+        "gpu_launches": launches, "clocks": clocks, "kernels": per_kernel,
+    }
+    if args.mode == "split" and "split_tc" in per_kernel:
+        avg = per_kernel["split_tc"]["avg_ms"]
+        peak = peaks.get("bf16_tflops_sustained", 1700.0) / 3.0
+        ach = flops / (avg * 1e-3) / 1e12
+        line["roofline"] = {
+            "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "traffic": _traffic_from_profiles("split_tc_8192.txt"),
+            "kernel": "split_tc",
+            "peak_note": "%s sustained BF16 dense / 3 (three BF16 products per useful FMA)" % peak_src,
+        }
+
+    if rank == 0 and not args.quick:
+        # other paths at the same size, for the split/SIMT ratio and FP64 rate
+        extra = {}
+        if args.mode == "split":
+            ms_s, _ = timed(lambda: step(mm.MM_MODE_SIMT), max(2, args.steps // 4), 1)
+            extra["simt_f32_tflops"] = flops / (ms_s / max(2, args.steps // 4) * 1e-3) / 1e12
+            extra["split_over_simt"] = value / world / extra["simt_f32_tflops"]
+        nd = args.dgemm_size
+        A64 = A[:nd, :nd].double().contiguous()
+        B64 = B[:nd, :nd].double().contiguous()
+        C64 = torch.empty((nd, nd), device="cuda", dtype=torch.float64)
+        f64 = lambda: mm.mm_gemm_async(nd, nd, nd, A64, B64, C64, mm.MM_F64, mm.MM_MODE_DGEMM,
+                                       stream)
+        ms_d, _ = timed(f64, 2, 1)
+        extra["dgemm_f64_tflops"] = 2.0 * nd ** 3 / (ms_d / 2 * 1e-3) / 1e12
+        extra["dgemm_size"] = nd
+        del A64, B64, C64
+        line["paths"] = extra
+
+        # end to end: mm_gemm with pinned host operands, copies inside the timing
+        Ah = A.cpu().pin_memory()
+        Bh = B.cpu().pin_memory()
+        Ch = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        torch.cuda.synchronize()
+        mm.check_status(mm.mm_gemm(n, n, n, Ah, Bh, Ch, mm.MM_F32, mode), "e2e warmup")
+        k = max(2, args.steps // 4)
+        t0 = time.perf_counter()
+        for _ in range(k):
+            mm.check_status(mm.mm_gemm(n, n, n, Ah, Bh, Ch, mm.MM_F32, mode), "e2e")
+        t_e2e = (time.perf_counter() - t0) / k
+        line["e2e"] = {"value": flops / t_e2e / 1e12, "unit": "TFLOP/s",
+                       "h2d_bytes_per_step": 2 * n * n * 4, "d2h_bytes_per_step": n * n * 4}
+        del Ah, Bh, Ch
+
+    if rank == 0 and not args.no_cpu_baseline and not args.quick:
+        rate, cores, rows, t = oracle_sample_rate(n)
+        line["cpu_baseline"] = {"value": rate, "unit": "TFLOP/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": "%d of %d rows of C, FP64, %.1f s" % (rows, n, t)}
+    mm.mm_shutdown()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
+    ap.add_argument("--size", type=int, default=N_DEFAULT)
+    ap.add_argument("--mode", choices=["split", "simt"], default="split")
+    ap.add_argument("--dgemm-size", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="headline step only")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "mine":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_mine(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

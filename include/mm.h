@@ -1,0 +1,217 @@
+/*
+ * mm.h - C ABI of the GB300 dense matrix-product library.
+ *
+ * The library computes the Cauchy product C = A.B of a row-major n x m matrix
+ * A and a row-major m x p matrix B:
+ *
+ *     c_ij = sum_{r=1..m} a_ir * b_rj,   1 <= i <= n, 1 <= j <= p
+ *
+ * (paper: Swierczewski, "Akceleracja obliczen algebry liniowej ...", Section
+ * "Implementacje algorytmow", the definition of the Cauchy product; storage
+ * as in its Listing 1: A[i*m + k], B[k*p + j], C[i*p + j]).  All matrices are
+ * dense: the leading dimension is the number of columns.
+ *
+ * Paths (selected by mm_mode):
+ *   MM_MODE_SIMT          FP32 in/out, FP32 FMA on the CUDA cores, shared-
+ *                         memory tiled with register blocking.  The paper's
+ *                         Listing 4 (shared-memory tiling) is its ancestor.
+ *   MM_MODE_SPLIT_BF16X3  FP32 in/out on the tensor cores: every operand is
+ *                         scaled per row (A) / per column (B) by a power of
+ *                         two and split into bf16 hi + lo parts; the product
+ *                         is accumulated in FP32 as hi.hi + hi.lo + lo.hi
+ *                         (tcgen05 MMA, accumulator in tensor memory) and
+ *                         unscaled exactly.  Not in the paper.
+ *   MM_MODE_DGEMM         FP64 in/out, FP64 FMA.  The paper's Table 2
+ *                         "double" column computes this product in double.
+ *   MM_MODE_FP8           FP32 in/out through e4m3 operands with per-tile
+ *                         power-of-two scales; accuracy is reported, not
+ *                         guaranteed.  Not in the paper.
+ *   MM_MODE_AUTO          SPLIT_BF16X3 for MM_F32, DGEMM for MM_F64.
+ *
+ * Accuracy contract (measured against an FP64 CPU evaluation of the
+ * definition): max_ij |c^_ij - c_ij| / (|A|.|B|)_ij <= 1e-6*sqrt(m) for SIMT
+ * and SPLIT_BF16X3, <= 1e-14*sqrt(m) for DGEMM, for finite inputs whose
+ * products stay in range.
+ *
+ * Conventions for every entry point:
+ *   - Return value: MM_OK or an error code; no function aborts or prints.
+ *   - Device pointers are CUDA device (or managed) memory of the library's
+ *     device.  mm_gemm also accepts host pointers (pageable or pinned): it
+ *     then stages the operands through library-owned device buffers.
+ *   - The caller owns A, B, C.  The library owns its scratch: packed bf16
+ *     operand splits, scale exponents, problem tables, tensor memory.
+ *   - n, m, p >= 0.  n == 0 or p == 0 is a no-op; m == 0 writes C = 0.
+ *   - dtype/mode mismatch (MM_F64 with SIMT/SPLIT/FP8, MM_F32 with DGEMM)
+ *     returns MM_EUNSUPPORTED.
+ *   - A sticky CUDA error (the context is lost) returns MM_ECUDA from then on.
+ *   - Device-side waits are bounded; a wait that runs out sets a device flag
+ *     that the next synchronising call reports as MM_ETIMEOUT.
+ *   - Not thread-safe except mm_submit / mm_poll / mm_wait, which may be
+ *     called from any thread while the serving loop runs.
+ */
+#ifndef MM_H
+#define MM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MM_OK = 0,
+  MM_EINVAL = 1,       /* bad argument (negative size, null pointer, ...) */
+  MM_ENOMEM = 2,       /* device or host allocation failed */
+  MM_EBUDGET = 3,      /* request larger than the serving HBM budget */
+  MM_EBUSY = 4,        /* mm_init called twice */
+  MM_ENOTFOUND = 5,    /* unknown request id */
+  MM_EPENDING = 6,     /* request not finished yet */
+  MM_ETIMEOUT = 7,     /* a bounded wait ran out (device or host side) */
+  MM_ECUDA = 8,        /* CUDA runtime/driver error */
+  MM_ENOTINIT = 9,     /* mm_init not called */
+  MM_EUNSUPPORTED = 10,/* dtype/mode combination or device not supported */
+  MM_ECANCELLED = 11   /* request cancelled by mm_shutdown */
+} mm_status;
+
+typedef enum { MM_F32 = 0, MM_F64 = 1 } mm_dtype;
+
+typedef enum {
+  MM_MODE_SIMT = 0,
+  MM_MODE_SPLIT_BF16X3 = 1,
+  MM_MODE_DGEMM = 2,
+  MM_MODE_FP8 = 3,
+  MM_MODE_AUTO = 4
+} mm_mode;
+
+typedef struct {
+  size_t hbm_budget_bytes; /* serving admission budget; 0 selects 40 GiB */
+  int n_streams;           /* serving streams; 0 selects 2 */
+  const char *tune_table;  /* autotuner table to load; NULL: built-in choice */
+  int check;               /* 1: the serving loop checks every result on the
+                              GPU (Freivalds + sampled entries, FP64) */
+  int device;              /* CUDA device ordinal; -1 keeps the current one */
+} mm_opts;
+
+/* One independent product C = A.B (row-major, dense; see conventions). */
+typedef struct {
+  int64_t n, m, p;
+  const void *A;
+  const void *B;
+  void *C;
+} mm_problem;
+
+/* Library set-up.  opts may be NULL (defaults).  Selects the device, creates
+ * the library stream and checks that the device is sm_103 (B300 class).
+ * Returns MM_EBUSY if already initialised, MM_EUNSUPPORTED on another GPU. */
+mm_status mm_init(const mm_opts *opts);
+
+/* Stops the serving loop (pending requests end MM_ECANCELLED), waits for the
+ * library's streams and frees every library allocation.  Idempotent. */
+mm_status mm_shutdown(void);
+
+/* Static string for a status code. */
+const char *mm_strerror(mm_status s);
+
+/* C = A.B (paper: definition of the Cauchy product; Listing 1 storage).
+ * A: n x m, B: m x p, C: n x p of dtype dt, row-major and dense.  Device or
+ * host pointers (host: staged through library buffers).  Synchronous: returns
+ * when C is written.  C is fully overwritten and must not alias A or B. */
+mm_status mm_gemm(int64_t n, int64_t m, int64_t p, const void *A, const void *B,
+                  void *C, mm_dtype dt, mm_mode mode);
+
+/* As mm_gemm, but device pointers only and asynchronous: the work is queued on
+ * `stream` (a cudaStream_t; NULL = the library stream) and the call returns
+ * after the launches.  Calls that use the split or FP8 path share the
+ * library's scratch and must be ordered on one stream. */
+mm_status mm_gemm_async(int64_t n, int64_t m, int64_t p, const void *A,
+                        const void *B, void *C, mm_dtype dt, mm_mode mode,
+                        void *stream);
+
+/* count independent products in one persistent launch per path (grouped
+ * GEMM).  probs is a host array; A/B/C inside it are device pointers.  Tile
+ * shapes and raster order come from the autotuner table.  Synchronous. */
+mm_status mm_gemm_grouped(int32_t count, const mm_problem *probs, mm_dtype dt,
+                          mm_mode mode);
+mm_status mm_gemm_grouped_async(int32_t count, const mm_problem *probs,
+                                mm_dtype dt, mm_mode mode, void *stream);
+
+/* Waits for `stream` (NULL = library stream) and reports a device-side
+ * timeout flag (MM_ETIMEOUT) or a CUDA error raised by earlier async calls. */
+mm_status mm_sync(void *stream);
+
+/* FP64 check of a computed product on the GPU.
+ * Freivalds' test: y = C.x and z = A.(B.x) in FP64 with x (device, length p,
+ * FP64) given; out[0] = max_i |y_i - z_i| / (|A|.(|B|.|x|))_i.
+ * Sampled entries: for t < nsamples, (I[t], J[t]) (device int64 arrays):
+ * out[1] = max_t |C_IJ - (A.B)_IJ| / (|A|.|B|)_IJ with the dot product in
+ * FP64.  out (host, 2 doubles) receives both; a zero normaliser with a
+ * non-zero difference gives +inf.  dt gives the element type of A, B, C.
+ * Synchronous. */
+mm_status mm_check(int64_t n, int64_t m, int64_t p, const void *A,
+                   const void *B, const void *C, mm_dtype dt, const double *x,
+                   int64_t nsamples, const int64_t *I, const int64_t *J,
+                   double *out);
+
+/* ----------------------------------------------------------------- serving */
+
+/* Queues one request (device pointers; they must stay valid until mm_poll or
+ * mm_wait reports a final status).  Admission: the request's operand, output
+ * and scratch bytes must fit the HBM budget; a request that can never fit
+ * returns MM_EBUDGET immediately.  *id_out receives the request id. */
+mm_status mm_submit(const mm_problem *pr, mm_dtype dt, mm_mode mode,
+                    uint64_t *id_out);
+
+/* Non-blocking status of a request.  Returns MM_EPENDING while queued or
+ * running, MM_ENOTFOUND for an unknown id, else MM_OK with *result = the
+ * product's own status, *err_out = the GPU check's max normalised error (or
+ * -1 when checking is off), *latency_ms_out = completion - submission time.
+ * A request is forgotten after its final status has been returned once. */
+mm_status mm_poll(uint64_t id, mm_status *result, double *err_out,
+                  double *latency_ms_out);
+
+/* Blocks until the request finishes or timeout_s passes (MM_ETIMEOUT); then
+ * as mm_poll. */
+mm_status mm_wait(uint64_t id, double timeout_s, mm_status *result,
+                  double *err_out, double *latency_ms_out);
+
+/* Serving counters: completed requests, batches launched, requests waiting,
+ * resident bytes admitted now.  Any pointer may be NULL. */
+mm_status mm_serve_stats(int64_t *completed, int64_t *batches,
+                         int64_t *waiting, int64_t *resident_bytes);
+
+/* --------------------------------------------------------------- autotuner */
+
+/* Times the candidate tile configurations of the split path for products of
+ * size n x m x p on the device (scratch operands, reps repetitions each) and
+ * records the fastest for the size bucket of (n, m, p).  Synchronous. */
+mm_status mm_tune(int64_t n, int64_t m, int64_t p, int reps);
+
+/* Writes / reads the tuning table (text, one bucket per line). */
+mm_status mm_tune_save(const char *path);
+mm_status mm_tune_load(const char *path);
+
+/* Tile configuration the split path would use for (n, m, p): block N width,
+ * K depth, pipeline stages and raster group height. */
+mm_status mm_tune_query(int64_t n, int64_t m, int64_t p, int *bn, int *bk,
+                        int *stages, int *group_m);
+
+/* ----------------------------------------------------------------- tracing */
+
+/* When enabled, every kernel the library launches is bracketed by CUDA events
+ * on its stream; mm_trace_read returns the launch count and summed device
+ * time (ms) of the kernel named `kernel` ("simt_f32", "dgemm_f64",
+ * "split_scale", "split_pack", "split_tc", "fp8_tc", "check_f64") since the
+ * last reset.  Reading synchronises the recorded events. */
+mm_status mm_trace_enable(int on);
+mm_status mm_trace_reset(void);
+mm_status mm_trace_read(const char *kernel, int64_t *launches, double *total_ms);
+
+/* Number of library kernel launches since mm_init (all kernels). */
+int64_t mm_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MM_H */

@@ -1,0 +1,557 @@
+// C ABI of the library (include/mm.h): context, scratch memory, dispatch to
+// the kernels, tracing.  The serving loop lives in serve.cu, the autotuner
+// table in tune.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <map>
+
+#include "ctx.h"
+
+namespace mm {
+
+Ctx g_ctx;
+std::mutex g_api_mutex;
+
+// ---------------------------------------------------------------- errors
+mm_status from_cuda(cudaError_t e) {
+  switch (e) {
+    case cudaSuccess: return MM_OK;
+    case cudaErrorMemoryAllocation: return MM_ENOMEM;
+    case cudaErrorInvalidValue: return MM_EINVAL;
+    case cudaErrorNotSupported: return MM_EUNSUPPORTED;
+    default: return MM_ECUDA;
+  }
+}
+
+// A sticky error (illegal address, launch failure ...) loses the context: the
+// library then refuses further work.
+static mm_status note_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return MM_OK;
+  cudaError_t last = cudaGetLastError();
+  (void)last;
+  cudaError_t probe = cudaDeviceSynchronize();
+  if (probe != cudaSuccess && probe != cudaErrorNotReady) g_ctx.sticky = true;
+  return from_cuda(e);
+}
+
+int sm_count() { return g_ctx.sms > 0 ? g_ctx.sms : 148; }
+
+// ---------------------------------------------------------------- scratch
+cudaError_t Scratch::reserve(size_t need, cudaStream_t s) {
+  if (need <= bytes) return cudaSuccess;
+  if (ptr) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+  }
+  size_t want = std::max(need, bytes + bytes / 4);
+  want = (want + (1u << 20) - 1) & ~(size_t)((1u << 20) - 1);
+  cudaError_t e = cudaMalloc(&ptr, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    e = cudaMalloc(&ptr, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      ptr = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+    want = need;
+  }
+  bytes = want;
+  return cudaSuccess;
+}
+
+void Scratch::release() {
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+  bytes = 0;
+}
+
+// ---------------------------------------------------------------- tracing
+namespace {
+struct TraceRec {
+  const char *name;
+  cudaEvent_t a, b;
+};
+std::mutex g_trace_mu;
+bool g_trace_on = false;
+std::vector<TraceRec> g_trace_open;   // begun, waiting for end
+std::vector<TraceRec> g_trace_done;
+std::vector<cudaEvent_t> g_event_pool;
+std::atomic<int64_t> g_launches{0};
+
+cudaEvent_t take_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+}  // namespace
+
+void trace_begin(const char *name, cudaStream_t s) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  if (!g_trace_on) return;
+  TraceRec r{name, take_event(), take_event()};
+  cudaEventRecord(r.a, s);
+  g_trace_open.push_back(r);
+}
+
+void trace_end(const char *name, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  if (!g_trace_on) return;
+  for (size_t i = g_trace_open.size(); i-- > 0;) {
+    if (g_trace_open[i].name == name) {
+      TraceRec r = g_trace_open[i];
+      g_trace_open.erase(g_trace_open.begin() + (long)i);
+      cudaEventRecord(r.b, s);
+      g_trace_done.push_back(r);
+      return;
+    }
+  }
+}
+
+void trace_clear() {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  for (auto &r : g_trace_done) {
+    g_event_pool.push_back(r.a);
+    g_event_pool.push_back(r.b);
+  }
+  g_trace_done.clear();
+}
+
+static void trace_destroy() {
+  trace_clear();
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  for (auto &r : g_trace_open) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  g_trace_open.clear();
+  for (auto e : g_event_pool) cudaEventDestroy(e);
+  g_event_pool.clear();
+  g_trace_on = false;
+}
+
+// ---------------------------------------------------------------- pointers
+// Classifies a pointer: 1 = device-accessible (device or managed memory of
+// the current device), 0 = host memory (pinned or pageable), -1 = invalid.
+int pointer_kind(const void *p) {
+  if (!p) return -1;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  switch (at.type) {
+    case cudaMemoryTypeDevice:
+    case cudaMemoryTypeManaged: return 1;
+    default: return 0;
+  }
+}
+
+// ---------------------------------------------------------------- split path
+// Builds the problem table of the split path for `count` products, lays out
+// the scratch (pack rows, scale arrays, table), and launches prep + tensor-
+// core kernels on stream s.  Problems with n == 0 or p == 0 are skipped;
+// m == 0 writes zeros.
+mm_status run_split(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s,
+                    const TcChoice *force) {
+  std::vector<SplitProb> tab;
+  tab.reserve(count);
+  int64_t rows = 0, scal = 0;
+  int64_t tiles = 0, packs = 0, reds = 0;
+  TcConfig cfg{0, 0, 0};
+  for (int g = 0; g < count; g++) {
+    const mm_problem &q = probs[g];
+    if (q.n == 0 || q.p == 0) continue;
+    if (q.m == 0) {
+      cudaError_t e = cudaMemsetAsync(q.C, 0, (size_t)(q.n * q.p) * sizeof(float), s);
+      if (e != cudaSuccess) return note_cuda(e);
+      continue;
+    }
+    TcChoice ch = force ? *force : tune_choose(q.n, q.m, q.p);
+    if (tab.empty()) cfg = TcConfig{ch.bk, ch.stages, ch.grid};
+    SplitProb sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.A = static_cast<const float *>(q.A);
+    sp.B = static_cast<const float *>(q.B);
+    sp.C = static_cast<float *>(q.C);
+    sp.n = (int32_t)q.n;
+    sp.m = (int32_t)q.m;
+    sp.p = (int32_t)q.p;
+    sp.bn = ch.bn;
+    sp.group_m = ch.group_m;
+    sp.mt = (int32_t)ceil_div(q.n, kTcBM);
+    sp.nt = (int32_t)ceil_div(q.p, ch.bn);
+    sp.kt = (int32_t)ceil_div(q.m, kPackK);
+    sp.a_row0 = rows;
+    rows += (int64_t)sp.mt * sp.kt * 2 * kTcBM;
+    sp.b_row0 = rows;
+    rows += (int64_t)sp.nt * sp.kt * 2 * ch.bn;
+    sp.sA = reinterpret_cast<uint32_t *>((uintptr_t)scal);  // offset, fixed below
+    scal += q.n;
+    sp.tB = reinterpret_cast<uint32_t *>((uintptr_t)scal);
+    scal += q.p;
+    sp.tile_start = (int32_t)tiles;
+    tiles += (int64_t)sp.mt * sp.nt;
+    sp.pack_start = (int32_t)packs;
+    packs += (int64_t)sp.mt * sp.kt + (int64_t)sp.nt * sp.kt;
+    sp.red_start = (int32_t)reds;
+    sp.red_a = (int32_t)ceil_div(q.n, 8);
+    reds += sp.red_a + ceil_div(q.p, 32) * ceil_div(q.m, 256);
+    tab.push_back(sp);
+  }
+  if (tab.empty()) return MM_OK;
+  if (tiles > 0x7fffffffLL || packs > 0x7fffffffLL || reds > 0x7fffffffLL ||
+      rows > 0x7fffffffLL)
+    return MM_EINVAL;
+  const size_t pack_bytes = (size_t)rows * kPackRowBytes;
+  const size_t scal_off = (pack_bytes + 255) & ~(size_t)255;
+  const size_t tab_off = (scal_off + (size_t)scal * 4 + 255) & ~(size_t)255;
+  const size_t need = tab_off + tab.size() * sizeof(SplitProb);
+  cudaError_t e = ws.reserve(need, s);
+  if (e != cudaSuccess) return note_cuda(e);
+  uint8_t *base = static_cast<uint8_t *>(ws.ptr);
+  for (auto &sp : tab) {
+    sp.sA = reinterpret_cast<uint32_t *>(base + scal_off) + (uintptr_t)sp.sA;
+    sp.tB = reinterpret_cast<uint32_t *>(base + scal_off) + (uintptr_t)sp.tB;
+  }
+  SplitProb *d_tab = reinterpret_cast<SplitProb *>(base + tab_off);
+  e = cudaMemcpyAsync(d_tab, tab.data(), tab.size() * sizeof(SplitProb),
+                      cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return note_cuda(e);
+  e = cudaMemsetAsync(base + scal_off, 0, (size_t)scal * 4, s);
+  if (e != cudaSuccess) return note_cuda(e);
+  const int np = (int)tab.size();
+  e = launch_split_scale(d_tab, np, (int)reds, s);
+  if (e != cudaSuccess) return note_cuda(e);
+  e = launch_split_pack(d_tab, np, (int)packs, base, s);
+  if (e != cudaSuccess) return note_cuda(e);
+  e = launch_split_tc(d_tab, np, (int)tiles, base, rows, cfg, g_ctx.d_err, s);
+  if (e != cudaSuccess) return note_cuda(e);
+  return MM_OK;
+}
+
+// ---------------------------------------------------------------- dispatch
+static mm_mode resolve_mode(mm_dtype dt, mm_mode mode) {
+  if (mode == MM_MODE_AUTO) return dt == MM_F64 ? MM_MODE_DGEMM : MM_MODE_SPLIT_BF16X3;
+  return mode;
+}
+
+mm_status validate(int64_t n, int64_t m, int64_t p, mm_dtype dt, mm_mode mode) {
+  if (n < 0 || m < 0 || p < 0) return MM_EINVAL;
+  if (dt != MM_F32 && dt != MM_F64) return MM_EINVAL;
+  if ((int)mode < 0 || (int)mode > (int)MM_MODE_AUTO) return MM_EINVAL;
+  const mm_mode md = resolve_mode(dt, mode);
+  if (dt == MM_F64 && md != MM_MODE_DGEMM) return MM_EUNSUPPORTED;
+  if (dt == MM_F32 && md == MM_MODE_DGEMM) return MM_EUNSUPPORTED;
+  // 32-bit tile bookkeeping of the kernels
+  if (n > (int64_t)1 << 31 || m > (int64_t)1 << 31 || p > (int64_t)1 << 31) return MM_EINVAL;
+  return MM_OK;
+}
+
+// Queues C = A.B (device pointers) on stream s.
+mm_status enqueue_gemm(int64_t n, int64_t m, int64_t p, const void *A, const void *B, void *C,
+                       mm_dtype dt, mm_mode mode, cudaStream_t s) {
+  const mm_mode md = resolve_mode(dt, mode);
+  if (n == 0 || p == 0) return MM_OK;
+  if (m == 0) {
+    const size_t es = dt == MM_F64 ? 8 : 4;
+    return note_cuda(cudaMemsetAsync(C, 0, (size_t)(n * p) * es, s));
+  }
+  switch (md) {
+    case MM_MODE_SIMT:
+      return note_cuda(launch_simt_f32(n, m, p, (const float *)A, (const float *)B, (float *)C, s));
+    case MM_MODE_DGEMM:
+      return note_cuda(
+          launch_simt_f64(n, m, p, (const double *)A, (const double *)B, (double *)C, s));
+    case MM_MODE_SPLIT_BF16X3: {
+      mm_problem q{n, m, p, A, B, C};
+      return run_split(g_ctx.split_ws, &q, 1, s, nullptr);
+    }
+    case MM_MODE_FP8: {
+      mm_problem q{n, m, p, A, B, C};
+      return run_fp8(g_ctx.fp8_ws, &q, 1, s);
+    }
+    default: return MM_EINVAL;
+  }
+}
+
+mm_status check_device_flag(cudaStream_t s) {
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return note_cuda(e);
+  int flag = 0;
+  e = cudaMemcpy(&flag, g_ctx.d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return note_cuda(e);
+  if (flag != 0) {
+    cudaMemset(g_ctx.d_err, 0, sizeof(int));
+    return MM_ETIMEOUT;
+  }
+  return MM_OK;
+}
+
+}  // namespace mm
+
+using namespace mm;
+
+#define MM_REQUIRE_INIT()                    \
+  do {                                       \
+    if (!g_ctx.inited) return MM_ENOTINIT;   \
+    if (g_ctx.sticky) return MM_ECUDA;       \
+  } while (0)
+
+extern "C" {
+
+const char *mm_strerror(mm_status s) {
+  switch (s) {
+    case MM_OK: return "ok";
+    case MM_EINVAL: return "invalid argument";
+    case MM_ENOMEM: return "out of memory";
+    case MM_EBUDGET: return "request exceeds the HBM budget";
+    case MM_EBUSY: return "already initialised";
+    case MM_ENOTFOUND: return "unknown request id";
+    case MM_EPENDING: return "request pending";
+    case MM_ETIMEOUT: return "bounded wait timed out";
+    case MM_ECUDA: return "CUDA error";
+    case MM_ENOTINIT: return "library not initialised";
+    case MM_EUNSUPPORTED: return "unsupported dtype/mode or device";
+    case MM_ECANCELLED: return "request cancelled";
+  }
+  return "unknown status";
+}
+
+mm_status mm_init(const mm_opts *opts) {
+  std::lock_guard<std::mutex> lk(g_api_mutex);
+  if (g_ctx.inited) return MM_EBUSY;
+  mm_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.device = -1;
+  if (opts) o = *opts;
+  if (o.hbm_budget_bytes == 0) o.hbm_budget_bytes = (size_t)40 << 30;
+  if (o.n_streams <= 0) o.n_streams = 2;
+  if (o.n_streams > 8) o.n_streams = 8;
+  int dev = 0;
+  cudaError_t e;
+  if (o.device >= 0) {
+    e = cudaSetDevice(o.device);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return from_cuda(e);
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return from_cuda(e);
+  // The kernels are built for sm_103a only.
+  if (prop.major != 10 || prop.minor != 3) return MM_EUNSUPPORTED;
+  g_ctx.device = dev;
+  g_ctx.sms = prop.multiProcessorCount;
+  g_ctx.opts = o;
+  e = cudaStreamCreateWithFlags(&g_ctx.stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return from_cuda(e);
+  e = cudaMalloc(&g_ctx.d_err, 256);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(g_ctx.stream);
+    return from_cuda(e);
+  }
+  cudaMemset(g_ctx.d_err, 0, 256);
+  tune_reset_defaults();
+  if (o.tune_table) {
+    mm_status st = tune_load_file(o.tune_table);
+    if (st != MM_OK) {
+      cudaFree(g_ctx.d_err);
+      cudaStreamDestroy(g_ctx.stream);
+      return st;
+    }
+  }
+  g_ctx.sticky = false;
+  g_ctx.inited = true;
+  mm_status st = serve_start();
+  if (st != MM_OK) {
+    g_ctx.inited = false;
+    cudaFree(g_ctx.d_err);
+    cudaStreamDestroy(g_ctx.stream);
+    return st;
+  }
+  return MM_OK;
+}
+
+mm_status mm_shutdown(void) {
+  std::lock_guard<std::mutex> lk(g_api_mutex);
+  if (!g_ctx.inited) return MM_OK;
+  serve_stop();
+  cudaStreamSynchronize(g_ctx.stream);
+  g_ctx.split_ws.release();
+  g_ctx.fp8_ws.release();
+  g_ctx.stage_ws.release();
+  g_ctx.check_ws.release();
+  if (g_ctx.d_err) cudaFree(g_ctx.d_err);
+  g_ctx.d_err = nullptr;
+  trace_destroy();
+  cudaStreamDestroy(g_ctx.stream);
+  g_ctx.stream = nullptr;
+  g_ctx.inited = false;
+  return MM_OK;
+}
+
+mm_status mm_gemm_async(int64_t n, int64_t m, int64_t p, const void *A, const void *B, void *C,
+                        mm_dtype dt, mm_mode mode, void *stream) {
+  MM_REQUIRE_INIT();
+  mm_status st = validate(n, m, p, dt, mode);
+  if (st != MM_OK) return st;
+  if (n == 0 || p == 0) return MM_OK;
+  if (!C || (m > 0 && (!A || !B))) return MM_EINVAL;
+  if (pointer_kind(C) != 1 || (m > 0 && (pointer_kind(A) != 1 || pointer_kind(B) != 1)))
+    return MM_EINVAL;
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : g_ctx.stream;
+  std::lock_guard<std::mutex> lk(g_api_mutex);
+  return enqueue_gemm(n, m, p, A, B, C, dt, mode, s);
+}
+
+mm_status mm_gemm(int64_t n, int64_t m, int64_t p, const void *A, const void *B, void *C,
+                  mm_dtype dt, mm_mode mode) {
+  MM_REQUIRE_INIT();
+  mm_status st = validate(n, m, p, dt, mode);
+  if (st != MM_OK) return st;
+  if (n == 0 || p == 0) return MM_OK;
+  if (!C || (m > 0 && (!A || !B))) return MM_EINVAL;
+  std::lock_guard<std::mutex> lk(g_api_mutex);
+  cudaStream_t s = g_ctx.stream;
+  const size_t es = dt == MM_F64 ? 8 : 4;
+  const bool dev_c = pointer_kind(C) == 1;
+  const bool dev_a = m == 0 || pointer_kind(A) == 1;
+  const bool dev_b = m == 0 || pointer_kind(B) == 1;
+  if (dev_a && dev_b && dev_c) {
+    st = enqueue_gemm(n, m, p, A, B, C, dt, mode, s);
+    if (st != MM_OK) return st;
+    return check_device_flag(s);
+  }
+  // Host operands: stage through library buffers (copies on the library
+  // stream, then the same device path).
+  const size_t ba = (size_t)(n * m) * es, bb = (size_t)(m * p) * es, bc = (size_t)(n * p) * es;
+  const size_t oa = 0, ob = (ba + 255) & ~(size_t)255, oc = (ob + bb + 255) & ~(size_t)255;
+  cudaError_t e = g_ctx.stage_ws.reserve(oc + bc, s);
+  if (e != cudaSuccess) return note_cuda(e);
+  uint8_t *base = static_cast<uint8_t *>(g_ctx.stage_ws.ptr);
+  const void *dA = dev_a ? A : base + oa;
+  const void *dB = dev_b ? B : base + ob;
+  void *dC = dev_c ? C : base + oc;
+  if (!dev_a && ba) {
+    e = cudaMemcpyAsync(base + oa, A, ba, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return note_cuda(e);
+  }
+  if (!dev_b && bb) {
+    e = cudaMemcpyAsync(base + ob, B, bb, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return note_cuda(e);
+  }
+  st = enqueue_gemm(n, m, p, dA, dB, dC, dt, mode, s);
+  if (st != MM_OK) return st;
+  if (!dev_c) {
+    e = cudaMemcpyAsync(C, dC, bc, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return note_cuda(e);
+  }
+  return check_device_flag(s);
+}
+
+mm_status mm_gemm_grouped_async(int32_t count, const mm_problem *probs, mm_dtype dt,
+                                mm_mode mode, void *stream) {
+  MM_REQUIRE_INIT();
+  if (count < 0 || (count > 0 && !probs)) return MM_EINVAL;
+  for (int32_t g = 0; g < count; g++) {
+    const mm_problem &q = probs[g];
+    mm_status st = validate(q.n, q.m, q.p, dt, mode);
+    if (st != MM_OK) return st;
+    if (q.n == 0 || q.p == 0) continue;
+    if (!q.C || (q.m > 0 && (!q.A || !q.B))) return MM_EINVAL;
+  }
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : g_ctx.stream;
+  std::lock_guard<std::mutex> lk(g_api_mutex);
+  return enqueue_grouped(g_ctx.split_ws, g_ctx.grouped_ws, count, probs, dt,
+                         resolve_mode(dt, mode), s);
+}
+
+mm_status mm_gemm_grouped(int32_t count, const mm_problem *probs, mm_dtype dt, mm_mode mode) {
+  mm_status st = mm_gemm_grouped_async(count, probs, dt, mode, nullptr);
+  if (st != MM_OK) return st;
+  std::lock_guard<std::mutex> lk(g_api_mutex);
+  return check_device_flag(g_ctx.stream);
+}
+
+mm_status mm_sync(void *stream) {
+  MM_REQUIRE_INIT();
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : g_ctx.stream;
+  return check_device_flag(s);
+}
+
+mm_status mm_check(int64_t n, int64_t m, int64_t p, const void *A, const void *B, const void *C,
+                   mm_dtype dt, const double *x, int64_t nsamples, const int64_t *I,
+                   const int64_t *J, double *out) {
+  MM_REQUIRE_INIT();
+  if (n < 0 || m < 0 || p < 0 || nsamples < 0 || !out) return MM_EINVAL;
+  if (dt != MM_F32 && dt != MM_F64) return MM_EINVAL;
+  if (n == 0 || p == 0) {
+    out[0] = out[1] = 0.0;
+    return MM_OK;
+  }
+  if (!C || !x || (m > 0 && (!A || !B)) || (nsamples > 0 && (!I || !J))) return MM_EINVAL;
+  if (pointer_kind(C) != 1 || pointer_kind(x) != 1) return MM_EINVAL;
+  if (m > 0 && (pointer_kind(A) != 1 || pointer_kind(B) != 1)) return MM_EINVAL;
+  if (nsamples > 0 && (pointer_kind(I) != 1 || pointer_kind(J) != 1)) return MM_EINVAL;
+  std::lock_guard<std::mutex> lk(g_api_mutex);
+  cudaStream_t s = g_ctx.stream;
+  const size_t work = check_work_doubles(n, m, p);
+  cudaError_t e = g_ctx.check_ws.reserve((work + 2) * sizeof(double), s);
+  if (e != cudaSuccess) return note_cuda(e);
+  double *d = static_cast<double *>(g_ctx.check_ws.ptr);
+  e = launch_check(dt == MM_F64, n, m, p, A, B, C, x, nsamples, I, J, d + 2, d, s);
+  if (e != cudaSuccess) return note_cuda(e);
+  e = cudaMemcpyAsync(out, d, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return note_cuda(e);
+  e = cudaStreamSynchronize(s);
+  return note_cuda(e);
+}
+
+mm_status mm_trace_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  g_trace_on = on != 0;
+  return MM_OK;
+}
+
+mm_status mm_trace_reset(void) {
+  trace_clear();
+  return MM_OK;
+}
+
+mm_status mm_trace_read(const char *kernel, int64_t *launches, double *total_ms) {
+  if (!kernel) return MM_EINVAL;
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  int64_t cnt = 0;
+  double ms = 0.0;
+  for (auto &r : g_trace_done) {
+    if (std::strcmp(r.name, kernel) != 0) continue;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e != cudaSuccess) return from_cuda(e);
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, r.a, r.b);
+    if (e != cudaSuccess) return from_cuda(e);
+    cnt++;
+    ms += t;
+  }
+  if (launches) *launches = cnt;
+  if (total_ms) *total_ms = ms;
+  return MM_OK;
+}
+
+int64_t mm_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,71 @@
+// Library context and host-side helpers shared by api.cu, grouped.cu,
+// tune.cu, serve.cu and fp8.cu.
+#pragma once
+
+#include "mm_internal.h"
+
+namespace mm {
+
+// Grow-only device buffer owned by the library.
+struct Scratch {
+  void *ptr = nullptr;
+  size_t bytes = 0;
+  // Makes room for `need` bytes; an existing buffer is freed after `s` has
+  // drained (its contents are not kept).
+  cudaError_t reserve(size_t need, cudaStream_t s);
+  void release();
+};
+
+// Tile choice of the split path for one size bucket.
+struct TcChoice {
+  int bn;       // 128 or 256
+  int bk;       // 32 or 64
+  int stages;   // pipeline depth for that bk
+  int group_m;  // raster band height in row tiles
+  int grid;     // persistent CTAs (0 = one per SM)
+};
+
+struct Ctx {
+  bool inited = false;
+  bool sticky = false;
+  int device = 0;
+  int sms = 0;
+  mm_opts opts{};
+  cudaStream_t stream = nullptr;
+  int *d_err = nullptr;  // device-side timeout flag
+  Scratch split_ws;      // packs, scales, tables of the split path
+  Scratch fp8_ws;        // operands of the FP8 path
+  Scratch grouped_ws;    // tables of the grouped SIMT path
+  Scratch stage_ws;      // device copies of host operands
+  Scratch check_ws;      // FP64 check work vectors
+};
+
+extern Ctx g_ctx;
+extern std::mutex g_api_mutex;
+
+int pointer_kind(const void *p);
+mm_status validate(int64_t n, int64_t m, int64_t p, mm_dtype dt, mm_mode mode);
+mm_status enqueue_gemm(int64_t n, int64_t m, int64_t p, const void *A, const void *B, void *C,
+                       mm_dtype dt, mm_mode mode, cudaStream_t s);
+mm_status check_device_flag(cudaStream_t s);
+
+// Split path over a table of problems (single GEMM = table of one).
+// `force` overrides the tuned tile choice (autotuner and tests).
+mm_status run_split(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s,
+                    const TcChoice *force);
+// FP8 path (report-only accuracy).
+mm_status run_fp8(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s);
+// Grouped dispatch: split / SIMT / DGEMM tables in one launch per path.
+mm_status enqueue_grouped(Scratch &split_ws, Scratch &tab_ws, int count, const mm_problem *probs,
+                          mm_dtype dt, mm_mode mode, cudaStream_t s);
+
+// Autotuner table.
+void tune_reset_defaults();
+TcChoice tune_choose(int64_t n, int64_t m, int64_t p);
+mm_status tune_load_file(const char *path);
+
+// Serving loop.
+mm_status serve_start();
+void serve_stop();
+
+}  // namespace mm

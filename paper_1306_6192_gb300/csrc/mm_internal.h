@@ -1,0 +1,122 @@
+// Internal declarations shared by the library's translation units.
+// Not part of the public ABI (include/mm.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/mm.h"
+
+namespace mm {
+
+// ------------------------------------------------------------ tile constants
+// SIMT FP32 tile (the shared-memory tiling of the paper's Listing 4, scaled up
+// with register blocking): 128 x 128 outputs per 256-thread block, 8 x 8 per
+// thread, k-slices of 8.
+constexpr int kSimtF32BM = 128, kSimtF32BN = 128, kSimtF32BK = 8;
+// SIMT FP64 tile: 64 x 64 outputs per 256-thread block, 4 x 4 per thread.
+constexpr int kSimtF64BM = 64, kSimtF64BN = 64, kSimtF64BK = 8;
+
+// Split-BF16x3 tensor-core path: M tile is the tcgen05 M (128 rows of A);
+// packed operands are stored in blocks of 64 along K (one 128-byte row of
+// bf16 per row of the block).
+constexpr int kTcBM = 128;
+constexpr int kPackK = 64;
+constexpr int kPackRowBytes = kPackK * 2;
+
+// ------------------------------------------------------------ device tables
+// One product of the split path, as the prep and tensor-core kernels see it.
+// Pack layout (rows of kPackK bf16 inside the scratch pack region):
+//   A pack tile (mt, kb): rows a_row0 + (mt*kt + kb)*256 .. +255:
+//       rows 0..127 = hi part of A rows mt*128 .. +127 (K block kb),
+//       rows 128..255 = lo part; entries outside A are zero.
+//   B pack tile (nt, kb): rows b_row0 + (nt*kt + kb)*2*bn .. +2*bn-1:
+//       rows 0..bn-1 = hi part of B columns nt*bn .. +bn-1 (K block kb,
+//       i.e. B transposed so K is contiguous), rows bn..2bn-1 = lo part.
+// sA[i] / tB[j] hold the bit pattern of max_r |a_ir| / max_r |b_rj|; the
+// scale exponent of a row/column is derived from it (scale_exponent()).
+struct SplitProb {
+  const float *A;
+  const float *B;
+  float *C;
+  int64_t a_row0, b_row0;
+  uint32_t *sA, *tB;
+  int32_t n, m, p;
+  int32_t mt, nt, kt;      // ceil(n/128), ceil(p/bn), ceil(m/64)
+  int32_t bn, group_m;     // N tile (128 or 256), raster group height
+  int32_t tile_start;      // prefix over problems of mt*nt (MMA tiles)
+  int32_t pack_start;      // prefix of pack tiles: mt*kt + nt*kt
+  int32_t red_start;       // prefix of scale-reduction items
+  int32_t red_a;           // reduction items for A rows: ceil(n/8)
+};
+
+// One product of the grouped SIMT path (f32 or f64 elements).
+struct SimtProb {
+  const void *A;
+  const void *B;
+  void *C;
+  int64_t n, m, p;
+  int32_t tiles_n;     // tiles along p
+  int32_t tile_start;  // prefix over problems of tiles
+};
+
+// ------------------------------------------------------------ launchers
+cudaError_t launch_simt_f32(int64_t n, int64_t m, int64_t p, const float *A,
+                            const float *B, float *C, cudaStream_t s);
+cudaError_t launch_simt_f64(int64_t n, int64_t m, int64_t p, const double *A,
+                            const double *B, double *C, cudaStream_t s);
+cudaError_t launch_simt_grouped(bool f64, const SimtProb *d_probs, int nprobs,
+                                int total_tiles, bool all_vec, cudaStream_t s);
+
+// Prep: per-row/column max-abs reduction, then hi/lo split into the packs.
+cudaError_t launch_split_scale(const SplitProb *d_probs, int nprobs,
+                               int total_items, cudaStream_t s);
+cudaError_t launch_split_pack(const SplitProb *d_probs, int nprobs,
+                              int total_tiles, void *pack_base,
+                              cudaStream_t s);
+
+// Tensor-core mainloop + epilogue over all tiles of all problems.
+struct TcConfig {
+  int bk;       // 32 or 64 (K per pipeline stage)
+  int stages;   // pipeline depth
+  int grid;     // persistent CTAs (<= number of SMs)
+};
+cudaError_t launch_split_tc(const SplitProb *d_probs, int nprobs,
+                            int total_tiles, void *pack_base,
+                            int64_t pack_rows, const TcConfig &cfg,
+                            int *d_err, cudaStream_t s);
+
+// FP64 check (Freivalds + sampled entries): writes 2 doubles to d_out.
+cudaError_t launch_check(bool f64, int64_t n, int64_t m, int64_t p,
+                         const void *A, const void *B, const void *C,
+                         const double *x, int64_t nsamples, const int64_t *I,
+                         const int64_t *J, double *d_work, double *d_out,
+                         cudaStream_t s);
+size_t check_work_doubles(int64_t n, int64_t m, int64_t p);
+
+// ------------------------------------------------------------ tracing
+// Brackets a launch with events when tracing is on; counts every launch.
+void trace_begin(const char *name, cudaStream_t s);
+void trace_end(const char *name, cudaStream_t s);
+void trace_clear();
+
+struct TraceScope {
+  const char *name;
+  cudaStream_t s;
+  TraceScope(const char *n, cudaStream_t st) : name(n), s(st) { trace_begin(n, st); }
+  ~TraceScope() { trace_end(name, s); }
+};
+
+int sm_count();
+
+// Status from a CUDA error code.
+mm_status from_cuda(cudaError_t e);
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace mm

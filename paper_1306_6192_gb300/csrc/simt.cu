@@ -1,0 +1,231 @@
+// Plain SIMT GEMM on the CUDA cores: C = A.B with FMA in the element type.
+//
+// Paper anchor: Listing 4 (shared-memory tiling: every block stages a tile of
+// A and a tile of B in shared memory per step along the inner dimension and
+// each thread accumulates its outputs from the staged tiles).  This is that
+// scheme sized for sm_103a: larger tiles, a register block of outputs per
+// thread (8 x 8 in FP32, 4 x 4 in FP64), 16-byte vector loads from global
+// memory, double-buffered shared memory (one barrier per K slice), and
+// predicated edges so any n, m, p works (the listing needs multiples of 16).
+//
+// Every output is accumulated by one thread with r ascending, as in the
+// definition of the Cauchy product.
+#include "mm_internal.h"
+
+namespace mm {
+namespace {
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
+
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+struct SimtShape {
+  static constexpr int W = 16 / (int)sizeof(T);  // elements per 16-byte vector
+  static constexpr int NTX = BN / TN, NTY = BM / TM;
+  static constexpr int NT = NTX * NTY;
+  static constexpr int APAD = W;                  // keeps rows 16-byte aligned
+  static_assert(TM == 2 * W && TN == 2 * W, "fragment = two 16-byte vectors");
+  static_assert(BM * BK / W == NT && BK * BN / W == NT, "one vector per thread");
+};
+
+// Loads W consecutive elements of row `row`, columns col..col+W-1 of a
+// row-major matrix (rows x cols, leading dimension ld), zero outside.
+template <typename T, bool VEC>
+__device__ __forceinline__ void load_vec(const T *__restrict__ X, int64_t ld,
+                                         int64_t rows, int64_t cols,
+                                         int64_t row, int64_t col, T (&v)[16 / sizeof(T)]) {
+  constexpr int W = 16 / (int)sizeof(T);
+  if (row < rows && col + W <= cols) {
+    if (VEC) {
+      typename Vec16<T>::type t = *reinterpret_cast<const typename Vec16<T>::type *>(X + row * ld + col);
+      const T *tp = reinterpret_cast<const T *>(&t);
+#pragma unroll
+      for (int e = 0; e < W; e++) v[e] = tp[e];
+    } else {
+#pragma unroll
+      for (int e = 0; e < W; e++) v[e] = X[row * ld + col + e];
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < W; e++)
+      v[e] = (row < rows && col + e < cols) ? X[row * ld + col + e] : T(0);
+  }
+}
+
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
+__device__ __forceinline__ void simt_tile(const T *__restrict__ A, const T *__restrict__ B,
+                                          T *__restrict__ C, int64_t n, int64_t m, int64_t p,
+                                          int64_t tile_m, int64_t tile_n) {
+  using S = SimtShape<T, BM, BN, BK, TM, TN>;
+  constexpr int W = S::W;
+  using V = typename Vec16<T>::type;
+  __shared__ __align__(16) T As[2][BK][BM + S::APAD];
+  __shared__ __align__(16) T Bs[2][BK][BN];
+
+  const int tid = threadIdx.x;
+  const int tx = tid % S::NTX, ty = tid / S::NTX;
+  const int64_t m0 = tile_m * BM, n0 = tile_n * BN;
+
+  // global -> shared mapping: one W-vector of A (along k) and of B (along n)
+  const int a_row = tid / (BK / W), a_kv = tid % (BK / W);
+  const int b_k = tid / (BN / W), b_nv = tid % (BN / W);
+
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; i++)
+#pragma unroll
+    for (int j = 0; j < TN; j++) acc[i][j] = T(0);
+
+  T ra[W], rb[W];
+  const int64_t ktiles = (m + BK - 1) / BK;
+  if (ktiles > 0) {
+    load_vec<T, VEC>(A, m, n, m, m0 + a_row, (int64_t)a_kv * W, ra);
+    load_vec<T, VEC>(B, p, m, p, (int64_t)b_k, n0 + (int64_t)b_nv * W, rb);
+#pragma unroll
+    for (int e = 0; e < W; e++) As[0][a_kv * W + e][a_row] = ra[e];
+    *reinterpret_cast<V *>(&Bs[0][b_k][b_nv * W]) = *reinterpret_cast<V *>(rb);
+  }
+  __syncthreads();
+
+  for (int64_t kt = 0; kt < ktiles; kt++) {
+    const int cur = (int)(kt & 1);
+    const bool more = kt + 1 < ktiles;
+    if (more) {
+      const int64_t k0 = (kt + 1) * BK;
+      load_vec<T, VEC>(A, m, n, m, m0 + a_row, k0 + (int64_t)a_kv * W, ra);
+      load_vec<T, VEC>(B, p, m, p, k0 + b_k, n0 + (int64_t)b_nv * W, rb);
+    }
+#pragma unroll
+    for (int k = 0; k < BK; k++) {
+      T af[TM], bf[TN];
+      *reinterpret_cast<V *>(&af[0]) = *reinterpret_cast<const V *>(&As[cur][k][ty * W]);
+      *reinterpret_cast<V *>(&af[W]) = *reinterpret_cast<const V *>(&As[cur][k][BM / 2 + ty * W]);
+      *reinterpret_cast<V *>(&bf[0]) = *reinterpret_cast<const V *>(&Bs[cur][k][tx * W]);
+      *reinterpret_cast<V *>(&bf[W]) = *reinterpret_cast<const V *>(&Bs[cur][k][BN / 2 + tx * W]);
+#pragma unroll
+      for (int i = 0; i < TM; i++)
+#pragma unroll
+        for (int j = 0; j < TN; j++) acc[i][j] = fma(af[i], bf[j], acc[i][j]);
+    }
+    if (more) {
+      const int nxt = cur ^ 1;
+#pragma unroll
+      for (int e = 0; e < W; e++) As[nxt][a_kv * W + e][a_row] = ra[e];
+      *reinterpret_cast<V *>(&Bs[nxt][b_k][b_nv * W]) = *reinterpret_cast<V *>(rb);
+    }
+    __syncthreads();
+  }
+
+  // store: rows {ty*W + i, BM/2 + ty*W + i}, columns {tx*W + j, BN/2 + tx*W + j}
+#pragma unroll
+  for (int hi = 0; hi < 2; hi++) {
+#pragma unroll
+    for (int i = 0; i < W; i++) {
+      const int64_t row = m0 + hi * (BM / 2) + ty * W + i;
+      if (row >= n) continue;
+#pragma unroll
+      for (int hj = 0; hj < 2; hj++) {
+        const int64_t col = n0 + hj * (BN / 2) + tx * W;
+        T *dst = C + row * p + col;
+        const T *src = &acc[hi * W + i][hj * W];
+        if (VEC && col + W <= p) {
+          V t;
+          T *tp = reinterpret_cast<T *>(&t);
+#pragma unroll
+          for (int e = 0; e < W; e++) tp[e] = src[e];
+          *reinterpret_cast<V *>(dst) = t;
+        } else {
+#pragma unroll
+          for (int e = 0; e < W; e++)
+            if (col + e < p) dst[e] = src[e];
+        }
+      }
+    }
+  }
+}
+
+// FP32: two blocks per SM (at most 128 registers per thread); FP64: as needed.
+template <typename T> struct MinBlocks { static constexpr int value = sizeof(T) == 4 ? 2 : 1; };
+
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
+__global__ void __launch_bounds__(256, MinBlocks<T>::value)
+simt_gemm_kernel(const T *__restrict__ A, const T *__restrict__ B, T *__restrict__ C,
+                 int64_t n, int64_t m, int64_t p) {
+  simt_tile<T, BM, BN, BK, TM, TN, VEC>(A, B, C, n, m, p, blockIdx.y, blockIdx.x);
+}
+
+// Grouped form: one block per output tile over all problems of a table; the
+// block finds its problem by binary search over the tile prefix.
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
+__global__ void __launch_bounds__(256, MinBlocks<T>::value)
+simt_grouped_kernel(const SimtProb *__restrict__ probs, int nprobs) {
+  const int t = blockIdx.x;
+  int lo = 0, hi = nprobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].tile_start <= t) lo = mid; else hi = mid - 1;
+  }
+  const SimtProb &pr = probs[lo];
+  const int local = t - pr.tile_start;
+  simt_tile<T, BM, BN, BK, TM, TN, VEC>(
+      static_cast<const T *>(pr.A), static_cast<const T *>(pr.B), static_cast<T *>(pr.C),
+      pr.n, pr.m, pr.p, local / pr.tiles_n, local % pr.tiles_n);
+}
+
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+cudaError_t launch_simt(int64_t n, int64_t m, int64_t p, const T *A, const T *B, T *C,
+                        cudaStream_t s, const char *name) {
+  constexpr int W = 16 / (int)sizeof(T);
+  const int64_t gy = ceil_div(n, BM), gx = ceil_div(p, BN);
+  if (gy > 65535 || gx > 2147483647LL) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)gx, (unsigned)gy);
+  const bool vec = aligned16(A) && aligned16(B) && aligned16(C) && m % W == 0 && p % W == 0;
+  TraceScope ts(name, s);
+  if (vec)
+    simt_gemm_kernel<T, BM, BN, BK, TM, TN, true><<<grid, 256, 0, s>>>(A, B, C, n, m, p);
+  else
+    simt_gemm_kernel<T, BM, BN, BK, TM, TN, false><<<grid, 256, 0, s>>>(A, B, C, n, m, p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_simt_f32(int64_t n, int64_t m, int64_t p, const float *A, const float *B,
+                            float *C, cudaStream_t s) {
+  return launch_simt<float, kSimtF32BM, kSimtF32BN, kSimtF32BK, 8, 8>(n, m, p, A, B, C, s,
+                                                                      "simt_f32");
+}
+
+cudaError_t launch_simt_f64(int64_t n, int64_t m, int64_t p, const double *A, const double *B,
+                            double *C, cudaStream_t s) {
+  return launch_simt<double, kSimtF64BM, kSimtF64BN, kSimtF64BK, 4, 4>(n, m, p, A, B, C, s,
+                                                                       "dgemm_f64");
+}
+
+cudaError_t launch_simt_grouped(bool f64, const SimtProb *d_probs, int nprobs, int total_tiles,
+                                bool all_vec, cudaStream_t s) {
+  if (total_tiles <= 0) return cudaSuccess;
+  if (f64) {
+    TraceScope ts("dgemm_f64", s);
+    if (all_vec)
+      simt_grouped_kernel<double, kSimtF64BM, kSimtF64BN, kSimtF64BK, 4, 4, true>
+          <<<total_tiles, 256, 0, s>>>(d_probs, nprobs);
+    else
+      simt_grouped_kernel<double, kSimtF64BM, kSimtF64BN, kSimtF64BK, 4, 4, false>
+          <<<total_tiles, 256, 0, s>>>(d_probs, nprobs);
+  } else {
+    TraceScope ts("simt_f32", s);
+    if (all_vec)
+      simt_grouped_kernel<float, kSimtF32BM, kSimtF32BN, kSimtF32BK, 8, 8, true>
+          <<<total_tiles, 256, 0, s>>>(d_probs, nprobs);
+    else
+      simt_grouped_kernel<float, kSimtF32BM, kSimtF32BN, kSimtF32BK, 8, 8, false>
+          <<<total_tiles, 256, 0, s>>>(d_probs, nprobs);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace mm

@@ -1,0 +1,489 @@
+// Split-BF16x3 GEMM on the sm_103a tensor cores (tcgen05 + TMA + TMEM).
+//
+// Computes C = A.B for FP32 A, B, C from the packed bf16 hi/lo operands
+// written by split_prep.cu:
+//     C_ij ~= 2^(s_i + t_j) * sum_r (Ah Bh + Ah Bl + Al Bh)_irj
+// accumulated in FP32 in tensor memory; the lo.lo product (below 2^-16
+// relative) is dropped.  The definition of the product is the paper's
+// (Section "Implementacje algorytmow", Cauchy product); the split-precision
+// method and everything below are this library's GB300 design, not the
+// paper's (its kernels, Listings 2-4, use CUDA cores only).
+//
+// Kernel structure (persistent, one CTA per SM, 192 threads):
+//   warp 0    TMEM allocation; lane 0 issues TMA loads of the A hi/lo and
+//             B hi/lo tiles of each K step into a STAGES-deep shared-memory
+//             ring (mbarrier "full" with transaction bytes).
+//   warp 1    lane 0 issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32,
+//             M = 128, N = bn) three times per 16-wide K step and commits
+//             each stage back to the producer ("empty") and each finished
+//             tile to the epilogue ("acc_full").
+//   warps 2-5 epilogue: tcgen05.ld of the accumulator (each warp reads its
+//             32 TMEM lanes = 32 rows), exact power-of-two unscaling, FP32
+//             stores with edge predication; then "acc_empty".
+// Two accumulators of 256 TMEM columns each let the epilogue of one tile
+// overlap the mainloop of the next.  Tiles of all problems of a table are
+// visited in a static stride over the CTAs, grouped in bands of group_m row
+// tiles for L2 reuse.
+//
+// Every mbarrier wait is bounded (kWaitLimitNs); on expiry a device flag is
+// set, the other roles stop at their next wait, in-flight copies and MMAs
+// are drained (bounded again) and TMEM is freed before the CTA exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "split_common.cuh"
+
+namespace mm {
+namespace {
+
+constexpr int kThreads = 192;
+constexpr int kMaxBN = 256;
+constexpr int kAccCols = 256;               // TMEM columns per accumulator
+constexpr uint32_t kTmemCols = 2 * kAccCols;
+constexpr int kBoxRows = 128;               // TMA box height (rows of the pack)
+constexpr uint64_t kWaitLimitNs = 4000000000ull;
+constexpr uint64_t kDrainLimitNs = 200000000ull;
+
+// ------------------------------------------------------------------ PTX glue
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for the phase with the given parity.  Returns false when the time
+// limit passes (the error flag is then set to `code`) or, if `watch_err`,
+// when another role has already set the flag.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, int code,
+                                       bool watch_err, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63u) == 0) {
+      if (watch_err && *(volatile int *)err != 0) return false;
+      if (globaltimer_ns() - t0 > limit_ns) {
+        atomicCAS(err, 0, code);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+// D(tmem) (+)= A(smem desc) * B(smem desc)^T, kind::f16 (bf16 inputs here).
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Arrives once on `bar` when all previously issued MMAs of this thread finish.
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+// 32 lanes x 32 consecutive 32-bit columns: thread t gets lane base+t.
+__device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+        "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+        "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+        "=r"(v[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major operand tile whose rows are
+// BK bf16 (BK*2 bytes) long, written by TMA with the matching swizzle:
+// BK = 64 -> 128-byte swizzle, BK = 32 -> 64-byte swizzle.  Groups of 8 rows
+// are 8*BK*2 bytes apart (stride byte offset); the leading byte offset is
+// not used by swizzled K-major layouts.
+template <int BK>
+__device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr) {
+  constexpr uint64_t kSbo = 8ull * BK * 2;
+  constexpr uint64_t kLayout = BK == 64 ? 2ull : 4ull;  // SWIZZLE_128B : SWIZZLE_64B
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | (1ull << 16) | ((kSbo >> 4) << 32) |
+         (1ull << 46) | (kLayout << 61);
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major,
+// N = bn, M = 128.
+__device__ __forceinline__ uint32_t make_idesc(int bn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) |
+         ((uint32_t)(kTcBM >> 4) << 24);
+}
+
+struct TileCoord {
+  int g, mt, nt;
+};
+
+__device__ __forceinline__ TileCoord decode_tile(const SplitProb *__restrict__ probs, int nprobs,
+                                                 int t) {
+  const int g = find_problem(probs, nprobs, t, [](const SplitProb &q) { return q.tile_start; });
+  const SplitProb &pr = probs[g];
+  const int local = t - pr.tile_start;
+  const int gm = pr.group_m;
+  const int band = gm * pr.nt;
+  const int first = (local / band) * gm;
+  const int rows = min(pr.mt - first, gm);
+  const int in = local % band;
+  return TileCoord{g, first + in % rows, in / rows};
+}
+
+template <int BK, int STAGES>
+struct TcLayout {
+  static constexpr int kABytes = kTcBM * BK * 2;       // one part (hi or lo) of A
+  static constexpr int kBBytesMax = kMaxBN * BK * 2;   // one part of B at bn = 256
+  static constexpr int kStageBytes = 2 * kABytes + 2 * kBBytesMax;
+  static constexpr int kBarOffset = STAGES * kStageBytes;
+  static constexpr int kNumBars = 2 * STAGES + 4 + 1;  // full, empty, acc_full/empty, drain
+  static constexpr int kSmemBytes = kBarOffset + kNumBars * 8 + 16 + 1024;  // + align slack
+};
+
+template <int BK, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+split_tc_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__restrict__ probs,
+                int nprobs, int total_tiles, int *err) {
+  using L = TcLayout<BK, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t sbase = (raw + 1023u) & ~1023u;
+  uint8_t *smem = smem_raw + (sbase - raw);
+  const uint32_t bars = sbase + L::kBarOffset;
+  auto full_bar = [&](int s) { return bars + 8u * s; };
+  auto empty_bar = [&](int s) { return bars + 8u * (STAGES + s); };
+  auto accf_bar = [&](int a) { return bars + 8u * (2 * STAGES + a); };
+  auto acce_bar = [&](int a) { return bars + 8u * (2 * STAGES + 2 + a); };
+  const uint32_t drain_bar = bars + 8u * (2 * STAGES + 4);
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(smem + L::kBarOffset + L::kNumBars * 8);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (warp == 0) {
+    tmem_alloc(smem_u32(tmem_holder), kTmemCols);
+    tmem_relinquish();
+  }
+  if (threadIdx.x == 32) {
+    for (int s = 0; s < STAGES; s++) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int a = 0; a < 2; a++) {
+      mbar_init(accf_bar(a), 1);
+      mbar_init(acce_bar(a), 4 * 32);
+    }
+    mbar_init(drain_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t *>(tmem_holder);
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------------ TMA producer
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap))
+                   : "memory");
+      int stage = 0;
+      uint32_t phase = 0;
+      int armed[STAGES];
+      uint32_t armed_parity[STAGES];
+      for (int s = 0; s < STAGES; s++) armed[s] = 0, armed_parity[s] = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+        const TileCoord tc = decode_tile(probs, nprobs, t);
+        const SplitProb &pr = probs[tc.g];
+        const int bn = pr.bn;
+        const int kiters = (pr.m + BK - 1) / BK;
+        const uint32_t bytes = (uint32_t)(2 * kTcBM + 2 * bn) * BK * 2;
+        for (int ki = 0; ki < kiters; ki++) {
+          if (!mbar_wait(empty_bar(stage), phase ^ 1u, err, 1, true, kWaitLimitNs)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(full_bar(stage), bytes);
+          armed[stage] = 1;
+          armed_parity[stage] = phase;
+          const int kb = (ki * BK) / kPackK;
+          const int x = (ki * BK) % kPackK;
+          const int64_t arow = pr.a_row0 + ((int64_t)tc.mt * pr.kt + kb) * (2 * kTcBM);
+          const int64_t brow = pr.b_row0 + ((int64_t)tc.nt * pr.kt + kb) * (2 * bn);
+          const uint32_t st = sbase + stage * L::kStageBytes;
+          tma_load_2d(st, &tmap, x, (int)arow, full_bar(stage));
+          tma_load_2d(st + L::kABytes, &tmap, x, (int)(arow + kTcBM), full_bar(stage));
+          for (int r = 0; r < 2 * bn; r += kBoxRows)
+            tma_load_2d(st + 2 * L::kABytes + r * BK * 2, &tmap, x, (int)(brow + r),
+                        full_bar(stage));
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (!ok) {
+        // drain copies still in flight before the CTA's shared memory goes away
+        for (int s = 0; s < STAGES; s++)
+          if (armed[s]) mbar_wait(full_bar(s), armed_parity[s], err, 1, false, kDrainLimitNs);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------------ MMA issuer
+      int stage = 0;
+      uint32_t phase = 0;
+      int acc = 0;
+      uint32_t acc_phase = 0;
+      bool ok = true, issued = false;
+      for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+        const TileCoord tc = decode_tile(probs, nprobs, t);
+        const SplitProb &pr = probs[tc.g];
+        const int kiters = (pr.m + BK - 1) / BK;
+        const uint32_t idesc = make_idesc(pr.bn);
+        const uint32_t blo = (uint32_t)pr.bn * BK * 2;
+        if (!mbar_wait(acce_bar(acc), acc_phase ^ 1u, err, 2, true, kWaitLimitNs)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * kAccCols);
+        for (int ki = 0; ki < kiters; ki++) {
+          if (!mbar_wait(full_bar(stage), phase, err, 3, true, kWaitLimitNs)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = sbase + stage * L::kStageBytes;
+          const uint64_t a_hi = kmajor_desc<BK>(st);
+          const uint64_t a_lo = kmajor_desc<BK>(st + L::kABytes);
+          const uint64_t b_hi = kmajor_desc<BK>(st + 2 * L::kABytes);
+          const uint64_t b_lo = kmajor_desc<BK>(st + 2 * L::kABytes + blo);
+#pragma unroll
+          for (int k16 = 0; k16 < BK / 16; k16++) {
+            const uint64_t adv = (uint64_t)(k16 * 32) >> 4;  // 16 bf16 = 32 bytes
+            tc_mma(d_tmem, a_hi + adv, b_hi + adv, idesc, (ki | k16) != 0 ? 1u : 0u);
+            tc_mma(d_tmem, a_hi + adv, b_lo + adv, idesc, 1u);
+            tc_mma(d_tmem, a_lo + adv, b_hi + adv, idesc, 1u);
+          }
+          issued = true;
+          tc_commit(empty_bar(stage));
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        tc_commit(accf_bar(acc));
+        if (++acc == 2) {
+          acc = 0;
+          acc_phase ^= 1u;
+        }
+      }
+      if (!ok && issued) {
+        // wait for MMAs in flight before TMEM is released
+        tc_commit(drain_bar);
+        mbar_wait(drain_bar, 0, err, 3, false, kDrainLimitNs);
+      }
+    }
+  } else {
+    // -------------------------------------------------------- epilogue
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int row = q * 32 + lane;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+      const TileCoord tc = decode_tile(probs, nprobs, t);
+      const SplitProb &pr = probs[tc.g];
+      if (!mbar_wait(accf_bar(acc), acc_phase, err, 4, true, kWaitLimitNs)) break;
+      tc_fence_after();
+      const int64_t i = (int64_t)tc.mt * kTcBM + row;
+      const bool row_ok = i < pr.n;
+      const int si = row_ok ? scale_exponent(pr.sA[i]) : 0;
+      float *crow = pr.C + (row_ok ? i : 0) * (int64_t)pr.p;
+      const bool vec = ((reinterpret_cast<uintptr_t>(pr.C) & 15u) == 0) && ((pr.p & 3) == 0);
+      const uint32_t tacc = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kAccCols);
+      for (int c = 0; c < pr.bn; c += 32) {
+        uint32_t v[32];
+        __syncwarp();  // tcgen05.ld is warp-collective: reconverge first
+        tmem_ld_32x32b_x32(tacc + (uint32_t)c, v);
+        tmem_ld_wait();
+        const int64_t j0 = (int64_t)tc.nt * pr.bn + c;
+        if (!row_ok || j0 >= pr.p) continue;
+        if (vec && j0 + 32 <= pr.p) {
+#pragma unroll
+          for (int e = 0; e < 32; e += 4) {
+            float4 o;
+            o.x = ldexpf(__uint_as_float(v[e + 0]), si + scale_exponent(pr.tB[j0 + e + 0]));
+            o.y = ldexpf(__uint_as_float(v[e + 1]), si + scale_exponent(pr.tB[j0 + e + 1]));
+            o.z = ldexpf(__uint_as_float(v[e + 2]), si + scale_exponent(pr.tB[j0 + e + 2]));
+            o.w = ldexpf(__uint_as_float(v[e + 3]), si + scale_exponent(pr.tB[j0 + e + 3]));
+            *reinterpret_cast<float4 *>(crow + j0 + e) = o;
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 32; e++)
+            if (j0 + e < pr.p)
+              crow[j0 + e] = ldexpf(__uint_as_float(v[e]), si + scale_exponent(pr.tB[j0 + e]));
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(acce_bar(acc));
+      if (++acc == 2) {
+        acc = 0;
+        acc_phase ^= 1u;
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, kTmemCols);
+  }
+}
+
+// ---------------------------------------------------------------- host side
+PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 2-D map over the pack region viewed as rows of 64 bf16 (128 bytes).
+cudaError_t encode_pack_map(CUtensorMap *map, void *base, int64_t rows, int bk) {
+  auto enc = get_encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  cuuint64_t dims[2] = {(cuuint64_t)kPackK, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kPackRowBytes};
+  cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)kBoxRows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int BK, int STAGES>
+cudaError_t launch_tc_t(const SplitProb *d_probs, int nprobs, int total_tiles, void *pack_base,
+                        int64_t pack_rows, int grid, int *d_err, cudaStream_t s) {
+  using L = TcLayout<BK, STAGES>;
+  static_assert(L::kSmemBytes <= 232448, "shared memory budget");
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(split_tc_kernel<BK, STAGES>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, L::kSmemBytes);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  CUtensorMap map;
+  cudaError_t e = encode_pack_map(&map, pack_base, pack_rows, BK);
+  if (e != cudaSuccess) return e;
+  TraceScope ts("split_tc", s);
+  split_tc_kernel<BK, STAGES><<<grid, kThreads, L::kSmemBytes, s>>>(map, d_probs, nprobs,
+                                                                     total_tiles, d_err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_split_tc(const SplitProb *d_probs, int nprobs, int total_tiles,
+                            void *pack_base, int64_t pack_rows, const TcConfig &cfg, int *d_err,
+                            cudaStream_t s) {
+  if (total_tiles <= 0) return cudaSuccess;
+  if (pack_rows <= 0 || pack_rows > 0x7fffffffLL) return cudaErrorInvalidValue;
+  int grid = cfg.grid > 0 ? cfg.grid : sm_count();
+  if (grid > total_tiles) grid = total_tiles;
+  if (cfg.bk == 64) return launch_tc_t<64, 2>(d_probs, nprobs, total_tiles, pack_base, pack_rows,
+                                             grid, d_err, s);
+  if (cfg.bk == 32) {
+    if (cfg.stages == 3)
+      return launch_tc_t<32, 3>(d_probs, nprobs, total_tiles, pack_base, pack_rows, grid, d_err,
+                                s);
+    return launch_tc_t<32, 4>(d_probs, nprobs, total_tiles, pack_base, pack_rows, grid, d_err, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace mm

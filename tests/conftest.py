@@ -26,3 +26,16 @@ def pytest_configure(config):
 def orc():
     import oracle
     return oracle.default()
+
+
+@pytest.fixture(scope="session")
+def mmlib():
+    """The CUDA library, initialised once per session on cuda:0."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test selected on a machine without a GPU")
+    import paper_1306_6192_gb300 as mm
+    st = mm.mm_init(device=0)
+    assert st == mm.MM_OK, mm.mm_strerror(st)
+    yield mm
+    mm.mm_shutdown()

@@ -1,0 +1,80 @@
+"""Grouped GEMM: uneven independent products in one launch per path, each
+result against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _problems(count, seed, lo=32, hi=1024, step=32, f64=False):
+    dims = synth.grouped_dims(seed, count, lo, hi, step)
+    tdt = torch.float64 if f64 else torch.float32
+    probs, host = [], []
+    for g, (n, m, p) in enumerate(dims):
+        A = synth.uniform_pm1(1000 + 2 * g, (n, m))
+        B = synth.uniform_pm1(1001 + 2 * g, (m, p))
+        C = torch.full((n, p), float("nan"), dtype=tdt, device="cuda")
+        probs.append((int(n), int(m), int(p), dev(A, tdt), dev(B, tdt), C))
+        host.append((A, B))
+    return probs, host
+
+
+@pytest.mark.parametrize("mode", ["split", "simt", "dgemm"])
+def test_grouped_uneven(mmlib, mode):
+    f64 = mode == "dgemm"
+    md = {"split": mmlib.MM_MODE_SPLIT_BF16X3, "simt": mmlib.MM_MODE_SIMT,
+          "dgemm": mmlib.MM_MODE_DGEMM}[mode]
+    probs, host = _problems(24, 7, lo=1, hi=700, step=1, f64=f64)
+    st = mmlib.mm_gemm_grouped(probs, mmlib.MM_F64 if f64 else mmlib.MM_F32, md)
+    assert st == 0, mmlib.mm_strerror(st)
+    orc = oracle.default()
+    for (n, m, p, _, _, C), (A, B) in zip(probs, host):
+        ref, absref = orc.gemm(A, B, with_abs=True)
+        e = oracle.rel_errors(C.cpu().numpy(), ref, absref).max()
+        assert e <= oracle.tolerance(m, "f64" if f64 else "f32"), (n, m, p, e)
+
+
+def test_grouped_matches_single(mmlib):
+    """Each grouped result equals the same product run alone (same tiles)."""
+    probs, host = _problems(12, 9)
+    assert mmlib.mm_gemm_grouped(probs, mmlib.MM_F32, mmlib.MM_MODE_SPLIT_BF16X3) == 0
+    for (n, m, p, A, B, C) in probs:
+        C1 = torch.full_like(C, float("nan"))
+        assert mmlib.mm_gemm(n, m, p, A, B, C1, mmlib.MM_F32, mmlib.MM_MODE_SPLIT_BF16X3) == 0
+        bn_g = mmlib.mm_tune_query(n, m, p)[1]
+        assert torch.equal(C, C1), (n, m, p, bn_g)
+
+
+def test_grouped_config4_sample(mmlib):
+    """Config-4 shape mix (n, m, p uniform over {32, 64, ..., 1024}): 256 of
+    the instances in one launch, every one checked against the oracle."""
+    probs, host = _problems(256, 4)
+    assert mmlib.mm_gemm_grouped(probs, mmlib.MM_F32, mmlib.MM_MODE_SPLIT_BF16X3) == 0
+    orc = oracle.default()
+    for g in range(0, 256, 8):
+        n, m, p, _, _, C = probs[g]
+        A, B = host[g]
+        ref, absref = orc.gemm(A, B, with_abs=True)
+        e = oracle.rel_errors(C.cpu().numpy(), ref, absref).max()
+        assert e <= oracle.tolerance(m, "f32"), (g, n, m, p, e)
+
+
+def test_grouped_with_empty_members(mmlib):
+    A = torch.ones((3, 0), device="cuda")
+    B = torch.ones((0, 4), device="cuda")
+    C = torch.full((3, 4), 5.0, device="cuda")
+    A2 = dev(synth.uniform_pm1(1, (40, 50)))
+    B2 = dev(synth.uniform_pm1(2, (50, 30)))
+    C2 = torch.zeros((40, 30), device="cuda")
+    probs = [(3, 0, 4, A, B, C), (0, 5, 5, None, None, None), (40, 50, 30, A2, B2, C2)]
+    assert mmlib.mm_gemm_grouped(probs, mmlib.MM_F32, mmlib.MM_MODE_SPLIT_BF16X3) == 0
+    assert torch.all(C == 0)
+    a2 = synth.uniform_pm1(1, (40, 50))
+    b2 = synth.uniform_pm1(2, (50, 30))
+    ref, absref = oracle.default().gemm(a2, b2, with_abs=True)
+    assert oracle.rel_errors(C2.cpu().numpy(), ref, absref).max() <= oracle.tolerance(50, "f32")
