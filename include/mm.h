@@ -91,6 +91,8 @@ typedef struct {
   int check;               /* 1: the serving loop checks every result on the
                               GPU (Freivalds + sampled entries, FP64) */
   int device;              /* CUDA device ordinal; -1 keeps the current one */
+  int max_batch;           /* serving: most requests per grouped launch; 0
+                              selects 256, 1 gives one request per launch */
 } mm_opts;
 
 /* One independent product C = A.B (row-major, dense; see conventions). */
@@ -106,8 +108,10 @@ typedef struct {
  * Returns MM_EBUSY if already initialised, MM_EUNSUPPORTED on another GPU. */
 mm_status mm_init(const mm_opts *opts);
 
-/* Stops the serving loop (pending requests end MM_ECANCELLED), waits for the
- * library's streams and frees every library allocation.  Idempotent. */
+/* Stops the serving loop: requests not yet launched end MM_ECANCELLED,
+ * launched ones finish; their final status stays pollable until the next
+ * mm_init.  Waits for the library's streams and frees every library
+ * allocation.  Idempotent. */
 mm_status mm_shutdown(void);
 
 /* Static string for a status code. */

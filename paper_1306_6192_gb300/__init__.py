@@ -30,7 +30,7 @@ _dp = ctypes.POINTER(ctypes.c_double)
 class mm_opts(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("n_streams", ctypes.c_int),
                 ("tune_table", ctypes.c_char_p), ("check", ctypes.c_int),
-                ("device", ctypes.c_int)]
+                ("device", ctypes.c_int), ("max_batch", ctypes.c_int)]
 
 
 class mm_problem(ctypes.Structure):
@@ -121,9 +121,9 @@ def mm_strerror(st: int) -> str:
 
 
 def mm_init(hbm_budget_bytes: int = 0, n_streams: int = 0, tune_table: str | None = None,
-            check: int = 0, device: int = -1) -> int:
+            check: int = 0, device: int = -1, max_batch: int = 0) -> int:
     o = mm_opts(hbm_budget_bytes, n_streams, tune_table.encode() if tune_table else None,
-                check, device)
+                check, device, max_batch)
     return lib().mm_init(ctypes.byref(o))
 
 
