@@ -24,6 +24,8 @@ the times.
 from __future__ import annotations
 
 import argparse
+import collections
+import itertools
 import json
 import os
 import statistics
@@ -229,6 +231,153 @@ def _traffic_from_profiles(name: str):
     return None
 
 
+def gpu_check(mm, n, m, p, A, B, C, dt, seed=2, samples=4096):
+    """The library's FP64 GPU check of a computed product: (Freivalds max
+    normalised residual, max normalised error on sampled entries)."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    x = torch.rand(p, device="cuda", dtype=torch.float64, generator=g) * 2 - 1
+    I = torch.randint(0, n, (samples,), device="cuda", generator=g)
+    J = torch.randint(0, p, (samples,), device="cuda", generator=g)
+    st, fr, sm = mm.mm_check(n, m, p, A, B, C, dt, x, I, J)
+    mm.check_status(st, "mm_check")
+    return fr, sm
+
+
+def bench_grouped(mm, stream, steps: int, seed: int = 4, count: int = 4096):
+    """Grouped GEMM of `count` products, n, m, p uniform over {32, ..., 1024}
+    step 32 (seeded), split path: one grouped launch per step vs one launch
+    per product.  Returns a dict of TFLOP/s and launch counts."""
+    import torch
+
+    import synth
+    dims = synth.grouped_dims(seed, count)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    probs = []
+    flops = 0.0
+    for (n, m, p) in dims:
+        n, m, p = int(n), int(m), int(p)
+        A = torch.rand((n, m), device="cuda", generator=gen) * 2 - 1
+        B = torch.rand((m, p), device="cuda", generator=gen) * 2 - 1
+        C = torch.empty((n, p), device="cuda")
+        probs.append((n, m, p, A, B, C))
+        flops += 2.0 * n * m * p
+    md = mm.MM_MODE_SPLIT_BF16X3
+
+    table = mm.mm_problems(probs)  # marshalled once, outside the timing
+
+    def grouped():
+        mm.check_status(mm.mm_gemm_grouped_async(table, mm.MM_F32, md, stream), "grouped")
+
+    def singles():
+        for (n, m, p, A, B, C) in probs:
+            mm.check_status(mm.mm_gemm_async(n, m, p, A, B, C, mm.MM_F32, md, stream), "single")
+
+    out = {"instances": count, "tflop": flops / 1e12}
+    for name, fn, k in (("grouped", grouped, steps), ("per_instance", singles, max(1, steps // 4))):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        l0 = mm.mm_launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        out[name + "_tflops"] = flops / (ms * 1e-3) / 1e12
+        out[name + "_ms"] = ms
+        out[name + "_launches_per_step"] = (mm.mm_launch_count() - l0) / k
+    mm.check_status(mm.mm_sync(stream), "grouped sync")
+    n, m, p, A, B, C = probs[0]
+    out["check_first"] = gpu_check(mm, n, m, p, A, B, C, mm.MM_F32)
+    del probs
+    return out
+
+
+def bench_serving(mm, count: int, rate_frac: float, seed: int = 5, streams: int = 2,
+                  max_batch: int = 0, capacity=None):
+    """Poisson replay of `count` requests (dims log-uniform in [64, 4096], 20%
+    FP64) through mm_submit/mm_poll with operands resident on the device.
+    The arrival rate is rate_frac x the measured capacity (requests/s of the
+    same mix submitted all at once).  Returns p50/p99 latency and rates."""
+    import numpy as np
+    import torch
+
+    import synth
+    _, dims, f64 = synth.serving_stream(seed, count, 1.0)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    big = 4096 * 4096
+    src32 = torch.rand(big, device="cuda", generator=gen) * 2 - 1
+    src64 = src32.double()
+
+    def submit(k):
+        n, m, p = (int(v) for v in dims[k])
+        if f64[k]:
+            A, B, dt, md = src64[:n * m], src64[:m * p], mm.MM_F64, mm.MM_MODE_DGEMM
+            C = torch.empty(n * p, device="cuda", dtype=torch.float64)
+        else:
+            A, B, dt, md = src32[:n * m], src32[:m * p], mm.MM_F32, mm.MM_MODE_SPLIT_BF16X3
+            C = torch.empty(n * p, device="cuda")
+        st, rid = mm.mm_submit(n, m, p, A, B, C, dt, md)
+        mm.check_status(st, "mm_submit")
+        return rid, C
+
+    def drain(live, lat, budget=32):
+        # polls the oldest requests first, a bounded number per call
+        done = []
+        for rid in itertools.islice(live, budget):
+            st, res, _, ms = mm.mm_poll(rid)
+            if st == mm.MM_OK:
+                mm.check_status(res, "request")
+                lat.append(ms)
+                done.append(rid)
+        for rid in done:
+            del live[rid]
+
+    flops = float(np.sum(2.0 * dims[:, 0] * dims[:, 1] * dims[:, 2]))
+    dev_index = torch.cuda.current_device()
+    mm.mm_shutdown()
+    mm.check_status(mm.mm_init(n_streams=streams, max_batch=max_batch, device=dev_index),
+                    "mm_init serving")
+    if capacity is None:
+        # capacity: everything submitted at once
+        live, lat = collections.OrderedDict(), []
+        t0 = time.perf_counter()
+        for k in range(count):
+            rid, C = submit(k)
+            live[rid] = C
+        while live:
+            drain(live, lat)
+        capacity = count / (time.perf_counter() - t0)
+    rate = rate_frac * capacity
+    gaps = -np.log1p(-synth.uniform01_f64(seed + 1, count)) / rate
+    arrivals = np.cumsum(gaps)
+    live, lat = collections.OrderedDict(), []
+    t0 = time.perf_counter()
+    for k in range(count):
+        while time.perf_counter() - t0 < arrivals[k]:
+            drain(live, lat)
+        rid, C = submit(k)
+        live[rid] = C
+    while live:
+        drain(live, lat)
+    wall = time.perf_counter() - t0
+    st, completed, batches, waiting, resident = mm.mm_serve_stats()
+    mm.mm_shutdown()
+    mm.check_status(mm.mm_init(device=dev_index), "mm_init default")
+    lat = np.asarray(lat)
+    return {"requests": count, "rate_req_s": rate, "capacity_req_s": capacity,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "throughput_req_s": count / wall, "tflops": flops / wall / 1e12,
+            "batches": batches, "streams": streams, "max_batch": max_batch or 256}
+
+
 def run_mine(args):
     import numpy as np
     import torch
@@ -343,8 +492,27 @@ def run_mine(args):
         ms_d, _ = timed(f64, 2, 1)
         extra["dgemm_f64_tflops"] = 2.0 * nd ** 3 / (ms_d / 2 * 1e-3) / 1e12
         extra["dgemm_size"] = nd
+        extra["dgemm_check"] = gpu_check(mm, nd, nd, nd, A64, B64, C64, mm.MM_F64)
         del A64, B64, C64
+        # FP8 e4m3 at the same size: rate and measured error (reported only)
+        ms_8, _ = timed(lambda: step(mm.MM_MODE_FP8), max(2, args.steps // 4), 1)
+        extra["fp8_tflops"] = flops / (ms_8 / max(2, args.steps // 4) * 1e-3) / 1e12
+        extra["fp8_check"] = gpu_check(mm, n, n, n, A, B, C, mm.MM_F32)
+        # accuracy of the headline product, FP64 check on the GPU
+        step()
+        mm.check_status(mm.mm_sync(stream), "split")
+        extra["split_check"] = gpu_check(mm, n, n, n, A, B, C, mm.MM_F32)
+        extra["tolerance_f32"] = 1e-6 * n ** 0.5
         line["paths"] = extra
+        line["grouped"] = bench_grouped(mm, stream, max(3, args.steps // 20))
+        cap = None
+        serving = {}
+        for name, st_, mb in (("batched", 2, 0), ("one_per_launch", 1, 1)):
+            r = bench_serving(mm, args.serve_requests, 0.9, streams=st_, max_batch=mb,
+                              capacity=cap)
+            cap = r["capacity_req_s"] if cap is None else cap
+            serving[name] = r
+        line["serving"] = serving
 
         # end to end: mm_gemm with pinned host operands, copies inside the timing
         Ah = A.cpu().pin_memory()
@@ -385,6 +553,7 @@ def main(argv=None):
     ap.add_argument("--dgemm-size", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="headline step only")
+    ap.add_argument("--serve-requests", type=int, default=1500)
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "mine":
         args.warmup = 3

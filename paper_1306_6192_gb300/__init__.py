@@ -139,7 +139,11 @@ def mm_gemm_async(n, m, p, A, B, C, dt, mode, stream=None) -> int:
     return lib().mm_gemm_async(n, m, p, _ptr(A), _ptr(B), _ptr(C), dt, mode, _stream(stream))
 
 
-def _problems(probs):
+def mm_problems(probs):
+    """A ctypes array of mm_problem from (n, m, p, A, B, C) tuples; pass it
+    to the grouped calls to marshal a large table only once."""
+    if isinstance(probs, ctypes.Array):
+        return probs
     arr = (mm_problem * max(len(probs), 1))()
     for k, (n, m, p, A, B, C) in enumerate(probs):
         arr[k] = mm_problem(n, m, p, _ptr(A), _ptr(B), _ptr(C))
@@ -148,11 +152,11 @@ def _problems(probs):
 
 def mm_gemm_grouped(probs, dt, mode) -> int:
     """probs: sequence of (n, m, p, A, B, C)."""
-    return lib().mm_gemm_grouped(len(probs), _problems(probs), dt, mode)
+    return lib().mm_gemm_grouped(len(probs), mm_problems(probs), dt, mode)
 
 
 def mm_gemm_grouped_async(probs, dt, mode, stream=None) -> int:
-    return lib().mm_gemm_grouped_async(len(probs), _problems(probs), dt, mode, _stream(stream))
+    return lib().mm_gemm_grouped_async(len(probs), mm_problems(probs), dt, mode, _stream(stream))
 
 
 def mm_sync(stream=None) -> int:

@@ -28,7 +28,7 @@ mm_status from_cuda(cudaError_t e) {
 
 // A sticky error (illegal address, launch failure ...) loses the context: the
 // library then refuses further work.
-static mm_status note_cuda(cudaError_t e) {
+mm_status note_cuda(cudaError_t e) {
   if (e == cudaSuccess) return MM_OK;
   cudaError_t last = cudaGetLastError();
   (void)last;
@@ -160,89 +160,6 @@ int pointer_kind(const void *p) {
   }
 }
 
-// ---------------------------------------------------------------- split path
-// Builds the problem table of the split path for `count` products, lays out
-// the scratch (pack rows, scale arrays, table), and launches prep + tensor-
-// core kernels on stream s.  Problems with n == 0 or p == 0 are skipped;
-// m == 0 writes zeros.
-mm_status run_split(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s,
-                    const TcChoice *force) {
-  std::vector<SplitProb> tab;
-  tab.reserve(count);
-  int64_t rows = 0, scal = 0;
-  int64_t tiles = 0, packs = 0, reds = 0;
-  TcConfig cfg{0, 0, 0};
-  for (int g = 0; g < count; g++) {
-    const mm_problem &q = probs[g];
-    if (q.n == 0 || q.p == 0) continue;
-    if (q.m == 0) {
-      cudaError_t e = cudaMemsetAsync(q.C, 0, (size_t)(q.n * q.p) * sizeof(float), s);
-      if (e != cudaSuccess) return note_cuda(e);
-      continue;
-    }
-    TcChoice ch = force ? *force : tune_choose(q.n, q.m, q.p);
-    if (tab.empty()) cfg = TcConfig{ch.bk, ch.stages, ch.grid};
-    SplitProb sp;
-    std::memset(&sp, 0, sizeof(sp));
-    sp.A = static_cast<const float *>(q.A);
-    sp.B = static_cast<const float *>(q.B);
-    sp.C = static_cast<float *>(q.C);
-    sp.n = (int32_t)q.n;
-    sp.m = (int32_t)q.m;
-    sp.p = (int32_t)q.p;
-    sp.bn = ch.bn;
-    sp.group_m = ch.group_m;
-    sp.mt = (int32_t)ceil_div(q.n, kTcBM);
-    sp.nt = (int32_t)ceil_div(q.p, ch.bn);
-    sp.kt = (int32_t)ceil_div(q.m, kPackK);
-    sp.a_row0 = rows;
-    rows += (int64_t)sp.mt * sp.kt * 2 * kTcBM;
-    sp.b_row0 = rows;
-    rows += (int64_t)sp.nt * sp.kt * 2 * ch.bn;
-    sp.sA = reinterpret_cast<uint32_t *>((uintptr_t)scal);  // offset, fixed below
-    scal += q.n;
-    sp.tB = reinterpret_cast<uint32_t *>((uintptr_t)scal);
-    scal += q.p;
-    sp.tile_start = (int32_t)tiles;
-    tiles += (int64_t)sp.mt * sp.nt;
-    sp.pack_start = (int32_t)packs;
-    packs += (int64_t)sp.mt * sp.kt + (int64_t)sp.nt * sp.kt;
-    sp.red_start = (int32_t)reds;
-    sp.red_a = (int32_t)ceil_div(q.n, 8);
-    reds += sp.red_a + ceil_div(q.p, 32) * ceil_div(q.m, 256);
-    tab.push_back(sp);
-  }
-  if (tab.empty()) return MM_OK;
-  if (tiles > 0x7fffffffLL || packs > 0x7fffffffLL || reds > 0x7fffffffLL ||
-      rows > 0x7fffffffLL)
-    return MM_EINVAL;
-  const size_t pack_bytes = (size_t)rows * kPackRowBytes;
-  const size_t scal_off = (pack_bytes + 255) & ~(size_t)255;
-  const size_t tab_off = (scal_off + (size_t)scal * 4 + 255) & ~(size_t)255;
-  const size_t need = tab_off + tab.size() * sizeof(SplitProb);
-  cudaError_t e = ws.reserve(need, s);
-  if (e != cudaSuccess) return note_cuda(e);
-  uint8_t *base = static_cast<uint8_t *>(ws.ptr);
-  for (auto &sp : tab) {
-    sp.sA = reinterpret_cast<uint32_t *>(base + scal_off) + (uintptr_t)sp.sA;
-    sp.tB = reinterpret_cast<uint32_t *>(base + scal_off) + (uintptr_t)sp.tB;
-  }
-  SplitProb *d_tab = reinterpret_cast<SplitProb *>(base + tab_off);
-  e = cudaMemcpyAsync(d_tab, tab.data(), tab.size() * sizeof(SplitProb),
-                      cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return note_cuda(e);
-  e = cudaMemsetAsync(base + scal_off, 0, (size_t)scal * 4, s);
-  if (e != cudaSuccess) return note_cuda(e);
-  const int np = (int)tab.size();
-  e = launch_split_scale(d_tab, np, (int)reds, s);
-  if (e != cudaSuccess) return note_cuda(e);
-  e = launch_split_pack(d_tab, np, (int)packs, base, s);
-  if (e != cudaSuccess) return note_cuda(e);
-  e = launch_split_tc(d_tab, np, (int)tiles, base, rows, cfg, g_ctx.d_err, s);
-  if (e != cudaSuccess) return note_cuda(e);
-  return MM_OK;
-}
-
 // ---------------------------------------------------------------- dispatch
 static mm_mode resolve_mode(mm_dtype dt, mm_mode mode) {
   if (mode == MM_MODE_AUTO) return dt == MM_F64 ? MM_MODE_DGEMM : MM_MODE_SPLIT_BF16X3;
@@ -278,7 +195,7 @@ mm_status enqueue_gemm(int64_t n, int64_t m, int64_t p, const void *A, const voi
           launch_simt_f64(n, m, p, (const double *)A, (const double *)B, (double *)C, s));
     case MM_MODE_SPLIT_BF16X3: {
       mm_problem q{n, m, p, A, B, C};
-      return run_split(g_ctx.split_ws, &q, 1, s, nullptr);
+      return run_split(g_ctx.split_ws, &q, 1, s, nullptr);  // two or three parts by m
     }
     case MM_MODE_FP8: {
       mm_problem q{n, m, p, A, B, C};

@@ -49,8 +49,16 @@ mm_status enqueue_gemm(int64_t n, int64_t m, int64_t p, const void *A, const voi
                        mm_dtype dt, mm_mode mode, cudaStream_t s);
 mm_status check_device_flag(cudaStream_t s);
 
-// Split path over a table of problems (single GEMM = table of one).
-// `force` overrides the tuned tile choice (autotuner and tests).
+mm_status note_cuda(cudaError_t e);
+
+// Kind of split used for inner dimension m: two bf16 parts (three products)
+// where their worst-case per-product error 3 * 2^-16 is within the stated
+// tolerance 1e-6 sqrt(m), three parts (six products) below that.
+TcKind split_kind_for(int64_t m);
+
+// Split path over a table of problems (single GEMM = table of one); each
+// problem takes the kind split_kind_for(m).  `force` overrides the tuned tile
+// choice (autotuner and tests).
 mm_status run_split(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s,
                     const TcChoice *force);
 // FP8 path (report-only accuracy).

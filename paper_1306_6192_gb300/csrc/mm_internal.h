@@ -22,24 +22,33 @@ constexpr int kSimtF32BM = 128, kSimtF32BN = 128, kSimtF32BK = 8;
 // SIMT FP64 tile: 64 x 64 outputs per 256-thread block, 4 x 4 per thread.
 constexpr int kSimtF64BM = 64, kSimtF64BN = 64, kSimtF64BK = 8;
 
-// Split-BF16x3 tensor-core path: M tile is the tcgen05 M (128 rows of A);
-// packed operands are stored in blocks of 64 along K (one 128-byte row of
-// bf16 per row of the block).
+// Tensor-core paths (split-BF16x3 and e4m3): the M tile is the tcgen05 M
+// (128 rows of A).  Packed operands live in the scratch "pack region", viewed
+// as rows of 128 bytes: one pack row holds one K block of one row of A (or
+// one column of B) - 64 bf16 values for the split path, 128 e4m3 values for
+// the FP8 path.
 constexpr int kTcBM = 128;
-constexpr int kPackK = 64;
-constexpr int kPackRowBytes = kPackK * 2;
+constexpr int kPackRowBytes = 128;
+// Split kinds: two bf16 parts (hi, lo; products hi.hi + hi.lo + lo.hi) or
+// three (hi, mid, lo; the six products down to 2^-16 relative).
+enum TcKind : int { kTcSplitBf16x3 = 0, kTcE4m3 = 1, kTcSplitBf16x6 = 2 };
+// elements per pack row and operand parts
+inline int pack_k(TcKind k) { return k == kTcE4m3 ? 128 : 64; }
+inline int pack_parts(TcKind k) { return k == kTcE4m3 ? 1 : (k == kTcSplitBf16x3 ? 2 : 3); }
+constexpr int kPackK = 64;  // bf16 elements per pack row
 
 // ------------------------------------------------------------ device tables
-// One product of the split path, as the prep and tensor-core kernels see it.
-// Pack layout (rows of kPackK bf16 inside the scratch pack region):
-//   A pack tile (mt, kb): rows a_row0 + (mt*kt + kb)*256 .. +255:
-//       rows 0..127 = hi part of A rows mt*128 .. +127 (K block kb),
-//       rows 128..255 = lo part; entries outside A are zero.
-//   B pack tile (nt, kb): rows b_row0 + (nt*kt + kb)*2*bn .. +2*bn-1:
-//       rows 0..bn-1 = hi part of B columns nt*bn .. +bn-1 (K block kb,
-//       i.e. B transposed so K is contiguous), rows bn..2bn-1 = lo part.
-// sA[i] / tB[j] hold the bit pattern of max_r |a_ir| / max_r |b_rj|; the
-// scale exponent of a row/column is derived from it (scale_exponent()).
+// One product of a tensor-core path, as the prep and tensor-core kernels see
+// it.  With P = pack_parts(kind) and kt = ceil(m / pack_k(kind)):
+//   A pack tile (mt, kb): rows a_row0 + (mt*kt + kb)*P*128 ..:
+//       part 0 (split: hi; FP8: the e4m3 values) of A rows mt*128 .. +127 for
+//       K block kb, then part 1 (split: lo) in the next 128 rows;
+//   B pack tile (nt, kb): rows b_row0 + (nt*kt + kb)*P*bn ..:
+//       part 0 of B columns nt*bn .. +bn-1 (B transposed so K is contiguous),
+//       then part 1 in the next bn rows.
+// Entries outside A or B are zero.  sA[i] / tB[j] hold the bit pattern of
+// max_r |a_ir| / max_r |b_rj|; each path derives its power-of-two scale
+// exponent of a row/column from it.
 struct SplitProb {
   const float *A;
   const float *B;
@@ -47,8 +56,8 @@ struct SplitProb {
   int64_t a_row0, b_row0;
   uint32_t *sA, *tB;
   int32_t n, m, p;
-  int32_t mt, nt, kt;      // ceil(n/128), ceil(p/bn), ceil(m/64)
-  int32_t bn, group_m;     // N tile (128 or 256), raster group height
+  int32_t mt, nt, kt;      // ceil(n/128), ceil(p/bn), ceil(m/pack_k)
+  int32_t bn, group_m;     // N tile (64, 128 or 256), raster band height
   int32_t tile_start;      // prefix over problems of mt*nt (MMA tiles)
   int32_t pack_start;      // prefix of pack tiles: mt*kt + nt*kt
   int32_t red_start;       // prefix of scale-reduction items
@@ -73,23 +82,25 @@ cudaError_t launch_simt_f64(int64_t n, int64_t m, int64_t p, const double *A,
 cudaError_t launch_simt_grouped(bool f64, const SimtProb *d_probs, int nprobs,
                                 int total_tiles, bool all_vec, cudaStream_t s);
 
-// Prep: per-row/column max-abs reduction, then hi/lo split into the packs.
+// Prep: per-row/column max-abs reduction, then the split (hi/lo bf16) or
+// e4m3 conversion into the packs.
 cudaError_t launch_split_scale(const SplitProb *d_probs, int nprobs,
                                int total_items, cudaStream_t s);
-cudaError_t launch_split_pack(const SplitProb *d_probs, int nprobs,
+cudaError_t launch_split_pack(TcKind kind, const SplitProb *d_probs, int nprobs,
                               int total_tiles, void *pack_base,
                               cudaStream_t s);
+cudaError_t launch_fp8_pack(const SplitProb *d_probs, int nprobs,
+                            int total_tiles, void *pack_base, cudaStream_t s);
 
 // Tensor-core mainloop + epilogue over all tiles of all problems.
 struct TcConfig {
-  int bk;       // 32 or 64 (K per pipeline stage)
+  int bkb;      // bytes of K per pipeline stage and pack row: 64 or 128
   int stages;   // pipeline depth
-  int grid;     // persistent CTAs (<= number of SMs)
+  int grid;     // persistent CTAs (<= number of SMs; 0 = one per SM)
 };
-cudaError_t launch_split_tc(const SplitProb *d_probs, int nprobs,
-                            int total_tiles, void *pack_base,
-                            int64_t pack_rows, const TcConfig &cfg,
-                            int *d_err, cudaStream_t s);
+cudaError_t launch_tc(TcKind kind, const SplitProb *d_probs, int nprobs,
+                      int total_tiles, void *pack_base, int64_t pack_rows,
+                      const TcConfig &cfg, int *d_err, cudaStream_t s);
 
 // FP64 check (Freivalds + sampled entries): writes 2 doubles to d_out.
 cudaError_t launch_check(bool f64, int64_t n, int64_t m, int64_t p,

@@ -2,6 +2,7 @@
 //
 // Method: an FP32 operand x is written as x = 2^s (hi + lo + d) with
 // hi = bf16_rn(x 2^-s), lo = bf16_rn(x 2^-s - hi) and |d| <= 2^-16 |x 2^-s|
+// (three parts: hi + mid + lo, |d| <= 2^-24 |x 2^-s|)
 // (G. Henry, P. T. P. Tang, A. Heinecke, "Leveraging the bfloat16 artificial
 // intelligence datatype for higher-precision computations", ARITH 2019).  The
 // power-of-two scale 2^s is chosen per row of A and per column of B from the
@@ -15,9 +16,10 @@
 //                       256 rows, atomicMax on the float bit pattern, which
 //                       orders like the value for non-negative floats).
 //   split_pack_kernel   one block per 128 x 64 tile of A or bn x 64 tile of
-//                       B^T: scale, split, write the hi and lo bf16 tiles of
-//                       the pack (layout in mm_internal.h); zero outside the
-//                       matrix so the tensor-core kernel needs no edge checks.
+//                       B^T: scale, split, write the bf16 parts (hi, lo - or
+//                       hi, mid, lo for the three-part split) of the pack
+//                       (layout in mm_internal.h); zero outside the matrix
+//                       so the tensor-core kernel needs no edge checks.
 #include "split_common.cuh"
 
 namespace mm {
@@ -77,14 +79,23 @@ split_scale_kernel(const SplitProb *__restrict__ probs, int nprobs) {
   }
 }
 
-__device__ __forceinline__ void split2(float x0, float x1, int s, __nv_bfloat162 &hi,
-                                       __nv_bfloat162 &lo) {
-  const float y0 = ldexpf(x0, -s), y1 = ldexpf(x1, -s);
-  hi = __floats2bfloat162_rn(y0, y1);
-  const float2 h = __bfloat1622float2(hi);
-  lo = __floats2bfloat162_rn(y0 - h.x, y1 - h.y);
+// Splits two values scaled by 2^-s into PARTS bf16 pairs: part 0 = RN(y),
+// part q = RN(y - part 0 - ... - part q-1).  Every remainder is exact in FP32
+// (the difference of a float and its rounding to fewer bits), so
+// y = sum of parts + d with |d| <= 2^(-8*PARTS) |y|.
+template <int PARTS>
+__device__ __forceinline__ void split_pair(float x0, float x1, int s, __nv_bfloat162 (&out)[PARTS]) {
+  float y0 = ldexpf(x0, -s), y1 = ldexpf(x1, -s);
+#pragma unroll
+  for (int q = 0; q < PARTS; q++) {
+    out[q] = __floats2bfloat162_rn(y0, y1);
+    const float2 h = __bfloat1622float2(out[q]);
+    y0 -= h.x;
+    y1 -= h.y;
+  }
 }
 
+template <int PARTS>
 __global__ void __launch_bounds__(256)
 split_pack_kernel(const SplitProb *__restrict__ probs, int nprobs,
                   __nv_bfloat162 *__restrict__ pack) {
@@ -97,7 +108,7 @@ split_pack_kernel(const SplitProb *__restrict__ probs, int nprobs,
   if (local < pr.mt * pr.kt) {
     // A tile (mt, kb): rows mt*128.., k kb*64..; a warp covers one row.
     const int mt = local / pr.kt, kb = local % pr.kt;
-    const int64_t base = pr.a_row0 + (int64_t)local * 2 * kTcBM;
+    const int64_t base = pr.a_row0 + (int64_t)local * PARTS * kTcBM;
     for (int q = tid; q < kTcBM * kPairs; q += 256) {
       const int r = q / kPairs, kp = q % kPairs;
       const int64_t i = (int64_t)mt * kTcBM + r;
@@ -110,10 +121,10 @@ split_pack_kernel(const SplitProb *__restrict__ probs, int nprobs,
         if (k + 1 < pr.m) x1 = row[k + 1];
         s = scale_exponent(pr.sA[i]);
       }
-      __nv_bfloat162 hi, lo;
-      split2(x0, x1, s, hi, lo);
-      pack[(base + r) * kPairs + kp] = hi;
-      pack[(base + kTcBM + r) * kPairs + kp] = lo;
+      __nv_bfloat162 part[PARTS];
+      split_pair<PARTS>(x0, x1, s, part);
+#pragma unroll
+      for (int h = 0; h < PARTS; h++) pack[(base + h * kTcBM + r) * kPairs + kp] = part[h];
     }
   } else {
     // B tile (nt, kb): columns nt*bn.., k kb*64..; transposed through shared
@@ -122,7 +133,7 @@ split_pack_kernel(const SplitProb *__restrict__ probs, int nprobs,
     const int b = local - pr.mt * pr.kt;
     const int nt = b / pr.kt, kb = b % pr.kt;
     const int bn = pr.bn;
-    const int64_t base = pr.b_row0 + (int64_t)b * 2 * bn;
+    const int64_t base = pr.b_row0 + (int64_t)b * PARTS * bn;
     for (int c0 = 0; c0 < bn; c0 += 64) {
       for (int q = tid; q < kPackK * 64; q += 256) {
         const int kk = q / 64, c = q % 64;
@@ -135,10 +146,10 @@ split_pack_kernel(const SplitProb *__restrict__ probs, int nprobs,
         const int c = q / kPairs, kp = q % kPairs;
         const int64_t j = (int64_t)nt * bn + c0 + c;
         const int s = j < pr.p ? scale_exponent(pr.tB[j]) : 0;
-        __nv_bfloat162 hi, lo;
-        split2(tile[2 * kp][c], tile[2 * kp + 1][c], s, hi, lo);
-        pack[(base + c0 + c) * kPairs + kp] = hi;
-        pack[(base + bn + c0 + c) * kPairs + kp] = lo;
+        __nv_bfloat162 part[PARTS];
+        split_pair<PARTS>(tile[2 * kp][c], tile[2 * kp + 1][c], s, part);
+#pragma unroll
+        for (int h = 0; h < PARTS; h++) pack[(base + h * bn + c0 + c) * kPairs + kp] = part[h];
       }
       __syncthreads();
     }
@@ -155,12 +166,15 @@ cudaError_t launch_split_scale(const SplitProb *d_probs, int nprobs, int total_i
   return cudaGetLastError();
 }
 
-cudaError_t launch_split_pack(const SplitProb *d_probs, int nprobs, int total_tiles,
+cudaError_t launch_split_pack(TcKind kind, const SplitProb *d_probs, int nprobs, int total_tiles,
                               void *pack_base, cudaStream_t s) {
   if (total_tiles <= 0) return cudaSuccess;
   TraceScope ts("split_pack", s);
-  split_pack_kernel<<<total_tiles, 256, 0, s>>>(d_probs, nprobs,
-                                                 static_cast<__nv_bfloat162 *>(pack_base));
+  auto *pk = static_cast<__nv_bfloat162 *>(pack_base);
+  if (kind == kTcSplitBf16x6)
+    split_pack_kernel<3><<<total_tiles, 256, 0, s>>>(d_probs, nprobs, pk);
+  else
+    split_pack_kernel<2><<<total_tiles, 256, 0, s>>>(d_probs, nprobs, pk);
   return cudaGetLastError();
 }
 

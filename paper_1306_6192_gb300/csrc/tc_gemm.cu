@@ -1,22 +1,26 @@
-// Split-BF16x3 GEMM on the sm_103a tensor cores (tcgen05 + TMA + TMEM).
+// Tensor-core GEMM on sm_103a (tcgen05 + TMA + TMEM) for the FP32-in/out
+// paths that run on the tensor cores.
 //
-// Computes C = A.B for FP32 A, B, C from the packed bf16 hi/lo operands
-// written by split_prep.cu:
+// Split-BF16x3 kind: computes C = A.B for FP32 A, B, C from the packed bf16
+// hi/lo operands written by split_prep.cu:
 //     C_ij ~= 2^(s_i + t_j) * sum_r (Ah Bh + Ah Bl + Al Bh)_irj
 // accumulated in FP32 in tensor memory; the lo.lo product (below 2^-16
-// relative) is dropped.  The definition of the product is the paper's
-// (Section "Implementacje algorytmow", Cauchy product); the split-precision
-// method and everything below are this library's GB300 design, not the
-// paper's (its kernels, Listings 2-4, use CUDA cores only).
+// relative) is dropped.
+// E4M3 kind: one e4m3 x e4m3 product per K step of the packs written by
+// fp8.cu, with the power-of-two row/column scales of that path.
+// The definition of the product is the paper's (Section "Implementacje
+// algorytmow", Cauchy product); the split-precision method, the FP8 variant
+// and everything below are this library's GB300 design, not the paper's (its
+// kernels, Listings 2-4, use CUDA cores only).
 //
 // Kernel structure (persistent, one CTA per SM, 192 threads):
-//   warp 0    TMEM allocation; lane 0 issues TMA loads of the A hi/lo and
-//             B hi/lo tiles of each K step into a STAGES-deep shared-memory
-//             ring (mbarrier "full" with transaction bytes).
-//   warp 1    lane 0 issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32,
-//             M = 128, N = bn) three times per 16-wide K step and commits
-//             each stage back to the producer ("empty") and each finished
-//             tile to the epilogue ("acc_full").
+//   warp 0    TMEM allocation; lane 0 issues TMA loads of the A and B pack
+//             tiles (all parts) of each K step into a STAGES-deep shared-
+//             memory ring (mbarrier "full" with transaction bytes).
+//   warp 1    lane 0 issues tcgen05.mma (M = 128, N = bn, 32 bytes of K per
+//             instruction) - three per K step for the split kind, one for
+//             e4m3 - and commits each stage back to the producer ("empty")
+//             and each finished tile to the epilogue ("acc_full").
 //   warps 2-5 epilogue: tcgen05.ld of the accumulator (each warp reads its
 //             32 TMEM lanes = 32 rows), exact power-of-two unscaling, FP32
 //             stores with edge predication; then "acc_empty".
@@ -139,6 +143,16 @@ __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t
       : "memory");
 }
 
+__device__ __forceinline__ void tc_mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // Arrives once on `bar` when all previously issued MMAs of this thread finish.
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
   asm volatile(
@@ -165,23 +179,37 @@ __device__ __forceinline__ void tmem_ld_wait() {
 }
 
 // Shared-memory matrix descriptor for a K-major operand tile whose rows are
-// BK bf16 (BK*2 bytes) long, written by TMA with the matching swizzle:
-// BK = 64 -> 128-byte swizzle, BK = 32 -> 64-byte swizzle.  Groups of 8 rows
-// are 8*BK*2 bytes apart (stride byte offset); the leading byte offset is
-// not used by swizzled K-major layouts.
-template <int BK>
+// BKB bytes long, written by TMA with the matching swizzle: BKB = 128 ->
+// 128-byte swizzle, BKB = 64 -> 64-byte swizzle.  Groups of 8 rows are 8*BKB
+// bytes apart (stride byte offset); the leading byte offset is not used by
+// swizzled K-major layouts.
+template <int BKB>
 __device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr) {
-  constexpr uint64_t kSbo = 8ull * BK * 2;
-  constexpr uint64_t kLayout = BK == 64 ? 2ull : 4ull;  // SWIZZLE_128B : SWIZZLE_64B
+  constexpr uint64_t kSbo = 8ull * BKB;
+  constexpr uint64_t kLayout = BKB == 128 ? 2ull : 4ull;  // SWIZZLE_128B : SWIZZLE_64B
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | (1ull << 16) | ((kSbo >> 4) << 32) |
          (1ull << 46) | (kLayout << 61);
 }
 
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major,
-// N = bn, M = 128.
+// Instruction descriptor: D = F32, both operands K-major, N = bn, M = 128;
+// kind::f16 with A = B = BF16 (format 1), or kind::f8f6f4 with A = B = E4M3
+// (format 0).
+template <int KIND>
 __device__ __forceinline__ uint32_t make_idesc(int bn) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) |
+  constexpr uint32_t fmt = KIND == kTcE4m3 ? 0u : 1u;
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(bn >> 3) << 17) |
          ((uint32_t)(kTcBM >> 4) << 24);
+}
+
+// Power-of-two exponent applied to a row/column in the epilogue: the split
+// path scales to max |x 2^-s| in [1, 2); the e4m3 path to [128, 256), which
+// stays below the e4m3 maximum 448 and keeps 13 binades above its subnormals.
+template <int KIND>
+__device__ __forceinline__ int kind_exponent(uint32_t max_bits) {
+  const int e = scale_exponent(max_bits);
+  if (KIND != kTcE4m3) return e;
+  const float f = __uint_as_float(max_bits);
+  return (f > 0.0f && f <= 3.402823466e38f) ? e - 7 : 0;
 }
 
 struct TileCoord {
@@ -201,21 +229,23 @@ __device__ __forceinline__ TileCoord decode_tile(const SplitProb *__restrict__ p
   return TileCoord{g, first + in % rows, in / rows};
 }
 
-template <int BK, int STAGES>
+template <int BKB, int STAGES, int KIND>
 struct TcLayout {
-  static constexpr int kABytes = kTcBM * BK * 2;       // one part (hi or lo) of A
-  static constexpr int kBBytesMax = kMaxBN * BK * 2;   // one part of B at bn = 256
-  static constexpr int kStageBytes = 2 * kABytes + 2 * kBBytesMax;
+  static constexpr int kParts = KIND == kTcE4m3 ? 1 : (KIND == kTcSplitBf16x3 ? 2 : 3);
+  static constexpr int kElemBytes = KIND == kTcE4m3 ? 1 : 2;
+  static constexpr int kAPart = kTcBM * BKB;            // one part of A per stage
+  static constexpr int kBPartMax = kMaxBN * BKB;        // one part of B at bn = 256
+  static constexpr int kStageBytes = kParts * (kAPart + kBPartMax);
   static constexpr int kBarOffset = STAGES * kStageBytes;
   static constexpr int kNumBars = 2 * STAGES + 4 + 1;  // full, empty, acc_full/empty, drain
   static constexpr int kSmemBytes = kBarOffset + kNumBars * 8 + 16 + 1024;  // + align slack
 };
 
-template <int BK, int STAGES>
+template <int BKB, int STAGES, int KIND>
 __global__ void __launch_bounds__(kThreads, 1)
-split_tc_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__restrict__ probs,
-                int nprobs, int total_tiles, int *err) {
-  using L = TcLayout<BK, STAGES>;
+tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__restrict__ probs,
+               int nprobs, int total_tiles, int *err) {
+  using L = TcLayout<BKB, STAGES, KIND>;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sbase = (raw + 1023u) & ~1023u;
@@ -267,8 +297,8 @@ split_tc_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__res
         const TileCoord tc = decode_tile(probs, nprobs, t);
         const SplitProb &pr = probs[tc.g];
         const int bn = pr.bn;
-        const int kiters = (pr.m + BK - 1) / BK;
-        const uint32_t bytes = (uint32_t)(2 * kTcBM + 2 * bn) * BK * 2;
+        const int kiters = (int)(((int64_t)pr.m * L::kElemBytes + BKB - 1) / BKB);
+        const uint32_t bytes = (uint32_t)(L::kParts * (kTcBM + bn) * BKB);
         for (int ki = 0; ki < kiters; ki++) {
           if (!mbar_wait(empty_bar(stage), phase ^ 1u, err, 1, true, kWaitLimitNs)) {
             ok = false;
@@ -277,16 +307,18 @@ split_tc_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__res
           mbar_arrive_expect_tx(full_bar(stage), bytes);
           armed[stage] = 1;
           armed_parity[stage] = phase;
-          const int kb = (ki * BK) / kPackK;
-          const int x = (ki * BK) % kPackK;
-          const int64_t arow = pr.a_row0 + ((int64_t)tc.mt * pr.kt + kb) * (2 * kTcBM);
-          const int64_t brow = pr.b_row0 + ((int64_t)tc.nt * pr.kt + kb) * (2 * bn);
+          const int kb = (ki * BKB) / kPackRowBytes;
+          const int x = (ki * BKB) % kPackRowBytes;  // byte offset in the pack row
+          const int64_t arow = pr.a_row0 + ((int64_t)tc.mt * pr.kt + kb) * (L::kParts * kTcBM);
+          const int64_t brow = pr.b_row0 + ((int64_t)tc.nt * pr.kt + kb) * (L::kParts * bn);
           const uint32_t st = sbase + stage * L::kStageBytes;
-          tma_load_2d(st, &tmap, x, (int)arow, full_bar(stage));
-          tma_load_2d(st + L::kABytes, &tmap, x, (int)(arow + kTcBM), full_bar(stage));
-          for (int r = 0; r < 2 * bn; r += kBoxRows)
-            tma_load_2d(st + 2 * L::kABytes + r * BK * 2, &tmap, x, (int)(brow + r),
+#pragma unroll
+          for (int part = 0; part < L::kParts; part++)
+            tma_load_2d(st + part * L::kAPart, &tmap, x, (int)(arow + part * kTcBM),
                         full_bar(stage));
+          const uint32_t sb = st + L::kParts * L::kAPart;
+          for (int r = 0; r < L::kParts * bn; r += kBoxRows)
+            tma_load_2d(sb + r * BKB, &tmap, x, (int)(brow + r), full_bar(stage));
           if (++stage == STAGES) {
             stage = 0;
             phase ^= 1u;
@@ -310,9 +342,9 @@ split_tc_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__res
       for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
         const TileCoord tc = decode_tile(probs, nprobs, t);
         const SplitProb &pr = probs[tc.g];
-        const int kiters = (pr.m + BK - 1) / BK;
-        const uint32_t idesc = make_idesc(pr.bn);
-        const uint32_t blo = (uint32_t)pr.bn * BK * 2;
+        const int kiters = (int)(((int64_t)pr.m * L::kElemBytes + BKB - 1) / BKB);
+        const uint32_t idesc = make_idesc<KIND>(pr.bn);
+        const uint32_t blo = (uint32_t)pr.bn * BKB;
         if (!mbar_wait(acce_bar(acc), acc_phase ^ 1u, err, 2, true, kWaitLimitNs)) {
           ok = false;
           break;
@@ -326,16 +358,36 @@ split_tc_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__res
           }
           tc_fence_after();
           const uint32_t st = sbase + stage * L::kStageBytes;
-          const uint64_t a_hi = kmajor_desc<BK>(st);
-          const uint64_t a_lo = kmajor_desc<BK>(st + L::kABytes);
-          const uint64_t b_hi = kmajor_desc<BK>(st + 2 * L::kABytes);
-          const uint64_t b_lo = kmajor_desc<BK>(st + 2 * L::kABytes + blo);
+          const uint32_t sb = st + L::kParts * L::kAPart;
+          const uint64_t a0 = kmajor_desc<BKB>(st);
+          const uint64_t b0 = kmajor_desc<BKB>(sb);
 #pragma unroll
-          for (int k16 = 0; k16 < BK / 16; k16++) {
-            const uint64_t adv = (uint64_t)(k16 * 32) >> 4;  // 16 bf16 = 32 bytes
-            tc_mma(d_tmem, a_hi + adv, b_hi + adv, idesc, (ki | k16) != 0 ? 1u : 0u);
-            tc_mma(d_tmem, a_hi + adv, b_lo + adv, idesc, 1u);
-            tc_mma(d_tmem, a_lo + adv, b_hi + adv, idesc, 1u);
+          for (int kk = 0; kk < BKB / 32; kk++) {
+            // 32 bytes of K per instruction: 16 bf16 or 32 e4m3
+            const uint64_t adv = (uint64_t)(kk * 32) >> 4;
+            const uint32_t acc_in = (ki | kk) != 0 ? 1u : 0u;
+            if (KIND == kTcSplitBf16x3) {
+              const uint64_t a1 = kmajor_desc<BKB>(st + L::kAPart);
+              const uint64_t b1 = kmajor_desc<BKB>(sb + blo);
+              tc_mma(d_tmem, a0 + adv, b0 + adv, idesc, acc_in);  // hi.hi
+              tc_mma(d_tmem, a0 + adv, b1 + adv, idesc, 1u);      // hi.lo
+              tc_mma(d_tmem, a1 + adv, b0 + adv, idesc, 1u);      // lo.hi
+            } else if (KIND == kTcSplitBf16x6) {
+              // parts 0/1/2 = hi/mid/lo; products of relative size >= 2^-16,
+              // smallest first
+              const uint64_t a1 = kmajor_desc<BKB>(st + L::kAPart);
+              const uint64_t a2 = kmajor_desc<BKB>(st + 2 * L::kAPart);
+              const uint64_t b1 = kmajor_desc<BKB>(sb + blo);
+              const uint64_t b2 = kmajor_desc<BKB>(sb + 2 * blo);
+              tc_mma(d_tmem, a1 + adv, b1 + adv, idesc, acc_in);  // mid.mid
+              tc_mma(d_tmem, a0 + adv, b2 + adv, idesc, 1u);      // hi.lo
+              tc_mma(d_tmem, a2 + adv, b0 + adv, idesc, 1u);      // lo.hi
+              tc_mma(d_tmem, a0 + adv, b1 + adv, idesc, 1u);      // hi.mid
+              tc_mma(d_tmem, a1 + adv, b0 + adv, idesc, 1u);      // mid.hi
+              tc_mma(d_tmem, a0 + adv, b0 + adv, idesc, 1u);      // hi.hi
+            } else {
+              tc_mma_f8(d_tmem, a0 + adv, b0 + adv, idesc, acc_in);
+            }
           }
           issued = true;
           tc_commit(empty_bar(stage));
@@ -370,7 +422,7 @@ split_tc_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__res
       tc_fence_after();
       const int64_t i = (int64_t)tc.mt * kTcBM + row;
       const bool row_ok = i < pr.n;
-      const int si = row_ok ? scale_exponent(pr.sA[i]) : 0;
+      const int si = row_ok ? kind_exponent<KIND>(pr.sA[i]) : 0;
       float *crow = pr.C + (row_ok ? i : 0) * (int64_t)pr.p;
       const bool vec = ((reinterpret_cast<uintptr_t>(pr.C) & 15u) == 0) && ((pr.p & 3) == 0);
       const uint32_t tacc = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kAccCols);
@@ -385,17 +437,17 @@ split_tc_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__res
 #pragma unroll
           for (int e = 0; e < 32; e += 4) {
             float4 o;
-            o.x = ldexpf(__uint_as_float(v[e + 0]), si + scale_exponent(pr.tB[j0 + e + 0]));
-            o.y = ldexpf(__uint_as_float(v[e + 1]), si + scale_exponent(pr.tB[j0 + e + 1]));
-            o.z = ldexpf(__uint_as_float(v[e + 2]), si + scale_exponent(pr.tB[j0 + e + 2]));
-            o.w = ldexpf(__uint_as_float(v[e + 3]), si + scale_exponent(pr.tB[j0 + e + 3]));
+            o.x = ldexpf(__uint_as_float(v[e + 0]), si + kind_exponent<KIND>(pr.tB[j0 + e + 0]));
+            o.y = ldexpf(__uint_as_float(v[e + 1]), si + kind_exponent<KIND>(pr.tB[j0 + e + 1]));
+            o.z = ldexpf(__uint_as_float(v[e + 2]), si + kind_exponent<KIND>(pr.tB[j0 + e + 2]));
+            o.w = ldexpf(__uint_as_float(v[e + 3]), si + kind_exponent<KIND>(pr.tB[j0 + e + 3]));
             *reinterpret_cast<float4 *>(crow + j0 + e) = o;
           }
         } else {
 #pragma unroll
           for (int e = 0; e < 32; e++)
             if (j0 + e < pr.p)
-              crow[j0 + e] = ldexpf(__uint_as_float(v[e]), si + scale_exponent(pr.tB[j0 + e]));
+              crow[j0 + e] = ldexpf(__uint_as_float(v[e]), si + kind_exponent<KIND>(pr.tB[j0 + e]));
         }
       }
       tc_fence_before();
@@ -430,58 +482,69 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
   return fn;
 }
 
-// 2-D map over the pack region viewed as rows of 64 bf16 (128 bytes).
-cudaError_t encode_pack_map(CUtensorMap *map, void *base, int64_t rows, int bk) {
+// 2-D map over the pack region viewed as rows of 128 bytes; a box is BKB
+// bytes of 128 consecutive rows.
+cudaError_t encode_pack_map(CUtensorMap *map, void *base, int64_t rows, int bkb) {
   auto enc = get_encode_fn();
   if (!enc) return cudaErrorNotSupported;
-  cuuint64_t dims[2] = {(cuuint64_t)kPackK, (cuuint64_t)rows};
+  cuuint64_t dims[2] = {(cuuint64_t)kPackRowBytes, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)kPackRowBytes};
-  cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)kBoxRows};
+  cuuint32_t box[2] = {(cuuint32_t)bkb, (cuuint32_t)kBoxRows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   bkb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int BK, int STAGES>
+template <int BKB, int STAGES, int KIND>
 cudaError_t launch_tc_t(const SplitProb *d_probs, int nprobs, int total_tiles, void *pack_base,
                         int64_t pack_rows, int grid, int *d_err, cudaStream_t s) {
-  using L = TcLayout<BK, STAGES>;
+  using L = TcLayout<BKB, STAGES, KIND>;
   static_assert(L::kSmemBytes <= 232448, "shared memory budget");
+  // one CTA per SM: the kernel allocates all 512 TMEM columns
+  static_assert(2 * L::kSmemBytes > 232448, "must not fit twice on one SM");
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(split_tc_kernel<BK, STAGES>,
+    attr_err = cudaFuncSetAttribute(tc_gemm_kernel<BKB, STAGES, KIND>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, L::kSmemBytes);
   });
   if (attr_err != cudaSuccess) return attr_err;
   CUtensorMap map;
-  cudaError_t e = encode_pack_map(&map, pack_base, pack_rows, BK);
+  cudaError_t e = encode_pack_map(&map, pack_base, pack_rows, BKB);
   if (e != cudaSuccess) return e;
-  TraceScope ts("split_tc", s);
-  split_tc_kernel<BK, STAGES><<<grid, kThreads, L::kSmemBytes, s>>>(map, d_probs, nprobs,
-                                                                     total_tiles, d_err);
+  TraceScope ts(KIND == kTcE4m3 ? "fp8_tc" : "split_tc", s);
+  tc_gemm_kernel<BKB, STAGES, KIND><<<grid, kThreads, L::kSmemBytes, s>>>(map, d_probs, nprobs,
+                                                                         total_tiles, d_err);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_split_tc(const SplitProb *d_probs, int nprobs, int total_tiles,
-                            void *pack_base, int64_t pack_rows, const TcConfig &cfg, int *d_err,
-                            cudaStream_t s) {
+cudaError_t launch_tc(TcKind kind, const SplitProb *d_probs, int nprobs, int total_tiles,
+                      void *pack_base, int64_t pack_rows, const TcConfig &cfg, int *d_err,
+                      cudaStream_t s) {
   if (total_tiles <= 0) return cudaSuccess;
   if (pack_rows <= 0 || pack_rows > 0x7fffffffLL) return cudaErrorInvalidValue;
   int grid = cfg.grid > 0 ? cfg.grid : sm_count();
   if (grid > total_tiles) grid = total_tiles;
-  if (cfg.bk == 64) return launch_tc_t<64, 2>(d_probs, nprobs, total_tiles, pack_base, pack_rows,
-                                             grid, d_err, s);
-  if (cfg.bk == 32) {
+  if (kind == kTcE4m3)
+    return launch_tc_t<128, 4, kTcE4m3>(d_probs, nprobs, total_tiles, pack_base, pack_rows, grid,
+                                        d_err, s);
+  if (kind == kTcSplitBf16x6)
+    return launch_tc_t<64, 3, kTcSplitBf16x6>(d_probs, nprobs, total_tiles, pack_base, pack_rows,
+                                              grid, d_err, s);
+  if (cfg.bkb == 128)
+    return launch_tc_t<128, 2, kTcSplitBf16x3>(d_probs, nprobs, total_tiles, pack_base, pack_rows,
+                                               grid, d_err, s);
+  if (cfg.bkb == 64) {
     if (cfg.stages == 3)
-      return launch_tc_t<32, 3>(d_probs, nprobs, total_tiles, pack_base, pack_rows, grid, d_err,
-                                s);
-    return launch_tc_t<32, 4>(d_probs, nprobs, total_tiles, pack_base, pack_rows, grid, d_err, s);
+      return launch_tc_t<64, 3, kTcSplitBf16x3>(d_probs, nprobs, total_tiles, pack_base,
+                                                pack_rows, grid, d_err, s);
+    return launch_tc_t<64, 4, kTcSplitBf16x3>(d_probs, nprobs, total_tiles, pack_base, pack_rows,
+                                              grid, d_err, s);
   }
   return cudaErrorInvalidValue;
 }

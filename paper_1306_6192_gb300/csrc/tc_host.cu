@@ -1,0 +1,133 @@
+// Host side of the tensor-core paths (split-BF16x3 / x6 and e4m3): builds the
+// problem tables, lays out the scratch (pack rows, scale words, tables) and
+// queues prep + tensor-core kernels, one launch per kernel and kind.
+#include <cmath>
+#include <cstring>
+
+#include "ctx.h"
+
+namespace mm {
+
+TcKind split_kind_for(int64_t m) {
+  return 3.1 * std::ldexp(1.0, -16) <= 1e-6 * std::sqrt((double)m) ? kTcSplitBf16x3
+                                                                    : kTcSplitBf16x6;
+}
+
+namespace {
+
+struct Group {
+  TcKind kind;
+  TcConfig cfg{0, 0, 0};
+  std::vector<SplitProb> tab;
+  int64_t tiles = 0, packs = 0, reds = 0;
+};
+
+mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s,
+                        const TcChoice *force, bool fp8) {
+  Group groups[3] = {{kTcSplitBf16x3}, {kTcSplitBf16x6}, {kTcE4m3}};
+  int64_t rows = 0, scal = 0;
+  for (int g = 0; g < count; g++) {
+    const mm_problem &q = probs[g];
+    if (q.n == 0 || q.p == 0) continue;
+    if (q.m == 0) {
+      cudaError_t e = cudaMemsetAsync(q.C, 0, (size_t)(q.n * q.p) * sizeof(float), s);
+      if (e != cudaSuccess) return note_cuda(e);
+      continue;
+    }
+    const TcKind kind = fp8 ? kTcE4m3 : split_kind_for(q.m);
+    Group &G = groups[kind == kTcSplitBf16x3 ? 0 : (kind == kTcSplitBf16x6 ? 1 : 2)];
+    const TcChoice ch = force ? *force : tune_choose(q.n, q.m, q.p);
+    if (G.tab.empty()) {
+      if (kind == kTcSplitBf16x3) G.cfg = TcConfig{2 * ch.bk, ch.stages, ch.grid};
+      else if (kind == kTcSplitBf16x6) G.cfg = TcConfig{64, 3, ch.grid};
+      else G.cfg = TcConfig{128, 4, ch.grid};
+    }
+    const int parts = pack_parts(kind);
+    SplitProb sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.A = static_cast<const float *>(q.A);
+    sp.B = static_cast<const float *>(q.B);
+    sp.C = static_cast<float *>(q.C);
+    sp.n = (int32_t)q.n;
+    sp.m = (int32_t)q.m;
+    sp.p = (int32_t)q.p;
+    sp.bn = ch.bn;
+    sp.group_m = ch.group_m;
+    sp.mt = (int32_t)ceil_div(q.n, kTcBM);
+    sp.nt = (int32_t)ceil_div(q.p, ch.bn);
+    sp.kt = (int32_t)ceil_div(q.m, pack_k(kind));
+    sp.a_row0 = rows;
+    rows += (int64_t)sp.mt * sp.kt * parts * kTcBM;
+    sp.b_row0 = rows;
+    rows += (int64_t)sp.nt * sp.kt * parts * ch.bn;
+    sp.sA = reinterpret_cast<uint32_t *>((uintptr_t)scal);  // offsets, fixed below
+    scal += q.n;
+    sp.tB = reinterpret_cast<uint32_t *>((uintptr_t)scal);
+    scal += q.p;
+    sp.tile_start = (int32_t)G.tiles;
+    G.tiles += (int64_t)sp.mt * sp.nt;
+    sp.pack_start = (int32_t)G.packs;
+    G.packs += (int64_t)sp.mt * sp.kt + (int64_t)sp.nt * sp.kt;
+    sp.red_start = (int32_t)G.reds;
+    sp.red_a = (int32_t)ceil_div(q.n, 8);
+    G.reds += sp.red_a + ceil_div(q.p, 32) * ceil_div(q.m, 256);
+    G.tab.push_back(sp);
+  }
+  size_t ntab = 0;
+  for (auto &G : groups) {
+    if (G.tiles > 0x7fffffffLL || G.packs > 0x7fffffffLL || G.reds > 0x7fffffffLL)
+      return MM_EINVAL;
+    ntab += G.tab.size();
+  }
+  if (ntab == 0) return MM_OK;
+  if (rows > 0x7fffffffLL) return MM_EINVAL;
+  const size_t pack_bytes = (size_t)rows * kPackRowBytes;
+  const size_t scal_off = (pack_bytes + 255) & ~(size_t)255;
+  const size_t tab_off = (scal_off + (size_t)scal * 4 + 255) & ~(size_t)255;
+  const size_t need = tab_off + ntab * sizeof(SplitProb);
+  cudaError_t e = ws.reserve(need, s);
+  if (e != cudaSuccess) return note_cuda(e);
+  uint8_t *base = static_cast<uint8_t *>(ws.ptr);
+  std::vector<SplitProb> all;
+  all.reserve(ntab);
+  for (auto &G : groups)
+    for (auto &sp : G.tab) {
+      sp.sA = reinterpret_cast<uint32_t *>(base + scal_off) + (uintptr_t)sp.sA;
+      sp.tB = reinterpret_cast<uint32_t *>(base + scal_off) + (uintptr_t)sp.tB;
+      all.push_back(sp);
+    }
+  SplitProb *d_tab = reinterpret_cast<SplitProb *>(base + tab_off);
+  e = cudaMemcpyAsync(d_tab, all.data(), all.size() * sizeof(SplitProb), cudaMemcpyHostToDevice,
+                      s);
+  if (e != cudaSuccess) return note_cuda(e);
+  e = cudaMemsetAsync(base + scal_off, 0, (size_t)scal * 4, s);
+  if (e != cudaSuccess) return note_cuda(e);
+  size_t off = 0;
+  for (auto &G : groups) {
+    if (G.tab.empty()) continue;
+    const SplitProb *dt = d_tab + off;
+    const int np = (int)G.tab.size();
+    off += G.tab.size();
+    e = launch_split_scale(dt, np, (int)G.reds, s);
+    if (e != cudaSuccess) return note_cuda(e);
+    e = G.kind == kTcE4m3 ? launch_fp8_pack(dt, np, (int)G.packs, base, s)
+                          : launch_split_pack(G.kind, dt, np, (int)G.packs, base, s);
+    if (e != cudaSuccess) return note_cuda(e);
+    e = launch_tc(G.kind, dt, np, (int)G.tiles, base, rows, G.cfg, g_ctx.d_err, s);
+    if (e != cudaSuccess) return note_cuda(e);
+  }
+  return MM_OK;
+}
+
+}  // namespace
+
+mm_status run_split(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s,
+                    const TcChoice *force) {
+  return run_tc_groups(ws, probs, count, s, force, false);
+}
+
+mm_status run_fp8(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s) {
+  return run_tc_groups(ws, probs, count, s, nullptr, true);
+}
+
+}  // namespace mm

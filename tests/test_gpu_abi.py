@@ -97,7 +97,8 @@ def test_tune_table_roundtrip(mmlib, tmp_path):
     path = str(tmp_path / "tune.txt")
     assert mm.mm_tune_save(path) == 0
     text = open(path).read()
-    assert "%d %d %d %d" % (9, 9, 9, bn) in text
+    # buckets are ceil(log2) of each size: 256 -> 8, 512 -> 9, 384 -> 9
+    assert "%d %d %d %d" % (8, 9, 9, bn) in text
     bad = tmp_path / "bad.txt"
     bad.write_text("9 9 9 100 32 4 8 0\n")
     assert mm.mm_tune_load(str(bad)) == mm.MM_EINVAL

@@ -29,7 +29,7 @@ def test_check_matches_oracle(mmlib, f64):
     tdt = torch.float64 if f64 else torch.float32
     # a computed product with a known perturbation in one entry
     C = (A.astype(np.float64) @ B.astype(np.float64))
-    C[17, 33] += 1e-3
+    C[17, 33] += 10.0
     C = C.astype(np.float64 if f64 else np.float32)
     x = synth.freivalds_vector(603, p)
     I, J = synth.sample_indices(604, n, p, 512)

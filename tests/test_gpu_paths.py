@@ -26,6 +26,22 @@ def test_uniform_matches_oracle(mmlib, shape, mode):
     assert_full(C, A, B, "f64" if mode == "dgemm" else "f32")
 
 
+@pytest.mark.parametrize("m", [1, 2, 15, 64, 2200, 2300, 3000])
+def test_split_across_the_part_threshold(mmlib, m):
+    """The split path uses three bf16 parts below m ~ 2240 and two above; both
+    sides of the switch meet the tolerance, including a single-term dot
+    product per entry (B with one non-zero per column)."""
+    n, p = 96, 140
+    A = synth.uniform_pm1(900 + m, (n, m))
+    B = synth.uniform_pm1(901 + m, (m, p))
+    C = run_gemm(mmlib, A, B, mmlib.MM_MODE_SPLIT_BF16X3)
+    assert_full(C, A, B, "f32")
+    Bs = np.zeros((m, p), np.float32)
+    Bs[np.arange(p) % m, np.arange(p)] = synth.uniform_pm1(902 + m, p)
+    C = run_gemm(mmlib, A, Bs, mmlib.MM_MODE_SPLIT_BF16X3)
+    assert_full(C, A, Bs, "f32")
+
+
 def test_config1_full_check(mmlib):
     """n = m = p = 256, entries uniform[-1,1) from seed 0 (A) / 1 (B): every
     entry of the plain SIMT kernel against the FP64 oracle."""
