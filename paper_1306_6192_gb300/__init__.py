@@ -9,6 +9,7 @@ instead of falling back to anything else.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
 
@@ -87,7 +88,14 @@ def lib():
                      "mm_tune_query", "mm_trace_enable", "mm_trace_reset", "mm_trace_read"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
+        atexit.register(_shutdown_at_exit)
     return _lib
+
+
+def _shutdown_at_exit():
+    # stops the serving thread and frees library memory while CUDA is alive
+    if _lib is not None:
+        _lib.mm_shutdown()
 
 
 def _ptr(x):

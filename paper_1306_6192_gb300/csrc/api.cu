@@ -70,6 +70,54 @@ void Scratch::release() {
   if (ptr) cudaFree(ptr);
   ptr = nullptr;
   bytes = 0;
+  stage.release();
+}
+
+cudaError_t HostStage::copy_to_device(void *dst, const void *src, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int k = next;
+  next = (next + 1) % kSlots;
+  if (pending[k]) {
+    cudaError_t e = cudaEventSynchronize(ev[k]);  // that slot's copy has run
+    if (e != cudaSuccess) return e;
+    pending[k] = false;
+  }
+  if (n > bytes[k]) {
+    if (ptr[k]) cudaFreeHost(ptr[k]);
+    ptr[k] = nullptr;
+    bytes[k] = 0;
+    const size_t want = std::max(n, (size_t)64 << 10);
+    if (cudaMallocHost(&ptr[k], want) != cudaSuccess) {
+      cudaGetLastError();
+      ptr[k] = nullptr;
+      return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s);  // pageable fallback
+    }
+    bytes[k] = want;
+  }
+  if (!ev[k] && cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    ev[k] = nullptr;
+    return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s);
+  }
+  std::memcpy(ptr[k], src, n);
+  cudaError_t e = cudaMemcpyAsync(dst, ptr[k], n, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  e = cudaEventRecord(ev[k], s);
+  pending[k] = e == cudaSuccess;
+  return e;
+}
+
+void HostStage::release() {
+  for (int k = 0; k < kSlots; k++) {
+    if (pending[k] && ev[k]) cudaEventSynchronize(ev[k]);
+    if (ptr[k]) cudaFreeHost(ptr[k]);
+    if (ev[k]) cudaEventDestroy(ev[k]);
+    ptr[k] = nullptr;
+    ev[k] = nullptr;
+    bytes[k] = 0;
+    pending[k] = false;
+  }
+  next = 0;
 }
 
 // ---------------------------------------------------------------- tracing
@@ -281,6 +329,13 @@ mm_status mm_init(const mm_opts *opts) {
     cudaStreamDestroy(g_ctx.stream);
     return from_cuda(e);
   }
+  bool ok = cudaStreamCreateWithFlags(&g_ctx.h2d, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&g_ctx.d2h, cudaStreamNonBlocking) == cudaSuccess;
+  for (int c = 0; c <= Ctx::kMaxChunks && ok; c++)
+    ok = cudaEventCreateWithFlags(&g_ctx.ev_in[c], cudaEventDisableTiming) == cudaSuccess;
+  for (int c = 0; c < Ctx::kMaxChunks && ok; c++)
+    ok = cudaEventCreateWithFlags(&g_ctx.ev_out[c], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) return MM_ECUDA;
   cudaMemset(g_ctx.d_err, 0, 256);
   tune_reset_defaults();
   if (o.tune_table) {
@@ -315,6 +370,13 @@ mm_status mm_shutdown(void) {
   if (g_ctx.d_err) cudaFree(g_ctx.d_err);
   g_ctx.d_err = nullptr;
   trace_destroy();
+  for (auto &ev : g_ctx.ev_in)
+    if (ev) cudaEventDestroy(ev), ev = nullptr;
+  for (auto &ev : g_ctx.ev_out)
+    if (ev) cudaEventDestroy(ev), ev = nullptr;
+  if (g_ctx.h2d) cudaStreamDestroy(g_ctx.h2d);
+  if (g_ctx.d2h) cudaStreamDestroy(g_ctx.d2h);
+  g_ctx.h2d = g_ctx.d2h = nullptr;
   cudaStreamDestroy(g_ctx.stream);
   g_ctx.stream = nullptr;
   g_ctx.inited = false;
@@ -354,7 +416,7 @@ mm_status mm_gemm(int64_t n, int64_t m, int64_t p, const void *A, const void *B,
     return check_device_flag(s);
   }
   // Host operands: stage through library buffers (copies on the library
-  // stream, then the same device path).
+  // streams, then the same device path).
   const size_t ba = (size_t)(n * m) * es, bb = (size_t)(m * p) * es, bc = (size_t)(n * p) * es;
   const size_t oa = 0, ob = (ba + 255) & ~(size_t)255, oc = (ob + bb + 255) & ~(size_t)255;
   cudaError_t e = g_ctx.stage_ws.reserve(oc + bc, s);
@@ -363,6 +425,39 @@ mm_status mm_gemm(int64_t n, int64_t m, int64_t p, const void *A, const void *B,
   const void *dA = dev_a ? A : base + oa;
   const void *dB = dev_b ? B : base + ob;
   void *dC = dev_c ? C : base + oc;
+  if (resolve_mode(dt, mode) == MM_MODE_SPLIT_BF16X3 && m > 0 && n >= 2048) {
+    // Pipelined: B first, then slabs of A rows on the copy stream; each slab
+    // is prepared and multiplied as soon as it lands (B packed once), and its
+    // rows of C go back on a second copy stream while the next slab runs.
+    const int chunks = (int)std::min<int64_t>(Ctx::kMaxChunks, n / 1024);
+    const int64_t rc = ceil_div(ceil_div(n, chunks), kTcBM) * kTcBM;
+    int64_t row0[Ctx::kMaxChunks + 1];
+    for (int c = 0; c <= chunks; c++) row0[c] = std::min<int64_t>(n, c * rc);
+    if (!dev_b) e = cudaMemcpyAsync(base + ob, B, bb, cudaMemcpyHostToDevice, g_ctx.h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(g_ctx.ev_in[0], g_ctx.h2d);
+    for (int c = 0; c < chunks && e == cudaSuccess; c++) {
+      const size_t off = (size_t)(row0[c] * m) * es, len = (size_t)((row0[c + 1] - row0[c]) * m) * es;
+      if (!dev_a && len) e = cudaMemcpyAsync(base + oa + off, static_cast<const uint8_t *>(A) + off,
+                                             len, cudaMemcpyHostToDevice, g_ctx.h2d);
+      if (e == cudaSuccess) e = cudaEventRecord(g_ctx.ev_in[c + 1], g_ctx.h2d);
+    }
+    if (e != cudaSuccess) return note_cuda(e);
+    st = run_split_chunked(g_ctx.split_ws, n, m, p, static_cast<const float *>(dA),
+                           static_cast<const float *>(dB), static_cast<float *>(dC), chunks, row0, s,
+                           g_ctx.ev_in, g_ctx.ev_out);
+    if (st != MM_OK) return st;
+    for (int c = 0; c < chunks && !dev_c && e == cudaSuccess; c++) {
+      const size_t off = (size_t)(row0[c] * p) * es, len = (size_t)((row0[c + 1] - row0[c]) * p) * es;
+      e = cudaStreamWaitEvent(g_ctx.d2h, g_ctx.ev_out[c], 0);
+      if (e == cudaSuccess && len)
+        e = cudaMemcpyAsync(static_cast<uint8_t *>(C) + off, base + oc + off, len,
+                            cudaMemcpyDeviceToHost, g_ctx.d2h);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g_ctx.d2h);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g_ctx.h2d);
+    if (e != cudaSuccess) return note_cuda(e);
+    return check_device_flag(s);
+  }
   if (!dev_a && ba) {
     e = cudaMemcpyAsync(base + oa, A, ba, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return note_cuda(e);

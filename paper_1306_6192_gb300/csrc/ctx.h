@@ -6,10 +6,26 @@
 
 namespace mm {
 
+// Pinned host staging for problem tables: an asynchronous copy from pinned
+// memory does not synchronise the host with the stream (a copy from pageable
+// memory may).  The event guards reuse until the previous copy has run.
+struct HostStage {
+  static constexpr int kSlots = 4;  // calls the host may run ahead of the copies
+  void *ptr[kSlots] = {};
+  size_t bytes[kSlots] = {};
+  cudaEvent_t ev[kSlots] = {};
+  bool pending[kSlots] = {};
+  int next = 0;
+  // Copies `n` bytes from `src` to `dst` on `s` through the staging buffer.
+  cudaError_t copy_to_device(void *dst, const void *src, size_t n, cudaStream_t s);
+  void release();
+};
+
 // Grow-only device buffer owned by the library.
 struct Scratch {
   void *ptr = nullptr;
   size_t bytes = 0;
+  HostStage stage;  // host side of the tables written into this scratch
   // Makes room for `need` bytes; an existing buffer is freed after `s` has
   // drained (its contents are not kept).
   cudaError_t reserve(size_t need, cudaStream_t s);
@@ -38,6 +54,11 @@ struct Ctx {
   Scratch grouped_ws;    // tables of the grouped SIMT path
   Scratch stage_ws;      // device copies of host operands
   Scratch check_ws;      // FP64 check work vectors
+  // host-operand pipeline of mm_gemm: copy streams and per-chunk events
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  static constexpr int kMaxChunks = 8;
+  cudaEvent_t ev_in[kMaxChunks + 1] = {};
+  cudaEvent_t ev_out[kMaxChunks] = {};
 };
 
 extern Ctx g_ctx;
@@ -61,6 +82,13 @@ TcKind split_kind_for(int64_t m);
 // choice (autotuner and tests).
 mm_status run_split(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s,
                     const TcChoice *force);
+// Split path for one product whose rows of A (and of C) are processed in
+// `chunks` slabs: slab c waits for event in_ready[c + 1] (B: in_ready[0])
+// before its prep and records out_ready[c] when its part of C is written.
+// B is scaled and packed once, with slab 0.
+mm_status run_split_chunked(Scratch &ws, int64_t n, int64_t m, int64_t p, const float *A,
+                            const float *B, float *C, int chunks, const int64_t *row0,
+                            cudaStream_t s, cudaEvent_t *in_ready, cudaEvent_t *out_ready);
 // FP8 path (report-only accuracy).
 mm_status run_fp8(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s);
 // Grouped dispatch: split / SIMT / DGEMM tables in one launch per path.

@@ -48,8 +48,7 @@ mm_status enqueue_grouped(Scratch &split_ws, Scratch &tab_ws, int count, const m
   if (tiles > 0x7fffffffLL) return MM_EINVAL;
   cudaError_t e = tab_ws.reserve(tab.size() * sizeof(SimtProb), s);
   if (e != cudaSuccess) return from_cuda(e);
-  e = cudaMemcpyAsync(tab_ws.ptr, tab.data(), tab.size() * sizeof(SimtProb),
-                      cudaMemcpyHostToDevice, s);
+  e = tab_ws.stage.copy_to_device(tab_ws.ptr, tab.data(), tab.size() * sizeof(SimtProb), s);
   if (e != cudaSuccess) return from_cuda(e);
   e = launch_simt_grouped(f64, static_cast<const SimtProb *>(tab_ws.ptr), (int)tab.size(),
                           (int)tiles, all_vec, s);

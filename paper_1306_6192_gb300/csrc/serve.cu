@@ -58,6 +58,7 @@ struct Slot {
 };
 
 struct Server {
+  ~Server();
   std::thread th;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -73,6 +74,21 @@ struct Server {
 };
 
 Server g_srv;
+
+// At process exit without mm_shutdown: the scheduler may still wait on the
+// condition variables that are about to be destroyed.  Stop it first; it
+// leaves as soon as nothing it launched is still in flight.
+Server::~Server() {
+  if (!th.joinable()) return;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    stop = true;
+    pending.clear();
+    admitted.clear();
+  }
+  cv_work.notify_all();
+  th.join();
+}
 
 // SplitMix64 (Steele, Lea, Flood 2014), counter form: the check's random
 // vector entries and sample positions.

@@ -29,6 +29,14 @@ constexpr int kRowsPerScaleItem = 8;    // warps per block, one row each
 constexpr int kColStrip = 32;
 constexpr int kRowChunk = 256;
 
+__device__ __forceinline__ uint32_t abs_bits(float x) { return __float_as_uint(x) & 0x7fffffffu; }
+
+__device__ __forceinline__ uint32_t umax(uint32_t a, uint32_t b) { return a > b ? a : b; }
+
+__device__ __forceinline__ bool aligned16(const void *p) {
+  return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
+}
+
 __global__ void __launch_bounds__(256)
 split_scale_kernel(const SplitProb *__restrict__ probs, int nprobs) {
   const int item = blockIdx.x;
@@ -37,94 +45,140 @@ split_scale_kernel(const SplitProb *__restrict__ probs, int nprobs) {
   const int local = item - pr.red_start;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (local < pr.red_a) {
+    // a warp per row of A; 16-byte loads when every row start is aligned
     const int64_t i = (int64_t)local * kRowsPerScaleItem + warp;
     if (i >= pr.n) return;
     const float *row = pr.A + i * pr.m;
     uint32_t mx = 0;
-    for (int64_t k = lane; k < pr.m; k += 32) {
-      const uint32_t b = __float_as_uint(row[k]) & 0x7fffffffu;
-      mx = b > mx ? b : mx;
+    if (aligned16(pr.A) && (pr.m & 3) == 0) {
+      const float4 *r4 = reinterpret_cast<const float4 *>(row);
+      const int64_t m4 = pr.m >> 2;
+#pragma unroll 4
+      for (int64_t k = lane; k < m4; k += 32) {
+        const float4 v = r4[k];
+        mx = umax(mx, umax(umax(abs_bits(v.x), abs_bits(v.y)), umax(abs_bits(v.z), abs_bits(v.w))));
+      }
+    } else {
+#pragma unroll 4
+      for (int64_t k = lane; k < pr.m; k += 32) mx = umax(mx, abs_bits(row[k]));
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const uint32_t t = __shfl_xor_sync(0xffffffffu, mx, o);
-      mx = t > mx ? t : mx;
-    }
+    for (int o = 16; o > 0; o >>= 1) mx = umax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) pr.sA[i] = mx;
   } else {
-    __shared__ uint32_t part[8][kColStrip];
+    // a strip of 32 columns x 256 rows of B; the block's maxima are merged
+    // into the column words with atomicMax
+    __shared__ uint32_t part[32][kColStrip + 1];
     const int b = local - pr.red_a;
     const int strips = (pr.p + kColStrip - 1) / kColStrip;
     const int strip = b % strips, chunk = b / strips;
-    const int64_t col = (int64_t)strip * kColStrip + lane;
-    const int64_t r0 = (int64_t)chunk * kRowChunk + warp * (kRowChunk / 8);
-    uint32_t mx = 0;
-    if (col < pr.p) {
-#pragma unroll 8
-      for (int r = 0; r < kRowChunk / 8; r++) {
+    const int64_t c0 = (int64_t)strip * kColStrip;
+    const int64_t r0 = (int64_t)chunk * kRowChunk;
+    const int tid = threadIdx.x;
+    if (aligned16(pr.B) && (pr.p & 3) == 0 && c0 + kColStrip <= pr.p) {
+      // 8 threads x 4 columns cover a 128-byte row segment; 32 row groups
+      const int cq = tid & 7, grp = tid >> 3;
+      uint32_t m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+#pragma unroll 4
+      for (int r = grp; r < kRowChunk; r += 32) {
         const int64_t k = r0 + r;
         if (k < pr.m) {
-          const uint32_t v = __float_as_uint(pr.B[k * pr.p + col]) & 0x7fffffffu;
-          mx = v > mx ? v : mx;
+          const float4 v = *reinterpret_cast<const float4 *>(pr.B + k * pr.p + c0 + 4 * cq);
+          m0 = umax(m0, abs_bits(v.x));
+          m1 = umax(m1, abs_bits(v.y));
+          m2 = umax(m2, abs_bits(v.z));
+          m3 = umax(m3, abs_bits(v.w));
         }
       }
-    }
-    part[warp][lane] = mx;
-    __syncthreads();
-    if (warp == 0) {
+      part[grp][4 * cq + 0] = m0;
+      part[grp][4 * cq + 1] = m1;
+      part[grp][4 * cq + 2] = m2;
+      part[grp][4 * cq + 3] = m3;
+      __syncthreads();
+      if (warp == 0) {
+        uint32_t mx = 0;
+#pragma unroll 8
+        for (int w = 0; w < 32; w++) mx = umax(mx, part[w][lane]);
+        atomicMax(&pr.tB[c0 + lane], mx);
+      }
+    } else {
+      const int64_t col = c0 + lane;
+      uint32_t mx = 0;
+      if (col < pr.p) {
+#pragma unroll 8
+        for (int r = warp; r < kRowChunk; r += 8) {
+          const int64_t k = r0 + r;
+          if (k < pr.m) mx = umax(mx, abs_bits(pr.B[k * pr.p + col]));
+        }
+      }
+      part[warp][lane] = mx;
+      __syncthreads();
+      if (warp == 0) {
 #pragma unroll
-      for (int w = 1; w < 8; w++) mx = part[w][lane] > mx ? part[w][lane] : mx;
-      if (col < pr.p) atomicMax(&pr.tB[col], mx);
+        for (int w = 1; w < 8; w++) mx = umax(mx, part[w][lane]);
+        if (col < pr.p) atomicMax(&pr.tB[col], mx);
+      }
     }
   }
 }
 
-// Splits two values scaled by 2^-s into PARTS bf16 pairs: part 0 = RN(y),
-// part q = RN(y - part 0 - ... - part q-1).  Every remainder is exact in FP32
-// (the difference of a float and its rounding to fewer bits), so
-// y = sum of parts + d with |d| <= 2^(-8*PARTS) |y|.
+// Splits four values scaled by 2^-s into PARTS groups of four bf16 (two
+// bf16x2 words each): part 0 = RN(y), part q = RN(y - part 0 - ... - part
+// q-1).  Every remainder is exact in FP32 (the difference of a float and its
+// rounding to fewer bits), so y = sum of parts + d, |d| <= 2^(-8*PARTS) |y|.
 template <int PARTS>
-__device__ __forceinline__ void split_pair(float x0, float x1, int s, __nv_bfloat162 (&out)[PARTS]) {
-  float y0 = ldexpf(x0, -s), y1 = ldexpf(x1, -s);
+__device__ __forceinline__ void split4(float4 x, int s, uint2 (&out)[PARTS]) {
+  float y[4] = {ldexpf(x.x, -s), ldexpf(x.y, -s), ldexpf(x.z, -s), ldexpf(x.w, -s)};
 #pragma unroll
   for (int q = 0; q < PARTS; q++) {
-    out[q] = __floats2bfloat162_rn(y0, y1);
-    const float2 h = __bfloat1622float2(out[q]);
-    y0 -= h.x;
-    y1 -= h.y;
+    const __nv_bfloat162 a = __floats2bfloat162_rn(y[0], y[1]);
+    const __nv_bfloat162 b = __floats2bfloat162_rn(y[2], y[3]);
+    const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+    y[0] -= fa.x;
+    y[1] -= fa.y;
+    y[2] -= fb.x;
+    y[3] -= fb.y;
+    out[q] = make_uint2(*reinterpret_cast<const uint32_t *>(&a),
+                        *reinterpret_cast<const uint32_t *>(&b));
   }
 }
 
 template <int PARTS>
 __global__ void __launch_bounds__(256)
-split_pack_kernel(const SplitProb *__restrict__ probs, int nprobs,
-                  __nv_bfloat162 *__restrict__ pack) {
+split_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, uint2 *__restrict__ pack) {
   const int item = blockIdx.x;
   const int g = find_problem(probs, nprobs, item, [](const SplitProb &q) { return q.pack_start; });
   const SplitProb &pr = probs[g];
   const int local = item - pr.pack_start;
   const int tid = threadIdx.x;
-  constexpr int kPairs = kPackK / 2;  // bf16x2 per pack row
+  constexpr int kQuads = kPackK / 4;  // groups of four bf16 (8 bytes) per pack row
   if (local < pr.mt * pr.kt) {
-    // A tile (mt, kb): rows mt*128.., k kb*64..; a warp covers one row.
+    // A tile (mt, kb): rows mt*128.., k kb*64..; a warp covers two rows.
     const int mt = local / pr.kt, kb = local % pr.kt;
     const int64_t base = pr.a_row0 + (int64_t)local * PARTS * kTcBM;
-    for (int q = tid; q < kTcBM * kPairs; q += 256) {
-      const int r = q / kPairs, kp = q % kPairs;
+    const bool vec = aligned16(pr.A) && (pr.m & 3) == 0;
+    for (int q = tid; q < kTcBM * kQuads; q += 256) {
+      const int r = q / kQuads, kq = q % kQuads;
       const int64_t i = (int64_t)mt * kTcBM + r;
-      const int64_t k = (int64_t)kb * kPackK + 2 * kp;
-      float x0 = 0.f, x1 = 0.f;
+      const int64_t k = (int64_t)kb * kPackK + 4 * kq;
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
       int s = 0;
       if (i < pr.n) {
         const float *row = pr.A + i * pr.m;
-        if (k < pr.m) x0 = row[k];
-        if (k + 1 < pr.m) x1 = row[k + 1];
+        if (vec && k + 4 <= pr.m) {
+          x = *reinterpret_cast<const float4 *>(row + k);
+        } else {
+          if (k < pr.m) x.x = row[k];
+          if (k + 1 < pr.m) x.y = row[k + 1];
+          if (k + 2 < pr.m) x.z = row[k + 2];
+          if (k + 3 < pr.m) x.w = row[k + 3];
+        }
         s = scale_exponent(pr.sA[i]);
       }
-      __nv_bfloat162 part[PARTS];
-      split_pair<PARTS>(x0, x1, s, part);
+      uint2 part[PARTS];
+      split4<PARTS>(x, s, part);
 #pragma unroll
-      for (int h = 0; h < PARTS; h++) pack[(base + h * kTcBM + r) * kPairs + kp] = part[h];
+      for (int h = 0; h < PARTS; h++) pack[(base + h * kTcBM + r) * kQuads + kq] = part[h];
     }
   } else {
     // B tile (nt, kb): columns nt*bn.., k kb*64..; transposed through shared
@@ -134,22 +188,40 @@ split_pack_kernel(const SplitProb *__restrict__ probs, int nprobs,
     const int nt = b / pr.kt, kb = b % pr.kt;
     const int bn = pr.bn;
     const int64_t base = pr.b_row0 + (int64_t)b * PARTS * bn;
+    const bool vec = aligned16(pr.B) && (pr.p & 3) == 0;
     for (int c0 = 0; c0 < bn; c0 += 64) {
-      for (int q = tid; q < kPackK * 64; q += 256) {
-        const int kk = q / 64, c = q % 64;
+      for (int q = tid; q < kPackK * 16; q += 256) {
+        const int kk = q / 16, c4 = q % 16;
         const int64_t k = (int64_t)kb * kPackK + kk;
-        const int64_t j = (int64_t)nt * bn + c0 + c;
-        tile[kk][c] = (k < pr.m && j < pr.p) ? pr.B[k * pr.p + j] : 0.f;
+        const int64_t j = (int64_t)nt * bn + c0 + 4 * c4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k < pr.m) {
+          const float *src = pr.B + k * pr.p + j;
+          if (vec && j + 4 <= pr.p) {
+            v = *reinterpret_cast<const float4 *>(src);
+          } else {
+            if (j < pr.p) v.x = src[0];
+            if (j + 1 < pr.p) v.y = src[1];
+            if (j + 2 < pr.p) v.z = src[2];
+            if (j + 3 < pr.p) v.w = src[3];
+          }
+        }
+        tile[kk][4 * c4 + 0] = v.x;
+        tile[kk][4 * c4 + 1] = v.y;
+        tile[kk][4 * c4 + 2] = v.z;
+        tile[kk][4 * c4 + 3] = v.w;
       }
       __syncthreads();
-      for (int q = tid; q < 64 * kPairs; q += 256) {
-        const int c = q / kPairs, kp = q % kPairs;
+      for (int q = tid; q < 64 * kQuads; q += 256) {
+        const int c = q / kQuads, kq = q % kQuads;
         const int64_t j = (int64_t)nt * bn + c0 + c;
         const int s = j < pr.p ? scale_exponent(pr.tB[j]) : 0;
-        __nv_bfloat162 part[PARTS];
-        split_pair<PARTS>(tile[2 * kp][c], tile[2 * kp + 1][c], s, part);
+        const float4 x = make_float4(tile[4 * kq][c], tile[4 * kq + 1][c], tile[4 * kq + 2][c],
+                                     tile[4 * kq + 3][c]);
+        uint2 part[PARTS];
+        split4<PARTS>(x, s, part);
 #pragma unroll
-        for (int h = 0; h < PARTS; h++) pack[(base + h * bn + c0 + c) * kPairs + kp] = part[h];
+        for (int h = 0; h < PARTS; h++) pack[(base + h * bn + c0 + c) * kQuads + kq] = part[h];
       }
       __syncthreads();
     }
@@ -170,7 +242,7 @@ cudaError_t launch_split_pack(TcKind kind, const SplitProb *d_probs, int nprobs,
                               void *pack_base, cudaStream_t s) {
   if (total_tiles <= 0) return cudaSuccess;
   TraceScope ts("split_pack", s);
-  auto *pk = static_cast<__nv_bfloat162 *>(pack_base);
+  auto *pk = static_cast<uint2 *>(pack_base);
   if (kind == kTcSplitBf16x6)
     split_pack_kernel<3><<<total_tiles, 256, 0, s>>>(d_probs, nprobs, pk);
   else

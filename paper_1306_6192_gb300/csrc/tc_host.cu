@@ -97,8 +97,7 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
       all.push_back(sp);
     }
   SplitProb *d_tab = reinterpret_cast<SplitProb *>(base + tab_off);
-  e = cudaMemcpyAsync(d_tab, all.data(), all.size() * sizeof(SplitProb), cudaMemcpyHostToDevice,
-                      s);
+  e = ws.stage.copy_to_device(d_tab, all.data(), all.size() * sizeof(SplitProb), s);
   if (e != cudaSuccess) return note_cuda(e);
   e = cudaMemsetAsync(base + scal_off, 0, (size_t)scal * 4, s);
   if (e != cudaSuccess) return note_cuda(e);
@@ -120,6 +119,77 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
 }
 
 }  // namespace
+
+mm_status run_split_chunked(Scratch &ws, int64_t n, int64_t m, int64_t p, const float *A,
+                            const float *B, float *C, int chunks, const int64_t *row0,
+                            cudaStream_t s, cudaEvent_t *in_ready, cudaEvent_t *out_ready) {
+  if (n == 0 || p == 0) return MM_OK;
+  const TcKind kind = split_kind_for(m);
+  const int parts = pack_parts(kind);
+  const TcChoice ch = tune_choose(n, m, p);
+  const TcConfig cfg = kind == kTcSplitBf16x3 ? TcConfig{2 * ch.bk, ch.stages, ch.grid}
+                                              : TcConfig{64, 3, ch.grid};
+  const int32_t kt = (int32_t)ceil_div(m, pack_k(kind));
+  const int32_t nt = (int32_t)ceil_div(p, ch.bn);
+  // layout: B pack, then each slab's A pack; scale words: B columns, then A rows
+  int64_t rows = (int64_t)nt * kt * parts * ch.bn;
+  std::vector<SplitProb> tab((size_t)chunks);
+  std::vector<int64_t> tiles((size_t)chunks), packs((size_t)chunks), reds((size_t)chunks);
+  for (int c = 0; c < chunks; c++) {
+    const int64_t r0 = row0[c], r1 = row0[c + 1];
+    SplitProb &sp = tab[(size_t)c];
+    std::memset(&sp, 0, sizeof(sp));
+    sp.A = A + r0 * m;
+    sp.B = B;
+    sp.C = C + r0 * p;
+    sp.n = (int32_t)(r1 - r0);
+    sp.m = (int32_t)m;
+    sp.p = (int32_t)p;
+    sp.bn = ch.bn;
+    sp.group_m = ch.group_m;
+    sp.mt = (int32_t)ceil_div(r1 - r0, kTcBM);
+    sp.nt = nt;
+    sp.kt = kt;
+    sp.b_row0 = 0;
+    sp.a_row0 = rows;
+    rows += (int64_t)sp.mt * kt * parts * kTcBM;
+    sp.sA = reinterpret_cast<uint32_t *>((uintptr_t)(p + r0));  // offsets, fixed below
+    sp.tB = reinterpret_cast<uint32_t *>((uintptr_t)0);
+    sp.red_a = (int32_t)ceil_div(r1 - r0, 8);
+    tiles[(size_t)c] = (int64_t)sp.mt * nt;
+    // slab 0 also scales and packs B; the other slabs reuse its pack
+    packs[(size_t)c] = (int64_t)sp.mt * kt + (c == 0 ? (int64_t)nt * kt : 0);
+    reds[(size_t)c] = sp.red_a + (c == 0 ? ceil_div(p, 32) * ceil_div(m, 256) : 0);
+  }
+  if (rows > 0x7fffffffLL) return MM_EINVAL;
+  const size_t pack_bytes = (size_t)rows * kPackRowBytes;
+  const size_t scal_off = (pack_bytes + 255) & ~(size_t)255;
+  const size_t tab_off = (scal_off + (size_t)(n + p) * 4 + 255) & ~(size_t)255;
+  cudaError_t e = ws.reserve(tab_off + tab.size() * sizeof(SplitProb), s);
+  if (e != cudaSuccess) return note_cuda(e);
+  uint8_t *base = static_cast<uint8_t *>(ws.ptr);
+  uint32_t *scal = reinterpret_cast<uint32_t *>(base + scal_off);
+  for (auto &sp : tab) {
+    sp.sA = scal + (uintptr_t)sp.sA;
+    sp.tB = scal + (uintptr_t)sp.tB;
+  }
+  SplitProb *d_tab = reinterpret_cast<SplitProb *>(base + tab_off);
+  e = ws.stage.copy_to_device(d_tab, tab.data(), tab.size() * sizeof(SplitProb), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(scal, 0, (size_t)(n + p) * 4, s);
+  if (e != cudaSuccess) return note_cuda(e);
+  for (int c = 0; c < chunks; c++) {
+    if (c == 0 && (e = cudaStreamWaitEvent(s, in_ready[0], 0)) != cudaSuccess) break;
+    if ((e = cudaStreamWaitEvent(s, in_ready[c + 1], 0)) != cudaSuccess) break;
+    const SplitProb *dt = d_tab + c;
+    if ((e = launch_split_scale(dt, 1, (int)reds[(size_t)c], s)) != cudaSuccess) break;
+    if ((e = launch_split_pack(kind, dt, 1, (int)packs[(size_t)c], base, s)) != cudaSuccess) break;
+    if ((e = launch_tc(kind, dt, 1, (int)tiles[(size_t)c], base, rows, cfg, g_ctx.d_err, s)) !=
+        cudaSuccess)
+      break;
+    if ((e = cudaEventRecord(out_ready[c], s)) != cudaSuccess) break;
+  }
+  return note_cuda(e);
+}
 
 mm_status run_split(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s,
                     const TcChoice *force) {

@@ -65,6 +65,26 @@ def test_host_operands(mmlib, mode):
     assert_full(Cd.cpu().numpy(), A, B, "f64" if f64 else "f32")
 
 
+@pytest.mark.parametrize("shape", [(2304, 700, 300), (4100, 2500, 129)])
+def test_host_operands_pipelined(mmlib, shape):
+    """Large host-operand split products go through the slab pipeline (B
+    packed once, rows of A in slabs, copies overlapping the tensor cores);
+    the result is identical to the device-operand call."""
+    mm = mmlib
+    n, m, p = shape
+    A = synth.uniform_pm1(731, (n, m))
+    B = synth.uniform_pm1(732, (m, p))
+    Ap = torch.from_numpy(A).pin_memory()
+    Bp = torch.from_numpy(B).pin_memory()
+    Cp = torch.full((n, p), float("nan")).pin_memory()
+    assert mm.mm_gemm(n, m, p, Ap, Bp, Cp, mm.MM_F32, mm.MM_MODE_SPLIT_BF16X3) == 0
+    Cd = torch.full((n, p), float("nan"), device="cuda")
+    assert mm.mm_gemm(n, m, p, dev(A), dev(B), Cd, mm.MM_F32, mm.MM_MODE_SPLIT_BF16X3) == 0
+    assert torch.equal(Cp, Cd.cpu())
+    from gpu_util import sampled_check
+    sampled_check(Cp.numpy(), A, B, "f32", count=1024, trials=1)
+
+
 def test_async_on_torch_stream_and_trace(mmlib):
     mm = mmlib
     n, m, p = 512, 384, 640

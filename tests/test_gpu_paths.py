@@ -26,12 +26,15 @@ def test_uniform_matches_oracle(mmlib, shape, mode):
     assert_full(C, A, B, "f64" if mode == "dgemm" else "f32")
 
 
+@pytest.mark.parametrize("p", [140, 50])
 @pytest.mark.parametrize("m", [1, 2, 15, 64, 2200, 2300, 3000])
-def test_split_across_the_part_threshold(mmlib, m):
+def test_split_across_the_part_threshold(mmlib, m, p):
     """The split path uses three bf16 parts below m ~ 2240 and two above; both
     sides of the switch meet the tolerance, including a single-term dot
-    product per entry (B with one non-zero per column)."""
-    n, p = 96, 140
+    product per entry (B with one non-zero per column).  p = 50 takes the
+    64-wide N tile (a 64-row remainder in the B loads of the three-part
+    split)."""
+    n = 96
     A = synth.uniform_pm1(900 + m, (n, m))
     B = synth.uniform_pm1(901 + m, (m, p))
     C = run_gemm(mmlib, A, B, mmlib.MM_MODE_SPLIT_BF16X3)
