@@ -71,7 +71,9 @@ typedef enum {
   MM_ECUDA = 8,        /* CUDA runtime/driver error */
   MM_ENOTINIT = 9,     /* mm_init not called */
   MM_EUNSUPPORTED = 10,/* dtype/mode combination or device not supported */
-  MM_ECANCELLED = 11   /* request cancelled by mm_shutdown */
+  MM_ECANCELLED = 11,  /* request cancelled by mm_shutdown */
+  MM_ESCRATCH = 12     /* product too large for mm_gemm_split_static's fixed
+                          scratch array */
 } mm_status;
 
 typedef enum { MM_F32 = 0, MM_F64 = 1 } mm_dtype;
@@ -213,6 +215,36 @@ mm_status mm_trace_read(const char *kernel, int64_t *launches, double *total_ms)
 
 /* Number of library kernel launches since mm_init (all kernels). */
 int64_t mm_launch_count(void);
+
+/* ------------------------------------------------ allocation-free variant */
+
+/* The FP32 split product of mm_gemm's MM_MODE_SPLIT_BF16X3 path, for callers
+ * that must not allocate device memory: a plug-in running inside a host
+ * framework that owns and accounts for all device memory, code on a latency-
+ * critical path where cudaMalloc's implicit synchronisation is not
+ * acceptable, or a process whose device memory budget is fixed at start-up.
+ * The paper has no counterpart to this entry point.
+ *
+ * Scratch: the scale words, problem table, packed bf16 operands and timeout
+ * flag of the split path live in one fixed 64 MiB device array compiled into
+ * the library (every GPU that loads the library holds it until the process
+ * exits).  The call makes no cudaMalloc, cudaFree or other allocating call and
+ * does not need mm_init.  Products whose scratch does not fit are rejected
+ * with MM_ESCRATCH (2048^3 fits, 3072^3 does not).
+ * A (n x m), B (m x p), C (n x p): device pointers, FP32, row-major and dense
+ * as in mm_gemm.  stream: a cudaStream_t (NULL: the legacy default stream);
+ * the call returns when C is written.  Same kernels and tile choices as
+ * mm_gemm's split path, hence the same results.
+ * Every call uses the same array, which keeps the previous call's contents
+ * (the call clears what must start at zero): calls whose work overlaps on the
+ * GPU - on different streams or from different host threads - race and
+ * corrupt each other; serialise them.  The first call on a device looks up
+ * the array's device address on that device (with it current); make that
+ * first call before any stream capture.  Returns MM_OK, MM_EINVAL,
+ * MM_ESCRATCH, MM_EUNSUPPORTED (not an sm_103 device), MM_ETIMEOUT (a
+ * device-side wait ran out) or MM_ECUDA. */
+mm_status mm_gemm_split_static(int64_t n, int64_t m, int64_t p, const float *A,
+                               const float *B, float *C, void *stream);
 
 #ifdef __cplusplus
 }

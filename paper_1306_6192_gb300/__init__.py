@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "libmm_gb300.so")
 # status codes
 MM_OK, MM_EINVAL, MM_ENOMEM, MM_EBUDGET, MM_EBUSY, MM_ENOTFOUND = 0, 1, 2, 3, 4, 5
 MM_EPENDING, MM_ETIMEOUT, MM_ECUDA, MM_ENOTINIT, MM_EUNSUPPORTED, MM_ECANCELLED = 6, 7, 8, 9, 10, 11
+MM_ESCRATCH = 12
 # element types and modes
 MM_F32, MM_F64 = 0, 1
 MM_MODE_SIMT, MM_MODE_SPLIT_BF16X3, MM_MODE_DGEMM, MM_MODE_FP8, MM_MODE_AUTO = 0, 1, 2, 3, 4
@@ -82,6 +83,8 @@ def lib():
         L.mm_trace_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(_i64), _dp]
         L.mm_launch_count.argtypes = []
         L.mm_launch_count.restype = _i64
+        L.mm_gemm_split_static.argtypes = [_i64, _i64, _i64, _vp, _vp, _vp, _vp]
+        L.mm_gemm_split_static.restype = ctypes.c_int
         for name in ("mm_init", "mm_shutdown", "mm_gemm", "mm_gemm_async", "mm_gemm_grouped",
                      "mm_gemm_grouped_async", "mm_sync", "mm_check", "mm_submit", "mm_poll",
                      "mm_wait", "mm_serve_stats", "mm_tune", "mm_tune_save", "mm_tune_load",
@@ -248,3 +251,9 @@ def mm_trace_read(kernel: str):
 
 def mm_launch_count() -> int:
     return int(lib().mm_launch_count())
+
+
+def mm_gemm_split_static(n, m, p, A, B, C, stream=None) -> int:
+    """Allocation-free split product (see include/mm.h): device operands,
+    scratch in the library's fixed device array, synchronous on `stream`."""
+    return lib().mm_gemm_split_static(n, m, p, _ptr(A), _ptr(B), _ptr(C), _stream(stream))

@@ -292,6 +292,7 @@ const char *mm_strerror(mm_status s) {
     case MM_ENOTINIT: return "library not initialised";
     case MM_EUNSUPPORTED: return "unsupported dtype/mode or device";
     case MM_ECANCELLED: return "request cancelled";
+    case MM_ESCRATCH: return "product too large for the fixed scratch array";
   }
   return "unknown status";
 }
