@@ -77,6 +77,13 @@ mm_status note_cuda(cudaError_t e);
 // tolerance 1e-6 sqrt(m), three parts (six products) below that.
 TcKind split_kind_for(int64_t m);
 
+// N tile used for a kind: the tensor-core kernel loads B in 128-row boxes, so
+// parts * bn must be a multiple of 128; with one or three parts that rules
+// out bn = 64, which then becomes 128.
+inline int tc_bn(TcKind kind, int bn) {
+  return (bn == 64 && pack_parts(kind) != 2) ? 128 : bn;
+}
+
 // Split path over a table of problems (single GEMM = table of one); each
 // problem takes the kind split_kind_for(m).  `force` overrides the tuned tile
 // choice (autotuner and tests).

@@ -96,8 +96,9 @@ mm_status mm_gemm_split_static(int64_t n, int64_t m, int64_t p, const float *A, 
     return cudaStreamSynchronize(s) == cudaSuccess ? MM_OK : MM_ECUDA;
   }
   // Same tile choice and split kind as mm_gemm's split path for this size.
-  const TcChoice ch = tune_choose(n, m, p);
+  TcChoice ch = tune_choose(n, m, p);
   const TcKind kind = split_kind_for(m);
+  ch.bn = tc_bn(kind, ch.bn);
   const int parts = pack_parts(kind);
   SplitProb sp;
   std::memset(&sp, 0, sizeof(sp));

@@ -107,8 +107,9 @@ size_t request_bytes(const mm_problem &q, mm_dtype dt, mm_mode mode) {
   const size_t es = elem_bytes(dt);
   size_t b = es * (size_t)(q.n * q.m + q.m * q.p + q.n * q.p);
   if (mode == MM_MODE_SPLIT_BF16X3 || mode == MM_MODE_FP8) {
-    const TcChoice c = tune_choose(q.n, q.m, q.p);
     const TcKind kind = mode == MM_MODE_FP8 ? kTcE4m3 : split_kind_for(q.m);
+    TcChoice c = tune_choose(q.n, q.m, q.p);
+    c.bn = tc_bn(kind, c.bn);
     const size_t kb = (size_t)ceil_div(q.m, pack_k(kind));  // pack rows per matrix row
     b += (size_t)kPackRowBytes * pack_parts(kind) * kb *
          ((size_t)ceil_div(q.n, kTcBM) * kTcBM + (size_t)ceil_div(q.p, c.bn) * c.bn);

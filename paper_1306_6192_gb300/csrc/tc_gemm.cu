@@ -45,7 +45,6 @@ constexpr int kMaxBN = 256;
 constexpr int kAccCols = 256;               // TMEM columns per accumulator
 constexpr uint32_t kTmemCols = 2 * kAccCols;
 constexpr int kBoxRows = 128;               // TMA box height (rows of the pack)
-constexpr int kTailRows = 64;               // second map's box for a 64-row remainder
 constexpr uint64_t kWaitLimitNs = 4000000000ull;
 constexpr uint64_t kDrainLimitNs = 200000000ull;
 
@@ -244,8 +243,8 @@ struct TcLayout {
 
 template <int BKB, int STAGES, int KIND>
 __global__ void __launch_bounds__(kThreads, 1)
-tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap64,
-               const SplitProb *__restrict__ probs, int nprobs, int total_tiles, int *err) {
+tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__restrict__ probs,
+               int nprobs, int total_tiles, int *err) {
   using L = TcLayout<BKB, STAGES, KIND>;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -288,8 +287,6 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__
       // ------------------------------------------------------ TMA producer
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap))
                    : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap64))
-                   : "memory");
       int stage = 0;
       uint32_t phase = 0;
       int armed[STAGES];
@@ -319,15 +316,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__
           for (int part = 0; part < L::kParts; part++)
             tma_load_2d(st + part * L::kAPart, &tmap, x, (int)(arow + part * kTcBM),
                         full_bar(stage));
-          // B: parts * bn rows (a multiple of 64) in 128-row boxes and, for
-          // a 64-row remainder, one 64-row box: exactly the bytes expected
+          // B: parts * bn rows, a multiple of the 128-row box (tc_bn keeps
+          // bn >= 128 unless parts = 2), so the boxes carry exactly the bytes
+          // expected
           const uint32_t sb = st + L::kParts * L::kAPart;
-          const int brows = L::kParts * bn;
-          int r = 0;
-          for (; r + kBoxRows <= brows; r += kBoxRows)
+          for (int r = 0; r < L::kParts * bn; r += kBoxRows)
             tma_load_2d(sb + r * BKB, &tmap, x, (int)(brow + r), full_bar(stage));
-          if (r < brows)
-            tma_load_2d(sb + r * BKB, &tmap64, x, (int)(brow + r), full_bar(stage));
           if (++stage == STAGES) {
             stage = 0;
             phase ^= 1u;
@@ -493,13 +487,12 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
 
 // 2-D map over the pack region viewed as rows of 128 bytes; a box is BKB
 // bytes of 128 consecutive rows.
-cudaError_t encode_pack_map(CUtensorMap *map, void *base, int64_t rows, int bkb,
-                            int box_rows) {
+cudaError_t encode_pack_map(CUtensorMap *map, void *base, int64_t rows, int bkb) {
   auto enc = get_encode_fn();
   if (!enc) return cudaErrorNotSupported;
   cuuint64_t dims[2] = {(cuuint64_t)kPackRowBytes, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)kPackRowBytes};
-  cuuint32_t box[2] = {(cuuint32_t)bkb, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)bkb, (cuuint32_t)kBoxRows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -522,12 +515,11 @@ cudaError_t launch_tc_t(const SplitProb *d_probs, int nprobs, int total_tiles, v
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, L::kSmemBytes);
   });
   if (attr_err != cudaSuccess) return attr_err;
-  CUtensorMap map, map64;
-  cudaError_t e = encode_pack_map(&map, pack_base, pack_rows, BKB, kBoxRows);
-  if (e == cudaSuccess) e = encode_pack_map(&map64, pack_base, pack_rows, BKB, kTailRows);
+  CUtensorMap map;
+  cudaError_t e = encode_pack_map(&map, pack_base, pack_rows, BKB);
   if (e != cudaSuccess) return e;
   TraceScope ts(KIND == kTcE4m3 ? "fp8_tc" : "split_tc", s);
-  tc_gemm_kernel<BKB, STAGES, KIND><<<grid, kThreads, L::kSmemBytes, s>>>(map, map64, d_probs, nprobs,
+  tc_gemm_kernel<BKB, STAGES, KIND><<<grid, kThreads, L::kSmemBytes, s>>>(map, d_probs, nprobs,
                                                                          total_tiles, d_err);
   return cudaGetLastError();
 }

@@ -36,7 +36,8 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
     }
     const TcKind kind = fp8 ? kTcE4m3 : split_kind_for(q.m);
     Group &G = groups[kind == kTcSplitBf16x3 ? 0 : (kind == kTcSplitBf16x6 ? 1 : 2)];
-    const TcChoice ch = force ? *force : tune_choose(q.n, q.m, q.p);
+    TcChoice ch = force ? *force : tune_choose(q.n, q.m, q.p);
+    ch.bn = tc_bn(kind, ch.bn);
     if (G.tab.empty()) {
       if (kind == kTcSplitBf16x3) G.cfg = TcConfig{2 * ch.bk, ch.stages, ch.grid};
       else if (kind == kTcSplitBf16x6) G.cfg = TcConfig{64, 3, ch.grid};
@@ -126,7 +127,8 @@ mm_status run_split_chunked(Scratch &ws, int64_t n, int64_t m, int64_t p, const 
   if (n == 0 || p == 0) return MM_OK;
   const TcKind kind = split_kind_for(m);
   const int parts = pack_parts(kind);
-  const TcChoice ch = tune_choose(n, m, p);
+  TcChoice ch = tune_choose(n, m, p);
+  ch.bn = tc_bn(kind, ch.bn);
   const TcConfig cfg = kind == kTcSplitBf16x3 ? TcConfig{2 * ch.bk, ch.stages, ch.grid}
                                               : TcConfig{64, 3, ch.grid};
   const int32_t kt = (int32_t)ceil_div(m, pack_k(kind));
