@@ -470,7 +470,7 @@ def run_mine(args):
         ach = flops / (avg * 1e-3) / 1e12
         line["roofline"] = {
             "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-            "frac": ach / peak, "traffic": _traffic_from_profiles("split_tc_8192.txt"),
+            "frac": ach / peak, "traffic": _traffic_from_profiles("tc_gemm_split_8192.txt"),
             "kernel": "split_tc",
             "peak_note": "%s %s BF16 dense / 3 (three BF16 products per useful FMA)" % (
                 peak_src, kind),
