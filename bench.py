@@ -316,6 +316,9 @@ def bench_serving(mm, count: int, rate_frac: float, seed: int = 5, streams: int 
     src32 = torch.rand(big, device="cuda", generator=gen) * 2 - 1
     src64 = src32.double()
 
+    out_cap = 40 << 30  # the client's outstanding output bytes (backpressure)
+    held = [0]
+
     def submit(k):
         n, m, p = (int(v) for v in dims[k])
         if f64[k]:
@@ -326,6 +329,7 @@ def bench_serving(mm, count: int, rate_frac: float, seed: int = 5, streams: int 
             C = torch.empty(n * p, device="cuda")
         st, rid = mm.mm_submit(n, m, p, A, B, C, dt, md)
         mm.check_status(st, "mm_submit")
+        held[0] += C.numel() * C.element_size()
         return rid, C
 
     def drain(live, lat, budget=32):
@@ -338,7 +342,14 @@ def bench_serving(mm, count: int, rate_frac: float, seed: int = 5, streams: int 
                 lat.append(ms)
                 done.append(rid)
         for rid in done:
-            del live[rid]
+            C = live.pop(rid)
+            held[0] -= C.numel() * C.element_size()
+
+    def make_room(live, lat, k):
+        n, _, p = (int(v) for v in dims[k])
+        need = n * p * (8 if f64[k] else 4)
+        while live and held[0] + need > out_cap:
+            drain(live, lat)
 
     flops = float(np.sum(2.0 * dims[:, 0] * dims[:, 1] * dims[:, 2]))
     dev_index = torch.cuda.current_device()
@@ -350,6 +361,7 @@ def bench_serving(mm, count: int, rate_frac: float, seed: int = 5, streams: int 
         live, lat = collections.OrderedDict(), []
         t0 = time.perf_counter()
         for k in range(count):
+            make_room(live, lat, k)
             rid, C = submit(k)
             live[rid] = C
         while live:
@@ -363,6 +375,7 @@ def bench_serving(mm, count: int, rate_frac: float, seed: int = 5, streams: int 
     for k in range(count):
         while time.perf_counter() - t0 < arrivals[k]:
             drain(live, lat)
+        make_room(live, lat, k)
         rid, C = submit(k)
         live[rid] = C
     while live:
@@ -376,6 +389,34 @@ def bench_serving(mm, count: int, rate_frac: float, seed: int = 5, streams: int 
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "throughput_req_s": count / wall, "tflops": flops / wall / 1e12,
             "batches": batches, "streams": streams, "max_batch": max_batch or 256}
+
+
+def run_serve_sweep(args):
+    """Config-5 sweep: the Poisson replay at several fractions of the measured
+    capacity, batched (2 streams, up to 256 per launch) against one request
+    per launch on one stream, same arrivals.  Prints one JSON line."""
+    import torch
+
+    import paper_1306_6192_gb300 as mm
+    torch.cuda.set_device(0)
+    mm.check_status(mm.mm_init(device=0), "mm_init")
+    rows = []
+    cap = None
+    for frac in args.serve_rates:
+        row = {"rate_frac": frac}
+        for name, st_, mb in (("batched", 2, 0), ("one_per_launch", 1, 1)):
+            r = bench_serving(mm, args.serve_requests, frac, streams=st_, max_batch=mb,
+                              capacity=cap)
+            cap = r["capacity_req_s"] if cap is None else cap
+            row[name] = {k: r[k] for k in ("rate_req_s", "p50_ms", "p99_ms", "throughput_req_s",
+                                           "tflops", "batches")}
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    mm.mm_shutdown()
+    print(json.dumps({"metric": "serving p50/p99 ms", "requests": args.serve_requests,
+                      "capacity_req_s": cap, "mix": "dims log-uniform [64,4096], 20% FP64",
+                      "sweep": rows}))
+    return 0
 
 
 def run_mine(args):
@@ -554,11 +595,17 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="headline step only")
     ap.add_argument("--serve-requests", type=int, default=1500)
+    ap.add_argument("--serve-sweep", action="store_true",
+                    help="only the serving rate sweep (config 5)")
+    ap.add_argument("--serve-rates", type=float, nargs="*",
+                    default=[0.1, 0.25, 0.5, 0.75, 0.9, 1.0, 1.1])
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "mine":
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve_sweep:
+        return run_serve_sweep(args)
     return run_mine(args)
 
 
