@@ -34,9 +34,11 @@ __device__ __forceinline__ uint32_t to_e4m3x4(float x0, float x1, float x2, floa
 }
 
 __global__ void __launch_bounds__(256)
-fp8_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, uint32_t *__restrict__ pack) {
+fp8_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *__restrict__ map,
+                uint32_t *__restrict__ pack) {
   const int item = blockIdx.x;
-  const int g = find_problem(probs, nprobs, item, [](const SplitProb &q) { return q.pack_start; });
+  const int g =
+      find_problem(probs, nprobs, map, item, [](const SplitProb &q) { return q.pack_start; });
   const SplitProb &pr = probs[g];
   const int local = item - pr.pack_start;
   const int tid = threadIdx.x;
@@ -91,11 +93,12 @@ fp8_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, uint32_t *__res
 
 }  // namespace
 
-cudaError_t launch_fp8_pack(const SplitProb *d_probs, int nprobs, int total_tiles, void *pack_base,
-                            cudaStream_t s) {
+cudaError_t launch_fp8_pack(const SplitProb *d_probs, int nprobs, int total_tiles, const int *map,
+                            void *pack_base, cudaStream_t s) {
   if (total_tiles <= 0) return cudaSuccess;
   TraceScope ts("fp8_pack", s);
-  fp8_pack_kernel<<<total_tiles, 256, 0, s>>>(d_probs, nprobs, static_cast<uint32_t *>(pack_base));
+  fp8_pack_kernel<<<total_tiles, 256, 0, s>>>(d_probs, nprobs, map,
+                                              static_cast<uint32_t *>(pack_base));
   return cudaGetLastError();
 }
 

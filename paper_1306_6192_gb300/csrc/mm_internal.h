@@ -84,13 +84,18 @@ cudaError_t launch_simt_grouped(bool f64, const SimtProb *d_probs, int nprobs,
 
 // Prep: per-row/column max-abs reduction, then the split (hi/lo bf16) or
 // e4m3 conversion into the packs.
+// `map` arguments: item -> problem index arrays written by
+// launch_split_maps for tables of several problems, or nullptr.
+cudaError_t launch_split_maps(const SplitProb *d_probs, int nprobs, int *tile_map,
+                              int *pack_map, int *red_map, cudaStream_t s);
 cudaError_t launch_split_scale(const SplitProb *d_probs, int nprobs,
-                               int total_items, cudaStream_t s);
+                               int total_items, const int *map, cudaStream_t s);
 cudaError_t launch_split_pack(TcKind kind, const SplitProb *d_probs, int nprobs,
-                              int total_tiles, void *pack_base,
+                              int total_tiles, const int *map, void *pack_base,
                               cudaStream_t s);
 cudaError_t launch_fp8_pack(const SplitProb *d_probs, int nprobs,
-                            int total_tiles, void *pack_base, cudaStream_t s);
+                            int total_tiles, const int *map, void *pack_base,
+                            cudaStream_t s);
 
 // Tensor-core mainloop + epilogue over all tiles of all problems.
 struct TcConfig {
@@ -99,8 +104,9 @@ struct TcConfig {
   int grid;     // persistent CTAs (<= number of SMs; 0 = one per SM)
 };
 cudaError_t launch_tc(TcKind kind, const SplitProb *d_probs, int nprobs,
-                      int total_tiles, void *pack_base, int64_t pack_rows,
-                      const TcConfig &cfg, int *d_err, cudaStream_t s);
+                      int total_tiles, const int *tile_map, void *pack_base,
+                      int64_t pack_rows, const TcConfig &cfg, int *d_err,
+                      cudaStream_t s);
 
 // FP64 check (Freivalds + sampled entries): writes 2 doubles to d_out.
 cudaError_t launch_check(bool f64, int64_t n, int64_t m, int64_t p,

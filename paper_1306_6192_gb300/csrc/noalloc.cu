@@ -138,12 +138,12 @@ mm_status mm_gemm_split_static(int64_t n, int64_t m, int64_t p, const float *A, 
   if (e == cudaSuccess) e = cudaMemsetAsync(sp.sA, 0, (size_t)(n + p) * 4, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_tab, &sp, sizeof(sp), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = launch_split_scale(d_tab, 1, (int)reds, s);
-  if (e == cudaSuccess) e = launch_split_pack(kind, d_tab, 1, (int)packs, pack, s);
+  if (e == cudaSuccess) e = launch_split_scale(d_tab, 1, (int)reds, nullptr, s);
+  if (e == cudaSuccess) e = launch_split_pack(kind, d_tab, 1, (int)packs, nullptr, pack, s);
   if (e == cudaSuccess) {
     TcConfig cfg = kind == kTcSplitBf16x3 ? TcConfig{2 * ch.bk, ch.stages, sms}
                                           : TcConfig{64, 3, sms};
-    e = launch_tc(kind, d_tab, 1, (int)tiles, pack, rows, cfg, d_flag, s);
+    e = launch_tc(kind, d_tab, 1, (int)tiles, nullptr, pack, rows, cfg, d_flag, s);
   }
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -18,10 +18,13 @@ __device__ __forceinline__ int scale_exponent(uint32_t max_bits) {
   return ilogbf(f);
 }
 
-// Finds the problem whose [start, next start) range holds `item`.
+// Finds the problem whose [start, next start) range holds `item`: one load
+// from the item -> problem map when there is one (tables of many problems),
+// else a binary search over the start prefixes.
 template <typename F>
 __device__ __forceinline__ int find_problem(const SplitProb *__restrict__ probs, int nprobs,
-                                            int item, F start_of) {
+                                            const int *__restrict__ map, int item, F start_of) {
+  if (map) return map[item];
   int lo = 0, hi = nprobs - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;

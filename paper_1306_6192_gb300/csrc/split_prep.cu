@@ -38,9 +38,10 @@ __device__ __forceinline__ bool aligned16(const void *p) {
 }
 
 __global__ void __launch_bounds__(256)
-split_scale_kernel(const SplitProb *__restrict__ probs, int nprobs) {
+split_scale_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *__restrict__ map) {
   const int item = blockIdx.x;
-  const int g = find_problem(probs, nprobs, item, [](const SplitProb &q) { return q.red_start; });
+  const int g =
+      find_problem(probs, nprobs, map, item, [](const SplitProb &q) { return q.red_start; });
   const SplitProb &pr = probs[g];
   const int local = item - pr.red_start;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -145,9 +146,11 @@ __device__ __forceinline__ void split4(float4 x, int s, uint2 (&out)[PARTS]) {
 
 template <int PARTS>
 __global__ void __launch_bounds__(256)
-split_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, uint2 *__restrict__ pack) {
+split_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *__restrict__ map,
+                  uint2 *__restrict__ pack) {
   const int item = blockIdx.x;
-  const int g = find_problem(probs, nprobs, item, [](const SplitProb &q) { return q.pack_start; });
+  const int g =
+      find_problem(probs, nprobs, map, item, [](const SplitProb &q) { return q.pack_start; });
   const SplitProb &pr = probs[g];
   const int local = item - pr.pack_start;
   const int tid = threadIdx.x;
@@ -228,25 +231,49 @@ split_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, uint2 *__rest
   }
 }
 
+// One block per problem: writes the problem's index over its ranges of MMA
+// tiles, pack tiles and scale-reduction items.
+__global__ void __launch_bounds__(256)
+split_maps_kernel(const SplitProb *__restrict__ probs, int *__restrict__ tile_map,
+                  int *__restrict__ pack_map, int *__restrict__ red_map) {
+  const int g = blockIdx.x;
+  const SplitProb &pr = probs[g];
+  const int tiles = pr.mt * pr.nt;
+  const int packs = pr.mt * pr.kt + pr.nt * pr.kt;
+  const int reds = pr.red_a + ((pr.p + kColStrip - 1) / kColStrip) *
+                                  ((pr.m + kRowChunk - 1) / kRowChunk);
+  for (int i = threadIdx.x; i < tiles; i += blockDim.x) tile_map[pr.tile_start + i] = g;
+  for (int i = threadIdx.x; i < packs; i += blockDim.x) pack_map[pr.pack_start + i] = g;
+  for (int i = threadIdx.x; i < reds; i += blockDim.x) red_map[pr.red_start + i] = g;
+}
+
 }  // namespace
 
+cudaError_t launch_split_maps(const SplitProb *d_probs, int nprobs, int *tile_map, int *pack_map,
+                              int *red_map, cudaStream_t s) {
+  if (nprobs <= 0) return cudaSuccess;
+  TraceScope ts("split_maps", s);
+  split_maps_kernel<<<nprobs, 256, 0, s>>>(d_probs, tile_map, pack_map, red_map);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_split_scale(const SplitProb *d_probs, int nprobs, int total_items,
-                               cudaStream_t s) {
+                               const int *map, cudaStream_t s) {
   if (total_items <= 0) return cudaSuccess;
   TraceScope ts("split_scale", s);
-  split_scale_kernel<<<total_items, 256, 0, s>>>(d_probs, nprobs);
+  split_scale_kernel<<<total_items, 256, 0, s>>>(d_probs, nprobs, map);
   return cudaGetLastError();
 }
 
 cudaError_t launch_split_pack(TcKind kind, const SplitProb *d_probs, int nprobs, int total_tiles,
-                              void *pack_base, cudaStream_t s) {
+                              const int *map, void *pack_base, cudaStream_t s) {
   if (total_tiles <= 0) return cudaSuccess;
   TraceScope ts("split_pack", s);
   auto *pk = static_cast<uint2 *>(pack_base);
   if (kind == kTcSplitBf16x6)
-    split_pack_kernel<3><<<total_tiles, 256, 0, s>>>(d_probs, nprobs, pk);
+    split_pack_kernel<3><<<total_tiles, 256, 0, s>>>(d_probs, nprobs, map, pk);
   else
-    split_pack_kernel<2><<<total_tiles, 256, 0, s>>>(d_probs, nprobs, pk);
+    split_pack_kernel<2><<<total_tiles, 256, 0, s>>>(d_probs, nprobs, map, pk);
   return cudaGetLastError();
 }
 

@@ -201,6 +201,28 @@ __device__ __forceinline__ uint32_t make_idesc(int bn) {
          ((uint32_t)(kTcBM >> 4) << 24);
 }
 
+// x * 2^e rounded once: a multiplication by the exact power of two when 2^e is
+// a normal float (then identical to ldexpf), ldexpf otherwise.
+__device__ __forceinline__ float scale_pow2(float x, int e) {
+  if (e >= -126 && e <= 127) return x * __int_as_float((e + 127) << 23);
+  return ldexpf(x, e);
+}
+
+// AND of `v` over the 128 epilogue threads (named barrier 1): every thread
+// arrives, so the four warps leave the tile loop together.
+__device__ __forceinline__ bool epilogue_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.and.pred p, 1, 128, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+
 // Power-of-two exponent applied to a row/column in the epilogue: the split
 // path scales to max |x 2^-s| in [1, 2); the e4m3 path to [128, 256), which
 // stays below the e4m3 maximum 448 and keeps 13 binades above its subnormals.
@@ -217,8 +239,9 @@ struct TileCoord {
 };
 
 __device__ __forceinline__ TileCoord decode_tile(const SplitProb *__restrict__ probs, int nprobs,
-                                                 int t) {
-  const int g = find_problem(probs, nprobs, t, [](const SplitProb &q) { return q.tile_start; });
+                                                 const int *__restrict__ map, int t) {
+  const int g =
+      find_problem(probs, nprobs, map, t, [](const SplitProb &q) { return q.tile_start; });
   const SplitProb &pr = probs[g];
   const int local = t - pr.tile_start;
   const int gm = pr.group_m;
@@ -238,13 +261,14 @@ struct TcLayout {
   static constexpr int kStageBytes = kParts * (kAPart + kBPartMax);
   static constexpr int kBarOffset = STAGES * kStageBytes;
   static constexpr int kNumBars = 2 * STAGES + 4 + 1;  // full, empty, acc_full/empty, drain
-  static constexpr int kSmemBytes = kBarOffset + kNumBars * 8 + 16 + 1024;  // + align slack
+  static constexpr int kColExpOffset = kBarOffset + kNumBars * 8 + 16;  // int[2][kMaxBN]
+  static constexpr int kSmemBytes = kColExpOffset + 2 * kMaxBN * 4 + 1024;  // + align slack
 };
 
 template <int BKB, int STAGES, int KIND>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__restrict__ probs,
-               int nprobs, int total_tiles, int *err) {
+               int nprobs, const int *__restrict__ tile_map, int total_tiles, int *err) {
   using L = TcLayout<BKB, STAGES, KIND>;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -257,6 +281,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
   auto acce_bar = [&](int a) { return bars + 8u * (2 * STAGES + 2 + a); };
   const uint32_t drain_bar = bars + 8u * (2 * STAGES + 4);
   uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(smem + L::kBarOffset + L::kNumBars * 8);
+  int *colexp = reinterpret_cast<int *>(smem + L::kColExpOffset);  // [2][kMaxBN]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -294,7 +319,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
       for (int s = 0; s < STAGES; s++) armed[s] = 0, armed_parity[s] = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
-        const TileCoord tc = decode_tile(probs, nprobs, t);
+        const TileCoord tc = decode_tile(probs, nprobs, tile_map, t);
         const SplitProb &pr = probs[tc.g];
         const int bn = pr.bn;
         const int kiters = (int)(((int64_t)pr.m * L::kElemBytes + BKB - 1) / BKB);
@@ -343,7 +368,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
       uint32_t acc_phase = 0;
       bool ok = true, issued = false;
       for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
-        const TileCoord tc = decode_tile(probs, nprobs, t);
+        const TileCoord tc = decode_tile(probs, nprobs, tile_map, t);
         const SplitProb &pr = probs[tc.g];
         const int kiters = (int)(((int64_t)pr.m * L::kElemBytes + BKB - 1) / BKB);
         const uint32_t idesc = make_idesc<KIND>(pr.bn);
@@ -418,10 +443,18 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
     const int row = q * 32 + lane;
     int acc = 0;
     uint32_t acc_phase = 0;
+    const int et = threadIdx.x - 64;  // 0..127 over the epilogue warps
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
-      const TileCoord tc = decode_tile(probs, nprobs, t);
+      const TileCoord tc = decode_tile(probs, nprobs, tile_map, t);
       const SplitProb &pr = probs[tc.g];
-      if (!mbar_wait(accf_bar(acc), acc_phase, err, 4, true, kWaitLimitNs)) break;
+      // column exponents of this tile, once per tile, while the MMAs run
+      int *cexp = colexp + acc * kMaxBN;
+      for (int c = et; c < pr.bn; c += 128) {
+        const int64_t j = (int64_t)tc.nt * pr.bn + c;
+        cexp[c] = j < pr.p ? kind_exponent<KIND>(pr.tB[j]) : 0;
+      }
+      const bool ok = mbar_wait(accf_bar(acc), acc_phase, err, 4, true, kWaitLimitNs);
+      if (!epilogue_all(ok)) break;  // also orders the cexp writes before the reads
       tc_fence_after();
       const int64_t i = (int64_t)tc.mt * kTcBM + row;
       const bool row_ok = i < pr.n;
@@ -436,21 +469,21 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
         tmem_ld_wait();
         const int64_t j0 = (int64_t)tc.nt * pr.bn + c;
         if (!row_ok || j0 >= pr.p) continue;
+        const int *ce = cexp + c;
         if (vec && j0 + 32 <= pr.p) {
 #pragma unroll
           for (int e = 0; e < 32; e += 4) {
             float4 o;
-            o.x = ldexpf(__uint_as_float(v[e + 0]), si + kind_exponent<KIND>(pr.tB[j0 + e + 0]));
-            o.y = ldexpf(__uint_as_float(v[e + 1]), si + kind_exponent<KIND>(pr.tB[j0 + e + 1]));
-            o.z = ldexpf(__uint_as_float(v[e + 2]), si + kind_exponent<KIND>(pr.tB[j0 + e + 2]));
-            o.w = ldexpf(__uint_as_float(v[e + 3]), si + kind_exponent<KIND>(pr.tB[j0 + e + 3]));
+            o.x = scale_pow2(__uint_as_float(v[e + 0]), si + ce[e + 0]);
+            o.y = scale_pow2(__uint_as_float(v[e + 1]), si + ce[e + 1]);
+            o.z = scale_pow2(__uint_as_float(v[e + 2]), si + ce[e + 2]);
+            o.w = scale_pow2(__uint_as_float(v[e + 3]), si + ce[e + 3]);
             *reinterpret_cast<float4 *>(crow + j0 + e) = o;
           }
         } else {
 #pragma unroll
           for (int e = 0; e < 32; e++)
-            if (j0 + e < pr.p)
-              crow[j0 + e] = ldexpf(__uint_as_float(v[e]), si + kind_exponent<KIND>(pr.tB[j0 + e]));
+            if (j0 + e < pr.p) crow[j0 + e] = scale_pow2(__uint_as_float(v[e]), si + ce[e]);
         }
       }
       tc_fence_before();
@@ -502,8 +535,8 @@ cudaError_t encode_pack_map(CUtensorMap *map, void *base, int64_t rows, int bkb)
 }
 
 template <int BKB, int STAGES, int KIND>
-cudaError_t launch_tc_t(const SplitProb *d_probs, int nprobs, int total_tiles, void *pack_base,
-                        int64_t pack_rows, int grid, int *d_err, cudaStream_t s) {
+cudaError_t launch_tc_t(const SplitProb *d_probs, int nprobs, const int *tile_map, int total_tiles,
+                        void *pack_base, int64_t pack_rows, int grid, int *d_err, cudaStream_t s) {
   using L = TcLayout<BKB, STAGES, KIND>;
   static_assert(L::kSmemBytes <= 232448, "shared memory budget");
   // one CTA per SM: the kernel allocates all 512 TMEM columns
@@ -520,34 +553,36 @@ cudaError_t launch_tc_t(const SplitProb *d_probs, int nprobs, int total_tiles, v
   if (e != cudaSuccess) return e;
   TraceScope ts(KIND == kTcE4m3 ? "fp8_tc" : "split_tc", s);
   tc_gemm_kernel<BKB, STAGES, KIND><<<grid, kThreads, L::kSmemBytes, s>>>(map, d_probs, nprobs,
-                                                                         total_tiles, d_err);
+                                                                         tile_map, total_tiles,
+                                                                         d_err);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_tc(TcKind kind, const SplitProb *d_probs, int nprobs, int total_tiles,
-                      void *pack_base, int64_t pack_rows, const TcConfig &cfg, int *d_err,
-                      cudaStream_t s) {
+                      const int *tile_map, void *pack_base, int64_t pack_rows, const TcConfig &cfg,
+                      int *d_err, cudaStream_t s) {
   if (total_tiles <= 0) return cudaSuccess;
   if (pack_rows <= 0 || pack_rows > 0x7fffffffLL) return cudaErrorInvalidValue;
   int grid = cfg.grid > 0 ? cfg.grid : sm_count();
   if (grid > total_tiles) grid = total_tiles;
+  const int *mp = tile_map;
   if (kind == kTcE4m3)
-    return launch_tc_t<128, 4, kTcE4m3>(d_probs, nprobs, total_tiles, pack_base, pack_rows, grid,
-                                        d_err, s);
+    return launch_tc_t<128, 4, kTcE4m3>(d_probs, nprobs, mp, total_tiles, pack_base, pack_rows,
+                                        grid, d_err, s);
   if (kind == kTcSplitBf16x6)
-    return launch_tc_t<64, 3, kTcSplitBf16x6>(d_probs, nprobs, total_tiles, pack_base, pack_rows,
-                                              grid, d_err, s);
+    return launch_tc_t<64, 3, kTcSplitBf16x6>(d_probs, nprobs, mp, total_tiles, pack_base,
+                                              pack_rows, grid, d_err, s);
   if (cfg.bkb == 128)
-    return launch_tc_t<128, 2, kTcSplitBf16x3>(d_probs, nprobs, total_tiles, pack_base, pack_rows,
-                                               grid, d_err, s);
+    return launch_tc_t<128, 2, kTcSplitBf16x3>(d_probs, nprobs, mp, total_tiles, pack_base,
+                                               pack_rows, grid, d_err, s);
   if (cfg.bkb == 64) {
     if (cfg.stages == 3)
-      return launch_tc_t<64, 3, kTcSplitBf16x3>(d_probs, nprobs, total_tiles, pack_base,
+      return launch_tc_t<64, 3, kTcSplitBf16x3>(d_probs, nprobs, mp, total_tiles, pack_base,
                                                 pack_rows, grid, d_err, s);
-    return launch_tc_t<64, 4, kTcSplitBf16x3>(d_probs, nprobs, total_tiles, pack_base, pack_rows,
-                                              grid, d_err, s);
+    return launch_tc_t<64, 4, kTcSplitBf16x3>(d_probs, nprobs, mp, total_tiles, pack_base,
+                                              pack_rows, grid, d_err, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -85,7 +85,13 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
   const size_t pack_bytes = (size_t)rows * kPackRowBytes;
   const size_t scal_off = (pack_bytes + 255) & ~(size_t)255;
   const size_t tab_off = (scal_off + (size_t)scal * 4 + 255) & ~(size_t)255;
-  const size_t need = tab_off + ntab * sizeof(SplitProb);
+  // item -> problem maps (tiles, pack tiles, reduction items) of each group
+  // with more than one problem
+  size_t map_ints = 0;
+  for (auto &G : groups)
+    if (G.tab.size() > 1) map_ints += (size_t)(G.tiles + G.packs + G.reds);
+  const size_t map_off = (tab_off + ntab * sizeof(SplitProb) + 255) & ~(size_t)255;
+  const size_t need = map_off + map_ints * sizeof(int);
   cudaError_t e = ws.reserve(need, s);
   if (e != cudaSuccess) return note_cuda(e);
   uint8_t *base = static_cast<uint8_t *>(ws.ptr);
@@ -103,17 +109,27 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
   e = cudaMemsetAsync(base + scal_off, 0, (size_t)scal * 4, s);
   if (e != cudaSuccess) return note_cuda(e);
   size_t off = 0;
+  int *maps = reinterpret_cast<int *>(base + map_off);
   for (auto &G : groups) {
     if (G.tab.empty()) continue;
     const SplitProb *dt = d_tab + off;
     const int np = (int)G.tab.size();
     off += G.tab.size();
-    e = launch_split_scale(dt, np, (int)G.reds, s);
+    int *tile_map = nullptr, *pack_map = nullptr, *red_map = nullptr;
+    if (np > 1) {
+      tile_map = maps;
+      pack_map = tile_map + G.tiles;
+      red_map = pack_map + G.packs;
+      maps = red_map + G.reds;
+      e = launch_split_maps(dt, np, tile_map, pack_map, red_map, s);
+      if (e != cudaSuccess) return note_cuda(e);
+    }
+    e = launch_split_scale(dt, np, (int)G.reds, red_map, s);
     if (e != cudaSuccess) return note_cuda(e);
-    e = G.kind == kTcE4m3 ? launch_fp8_pack(dt, np, (int)G.packs, base, s)
-                          : launch_split_pack(G.kind, dt, np, (int)G.packs, base, s);
+    e = G.kind == kTcE4m3 ? launch_fp8_pack(dt, np, (int)G.packs, pack_map, base, s)
+                          : launch_split_pack(G.kind, dt, np, (int)G.packs, pack_map, base, s);
     if (e != cudaSuccess) return note_cuda(e);
-    e = launch_tc(G.kind, dt, np, (int)G.tiles, base, rows, G.cfg, g_ctx.d_err, s);
+    e = launch_tc(G.kind, dt, np, (int)G.tiles, tile_map, base, rows, G.cfg, g_ctx.d_err, s);
     if (e != cudaSuccess) return note_cuda(e);
   }
   return MM_OK;
@@ -183,10 +199,12 @@ mm_status run_split_chunked(Scratch &ws, int64_t n, int64_t m, int64_t p, const 
     if (c == 0 && (e = cudaStreamWaitEvent(s, in_ready[0], 0)) != cudaSuccess) break;
     if ((e = cudaStreamWaitEvent(s, in_ready[c + 1], 0)) != cudaSuccess) break;
     const SplitProb *dt = d_tab + c;
-    if ((e = launch_split_scale(dt, 1, (int)reds[(size_t)c], s)) != cudaSuccess) break;
-    if ((e = launch_split_pack(kind, dt, 1, (int)packs[(size_t)c], base, s)) != cudaSuccess) break;
-    if ((e = launch_tc(kind, dt, 1, (int)tiles[(size_t)c], base, rows, cfg, g_ctx.d_err, s)) !=
+    if ((e = launch_split_scale(dt, 1, (int)reds[(size_t)c], nullptr, s)) != cudaSuccess) break;
+    if ((e = launch_split_pack(kind, dt, 1, (int)packs[(size_t)c], nullptr, base, s)) !=
         cudaSuccess)
+      break;
+    if ((e = launch_tc(kind, dt, 1, (int)tiles[(size_t)c], nullptr, base, rows, cfg, g_ctx.d_err,
+                       s)) != cudaSuccess)
       break;
     if ((e = cudaEventRecord(out_ready[c], s)) != cudaSuccess) break;
   }
