@@ -245,6 +245,72 @@ def gpu_check(mm, n, m, p, A, B, C, dt, seed=2, samples=4096):
     return fr, sm
 
 
+def bench_paper_workloads(mm, stream, peaks, n: int = 4096, reps: int = 5):
+    """The paper's Table 2 products at its size (4096 x 4096: float, double,
+    complex float), in seconds per product beside the paper's fastest device
+    (Tesla C2050 with shared memory: 0.83 s, 1.6 s, 2.07 s), and its matrix
+    addition plus the diagonal special case as HBM bandwidth."""
+    import torch
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(0)
+    A = torch.rand((n, n), device="cuda", generator=gen) * 2 - 1
+    B = torch.rand((n, n), device="cuda", generator=gen) * 2 - 1
+    C = torch.empty((n, n), device="cuda")
+
+    def t_ms(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps * 1e3
+
+    ok = lambda st, w: mm.check_status(st, w)
+    out = {"n": n}
+    out["float_split_s"] = t_ms(lambda: ok(mm.mm_gemm(n, n, n, A, B, C, mm.MM_F32,
+                                                      mm.MM_MODE_SPLIT_BF16X3), "f")) / 1e3
+    out["float_simt_s"] = t_ms(lambda: ok(mm.mm_gemm(n, n, n, A, B, C, mm.MM_F32,
+                                                     mm.MM_MODE_SIMT), "s")) / 1e3
+    A64, B64 = A.double(), B.double()
+    C64 = torch.empty((n, n), device="cuda", dtype=torch.float64)
+    out["double_s"] = t_ms(lambda: ok(mm.mm_gemm(n, n, n, A64, B64, C64, mm.MM_F64,
+                                                 mm.MM_MODE_DGEMM), "d")) / 1e3
+    del A64, B64, C64
+    Az = torch.complex(A, B)
+    Bz = torch.complex(B, A)
+    Cz = torch.empty((n, n), device="cuda", dtype=torch.complex64)
+    out["complex_float_s"] = t_ms(lambda: ok(mm.mm_cgemm(n, n, n, Az, Bz, Cz,
+                                                         mm.MM_MODE_SPLIT_BF16X3), "c")) / 1e3
+    out["complex_float_tflops"] = 8.0 * n ** 3 / out["complex_float_s"] / 1e12
+    del Az, Bz, Cz
+    out["paper_c2050_shared_s"] = {"float": 0.83, "double": 1.6, "complex_float": 2.07}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    d = A[0].contiguous()
+
+    def kernel_ms(name, fn):
+        # device time of the library's kernel (tracer events on its stream)
+        fn()
+        mm.mm_trace_reset()
+        mm.mm_trace_enable(True)
+        for _ in range(reps):
+            fn()
+        mm.mm_trace_enable(False)
+        _, k, tot = mm.mm_trace_read(name)
+        mm.mm_trace_reset()
+        return tot / max(k, 1)
+
+    ms = kernel_ms("add", lambda: ok(mm.mm_add(n, n, 1.0, A, -1.0, B, C, mm.MM_F32), "add"))
+    out["add_gbs"] = 3 * 4 * n * n / (ms * 1e-3) / 1e9
+    out["add_frac_hbm"] = out["add_gbs"] / hbm
+    ms = kernel_ms("diag", lambda: ok(mm.mm_diag(n, n, A, d, C, 0, mm.MM_F32), "diag"))
+    out["diag_gbs"] = (2 * 4 * n * n + 4 * n) / (ms * 1e-3) / 1e9
+    out["diag_frac_hbm"] = out["diag_gbs"] / hbm
+    out["note"] = ("products: synchronous calls timed on the host; add / diag: kernel time from "
+                   "the library's event tracer; add moves 192 MB and diag 128 MB per call")
+    return out
+
+
 def bench_grouped(mm, stream, steps: int, seed: int = 4, count: int = 4096):
     """Grouped GEMM of `count` products, n, m, p uniform over {32, ..., 1024}
     step 32 (seeded), split path: one grouped launch per step vs one launch
@@ -545,6 +611,7 @@ def run_mine(args):
         extra["split_check"] = gpu_check(mm, n, n, n, A, B, C, mm.MM_F32)
         extra["tolerance_f32"] = 1e-6 * n ** 0.5
         line["paths"] = extra
+        line["paper_workloads_4096"] = bench_paper_workloads(mm, stream, peaks)
         line["grouped"] = bench_grouped(mm, stream, max(3, args.steps // 20))
         cap = None
         serving = {}

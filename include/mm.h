@@ -216,6 +216,34 @@ mm_status mm_trace_read(const char *kernel, int64_t *launches, double *total_ms)
 /* Number of library kernel launches since mm_init (all kernels). */
 int64_t mm_launch_count(void);
 
+/* ------------------------------------------- related products of the paper */
+
+/* Complex C = A.B for complex64 matrices (interleaved re, im; row-major,
+ * dense): the product of the paper's Table 2 "complex float" column.  Runs
+ * the four real products Ar.Br, Ai.Bi, Ar.Bi, Ai.Br as one grouped call of the
+ * chosen real path (MM_MODE_SIMT or MM_MODE_SPLIT_BF16X3; AUTO = split) and
+ * assembles C.  Device pointers; synchronous; library scratch holds the
+ * planes and partial products.  Accuracy: max |c^ - c| / sum_r |a_ir||b_rj|
+ * <= 2e-6 sqrt(m) (moduli). */
+mm_status mm_cgemm(int64_t n, int64_t m, int64_t p, const void *A, const void *B,
+                   void *C, mm_mode mode);
+
+/* C = alpha A + beta B elementwise for n x p matrices (device pointers, dtype
+ * dt): the matrix addition / subtraction the paper measures beside the
+ * product (results section).  alpha = 1, beta = +-1 give one correctly
+ * rounded addition or subtraction per entry; otherwise fma(alpha, a, beta b).
+ * Synchronous. */
+mm_status mm_add(int64_t n, int64_t p, double alpha, const void *A, double beta,
+                 const void *B, void *C, mm_dtype dt);
+
+/* Product with a diagonal matrix, the special case the paper names in its
+ * algorithms section: side 0: C = X.diag(d) (c_ij = x_ij d_j, d has p
+ * entries); side 1: C = diag(d).X (c_ij = d_i x_ij, d has n entries).  One
+ * correctly rounded product per entry; reads X once.  X, C: n x p, device
+ * pointers, dtype dt.  Synchronous. */
+mm_status mm_diag(int64_t n, int64_t p, const void *X, const void *d, void *C,
+                  int side, mm_dtype dt);
+
 /* ------------------------------------------------ allocation-free variant */
 
 /* The FP32 split product of mm_gemm's MM_MODE_SPLIT_BF16X3 path, for callers

@@ -41,6 +41,8 @@ def _bind(lib):
     lib.oracle_gemv_dot2.restype = None
     lib.oracle_gemm_pow2_exact.argtypes = [_i64, _i64, _i64, _dp, _dp, ctypes.c_int, _dp, _dp]
     lib.oracle_gemm_pow2_exact.restype = _i64
+    lib.oracle_cgemm_f64.argtypes = [_i64, _i64, _i64, _dp, _dp, _dp, _dp]
+    lib.oracle_cgemm_f64.restype = None
     lib.oracle_default_threads.restype = ctypes.c_int
     lib.oracle_ldbl_mant_dig.restype = ctypes.c_int
     lib.oracle_mutant.restype = ctypes.c_int
@@ -126,6 +128,18 @@ class Oracle:
         za, _ = self.gemv(np.abs(_f64(A)), wa)
         return z, za
 
+    def cgemm(self, A, B):
+        """Complex C = A.B in FP64 (Listing 1 order) and |A|.|B| (moduli)."""
+        A = np.ascontiguousarray(A, np.complex128)
+        B = np.ascontiguousarray(B, np.complex128)
+        n, m = A.shape
+        p = B.shape[1]
+        C = np.empty((n, p), np.complex128)
+        absC = np.empty((n, p), np.float64)
+        self.lib.oracle_cgemm_f64(n, m, p, A.ctypes.data_as(_dp), B.ctypes.data_as(_dp),
+                                  C.ctypes.data_as(_dp), _p(absC))
+        return C, absC
+
     def pow2_exact(self, A, B, shift: int = 50):
         """Exact C for inputs that are 0 or +-2^k: (hi, lo) doubles."""
         A = _f64(A); B = _f64(B)
@@ -173,6 +187,18 @@ def rel_errors(c_hat, c_ref, abs_ref):
     return e
 
 
+def rel_errors_complex(c_hat, c_ref, abs_ref):
+    """Complex version of rel_errors: |c_hat - c_ref| (modulus) / abs_ref."""
+    c_hat = np.asarray(c_hat, np.complex128)
+    c_ref = np.asarray(c_ref, np.complex128)
+    abs_ref = np.asarray(abs_ref, np.float64)
+    diff = np.abs(c_hat - c_ref)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        e = np.where(abs_ref > 0, diff / np.where(abs_ref > 0, abs_ref, 1.0),
+                     np.where(diff == 0, 0.0, np.inf))
+    return np.where(np.isnan(diff), np.inf, e)
+
+
 def tolerance(m: int, dtype: str) -> float:
     """Stated tolerance on max e_ij: 1e-6*sqrt(m) for the FP32-accuracy paths,
     1e-14*sqrt(m) for FP64 (m = inner dimension, at least 1)."""
@@ -181,6 +207,10 @@ def tolerance(m: int, dtype: str) -> float:
         return 1e-6 * np.sqrt(m)
     if dtype in ("f64", "dgemm"):
         return 1e-14 * np.sqrt(m)
+    if dtype == "c32":
+        # each part of a complex entry is a difference/sum of two real
+        # products, each within 1e-6 sqrt(m) of its own normaliser <= |A||B|
+        return 2e-6 * np.sqrt(m)
     raise ValueError(dtype)
 
 

@@ -34,7 +34,7 @@
  *   oracle_gemm_pow2_exact  exact fixed-point sum for inputs that are 0 or
  *                        +-2^k (the power-of-two stress case).
  *
- * Compile-time mutants (ORACLE_MUTANT=1..8) plant plausible mistakes; the
+ * Compile-time mutants (ORACLE_MUTANT=1..9) plant plausible mistakes; the
  * pin tests build them to show that every such mistake is caught.
  */
 #include <math.h>
@@ -231,6 +231,34 @@ void oracle_gemv_dot2(int64_t rows, int64_t cols, const double *X,
       yabs[i] = sa;
     }
   }
+}
+
+/* ------------------------------------------------------- complex product */
+
+/* Complex C = A.B (the definition with complex entries; Table 2's "complex
+ * float" column computes this product): interleaved (re, im) row-major
+ * arrays of doubles, A n x m, B m x p, C n x p, Listing 1's order per entry.
+ * absC (optional, real n x p) = sum_r |a_ir| |b_rj| with complex moduli. */
+void oracle_cgemm_f64(int64_t n, int64_t m, int64_t p, const double *A, const double *B,
+                      double *C, double *absC) {
+  for (int64_t i = 0; i < n; i++)
+    for (int64_t j = 0; j < p; j++) {
+      double sr = 0.0, si = 0.0, sa = 0.0;
+      for (int64_t k = 0; k < m; k++) {
+        const double ar = A[2 * (i * m + k)], ai = A[2 * (i * m + k) + 1];
+        const double br = B[2 * (k * p + j)], bi = B[2 * (k * p + j) + 1];
+        sr += ar * br - ai * bi;
+#if ORACLE_MUTANT == 9
+        si += ar * bi - ai * br; /* mutant: sign of a cross term */
+#else
+        si += ar * bi + ai * br;
+#endif
+        sa += sqrt(ar * ar + ai * ai) * sqrt(br * br + bi * bi);
+      }
+      C[2 * (i * p + j)] = sr;
+      C[2 * (i * p + j) + 1] = si;
+      if (absC) absC[i * p + j] = sa;
+    }
 }
 
 /* ------------------------------------------------------ exact power-of-two */

@@ -83,6 +83,11 @@ def lib():
         L.mm_trace_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(_i64), _dp]
         L.mm_launch_count.argtypes = []
         L.mm_launch_count.restype = _i64
+        L.mm_cgemm.argtypes = [_i64, _i64, _i64, _vp, _vp, _vp, st]
+        L.mm_add.argtypes = [_i64, _i64, ctypes.c_double, _vp, ctypes.c_double, _vp, _vp, st]
+        L.mm_diag.argtypes = [_i64, _i64, _vp, _vp, _vp, ctypes.c_int, st]
+        for name in ("mm_cgemm", "mm_add", "mm_diag"):
+            getattr(L, name).restype = ctypes.c_int
         L.mm_gemm_split_static.argtypes = [_i64, _i64, _i64, _vp, _vp, _vp, _vp]
         L.mm_gemm_split_static.restype = ctypes.c_int
         for name in ("mm_init", "mm_shutdown", "mm_gemm", "mm_gemm_async", "mm_gemm_grouped",
@@ -251,6 +256,21 @@ def mm_trace_read(kernel: str):
 
 def mm_launch_count() -> int:
     return int(lib().mm_launch_count())
+
+
+def mm_cgemm(n, m, p, A, B, C, mode) -> int:
+    """Complex product of complex64 device matrices (see include/mm.h)."""
+    return lib().mm_cgemm(n, m, p, _ptr(A), _ptr(B), _ptr(C), mode)
+
+
+def mm_add(n, p, alpha, A, beta, B, C, dt) -> int:
+    """C = alpha A + beta B elementwise (device matrices)."""
+    return lib().mm_add(n, p, float(alpha), _ptr(A), float(beta), _ptr(B), _ptr(C), dt)
+
+
+def mm_diag(n, p, X, d, C, side, dt) -> int:
+    """side 0: C = X.diag(d); side 1: C = diag(d).X (device matrices)."""
+    return lib().mm_diag(n, p, _ptr(X), _ptr(d), _ptr(C), side, dt)
 
 
 def mm_gemm_split_static(n, m, p, A, B, C, stream=None) -> int:

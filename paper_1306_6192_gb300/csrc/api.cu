@@ -368,6 +368,7 @@ mm_status mm_shutdown(void) {
   g_ctx.fp8_ws.release();
   g_ctx.stage_ws.release();
   g_ctx.check_ws.release();
+  g_ctx.cplx_ws.release();
   if (g_ctx.d_err) cudaFree(g_ctx.d_err);
   g_ctx.d_err = nullptr;
   trace_destroy();

@@ -54,6 +54,7 @@ struct Ctx {
   Scratch grouped_ws;    // tables of the grouped SIMT path
   Scratch stage_ws;      // device copies of host operands
   Scratch check_ws;      // FP64 check work vectors
+  Scratch cplx_ws;       // real/imaginary planes and partial products (mm_cgemm)
   // host-operand pipeline of mm_gemm: copy streams and per-chunk events
   cudaStream_t h2d = nullptr, d2h = nullptr;
   static constexpr int kMaxChunks = 8;

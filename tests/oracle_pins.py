@@ -226,9 +226,39 @@ def pin_pow2_exact(orc):
             assert got == Cx[i][j], (i, j)
 
 
+def pin_complex(orc):
+    """Complex product: exact Gaussian rationals on tiny shapes, numpy's exact
+    complex product on small integers, and c = A.B with real A, B reducing to
+    the real oracle."""
+    def cfrac(z):
+        return (Fraction(float(z.real)), Fraction(float(z.imag)))
+    for t, (n, m, p) in enumerate([(1, 1, 1), (2, 3, 4), (5, 7, 3)]):
+        A = synth.uniform_pm1(1300 + t, (n, m)) + 1j * synth.uniform_pm1(1310 + t, (n, m))
+        B = synth.uniform_pm1(1320 + t, (m, p)) + 1j * synth.uniform_pm1(1330 + t, (m, p))
+        C, absC = orc.cgemm(A, B)
+        for i in range(n):
+            for j in range(p):
+                er = Fraction(0); ei = Fraction(0)
+                for r in range(m):
+                    ar, ai = cfrac(A[i, r]); br, bi = cfrac(B[r, j])
+                    er += ar * br - ai * bi
+                    ei += ar * bi + ai * br
+                bound = 4 * m * U64 * float(absC[i, j]) + 1e-300
+                assert abs(float(Fraction(float(C[i, j].real)) - er)) <= bound
+                assert abs(float(Fraction(float(C[i, j].imag)) - ei)) <= bound
+    Ai = synth.small_ints(1340, (20, 33)) + 1j * synth.small_ints(1341, (20, 33))
+    Bi = synth.small_ints(1342, (33, 17)) + 1j * synth.small_ints(1343, (33, 17))
+    C, _ = orc.cgemm(Ai, Bi)
+    assert np.array_equal(C, Ai.astype(np.complex128) @ Bi.astype(np.complex128))
+    Ar = synth.uniform_pm1(1344, (9, 11)); Br = synth.uniform_pm1(1345, (11, 6))
+    C, absC = orc.cgemm(Ar, Br)
+    Cr, Sr = orc.gemm(Ar, Br, with_abs=True)
+    assert np.array_equal(C.real, Cr) and np.all(C.imag == 0) and np.array_equal(absC, Sr)
+
+
 ALL_PINS = [
     pin_bruteforce_definition, pin_small_ints_exact, pin_hand_example,
     pin_identity, pin_diagonal, pin_transpose, pin_freivalds,
     pin_threads_invariant, pin_empty_dims, pin_dot2_and_long_double,
-    pin_gemv, pin_pow2_exact,
+    pin_gemv, pin_pow2_exact, pin_complex,
 ]

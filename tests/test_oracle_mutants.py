@@ -1,13 +1,14 @@
 """Every planted mistake in the oracle (a dropped term, a reversed index, a
 sign error, a transposed operand, a missing reset, a normaliser without
-absolute values, a Dot2 without compensation) must fail at least one pin."""
+absolute values, a Dot2 without compensation, a wrong sign in the complex
+product) must fail at least one pin."""
 import pytest
 
 import oracle
 from oracle import build as obuild
 import oracle_pins
 
-MUTANTS = list(range(1, 9))
+MUTANTS = list(range(1, 10))
 MUTANTS.remove(6)  # 6 is unused (its slot was merged into 4)
 
 
