@@ -548,7 +548,7 @@ def run_mine(args):
         ms, launches = timed(step, args.steps, args.warmup, trace=True)
     clocks = clk.summary()
     per_kernel = {}
-    for k in ("split_scale", "split_pack", "split_tc", "simt_f32"):
+    for k in ("split_scale", "split_pack", "split_verify", "split_fix", "split_tc", "simt_f32"):
         st, cnt, kms = mm.mm_trace_read(k)
         if cnt:
             per_kernel[k] = {"launches": cnt, "avg_ms": kms / cnt}

@@ -55,6 +55,9 @@ struct SplitProb {
   float *C;
   int64_t a_row0, b_row0;
   uint32_t *sA, *tB;
+  // split kinds: max |x| per (K block, row of A) and (K block, column of B),
+  // written by the unscaled pack: pA[kb*n + i], pB[kb*p + j]
+  uint32_t *pA, *pB;
   int32_t n, m, p;
   int32_t mt, nt, kt;      // ceil(n/128), ceil(p/bn), ceil(m/pack_k)
   int32_t bn, group_m;     // N tile (64, 128 or 256), raster band height
@@ -90,9 +93,16 @@ cudaError_t launch_split_maps(const SplitProb *d_probs, int nprobs, int *tile_ma
                               int *pack_map, int *red_map, cudaStream_t s);
 cudaError_t launch_split_scale(const SplitProb *d_probs, int nprobs,
                                int total_items, const int *map, cudaStream_t s);
-cudaError_t launch_split_pack(TcKind kind, const SplitProb *d_probs, int nprobs,
-                              int total_tiles, const int *map, void *pack_base,
-                              cudaStream_t s);
+// Pack modes (split kinds) and the per-problem flags they use.
+constexpr int kPackUnscaled = 1, kPackFix = 2;
+constexpr int kFlagScaleA = 1, kFlagScaleB = 2;
+cudaError_t launch_split_pack(TcKind kind, int mode, const SplitProb *d_probs, int nprobs,
+                              int total_tiles, const int *map, const int *flags,
+                              void *pack_base, cudaStream_t s);
+// After an unscaled pack: reduces the partial maxima into sA / tB and sets
+// flags[g] (zeroed by the caller).  max_words = max over problems of n + p.
+cudaError_t launch_split_verify(const SplitProb *d_probs, int nprobs, int64_t max_words,
+                                int *flags, cudaStream_t s);
 cudaError_t launch_fp8_pack(const SplitProb *d_probs, int nprobs,
                             int total_tiles, const int *map, void *pack_base,
                             cudaStream_t s);
@@ -103,10 +113,12 @@ struct TcConfig {
   int stages;   // pipeline depth
   int grid;     // persistent CTAs (<= number of SMs; 0 = one per SM)
 };
+// flags: per-problem kFlagScaleA / kFlagScaleB (nullptr: both operands were
+// packed scaled).
 cudaError_t launch_tc(TcKind kind, const SplitProb *d_probs, int nprobs,
-                      int total_tiles, const int *tile_map, void *pack_base,
-                      int64_t pack_rows, const TcConfig &cfg, int *d_err,
-                      cudaStream_t s);
+                      int total_tiles, const int *tile_map, const int *flags,
+                      void *pack_base, int64_t pack_rows, const TcConfig &cfg,
+                      int *d_err, cudaStream_t s);
 
 // FP64 check (Freivalds + sampled entries): writes 2 doubles to d_out.
 cudaError_t launch_check(bool f64, int64_t n, int64_t m, int64_t p,

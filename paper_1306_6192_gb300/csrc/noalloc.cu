@@ -33,6 +33,7 @@ namespace {
 
 constexpr size_t kNoAllocBytes = (size_t)64 << 20;
 constexpr size_t kFlagOff = 0;      // int timeout flag
+constexpr size_t kScaleFlagOff = 64;  // int per-operand scale flags
 constexpr size_t kTableOff = 256;   // one SplitProb
 constexpr size_t kScalesOff = 512;  // uint32 per row of A and column of B
 constexpr int kMaxDevices = 64;
@@ -115,13 +116,16 @@ mm_status mm_gemm_split_static(int64_t n, int64_t m, int64_t p, const float *A, 
   sp.kt = (int32_t)ceil_div(m, pack_k(kind));
   const int64_t a_rows = (int64_t)sp.mt * sp.kt * parts * kTcBM;
   const int64_t rows = a_rows + (int64_t)sp.nt * sp.kt * parts * ch.bn;
-  const size_t pack_off = (kScalesOff + (size_t)(n + p) * 4 + 1023) & ~(size_t)1023;
+  const size_t part_off = (kScalesOff + (size_t)(n + p) * 4 + 255) & ~(size_t)255;
+  const size_t pack_off = (part_off + (size_t)sp.kt * (n + p) * 4 + 1023) & ~(size_t)1023;
   if (pack_off + (size_t)rows * kPackRowBytes > kNoAllocBytes) return MM_ESCRATCH;
   uint8_t *pack = base + pack_off;
   sp.a_row0 = 0;
   sp.b_row0 = a_rows;
   sp.sA = reinterpret_cast<uint32_t *>(base + kScalesOff);
   sp.tB = sp.sA + n;
+  sp.pA = reinterpret_cast<uint32_t *>(base + part_off);
+  sp.pB = sp.pA + (int64_t)sp.kt * n;
   sp.tile_start = 0;
   sp.pack_start = 0;
   sp.red_start = 0;
@@ -131,19 +135,26 @@ mm_status mm_gemm_split_static(int64_t n, int64_t m, int64_t p, const float *A, 
   const int64_t reds = sp.red_a + ceil_div(p, 32) * ceil_div(m, 256);
   SplitProb *d_tab = reinterpret_cast<SplitProb *>(base + kTableOff);
   int *d_flag = reinterpret_cast<int *>(base + kFlagOff);
-  // The array keeps the previous call's contents: the column maxima (reduced
-  // with atomicMax) and the timeout flag must start at zero; every pack row
-  // the kernels read is rewritten (zero padding included) by the pack kernel.
-  cudaError_t e = cudaMemsetAsync(d_flag, 0, sizeof(int), s);
+  // The array keeps the previous call's contents: the timeout and scale flags
+  // must start at zero; the maxima and every pack row the kernels read are
+  // rewritten (zero padding included) by the pack and verify kernels.
+  cudaError_t e = cudaMemsetAsync(d_flag, 0, 128, s);  // timeout flag and scale flags
   if (e == cudaSuccess) e = cudaMemsetAsync(sp.sA, 0, (size_t)(n + p) * 4, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_tab, &sp, sizeof(sp), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = launch_split_scale(d_tab, 1, (int)reds, nullptr, s);
-  if (e == cudaSuccess) e = launch_split_pack(kind, d_tab, 1, (int)packs, nullptr, pack, s);
+  int *d_sflag = reinterpret_cast<int *>(base + kScaleFlagOff);
+  (void)reds;
+  // same passes as mm_gemm's split path: unscaled pack with the maxima,
+  // verification, re-pack of operands out of range
+  if (e == cudaSuccess)
+    e = launch_split_pack(kind, kPackUnscaled, d_tab, 1, (int)packs, nullptr, nullptr, pack, s);
+  if (e == cudaSuccess) e = launch_split_verify(d_tab, 1, n + p, d_sflag, s);
+  if (e == cudaSuccess)
+    e = launch_split_pack(kind, kPackFix, d_tab, 1, (int)packs, nullptr, d_sflag, pack, s);
   if (e == cudaSuccess) {
     TcConfig cfg = kind == kTcSplitBf16x3 ? TcConfig{2 * ch.bk, ch.stages, sms}
                                           : TcConfig{64, 3, sms};
-    e = launch_tc(kind, d_tab, 1, (int)tiles, nullptr, pack, rows, cfg, d_flag, s);
+    e = launch_tc(kind, d_tab, 1, (int)tiles, nullptr, d_sflag, pack, rows, cfg, d_flag, s);
   }
   if (e != cudaSuccess) {
     cudaGetLastError();

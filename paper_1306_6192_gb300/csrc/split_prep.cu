@@ -20,6 +20,16 @@
 //                       hi, mid, lo for the three-part split) of the pack
 //                       (layout in mm_internal.h); zero outside the matrix
 //                       so the tensor-core kernel needs no edge checks.
+//
+// The split path packs in one pass over A and B (kPackUnscaled): scaling by
+// a power of two commutes with rounding to bf16 and with the FP32 sums as long
+// as nothing leaves the normal range, so for rows/columns whose largest
+// magnitude lies in [2^-40, 2^40] the unscaled split gives the same bits as
+// the scaled one.  That pass also writes each tile's row/column maxima;
+// split_verify_kernel reduces them to the maxima of whole rows/columns and
+// flags, per problem, an operand with a row/column outside the range, and a
+// second pack launch (kPackFix) re-packs only the flagged operands with their
+// scales.  The epilogue applies 2^(s_i + t_j) only for flagged operands.
 #include "split_common.cuh"
 
 namespace mm {
@@ -144,10 +154,27 @@ __device__ __forceinline__ void split4(float4 x, int s, uint2 (&out)[PARTS]) {
   }
 }
 
-template <int PARTS>
+// max |x| over four values as a float bit pattern
+__device__ __forceinline__ uint32_t max4_bits(float4 x) {
+  return umax(umax(abs_bits(x.x), abs_bits(x.y)), umax(abs_bits(x.z), abs_bits(x.w)));
+}
+
+// max over the 16 lanes of a half warp (lanes 0-15 or 16-31)
+__device__ __forceinline__ uint32_t half_warp_max(uint32_t v) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v = umax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// MODE: kPackUnscaled - no scaling; write the tile's row (A) / column (B)
+//                       maxima to pA / pB;
+//       kPackFix      - scale by 2^-s from the maxima in sA / tB; only the
+//                       operands flagged by split_verify_kernel (the other
+//                       blocks return).
+template <int PARTS, int MODE>
 __global__ void __launch_bounds__(256)
 split_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *__restrict__ map,
-                  uint2 *__restrict__ pack) {
+                  const int *__restrict__ flags, uint2 *__restrict__ pack) {
   const int item = blockIdx.x;
   const int g =
       find_problem(probs, nprobs, map, item, [](const SplitProb &q) { return q.pack_start; });
@@ -155,7 +182,9 @@ split_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *__
   const int local = item - pr.pack_start;
   const int tid = threadIdx.x;
   constexpr int kQuads = kPackK / 4;  // groups of four bf16 (8 bytes) per pack row
-  if (local < pr.mt * pr.kt) {
+  const bool a_tile = local < pr.mt * pr.kt;
+  if (MODE == kPackFix && !(flags[g] & (a_tile ? kFlagScaleA : kFlagScaleB))) return;
+  if (a_tile) {
     // A tile (mt, kb): rows mt*128.., k kb*64..; a warp covers two rows.
     const int mt = local / pr.kt, kb = local % pr.kt;
     const int64_t base = pr.a_row0 + (int64_t)local * PARTS * kTcBM;
@@ -176,7 +205,12 @@ split_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *__
           if (k + 2 < pr.m) x.z = row[k + 2];
           if (k + 3 < pr.m) x.w = row[k + 3];
         }
-        s = scale_exponent(pr.sA[i]);
+        if (MODE != kPackUnscaled) s = scale_exponent(pr.sA[i]);
+      }
+      if (MODE == kPackUnscaled) {
+        // the 16 threads of a half warp hold one row's 64 values
+        const uint32_t mx = half_warp_max(max4_bits(x));
+        if (kq == 0 && i < pr.n) pr.pA[(int64_t)kb * pr.n + i] = mx;
       }
       uint2 part[PARTS];
       split4<PARTS>(x, s, part);
@@ -218,15 +252,64 @@ split_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *__
       for (int q = tid; q < 64 * kQuads; q += 256) {
         const int c = q / kQuads, kq = q % kQuads;
         const int64_t j = (int64_t)nt * bn + c0 + c;
-        const int s = j < pr.p ? scale_exponent(pr.tB[j]) : 0;
+        const int s = (MODE != kPackUnscaled && j < pr.p) ? scale_exponent(pr.tB[j]) : 0;
         const float4 x = make_float4(tile[4 * kq][c], tile[4 * kq + 1][c], tile[4 * kq + 2][c],
                                      tile[4 * kq + 3][c]);
+        if (MODE == kPackUnscaled) {
+          // the 16 threads of a half warp hold one column's 64 values
+          const uint32_t mx = half_warp_max(max4_bits(x));
+          if (kq == 0 && j < pr.p) pr.pB[(int64_t)kb * pr.p + j] = mx;
+        }
         uint2 part[PARTS];
         split4<PARTS>(x, s, part);
 #pragma unroll
         for (int h = 0; h < PARTS; h++) pack[(base + h * bn + c0 + c) * kQuads + kq] = part[h];
       }
       __syncthreads();
+    }
+  }
+}
+
+// A row/column maximum outside [2^-40, 2^40] (or not finite) needs scaling;
+// zero needs none.
+__device__ __forceinline__ bool needs_scale(uint32_t max_bits) {
+  return max_bits != 0 && (max_bits < 0x2B800000u /* 2^-40 */ || max_bits > 0x53800000u /* 2^40 */);
+}
+
+// Blocks (x: 32 rows/columns, y: problems; 8 warps split the K blocks): the
+// maximum of a row of A over its K blocks -> sA (columns of B -> tB), and
+// flags[g] |= kFlagScaleA / kFlagScaleB where a maximum is outside the range
+// packed unscaled.
+__global__ void __launch_bounds__(256)
+split_verify_kernel(const SplitProb *__restrict__ probs, int nprobs, int *__restrict__ flags) {
+  __shared__ uint32_t part[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int g = blockIdx.y; g < nprobs; g += gridDim.y) {
+    const SplitProb &pr = probs[g];
+    const int64_t w = (int64_t)blockIdx.x * 32 + lane;
+    const bool is_row = w < pr.n;
+    const bool valid = w < (int64_t)pr.n + pr.p;
+    const uint32_t *src = is_row ? pr.pA + w : pr.pB + (w - pr.n);
+    const int64_t stride = is_row ? pr.n : pr.p;
+    uint32_t mx = 0;
+    if (valid) {
+#pragma unroll 4
+      for (int kb = warp; kb < pr.kt; kb += 8) mx = umax(mx, src[kb * stride]);
+    }
+    part[warp][lane] = mx;
+    __syncthreads();
+    int bad = 0;
+    if (warp == 0 && valid) {
+#pragma unroll
+      for (int q = 1; q < 8; q++) mx = umax(mx, part[q][lane]);
+      if (is_row) pr.sA[w] = mx; else pr.tB[w - pr.n] = mx;
+      if (needs_scale(mx)) bad = is_row ? kFlagScaleA : kFlagScaleB;
+    }
+    const int any = __syncthreads_or(bad);
+    if (any) {
+      const int a = __syncthreads_or(bad & kFlagScaleA);
+      const int b = __syncthreads_or(bad & kFlagScaleB);
+      if (threadIdx.x == 0) atomicOr(&flags[g], (a ? kFlagScaleA : 0) | (b ? kFlagScaleB : 0));
     }
   }
 }
@@ -265,15 +348,26 @@ cudaError_t launch_split_scale(const SplitProb *d_probs, int nprobs, int total_i
   return cudaGetLastError();
 }
 
-cudaError_t launch_split_pack(TcKind kind, const SplitProb *d_probs, int nprobs, int total_tiles,
-                              const int *map, void *pack_base, cudaStream_t s) {
+cudaError_t launch_split_pack(TcKind kind, int mode, const SplitProb *d_probs, int nprobs,
+                              int total_tiles, const int *map, const int *flags, void *pack_base,
+                              cudaStream_t s) {
   if (total_tiles <= 0) return cudaSuccess;
-  TraceScope ts("split_pack", s);
+  TraceScope ts(mode == kPackFix ? "split_fix" : "split_pack", s);
   auto *pk = static_cast<uint2 *>(pack_base);
-  if (kind == kTcSplitBf16x6)
-    split_pack_kernel<3><<<total_tiles, 256, 0, s>>>(d_probs, nprobs, map, pk);
-  else
-    split_pack_kernel<2><<<total_tiles, 256, 0, s>>>(d_probs, nprobs, map, pk);
+  const bool x6 = kind == kTcSplitBf16x6;
+#define MM_PACK(P, M) split_pack_kernel<P, M><<<total_tiles, 256, 0, s>>>(d_probs, nprobs, map, flags, pk)
+  if (mode == kPackUnscaled) { if (x6) MM_PACK(3, kPackUnscaled); else MM_PACK(2, kPackUnscaled); }
+  else { if (x6) MM_PACK(3, kPackFix); else MM_PACK(2, kPackFix); }
+#undef MM_PACK
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_verify(const SplitProb *d_probs, int nprobs, int64_t max_words,
+                                int *flags, cudaStream_t s) {
+  if (nprobs <= 0 || max_words <= 0) return cudaSuccess;
+  TraceScope ts("split_verify", s);
+  dim3 grid((unsigned)((max_words + 31) / 32), (unsigned)(nprobs < 65535 ? nprobs : 65535));
+  split_verify_kernel<<<grid, 256, 0, s>>>(d_probs, nprobs, flags);
   return cudaGetLastError();
 }
 

@@ -268,7 +268,8 @@ struct TcLayout {
 template <int BKB, int STAGES, int KIND>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__restrict__ probs,
-               int nprobs, const int *__restrict__ tile_map, int total_tiles, int *err) {
+               int nprobs, const int *__restrict__ tile_map, const int *__restrict__ flags,
+               int total_tiles, int *err) {
   using L = TcLayout<BKB, STAGES, KIND>;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -448,17 +449,19 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
       const TileCoord tc = decode_tile(probs, nprobs, tile_map, t);
       const SplitProb &pr = probs[tc.g];
       // column exponents of this tile, once per tile, while the MMAs run
+      // operands packed without scaling (flags) take exponent 0
+      const int fl = flags ? flags[tc.g] : (kFlagScaleA | kFlagScaleB);
       int *cexp = colexp + acc * kMaxBN;
       for (int c = et; c < pr.bn; c += 128) {
         const int64_t j = (int64_t)tc.nt * pr.bn + c;
-        cexp[c] = j < pr.p ? kind_exponent<KIND>(pr.tB[j]) : 0;
+        cexp[c] = (j < pr.p && (fl & kFlagScaleB)) ? kind_exponent<KIND>(pr.tB[j]) : 0;
       }
       const bool ok = mbar_wait(accf_bar(acc), acc_phase, err, 4, true, kWaitLimitNs);
       if (!epilogue_all(ok)) break;  // also orders the cexp writes before the reads
       tc_fence_after();
       const int64_t i = (int64_t)tc.mt * kTcBM + row;
       const bool row_ok = i < pr.n;
-      const int si = row_ok ? kind_exponent<KIND>(pr.sA[i]) : 0;
+      const int si = (row_ok && (fl & kFlagScaleA)) ? kind_exponent<KIND>(pr.sA[i]) : 0;
       float *crow = pr.C + (row_ok ? i : 0) * (int64_t)pr.p;
       const bool vec = ((reinterpret_cast<uintptr_t>(pr.C) & 15u) == 0) && ((pr.p & 3) == 0);
       const uint32_t tacc = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kAccCols);
@@ -535,8 +538,9 @@ cudaError_t encode_pack_map(CUtensorMap *map, void *base, int64_t rows, int bkb)
 }
 
 template <int BKB, int STAGES, int KIND>
-cudaError_t launch_tc_t(const SplitProb *d_probs, int nprobs, const int *tile_map, int total_tiles,
-                        void *pack_base, int64_t pack_rows, int grid, int *d_err, cudaStream_t s) {
+cudaError_t launch_tc_t(const SplitProb *d_probs, int nprobs, const int *tile_map,
+                        const int *flags, int total_tiles, void *pack_base, int64_t pack_rows,
+                        int grid, int *d_err, cudaStream_t s) {
   using L = TcLayout<BKB, STAGES, KIND>;
   static_assert(L::kSmemBytes <= 232448, "shared memory budget");
   // one CTA per SM: the kernel allocates all 512 TMEM columns
@@ -553,35 +557,35 @@ cudaError_t launch_tc_t(const SplitProb *d_probs, int nprobs, const int *tile_ma
   if (e != cudaSuccess) return e;
   TraceScope ts(KIND == kTcE4m3 ? "fp8_tc" : "split_tc", s);
   tc_gemm_kernel<BKB, STAGES, KIND><<<grid, kThreads, L::kSmemBytes, s>>>(map, d_probs, nprobs,
-                                                                         tile_map, total_tiles,
-                                                                         d_err);
+                                                                         tile_map, flags,
+                                                                         total_tiles, d_err);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_tc(TcKind kind, const SplitProb *d_probs, int nprobs, int total_tiles,
-                      const int *tile_map, void *pack_base, int64_t pack_rows, const TcConfig &cfg,
-                      int *d_err, cudaStream_t s) {
+                      const int *tile_map, const int *flags, void *pack_base, int64_t pack_rows,
+                      const TcConfig &cfg, int *d_err, cudaStream_t s) {
   if (total_tiles <= 0) return cudaSuccess;
   if (pack_rows <= 0 || pack_rows > 0x7fffffffLL) return cudaErrorInvalidValue;
   int grid = cfg.grid > 0 ? cfg.grid : sm_count();
   if (grid > total_tiles) grid = total_tiles;
   const int *mp = tile_map;
   if (kind == kTcE4m3)
-    return launch_tc_t<128, 4, kTcE4m3>(d_probs, nprobs, mp, total_tiles, pack_base, pack_rows,
+    return launch_tc_t<128, 4, kTcE4m3>(d_probs, nprobs, mp, flags, total_tiles, pack_base, pack_rows,
                                         grid, d_err, s);
   if (kind == kTcSplitBf16x6)
-    return launch_tc_t<64, 3, kTcSplitBf16x6>(d_probs, nprobs, mp, total_tiles, pack_base,
+    return launch_tc_t<64, 3, kTcSplitBf16x6>(d_probs, nprobs, mp, flags, total_tiles, pack_base,
                                               pack_rows, grid, d_err, s);
   if (cfg.bkb == 128)
-    return launch_tc_t<128, 2, kTcSplitBf16x3>(d_probs, nprobs, mp, total_tiles, pack_base,
+    return launch_tc_t<128, 2, kTcSplitBf16x3>(d_probs, nprobs, mp, flags, total_tiles, pack_base,
                                                pack_rows, grid, d_err, s);
   if (cfg.bkb == 64) {
     if (cfg.stages == 3)
-      return launch_tc_t<64, 3, kTcSplitBf16x3>(d_probs, nprobs, mp, total_tiles, pack_base,
+      return launch_tc_t<64, 3, kTcSplitBf16x3>(d_probs, nprobs, mp, flags, total_tiles, pack_base,
                                                 pack_rows, grid, d_err, s);
-    return launch_tc_t<64, 4, kTcSplitBf16x3>(d_probs, nprobs, mp, total_tiles, pack_base,
+    return launch_tc_t<64, 4, kTcSplitBf16x3>(d_probs, nprobs, mp, flags, total_tiles, pack_base,
                                               pack_rows, grid, d_err, s);
   }
   return cudaErrorInvalidValue;

@@ -20,12 +20,13 @@ struct Group {
   TcConfig cfg{0, 0, 0};
   std::vector<SplitProb> tab;
   int64_t tiles = 0, packs = 0, reds = 0;
+  int64_t max_words = 0;  // max over problems of n + p (verify grid)
 };
 
 mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s,
                         const TcChoice *force, bool fp8) {
   Group groups[3] = {{kTcSplitBf16x3}, {kTcSplitBf16x6}, {kTcE4m3}};
-  int64_t rows = 0, scal = 0;
+  int64_t rows = 0, scal = 0, part = 0;
   for (int g = 0; g < count; g++) {
     const mm_problem &q = probs[g];
     if (q.n == 0 || q.p == 0) continue;
@@ -65,6 +66,13 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
     scal += q.n;
     sp.tB = reinterpret_cast<uint32_t *>((uintptr_t)scal);
     scal += q.p;
+    if (kind != kTcE4m3) {  // partial maxima of the unscaled pack
+      sp.pA = reinterpret_cast<uint32_t *>((uintptr_t)part);
+      part += (int64_t)sp.kt * q.n;
+      sp.pB = reinterpret_cast<uint32_t *>((uintptr_t)part);
+      part += (int64_t)sp.kt * q.p;
+      G.max_words = std::max<int64_t>(G.max_words, q.n + q.p);
+    }
     sp.tile_start = (int32_t)G.tiles;
     G.tiles += (int64_t)sp.mt * sp.nt;
     sp.pack_start = (int32_t)G.packs;
@@ -84,12 +92,14 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
   if (rows > 0x7fffffffLL) return MM_EINVAL;
   const size_t pack_bytes = (size_t)rows * kPackRowBytes;
   const size_t scal_off = (pack_bytes + 255) & ~(size_t)255;
-  const size_t tab_off = (scal_off + (size_t)scal * 4 + 255) & ~(size_t)255;
+  const size_t part_off = (scal_off + (size_t)scal * 4 + 255) & ~(size_t)255;
+  const size_t tab_off = (part_off + (size_t)part * 4 + 255) & ~(size_t)255;
   // item -> problem maps (tiles, pack tiles, reduction items) of each group
   // with more than one problem
   size_t map_ints = 0;
   for (auto &G : groups)
     if (G.tab.size() > 1) map_ints += (size_t)(G.tiles + G.packs + G.reds);
+  map_ints += ntab;  // per-problem scale flags (split kinds)
   const size_t map_off = (tab_off + ntab * sizeof(SplitProb) + 255) & ~(size_t)255;
   const size_t need = map_off + map_ints * sizeof(int);
   cudaError_t e = ws.reserve(need, s);
@@ -101,18 +111,25 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
     for (auto &sp : G.tab) {
       sp.sA = reinterpret_cast<uint32_t *>(base + scal_off) + (uintptr_t)sp.sA;
       sp.tB = reinterpret_cast<uint32_t *>(base + scal_off) + (uintptr_t)sp.tB;
+      if (G.kind != kTcE4m3) {
+        sp.pA = reinterpret_cast<uint32_t *>(base + part_off) + (uintptr_t)sp.pA;
+        sp.pB = reinterpret_cast<uint32_t *>(base + part_off) + (uintptr_t)sp.pB;
+      }
       all.push_back(sp);
     }
   SplitProb *d_tab = reinterpret_cast<SplitProb *>(base + tab_off);
   e = ws.stage.copy_to_device(d_tab, all.data(), all.size() * sizeof(SplitProb), s);
   if (e != cudaSuccess) return note_cuda(e);
   e = cudaMemsetAsync(base + scal_off, 0, (size_t)scal * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + map_off, 0, ntab * sizeof(int), s);  // flags
   if (e != cudaSuccess) return note_cuda(e);
   size_t off = 0;
-  int *maps = reinterpret_cast<int *>(base + map_off);
+  int *flags_all = reinterpret_cast<int *>(base + map_off);
+  int *maps = flags_all + ntab;
   for (auto &G : groups) {
     if (G.tab.empty()) continue;
     const SplitProb *dt = d_tab + off;
+    int *flags = flags_all + off;
     const int np = (int)G.tab.size();
     off += G.tab.size();
     int *tile_map = nullptr, *pack_map = nullptr, *red_map = nullptr;
@@ -124,12 +141,25 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
       e = launch_split_maps(dt, np, tile_map, pack_map, red_map, s);
       if (e != cudaSuccess) return note_cuda(e);
     }
-    e = launch_split_scale(dt, np, (int)G.reds, red_map, s);
-    if (e != cudaSuccess) return note_cuda(e);
-    e = G.kind == kTcE4m3 ? launch_fp8_pack(dt, np, (int)G.packs, pack_map, base, s)
-                          : launch_split_pack(G.kind, dt, np, (int)G.packs, pack_map, base, s);
-    if (e != cudaSuccess) return note_cuda(e);
-    e = launch_tc(G.kind, dt, np, (int)G.tiles, tile_map, base, rows, G.cfg, g_ctx.d_err, s);
+    if (G.kind == kTcE4m3) {
+      // e4m3 needs its scales before the conversion: reduce, then pack
+      e = launch_split_scale(dt, np, (int)G.reds, red_map, s);
+      if (e == cudaSuccess) e = launch_fp8_pack(dt, np, (int)G.packs, pack_map, base, s);
+      if (e == cudaSuccess)
+        e = launch_tc(G.kind, dt, np, (int)G.tiles, tile_map, nullptr, base, rows, G.cfg,
+                      g_ctx.d_err, s);
+    } else {
+      // split: one unscaled pass that also reduces the maxima, then the
+      // operands out of range are re-packed with their scales
+      e = launch_split_pack(G.kind, kPackUnscaled, dt, np, (int)G.packs, pack_map, nullptr, base,
+                            s);
+      if (e == cudaSuccess) e = launch_split_verify(dt, np, G.max_words, flags, s);
+      if (e == cudaSuccess)
+        e = launch_split_pack(G.kind, kPackFix, dt, np, (int)G.packs, pack_map, flags, base, s);
+      if (e == cudaSuccess)
+        e = launch_tc(G.kind, dt, np, (int)G.tiles, tile_map, flags, base, rows, G.cfg,
+                      g_ctx.d_err, s);
+    }
     if (e != cudaSuccess) return note_cuda(e);
   }
   return MM_OK;
@@ -173,38 +203,53 @@ mm_status run_split_chunked(Scratch &ws, int64_t n, int64_t m, int64_t p, const 
     rows += (int64_t)sp.mt * kt * parts * kTcBM;
     sp.sA = reinterpret_cast<uint32_t *>((uintptr_t)(p + r0));  // offsets, fixed below
     sp.tB = reinterpret_cast<uint32_t *>((uintptr_t)0);
+    // partial maxima: B's columns first (kt * p), then each slab's rows
+    sp.pA = reinterpret_cast<uint32_t *>((uintptr_t)((int64_t)kt * p + (int64_t)kt * r0));
+    sp.pB = reinterpret_cast<uint32_t *>((uintptr_t)0);
     sp.red_a = (int32_t)ceil_div(r1 - r0, 8);
     tiles[(size_t)c] = (int64_t)sp.mt * nt;
     // slab 0 also scales and packs B; the other slabs reuse its pack
     packs[(size_t)c] = (int64_t)sp.mt * kt + (c == 0 ? (int64_t)nt * kt : 0);
-    reds[(size_t)c] = sp.red_a + (c == 0 ? ceil_div(p, 32) * ceil_div(m, 256) : 0);
+    reds[(size_t)c] = 0;  // maxima are reduced by the unscaled pack
   }
   if (rows > 0x7fffffffLL) return MM_EINVAL;
   const size_t pack_bytes = (size_t)rows * kPackRowBytes;
   const size_t scal_off = (pack_bytes + 255) & ~(size_t)255;
-  const size_t tab_off = (scal_off + (size_t)(n + p) * 4 + 255) & ~(size_t)255;
-  cudaError_t e = ws.reserve(tab_off + tab.size() * sizeof(SplitProb), s);
+  const size_t part_off = (scal_off + (size_t)(n + p) * 4 + 255) & ~(size_t)255;
+  const size_t tab_off = (part_off + (size_t)kt * (n + p) * 4 + 255) & ~(size_t)255;
+  const size_t flag_off = (tab_off + tab.size() * sizeof(SplitProb) + 255) & ~(size_t)255;
+  cudaError_t e = ws.reserve(flag_off + tab.size() * sizeof(int), s);
   if (e != cudaSuccess) return note_cuda(e);
   uint8_t *base = static_cast<uint8_t *>(ws.ptr);
   uint32_t *scal = reinterpret_cast<uint32_t *>(base + scal_off);
+  uint32_t *part = reinterpret_cast<uint32_t *>(base + part_off);
   for (auto &sp : tab) {
     sp.sA = scal + (uintptr_t)sp.sA;
     sp.tB = scal + (uintptr_t)sp.tB;
+    sp.pA = part + (uintptr_t)sp.pA;
+    sp.pB = part + (uintptr_t)sp.pB;
   }
   SplitProb *d_tab = reinterpret_cast<SplitProb *>(base + tab_off);
   e = ws.stage.copy_to_device(d_tab, tab.data(), tab.size() * sizeof(SplitProb), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(scal, 0, (size_t)(n + p) * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + flag_off, 0, tab.size() * sizeof(int), s);
   if (e != cudaSuccess) return note_cuda(e);
   for (int c = 0; c < chunks; c++) {
     if (c == 0 && (e = cudaStreamWaitEvent(s, in_ready[0], 0)) != cudaSuccess) break;
     if ((e = cudaStreamWaitEvent(s, in_ready[c + 1], 0)) != cudaSuccess) break;
     const SplitProb *dt = d_tab + c;
-    if ((e = launch_split_scale(dt, 1, (int)reds[(size_t)c], nullptr, s)) != cudaSuccess) break;
-    if ((e = launch_split_pack(kind, dt, 1, (int)packs[(size_t)c], nullptr, base, s)) !=
-        cudaSuccess)
+    int *flag = reinterpret_cast<int *>(base + flag_off) + c;
+    // slab 0 packs (and reduces) B as well; a later slab's verify sees all of
+    // B's column maxima, so its B flag equals slab 0's
+    if ((e = launch_split_pack(kind, kPackUnscaled, dt, 1, (int)packs[(size_t)c], nullptr, nullptr,
+                               base, s)) != cudaSuccess)
       break;
-    if ((e = launch_tc(kind, dt, 1, (int)tiles[(size_t)c], nullptr, base, rows, cfg, g_ctx.d_err,
-                       s)) != cudaSuccess)
+    if ((e = launch_split_verify(dt, 1, tab[(size_t)c].n + p, flag, s)) != cudaSuccess) break;
+    if ((e = launch_split_pack(kind, kPackFix, dt, 1, (int)packs[(size_t)c], nullptr, flag, base,
+                               s)) != cudaSuccess)
+      break;
+    if ((e = launch_tc(kind, dt, 1, (int)tiles[(size_t)c], nullptr, flag, base, rows, cfg,
+                       g_ctx.d_err, s)) != cudaSuccess)
       break;
     if ((e = cudaEventRecord(out_ready[c], s)) != cudaSuccess) break;
   }
