@@ -91,6 +91,39 @@ def test_wide_exponent_rows(mmlib, mode):
     assert_full(C, A, B, "f32")
 
 
+def test_wide_exponent_columns_split(mmlib):
+    """Columns of B scaled by 2^-120 or 2^100 (A in range): the split path
+    re-packs B with its column scales and applies them in the epilogue."""
+    n, m, p = 150, 2500, 190
+    e = synth.row_scale_exponents(95, p)
+    A = synth.uniform_pm1(96, (n, m))
+    B = (synth.uniform_pm1(97, (m, p)).astype(np.float64) * np.ldexp(1.0, e)[None, :]).astype(np.float32)
+    C = run_gemm(mmlib, A, B, mmlib.MM_MODE_SPLIT_BF16X3)
+    assert_full(C, A, B, "f32")
+
+
+def test_grouped_mixed_scaling(mmlib):
+    """A grouped call where one problem needs row scales, one column scales and
+    the others none: each result equals its single call and the oracle."""
+    probs, host = [], []
+    for g in range(6):
+        n, m, p = 70 + 13 * g, 300 + 500 * g, 90 + 7 * g
+        A = synth.uniform_pm1(1600 + g, (n, m))
+        B = synth.uniform_pm1(1610 + g, (m, p))
+        if g == 1:
+            A = (A.astype(np.float64) * np.ldexp(1.0, synth.row_scale_exponents(1620, n))[:, None]).astype(np.float32)
+        if g == 4:
+            B = (B.astype(np.float64) * np.ldexp(1.0, synth.row_scale_exponents(1621, p))[None, :]).astype(np.float32)
+        probs.append((n, m, p, dev(A), dev(B), torch.full((n, p), float("nan"), device="cuda")))
+        host.append((A, B))
+    assert mmlib.mm_gemm_grouped(probs, mmlib.MM_F32, mmlib.MM_MODE_SPLIT_BF16X3) == 0
+    for (n, m, p, dA, dB, C), (A, B) in zip(probs, host):
+        assert_full(C.cpu().numpy(), A, B, "f32")
+        C1 = torch.full_like(C, float("nan"))
+        assert mmlib.mm_gemm(n, m, p, dA, dB, C1, mmlib.MM_F32, mmlib.MM_MODE_SPLIT_BF16X3) == 0
+        assert torch.equal(C, C1)
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_empty_and_zero_inner(mmlib, mode):
     f64 = mode == "dgemm"
