@@ -508,8 +508,9 @@ def run_mine(args):
     stream = torch.cuda.Stream()
     mode = {"split": mm.MM_MODE_SPLIT_BF16X3, "simt": mm.MM_MODE_SIMT}[args.mode]
 
-    def step(md=mode, a=A, b=B, c=C, dt=mm.MM_F32):
-        st = mm.mm_gemm_async(n, n, n, a, b, c, dt, md, stream)
+    def step(md=mode, a=A, b=B, c=C, dt=mm.MM_F32, sz=None):
+        sz = n if sz is None else sz
+        st = mm.mm_gemm_async(sz, sz, sz, a, b, c, dt, md, stream)
         if st != mm.MM_OK:
             raise mm.MMError(st, "mm_gemm_async")
 
@@ -610,6 +611,16 @@ def run_mine(args):
         mm.check_status(mm.mm_sync(stream), "split")
         extra["split_check"] = gpu_check(mm, n, n, n, A, B, C, mm.MM_F32)
         extra["tolerance_f32"] = 1e-6 * n ** 0.5
+        # the other square sizes of the workload (device time, same stream)
+        sizes = {}
+        for sz in (1024, 2048, 4096):
+            a, b, c = A[:sz, :sz].contiguous(), B[:sz, :sz].contiguous(), C.view(-1)[:sz * sz]
+            reps = 20
+            ms_z, _ = timed(lambda: step(mode, a, b, c, sz=sz), reps, 3)
+            ms_y, _ = timed(lambda: step(mm.MM_MODE_SIMT, a, b, c, sz=sz), 5, 1)
+            sizes[str(sz)] = {"split_tflops": 2.0 * sz ** 3 / (ms_z / reps * 1e-3) / 1e12,
+                              "simt_tflops": 2.0 * sz ** 3 / (ms_y / 5 * 1e-3) / 1e12}
+        extra["square_sizes"] = sizes
         line["paths"] = extra
         line["paper_workloads_4096"] = bench_paper_workloads(mm, stream, peaks)
         line["grouped"] = bench_grouped(mm, stream, max(3, args.steps // 20))

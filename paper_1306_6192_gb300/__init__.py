@@ -136,8 +136,14 @@ def mm_strerror(st: int) -> str:
     return lib().mm_strerror(int(st)).decode()
 
 
+# Tuning table measured on GB300 (tune_gb300.py); loaded unless another is given.
+DEFAULT_TUNE_TABLE = os.path.join(HERE, "tune_gb300.txt")
+
+
 def mm_init(hbm_budget_bytes: int = 0, n_streams: int = 0, tune_table: str | None = None,
             check: int = 0, device: int = -1, max_batch: int = 0) -> int:
+    if tune_table is None and os.path.exists(DEFAULT_TUNE_TABLE):
+        tune_table = DEFAULT_TUNE_TABLE
     o = mm_opts(hbm_budget_bytes, n_streams, tune_table.encode() if tune_table else None,
                 check, device, max_batch)
     return lib().mm_init(ctypes.byref(o))
