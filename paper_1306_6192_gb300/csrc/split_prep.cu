@@ -14,7 +14,9 @@
 //   split_scale_kernel  max |a_ir| per row of A (a warp per row) and
 //                       max |b_rj| per column of B (strips of 32 columns x
 //                       256 rows, atomicMax on the float bit pattern, which
-//                       orders like the value for non-negative floats).
+//                       orders like the value for non-negative floats); used
+//                       by the e4m3 path, whose conversion needs the scales
+//                       first.
 //   split_pack_kernel   one block per 128 x 64 tile of A or bn x 64 tile of
 //                       B^T: scale, split, write the bf16 parts (hi, lo - or
 //                       hi, mid, lo for the three-part split) of the pack
@@ -327,7 +329,8 @@ split_maps_kernel(const SplitProb *__restrict__ probs, int *__restrict__ tile_ma
                                   ((pr.m + kRowChunk - 1) / kRowChunk);
   for (int i = threadIdx.x; i < tiles; i += blockDim.x) tile_map[pr.tile_start + i] = g;
   for (int i = threadIdx.x; i < packs; i += blockDim.x) pack_map[pr.pack_start + i] = g;
-  for (int i = threadIdx.x; i < reds; i += blockDim.x) red_map[pr.red_start + i] = g;
+  if (red_map)  // only tables that run split_scale_kernel (the e4m3 path)
+    for (int i = threadIdx.x; i < reds; i += blockDim.x) red_map[pr.red_start + i] = g;
 }
 
 }  // namespace

@@ -77,9 +77,11 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
     G.tiles += (int64_t)sp.mt * sp.nt;
     sp.pack_start = (int32_t)G.packs;
     G.packs += (int64_t)sp.mt * sp.kt + (int64_t)sp.nt * sp.kt;
-    sp.red_start = (int32_t)G.reds;
-    sp.red_a = (int32_t)ceil_div(q.n, 8);
-    G.reds += sp.red_a + ceil_div(q.p, 32) * ceil_div(q.m, 256);
+    if (kind == kTcE4m3) {  // the e4m3 path reduces its maxima in a separate pass
+      sp.red_start = (int32_t)G.reds;
+      sp.red_a = (int32_t)ceil_div(q.n, 8);
+      G.reds += sp.red_a + ceil_div(q.p, 32) * ceil_div(q.m, 256);
+    }
     G.tab.push_back(sp);
   }
   size_t ntab = 0;
@@ -136,8 +138,8 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
     if (np > 1) {
       tile_map = maps;
       pack_map = tile_map + G.tiles;
-      red_map = pack_map + G.packs;
-      maps = red_map + G.reds;
+      red_map = G.reds > 0 ? pack_map + G.packs : nullptr;
+      maps = pack_map + G.packs + G.reds;
       e = launch_split_maps(dt, np, tile_map, pack_map, red_map, s);
       if (e != cudaSuccess) return note_cuda(e);
     }
@@ -182,7 +184,7 @@ mm_status run_split_chunked(Scratch &ws, int64_t n, int64_t m, int64_t p, const 
   // layout: B pack, then each slab's A pack; scale words: B columns, then A rows
   int64_t rows = (int64_t)nt * kt * parts * ch.bn;
   std::vector<SplitProb> tab((size_t)chunks);
-  std::vector<int64_t> tiles((size_t)chunks), packs((size_t)chunks), reds((size_t)chunks);
+  std::vector<int64_t> tiles((size_t)chunks), packs((size_t)chunks);
   for (int c = 0; c < chunks; c++) {
     const int64_t r0 = row0[c], r1 = row0[c + 1];
     SplitProb &sp = tab[(size_t)c];
@@ -210,7 +212,6 @@ mm_status run_split_chunked(Scratch &ws, int64_t n, int64_t m, int64_t p, const 
     tiles[(size_t)c] = (int64_t)sp.mt * nt;
     // slab 0 also scales and packs B; the other slabs reuse its pack
     packs[(size_t)c] = (int64_t)sp.mt * kt + (c == 0 ? (int64_t)nt * kt : 0);
-    reds[(size_t)c] = 0;  // maxima are reduced by the unscaled pack
   }
   if (rows > 0x7fffffffLL) return MM_EINVAL;
   const size_t pack_bytes = (size_t)rows * kPackRowBytes;
