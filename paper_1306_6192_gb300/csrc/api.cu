@@ -335,7 +335,10 @@ mm_status mm_init(const mm_opts *opts) {
   for (int c = 0; c <= Ctx::kMaxChunks && ok; c++)
     ok = cudaEventCreateWithFlags(&g_ctx.ev_in[c], cudaEventDisableTiming) == cudaSuccess;
   for (int c = 0; c < Ctx::kMaxChunks && ok; c++)
-    ok = cudaEventCreateWithFlags(&g_ctx.ev_out[c], cudaEventDisableTiming) == cudaSuccess;
+    ok = cudaEventCreateWithFlags(&g_ctx.ev_out[c], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&g_ctx.ev_prep[c], cudaEventDisableTiming) == cudaSuccess;
+  for (auto &ts : g_ctx.tc_streams)
+    ok = ok && cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) == cudaSuccess;
   if (!ok) return MM_ECUDA;
   cudaMemset(g_ctx.d_err, 0, 256);
   tune_reset_defaults();
@@ -376,6 +379,10 @@ mm_status mm_shutdown(void) {
     if (ev) cudaEventDestroy(ev), ev = nullptr;
   for (auto &ev : g_ctx.ev_out)
     if (ev) cudaEventDestroy(ev), ev = nullptr;
+  for (auto &ev : g_ctx.ev_prep)
+    if (ev) cudaEventDestroy(ev), ev = nullptr;
+  for (auto &ts : g_ctx.tc_streams)
+    if (ts) cudaStreamDestroy(ts), ts = nullptr;
   if (g_ctx.h2d) cudaStreamDestroy(g_ctx.h2d);
   if (g_ctx.d2h) cudaStreamDestroy(g_ctx.d2h);
   g_ctx.h2d = g_ctx.d2h = nullptr;

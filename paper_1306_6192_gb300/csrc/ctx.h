@@ -57,8 +57,10 @@ struct Ctx {
   Scratch cplx_ws;       // real/imaginary planes and partial products (mm_cgemm)
   // host-operand pipeline of mm_gemm: copy streams and per-chunk events
   cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaStream_t tc_streams[2] = {};  // slab GEMMs alternate between these
   static constexpr int kMaxChunks = 8;
   cudaEvent_t ev_in[kMaxChunks + 1] = {};
+  cudaEvent_t ev_prep[kMaxChunks] = {};
   cudaEvent_t ev_out[kMaxChunks] = {};
 };
 

@@ -101,8 +101,10 @@ cudaError_t launch_split_pack(TcKind kind, int mode, const SplitProb *d_probs, i
                               void *pack_base, cudaStream_t s);
 // After an unscaled pack: reduces the partial maxima into sA / tB and sets
 // flags[g] (zeroed by the caller).  max_words = max over problems of n + p.
+// write_cols = false leaves tB as it is (a later slab sharing B's words,
+// which another stream may be reading) but still flags B.
 cudaError_t launch_split_verify(const SplitProb *d_probs, int nprobs, int64_t max_words,
-                                int *flags, cudaStream_t s);
+                                int *flags, cudaStream_t s, bool write_cols = true);
 cudaError_t launch_fp8_pack(const SplitProb *d_probs, int nprobs,
                             int total_tiles, const int *map, void *pack_base,
                             cudaStream_t s);

@@ -283,7 +283,8 @@ __device__ __forceinline__ bool needs_scale(uint32_t max_bits) {
 // flags[g] |= kFlagScaleA / kFlagScaleB where a maximum is outside the range
 // packed unscaled.
 __global__ void __launch_bounds__(256)
-split_verify_kernel(const SplitProb *__restrict__ probs, int nprobs, int *__restrict__ flags) {
+split_verify_kernel(const SplitProb *__restrict__ probs, int nprobs, int *__restrict__ flags,
+                    bool write_cols) {
   __shared__ uint32_t part[8][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int g = blockIdx.y; g < nprobs; g += gridDim.y) {
@@ -304,7 +305,7 @@ split_verify_kernel(const SplitProb *__restrict__ probs, int nprobs, int *__rest
     if (warp == 0 && valid) {
 #pragma unroll
       for (int q = 1; q < 8; q++) mx = umax(mx, part[q][lane]);
-      if (is_row) pr.sA[w] = mx; else pr.tB[w - pr.n] = mx;
+      if (is_row) pr.sA[w] = mx; else if (write_cols) pr.tB[w - pr.n] = mx;
       if (needs_scale(mx)) bad = is_row ? kFlagScaleA : kFlagScaleB;
     }
     const int any = __syncthreads_or(bad);
@@ -366,11 +367,11 @@ cudaError_t launch_split_pack(TcKind kind, int mode, const SplitProb *d_probs, i
 }
 
 cudaError_t launch_split_verify(const SplitProb *d_probs, int nprobs, int64_t max_words,
-                                int *flags, cudaStream_t s) {
+                                int *flags, cudaStream_t s, bool write_cols) {
   if (nprobs <= 0 || max_words <= 0) return cudaSuccess;
   TraceScope ts("split_verify", s);
   dim3 grid((unsigned)((max_words + 31) / 32), (unsigned)(nprobs < 65535 ? nprobs : 65535));
-  split_verify_kernel<<<grid, 256, 0, s>>>(d_probs, nprobs, flags);
+  split_verify_kernel<<<grid, 256, 0, s>>>(d_probs, nprobs, flags, write_cols);
   return cudaGetLastError();
 }
 

@@ -235,25 +235,35 @@ mm_status run_split_chunked(Scratch &ws, int64_t n, int64_t m, int64_t p, const 
   if (e == cudaSuccess) e = cudaMemsetAsync(scal, 0, (size_t)(n + p) * 4, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(base + flag_off, 0, tab.size() * sizeof(int), s);
   if (e != cudaSuccess) return note_cuda(e);
+  // Preparation of the slabs runs in order on s; each slab's tensor-core
+  // launch goes to one of two streams, so the next slab's preparation and
+  // GEMM fill the last partial wave of the previous one.
   for (int c = 0; c < chunks; c++) {
     if (c == 0 && (e = cudaStreamWaitEvent(s, in_ready[0], 0)) != cudaSuccess) break;
     if ((e = cudaStreamWaitEvent(s, in_ready[c + 1], 0)) != cudaSuccess) break;
     const SplitProb *dt = d_tab + c;
     int *flag = reinterpret_cast<int *>(base + flag_off) + c;
     // slab 0 packs (and reduces) B as well; a later slab's verify sees all of
-    // B's column maxima, so its B flag equals slab 0's
+    // B's column maxima, so its B flag equals slab 0's, and it leaves B's
+    // column words (read by the GEMMs in flight) untouched
     if ((e = launch_split_pack(kind, kPackUnscaled, dt, 1, (int)packs[(size_t)c], nullptr, nullptr,
                                base, s)) != cudaSuccess)
       break;
-    if ((e = launch_split_verify(dt, 1, tab[(size_t)c].n + p, flag, s)) != cudaSuccess) break;
+    if ((e = launch_split_verify(dt, 1, tab[(size_t)c].n + p, flag, s, c == 0)) != cudaSuccess)
+      break;
     if ((e = launch_split_pack(kind, kPackFix, dt, 1, (int)packs[(size_t)c], nullptr, flag, base,
                                s)) != cudaSuccess)
       break;
+    if ((e = cudaEventRecord(g_ctx.ev_prep[c], s)) != cudaSuccess) break;
+    cudaStream_t t = g_ctx.tc_streams[c & 1];
+    if ((e = cudaStreamWaitEvent(t, g_ctx.ev_prep[c], 0)) != cudaSuccess) break;
     if ((e = launch_tc(kind, dt, 1, (int)tiles[(size_t)c], nullptr, flag, base, rows, cfg,
-                       g_ctx.d_err, s)) != cudaSuccess)
+                       g_ctx.d_err, t)) != cudaSuccess)
       break;
-    if ((e = cudaEventRecord(out_ready[c], s)) != cudaSuccess) break;
+    if ((e = cudaEventRecord(out_ready[c], t)) != cudaSuccess) break;
   }
+  // s waits for every slab's GEMM: the caller's later work on s is ordered
+  for (int c = 0; c < chunks && e == cudaSuccess; c++) e = cudaStreamWaitEvent(s, out_ready[c], 0);
   return note_cuda(e);
 }
 
