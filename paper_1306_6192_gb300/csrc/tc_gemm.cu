@@ -84,12 +84,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Waits for the phase with the given parity.  Returns false when the time
-// limit passes (the error flag is then set to `code`) or, if `watch_err`,
-// when another role has already set the flag.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, int code,
-                                       bool watch_err, uint64_t limit_ns) {
-  if (mbar_try_wait(bar, parity)) return true;
+// Slow path of mbar_wait, out of line so that the pipeline loops stay short.
+__device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, int *err, int code,
+                                            bool watch_err, uint64_t limit_ns) {
   const uint64_t t0 = globaltimer_ns();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
@@ -101,6 +98,15 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, 
       }
     }
   }
+}
+
+// Waits for the phase with the given parity.  Returns false when the time
+// limit passes (the error flag is then set to `code`) or, if `watch_err`,
+// when another role has already set the flag.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, int code,
+                                          bool watch_err, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  return mbar_wait_slow(bar, parity, err, code, watch_err, limit_ns);
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
@@ -315,9 +321,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
                    : "memory");
       int stage = 0;
       uint32_t phase = 0;
-      int armed[STAGES];
-      uint32_t armed_parity[STAGES];
-      for (int s = 0; s < STAGES; s++) armed[s] = 0, armed_parity[s] = 0;
+      uint32_t issued = 0;  // stage loads armed so far
       bool ok = true;
       for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
         const TileCoord tc = decode_tile(probs, nprobs, tile_map, t);
@@ -331,8 +335,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
             break;
           }
           mbar_arrive_expect_tx(full_bar(stage), bytes);
-          armed[stage] = 1;
-          armed_parity[stage] = phase;
+          ++issued;
           const int kb = (ki * BKB) / kPackRowBytes;
           const int x = (ki * BKB) % kPackRowBytes;  // byte offset in the pack row
           const int64_t arow = pr.a_row0 + ((int64_t)tc.mt * pr.kt + kb) * (L::kParts * kTcBM);
@@ -355,9 +358,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
         }
       }
       if (!ok) {
-        // drain copies still in flight before the CTA's shared memory goes away
-        for (int s = 0; s < STAGES; s++)
-          if (armed[s]) mbar_wait(full_bar(s), armed_parity[s], err, 1, false, kDrainLimitNs);
+        // drain copies still in flight before the CTA's shared memory goes
+        // away: the last STAGES loads armed, one per stage, load j in stage
+        // j % STAGES with parity (j / STAGES) & 1
+        for (uint32_t j = issued > STAGES ? issued - STAGES : 0; j < issued; j++)
+          mbar_wait(full_bar((int)(j % STAGES)), (j / STAGES) & 1u, err, 1, false, kDrainLimitNs);
       }
     }
   } else if (warp == 1) {
