@@ -202,6 +202,17 @@ mm_status mm_tune_load(const char *path);
 mm_status mm_tune_query(int64_t n, int64_t m, int64_t p, int *bn, int *bk,
                         int *stages, int *group_m);
 
+/* Tail split the split path would use for one product n x m x p (mm_gemm,
+ * or a grouped call holding only this product) on the current device:
+ * *tiles = number of 128 x bn output tiles; tiles *split_from .. *tiles - 1,
+ * the last, partly filled wave of the persistent grid, each run as *split_s
+ * parts along K whose FP32 partial tiles the part finishing last adds in part
+ * order (*split_s = 1, *split_from = *tiles: no split).  Grouped calls of
+ * several products and the allocation-free entry point do not split.
+ * Needs mm_init (the SM count); any pointer may be NULL. */
+mm_status mm_tune_query_tail(int64_t n, int64_t m, int64_t p, int *tiles,
+                             int *split_from, int *split_s);
+
 /* ----------------------------------------------------------------- tracing */
 
 /* When enabled, every kernel the library launches is bracketed by CUDA events
@@ -262,7 +273,10 @@ mm_status mm_diag(int64_t n, int64_t p, const void *X, const void *d, void *C,
  * A (n x m), B (m x p), C (n x p): device pointers, FP32, row-major and dense
  * as in mm_gemm.  stream: a cudaStream_t (NULL: the legacy default stream);
  * the call returns when C is written.  Same kernels and tile choices as
- * mm_gemm's split path, hence the same results.
+ * mm_gemm's split path, without its tail split (mm_tune_query_tail): where
+ * mm_gemm splits tiles along K the two results differ only in the rounding
+ * of that one extra addition, within the split path's tolerance; elsewhere
+ * they are identical.
  * Every call uses the same array, which keeps the previous call's contents
  * (the call clears what must start at zero): calls whose work overlaps on the
  * GPU - on different streams or from different host threads - race and

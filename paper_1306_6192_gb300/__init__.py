@@ -78,6 +78,7 @@ def lib():
         L.mm_tune_save.argtypes = [ctypes.c_char_p]
         L.mm_tune_load.argtypes = [ctypes.c_char_p]
         L.mm_tune_query.argtypes = [_i64, _i64, _i64] + [ctypes.POINTER(ctypes.c_int)] * 4
+        L.mm_tune_query_tail.argtypes = [_i64, _i64, _i64] + [ctypes.POINTER(ctypes.c_int)] * 3
         L.mm_trace_enable.argtypes = [ctypes.c_int]
         L.mm_trace_reset.argtypes = []
         L.mm_trace_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(_i64), _dp]
@@ -93,7 +94,8 @@ def lib():
         for name in ("mm_init", "mm_shutdown", "mm_gemm", "mm_gemm_async", "mm_gemm_grouped",
                      "mm_gemm_grouped_async", "mm_sync", "mm_check", "mm_submit", "mm_poll",
                      "mm_wait", "mm_serve_stats", "mm_tune", "mm_tune_save", "mm_tune_load",
-                     "mm_tune_query", "mm_trace_enable", "mm_trace_reset", "mm_trace_read"):
+                     "mm_tune_query", "mm_tune_query_tail", "mm_trace_enable",
+                     "mm_trace_reset", "mm_trace_read"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         atexit.register(_shutdown_at_exit)
@@ -241,6 +243,14 @@ def mm_tune_query(n, m, p):
     """Returns (status, bn, bk, stages, group_m)."""
     v = [ctypes.c_int(0) for _ in range(4)]
     st = lib().mm_tune_query(n, m, p, *[ctypes.byref(x) for x in v])
+    return (st,) + tuple(x.value for x in v)
+
+
+def mm_tune_query_tail(n, m, p):
+    """Returns (status, tiles, split_from, split_s) of the split path's tail
+    split for one n x m x p product."""
+    v = [ctypes.c_int(0) for _ in range(3)]
+    st = lib().mm_tune_query_tail(n, m, p, *[ctypes.byref(x) for x in v])
     return (st,) + tuple(x.value for x in v)
 
 

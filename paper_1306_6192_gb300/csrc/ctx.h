@@ -39,6 +39,7 @@ struct TcChoice {
   int stages;   // pipeline depth for that bk
   int group_m;  // raster band height in row tiles
   int grid;     // persistent CTAs (0 = one per SM)
+  int tail = 1; // 1: split the last wave's tiles along K where the plan gains
 };
 
 struct Ctx {
@@ -99,6 +100,10 @@ mm_status run_split(Scratch &ws, const mm_problem *probs, int count, cudaStream_
 mm_status run_split_chunked(Scratch &ws, int64_t n, int64_t m, int64_t p, const float *A,
                             const float *B, float *C, int chunks, const int64_t *row0,
                             cudaStream_t s, cudaEvent_t *in_ready, cudaEvent_t *out_ready);
+// Tail split one product gets from its own shape (see tc_tail_plan), and the
+// scratch bytes of its partial tiles and counters.
+TcTail product_tail(int64_t n, int64_t m, int64_t p, TcKind kind, int64_t *tiles_out);
+size_t tail_scratch_bytes(int64_t n, int64_t m, int64_t p, TcKind kind);
 // FP8 path (report-only accuracy).
 mm_status run_fp8(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s);
 // Grouped dispatch: split / SIMT / DGEMM tables in one launch per path.

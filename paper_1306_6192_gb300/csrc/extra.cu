@@ -51,48 +51,102 @@ add_kernel(const T *__restrict__ a, const T *__restrict__ b, T *__restrict__ c, 
   }
 }
 
+// The 16-byte kernels below keep kEwUnroll vectors of each operand in
+// flight per thread (loads first, then the stores), with streaming cache
+// hints: every byte is touched once, so nothing is worth keeping in L2.
+constexpr int kEwUnroll = 4;
+
 // 16-byte variant for aligned float operands
 __global__ void __launch_bounds__(256)
 add4_kernel(const float4 *__restrict__ a, const float4 *__restrict__ b, float4 *__restrict__ c,
             float alpha, float beta, int64_t count4, bool unit) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count4;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float4 x = a[i], y = b[i];
-    float4 r;
-    if (unit) {
-      r = make_float4(x.x + beta * y.x, x.y + beta * y.y, x.z + beta * y.z, x.w + beta * y.w);
-    } else {
-      r = make_float4(fmaf(alpha, x.x, beta * y.x), fmaf(alpha, x.y, beta * y.y),
-                      fmaf(alpha, x.z, beta * y.z), fmaf(alpha, x.w, beta * y.w));
+  auto op = [&](const float4 &x, const float4 &y) {
+    if (unit)
+      return make_float4(x.x + beta * y.x, x.y + beta * y.y, x.z + beta * y.z, x.w + beta * y.w);
+    return make_float4(fmaf(alpha, x.x, beta * y.x), fmaf(alpha, x.y, beta * y.y),
+                       fmaf(alpha, x.z, beta * y.z), fmaf(alpha, x.w, beta * y.w));
+  };
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + (kEwUnroll - 1) * stride < count4; i += kEwUnroll * stride) {
+    float4 x[kEwUnroll], y[kEwUnroll];
+#pragma unroll
+    for (int u = 0; u < kEwUnroll; u++) {
+      x[u] = __ldcs(a + i + u * stride);
+      y[u] = __ldcs(b + i + u * stride);
     }
-    c[i] = r;
+#pragma unroll
+    for (int u = 0; u < kEwUnroll; u++) __stcs(c + i + u * stride, op(x[u], y[u]));
   }
+  for (; i < count4; i += stride) __stcs(c + i, op(__ldcs(a + i), __ldcs(b + i)));
 }
 
 // side 0: C[i][j] = X[i][j] * d[j];  side 1: C[i][j] = d[i] * X[i][j].
-// Blocks stride over rows (y) and column chunks (x); VEC: 4 columns per
-// thread with 16-byte accesses (aligned float operands, p % 4 == 0).
-template <typename T, bool VEC>
+// Scalar form: blocks stride over rows (y) and column chunks (x).
+template <typename T>
 __global__ void __launch_bounds__(256)
 diag_kernel(const T *__restrict__ x, const T *__restrict__ d, T *__restrict__ c, int64_t n,
             int64_t p, int side) {
-  constexpr int W = VEC ? 4 : 1;
   for (int64_t r = blockIdx.y; r < n; r += gridDim.y) {
     const T dr = side == 1 ? d[r] : T(0);
-    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * W; j < p;
-         j += (int64_t)gridDim.x * blockDim.x * W) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
+         j += (int64_t)gridDim.x * blockDim.x) {
       const int64_t i = r * p + j;
-      if (VEC) {
-        const float4 v = *reinterpret_cast<const float4 *>(x + i);
-        const float4 s4 = side == 0 ? *reinterpret_cast<const float4 *>(d + j)
-                                    : make_float4(dr, dr, dr, dr);
-        *reinterpret_cast<float4 *>(c + i) =
-            make_float4(v.x * s4.x, v.y * s4.y, v.z * s4.z, v.w * s4.w);
-      } else {
-        c[i] = x[i] * (side == 0 ? d[j] : dr);
-      }
+      c[i] = x[i] * (side == 0 ? d[j] : dr);
     }
   }
+}
+
+// 16-byte form for aligned float operands with p % 4 == 0: a flat grid-
+// stride loop over the n * p4 vectors (p4 = p / 4); each thread tracks the
+// (row, vector column) of its position and advances it by the stride's
+// quotient and remainder, so no division runs in the loop.
+__global__ void __launch_bounds__(256)
+diag4_kernel(const float4 *__restrict__ x, const float *__restrict__ d, float4 *__restrict__ c,
+             int64_t n, int64_t p4, int side) {
+  const int64_t count4 = n * p4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t s_row = stride / p4, s_col = stride % p4;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t r = i / p4, j = i % p4;
+  auto advance = [&](int64_t &rr, int64_t &jj) {
+    rr += s_row;
+    jj += s_col;
+    if (jj >= p4) {
+      jj -= p4;
+      rr++;
+    }
+  };
+  auto scale = [&](const float4 &v, int64_t rr, int64_t jj) {
+    const float4 s4 = side == 0 ? __ldg(reinterpret_cast<const float4 *>(d) + jj)
+                                : make_float4(d[rr], d[rr], d[rr], d[rr]);
+    return make_float4(v.x * s4.x, v.y * s4.y, v.z * s4.z, v.w * s4.w);
+  };
+  for (; i + (kEwUnroll - 1) * stride < count4; i += kEwUnroll * stride) {
+    float4 v[kEwUnroll];
+    int64_t rs[kEwUnroll], js[kEwUnroll];
+#pragma unroll
+    for (int u = 0; u < kEwUnroll; u++) {
+      v[u] = __ldcs(x + i + u * stride);
+      rs[u] = r;
+      js[u] = j;
+      advance(r, j);
+    }
+#pragma unroll
+    for (int u = 0; u < kEwUnroll; u++) __stcs(c + i + u * stride, scale(v[u], rs[u], js[u]));
+  }
+  for (; i < count4; i += stride) {
+    __stcs(c + i, scale(__ldcs(x + i), r, j));
+    advance(r, j);
+  }
+}
+
+// Persistent grid for the 16-byte kernels: full occupancy (8 blocks of 256
+// threads per SM), fewer when the vectors run out.
+int grid_ew(int64_t count4) {
+  const int64_t want = (count4 + 256 * kEwUnroll - 1) / (256 * kEwUnroll);
+  const int64_t cap = (int64_t)sm_count() * 8;
+  return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
 int grid_for(int64_t count) {
@@ -176,7 +230,7 @@ mm_status mm_add(int64_t n, int64_t p, double alpha, const void *A, double beta,
     const bool vec = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) |
                        reinterpret_cast<uintptr_t>(C)) & 15) == 0 && count % 4 == 0;
     if (vec)
-      add4_kernel<<<grid_for(count / 4), 256, 0, s>>>(
+      add4_kernel<<<grid_ew(count / 4), 256, 0, s>>>(
           static_cast<const float4 *>(A), static_cast<const float4 *>(B), static_cast<float4 *>(C),
           (float)alpha, (float)beta, count / 4, unit);
     else
@@ -204,27 +258,24 @@ mm_status mm_diag(int64_t n, int64_t p, const void *X, const void *d, void *C, i
     return MM_EINVAL;
   std::lock_guard<std::mutex> lk(g_api_mutex);
   cudaStream_t s = g_ctx.stream;
-  const int64_t count = n * p;
-  (void)count;
   const bool vec = dt == MM_F32 && p % 4 == 0 &&
                    ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(d) |
                      reinterpret_cast<uintptr_t>(C)) & 15) == 0;
-  const int64_t per_row = vec ? p / 4 : p;
-  dim3 grid((unsigned)std::min<int64_t>((per_row + 255) / 256, 64),
+  dim3 grid((unsigned)std::min<int64_t>((p + 255) / 256, 64),
             (unsigned)std::min<int64_t>(n, 65535));
   TraceScope ts("diag", s);
-  if (dt == MM_F32 && vec)
-    diag_kernel<float, true><<<grid, 256, 0, s>>>(static_cast<const float *>(X),
-                                                  static_cast<const float *>(d),
-                                                  static_cast<float *>(C), n, p, side);
+  if (vec)
+    diag4_kernel<<<grid_ew(n * (p / 4)), 256, 0, s>>>(static_cast<const float4 *>(X),
+                                                      static_cast<const float *>(d),
+                                                      static_cast<float4 *>(C), n, p / 4, side);
   else if (dt == MM_F32)
-    diag_kernel<float, false><<<grid, 256, 0, s>>>(static_cast<const float *>(X),
-                                                   static_cast<const float *>(d),
-                                                   static_cast<float *>(C), n, p, side);
+    diag_kernel<float><<<grid, 256, 0, s>>>(static_cast<const float *>(X),
+                                            static_cast<const float *>(d),
+                                            static_cast<float *>(C), n, p, side);
   else
-    diag_kernel<double, false><<<grid, 256, 0, s>>>(static_cast<const double *>(X),
-                                                    static_cast<const double *>(d),
-                                                    static_cast<double *>(C), n, p, side);
+    diag_kernel<double><<<grid, 256, 0, s>>>(static_cast<const double *>(X),
+                                             static_cast<const double *>(d),
+                                             static_cast<double *>(C), n, p, side);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return note_cuda(e);
   return check_device_flag(s);

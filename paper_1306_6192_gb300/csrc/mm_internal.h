@@ -49,6 +49,14 @@ constexpr int kPackK = 64;  // bf16 elements per pack row
 // Entries outside A or B are zero.  sA[i] / tB[j] hold the bit pattern of
 // max_r |a_ir| / max_r |b_rj|; each path derives its power-of-two scale
 // exponent of a row/column from it.
+// Tail split (a property of the product's own shape, see tc_tail_plan): its
+// tiles split_from .. mt*nt-1 in raster order run as split_s parts along K
+// (part h: pack rows [h*kt/split_s, (h+1)*kt/split_s)); part h of split tile
+// t writes its FP32 partial tile to part + ((t - split_from)*split_s + h) *
+// 128*bn ([column][row] order) and counts itself in cnt[t - split_from]
+// (zero before the launch); the last part adds the parts in order 0, 1, ...
+// The tensor-core kernel's work units of the product: split_from whole tiles,
+// then the parts; unit_start is their prefix over the problems of a table.
 struct SplitProb {
   const float *A;
   const float *B;
@@ -61,11 +69,21 @@ struct SplitProb {
   int32_t n, m, p;
   int32_t mt, nt, kt;      // ceil(n/128), ceil(p/bn), ceil(m/pack_k)
   int32_t bn, group_m;     // N tile (64, 128 or 256), raster band height
-  int32_t tile_start;      // prefix over problems of mt*nt (MMA tiles)
+  int32_t unit_start;      // prefix over problems of tensor-core work units
   int32_t pack_start;      // prefix of pack tiles: mt*kt + nt*kt
   int32_t red_start;       // prefix of scale-reduction items
   int32_t red_a;           // reduction items for A rows: ceil(n/8)
+  int32_t split_from;      // tail split (split_s <= 1: none; then split_from
+  int32_t split_s;         //   is ignored and every tile is one unit)
+  float *part;             // partial tiles of the split tiles
+  int *cnt;                // parts finished per split tile
 };
+
+// Work units of a product with its tail split: whole tiles, then the parts.
+__host__ __device__ inline int64_t split_units(const SplitProb &sp) {
+  const int64_t tiles = (int64_t)sp.mt * sp.nt;
+  return sp.split_s > 1 ? sp.split_from + (tiles - sp.split_from) * sp.split_s : tiles;
+}
 
 // One product of the grouped SIMT path (f32 or f64 elements).
 struct SimtProb {
@@ -89,7 +107,7 @@ cudaError_t launch_simt_grouped(bool f64, const SimtProb *d_probs, int nprobs,
 // e4m3 conversion into the packs.
 // `map` arguments: item -> problem index arrays written by
 // launch_split_maps for tables of several problems, or nullptr.
-cudaError_t launch_split_maps(const SplitProb *d_probs, int nprobs, int *tile_map,
+cudaError_t launch_split_maps(const SplitProb *d_probs, int nprobs, int *unit_map,
                               int *pack_map, int *red_map, cudaStream_t s);
 cudaError_t launch_split_scale(const SplitProb *d_probs, int nprobs,
                                int total_items, const int *map, cudaStream_t s);
@@ -109,16 +127,31 @@ cudaError_t launch_fp8_pack(const SplitProb *d_probs, int nprobs,
                             int total_tiles, const int *map, void *pack_base,
                             cudaStream_t s);
 
-// Tensor-core mainloop + epilogue over all tiles of all problems.
+// Tensor-core mainloop + epilogue over all work units of all problems.
 struct TcConfig {
   int bkb;      // bytes of K per pipeline stage and pack row: 64 or 128
   int stages;   // pipeline depth
   int grid;     // persistent CTAs (<= number of SMs; 0 = one per SM)
 };
+int tc_grid(const TcConfig &cfg);
+// Tail-split plan of one product from its own shape only (so that a product
+// gets the same split, hence the same bits, alone and in any grouped table):
+// `tiles` output tiles of 128 x bn, kt pack rows of K, the kind's bf16 (or
+// e4m3) products per K step, on `grid` persistent CTAs.  The makespan model
+// of the product run alone decides; a product that fills less than one wave
+// and has fewer than 32 pack rows is never split (grouped tables of many
+// small products gain nothing from it).
+struct TcTail {
+  int split_from, split_s;
+};
+TcTail tc_tail_plan(int64_t tiles, int grid, int kt, int bn, int64_t m, double products);
+// Scratch of a plan: partial tiles (256-byte aligned), then the counters.
+size_t tc_tail_bytes(const TcTail &t, int64_t tiles, int bn);
+size_t tc_tail_part_bytes(const TcTail &t, int64_t tiles, int bn);
 // flags: per-problem kFlagScaleA / kFlagScaleB (nullptr: both operands were
 // packed scaled).
 cudaError_t launch_tc(TcKind kind, const SplitProb *d_probs, int nprobs,
-                      int total_tiles, const int *tile_map, const int *flags,
+                      int total_units, const int *unit_map, const int *flags,
                       void *pack_base, int64_t pack_rows, const TcConfig &cfg,
                       int *d_err, cudaStream_t s);
 

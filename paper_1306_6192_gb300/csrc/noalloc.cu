@@ -126,7 +126,7 @@ mm_status mm_gemm_split_static(int64_t n, int64_t m, int64_t p, const float *A, 
   sp.tB = sp.sA + n;
   sp.pA = reinterpret_cast<uint32_t *>(base + part_off);
   sp.pB = sp.pA + (int64_t)sp.kt * n;
-  sp.tile_start = 0;
+  sp.unit_start = 0;  // no tail split: split_s = 0 from the memset
   sp.pack_start = 0;
   sp.red_start = 0;
   sp.red_a = (int32_t)ceil_div(n, 8);

@@ -114,6 +114,7 @@ size_t request_bytes(const mm_problem &q, mm_dtype dt, mm_mode mode) {
     b += (size_t)kPackRowBytes * pack_parts(kind) * kb *
          ((size_t)ceil_div(q.n, kTcBM) * kTcBM + (size_t)ceil_div(q.p, c.bn) * c.bn);
     b += 4 * (size_t)(q.n + q.p) + sizeof(SplitProb);
+    b += tail_scratch_bytes(q.n, q.m, q.p, kind);  // partial tiles of a tail split
   }
   return b;
 }

@@ -320,15 +320,15 @@ split_verify_kernel(const SplitProb *__restrict__ probs, int nprobs, int *__rest
 // One block per problem: writes the problem's index over its ranges of MMA
 // tiles, pack tiles and scale-reduction items.
 __global__ void __launch_bounds__(256)
-split_maps_kernel(const SplitProb *__restrict__ probs, int *__restrict__ tile_map,
+split_maps_kernel(const SplitProb *__restrict__ probs, int *__restrict__ unit_map,
                   int *__restrict__ pack_map, int *__restrict__ red_map) {
   const int g = blockIdx.x;
   const SplitProb &pr = probs[g];
-  const int tiles = pr.mt * pr.nt;
+  const int units = (int)split_units(pr);
   const int packs = pr.mt * pr.kt + pr.nt * pr.kt;
   const int reds = pr.red_a + ((pr.p + kColStrip - 1) / kColStrip) *
                                   ((pr.m + kRowChunk - 1) / kRowChunk);
-  for (int i = threadIdx.x; i < tiles; i += blockDim.x) tile_map[pr.tile_start + i] = g;
+  for (int i = threadIdx.x; i < units; i += blockDim.x) unit_map[pr.unit_start + i] = g;
   for (int i = threadIdx.x; i < packs; i += blockDim.x) pack_map[pr.pack_start + i] = g;
   if (red_map)  // only tables that run split_scale_kernel (the e4m3 path)
     for (int i = threadIdx.x; i < reds; i += blockDim.x) red_map[pr.red_start + i] = g;
@@ -336,11 +336,11 @@ split_maps_kernel(const SplitProb *__restrict__ probs, int *__restrict__ tile_ma
 
 }  // namespace
 
-cudaError_t launch_split_maps(const SplitProb *d_probs, int nprobs, int *tile_map, int *pack_map,
+cudaError_t launch_split_maps(const SplitProb *d_probs, int nprobs, int *unit_map, int *pack_map,
                               int *red_map, cudaStream_t s) {
   if (nprobs <= 0) return cudaSuccess;
   TraceScope ts("split_maps", s);
-  split_maps_kernel<<<nprobs, 256, 0, s>>>(d_probs, tile_map, pack_map, red_map);
+  split_maps_kernel<<<nprobs, 256, 0, s>>>(d_probs, unit_map, pack_map, red_map);
   return cudaGetLastError();
 }
 

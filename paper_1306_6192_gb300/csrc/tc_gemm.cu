@@ -28,6 +28,15 @@
 // overlap the mainloop of the next.  Tiles of all problems of a table are
 // visited in a static stride over the CTAs, grouped in bands of group_m row
 // tiles for L2 reuse.
+// Tail split: where a product's tile count leaves the last wave of the
+// persistent grid partly empty, the host cuts that product's last tiles into
+// split_s parts along K (a plan fixed by the product's own shape, so a
+// product gets the same bits alone and in any table).  Each part is a work
+// unit of its own; its epilogue writes the FP32 partial tile to scratch and
+// counts itself on the tile's counter, and the part that arrives last adds
+// the parts in the fixed order 0..split_s-1 (its own from TMEM) before the
+// usual unscaling and store, so the result does not depend on which part
+// finishes first.  No CTA waits for another.
 //
 // Every mbarrier wait is bounded (kWaitLimitNs); on expiry a device flag is
 // set, the other roles stop at their next wait, in-flight copies and MMAs
@@ -45,6 +54,7 @@ constexpr int kMaxBN = 256;
 constexpr int kAccCols = 256;               // TMEM columns per accumulator
 constexpr uint32_t kTmemCols = 2 * kAccCols;
 constexpr int kBoxRows = 128;               // TMA box height (rows of the pack)
+constexpr int kMaxSplit = 4;                // most K parts of a tail-split tile
 constexpr uint64_t kWaitLimitNs = 4000000000ull;
 constexpr uint64_t kDrainLimitNs = 200000000ull;
 
@@ -240,22 +250,50 @@ __device__ __forceinline__ int kind_exponent(uint32_t max_bits) {
   return (f > 0.0f && f <= 3.402823466e38f) ? e - 7 : 0;
 }
 
-struct TileCoord {
-  int g, mt, nt;
+// Work unit u of a table: problem g, output tile (mt, nt) = local tile t of
+// the problem in raster order (bands of group_m row tiles), and part h of a
+// tile split along K (h = -1: the whole tile).
+struct UnitCoord {
+  int g, mt, nt, t, h;
 };
 
-__device__ __forceinline__ TileCoord decode_tile(const SplitProb *__restrict__ probs, int nprobs,
-                                                 const int *__restrict__ map, int t) {
+__device__ __forceinline__ UnitCoord decode_unit(const SplitProb *__restrict__ probs, int nprobs,
+                                                 const int *__restrict__ map, int u) {
   const int g =
-      find_problem(probs, nprobs, map, t, [](const SplitProb &q) { return q.tile_start; });
+      find_problem(probs, nprobs, map, u, [](const SplitProb &q) { return q.unit_start; });
   const SplitProb &pr = probs[g];
-  const int local = t - pr.tile_start;
+  int t = u - pr.unit_start, h = -1;
+  if (pr.split_s > 1 && t >= pr.split_from) {
+    const int v = t - pr.split_from;
+    t = pr.split_from + v / pr.split_s;
+    h = v % pr.split_s;
+  }
   const int gm = pr.group_m;
   const int band = gm * pr.nt;
-  const int first = (local / band) * gm;
+  const int first = (t / band) * gm;
   const int rows = min(pr.mt - first, gm);
-  const int in = local % band;
-  return TileCoord{g, first + in % rows, in / rows};
+  const int in = t % band;
+  return UnitCoord{g, first + in % rows, in / rows, t, h};
+}
+
+// Pipeline stages [k0, k1) of a unit: all kiters of a whole tile; for part h
+// the stages of pack rows [h*kt/S, (h+1)*kt/S), so the split points do not
+// depend on the stage depth BKB.
+template <int BKB>
+__device__ __forceinline__ void unit_krange(const SplitProb &pr, int h, int kiters, int &k0,
+                                            int &k1) {
+  if (h < 0) {
+    k0 = 0;
+    k1 = kiters;
+    return;
+  }
+  constexpr int kStagesPerRow = kPackRowBytes / BKB;
+  k0 = (int)((int64_t)h * pr.kt / pr.split_s) * kStagesPerRow;
+  k1 = min((int)((int64_t)(h + 1) * pr.kt / pr.split_s) * kStagesPerRow, kiters);
+}
+
+__device__ __forceinline__ void epilogue_sync() {
+  asm volatile("bar.sync 1, 128;" ::: "memory");
 }
 
 template <int BKB, int STAGES, int KIND>
@@ -268,14 +306,15 @@ struct TcLayout {
   static constexpr int kBarOffset = STAGES * kStageBytes;
   static constexpr int kNumBars = 2 * STAGES + 4 + 1;  // full, empty, acc_full/empty, drain
   static constexpr int kColExpOffset = kBarOffset + kNumBars * 8 + 16;  // int[2][kMaxBN]
-  static constexpr int kSmemBytes = kColExpOffset + 2 * kMaxBN * 4 + 1024;  // + align slack
+  static constexpr int kLastOffset = kColExpOffset + 2 * kMaxBN * 4;   // int: last-part flag
+  static constexpr int kSmemBytes = kLastOffset + 16 + 1024;          // + align slack
 };
 
 template <int BKB, int STAGES, int KIND>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__restrict__ probs,
-               int nprobs, const int *__restrict__ tile_map, const int *__restrict__ flags,
-               int total_tiles, int *err) {
+               int nprobs, const int *__restrict__ unit_map, const int *__restrict__ flags,
+               int total_units, int *err) {
   using L = TcLayout<BKB, STAGES, KIND>;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -289,6 +328,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
   const uint32_t drain_bar = bars + 8u * (2 * STAGES + 4);
   uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(smem + L::kBarOffset + L::kNumBars * 8);
   int *colexp = reinterpret_cast<int *>(smem + L::kColExpOffset);  // [2][kMaxBN]
+  volatile int *last_flag = reinterpret_cast<volatile int *>(smem + L::kLastOffset);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -323,13 +363,15 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
       uint32_t phase = 0;
       uint32_t issued = 0;  // stage loads armed so far
       bool ok = true;
-      for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
-        const TileCoord tc = decode_tile(probs, nprobs, tile_map, t);
+      for (int u = blockIdx.x; u < total_units && ok; u += gridDim.x) {
+        const UnitCoord tc = decode_unit(probs, nprobs, unit_map, u);
         const SplitProb &pr = probs[tc.g];
         const int bn = pr.bn;
         const int kiters = (int)(((int64_t)pr.m * L::kElemBytes + BKB - 1) / BKB);
         const uint32_t bytes = (uint32_t)(L::kParts * (kTcBM + bn) * BKB);
-        for (int ki = 0; ki < kiters; ki++) {
+        int k0, k1;
+        unit_krange<BKB>(pr, tc.h, kiters, k0, k1);
+        for (int ki = k0; ki < k1; ki++) {
           if (!mbar_wait(empty_bar(stage), phase ^ 1u, err, 1, true, kWaitLimitNs)) {
             ok = false;
             break;
@@ -373,10 +415,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
       int acc = 0;
       uint32_t acc_phase = 0;
       bool ok = true, issued = false;
-      for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
-        const TileCoord tc = decode_tile(probs, nprobs, tile_map, t);
+      for (int u = blockIdx.x; u < total_units && ok; u += gridDim.x) {
+        const UnitCoord tc = decode_unit(probs, nprobs, unit_map, u);
         const SplitProb &pr = probs[tc.g];
         const int kiters = (int)(((int64_t)pr.m * L::kElemBytes + BKB - 1) / BKB);
+        int k0, k1;
+        unit_krange<BKB>(pr, tc.h, kiters, k0, k1);
         const uint32_t idesc = make_idesc<KIND>(pr.bn);
         const uint32_t blo = (uint32_t)pr.bn * BKB;
         if (!mbar_wait(acce_bar(acc), acc_phase ^ 1u, err, 2, true, kWaitLimitNs)) {
@@ -385,7 +429,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
         }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * kAccCols);
-        for (int ki = 0; ki < kiters; ki++) {
+        for (int ki = k0; ki < k1; ki++) {
           if (!mbar_wait(full_bar(stage), phase, err, 3, true, kWaitLimitNs)) {
             ok = false;
             break;
@@ -399,7 +443,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
           for (int kk = 0; kk < BKB / 32; kk++) {
             // 32 bytes of K per instruction: 16 bf16 or 32 e4m3
             const uint64_t adv = (uint64_t)(kk * 32) >> 4;
-            const uint32_t acc_in = (ki | kk) != 0 ? 1u : 0u;
+            const uint32_t acc_in = (ki != k0 || kk != 0) ? 1u : 0u;
             if (KIND == kTcSplitBf16x3) {
               const uint64_t a1 = kmajor_desc<BKB>(st + L::kAPart);
               const uint64_t b1 = kmajor_desc<BKB>(sb + blo);
@@ -450,8 +494,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
     int acc = 0;
     uint32_t acc_phase = 0;
     const int et = threadIdx.x - 64;  // 0..127 over the epilogue warps
-    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
-      const TileCoord tc = decode_tile(probs, nprobs, tile_map, t);
+    for (int u = blockIdx.x; u < total_units; u += gridDim.x) {
+      const UnitCoord tc = decode_unit(probs, nprobs, unit_map, u);
       const SplitProb &pr = probs[tc.g];
       // column exponents of this tile, once per tile, while the MMAs run
       // operands packed without scaling (flags) take exponent 0
@@ -470,11 +514,83 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
       float *crow = pr.C + (row_ok ? i : 0) * (int64_t)pr.p;
       const bool vec = ((reinterpret_cast<uintptr_t>(pr.C) & 15u) == 0) && ((pr.p & 3) == 0);
       const uint32_t tacc = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kAccCols);
-      for (int c = 0; c < pr.bn; c += 32) {
+      // part of a split tile: a partial slot holds bn/4 groups of 4 columns,
+      // each group 128 rows x 4 floats, so that a warp's 16-byte accesses to
+      // one group (32 rows) are 512 consecutive bytes
+      const size_t slot_floats = (size_t)kTcBM * pr.bn;
+      const int split_s = pr.split_s;
+      const int st = tc.t - pr.split_from;  // index among the split tiles
+      const float4 *slots = tc.h >= 0 ? reinterpret_cast<const float4 *>(
+                                            pr.part + (size_t)st * split_s * slot_floats) + row
+                                      : nullptr;
+      bool store = true;
+      if (tc.h >= 0) {
+        float4 *mine = reinterpret_cast<float4 *>(
+                           pr.part + ((size_t)st * split_s + tc.h) * slot_floats) + row;
+        for (int c = 0; c < pr.bn; c += 32) {
+          uint32_t v[32];
+          __syncwarp();
+          tmem_ld_32x32b_x32(tacc + (uint32_t)c, v);
+          tmem_ld_wait();
+#pragma unroll
+          for (int e = 0; e < 32; e += 4)
+            __stcg(mine + (size_t)((c + e) >> 2) * kTcBM,
+                   make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]),
+                               __uint_as_float(v[e + 2]), __uint_as_float(v[e + 3])));
+        }
+        __threadfence();
+        epilogue_sync();  // every row of this part written and fenced
+        if (et == 0) *last_flag = atomicAdd(pr.cnt + st, 1) == split_s - 1;
+        epilogue_sync();
+        store = *last_flag != 0;
+        if (store) {
+          __threadfence();
+          if (et == 0) pr.cnt[st] = 0;  // ready for the next launch
+        }
+      }
+      for (int c = 0; c < pr.bn && store; c += 32) {
         uint32_t v[32];
         __syncwarp();  // tcgen05.ld is warp-collective: reconverge first
         tmem_ld_32x32b_x32(tacc + (uint32_t)c, v);
         tmem_ld_wait();
+        if (tc.h >= 0) {
+          // sum of the parts in order 0..split_s-1 (this part's from TMEM);
+          // the loads of all other parts of the chunk are issued first
+          float4 x[kMaxSplit][8];
+#pragma unroll
+          for (int hh = 0; hh < kMaxSplit; hh++) {
+            if (hh < split_s && hh != tc.h) {
+              const float4 *src = slots + (size_t)hh * (slot_floats / 4) + (size_t)(c >> 2) * kTcBM;
+#pragma unroll
+              for (int e = 0; e < 8; e++) x[hh][e] = __ldcg(src + (size_t)e * kTcBM);
+            }
+          }
+#pragma unroll
+          for (int e = 0; e < 8; e++) {
+            float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int hh = 0; hh < kMaxSplit; hh++) {
+              if (hh >= split_s) break;
+              const float4 y = hh == tc.h ? make_float4(__uint_as_float(v[4 * e]),
+                                                        __uint_as_float(v[4 * e + 1]),
+                                                        __uint_as_float(v[4 * e + 2]),
+                                                        __uint_as_float(v[4 * e + 3]))
+                                          : x[hh][e];
+              if (hh == 0) {
+                sum = y;
+              } else {
+                sum.x += y.x;
+                sum.y += y.y;
+                sum.z += y.z;
+                sum.w += y.w;
+              }
+            }
+            v[4 * e] = __float_as_uint(sum.x);
+            v[4 * e + 1] = __float_as_uint(sum.y);
+            v[4 * e + 2] = __float_as_uint(sum.z);
+            v[4 * e + 3] = __float_as_uint(sum.w);
+          }
+        }
         const int64_t j0 = (int64_t)tc.nt * pr.bn + c;
         if (!row_ok || j0 >= pr.p) continue;
         const int *ce = cexp + c;
@@ -543,8 +659,8 @@ cudaError_t encode_pack_map(CUtensorMap *map, void *base, int64_t rows, int bkb)
 }
 
 template <int BKB, int STAGES, int KIND>
-cudaError_t launch_tc_t(const SplitProb *d_probs, int nprobs, const int *tile_map,
-                        const int *flags, int total_tiles, void *pack_base, int64_t pack_rows,
+cudaError_t launch_tc_t(const SplitProb *d_probs, int nprobs, const int *unit_map,
+                        const int *flags, int total_units, void *pack_base, int64_t pack_rows,
                         int grid, int *d_err, cudaStream_t s) {
   using L = TcLayout<BKB, STAGES, KIND>;
   static_assert(L::kSmemBytes <= 232448, "shared memory budget");
@@ -561,39 +677,84 @@ cudaError_t launch_tc_t(const SplitProb *d_probs, int nprobs, const int *tile_ma
   cudaError_t e = encode_pack_map(&map, pack_base, pack_rows, BKB);
   if (e != cudaSuccess) return e;
   TraceScope ts(KIND == kTcE4m3 ? "fp8_tc" : "split_tc", s);
-  tc_gemm_kernel<BKB, STAGES, KIND><<<grid, kThreads, L::kSmemBytes, s>>>(map, d_probs, nprobs,
-                                                                         tile_map, flags,
-                                                                         total_tiles, d_err);
+  tc_gemm_kernel<BKB, STAGES, KIND><<<grid, kThreads, L::kSmemBytes, s>>>(
+      map, d_probs, nprobs, unit_map, flags, total_units, d_err);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_tc(TcKind kind, const SplitProb *d_probs, int nprobs, int total_tiles,
-                      const int *tile_map, const int *flags, void *pack_base, int64_t pack_rows,
-                      const TcConfig &cfg, int *d_err, cudaStream_t s) {
-  if (total_tiles <= 0) return cudaSuccess;
-  if (pack_rows <= 0 || pack_rows > 0x7fffffffLL) return cudaErrorInvalidValue;
-  int grid = cfg.grid > 0 ? cfg.grid : sm_count();
-  if (grid > total_tiles) grid = total_tiles;
-  const int *mp = tile_map;
-  if (kind == kTcE4m3)
-    return launch_tc_t<128, 4, kTcE4m3>(d_probs, nprobs, mp, flags, total_tiles, pack_base, pack_rows,
-                                        grid, d_err, s);
-  if (kind == kTcSplitBf16x6)
-    return launch_tc_t<64, 3, kTcSplitBf16x6>(d_probs, nprobs, mp, flags, total_tiles, pack_base,
-                                              pack_rows, grid, d_err, s);
-  if (cfg.bkb == 128)
-    return launch_tc_t<128, 2, kTcSplitBf16x3>(d_probs, nprobs, mp, flags, total_tiles, pack_base,
-                                               pack_rows, grid, d_err, s);
-  if (cfg.bkb == 64) {
-    if (cfg.stages == 3)
-      return launch_tc_t<64, 3, kTcSplitBf16x3>(d_probs, nprobs, mp, flags, total_tiles, pack_base,
-                                                pack_rows, grid, d_err, s);
-    return launch_tc_t<64, 4, kTcSplitBf16x3>(d_probs, nprobs, mp, flags, total_tiles, pack_base,
-                                              pack_rows, grid, d_err, s);
+int tc_grid(const TcConfig &cfg) { return cfg.grid > 0 ? cfg.grid : sm_count(); }
+
+TcTail tc_tail_plan(int64_t tiles, int grid, int kt, int bn, int64_t m, double products) {
+  TcTail best{(int)tiles, 1};
+  if (tiles <= 0 || grid <= 1 || kt < 4) return best;
+  const int64_t G = grid;
+  if (tiles < G && kt < 32) return best;  // small products: grouped tables hold many
+  // units c, c + G, c + 2G, ... below x go to CTA c
+  auto upto = [G](int64_t x, int64_t c) -> int64_t { return x > c ? (x - c + G - 1) / G : 0; };
+  // per-unit overhead of a part, in tiles: the pipeline refill (~2 us)
+  // against a tile's time at the per-SM tensor rate (~12.8 TFLOP/s of bf16
+  // products); the part that finishes a tile writes its partial and reads
+  // the others, latency-bound while the other SMs load L2 (~40 GB/s per SM
+  // measured for this pattern on GB300)
+  const double tile_us = 2.0 * kTcBM * bn * (double)m * products / 12.8e6;
+  const double eps = 0.01 + 2.0 / tile_us;
+  const double slot_us = (double)kTcBM * bn * 4.0 / 40e3;
+  auto makespan = [&](int64_t F, int S) {
+    const int64_t U = F + (tiles - F) * S;
+    double worst = 0.0;
+    for (int64_t c = 0; c < G; c++) {
+      const double cost =
+          (double)upto(F, c) + (double)(upto(U, c) - upto(F, c)) * (1.0 / S + eps);
+      worst = cost > worst ? cost : worst;
+    }
+    return S > 1 ? worst + S * slot_us / tile_us : worst;
+  };
+  double best_cost = makespan(tiles, 1);
+  const int64_t rem = tiles % G;
+  for (int64_t R : {rem, rem + G}) {
+    if (R <= 0 || R > tiles) continue;
+    for (int S = 2; S <= kMaxSplit && R * S <= 2 * G && kt / S >= 2; S++) {
+      const double c = makespan(tiles - R, S);
+      if (c < best_cost - 1e-9) {
+        best_cost = c;
+        best = TcTail{(int)(tiles - R), S};
+      }
+    }
   }
-  return cudaErrorInvalidValue;
+  return best;
+}
+
+size_t tc_tail_part_bytes(const TcTail &t, int64_t tiles, int bn) {
+  if (t.split_s <= 1) return 0;
+  const int64_t R = tiles - t.split_from;
+  return ((size_t)R * t.split_s * kTcBM * bn * sizeof(float) + 255) & ~(size_t)255;
+}
+
+size_t tc_tail_bytes(const TcTail &t, int64_t tiles, int bn) {
+  if (t.split_s <= 1) return 0;
+  const int64_t R = tiles - t.split_from;
+  return tc_tail_part_bytes(t, tiles, bn) + (((size_t)R * sizeof(int) + 255) & ~(size_t)255);
+}
+
+cudaError_t launch_tc(TcKind kind, const SplitProb *d_probs, int nprobs, int total_units,
+                      const int *unit_map, const int *flags, void *pack_base, int64_t pack_rows,
+                      const TcConfig &cfg, int *d_err, cudaStream_t s) {
+  if (total_units <= 0) return cudaSuccess;
+  if (pack_rows <= 0 || pack_rows > 0x7fffffffLL) return cudaErrorInvalidValue;
+  int grid = tc_grid(cfg);
+  if (grid > total_units) grid = total_units;
+  const int *mp = unit_map;
+#define MM_TC_ARGS d_probs, nprobs, mp, flags, total_units, pack_base, pack_rows, grid, d_err, s
+  cudaError_t e = cudaErrorInvalidValue;
+  if (kind == kTcE4m3) e = launch_tc_t<128, 4, kTcE4m3>(MM_TC_ARGS);
+  else if (kind == kTcSplitBf16x6) e = launch_tc_t<64, 3, kTcSplitBf16x6>(MM_TC_ARGS);
+  else if (cfg.bkb == 128) e = launch_tc_t<128, 2, kTcSplitBf16x3>(MM_TC_ARGS);
+  else if (cfg.bkb == 64 && cfg.stages == 3) e = launch_tc_t<64, 3, kTcSplitBf16x3>(MM_TC_ARGS);
+  else if (cfg.bkb == 64) e = launch_tc_t<64, 4, kTcSplitBf16x3>(MM_TC_ARGS);
+#undef MM_TC_ARGS
+  return e;
 }
 
 }  // namespace mm

@@ -19,14 +19,31 @@ struct Group {
   TcKind kind;
   TcConfig cfg{0, 0, 0};
   std::vector<SplitProb> tab;
-  int64_t tiles = 0, packs = 0, reds = 0;
+  int64_t units = 0, packs = 0, reds = 0;  // tensor-core work units, pack tiles, reductions
   int64_t max_words = 0;  // max over problems of n + p (verify grid)
 };
+
+double kind_products(TcKind k) {
+  return k == kTcSplitBf16x3 ? 3.0 : (k == kTcSplitBf16x6 ? 6.0 : 0.5);
+}
+
+// Tail split of one product from its own shape and tile choice; fills
+// split_from / split_s and returns the plan.
+TcTail plan_tail(SplitProb &sp, TcKind kind, const TcChoice &ch) {
+  const TcConfig cfg{0, 0, ch.grid};
+  TcTail t = ch.tail ? tc_tail_plan((int64_t)sp.mt * sp.nt, tc_grid(cfg), sp.kt, sp.bn, sp.m,
+                                    kind_products(kind))
+                     : TcTail{sp.mt * sp.nt, 1};
+  sp.split_from = t.split_from;
+  sp.split_s = t.split_s;
+  return t;
+}
 
 mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s,
                         const TcChoice *force, bool fp8) {
   Group groups[3] = {{kTcSplitBf16x3}, {kTcSplitBf16x6}, {kTcE4m3}};
   int64_t rows = 0, scal = 0, part = 0;
+  size_t tail_parts = 0, tail_cnts = 0;  // partial tiles and counters of tail splits
   for (int g = 0; g < count; g++) {
     const mm_problem &q = probs[g];
     if (q.n == 0 || q.p == 0) continue;
@@ -73,8 +90,15 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
       part += (int64_t)sp.kt * q.p;
       G.max_words = std::max<int64_t>(G.max_words, q.n + q.p);
     }
-    sp.tile_start = (int32_t)G.tiles;
-    G.tiles += (int64_t)sp.mt * sp.nt;
+    const TcTail tail = plan_tail(sp, kind, ch);
+    if (tail.split_s > 1) {  // offsets, fixed below
+      sp.part = reinterpret_cast<float *>((uintptr_t)tail_parts);
+      sp.cnt = reinterpret_cast<int *>((uintptr_t)tail_cnts);
+      tail_parts += tc_tail_part_bytes(tail, (int64_t)sp.mt * sp.nt, sp.bn);
+      tail_cnts += (size_t)((int64_t)sp.mt * sp.nt - tail.split_from);
+    }
+    sp.unit_start = (int32_t)G.units;
+    G.units += split_units(sp);
     sp.pack_start = (int32_t)G.packs;
     G.packs += (int64_t)sp.mt * sp.kt + (int64_t)sp.nt * sp.kt;
     if (kind == kTcE4m3) {  // the e4m3 path reduces its maxima in a separate pass
@@ -86,7 +110,7 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
   }
   size_t ntab = 0;
   for (auto &G : groups) {
-    if (G.tiles > 0x7fffffffLL || G.packs > 0x7fffffffLL || G.reds > 0x7fffffffLL)
+    if (G.units > 0x7fffffffLL || G.packs > 0x7fffffffLL || G.reds > 0x7fffffffLL)
       return MM_EINVAL;
     ntab += G.tab.size();
   }
@@ -100,10 +124,12 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
   // with more than one problem
   size_t map_ints = 0;
   for (auto &G : groups)
-    if (G.tab.size() > 1) map_ints += (size_t)(G.tiles + G.packs + G.reds);
+    if (G.tab.size() > 1) map_ints += (size_t)(G.units + G.packs + G.reds);
   map_ints += ntab;  // per-problem scale flags (split kinds)
   const size_t map_off = (tab_off + ntab * sizeof(SplitProb) + 255) & ~(size_t)255;
-  const size_t need = map_off + map_ints * sizeof(int);
+  const size_t tpart_off = (map_off + map_ints * sizeof(int) + 255) & ~(size_t)255;
+  const size_t tcnt_off = tpart_off + tail_parts;  // tail_parts is a multiple of 256
+  const size_t need = tcnt_off + tail_cnts * sizeof(int);
   cudaError_t e = ws.reserve(need, s);
   if (e != cudaSuccess) return note_cuda(e);
   uint8_t *base = static_cast<uint8_t *>(ws.ptr);
@@ -117,6 +143,10 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
         sp.pA = reinterpret_cast<uint32_t *>(base + part_off) + (uintptr_t)sp.pA;
         sp.pB = reinterpret_cast<uint32_t *>(base + part_off) + (uintptr_t)sp.pB;
       }
+      if (sp.split_s > 1) {
+        sp.part = reinterpret_cast<float *>(base + tpart_off + (uintptr_t)sp.part);
+        sp.cnt = reinterpret_cast<int *>(base + tcnt_off) + (uintptr_t)sp.cnt;
+      }
       all.push_back(sp);
     }
   SplitProb *d_tab = reinterpret_cast<SplitProb *>(base + tab_off);
@@ -124,6 +154,8 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
   if (e != cudaSuccess) return note_cuda(e);
   e = cudaMemsetAsync(base + scal_off, 0, (size_t)scal * 4, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(base + map_off, 0, ntab * sizeof(int), s);  // flags
+  if (e == cudaSuccess && tail_cnts > 0)
+    e = cudaMemsetAsync(base + tcnt_off, 0, tail_cnts * sizeof(int), s);
   if (e != cudaSuccess) return note_cuda(e);
   size_t off = 0;
   int *flags_all = reinterpret_cast<int *>(base + map_off);
@@ -137,7 +169,7 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
     int *tile_map = nullptr, *pack_map = nullptr, *red_map = nullptr;
     if (np > 1) {
       tile_map = maps;
-      pack_map = tile_map + G.tiles;
+      pack_map = tile_map + G.units;
       red_map = G.reds > 0 ? pack_map + G.packs : nullptr;
       maps = pack_map + G.packs + G.reds;
       e = launch_split_maps(dt, np, tile_map, pack_map, red_map, s);
@@ -148,7 +180,7 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
       e = launch_split_scale(dt, np, (int)G.reds, red_map, s);
       if (e == cudaSuccess) e = launch_fp8_pack(dt, np, (int)G.packs, pack_map, base, s);
       if (e == cudaSuccess)
-        e = launch_tc(G.kind, dt, np, (int)G.tiles, tile_map, nullptr, base, rows, G.cfg,
+        e = launch_tc(G.kind, dt, np, (int)G.units, tile_map, nullptr, base, rows, G.cfg,
                       g_ctx.d_err, s);
     } else {
       // split: one unscaled pass that also reduces the maxima, then the
@@ -159,7 +191,7 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
       if (e == cudaSuccess)
         e = launch_split_pack(G.kind, kPackFix, dt, np, (int)G.packs, pack_map, flags, base, s);
       if (e == cudaSuccess)
-        e = launch_tc(G.kind, dt, np, (int)G.tiles, tile_map, flags, base, rows, G.cfg,
+        e = launch_tc(G.kind, dt, np, (int)G.units, tile_map, flags, base, rows, G.cfg,
                       g_ctx.d_err, s);
     }
     if (e != cudaSuccess) return note_cuda(e);
@@ -209,6 +241,10 @@ mm_status run_split_chunked(Scratch &ws, int64_t n, int64_t m, int64_t p, const 
     sp.pA = reinterpret_cast<uint32_t *>((uintptr_t)((int64_t)kt * p + (int64_t)kt * r0));
     sp.pB = reinterpret_cast<uint32_t *>((uintptr_t)0);
     sp.red_a = (int32_t)ceil_div(r1 - r0, 8);
+    // slabs are not tail-split: each slab's last wave is filled by the next
+    // slab's GEMM on the other tensor-core stream
+    sp.split_s = 1;
+    sp.unit_start = 0;
     tiles[(size_t)c] = (int64_t)sp.mt * nt;
     // slab 0 also scales and packs B; the other slabs reuse its pack
     packs[(size_t)c] = (int64_t)sp.mt * kt + (c == 0 ? (int64_t)nt * kt : 0);
@@ -277,3 +313,51 @@ mm_status run_fp8(Scratch &ws, const mm_problem *probs, int count, cudaStream_t 
 }
 
 }  // namespace mm
+
+namespace mm {
+
+TcTail product_tail(int64_t n, int64_t m, int64_t p, TcKind kind, int64_t *tiles_out) {
+  TcChoice ch = tune_choose(n, m, p);
+  ch.bn = tc_bn(kind, ch.bn);
+  SplitProb sp;
+  std::memset(&sp, 0, sizeof(sp));
+  sp.n = (int32_t)n;
+  sp.m = (int32_t)m;
+  sp.p = (int32_t)p;
+  sp.bn = ch.bn;
+  sp.mt = (int32_t)ceil_div(n, kTcBM);
+  sp.nt = (int32_t)ceil_div(p, ch.bn);
+  sp.kt = (int32_t)ceil_div(m, pack_k(kind));
+  if (tiles_out) *tiles_out = (int64_t)sp.mt * sp.nt;
+  return plan_tail(sp, kind, ch);
+}
+
+size_t tail_scratch_bytes(int64_t n, int64_t m, int64_t p, TcKind kind) {
+  if (n <= 0 || m <= 0 || p <= 0) return 0;
+  int64_t tiles = 0;
+  const TcTail t = product_tail(n, m, p, kind, &tiles);
+  TcChoice ch = tune_choose(n, m, p);
+  return tc_tail_bytes(t, tiles, tc_bn(kind, ch.bn));
+}
+
+}  // namespace mm
+
+using namespace mm;
+
+extern "C" mm_status mm_tune_query_tail(int64_t n, int64_t m, int64_t p, int *tiles,
+                                        int *split_from, int *split_s) {
+  if (!g_ctx.inited) return MM_ENOTINIT;
+  if (n < 0 || m < 0 || p < 0) return MM_EINVAL;
+  int64_t t = 0;
+  TcTail tail{0, 1};
+  if (n > 0 && m > 0 && p > 0) {
+    const TcKind kind = split_kind_for(m);
+    tail = product_tail(n, m, p, kind, &t);
+    if (t > 0x7fffffffLL) return MM_EINVAL;
+  }
+  if (tail.split_s <= 1) tail = TcTail{(int)t, 1};
+  if (tiles) *tiles = (int)t;
+  if (split_from) *split_from = tail.split_from;
+  if (split_s) *split_s = tail.split_s;
+  return MM_OK;
+}

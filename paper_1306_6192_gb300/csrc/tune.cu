@@ -3,7 +3,9 @@
 // grid size, chosen per size bucket by timing the candidates on the device.
 // Buckets are (ceil(log2 n), ceil(log2 m), ceil(log2 p)) clamped to [5, 16].
 // The table persists as text, one bucket per line:
-//   ln lm lp bn bk stages group_m grid
+//   ln lm lp bn bk stages group_m grid [tail]
+// (tail: 1 = split the last wave's tiles along K where the tail plan gains,
+// 0 = never; lines without it mean 1).
 #include <cstdio>
 #include <map>
 #include <tuple>
@@ -45,7 +47,8 @@ TcChoice heuristic(int64_t n, int64_t m, int64_t p) {
 bool valid_choice(const TcChoice &c) {
   const bool bn_ok = c.bn == 64 || c.bn == 128 || c.bn == 256;
   const bool bk_ok = (c.bk == 64 && c.stages == 2) || (c.bk == 32 && (c.stages == 3 || c.stages == 4));
-  return bn_ok && bk_ok && c.group_m >= 1 && c.group_m <= 64 && c.grid >= 0;
+  return bn_ok && bk_ok && c.group_m >= 1 && c.group_m <= 64 && c.grid >= 0 &&
+         (c.tail == 0 || c.tail == 1);
 }
 
 __global__ void fill_kernel(float *x, int64_t count, float v) {
@@ -78,9 +81,10 @@ mm_status tune_load_file(const char *path) {
     if (line[0] == '#' || line[0] == '\n') continue;
     int ln, lm, lp;
     TcChoice c;
-    if (std::sscanf(line, "%d %d %d %d %d %d %d %d", &ln, &lm, &lp, &c.bn, &c.bk, &c.stages,
-                    &c.group_m, &c.grid) != 8 ||
-        !valid_choice(c)) {
+    c.tail = 1;
+    const int got = std::sscanf(line, "%d %d %d %d %d %d %d %d %d", &ln, &lm, &lp, &c.bn, &c.bk,
+                                &c.stages, &c.group_m, &c.grid, &c.tail);
+    if ((got != 8 && got != 9) || !valid_choice(c)) {
       st = MM_EINVAL;
       break;
     }
@@ -104,11 +108,11 @@ mm_status mm_tune_save(const char *path) {
   FILE *f = std::fopen(path, "w");
   if (!f) return MM_EINVAL;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  std::fprintf(f, "# ln lm lp bn bk stages group_m grid\n");
+  std::fprintf(f, "# ln lm lp bn bk stages group_m grid tail\n");
   for (auto &kv : g_table) {
     const TcChoice &c = kv.second;
-    std::fprintf(f, "%d %d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
-                 std::get<2>(kv.first), c.bn, c.bk, c.stages, c.group_m, c.grid);
+    std::fprintf(f, "%d %d %d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
+                 std::get<2>(kv.first), c.bn, c.bk, c.stages, c.group_m, c.grid, c.tail);
   }
   std::fclose(f);
   return MM_OK;
@@ -155,8 +159,9 @@ mm_status mm_tune(int64_t n, int64_t m, int64_t p, int reps) {
     if (bn == 64 && p > 128) continue;
     if (bn == 256 && p <= 128) continue;
     for (auto &kb : bks)
-      for (int gm : gms) {
-        TcChoice c{bn, kb[0], kb[1], gm, 0};
+      for (int gm : gms)
+      for (int tail = 1; tail >= 0; tail--) {
+        TcChoice c{bn, kb[0], kb[1], gm, 0, tail};
         st = run_split(g_ctx.split_ws, &q, 1, s, &c);  // warm-up
         if (st != MM_OK) break;
         cudaEventRecord(e0, s);

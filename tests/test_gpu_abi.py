@@ -65,11 +65,13 @@ def test_host_operands(mmlib, mode):
     assert_full(Cd.cpu().numpy(), A, B, "f64" if f64 else "f32")
 
 
-@pytest.mark.parametrize("shape", [(2304, 700, 300), (4100, 2500, 129)])
+@pytest.mark.parametrize("shape", [(2304, 700, 300), (4100, 2500, 129), (4100, 2500, 2000)])
 def test_host_operands_pipelined(mmlib, shape):
     """Large host-operand split products go through the slab pipeline (B
     packed once, rows of A in slabs, copies overlapping the tensor cores);
-    the result is identical to the device-operand call."""
+    the result is identical to the device-operand call where that call does
+    not split its last wave of tiles along K (the slabs never do), else
+    within the tolerance of it."""
     mm = mmlib
     n, m, p = shape
     A = synth.uniform_pm1(731, (n, m))
@@ -80,7 +82,14 @@ def test_host_operands_pipelined(mmlib, shape):
     assert mm.mm_gemm(n, m, p, Ap, Bp, Cp, mm.MM_F32, mm.MM_MODE_SPLIT_BF16X3) == 0
     Cd = torch.full((n, p), float("nan"), device="cuda")
     assert mm.mm_gemm(n, m, p, dev(A), dev(B), Cd, mm.MM_F32, mm.MM_MODE_SPLIT_BF16X3) == 0
-    assert torch.equal(Cp, Cd.cpu())
+    st, _, _, split_s = mm.mm_tune_query_tail(n, m, p)
+    assert st == 0
+    if split_s == 1:
+        assert torch.equal(Cp, Cd.cpu())
+    else:
+        absref = np.abs(A.astype(np.float64)) @ np.abs(B.astype(np.float64))
+        e = oracle.rel_errors(Cp.numpy(), Cd.cpu().numpy().astype(np.float64), absref)
+        assert e.max() <= oracle.tolerance(m, "f32")
     from gpu_util import sampled_check
     sampled_check(Cp.numpy(), A, B, "f32", count=1024, trials=1)
 
