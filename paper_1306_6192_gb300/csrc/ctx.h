@@ -83,8 +83,11 @@ TcKind split_kind_for(int64_t m);
 
 // N tile used for a kind: the tensor-core kernel loads B in 128-row boxes, so
 // parts * bn must be a multiple of 128; with one or three parts that rules
-// out bn = 64, which then becomes 128.
+// out bn = 64, which then becomes 128.  The three-part kind (small inner
+// dimensions only) always takes bn = 128: its 128-wide layout keeps a
+// four-stage ring beside the epilogue's staging buffers.
 inline int tc_bn(TcKind kind, int bn) {
+  if (kind == kTcSplitBf16x6) return 128;
   return (bn == 64 && pack_parts(kind) != 2) ? 128 : bn;
 }
 

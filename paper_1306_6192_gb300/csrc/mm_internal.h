@@ -73,6 +73,7 @@ struct SplitProb {
   int32_t pack_start;      // prefix of pack tiles: mt*kt + nt*kt
   int32_t red_start;       // prefix of scale-reduction items
   int32_t red_a;           // reduction items for A rows: ceil(n/8)
+  int32_t ver_start;       // prefix of verify items: ceil((n + p) / 32) each
   int32_t split_from;      // tail split (split_s <= 1: none; then split_from
   int32_t split_s;         //   is ignored and every tile is one unit)
   float *part;             // partial tiles of the split tiles
@@ -108,21 +109,30 @@ cudaError_t launch_simt_grouped(bool f64, const SimtProb *d_probs, int nprobs,
 // `map` arguments: item -> problem index arrays written by
 // launch_split_maps for tables of several problems, or nullptr.
 cudaError_t launch_split_maps(const SplitProb *d_probs, int nprobs, int *unit_map,
-                              int *pack_map, int *red_map, cudaStream_t s);
+                              int *pack_map, int *red_map, int *ver_map, cudaStream_t s);
+// Verify items of a product: 32 rows/columns each.
+__host__ __device__ inline int64_t verify_items(int64_t n, int64_t p) { return (n + p + 31) / 32; }
 cudaError_t launch_split_scale(const SplitProb *d_probs, int nprobs,
                                int total_items, const int *map, cudaStream_t s);
 // Pack modes (split kinds) and the per-problem flags they use.
 constexpr int kPackUnscaled = 1, kPackFix = 2;
 constexpr int kFlagScaleA = 1, kFlagScaleB = 2;
+// kPackUnscaled: one block per pack tile.  kPackFix: a persistent grid that
+// returns at once unless *any is set, then re-packs the tiles of flagged
+// operands (flags[g]).
 cudaError_t launch_split_pack(TcKind kind, int mode, const SplitProb *d_probs, int nprobs,
-                              int total_tiles, const int *map, const int *flags,
+                              int total_tiles, const int *map, const int *flags, const int *any,
                               void *pack_base, cudaStream_t s);
 // After an unscaled pack: reduces the partial maxima into sA / tB and sets
-// flags[g] (zeroed by the caller).  max_words = max over problems of n + p.
-// write_cols = false leaves tB as it is (a later slab sharing B's words,
-// which another stream may be reading) but still flags B.
-cudaError_t launch_split_verify(const SplitProb *d_probs, int nprobs, int64_t max_words,
-                                int *flags, cudaStream_t s, bool write_cols = true);
+// flags[g] (and *any) for operands out of range; flags and *any zeroed by
+// the caller.  total_items = sum over problems of verify_items(n, p); map:
+// item -> problem (tables of several problems) or nullptr; max_kt = the
+// largest kt of the table.  write_cols = false leaves tB as it is (a later
+// slab sharing B's words, which another stream may be reading) but still
+// flags B.
+cudaError_t launch_split_verify(const SplitProb *d_probs, int nprobs, int64_t total_items,
+                                const int *map, int *flags, int *any, int max_kt, cudaStream_t s,
+                                bool write_cols = true);
 cudaError_t launch_fp8_pack(const SplitProb *d_probs, int nprobs,
                             int total_tiles, const int *map, void *pack_base,
                             cudaStream_t s);
@@ -130,8 +140,10 @@ cudaError_t launch_fp8_pack(const SplitProb *d_probs, int nprobs,
 // Tensor-core mainloop + epilogue over all work units of all problems.
 struct TcConfig {
   int bkb;      // bytes of K per pipeline stage and pack row: 64 or 128
-  int stages;   // pipeline depth
+  int stages;   // pipeline depth (tables with max_bn > 128)
   int grid;     // persistent CTAs (<= number of SMs; 0 = one per SM)
+  int max_bn = 256;  // widest N tile of the table: <= 128 selects the deeper
+                     // rings of the 128-wide layouts
 };
 int tc_grid(const TcConfig &cfg);
 // Tail-split plan of one product from its own shape only (so that a product

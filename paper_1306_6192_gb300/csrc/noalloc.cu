@@ -147,13 +147,18 @@ mm_status mm_gemm_split_static(int64_t n, int64_t m, int64_t p, const float *A, 
   // same passes as mm_gemm's split path: unscaled pack with the maxima,
   // verification, re-pack of operands out of range
   if (e == cudaSuccess)
-    e = launch_split_pack(kind, kPackUnscaled, d_tab, 1, (int)packs, nullptr, nullptr, pack, s);
-  if (e == cudaSuccess) e = launch_split_verify(d_tab, 1, n + p, d_sflag, s);
+    e = launch_split_pack(kind, kPackUnscaled, d_tab, 1, (int)packs, nullptr, nullptr, nullptr,
+                          pack, s);
+  // d_sflag[0]: the operands' scale flags; d_sflag[1]: set when any is flagged
   if (e == cudaSuccess)
-    e = launch_split_pack(kind, kPackFix, d_tab, 1, (int)packs, nullptr, d_sflag, pack, s);
+    e = launch_split_verify(d_tab, 1, verify_items(n, p), nullptr, d_sflag, d_sflag + 1, sp.kt,
+                            s);
+  if (e == cudaSuccess)
+    e = launch_split_pack(kind, kPackFix, d_tab, 1, (int)packs, nullptr, d_sflag, d_sflag + 1,
+                          pack, s);
   if (e == cudaSuccess) {
-    TcConfig cfg = kind == kTcSplitBf16x3 ? TcConfig{2 * ch.bk, ch.stages, sms}
-                                          : TcConfig{64, 3, sms};
+    TcConfig cfg = kind == kTcSplitBf16x3 ? TcConfig{2 * ch.bk, ch.stages, sms, ch.bn}
+                                          : TcConfig{64, 3, sms, ch.bn};
     e = launch_tc(kind, d_tab, 1, (int)tiles, nullptr, d_sflag, pack, rows, cfg, d_flag, s);
   }
   if (e != cudaSuccess) {

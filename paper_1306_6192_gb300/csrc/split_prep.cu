@@ -32,6 +32,8 @@
 // flags, per problem, an operand with a row/column outside the range, and a
 // second pack launch (kPackFix) re-packs only the flagged operands with their
 // scales.  The epilogue applies 2^(s_i + t_j) only for flagged operands.
+#include <algorithm>
+
 #include "split_common.cuh"
 
 namespace mm {
@@ -169,105 +171,132 @@ __device__ __forceinline__ uint32_t half_warp_max(uint32_t v) {
 }
 
 // MODE: kPackUnscaled - no scaling; write the tile's row (A) / column (B)
-//                       maxima to pA / pB;
+//                       maxima to pA / pB; one block per pack tile;
 //       kPackFix      - scale by 2^-s from the maxima in sA / tB; only the
-//                       operands flagged by split_verify_kernel (the other
-//                       blocks return).
+//                       operands flagged by split_verify_kernel; a persistent
+//                       grid over the pack tiles that returns at once when
+//                       no operand of the table is flagged (*any == 0).
+// Every thread first loads all its 16-byte vectors of a tile (eight of A, or
+// four of a 64-column slice of B), then splits and stores them, so that each
+// thread keeps several loads in flight.
 template <int PARTS, int MODE>
 __global__ void __launch_bounds__(256)
 split_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *__restrict__ map,
-                  const int *__restrict__ flags, uint2 *__restrict__ pack) {
-  const int item = blockIdx.x;
-  const int g =
-      find_problem(probs, nprobs, map, item, [](const SplitProb &q) { return q.pack_start; });
-  const SplitProb &pr = probs[g];
-  const int local = item - pr.pack_start;
-  const int tid = threadIdx.x;
+                  const int *__restrict__ flags, const int *__restrict__ any, int total_tiles,
+                  uint2 *__restrict__ pack) {
   constexpr int kQuads = kPackK / 4;  // groups of four bf16 (8 bytes) per pack row
-  const bool a_tile = local < pr.mt * pr.kt;
-  if (MODE == kPackFix && !(flags[g] & (a_tile ? kFlagScaleA : kFlagScaleB))) return;
-  if (a_tile) {
-    // A tile (mt, kb): rows mt*128.., k kb*64..; a warp covers two rows.
-    const int mt = local / pr.kt, kb = local % pr.kt;
-    const int64_t base = pr.a_row0 + (int64_t)local * PARTS * kTcBM;
-    const bool vec = aligned16(pr.A) && (pr.m & 3) == 0;
-    for (int q = tid; q < kTcBM * kQuads; q += 256) {
-      const int r = q / kQuads, kq = q % kQuads;
-      const int64_t i = (int64_t)mt * kTcBM + r;
-      const int64_t k = (int64_t)kb * kPackK + 4 * kq;
-      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-      int s = 0;
-      if (i < pr.n) {
-        const float *row = pr.A + i * pr.m;
-        if (vec && k + 4 <= pr.m) {
-          x = *reinterpret_cast<const float4 *>(row + k);
-        } else {
-          if (k < pr.m) x.x = row[k];
-          if (k + 1 < pr.m) x.y = row[k + 1];
-          if (k + 2 < pr.m) x.z = row[k + 2];
-          if (k + 3 < pr.m) x.w = row[k + 3];
-        }
-        if (MODE != kPackUnscaled) s = scale_exponent(pr.sA[i]);
-      }
-      if (MODE == kPackUnscaled) {
-        // the 16 threads of a half warp hold one row's 64 values
-        const uint32_t mx = half_warp_max(max4_bits(x));
-        if (kq == 0 && i < pr.n) pr.pA[(int64_t)kb * pr.n + i] = mx;
-      }
-      uint2 part[PARTS];
-      split4<PARTS>(x, s, part);
+  constexpr int kAIter = kTcBM * kQuads / 256;
+  constexpr int kBIter = kPackK * 16 / 256;
+  __shared__ float tile[kPackK][64 + 1];
+  if (MODE == kPackFix && *any == 0) return;
+  const int tid = threadIdx.x;
+  for (int item = blockIdx.x; item < total_tiles; item += gridDim.x) {
+    const int g =
+        find_problem(probs, nprobs, map, item, [](const SplitProb &q) { return q.pack_start; });
+    const SplitProb &pr = probs[g];
+    const int local = item - pr.pack_start;
+    const bool a_tile = local < pr.mt * pr.kt;
+    if (MODE == kPackFix && !(flags[g] & (a_tile ? kFlagScaleA : kFlagScaleB))) continue;
+    if (a_tile) {
+      // A tile (mt, kb): rows mt*128.., k kb*64..; a warp covers two rows.
+      const int mt = local / pr.kt, kb = local % pr.kt;
+      const int64_t base = pr.a_row0 + (int64_t)local * PARTS * kTcBM;
+      const bool vec = aligned16(pr.A) && (pr.m & 3) == 0;
+      float4 xs[kAIter];
 #pragma unroll
-      for (int h = 0; h < PARTS; h++) pack[(base + h * kTcBM + r) * kQuads + kq] = part[h];
-    }
-  } else {
-    // B tile (nt, kb): columns nt*bn.., k kb*64..; transposed through shared
-    // memory 64 columns at a time so both the read and the write coalesce.
-    __shared__ float tile[kPackK][64 + 1];
-    const int b = local - pr.mt * pr.kt;
-    const int nt = b / pr.kt, kb = b % pr.kt;
-    const int bn = pr.bn;
-    const int64_t base = pr.b_row0 + (int64_t)b * PARTS * bn;
-    const bool vec = aligned16(pr.B) && (pr.p & 3) == 0;
-    for (int c0 = 0; c0 < bn; c0 += 64) {
-      for (int q = tid; q < kPackK * 16; q += 256) {
-        const int kk = q / 16, c4 = q % 16;
-        const int64_t k = (int64_t)kb * kPackK + kk;
-        const int64_t j = (int64_t)nt * bn + c0 + 4 * c4;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (k < pr.m) {
-          const float *src = pr.B + k * pr.p + j;
-          if (vec && j + 4 <= pr.p) {
-            v = *reinterpret_cast<const float4 *>(src);
+      for (int it = 0; it < kAIter; it++) {
+        const int q = tid + it * 256;
+        const int r = q / kQuads, kq = q % kQuads;
+        const int64_t i = (int64_t)mt * kTcBM + r;
+        const int64_t k = (int64_t)kb * kPackK + 4 * kq;
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < pr.n) {
+          const float *row = pr.A + i * pr.m;
+          if (vec && k + 4 <= pr.m) {
+            x = __ldcs(reinterpret_cast<const float4 *>(row + k));
           } else {
-            if (j < pr.p) v.x = src[0];
-            if (j + 1 < pr.p) v.y = src[1];
-            if (j + 2 < pr.p) v.z = src[2];
-            if (j + 3 < pr.p) v.w = src[3];
+            if (k < pr.m) x.x = row[k];
+            if (k + 1 < pr.m) x.y = row[k + 1];
+            if (k + 2 < pr.m) x.z = row[k + 2];
+            if (k + 3 < pr.m) x.w = row[k + 3];
           }
         }
-        tile[kk][4 * c4 + 0] = v.x;
-        tile[kk][4 * c4 + 1] = v.y;
-        tile[kk][4 * c4 + 2] = v.z;
-        tile[kk][4 * c4 + 3] = v.w;
+        xs[it] = x;
       }
-      __syncthreads();
-      for (int q = tid; q < 64 * kQuads; q += 256) {
-        const int c = q / kQuads, kq = q % kQuads;
-        const int64_t j = (int64_t)nt * bn + c0 + c;
-        const int s = (MODE != kPackUnscaled && j < pr.p) ? scale_exponent(pr.tB[j]) : 0;
-        const float4 x = make_float4(tile[4 * kq][c], tile[4 * kq + 1][c], tile[4 * kq + 2][c],
-                                     tile[4 * kq + 3][c]);
+#pragma unroll
+      for (int it = 0; it < kAIter; it++) {
+        const int q = tid + it * 256;
+        const int r = q / kQuads, kq = q % kQuads;
+        const int64_t i = (int64_t)mt * kTcBM + r;
+        const int s = (MODE != kPackUnscaled && i < pr.n) ? scale_exponent(pr.sA[i]) : 0;
         if (MODE == kPackUnscaled) {
-          // the 16 threads of a half warp hold one column's 64 values
-          const uint32_t mx = half_warp_max(max4_bits(x));
-          if (kq == 0 && j < pr.p) pr.pB[(int64_t)kb * pr.p + j] = mx;
+          // the 16 threads of a half warp hold one row's 64 values
+          const uint32_t mx = half_warp_max(max4_bits(xs[it]));
+          if (kq == 0 && i < pr.n) pr.pA[(int64_t)kb * pr.n + i] = mx;
         }
         uint2 part[PARTS];
-        split4<PARTS>(x, s, part);
+        split4<PARTS>(xs[it], s, part);
 #pragma unroll
-        for (int h = 0; h < PARTS; h++) pack[(base + h * bn + c0 + c) * kQuads + kq] = part[h];
+        for (int h = 0; h < PARTS; h++) pack[(base + h * kTcBM + r) * kQuads + kq] = part[h];
       }
-      __syncthreads();
+    } else {
+      // B tile (nt, kb): columns nt*bn.., k kb*64..; transposed through shared
+      // memory 64 columns at a time so both the read and the write coalesce.
+      const int b = local - pr.mt * pr.kt;
+      const int nt = b / pr.kt, kb = b % pr.kt;
+      const int bn = pr.bn;
+      const int64_t base = pr.b_row0 + (int64_t)b * PARTS * bn;
+      const bool vec = aligned16(pr.B) && (pr.p & 3) == 0;
+      for (int c0 = 0; c0 < bn; c0 += 64) {
+        float4 vs[kBIter];
+#pragma unroll
+        for (int it = 0; it < kBIter; it++) {
+          const int q = tid + it * 256;
+          const int kk = q / 16, c4 = q % 16;
+          const int64_t k = (int64_t)kb * kPackK + kk;
+          const int64_t j = (int64_t)nt * bn + c0 + 4 * c4;
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (k < pr.m) {
+            const float *src = pr.B + k * pr.p + j;
+            if (vec && j + 4 <= pr.p) {
+              v = __ldcs(reinterpret_cast<const float4 *>(src));
+            } else {
+              if (j < pr.p) v.x = src[0];
+              if (j + 1 < pr.p) v.y = src[1];
+              if (j + 2 < pr.p) v.z = src[2];
+              if (j + 3 < pr.p) v.w = src[3];
+            }
+          }
+          vs[it] = v;
+        }
+#pragma unroll
+        for (int it = 0; it < kBIter; it++) {
+          const int q = tid + it * 256;
+          const int kk = q / 16, c4 = q % 16;
+          tile[kk][4 * c4 + 0] = vs[it].x;
+          tile[kk][4 * c4 + 1] = vs[it].y;
+          tile[kk][4 * c4 + 2] = vs[it].z;
+          tile[kk][4 * c4 + 3] = vs[it].w;
+        }
+        __syncthreads();
+        for (int q = tid; q < 64 * kQuads; q += 256) {
+          const int c = q / kQuads, kq = q % kQuads;
+          const int64_t j = (int64_t)nt * bn + c0 + c;
+          const int s = (MODE != kPackUnscaled && j < pr.p) ? scale_exponent(pr.tB[j]) : 0;
+          const float4 x = make_float4(tile[4 * kq][c], tile[4 * kq + 1][c], tile[4 * kq + 2][c],
+                                       tile[4 * kq + 3][c]);
+          if (MODE == kPackUnscaled) {
+            // the 16 threads of a half warp hold one column's 64 values
+            const uint32_t mx = half_warp_max(max4_bits(x));
+            if (kq == 0 && j < pr.p) pr.pB[(int64_t)kb * pr.p + j] = mx;
+          }
+          uint2 part[PARTS];
+          split4<PARTS>(x, s, part);
+#pragma unroll
+          for (int h = 0; h < PARTS; h++) pack[(base + h * bn + c0 + c) * kQuads + kq] = part[h];
+        }
+        __syncthreads();
+      }
     }
   }
 }
@@ -278,42 +307,60 @@ __device__ __forceinline__ bool needs_scale(uint32_t max_bits) {
   return max_bits != 0 && (max_bits < 0x2B800000u /* 2^-40 */ || max_bits > 0x53800000u /* 2^40 */);
 }
 
-// Blocks (x: 32 rows/columns, y: problems; 8 warps split the K blocks): the
-// maximum of a row of A over its K blocks -> sA (columns of B -> tB), and
-// flags[g] |= kFlagScaleA / kFlagScaleB where a maximum is outside the range
-// packed unscaled.
+// Verify items of 32 rows/columns of one problem; WPI warps per item split
+// its K blocks, 8 / WPI items per block (WPI from the table's longest K, so
+// that short products do not pay for idle warps): the maximum of a row of A
+// over its K blocks -> sA (columns of B -> tB), and flags[g] |= kFlagScaleA /
+// kFlagScaleB (and *any) where a maximum is outside the range packed
+// unscaled.
+template <int WPI>
 __global__ void __launch_bounds__(256)
-split_verify_kernel(const SplitProb *__restrict__ probs, int nprobs, int *__restrict__ flags,
+split_verify_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *__restrict__ map,
+                    int total_items, int *__restrict__ flags, int *__restrict__ any,
                     bool write_cols) {
   __shared__ uint32_t part[8][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int g = blockIdx.y; g < nprobs; g += gridDim.y) {
-    const SplitProb &pr = probs[g];
-    const int64_t w = (int64_t)blockIdx.x * 32 + lane;
-    const bool is_row = w < pr.n;
-    const bool valid = w < (int64_t)pr.n + pr.p;
-    const uint32_t *src = is_row ? pr.pA + w : pr.pB + (w - pr.n);
-    const int64_t stride = is_row ? pr.n : pr.p;
-    uint32_t mx = 0;
+  const int sub = warp % WPI;
+  const int item = blockIdx.x * (8 / WPI) + warp / WPI;
+  const bool live = item < total_items;
+  const SplitProb *pp = nullptr;
+  int g = 0;
+  int64_t w = 0;
+  bool valid = false;
+  uint32_t mx = 0;
+  if (live) {
+    g = find_problem(probs, nprobs, map, item, [](const SplitProb &q) { return q.ver_start; });
+    pp = probs + g;
+    w = (int64_t)(item - pp->ver_start) * 32 + lane;
+    valid = w < (int64_t)pp->n + pp->p;
     if (valid) {
+      const bool is_row = w < pp->n;
+      const uint32_t *src = is_row ? pp->pA + w : pp->pB + (w - pp->n);
+      const int64_t stride = is_row ? pp->n : pp->p;
 #pragma unroll 4
-      for (int kb = warp; kb < pr.kt; kb += 8) mx = umax(mx, src[kb * stride]);
+      for (int kb = sub; kb < pp->kt; kb += WPI) mx = umax(mx, src[kb * stride]);
     }
+  }
+  if (WPI > 1) {
     part[warp][lane] = mx;
     __syncthreads();
-    int bad = 0;
-    if (warp == 0 && valid) {
+    if (sub == 0)
 #pragma unroll
-      for (int q = 1; q < 8; q++) mx = umax(mx, part[q][lane]);
-      if (is_row) pr.sA[w] = mx; else if (write_cols) pr.tB[w - pr.n] = mx;
-      if (needs_scale(mx)) bad = is_row ? kFlagScaleA : kFlagScaleB;
-    }
-    const int any = __syncthreads_or(bad);
-    if (any) {
-      const int a = __syncthreads_or(bad & kFlagScaleA);
-      const int b = __syncthreads_or(bad & kFlagScaleB);
-      if (threadIdx.x == 0) atomicOr(&flags[g], (a ? kFlagScaleA : 0) | (b ? kFlagScaleB : 0));
-    }
+      for (int q = 1; q < WPI; q++) mx = umax(mx, part[warp + q][lane]);
+  }
+  if (sub != 0 || !live) return;
+  int bad = 0;
+  if (valid) {
+    const bool is_row = w < pp->n;
+    if (is_row) pp->sA[w] = mx; else if (write_cols) pp->tB[w - pp->n] = mx;
+    if (needs_scale(mx)) bad = is_row ? kFlagScaleA : kFlagScaleB;
+  }
+  const unsigned mask = __activemask();
+  const unsigned a = __ballot_sync(mask, bad & kFlagScaleA);
+  const unsigned b = __ballot_sync(mask, bad & kFlagScaleB);
+  if (lane == 0 && (a || b)) {
+    atomicOr(&flags[g], (a ? kFlagScaleA : 0) | (b ? kFlagScaleB : 0));
+    atomicOr(any, 1);
   }
 }
 
@@ -321,7 +368,8 @@ split_verify_kernel(const SplitProb *__restrict__ probs, int nprobs, int *__rest
 // tiles, pack tiles and scale-reduction items.
 __global__ void __launch_bounds__(256)
 split_maps_kernel(const SplitProb *__restrict__ probs, int *__restrict__ unit_map,
-                  int *__restrict__ pack_map, int *__restrict__ red_map) {
+                  int *__restrict__ pack_map, int *__restrict__ red_map,
+                  int *__restrict__ ver_map) {
   const int g = blockIdx.x;
   const SplitProb &pr = probs[g];
   const int units = (int)split_units(pr);
@@ -332,15 +380,19 @@ split_maps_kernel(const SplitProb *__restrict__ probs, int *__restrict__ unit_ma
   for (int i = threadIdx.x; i < packs; i += blockDim.x) pack_map[pr.pack_start + i] = g;
   if (red_map)  // only tables that run split_scale_kernel (the e4m3 path)
     for (int i = threadIdx.x; i < reds; i += blockDim.x) red_map[pr.red_start + i] = g;
+  if (ver_map) {  // only tables that run split_verify_kernel (the split kinds)
+    const int vers = (int)verify_items(pr.n, pr.p);
+    for (int i = threadIdx.x; i < vers; i += blockDim.x) ver_map[pr.ver_start + i] = g;
+  }
 }
 
 }  // namespace
 
 cudaError_t launch_split_maps(const SplitProb *d_probs, int nprobs, int *unit_map, int *pack_map,
-                              int *red_map, cudaStream_t s) {
+                              int *red_map, int *ver_map, cudaStream_t s) {
   if (nprobs <= 0) return cudaSuccess;
   TraceScope ts("split_maps", s);
-  split_maps_kernel<<<nprobs, 256, 0, s>>>(d_probs, unit_map, pack_map, red_map);
+  split_maps_kernel<<<nprobs, 256, 0, s>>>(d_probs, unit_map, pack_map, red_map, ver_map);
   return cudaGetLastError();
 }
 
@@ -353,25 +405,38 @@ cudaError_t launch_split_scale(const SplitProb *d_probs, int nprobs, int total_i
 }
 
 cudaError_t launch_split_pack(TcKind kind, int mode, const SplitProb *d_probs, int nprobs,
-                              int total_tiles, const int *map, const int *flags, void *pack_base,
-                              cudaStream_t s) {
+                              int total_tiles, const int *map, const int *flags, const int *any,
+                              void *pack_base, cudaStream_t s) {
   if (total_tiles <= 0) return cudaSuccess;
   TraceScope ts(mode == kPackFix ? "split_fix" : "split_pack", s);
   auto *pk = static_cast<uint2 *>(pack_base);
   const bool x6 = kind == kTcSplitBf16x6;
-#define MM_PACK(P, M) split_pack_kernel<P, M><<<total_tiles, 256, 0, s>>>(d_probs, nprobs, map, flags, pk)
+  // the fix pass: a persistent grid (8 blocks per SM) over the tiles
+  const int grid = mode == kPackFix ? std::min(total_tiles, sm_count() * 8) : total_tiles;
+#define MM_PACK(P, M) \
+  split_pack_kernel<P, M><<<grid, 256, 0, s>>>(d_probs, nprobs, map, flags, any, total_tiles, pk)
   if (mode == kPackUnscaled) { if (x6) MM_PACK(3, kPackUnscaled); else MM_PACK(2, kPackUnscaled); }
   else { if (x6) MM_PACK(3, kPackFix); else MM_PACK(2, kPackFix); }
 #undef MM_PACK
   return cudaGetLastError();
 }
 
-cudaError_t launch_split_verify(const SplitProb *d_probs, int nprobs, int64_t max_words,
-                                int *flags, cudaStream_t s, bool write_cols) {
-  if (nprobs <= 0 || max_words <= 0) return cudaSuccess;
+cudaError_t launch_split_verify(const SplitProb *d_probs, int nprobs, int64_t total_items,
+                                const int *map, int *flags, int *any, int max_kt, cudaStream_t s,
+                                bool write_cols) {
+  if (nprobs <= 0 || total_items <= 0) return cudaSuccess;
+  if (total_items > 0x7fffffffLL) return cudaErrorInvalidValue;
   TraceScope ts("split_verify", s);
-  dim3 grid((unsigned)((max_words + 31) / 32), (unsigned)(nprobs < 65535 ? nprobs : 65535));
-  split_verify_kernel<<<grid, 256, 0, s>>>(d_probs, nprobs, flags, write_cols);
+  const int wpi = max_kt >= 64 ? 8 : (max_kt >= 32 ? 4 : (max_kt >= 16 ? 2 : 1));
+  const int ti = (int)total_items;
+  const unsigned blocks = (unsigned)((total_items * wpi + 7) / 8);
+#define MM_VERIFY(W) \
+  split_verify_kernel<W><<<blocks, 256, 0, s>>>(d_probs, nprobs, map, ti, flags, any, write_cols)
+  if (wpi == 8) MM_VERIFY(8);
+  else if (wpi == 4) MM_VERIFY(4);
+  else if (wpi == 2) MM_VERIFY(2);
+  else MM_VERIFY(1);
+#undef MM_VERIFY
   return cudaGetLastError();
 }
 

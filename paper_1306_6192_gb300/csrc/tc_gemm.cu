@@ -50,7 +50,6 @@ namespace mm {
 namespace {
 
 constexpr int kThreads = 192;
-constexpr int kMaxBN = 256;
 constexpr int kAccCols = 256;               // TMEM columns per accumulator
 constexpr uint32_t kTmemCols = 2 * kAccCols;
 constexpr int kBoxRows = 128;               // TMA box height (rows of the pack)
@@ -296,26 +295,34 @@ __device__ __forceinline__ void epilogue_sync() {
   asm volatile("bar.sync 1, 128;" ::: "memory");
 }
 
-template <int BKB, int STAGES, int KIND>
+// Shared-memory layout of one instantiation: STAGES ring stages of BKB bytes
+// of K for A (128 rows) and B (up to MAXBN rows) in every part.  Tables whose
+// widest N tile is 128 take MAXBN = 128 layouts, whose smaller stages leave
+// room for a deeper ring (small products have short K loops and need more
+// loads in flight to cover the TMA latency).
+template <int BKB, int STAGES, int KIND, int MAXBN>
 struct TcLayout {
+  static constexpr int kMaxBN = MAXBN;
   static constexpr int kParts = KIND == kTcE4m3 ? 1 : (KIND == kTcSplitBf16x3 ? 2 : 3);
   static constexpr int kElemBytes = KIND == kTcE4m3 ? 1 : 2;
   static constexpr int kAPart = kTcBM * BKB;            // one part of A per stage
-  static constexpr int kBPartMax = kMaxBN * BKB;        // one part of B at bn = 256
+  static constexpr int kBPartMax = kMaxBN * BKB;        // one part of B at bn = MAXBN
   static constexpr int kStageBytes = kParts * (kAPart + kBPartMax);
   static constexpr int kBarOffset = STAGES * kStageBytes;
   static constexpr int kNumBars = 2 * STAGES + 4 + 1;  // full, empty, acc_full/empty, drain
   static constexpr int kColExpOffset = kBarOffset + kNumBars * 8 + 16;  // int[2][kMaxBN]
   static constexpr int kLastOffset = kColExpOffset + 2 * kMaxBN * 4;   // int: last-part flag
-  static constexpr int kSmemBytes = kLastOffset + 16 + 1024;          // + align slack
+  // epilogue staging: one 32 x 33 float block per epilogue warp
+  static constexpr int kStageOffset = kLastOffset + 16;
+  static constexpr int kSmemBytes = kStageOffset + 4 * 32 * 33 * 4 + 1024;  // + align slack
 };
 
-template <int BKB, int STAGES, int KIND>
+template <int BKB, int STAGES, int KIND, int MAXBN>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__restrict__ probs,
                int nprobs, const int *__restrict__ unit_map, const int *__restrict__ flags,
                int total_units, int *err) {
-  using L = TcLayout<BKB, STAGES, KIND>;
+  using L = TcLayout<BKB, STAGES, KIND, MAXBN>;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sbase = (raw + 1023u) & ~1023u;
@@ -327,8 +334,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
   auto acce_bar = [&](int a) { return bars + 8u * (2 * STAGES + 2 + a); };
   const uint32_t drain_bar = bars + 8u * (2 * STAGES + 4);
   uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(smem + L::kBarOffset + L::kNumBars * 8);
-  int *colexp = reinterpret_cast<int *>(smem + L::kColExpOffset);  // [2][kMaxBN]
+  int *colexp = reinterpret_cast<int *>(smem + L::kColExpOffset);  // [2][MAXBN]
   volatile int *last_flag = reinterpret_cast<volatile int *>(smem + L::kLastOffset);
+  float *stage_buf = reinterpret_cast<float *>(smem + L::kStageOffset);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -500,7 +508,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
       // column exponents of this tile, once per tile, while the MMAs run
       // operands packed without scaling (flags) take exponent 0
       const int fl = flags ? flags[tc.g] : (kFlagScaleA | kFlagScaleB);
-      int *cexp = colexp + acc * kMaxBN;
+      int *cexp = colexp + acc * MAXBN;
       for (int c = et; c < pr.bn; c += 128) {
         const int64_t j = (int64_t)tc.nt * pr.bn + c;
         cexp[c] = (j < pr.p && (fl & kFlagScaleB)) ? kind_exponent<KIND>(pr.tB[j]) : 0;
@@ -511,8 +519,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
       const int64_t i = (int64_t)tc.mt * kTcBM + row;
       const bool row_ok = i < pr.n;
       const int si = (row_ok && (fl & kFlagScaleA)) ? kind_exponent<KIND>(pr.sA[i]) : 0;
-      float *crow = pr.C + (row_ok ? i : 0) * (int64_t)pr.p;
-      const bool vec = ((reinterpret_cast<uintptr_t>(pr.C) & 15u) == 0) && ((pr.p & 3) == 0);
+      float *buf = stage_buf + q * 32 * 33;  // this warp's 32 x 32 block (row pitch 33)
+      const int64_t row0 = (int64_t)tc.mt * kTcBM + q * 32;  // first row of the warp
       const uint32_t tacc = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kAccCols);
       // part of a split tile: a partial slot holds bn/4 groups of 4 columns,
       // each group 128 rows x 4 floats, so that a warp's 16-byte accesses to
@@ -592,23 +600,24 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
           }
         }
         const int64_t j0 = (int64_t)tc.nt * pr.bn + c;
-        if (!row_ok || j0 >= pr.p) continue;
+        if (j0 >= pr.p) continue;  // the same for the whole warp
+        // unscale this thread's row of the 32 x 32 block into shared memory,
+        // then write the block row by row: each store is 32 consecutive
+        // columns of one row, a whole 128-byte line
         const int *ce = cexp + c;
-        if (vec && j0 + 32 <= pr.p) {
 #pragma unroll
-          for (int e = 0; e < 32; e += 4) {
-            float4 o;
-            o.x = scale_pow2(__uint_as_float(v[e + 0]), si + ce[e + 0]);
-            o.y = scale_pow2(__uint_as_float(v[e + 1]), si + ce[e + 1]);
-            o.z = scale_pow2(__uint_as_float(v[e + 2]), si + ce[e + 2]);
-            o.w = scale_pow2(__uint_as_float(v[e + 3]), si + ce[e + 3]);
-            *reinterpret_cast<float4 *>(crow + j0 + e) = o;
-          }
-        } else {
-#pragma unroll
-          for (int e = 0; e < 32; e++)
-            if (j0 + e < pr.p) crow[j0 + e] = scale_pow2(__uint_as_float(v[e]), si + ce[e]);
+        for (int e = 0; e < 32; e++)
+          buf[lane * 33 + e] = scale_pow2(__uint_as_float(v[e]), si + ce[e]);
+        __syncwarp();
+        const int64_t j = j0 + lane;
+        if (j < pr.p) {
+          float *dst = pr.C + row0 * pr.p + j;
+          const int64_t left = pr.n - row0;
+          const int rows = left < 32 ? (int)left : 32;
+#pragma unroll 8
+          for (int r = 0; r < rows; r++, dst += pr.p) __stcs(dst, buf[r * 33 + lane]);
         }
+        __syncwarp();
       }
       tc_fence_before();
       mbar_arrive(acce_bar(acc));
@@ -658,18 +667,18 @@ cudaError_t encode_pack_map(CUtensorMap *map, void *base, int64_t rows, int bkb)
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int BKB, int STAGES, int KIND>
+template <int BKB, int STAGES, int KIND, int MAXBN>
 cudaError_t launch_tc_t(const SplitProb *d_probs, int nprobs, const int *unit_map,
                         const int *flags, int total_units, void *pack_base, int64_t pack_rows,
                         int grid, int *d_err, cudaStream_t s) {
-  using L = TcLayout<BKB, STAGES, KIND>;
+  using L = TcLayout<BKB, STAGES, KIND, MAXBN>;
   static_assert(L::kSmemBytes <= 232448, "shared memory budget");
   // one CTA per SM: the kernel allocates all 512 TMEM columns
   static_assert(2 * L::kSmemBytes > 232448, "must not fit twice on one SM");
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(tc_gemm_kernel<BKB, STAGES, KIND>,
+    attr_err = cudaFuncSetAttribute(tc_gemm_kernel<BKB, STAGES, KIND, MAXBN>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, L::kSmemBytes);
   });
   if (attr_err != cudaSuccess) return attr_err;
@@ -677,7 +686,7 @@ cudaError_t launch_tc_t(const SplitProb *d_probs, int nprobs, const int *unit_ma
   cudaError_t e = encode_pack_map(&map, pack_base, pack_rows, BKB);
   if (e != cudaSuccess) return e;
   TraceScope ts(KIND == kTcE4m3 ? "fp8_tc" : "split_tc", s);
-  tc_gemm_kernel<BKB, STAGES, KIND><<<grid, kThreads, L::kSmemBytes, s>>>(
+  tc_gemm_kernel<BKB, STAGES, KIND, MAXBN><<<grid, kThreads, L::kSmemBytes, s>>>(
       map, d_probs, nprobs, unit_map, flags, total_units, d_err);
   return cudaGetLastError();
 }
@@ -748,11 +757,14 @@ cudaError_t launch_tc(TcKind kind, const SplitProb *d_probs, int nprobs, int tot
   const int *mp = unit_map;
 #define MM_TC_ARGS d_probs, nprobs, mp, flags, total_units, pack_base, pack_rows, grid, d_err, s
   cudaError_t e = cudaErrorInvalidValue;
-  if (kind == kTcE4m3) e = launch_tc_t<128, 4, kTcE4m3>(MM_TC_ARGS);
-  else if (kind == kTcSplitBf16x6) e = launch_tc_t<64, 3, kTcSplitBf16x6>(MM_TC_ARGS);
-  else if (cfg.bkb == 128) e = launch_tc_t<128, 2, kTcSplitBf16x3>(MM_TC_ARGS);
-  else if (cfg.bkb == 64 && cfg.stages == 3) e = launch_tc_t<64, 3, kTcSplitBf16x3>(MM_TC_ARGS);
-  else if (cfg.bkb == 64) e = launch_tc_t<64, 4, kTcSplitBf16x3>(MM_TC_ARGS);
+  const bool narrow = cfg.max_bn <= 128;  // every N tile of the table fits 128
+  if (kind == kTcE4m3) e = launch_tc_t<128, 4, kTcE4m3, 256>(MM_TC_ARGS);
+  else if (kind == kTcSplitBf16x6 && narrow) e = launch_tc_t<64, 4, kTcSplitBf16x6, 128>(MM_TC_ARGS);
+  else if (cfg.bkb == 128 && narrow) e = launch_tc_t<128, 3, kTcSplitBf16x3, 128>(MM_TC_ARGS);
+  else if (cfg.bkb == 128) e = launch_tc_t<128, 2, kTcSplitBf16x3, 256>(MM_TC_ARGS);
+  else if (cfg.bkb == 64 && narrow) e = launch_tc_t<64, 6, kTcSplitBf16x3, 128>(MM_TC_ARGS);
+  else if (cfg.bkb == 64 && cfg.stages == 3) e = launch_tc_t<64, 3, kTcSplitBf16x3, 256>(MM_TC_ARGS);
+  else if (cfg.bkb == 64) e = launch_tc_t<64, 4, kTcSplitBf16x3, 256>(MM_TC_ARGS);
 #undef MM_TC_ARGS
   return e;
 }

@@ -20,7 +20,8 @@ struct Group {
   TcConfig cfg{0, 0, 0};
   std::vector<SplitProb> tab;
   int64_t units = 0, packs = 0, reds = 0;  // tensor-core work units, pack tiles, reductions
-  int64_t max_words = 0;  // max over problems of n + p (verify grid)
+  int64_t vers = 0;                         // verify items (split kinds)
+  int max_kt = 0;                           // longest K (pack rows) of the table
 };
 
 double kind_products(TcKind k) {
@@ -88,7 +89,9 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
       part += (int64_t)sp.kt * q.n;
       sp.pB = reinterpret_cast<uint32_t *>((uintptr_t)part);
       part += (int64_t)sp.kt * q.p;
-      G.max_words = std::max<int64_t>(G.max_words, q.n + q.p);
+      sp.ver_start = (int32_t)G.vers;
+      G.vers += verify_items(q.n, q.p);
+      G.max_kt = std::max(G.max_kt, sp.kt);
     }
     const TcTail tail = plan_tail(sp, kind, ch);
     if (tail.split_s > 1) {  // offsets, fixed below
@@ -99,6 +102,7 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
     }
     sp.unit_start = (int32_t)G.units;
     G.units += split_units(sp);
+    G.cfg.max_bn = G.tab.empty() ? sp.bn : std::max(G.cfg.max_bn, sp.bn);
     sp.pack_start = (int32_t)G.packs;
     G.packs += (int64_t)sp.mt * sp.kt + (int64_t)sp.nt * sp.kt;
     if (kind == kTcE4m3) {  // the e4m3 path reduces its maxima in a separate pass
@@ -110,7 +114,8 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
   }
   size_t ntab = 0;
   for (auto &G : groups) {
-    if (G.units > 0x7fffffffLL || G.packs > 0x7fffffffLL || G.reds > 0x7fffffffLL)
+    if (G.units > 0x7fffffffLL || G.packs > 0x7fffffffLL || G.reds > 0x7fffffffLL ||
+        G.vers > 0x7fffffffLL)
       return MM_EINVAL;
     ntab += G.tab.size();
   }
@@ -120,12 +125,12 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
   const size_t scal_off = (pack_bytes + 255) & ~(size_t)255;
   const size_t part_off = (scal_off + (size_t)scal * 4 + 255) & ~(size_t)255;
   const size_t tab_off = (part_off + (size_t)part * 4 + 255) & ~(size_t)255;
-  // item -> problem maps (tiles, pack tiles, reduction items) of each group
-  // with more than one problem
+  // item -> problem maps (work units, pack tiles, reduction and verify items)
+  // of each group with more than one problem
   size_t map_ints = 0;
   for (auto &G : groups)
-    if (G.tab.size() > 1) map_ints += (size_t)(G.units + G.packs + G.reds);
-  map_ints += ntab;  // per-problem scale flags (split kinds)
+    if (G.tab.size() > 1) map_ints += (size_t)(G.units + G.packs + G.reds + G.vers);
+  map_ints += ntab + 3;  // per-problem scale flags, one "any flagged" word per group
   const size_t map_off = (tab_off + ntab * sizeof(SplitProb) + 255) & ~(size_t)255;
   const size_t tpart_off = (map_off + map_ints * sizeof(int) + 255) & ~(size_t)255;
   const size_t tcnt_off = tpart_off + tail_parts;  // tail_parts is a multiple of 256
@@ -153,26 +158,30 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
   e = ws.stage.copy_to_device(d_tab, all.data(), all.size() * sizeof(SplitProb), s);
   if (e != cudaSuccess) return note_cuda(e);
   e = cudaMemsetAsync(base + scal_off, 0, (size_t)scal * 4, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(base + map_off, 0, ntab * sizeof(int), s);  // flags
+  if (e == cudaSuccess)  // flags and "any" words
+    e = cudaMemsetAsync(base + map_off, 0, (ntab + 3) * sizeof(int), s);
   if (e == cudaSuccess && tail_cnts > 0)
     e = cudaMemsetAsync(base + tcnt_off, 0, tail_cnts * sizeof(int), s);
   if (e != cudaSuccess) return note_cuda(e);
   size_t off = 0;
   int *flags_all = reinterpret_cast<int *>(base + map_off);
-  int *maps = flags_all + ntab;
-  for (auto &G : groups) {
+  int *maps = flags_all + ntab + 3;
+  for (int gi = 0; gi < 3; gi++) {
+    Group &G = groups[gi];
     if (G.tab.empty()) continue;
     const SplitProb *dt = d_tab + off;
     int *flags = flags_all + off;
+    int *any = flags_all + ntab + gi;
     const int np = (int)G.tab.size();
     off += G.tab.size();
-    int *tile_map = nullptr, *pack_map = nullptr, *red_map = nullptr;
+    int *tile_map = nullptr, *pack_map = nullptr, *red_map = nullptr, *ver_map = nullptr;
     if (np > 1) {
       tile_map = maps;
       pack_map = tile_map + G.units;
       red_map = G.reds > 0 ? pack_map + G.packs : nullptr;
-      maps = pack_map + G.packs + G.reds;
-      e = launch_split_maps(dt, np, tile_map, pack_map, red_map, s);
+      ver_map = G.vers > 0 ? pack_map + G.packs + G.reds : nullptr;
+      maps = pack_map + G.packs + G.reds + G.vers;
+      e = launch_split_maps(dt, np, tile_map, pack_map, red_map, ver_map, s);
       if (e != cudaSuccess) return note_cuda(e);
     }
     if (G.kind == kTcE4m3) {
@@ -185,11 +194,13 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
     } else {
       // split: one unscaled pass that also reduces the maxima, then the
       // operands out of range are re-packed with their scales
-      e = launch_split_pack(G.kind, kPackUnscaled, dt, np, (int)G.packs, pack_map, nullptr, base,
-                            s);
-      if (e == cudaSuccess) e = launch_split_verify(dt, np, G.max_words, flags, s);
+      e = launch_split_pack(G.kind, kPackUnscaled, dt, np, (int)G.packs, pack_map, nullptr,
+                            nullptr, base, s);
       if (e == cudaSuccess)
-        e = launch_split_pack(G.kind, kPackFix, dt, np, (int)G.packs, pack_map, flags, base, s);
+        e = launch_split_verify(dt, np, G.vers, ver_map, flags, any, G.max_kt, s);
+      if (e == cudaSuccess)
+        e = launch_split_pack(G.kind, kPackFix, dt, np, (int)G.packs, pack_map, flags, any, base,
+                              s);
       if (e == cudaSuccess)
         e = launch_tc(G.kind, dt, np, (int)G.units, tile_map, flags, base, rows, G.cfg,
                       g_ctx.d_err, s);
@@ -209,8 +220,8 @@ mm_status run_split_chunked(Scratch &ws, int64_t n, int64_t m, int64_t p, const 
   const int parts = pack_parts(kind);
   TcChoice ch = tune_choose(n, m, p);
   ch.bn = tc_bn(kind, ch.bn);
-  const TcConfig cfg = kind == kTcSplitBf16x3 ? TcConfig{2 * ch.bk, ch.stages, ch.grid}
-                                              : TcConfig{64, 3, ch.grid};
+  const TcConfig cfg = kind == kTcSplitBf16x3 ? TcConfig{2 * ch.bk, ch.stages, ch.grid, ch.bn}
+                                              : TcConfig{64, 3, ch.grid, ch.bn};
   const int32_t kt = (int32_t)ceil_div(m, pack_k(kind));
   const int32_t nt = (int32_t)ceil_div(p, ch.bn);
   // layout: B pack, then each slab's A pack; scale words: B columns, then A rows
@@ -254,8 +265,9 @@ mm_status run_split_chunked(Scratch &ws, int64_t n, int64_t m, int64_t p, const 
   const size_t scal_off = (pack_bytes + 255) & ~(size_t)255;
   const size_t part_off = (scal_off + (size_t)(n + p) * 4 + 255) & ~(size_t)255;
   const size_t tab_off = (part_off + (size_t)kt * (n + p) * 4 + 255) & ~(size_t)255;
+  // per slab: its scale flags word, then (chunks words later) its "any" word
   const size_t flag_off = (tab_off + tab.size() * sizeof(SplitProb) + 255) & ~(size_t)255;
-  cudaError_t e = ws.reserve(flag_off + tab.size() * sizeof(int), s);
+  cudaError_t e = ws.reserve(flag_off + 2 * tab.size() * sizeof(int), s);
   if (e != cudaSuccess) return note_cuda(e);
   uint8_t *base = static_cast<uint8_t *>(ws.ptr);
   uint32_t *scal = reinterpret_cast<uint32_t *>(base + scal_off);
@@ -269,7 +281,7 @@ mm_status run_split_chunked(Scratch &ws, int64_t n, int64_t m, int64_t p, const 
   SplitProb *d_tab = reinterpret_cast<SplitProb *>(base + tab_off);
   e = ws.stage.copy_to_device(d_tab, tab.data(), tab.size() * sizeof(SplitProb), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(scal, 0, (size_t)(n + p) * 4, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(base + flag_off, 0, tab.size() * sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + flag_off, 0, 2 * tab.size() * sizeof(int), s);
   if (e != cudaSuccess) return note_cuda(e);
   // Preparation of the slabs runs in order on s; each slab's tensor-core
   // launch goes to one of two streams, so the next slab's preparation and
@@ -279,16 +291,18 @@ mm_status run_split_chunked(Scratch &ws, int64_t n, int64_t m, int64_t p, const 
     if ((e = cudaStreamWaitEvent(s, in_ready[c + 1], 0)) != cudaSuccess) break;
     const SplitProb *dt = d_tab + c;
     int *flag = reinterpret_cast<int *>(base + flag_off) + c;
+    int *any = flag + chunks;
     // slab 0 packs (and reduces) B as well; a later slab's verify sees all of
     // B's column maxima, so its B flag equals slab 0's, and it leaves B's
     // column words (read by the GEMMs in flight) untouched
     if ((e = launch_split_pack(kind, kPackUnscaled, dt, 1, (int)packs[(size_t)c], nullptr, nullptr,
+                               nullptr, base, s)) != cudaSuccess)
+      break;
+    if ((e = launch_split_verify(dt, 1, verify_items(tab[(size_t)c].n, p), nullptr, flag, any, kt,
+                                 s, c == 0)) != cudaSuccess)
+      break;
+    if ((e = launch_split_pack(kind, kPackFix, dt, 1, (int)packs[(size_t)c], nullptr, flag, any,
                                base, s)) != cudaSuccess)
-      break;
-    if ((e = launch_split_verify(dt, 1, tab[(size_t)c].n + p, flag, s, c == 0)) != cudaSuccess)
-      break;
-    if ((e = launch_split_pack(kind, kPackFix, dt, 1, (int)packs[(size_t)c], nullptr, flag, base,
-                               s)) != cudaSuccess)
       break;
     if ((e = cudaEventRecord(g_ctx.ev_prep[c], s)) != cudaSuccess) break;
     cudaStream_t t = g_ctx.tc_streams[c & 1];
