@@ -457,6 +457,23 @@ def bench_serving(mm, count: int, rate_frac: float, seed: int = 5, streams: int 
             "batches": batches, "streams": streams, "max_batch": max_batch or 256}
 
 
+def run_grouped_only(args):
+    """Only the grouped leg (config 4) with --grouped-count instances (the
+    first ones of the seeded 4096-instance workload): grouped launch vs one
+    launch per instance.  Prints one JSON line; also the profiling driver of
+    the grouped tensor-core kernel."""
+    import torch
+
+    import paper_1306_6192_gb300 as mm
+    torch.cuda.set_device(0)
+    mm.check_status(mm.mm_init(device=0), "mm_init")
+    stream = torch.cuda.Stream()
+    out = bench_grouped(mm, stream, max(1, args.steps), count=args.grouped_count)
+    mm.mm_shutdown()
+    print(json.dumps({"metric": "grouped GEMM TFLOP/s", "grouped": out}))
+    return 0
+
+
 def run_serve_sweep(args):
     """Config-5 sweep: the Poisson replay at several fractions of the measured
     capacity, batched (2 streams, up to 256 per launch) against one request
@@ -677,6 +694,9 @@ def main(argv=None):
                     help="only the serving rate sweep (config 5)")
     ap.add_argument("--serve-rates", type=float, nargs="*",
                     default=[0.1, 0.25, 0.5, 0.75, 0.9, 1.0, 1.1])
+    ap.add_argument("--grouped-only", action="store_true",
+                    help="only the grouped leg (config 4), --steps grouped launches")
+    ap.add_argument("--grouped-count", type=int, default=4096)
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "mine":
         args.warmup = 3
@@ -684,6 +704,8 @@ def main(argv=None):
         return run_reference(args)
     if args.serve_sweep:
         return run_serve_sweep(args)
+    if args.grouped_only:
+        return run_grouped_only(args)
     return run_mine(args)
 
 

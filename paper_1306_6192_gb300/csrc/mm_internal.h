@@ -17,8 +17,8 @@ namespace mm {
 // ------------------------------------------------------------ tile constants
 // SIMT FP32 tile (the shared-memory tiling of the paper's Listing 4, scaled up
 // with register blocking): 128 x 128 outputs per 256-thread block, 8 x 8 per
-// thread, k-slices of 8.
-constexpr int kSimtF32BM = 128, kSimtF32BN = 128, kSimtF32BK = 8;
+// thread, k-slices of 16.
+constexpr int kSimtF32BM = 128, kSimtF32BN = 128, kSimtF32BK = 16;
 // SIMT FP64 tile: 64 x 64 outputs per 256-thread block, 4 x 4 per thread.
 constexpr int kSimtF64BM = 64, kSimtF64BN = 64, kSimtF64BK = 8;
 

@@ -25,8 +25,11 @@ struct SimtShape {
   static constexpr int NTX = BN / TN, NTY = BM / TM;
   static constexpr int NT = NTX * NTY;
   static constexpr int APAD = W;                  // keeps rows 16-byte aligned
+  static constexpr int VA = BM * BK / W / NT;     // vectors of A per thread and K slice
+  static constexpr int VB = BK * BN / W / NT;     // vectors of B per thread and K slice
   static_assert(TM == 2 * W && TN == 2 * W, "fragment = two 16-byte vectors");
-  static_assert(BM * BK / W == NT && BK * BN / W == NT, "one vector per thread");
+  static_assert(VA >= 1 && VB >= 1 && VA * W * NT == BM * BK && VB * W * NT == BK * BN,
+                "whole vectors per thread");
 };
 
 // Loads W consecutive elements of row `row`, columns col..col+W-1 of a
@@ -53,23 +56,30 @@ __device__ __forceinline__ void load_vec(const T *__restrict__ X, int64_t ld,
   }
 }
 
-template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
+// One BM x BN output tile.  EDGE = false: an interior tile of aligned
+// operands (the tile inside C, m a multiple of BK): every load is a 16-byte
+// vector through a pointer advanced by one K slice per step, no bounds checks.
+// EDGE = true: predicated loads and stores for ragged edges and unaligned
+// operands.
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC, bool EDGE>
 __device__ __forceinline__ void simt_tile(const T *__restrict__ A, const T *__restrict__ B,
                                           T *__restrict__ C, int64_t n, int64_t m, int64_t p,
-                                          int64_t tile_m, int64_t tile_n) {
+                                          int64_t tile_m, int64_t tile_n,
+                                          T (&As)[2][BK][BM + 16 / sizeof(T)], T (&Bs)[2][BK][BN]) {
   using S = SimtShape<T, BM, BN, BK, TM, TN>;
   constexpr int W = S::W;
   using V = typename Vec16<T>::type;
-  __shared__ __align__(16) T As[2][BK][BM + S::APAD];
-  __shared__ __align__(16) T Bs[2][BK][BN];
 
   const int tid = threadIdx.x;
   const int tx = tid % S::NTX, ty = tid / S::NTX;
   const int64_t m0 = tile_m * BM, n0 = tile_n * BN;
 
-  // global -> shared mapping: one W-vector of A (along k) and of B (along n)
-  const int a_row = tid / (BK / W), a_kv = tid % (BK / W);
-  const int b_k = tid / (BN / W), b_nv = tid % (BN / W);
+  // global -> shared mapping: vector v = tid + i*NT holds A row v / (BK/W),
+  // k v % (BK/W) (times W); B k v / (BN/W), columns v % (BN/W) (times W)
+  constexpr int AKV = BK / W, BNV = BN / W;
+  const int a_row = tid / AKV, a_kv = tid % AKV;
+  const int b_k = tid / BNV, b_nv = tid % BNV;
+  constexpr int ROWS_A = S::NT / AKV, KS_B = S::NT / BNV;  // strides between a thread's vectors
 
   T acc[TM][TN];
 #pragma unroll
@@ -77,25 +87,49 @@ __device__ __forceinline__ void simt_tile(const T *__restrict__ A, const T *__re
 #pragma unroll
     for (int j = 0; j < TN; j++) acc[i][j] = T(0);
 
-  T ra[W], rb[W];
+  T ra[S::VA][W], rb[S::VB][W];
+  const T *pa = A + (m0 + a_row) * m + (int64_t)a_kv * W;  // interior pointers
+  const T *pb = B + (int64_t)b_k * p + n0 + (int64_t)b_nv * W;
+  auto load_slice = [&](int64_t k0) {
+    if (!EDGE) {
+#pragma unroll
+      for (int i = 0; i < S::VA; i++)
+        *reinterpret_cast<V *>(ra[i]) = *reinterpret_cast<const V *>(pa + (int64_t)i * ROWS_A * m);
+#pragma unroll
+      for (int i = 0; i < S::VB; i++)
+        *reinterpret_cast<V *>(rb[i]) = *reinterpret_cast<const V *>(pb + (int64_t)i * KS_B * p);
+      pa += BK;
+      pb += (int64_t)BK * p;
+    } else {
+#pragma unroll
+      for (int i = 0; i < S::VA; i++)
+        load_vec<T, VEC>(A, m, n, m, m0 + a_row + i * ROWS_A, k0 + (int64_t)a_kv * W, ra[i]);
+#pragma unroll
+      for (int i = 0; i < S::VB; i++)
+        load_vec<T, VEC>(B, p, m, p, k0 + b_k + i * KS_B, n0 + (int64_t)b_nv * W, rb[i]);
+    }
+  };
+  auto store_slice = [&](int buf) {
+#pragma unroll
+    for (int i = 0; i < S::VA; i++)
+#pragma unroll
+      for (int e = 0; e < W; e++) As[buf][a_kv * W + e][a_row + i * ROWS_A] = ra[i][e];
+#pragma unroll
+    for (int i = 0; i < S::VB; i++)
+      *reinterpret_cast<V *>(&Bs[buf][b_k + i * KS_B][b_nv * W]) = *reinterpret_cast<V *>(rb[i]);
+  };
+
   const int64_t ktiles = (m + BK - 1) / BK;
   if (ktiles > 0) {
-    load_vec<T, VEC>(A, m, n, m, m0 + a_row, (int64_t)a_kv * W, ra);
-    load_vec<T, VEC>(B, p, m, p, (int64_t)b_k, n0 + (int64_t)b_nv * W, rb);
-#pragma unroll
-    for (int e = 0; e < W; e++) As[0][a_kv * W + e][a_row] = ra[e];
-    *reinterpret_cast<V *>(&Bs[0][b_k][b_nv * W]) = *reinterpret_cast<V *>(rb);
+    load_slice(0);
+    store_slice(0);
   }
   __syncthreads();
 
   for (int64_t kt = 0; kt < ktiles; kt++) {
     const int cur = (int)(kt & 1);
     const bool more = kt + 1 < ktiles;
-    if (more) {
-      const int64_t k0 = (kt + 1) * BK;
-      load_vec<T, VEC>(A, m, n, m, m0 + a_row, k0 + (int64_t)a_kv * W, ra);
-      load_vec<T, VEC>(B, p, m, p, k0 + b_k, n0 + (int64_t)b_nv * W, rb);
-    }
+    if (more) load_slice((kt + 1) * BK);
 #pragma unroll
     for (int k = 0; k < BK; k++) {
       T af[TM], bf[TN];
@@ -108,12 +142,7 @@ __device__ __forceinline__ void simt_tile(const T *__restrict__ A, const T *__re
 #pragma unroll
         for (int j = 0; j < TN; j++) acc[i][j] = fma(af[i], bf[j], acc[i][j]);
     }
-    if (more) {
-      const int nxt = cur ^ 1;
-#pragma unroll
-      for (int e = 0; e < W; e++) As[nxt][a_kv * W + e][a_row] = ra[e];
-      *reinterpret_cast<V *>(&Bs[nxt][b_k][b_nv * W]) = *reinterpret_cast<V *>(rb);
-    }
+    if (more) store_slice(cur ^ 1);
     __syncthreads();
   }
 
@@ -123,13 +152,13 @@ __device__ __forceinline__ void simt_tile(const T *__restrict__ A, const T *__re
 #pragma unroll
     for (int i = 0; i < W; i++) {
       const int64_t row = m0 + hi * (BM / 2) + ty * W + i;
-      if (row >= n) continue;
+      if (EDGE && row >= n) continue;
 #pragma unroll
       for (int hj = 0; hj < 2; hj++) {
         const int64_t col = n0 + hj * (BN / 2) + tx * W;
         T *dst = C + row * p + col;
         const T *src = &acc[hi * W + i][hj * W];
-        if (VEC && col + W <= p) {
+        if (!EDGE || (VEC && col + W <= p)) {
           V t;
           T *tp = reinterpret_cast<T *>(&t);
 #pragma unroll
@@ -145,6 +174,20 @@ __device__ __forceinline__ void simt_tile(const T *__restrict__ A, const T *__re
   }
 }
 
+// Interior tiles of aligned operands take the unchecked form.
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
+__device__ __forceinline__ void simt_tile_any(const T *__restrict__ A, const T *__restrict__ B,
+                                              T *__restrict__ C, int64_t n, int64_t m, int64_t p,
+                                              int64_t tile_m, int64_t tile_n) {
+  __shared__ __align__(16) T As[2][BK][BM + 16 / sizeof(T)];  // + pad keeps rows aligned
+  __shared__ __align__(16) T Bs[2][BK][BN];
+  const bool interior = VEC && (tile_m + 1) * BM <= n && (tile_n + 1) * BN <= p && m % BK == 0;
+  if (interior)
+    simt_tile<T, BM, BN, BK, TM, TN, VEC, false>(A, B, C, n, m, p, tile_m, tile_n, As, Bs);
+  else
+    simt_tile<T, BM, BN, BK, TM, TN, VEC, true>(A, B, C, n, m, p, tile_m, tile_n, As, Bs);
+}
+
 // FP32: two blocks per SM (at most 128 registers per thread); FP64: as needed.
 template <typename T> struct MinBlocks { static constexpr int value = sizeof(T) == 4 ? 2 : 1; };
 
@@ -152,7 +195,7 @@ template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
 __global__ void __launch_bounds__(256, MinBlocks<T>::value)
 simt_gemm_kernel(const T *__restrict__ A, const T *__restrict__ B, T *__restrict__ C,
                  int64_t n, int64_t m, int64_t p) {
-  simt_tile<T, BM, BN, BK, TM, TN, VEC>(A, B, C, n, m, p, blockIdx.y, blockIdx.x);
+  simt_tile_any<T, BM, BN, BK, TM, TN, VEC>(A, B, C, n, m, p, blockIdx.y, blockIdx.x);
 }
 
 // Grouped form: one block per output tile over all problems of a table; the
@@ -168,7 +211,7 @@ simt_grouped_kernel(const SimtProb *__restrict__ probs, int nprobs) {
   }
   const SimtProb &pr = probs[lo];
   const int local = t - pr.tile_start;
-  simt_tile<T, BM, BN, BK, TM, TN, VEC>(
+  simt_tile_any<T, BM, BN, BK, TM, TN, VEC>(
       static_cast<const T *>(pr.A), static_cast<const T *>(pr.B), static_cast<T *>(pr.C),
       pr.n, pr.m, pr.p, local / pr.tiles_n, local % pr.tiles_n);
 }

@@ -180,7 +180,7 @@ __device__ __forceinline__ uint32_t half_warp_max(uint32_t v) {
 // four of a 64-column slice of B), then splits and stores them, so that each
 // thread keeps several loads in flight.
 template <int PARTS, int MODE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 split_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *__restrict__ map,
                   const int *__restrict__ flags, const int *__restrict__ any, int total_tiles,
                   uint2 *__restrict__ pack) {

@@ -24,8 +24,8 @@
 //   warps 2-5 epilogue: tcgen05.ld of the accumulator (each warp reads its
 //             32 TMEM lanes = 32 rows), exact power-of-two unscaling, FP32
 //             stores with edge predication; then "acc_empty".
-// Two accumulators of 256 TMEM columns each let the epilogue of one tile
-// overlap the mainloop of the next.  Tiles of all problems of a table are
+// Two accumulators of 256 TMEM columns each (four of 128 in the 128-wide
+// layouts) let the epilogue of one tile overlap the mainloop of the next.  Tiles of all problems of a table are
 // visited in a static stride over the CTAs, grouped in bands of group_m row
 // tiles for L2 reuse.
 // Tail split: where a product's tile count leaves the last wave of the
@@ -50,8 +50,7 @@ namespace mm {
 namespace {
 
 constexpr int kThreads = 192;
-constexpr int kAccCols = 256;               // TMEM columns per accumulator
-constexpr uint32_t kTmemCols = 2 * kAccCols;
+constexpr uint32_t kTmemCols = 512;         // all of TMEM: the accumulators
 constexpr int kBoxRows = 128;               // TMA box height (rows of the pack)
 constexpr int kMaxSplit = 4;                // most K parts of a tail-split tile
 constexpr uint64_t kWaitLimitNs = 4000000000ull;
@@ -309,9 +308,12 @@ struct TcLayout {
   static constexpr int kBPartMax = kMaxBN * BKB;        // one part of B at bn = MAXBN
   static constexpr int kStageBytes = kParts * (kAPart + kBPartMax);
   static constexpr int kBarOffset = STAGES * kStageBytes;
-  static constexpr int kNumBars = 2 * STAGES + 4 + 1;  // full, empty, acc_full/empty, drain
-  static constexpr int kColExpOffset = kBarOffset + kNumBars * 8 + 16;  // int[2][kMaxBN]
-  static constexpr int kLastOffset = kColExpOffset + 2 * kMaxBN * 4;   // int: last-part flag
+  // accumulators of MAXBN TMEM columns: two at MAXBN = 256, four at 128, so
+  // that the epilogues of short tiles can lag the MMAs by several tiles
+  static constexpr int kNumAcc = (int)kTmemCols / kMaxBN;
+  static constexpr int kNumBars = 2 * STAGES + 2 * kNumAcc + 1;  // full, empty, acc f/e, drain
+  static constexpr int kColExpOffset = kBarOffset + kNumBars * 8 + 16;  // int[kNumAcc][kMaxBN]
+  static constexpr int kLastOffset = kColExpOffset + kNumAcc * kMaxBN * 4;  // last-part flag
   // epilogue staging: one 32 x 33 float block per epilogue warp
   static constexpr int kStageOffset = kLastOffset + 16;
   static constexpr int kSmemBytes = kStageOffset + 4 * 32 * 33 * 4 + 1024;  // + align slack
@@ -331,10 +333,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
   auto full_bar = [&](int s) { return bars + 8u * s; };
   auto empty_bar = [&](int s) { return bars + 8u * (STAGES + s); };
   auto accf_bar = [&](int a) { return bars + 8u * (2 * STAGES + a); };
-  auto acce_bar = [&](int a) { return bars + 8u * (2 * STAGES + 2 + a); };
-  const uint32_t drain_bar = bars + 8u * (2 * STAGES + 4);
+  auto acce_bar = [&](int a) { return bars + 8u * (2 * STAGES + L::kNumAcc + a); };
+  const uint32_t drain_bar = bars + 8u * (2 * STAGES + 2 * L::kNumAcc);
   uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(smem + L::kBarOffset + L::kNumBars * 8);
-  int *colexp = reinterpret_cast<int *>(smem + L::kColExpOffset);  // [2][MAXBN]
+  int *colexp = reinterpret_cast<int *>(smem + L::kColExpOffset);  // [kNumAcc][MAXBN]
   volatile int *last_flag = reinterpret_cast<volatile int *>(smem + L::kLastOffset);
   float *stage_buf = reinterpret_cast<float *>(smem + L::kStageOffset);
 
@@ -349,7 +351,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), 1);
     }
-    for (int a = 0; a < 2; a++) {
+    for (int a = 0; a < L::kNumAcc; a++) {
       mbar_init(accf_bar(a), 1);
       mbar_init(acce_bar(a), 4 * 32);
     }
@@ -436,7 +438,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
           break;
         }
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * kAccCols);
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * MAXBN);
         for (int ki = k0; ki < k1; ki++) {
           if (!mbar_wait(full_bar(stage), phase, err, 3, true, kWaitLimitNs)) {
             ok = false;
@@ -484,7 +486,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
         }
         if (!ok) break;
         tc_commit(accf_bar(acc));
-        if (++acc == 2) {
+        if (++acc == L::kNumAcc) {
           acc = 0;
           acc_phase ^= 1u;
         }
@@ -521,7 +523,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
       const int si = (row_ok && (fl & kFlagScaleA)) ? kind_exponent<KIND>(pr.sA[i]) : 0;
       float *buf = stage_buf + q * 32 * 33;  // this warp's 32 x 32 block (row pitch 33)
       const int64_t row0 = (int64_t)tc.mt * kTcBM + q * 32;  // first row of the warp
-      const uint32_t tacc = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kAccCols);
+      const uint32_t tacc = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * MAXBN);
       // part of a split tile: a partial slot holds bn/4 groups of 4 columns,
       // each group 128 rows x 4 floats, so that a warp's 16-byte accesses to
       // one group (32 rows) are 512 consecutive bytes
@@ -621,7 +623,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
       }
       tc_fence_before();
       mbar_arrive(acce_bar(acc));
-      if (++acc == 2) {
+      if (++acc == L::kNumAcc) {
         acc = 0;
         acc_phase ^= 1u;
       }
