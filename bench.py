@@ -306,8 +306,25 @@ def bench_paper_workloads(mm, stream, peaks, n: int = 4096, reps: int = 5):
     ms = kernel_ms("diag", lambda: ok(mm.mm_diag(n, n, A, d, C, 0, mm.MM_F32), "diag"))
     out["diag_gbs"] = (2 * 4 * n * n + 4 * n) / (ms * 1e-3) / 1e9
     out["diag_frac_hbm"] = out["diag_gbs"] / hbm
-    out["note"] = ("products: synchronous calls timed on the host; add / diag: kernel time from "
-                   "the library's event tracer; add moves 192 MB and diag 128 MB per call")
+    # the same kernels on 8192^2 operands, where the ~10 us between a synchronous
+    # call's first trace event and its kernel weighs less
+    del A, B, C
+    n2 = 2 * n
+    A2 = torch.rand((n2, n2), device="cuda", generator=gen)
+    B2 = torch.rand((n2, n2), device="cuda", generator=gen)
+    C2 = torch.empty((n2, n2), device="cuda")
+    d2 = A2[0].contiguous()
+    ms = kernel_ms("add", lambda: ok(mm.mm_add(n2, n2, 1.0, A2, -1.0, B2, C2, mm.MM_F32), "add"))
+    out["add_gbs_%d" % n2] = 3 * 4 * n2 * n2 / (ms * 1e-3) / 1e9
+    out["add_frac_hbm_%d" % n2] = out["add_gbs_%d" % n2] / hbm
+    ms = kernel_ms("diag", lambda: ok(mm.mm_diag(n2, n2, A2, d2, C2, 0, mm.MM_F32), "diag"))
+    out["diag_gbs_%d" % n2] = (2 * 4 * n2 * n2 + 4 * n2) / (ms * 1e-3) / 1e9
+    out["diag_frac_hbm_%d" % n2] = out["diag_gbs_%d" % n2] / hbm
+    del A2, B2, C2
+    out["note"] = ("products: synchronous calls timed on the host; add / diag: time from the "
+                   "library's event tracer, which includes the launch latency of a synchronous "
+                   "call (~10 us); add moves 192 MB (768 MB at 8192^2) and diag 128 MB (512 MB) "
+                   "per call")
     return out
 
 

@@ -51,13 +51,16 @@ add_kernel(const T *__restrict__ a, const T *__restrict__ b, T *__restrict__ c, 
   }
 }
 
-// The 16-byte kernels below keep kEwUnroll vectors of each operand in
-// flight per thread (loads first, then the stores), with streaming cache
-// hints: every byte is touched once, so nothing is worth keeping in L2.
+// The 16-byte kernels below give each block one contiguous run of
+// 256 * kEwUnroll vectors (thread t takes vectors t, t + 256, ...): all loads
+// of a thread are issued before its stores, and consecutive blocks sweep
+// memory in order.  (Measured on GB300 against a persistent grid-stride form
+// of the same loop: 5.9 vs 5.5 TB/s at 4096^2, 7.2 vs 6.8 TB/s at 16384^2.)
 constexpr int kEwUnroll = 4;
+constexpr int kEwThreads = 256;
 
 // 16-byte variant for aligned float operands
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kEwThreads)
 add4_kernel(const float4 *__restrict__ a, const float4 *__restrict__ b, float4 *__restrict__ c,
             float alpha, float beta, int64_t count4, bool unit) {
   auto op = [&](const float4 &x, const float4 &y) {
@@ -66,19 +69,21 @@ add4_kernel(const float4 *__restrict__ a, const float4 *__restrict__ b, float4 *
     return make_float4(fmaf(alpha, x.x, beta * y.x), fmaf(alpha, x.y, beta * y.y),
                        fmaf(alpha, x.z, beta * y.z), fmaf(alpha, x.w, beta * y.w));
   };
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  for (; i + (kEwUnroll - 1) * stride < count4; i += kEwUnroll * stride) {
-    float4 x[kEwUnroll], y[kEwUnroll];
+  const int64_t base = (int64_t)blockIdx.x * kEwThreads * kEwUnroll + threadIdx.x;
+  float4 x[kEwUnroll], y[kEwUnroll];
 #pragma unroll
-    for (int u = 0; u < kEwUnroll; u++) {
-      x[u] = __ldcs(a + i + u * stride);
-      y[u] = __ldcs(b + i + u * stride);
+  for (int u = 0; u < kEwUnroll; u++) {
+    const int64_t i = base + (int64_t)u * kEwThreads;
+    if (i < count4) {
+      x[u] = a[i];
+      y[u] = b[i];
     }
-#pragma unroll
-    for (int u = 0; u < kEwUnroll; u++) __stcs(c + i + u * stride, op(x[u], y[u]));
   }
-  for (; i < count4; i += stride) __stcs(c + i, op(__ldcs(a + i), __ldcs(b + i)));
+#pragma unroll
+  for (int u = 0; u < kEwUnroll; u++) {
+    const int64_t i = base + (int64_t)u * kEwThreads;
+    if (i < count4) c[i] = op(x[u], y[u]);
+  }
 }
 
 // side 0: C[i][j] = X[i][j] * d[j];  side 1: C[i][j] = d[i] * X[i][j].
@@ -97,56 +102,47 @@ diag_kernel(const T *__restrict__ x, const T *__restrict__ d, T *__restrict__ c,
   }
 }
 
-// 16-byte form for aligned float operands with p % 4 == 0: a flat grid-
-// stride loop over the n * p4 vectors (p4 = p / 4); each thread tracks the
-// (row, vector column) of its position and advances it by the stride's
-// quotient and remainder, so no division runs in the loop.
-__global__ void __launch_bounds__(256)
+// 16-byte form for aligned float operands with p % 4 == 0: vectors of the
+// flat n * p4 range (p4 = p / 4) in the same contiguous runs as add4_kernel;
+// each thread finds the (row, vector column) of its first vector and advances
+// it by the block width's quotient and remainder, so no division runs per
+// vector.
+__global__ void __launch_bounds__(kEwThreads)
 diag4_kernel(const float4 *__restrict__ x, const float *__restrict__ d, float4 *__restrict__ c,
              int64_t n, int64_t p4, int side) {
   const int64_t count4 = n * p4;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t s_row = stride / p4, s_col = stride % p4;
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t r = i / p4, j = i % p4;
-  auto advance = [&](int64_t &rr, int64_t &jj) {
-    rr += s_row;
-    jj += s_col;
-    if (jj >= p4) {
-      jj -= p4;
-      rr++;
-    }
-  };
-  auto scale = [&](const float4 &v, int64_t rr, int64_t jj) {
-    const float4 s4 = side == 0 ? __ldg(reinterpret_cast<const float4 *>(d) + jj)
-                                : make_float4(d[rr], d[rr], d[rr], d[rr]);
-    return make_float4(v.x * s4.x, v.y * s4.y, v.z * s4.z, v.w * s4.w);
-  };
-  for (; i + (kEwUnroll - 1) * stride < count4; i += kEwUnroll * stride) {
-    float4 v[kEwUnroll];
-    int64_t rs[kEwUnroll], js[kEwUnroll];
+  const int64_t base = (int64_t)blockIdx.x * kEwThreads * kEwUnroll + threadIdx.x;
+  const int64_t s_row = kEwThreads / p4, s_col = kEwThreads % p4;
+  int64_t r = base / p4, j = base % p4;
+  float4 v[kEwUnroll];
+  int64_t rs[kEwUnroll], js[kEwUnroll];
 #pragma unroll
-    for (int u = 0; u < kEwUnroll; u++) {
-      v[u] = __ldcs(x + i + u * stride);
-      rs[u] = r;
-      js[u] = j;
-      advance(r, j);
+  for (int u = 0; u < kEwUnroll; u++) {
+    const int64_t i = base + (int64_t)u * kEwThreads;
+    if (i < count4) v[u] = x[i];
+    rs[u] = r;
+    js[u] = j;
+    r += s_row;
+    j += s_col;
+    if (j >= p4) {
+      j -= p4;
+      r++;
     }
-#pragma unroll
-    for (int u = 0; u < kEwUnroll; u++) __stcs(c + i + u * stride, scale(v[u], rs[u], js[u]));
   }
-  for (; i < count4; i += stride) {
-    __stcs(c + i, scale(__ldcs(x + i), r, j));
-    advance(r, j);
+#pragma unroll
+  for (int u = 0; u < kEwUnroll; u++) {
+    const int64_t i = base + (int64_t)u * kEwThreads;
+    if (i >= count4) continue;
+    const float4 s4 = side == 0 ? __ldg(reinterpret_cast<const float4 *>(d) + js[u])
+                                : make_float4(d[rs[u]], d[rs[u]], d[rs[u]], d[rs[u]]);
+    c[i] = make_float4(v[u].x * s4.x, v[u].y * s4.y, v[u].z * s4.z, v[u].w * s4.w);
   }
 }
 
-// Persistent grid for the 16-byte kernels: full occupancy (8 blocks of 256
-// threads per SM), fewer when the vectors run out.
-int grid_ew(int64_t count4) {
-  const int64_t want = (count4 + 256 * kEwUnroll - 1) / (256 * kEwUnroll);
-  const int64_t cap = (int64_t)sm_count() * 8;
-  return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+// Grid of the 16-byte kernels: one block per run of 256 * kEwUnroll vectors.
+int64_t grid_ew(int64_t count4) {
+  const int64_t g = (count4 + (int64_t)kEwThreads * kEwUnroll - 1) / ((int64_t)kEwThreads * kEwUnroll);
+  return g > 0 ? g : 1;
 }
 
 int grid_for(int64_t count) {
@@ -230,7 +226,7 @@ mm_status mm_add(int64_t n, int64_t p, double alpha, const void *A, double beta,
     const bool vec = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) |
                        reinterpret_cast<uintptr_t>(C)) & 15) == 0 && count % 4 == 0;
     if (vec)
-      add4_kernel<<<grid_ew(count / 4), 256, 0, s>>>(
+      add4_kernel<<<(unsigned)grid_ew(count / 4), kEwThreads, 0, s>>>(
           static_cast<const float4 *>(A), static_cast<const float4 *>(B), static_cast<float4 *>(C),
           (float)alpha, (float)beta, count / 4, unit);
     else
@@ -265,7 +261,7 @@ mm_status mm_diag(int64_t n, int64_t p, const void *X, const void *d, void *C, i
             (unsigned)std::min<int64_t>(n, 65535));
   TraceScope ts("diag", s);
   if (vec)
-    diag4_kernel<<<grid_ew(n * (p / 4)), 256, 0, s>>>(static_cast<const float4 *>(X),
+    diag4_kernel<<<(unsigned)grid_ew(n * (p / 4)), kEwThreads, 0, s>>>(static_cast<const float4 *>(X),
                                                       static_cast<const float *>(d),
                                                       static_cast<float4 *>(C), n, p / 4, side);
   else if (dt == MM_F32)

@@ -24,7 +24,11 @@ struct SimtShape {
   static constexpr int W = 16 / (int)sizeof(T);  // elements per 16-byte vector
   static constexpr int NTX = BN / TN, NTY = BM / TM;
   static constexpr int NT = NTX * NTY;
-  static constexpr int APAD = W;                  // keeps rows 16-byte aligned
+  // FP32: A's shared tile is unpadded and its 4-float groups are XOR-swizzled
+  // by the K index (conflict-free transposing stores, aligned 16-byte reads);
+  // FP64: rows padded by one 16-byte vector
+  static constexpr bool SWZ = sizeof(T) == 4 && BK == 16 && BM % 32 == 0;
+  static constexpr int APAD = SWZ ? 0 : W;
   static constexpr int VA = BM * BK / W / NT;     // vectors of A per thread and K slice
   static constexpr int VB = BK * BN / W / NT;     // vectors of B per thread and K slice
   static_assert(TM == 2 * W && TN == 2 * W, "fragment = two 16-byte vectors");
@@ -65,7 +69,8 @@ template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC, bool EDG
 __device__ __forceinline__ void simt_tile(const T *__restrict__ A, const T *__restrict__ B,
                                           T *__restrict__ C, int64_t n, int64_t m, int64_t p,
                                           int64_t tile_m, int64_t tile_n,
-                                          T (&As)[2][BK][BM + 16 / sizeof(T)], T (&Bs)[2][BK][BN]) {
+                                          T (&As)[2][BK][BM + SimtShape<T, BM, BN, BK, TM, TN>::APAD],
+                                          T (&Bs)[2][BK][BN]) {
   using S = SimtShape<T, BM, BN, BK, TM, TN>;
   constexpr int W = S::W;
   using V = typename Vec16<T>::type;
@@ -109,11 +114,17 @@ __device__ __forceinline__ void simt_tile(const T *__restrict__ A, const T *__re
         load_vec<T, VEC>(B, p, m, p, k0 + b_k + i * KS_B, n0 + (int64_t)b_nv * W, rb[i]);
     }
   };
+  // column of A's shared tile for row r at K index k: groups of 4 rows XOR
+  // 2 * (k / 4) under SWZ (a warp's stores then hit 32 different banks)
+  auto acol = [](int k, int r) {
+    return S::SWZ ? ((((r >> 2) ^ (((k >> 2) & 3) << 1)) << 2) | (r & 3)) : r;
+  };
   auto store_slice = [&](int buf) {
 #pragma unroll
     for (int i = 0; i < S::VA; i++)
 #pragma unroll
-      for (int e = 0; e < W; e++) As[buf][a_kv * W + e][a_row + i * ROWS_A] = ra[i][e];
+      for (int e = 0; e < W; e++)
+        As[buf][a_kv * W + e][acol(a_kv * W + e, a_row + i * ROWS_A)] = ra[i][e];
 #pragma unroll
     for (int i = 0; i < S::VB; i++)
       *reinterpret_cast<V *>(&Bs[buf][b_k + i * KS_B][b_nv * W]) = *reinterpret_cast<V *>(rb[i]);
@@ -133,8 +144,9 @@ __device__ __forceinline__ void simt_tile(const T *__restrict__ A, const T *__re
 #pragma unroll
     for (int k = 0; k < BK; k++) {
       T af[TM], bf[TN];
-      *reinterpret_cast<V *>(&af[0]) = *reinterpret_cast<const V *>(&As[cur][k][ty * W]);
-      *reinterpret_cast<V *>(&af[W]) = *reinterpret_cast<const V *>(&As[cur][k][BM / 2 + ty * W]);
+      *reinterpret_cast<V *>(&af[0]) = *reinterpret_cast<const V *>(&As[cur][k][acol(k, ty * W)]);
+      *reinterpret_cast<V *>(&af[W]) =
+          *reinterpret_cast<const V *>(&As[cur][k][acol(k, BM / 2 + ty * W)]);
       *reinterpret_cast<V *>(&bf[0]) = *reinterpret_cast<const V *>(&Bs[cur][k][tx * W]);
       *reinterpret_cast<V *>(&bf[W]) = *reinterpret_cast<const V *>(&Bs[cur][k][BN / 2 + tx * W]);
 #pragma unroll
@@ -179,7 +191,7 @@ template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
 __device__ __forceinline__ void simt_tile_any(const T *__restrict__ A, const T *__restrict__ B,
                                               T *__restrict__ C, int64_t n, int64_t m, int64_t p,
                                               int64_t tile_m, int64_t tile_n) {
-  __shared__ __align__(16) T As[2][BK][BM + 16 / sizeof(T)];  // + pad keeps rows aligned
+  __shared__ __align__(16) T As[2][BK][BM + SimtShape<T, BM, BN, BK, TM, TN>::APAD];
   __shared__ __align__(16) T Bs[2][BK][BN];
   const bool interior = VEC && (tile_m + 1) * BM <= n && (tile_n + 1) * BN <= p && m % BK == 0;
   if (interior)

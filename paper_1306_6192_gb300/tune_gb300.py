@@ -1,7 +1,8 @@
 """Generates the shipped tuning table of the split path on a GB300.
 
 Runs the library's autotuner (mm_tune: times every candidate tile width, K
-depth / pipeline depth and raster band height on the device) for one
+depth / pipeline depth, raster band height and tail split on or off on the
+device) for one
 representative size per bucket and writes the table next to this file
 (tune_gb300.txt), which the binding loads at mm_init.  Buckets are
 (ceil(log2 n), ceil(log2 m), ceil(log2 p)).

@@ -102,3 +102,32 @@ def test_tail_deterministic_and_batch_invariant(mmlib):
                                 mm.MM_MODE_SPLIT_BF16X3)
         assert st == 0
         assert np.array_equal(Cg.cpu().numpy(), outs[0])
+
+
+def test_tail_three_part_kind(mmlib):
+    """m = 2100 (< 2237) takes the three-part split (six products); with 320
+    tiles the last wave is split too.  Integer inputs stay exact; uniform
+    inputs stay within the tolerance on sampled entries and Freivalds."""
+    n, m, p = 5000, 2100, 1024
+    tiles, f, s = _plan(mmlib, (n, m, p))
+    assert s > 1 and 0 < f < tiles
+    A = synth.small_ints(2501, (n, m))
+    B = synth.small_ints(2502, (m, p))
+    C = run_gemm(mmlib, A, B, mmlib.MM_MODE_SPLIT_BF16X3)
+    assert np.array_equal(C.astype(np.float64), A.astype(np.float64) @ B.astype(np.float64))
+    A = synth.uniform_pm1(2503, (n, m))
+    B = synth.uniform_pm1(2504, (m, p))
+    C = run_gemm(mmlib, A, B, mmlib.MM_MODE_SPLIT_BF16X3)
+    sampled_check(C, A, B, "f32")
+
+
+def test_tail_fp8_small_integers(mmlib):
+    """The e4m3 path plans its tail from its own K blocks (128 values per pack
+    row); at 5120 x 8192 x 1024 (160 tiles of 128 x 256, 64 K blocks) its last
+    wave is split.  Small integers are exact through e4m3 and through the
+    ordered sum of the parts (|c| <= 8192 * 64 < 2^24)."""
+    n, m, p = 5120, 8192, 1024
+    A = synth.small_ints(2601, (n, m))
+    B = synth.small_ints(2602, (m, p))
+    C = run_gemm(mmlib, A, B, mmlib.MM_MODE_FP8)
+    assert np.array_equal(C.astype(np.float64), A.astype(np.float64) @ B.astype(np.float64))
