@@ -213,6 +213,19 @@ mm_status mm_tune_query(int64_t n, int64_t m, int64_t p, int *bn, int *bk,
 mm_status mm_tune_query_tail(int64_t n, int64_t m, int64_t p, int *tiles,
                              int *split_from, int *split_s);
 
+/* The tail-split planner itself, a pure host function (no device, no
+ * mm_init): for a product of `tiles` output tiles of 128 x bn, kt pack rows
+ * of K (64 bf16 or 128 e4m3 values each), inner dimension m and `products`
+ * bf16 products per K step (3 or 6 for the split kinds, 0.5 for e4m3) on
+ * `grid` persistent CTAs, writes the first split tile and the number of K
+ * parts (1: no split).  It picks the split that minimises a makespan model of
+ * the round-robin assignment of work units to CTAs: at most 4 parts, at
+ * least 2 pack rows per part, at most 2 x grid split units, and no split for
+ * products with fewer tiles than CTAs and fewer than 32 pack rows.
+ * Returns MM_EINVAL for negative sizes or NULL outputs. */
+mm_status mm_tail_plan(int64_t tiles, int grid, int kt, int bn, int64_t m,
+                       double products, int *split_from, int *split_s);
+
 /* ----------------------------------------------------------------- tracing */
 
 /* When enabled, every kernel the library launches is bracketed by CUDA events

@@ -79,6 +79,8 @@ def lib():
         L.mm_tune_load.argtypes = [ctypes.c_char_p]
         L.mm_tune_query.argtypes = [_i64, _i64, _i64] + [ctypes.POINTER(ctypes.c_int)] * 4
         L.mm_tune_query_tail.argtypes = [_i64, _i64, _i64] + [ctypes.POINTER(ctypes.c_int)] * 3
+        L.mm_tail_plan.argtypes = [_i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64,
+                                   ctypes.c_double] + [ctypes.POINTER(ctypes.c_int)] * 2
         L.mm_trace_enable.argtypes = [ctypes.c_int]
         L.mm_trace_reset.argtypes = []
         L.mm_trace_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(_i64), _dp]
@@ -94,7 +96,7 @@ def lib():
         for name in ("mm_init", "mm_shutdown", "mm_gemm", "mm_gemm_async", "mm_gemm_grouped",
                      "mm_gemm_grouped_async", "mm_sync", "mm_check", "mm_submit", "mm_poll",
                      "mm_wait", "mm_serve_stats", "mm_tune", "mm_tune_save", "mm_tune_load",
-                     "mm_tune_query", "mm_tune_query_tail", "mm_trace_enable",
+                     "mm_tune_query", "mm_tune_query_tail", "mm_tail_plan", "mm_trace_enable",
                      "mm_trace_reset", "mm_trace_read"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -252,6 +254,15 @@ def mm_tune_query_tail(n, m, p):
     v = [ctypes.c_int(0) for _ in range(3)]
     st = lib().mm_tune_query_tail(n, m, p, *[ctypes.byref(x) for x in v])
     return (st,) + tuple(x.value for x in v)
+
+
+def mm_tail_plan(tiles, grid, kt, bn, m, products):
+    """Returns (status, split_from, split_s) of the tail-split planner (a
+    pure host function; no GPU needed)."""
+    a, b = ctypes.c_int(0), ctypes.c_int(0)
+    st = lib().mm_tail_plan(tiles, grid, kt, bn, m, float(products), ctypes.byref(a),
+                            ctypes.byref(b))
+    return st, a.value, b.value
 
 
 def mm_trace_enable(on: bool = True) -> int:

@@ -375,3 +375,14 @@ extern "C" mm_status mm_tune_query_tail(int64_t n, int64_t m, int64_t p, int *ti
   if (split_s) *split_s = tail.split_s;
   return MM_OK;
 }
+
+extern "C" mm_status mm_tail_plan(int64_t tiles, int grid, int kt, int bn, int64_t m,
+                                  double products, int *split_from, int *split_s) {
+  if (tiles < 0 || tiles > 0x7fffffffLL || grid < 0 || kt < 0 || bn <= 0 || m < 0 ||
+      !(products > 0.0) || !split_from || !split_s)
+    return MM_EINVAL;
+  const TcTail t = tc_tail_plan(tiles, grid, kt, bn, m, products);
+  *split_from = t.split_s > 1 ? t.split_from : (int)tiles;
+  *split_s = t.split_s > 1 ? t.split_s : 1;
+  return MM_OK;
+}
