@@ -22,12 +22,15 @@
 //             e4m3 - and commits each stage back to the producer ("empty")
 //             and each finished tile to the epilogue ("acc_full").
 //   warps 2-5 epilogue: tcgen05.ld of the accumulator (each warp reads its
-//             32 TMEM lanes = 32 rows), exact power-of-two unscaling, FP32
-//             stores with edge predication; then "acc_empty".
+//             32 TMEM lanes = 32 rows), exact power-of-two unscaling, each
+//             32 x 32 block through shared memory so that every global store
+//             is one whole 128-byte line of a row (edge rows and columns
+//             predicated); then "acc_empty".
 // Two accumulators of 256 TMEM columns each (four of 128 in the 128-wide
-// layouts) let the epilogue of one tile overlap the mainloop of the next.  Tiles of all problems of a table are
-// visited in a static stride over the CTAs, grouped in bands of group_m row
-// tiles for L2 reuse.
+// layouts) let the epilogue of one tile overlap the mainloop of the next.
+// The work units (tiles, or K parts of split tiles) of all problems of a
+// table are visited in a static stride over the CTAs, the tiles of a problem
+// in bands of group_m row tiles for L2 reuse.
 // Tail split: where a product's tile count leaves the last wave of the
 // persistent grid partly empty, the host cuts that product's last tiles into
 // split_s parts along K (a plan fixed by the product's own shape, so a

@@ -131,3 +131,20 @@ def test_tail_fp8_small_integers(mmlib):
     B = synth.small_ints(2602, (m, p))
     C = run_gemm(mmlib, A, B, mmlib.MM_MODE_FP8)
     assert np.array_equal(C.astype(np.float64), A.astype(np.float64) @ B.astype(np.float64))
+
+
+def test_tail_with_scaled_operands(mmlib):
+    """Rows of A at 2^-70 / 2^60 and columns of B at 2^-45 / 2^45 (outside
+    the range packed unscaled, and every product still a normal FP32 number)
+    force the re-pack of both operands with power-of-two scales; the split
+    tiles' parts are summed unscaled and the row and column scales applied
+    once to the sum.  Every tile is split here (1000 x 3000 x 1000), and the
+    full oracle checks every entry."""
+    n, m, p = ALL_SPLIT
+    ea = synth.row_scale_exponents(2701, n, choices=(-70, 60))
+    eb = synth.row_scale_exponents(2702, p, choices=(-45, 45))
+    A = (synth.uniform_pm1(2703, (n, m)).astype(np.float64) * np.ldexp(1.0, ea)[:, None]).astype(np.float32)
+    B = (synth.uniform_pm1(2704, (m, p)).astype(np.float64) * np.ldexp(1.0, eb)[None, :]).astype(np.float32)
+    C = run_gemm(mmlib, A, B, mmlib.MM_MODE_SPLIT_BF16X3)
+    assert np.all(np.isfinite(C))
+    assert_full(C, A, B, "f32")
