@@ -300,12 +300,33 @@ def bench_paper_workloads(mm, stream, peaks, n: int = 4096, reps: int = 5):
         mm.mm_trace_reset()
         return tot / max(k, 1)
 
+    def queued_ms(fn, k=20):
+        # asynchronous calls queued back to back on one stream, timed by events
+        # around all of them: kernel time without a synchronous call's launch
+        # latency
+        fn()
+        mm.check_status(mm.mm_sync(stream), "sync")
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
     ms = kernel_ms("add", lambda: ok(mm.mm_add(n, n, 1.0, A, -1.0, B, C, mm.MM_F32), "add"))
     out["add_gbs"] = 3 * 4 * n * n / (ms * 1e-3) / 1e9
     out["add_frac_hbm"] = out["add_gbs"] / hbm
     ms = kernel_ms("diag", lambda: ok(mm.mm_diag(n, n, A, d, C, 0, mm.MM_F32), "diag"))
     out["diag_gbs"] = (2 * 4 * n * n + 4 * n) / (ms * 1e-3) / 1e9
     out["diag_frac_hbm"] = out["diag_gbs"] / hbm
+    ms = queued_ms(lambda: ok(mm.mm_add_async(n, n, 1.0, A, -1.0, B, C, mm.MM_F32, stream), "add"))
+    out["add_gbs_queued"] = 3 * 4 * n * n / (ms * 1e-3) / 1e9
+    out["add_frac_hbm_queued"] = out["add_gbs_queued"] / hbm
+    ms = queued_ms(lambda: ok(mm.mm_diag_async(n, n, A, d, C, 0, mm.MM_F32, stream), "diag"))
+    out["diag_gbs_queued"] = (2 * 4 * n * n + 4 * n) / (ms * 1e-3) / 1e9
+    out["diag_frac_hbm_queued"] = out["diag_gbs_queued"] / hbm
     # the same kernels on 8192^2 operands, where the ~10 us between a synchronous
     # call's first trace event and its kernel weighs less
     del A, B, C
@@ -323,8 +344,9 @@ def bench_paper_workloads(mm, stream, peaks, n: int = 4096, reps: int = 5):
     del A2, B2, C2
     out["note"] = ("products: synchronous calls timed on the host; add / diag: time from the "
                    "library's event tracer, which includes the launch latency of a synchronous "
-                   "call (~10 us); add moves 192 MB (768 MB at 8192^2) and diag 128 MB (512 MB) "
-                   "per call")
+                   "call (~10 us); *_queued: 20 asynchronous calls queued on one stream, timed "
+                   "by events around all of them; add moves 192 MB (768 MB at 8192^2) and diag "
+                   "128 MB (512 MB) per call")
     return out
 
 

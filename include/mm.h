@@ -268,6 +268,16 @@ mm_status mm_add(int64_t n, int64_t p, double alpha, const void *A, double beta,
 mm_status mm_diag(int64_t n, int64_t p, const void *X, const void *d, void *C,
                   int side, mm_dtype dt);
 
+/* Asynchronous forms of mm_add and mm_diag: the same arguments plus `stream`
+ * (a cudaStream_t; NULL = the library stream).  They validate the arguments,
+ * queue the kernel and return; C is complete when the stream reaches that
+ * point (mm_sync(stream), or any later work on the stream).  A failure of
+ * the kernel itself shows at the next synchronising call. */
+mm_status mm_add_async(int64_t n, int64_t p, double alpha, const void *A, double beta,
+                       const void *B, void *C, mm_dtype dt, void *stream);
+mm_status mm_diag_async(int64_t n, int64_t p, const void *X, const void *d, void *C,
+                        int side, mm_dtype dt, void *stream);
+
 /* ------------------------------------------------ allocation-free variant */
 
 /* The FP32 split product of mm_gemm's MM_MODE_SPLIT_BF16X3 path, for callers

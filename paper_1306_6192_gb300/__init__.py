@@ -89,7 +89,10 @@ def lib():
         L.mm_cgemm.argtypes = [_i64, _i64, _i64, _vp, _vp, _vp, st]
         L.mm_add.argtypes = [_i64, _i64, ctypes.c_double, _vp, ctypes.c_double, _vp, _vp, st]
         L.mm_diag.argtypes = [_i64, _i64, _vp, _vp, _vp, ctypes.c_int, st]
-        for name in ("mm_cgemm", "mm_add", "mm_diag"):
+        L.mm_add_async.argtypes = [_i64, _i64, ctypes.c_double, _vp, ctypes.c_double, _vp, _vp, st,
+                                   _vp]
+        L.mm_diag_async.argtypes = [_i64, _i64, _vp, _vp, _vp, ctypes.c_int, st, _vp]
+        for name in ("mm_cgemm", "mm_add", "mm_diag", "mm_add_async", "mm_diag_async"):
             getattr(L, name).restype = ctypes.c_int
         L.mm_gemm_split_static.argtypes = [_i64, _i64, _i64, _vp, _vp, _vp, _vp]
         L.mm_gemm_split_static.restype = ctypes.c_int
@@ -298,6 +301,15 @@ def mm_add(n, p, alpha, A, beta, B, C, dt) -> int:
 def mm_diag(n, p, X, d, C, side, dt) -> int:
     """side 0: C = X.diag(d); side 1: C = diag(d).X (device matrices)."""
     return lib().mm_diag(n, p, _ptr(X), _ptr(d), _ptr(C), side, dt)
+
+
+def mm_add_async(n, p, alpha, A, beta, B, C, dt, stream=None) -> int:
+    return lib().mm_add_async(n, p, float(alpha), _ptr(A), float(beta), _ptr(B), _ptr(C), dt,
+                              _stream(stream))
+
+
+def mm_diag_async(n, p, X, d, C, side, dt, stream=None) -> int:
+    return lib().mm_diag_async(n, p, _ptr(X), _ptr(d), _ptr(C), side, dt, _stream(stream))
 
 
 def mm_gemm_split_static(n, m, p, A, B, C, stream=None) -> int:

@@ -209,16 +209,24 @@ mm_status mm_cgemm(int64_t n, int64_t m, int64_t p, const void *A, const void *B
   return check_device_flag(s);
 }
 
-mm_status mm_add(int64_t n, int64_t p, double alpha, const void *A, double beta, const void *B,
-                 void *C, mm_dtype dt) {
+}  // extern "C"
+
+namespace mm {
+namespace {
+
+mm_status check_add_args(int64_t n, int64_t p, const void *A, const void *B, const void *C,
+                         mm_dtype dt) {
   if (!g_ctx.inited) return MM_ENOTINIT;
   if (g_ctx.sticky) return MM_ECUDA;
   if (n < 0 || p < 0 || (dt != MM_F32 && dt != MM_F64)) return MM_EINVAL;
   if (n == 0 || p == 0) return MM_OK;
   if (!A || !B || !C || pointer_kind(A) != 1 || pointer_kind(B) != 1 || pointer_kind(C) != 1)
     return MM_EINVAL;
-  std::lock_guard<std::mutex> lk(g_api_mutex);
-  cudaStream_t s = g_ctx.stream;
+  return MM_EPENDING;  // valid and non-empty: queue the kernel
+}
+
+mm_status enqueue_add(int64_t n, int64_t p, double alpha, const void *A, double beta,
+                      const void *B, void *C, mm_dtype dt, cudaStream_t s) {
   const int64_t count = n * p;
   const bool unit = alpha == 1.0 && (beta == 1.0 || beta == -1.0);
   TraceScope ts("add", s);
@@ -238,13 +246,11 @@ mm_status mm_add(int64_t n, int64_t p, double alpha, const void *A, double beta,
         static_cast<const double *>(A), static_cast<const double *>(B), static_cast<double *>(C),
         alpha, beta, count, unit);
   }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return note_cuda(e);
-  return check_device_flag(s);
+  return note_cuda(cudaGetLastError());
 }
 
-mm_status mm_diag(int64_t n, int64_t p, const void *X, const void *d, void *C, int side,
-                  mm_dtype dt) {
+mm_status check_diag_args(int64_t n, int64_t p, const void *X, const void *d, const void *C,
+                          int side, mm_dtype dt) {
   if (!g_ctx.inited) return MM_ENOTINIT;
   if (g_ctx.sticky) return MM_ECUDA;
   if (n < 0 || p < 0 || (side != 0 && side != 1) || (dt != MM_F32 && dt != MM_F64))
@@ -252,8 +258,11 @@ mm_status mm_diag(int64_t n, int64_t p, const void *X, const void *d, void *C, i
   if (n == 0 || p == 0) return MM_OK;
   if (!X || !d || !C || pointer_kind(X) != 1 || pointer_kind(d) != 1 || pointer_kind(C) != 1)
     return MM_EINVAL;
-  std::lock_guard<std::mutex> lk(g_api_mutex);
-  cudaStream_t s = g_ctx.stream;
+  return MM_EPENDING;
+}
+
+mm_status enqueue_diag(int64_t n, int64_t p, const void *X, const void *d, void *C, int side,
+                       mm_dtype dt, cudaStream_t s) {
   const bool vec = dt == MM_F32 && p % 4 == 0 &&
                    ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(d) |
                      reinterpret_cast<uintptr_t>(C)) & 15) == 0;
@@ -261,9 +270,9 @@ mm_status mm_diag(int64_t n, int64_t p, const void *X, const void *d, void *C, i
             (unsigned)std::min<int64_t>(n, 65535));
   TraceScope ts("diag", s);
   if (vec)
-    diag4_kernel<<<(unsigned)grid_ew(n * (p / 4)), kEwThreads, 0, s>>>(static_cast<const float4 *>(X),
-                                                      static_cast<const float *>(d),
-                                                      static_cast<float4 *>(C), n, p / 4, side);
+    diag4_kernel<<<(unsigned)grid_ew(n * (p / 4)), kEwThreads, 0, s>>>(
+        static_cast<const float4 *>(X), static_cast<const float *>(d), static_cast<float4 *>(C), n,
+        p / 4, side);
   else if (dt == MM_F32)
     diag_kernel<float><<<grid, 256, 0, s>>>(static_cast<const float *>(X),
                                             static_cast<const float *>(d),
@@ -272,9 +281,48 @@ mm_status mm_diag(int64_t n, int64_t p, const void *X, const void *d, void *C, i
     diag_kernel<double><<<grid, 256, 0, s>>>(static_cast<const double *>(X),
                                              static_cast<const double *>(d),
                                              static_cast<double *>(C), n, p, side);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return note_cuda(e);
-  return check_device_flag(s);
+  return note_cuda(cudaGetLastError());
+}
+
+}  // namespace
+}  // namespace mm
+
+extern "C" {
+
+mm_status mm_add(int64_t n, int64_t p, double alpha, const void *A, double beta, const void *B,
+                 void *C, mm_dtype dt) {
+  mm_status st = check_add_args(n, p, A, B, C, dt);
+  if (st != MM_EPENDING) return st;
+  std::lock_guard<std::mutex> lk(g_api_mutex);
+  st = enqueue_add(n, p, alpha, A, beta, B, C, dt, g_ctx.stream);
+  return st != MM_OK ? st : check_device_flag(g_ctx.stream);
+}
+
+mm_status mm_add_async(int64_t n, int64_t p, double alpha, const void *A, double beta,
+                       const void *B, void *C, mm_dtype dt, void *stream) {
+  mm_status st = check_add_args(n, p, A, B, C, dt);
+  if (st != MM_EPENDING) return st;
+  std::lock_guard<std::mutex> lk(g_api_mutex);
+  return enqueue_add(n, p, alpha, A, beta, B, C, dt,
+                     stream ? static_cast<cudaStream_t>(stream) : g_ctx.stream);
+}
+
+mm_status mm_diag(int64_t n, int64_t p, const void *X, const void *d, void *C, int side,
+                  mm_dtype dt) {
+  mm_status st = check_diag_args(n, p, X, d, C, side, dt);
+  if (st != MM_EPENDING) return st;
+  std::lock_guard<std::mutex> lk(g_api_mutex);
+  st = enqueue_diag(n, p, X, d, C, side, dt, g_ctx.stream);
+  return st != MM_OK ? st : check_device_flag(g_ctx.stream);
+}
+
+mm_status mm_diag_async(int64_t n, int64_t p, const void *X, const void *d, void *C, int side,
+                        mm_dtype dt, void *stream) {
+  mm_status st = check_diag_args(n, p, X, d, C, side, dt);
+  if (st != MM_EPENDING) return st;
+  std::lock_guard<std::mutex> lk(g_api_mutex);
+  return enqueue_diag(n, p, X, d, C, side, dt,
+                      stream ? static_cast<cudaStream_t>(stream) : g_ctx.stream);
 }
 
 }  // extern "C"

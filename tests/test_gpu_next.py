@@ -127,3 +127,34 @@ def test_diag_add_args(mmlib):
     assert mm.mm_diag(2, 2, x, x, x, 2, mm.MM_F32) == mm.MM_EINVAL
     assert mm.mm_add(2, 2, 1.0, np.zeros(4, np.float32), 1.0, x, x, mm.MM_F32) == mm.MM_EINVAL
     assert mm.mm_add(0, 5, 1.0, None, 1.0, None, None, mm.MM_F32) == mm.MM_OK
+
+
+def test_add_diag_async_on_a_stream(mmlib):
+    """The asynchronous forms on a caller stream give the same bits as the
+    synchronous calls once the stream has been synchronised."""
+    mm = mmlib
+    n, p = 1000, 1028
+    A = dev(synth.uniform_pm1(1530, (n, p)))
+    B = dev(synth.uniform_pm1(1531, (n, p)))
+    d = dev(synth.uniform_pm1(1532, p))
+    s = torch.cuda.Stream()
+    for side in (0, 1):
+        dd = d if side == 0 else dev(synth.uniform_pm1(1533, n))
+        C1 = torch.full((n, p), float("nan"), device="cuda")
+        C2 = torch.full((n, p), float("nan"), device="cuda")
+        assert mm.mm_diag(n, p, A, dd, C1, side, mm.MM_F32) == 0
+        torch.cuda.synchronize()
+        assert mm.mm_diag_async(n, p, A, dd, C2, side, mm.MM_F32, s) == 0
+        assert mm.mm_sync(s) == 0
+        assert torch.equal(C1, C2)
+    C1 = torch.full((n, p), float("nan"), device="cuda")
+    C2 = torch.full((n, p), float("nan"), device="cuda")
+    assert mm.mm_add(n, p, 0.5, A, -3.0, B, C1, mm.MM_F32) == 0
+    torch.cuda.synchronize()
+    assert mm.mm_add_async(n, p, 0.5, A, -3.0, B, C2, mm.MM_F32, s) == 0
+    assert mm.mm_sync(s) == 0
+    assert torch.equal(C1, C2)
+    x = torch.zeros(4, device="cuda")
+    assert mm.mm_add_async(2, 2, 1.0, np.zeros(4, np.float32), 1.0, x, x, mm.MM_F32, s) == mm.MM_EINVAL
+    assert mm.mm_diag_async(2, 2, x, x, x, 2, mm.MM_F32, s) == mm.MM_EINVAL
+    assert mm.mm_add_async(0, 5, 1.0, None, 1.0, None, None, mm.MM_F32, s) == mm.MM_OK
