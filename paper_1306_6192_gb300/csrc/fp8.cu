@@ -23,68 +23,132 @@ __device__ __forceinline__ int e4m3_exponent(uint32_t max_bits) {
   return (f > 0.0f && f <= 3.402823466e38f) ? scale_exponent(max_bits) - 7 : 0;
 }
 
+// x * 2^-e rounded once: a multiplication by the exact power of two when
+// 2^-e is a normal float (the same result as ldexpf), ldexpf otherwise.
+__device__ __forceinline__ float scale_down(float x, int e) {
+  if (e >= -127 && e <= 126) return x * __int_as_float((127 - e) << 23);
+  return ldexpf(x, -e);
+}
+
 // Four consecutive values scaled by 2^-e -> four e4m3 bytes (first in the
 // lowest byte).
-__device__ __forceinline__ uint32_t to_e4m3x4(float x0, float x1, float x2, float x3, int e) {
-  const __nv_fp8x2_storage_t lo =
-      __nv_cvt_float2_to_fp8x2(make_float2(ldexpf(x0, -e), ldexpf(x1, -e)), __NV_SATFINITE, __NV_E4M3);
-  const __nv_fp8x2_storage_t hi =
-      __nv_cvt_float2_to_fp8x2(make_float2(ldexpf(x2, -e), ldexpf(x3, -e)), __NV_SATFINITE, __NV_E4M3);
+__device__ __forceinline__ uint32_t to_e4m3x4(float4 x, int e) {
+  const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(
+      make_float2(scale_down(x.x, e), scale_down(x.y, e)), __NV_SATFINITE, __NV_E4M3);
+  const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(
+      make_float2(scale_down(x.z, e), scale_down(x.w, e)), __NV_SATFINITE, __NV_E4M3);
   return (uint32_t)lo | ((uint32_t)hi << 16);
 }
 
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ bool aligned16(const void *p) {
+  return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
+}
+
+// One block per pack tile.  A tile (mt, kb): 128 rows x 128 k, read as
+// 16-byte vectors (eight per thread in flight), written as one 128-byte pack
+// row per row.  B tile (nt, kb): bn columns x 128 k, transposed through
+// shared memory 64 columns at a time (eight 16-byte loads per thread in
+// flight), written as one pack row per column, 16 bytes per store.
+__global__ void __launch_bounds__(256, 4)
 fp8_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *__restrict__ map,
                 uint32_t *__restrict__ pack) {
+  constexpr int kQuads = kK / 4;            // 32-bit words per pack row
+  constexpr int kBatch = 8;                 // vectors per thread in flight
+  __shared__ float tile[kK][64 + 1];
   const int item = blockIdx.x;
   const int g =
       find_problem(probs, nprobs, map, item, [](const SplitProb &q) { return q.pack_start; });
   const SplitProb &pr = probs[g];
   const int local = item - pr.pack_start;
   const int tid = threadIdx.x;
-  constexpr int kQuads = kK / 4;  // 32-bit words per pack row
   if (local < pr.mt * pr.kt) {
-    // A tile (mt, kb): 128 rows x 128 k; a warp writes one 128-byte row.
     const int mt = local / pr.kt, kb = local % pr.kt;
     const int64_t base = pr.a_row0 + (int64_t)local * kTcBM;
-    for (int q = tid; q < kTcBM * kQuads; q += 256) {
-      const int r = q / kQuads, kq = q % kQuads;
-      const int64_t i = (int64_t)mt * kTcBM + r;
-      const int64_t k = (int64_t)kb * kK + 4 * kq;
-      float x[4] = {0.f, 0.f, 0.f, 0.f};
-      int e = 0;
-      if (i < pr.n) {
-        const float *row = pr.A + i * pr.m;
+    const bool vec = aligned16(pr.A) && (pr.m & 3) == 0;
+    for (int q0 = 0; q0 < kTcBM * kQuads; q0 += 256 * kBatch) {
+      float4 xs[kBatch];
 #pragma unroll
-        for (int t = 0; t < 4; t++)
-          if (k + t < pr.m) x[t] = row[k + t];
-        e = e4m3_exponent(pr.sA[i]);
+      for (int it = 0; it < kBatch; it++) {
+        const int q = q0 + tid + it * 256;
+        const int r = q / kQuads, kq = q % kQuads;
+        const int64_t i = (int64_t)mt * kTcBM + r;
+        const int64_t k = (int64_t)kb * kK + 4 * kq;
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < pr.n) {
+          const float *row = pr.A + i * pr.m;
+          if (vec && k + 4 <= pr.m) {
+            x = __ldcs(reinterpret_cast<const float4 *>(row + k));
+          } else {
+            if (k < pr.m) x.x = row[k];
+            if (k + 1 < pr.m) x.y = row[k + 1];
+            if (k + 2 < pr.m) x.z = row[k + 2];
+            if (k + 3 < pr.m) x.w = row[k + 3];
+          }
+        }
+        xs[it] = x;
       }
-      pack[(base + r) * kQuads + kq] = to_e4m3x4(x[0], x[1], x[2], x[3], e);
+#pragma unroll
+      for (int it = 0; it < kBatch; it++) {
+        const int q = q0 + tid + it * 256;
+        const int r = q / kQuads, kq = q % kQuads;
+        const int64_t i = (int64_t)mt * kTcBM + r;
+        const int e = i < pr.n ? e4m3_exponent(pr.sA[i]) : 0;
+        pack[(base + r) * kQuads + kq] = to_e4m3x4(xs[it], e);
+      }
     }
   } else {
-    // B tile (nt, kb): bn columns x 128 k, transposed through shared memory
-    // 32 columns at a time.
-    __shared__ float tile[kK][32 + 1];
     const int b = local - pr.mt * pr.kt;
     const int nt = b / pr.kt, kb = b % pr.kt;
     const int bn = pr.bn;
     const int64_t base = pr.b_row0 + (int64_t)b * bn;
-    for (int c0 = 0; c0 < bn; c0 += 32) {
-      for (int q = tid; q < kK * 32; q += 256) {
-        const int kk = q / 32, c = q % 32;
+    const bool vec = aligned16(pr.B) && (pr.p & 3) == 0;
+    for (int c0 = 0; c0 < bn; c0 += 64) {
+      float4 vs[kBatch];
+#pragma unroll
+      for (int it = 0; it < kBatch; it++) {
+        const int q = tid + it * 256;  // 128 k rows x 16 vectors of 4 columns
+        const int kk = q / 16, c4 = q % 16;
         const int64_t k = (int64_t)kb * kK + kk;
-        const int64_t j = (int64_t)nt * bn + c0 + c;
-        tile[kk][c] = (k < pr.m && j < pr.p) ? pr.B[k * pr.p + j] : 0.f;
+        const int64_t j = (int64_t)nt * bn + c0 + 4 * c4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k < pr.m) {
+          const float *src = pr.B + k * pr.p + j;
+          if (vec && j + 4 <= pr.p) {
+            v = __ldcs(reinterpret_cast<const float4 *>(src));
+          } else {
+            if (j < pr.p) v.x = src[0];
+            if (j + 1 < pr.p) v.y = src[1];
+            if (j + 2 < pr.p) v.z = src[2];
+            if (j + 3 < pr.p) v.w = src[3];
+          }
+        }
+        vs[it] = v;
+      }
+#pragma unroll
+      for (int it = 0; it < kBatch; it++) {
+        const int q = tid + it * 256;
+        const int kk = q / 16, c4 = q % 16;
+        tile[kk][4 * c4 + 0] = vs[it].x;
+        tile[kk][4 * c4 + 1] = vs[it].y;
+        tile[kk][4 * c4 + 2] = vs[it].z;
+        tile[kk][4 * c4 + 3] = vs[it].w;
       }
       __syncthreads();
-      for (int q = tid; q < 32 * kQuads; q += 256) {
-        const int c = q / kQuads, kq = q % kQuads;
+      // a lane per column (the warp reads 32 consecutive columns of a tile
+      // row: no bank conflicts), 16 k values per item written as 16 bytes
+      for (int q = tid; q < 64 * (kK / 16); q += 256) {
+        const int c = q % 64, k16 = q / 64;
         const int64_t j = (int64_t)nt * bn + c0 + c;
         const int e = j < pr.p ? e4m3_exponent(pr.tB[j]) : 0;
-        pack[(base + c0 + c) * kQuads + kq] =
-            to_e4m3x4(tile[4 * kq][c], tile[4 * kq + 1][c], tile[4 * kq + 2][c],
-                      tile[4 * kq + 3][c], e);
+        uint4 w;
+        uint32_t *wp = reinterpret_cast<uint32_t *>(&w);
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+          const int r = 16 * k16 + 4 * t;
+          wp[t] = to_e4m3x4(make_float4(tile[r][c], tile[r + 1][c], tile[r + 2][c], tile[r + 3][c]),
+                            e);
+        }
+        *reinterpret_cast<uint4 *>(pack + (base + c0 + c) * kQuads + 4 * k16) = w;
       }
       __syncthreads();
     }
