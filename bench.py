@@ -659,8 +659,15 @@ def run_mine(args):
         extra["dgemm_check"] = gpu_check(mm, nd, nd, nd, A64, B64, C64, mm.MM_F64)
         del A64, B64, C64
         # FP8 e4m3 at the same size: rate and measured error (reported only)
-        ms_8, _ = timed(lambda: step(mm.MM_MODE_FP8), max(2, args.steps // 4), 1)
+        ms_8, _ = timed(lambda: step(mm.MM_MODE_FP8), max(2, args.steps // 4), 1, trace=True)
         extra["fp8_tflops"] = flops / (ms_8 / max(2, args.steps // 4) * 1e-3) / 1e12
+        _, k8, t8 = mm.mm_trace_read("fp8_tc")
+        if k8:
+            # its tensor-core kernel against the nominal FP8 rate: the measured
+            # burst BF16 peak x 2 (FP8 / BF16 dense ratio)
+            extra["fp8_tc_tflops"] = flops / (t8 / k8 * 1e-3) / 1e12
+            extra["fp8_tc_frac"] = extra["fp8_tc_tflops"] / (2.0 * peaks.get("bf16_tflops", 1941.7))
+        mm.mm_trace_reset()
         extra["fp8_check"] = gpu_check(mm, n, n, n, A, B, C, mm.MM_F32)
         # accuracy of the headline product, FP64 check on the GPU
         step()
