@@ -4,9 +4,11 @@
 // them in that order while the bytes they hold on the device (operands,
 // output and the library scratch they need) fit the HBM budget, groups the
 // admitted-but-unlaunched ones by path (split FP32, DGEMM FP64, SIMT, FP8)
-// into grouped launches of at most max_batch requests, and puts each batch
-// on the first free stream of a small pool, so batches that arrive while
-// others run overlap on the device.  A CUDA event per batch marks completion;
+// into grouped launches of at most max_batch requests and about kBatchMs of
+// estimated device time (every request of a batch completes when the batch
+// does, so a batch of long FP64 products would hold all of them back), and
+// puts each batch on the first free stream of a small pool, so batches that
+// arrive while others run overlap on the device.  A CUDA event per batch marks completion;
 // the scheduler polls the events, releases the requests' bytes and stamps
 // their latency (completion seen by the host - submission).
 //
@@ -31,6 +33,7 @@ namespace {
 using Clock = std::chrono::steady_clock;
 constexpr int kCheckSamples = 64;
 constexpr int kDefaultMaxBatch = 256;
+constexpr double kBatchMs = 16.0;  // estimated device time per batch (at least one request)
 
 struct Request {
   uint64_t id = 0;
@@ -44,6 +47,17 @@ struct Request {
   double latency_ms = 0.0;
   bool done = false;
 };
+
+// Estimated device time of a request (ms): its flops at a rough rate of its
+// path on GB300.
+double request_ms(const Request &r) {
+  const double flops = 2.0 * (double)r.pr.n * (double)r.pr.m * (double)r.pr.p;
+  double rate = 3e14;                                  // split BF16 x3 / x6
+  if (r.mode == MM_MODE_DGEMM) rate = 1.2e12;          // FP64 FMA
+  else if (r.mode == MM_MODE_SIMT) rate = 4.5e13;      // FP32 FMA
+  else if (r.mode == MM_MODE_FP8) rate = 1e15;
+  return flops / rate * 1e3;
+}
 
 struct Slot {
   cudaStream_t s = nullptr;
@@ -241,18 +255,27 @@ void scheduler() {
       g_srv.resident += r->bytes;
       g_srv.admitted.push_back(r);
     }
-    // 3. batches onto free streams
+    // 3. batches onto free streams: the path of the oldest admitted request,
+    // its requests in arrival order up to max_batch and ~kBatchMs of work
     for (Slot &sl : g_srv.slots) {
       if (sl.busy || g_srv.admitted.empty()) continue;
       const mm_mode mode = g_srv.admitted.front()->mode;
       const mm_dtype dt = g_srv.admitted.front()->dt;
       std::vector<Request *> take;
       std::deque<Request *> rest;
+      double ms = 0.0;
+      bool full = false;
       for (Request *r : g_srv.admitted) {
-        if ((int)take.size() < g_srv.max_batch && r->mode == mode && r->dt == dt)
-          take.push_back(r);
-        else
-          rest.push_back(r);
+        if (!full && r->mode == mode && r->dt == dt) {
+          const double c = request_ms(*r);
+          if ((int)take.size() < g_srv.max_batch && (take.empty() || ms + c <= kBatchMs)) {
+            take.push_back(r);
+            ms += c;
+            continue;
+          }
+          full = true;  // later requests of this path wait for the next batch
+        }
+        rest.push_back(r);
       }
       g_srv.admitted.swap(rest);
       const mm_status st = launch_batch(sl, take);
