@@ -41,8 +41,18 @@ if ROOT not in sys.path:
 N_DEFAULT = 8192
 
 
-def workload(n: int, path: str = "split-BF16x3 tcgen05") -> str:
-    return "square FP32 GEMM n=m=p=%d, uniform[-1,1) seeds 0/1, %s" % (n, path)
+def workload(n: int) -> str:
+    return "square FP32 GEMM n=m=p=%d, uniform[-1,1) seeds 0/1" % n
+
+
+def workload_config(n: int, world: int) -> dict:
+    """The workload both arms run (the same dict in the reference arm's line);
+    the method that computes it is the line's "path"."""
+    mb = 4 * n * n / 1e6
+    l2 = ("inputs larger than L2 (%.0f MB per operand)" % mb if mb > 129
+          else "operands of %.1f MB each (within L2)" % mb)
+    return {"workload": workload(n), "n": n, "m": n, "p": n, "l2": l2,
+            "parallelism": "replicas x%d" % world}
 
 
 def _peaks():
@@ -206,9 +216,8 @@ def run_reference(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sum(times) / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": workload(n, "CPU FP64 oracle"),
-                   "n": n, "m": n, "p": n},
+        "data": "synthetic", "path": "CPU FP64 oracle",
+        "config": workload_config(n, world),
         "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": smp.cores,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
@@ -619,10 +628,8 @@ def run_mine(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16x3->f32" if args.mode == "split" else "f32", "data": "synthetic",
-        "config": {"workload": workload(n) if args.mode == "split" else workload(n, "SIMT FP32"),
-                   "n": n, "m": n, "p": n, "mode": args.mode,
-                   "l2": "inputs larger than L2 (268 MB per operand)",
-                   "parallelism": "replicas x%d" % world},
+        "path": "split-BF16x3 tcgen05" if args.mode == "split" else "SIMT FP32",
+        "config": workload_config(n, world),
         "gpu_launches": launches, "clocks": clocks, "kernels": per_kernel,
     }
     if args.mode == "split" and "split_tc" in per_kernel:

@@ -18,3 +18,7 @@ def test_reference_arm_line():
     assert line["unit"] == "TFLOP/s" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+    # the same workload description as the library's own line
+    sys.path.insert(0, ROOT)
+    import bench
+    assert line["config"] == bench.workload_config(256, 1)
