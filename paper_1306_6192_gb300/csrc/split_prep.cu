@@ -170,6 +170,69 @@ __device__ __forceinline__ uint32_t half_warp_max(uint32_t v) {
   return v;
 }
 
+// One B pack tile (nt, kb) of split_pack_kernel: bn columns x 64 k,
+// transposed through shared memory CW columns at a time.
+template <int PARTS, int MODE, int CW>
+__device__ __forceinline__ void pack_b_tile(const SplitProb &pr, int b, uint2 *__restrict__ pack,
+                                            float (&tile)[kPackK][128 + 1], int tid) {
+  constexpr int kQuads = kPackK / 4;                 // groups of four bf16 per pack row
+  constexpr int kIter = kPackK * (CW / 4) / 256;     // 16-byte loads per thread and chunk
+  const int nt = b / pr.kt, kb = b % pr.kt;
+  const int bn = pr.bn;
+  const int64_t base = pr.b_row0 + (int64_t)b * PARTS * bn;
+  const bool vec = aligned16(pr.B) && (pr.p & 3) == 0;
+  for (int c0 = 0; c0 < bn; c0 += CW) {
+    float4 vs[kIter];
+#pragma unroll
+    for (int it = 0; it < kIter; it++) {
+      const int q = tid + it * 256;
+      const int kk = q / (CW / 4), c4 = q % (CW / 4);
+      const int64_t k = (int64_t)kb * kPackK + kk;
+      const int64_t j = (int64_t)nt * bn + c0 + 4 * c4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (k < pr.m) {
+        const float *src = pr.B + k * pr.p + j;
+        if (vec && j + 4 <= pr.p) {
+          v = __ldcs(reinterpret_cast<const float4 *>(src));
+        } else {
+          if (j < pr.p) v.x = src[0];
+          if (j + 1 < pr.p) v.y = src[1];
+          if (j + 2 < pr.p) v.z = src[2];
+          if (j + 3 < pr.p) v.w = src[3];
+        }
+      }
+      vs[it] = v;
+    }
+#pragma unroll
+    for (int it = 0; it < kIter; it++) {
+      const int q = tid + it * 256;
+      const int kk = q / (CW / 4), c4 = q % (CW / 4);
+      tile[kk][4 * c4 + 0] = vs[it].x;
+      tile[kk][4 * c4 + 1] = vs[it].y;
+      tile[kk][4 * c4 + 2] = vs[it].z;
+      tile[kk][4 * c4 + 3] = vs[it].w;
+    }
+    __syncthreads();
+    for (int q = tid; q < CW * kQuads; q += 256) {
+      const int c = q / kQuads, kq = q % kQuads;
+      const int64_t j = (int64_t)nt * bn + c0 + c;
+      const int s = (MODE != kPackUnscaled && j < pr.p) ? scale_exponent(pr.tB[j]) : 0;
+      const float4 x = make_float4(tile[4 * kq][c], tile[4 * kq + 1][c], tile[4 * kq + 2][c],
+                                   tile[4 * kq + 3][c]);
+      if (MODE == kPackUnscaled) {
+        // the 16 threads of a half warp hold one column's 64 values
+        const uint32_t mx = half_warp_max(max4_bits(x));
+        if (kq == 0 && j < pr.p) pr.pB[(int64_t)kb * pr.p + j] = mx;
+      }
+      uint2 part[PARTS];
+      split4<PARTS>(x, s, part);
+#pragma unroll
+      for (int h = 0; h < PARTS; h++) pack[(base + h * bn + c0 + c) * kQuads + kq] = part[h];
+    }
+    __syncthreads();
+  }
+}
+
 // MODE: kPackUnscaled - no scaling; write the tile's row (A) / column (B)
 //                       maxima to pA / pB; one block per pack tile;
 //       kPackFix      - scale by 2^-s from the maxima in sA / tB; only the
@@ -186,8 +249,7 @@ split_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *__
                   uint2 *__restrict__ pack) {
   constexpr int kQuads = kPackK / 4;  // groups of four bf16 (8 bytes) per pack row
   constexpr int kAIter = kTcBM * kQuads / 256;
-  constexpr int kBIter = kPackK * 16 / 256;
-  __shared__ float tile[kPackK][64 + 1];
+  __shared__ float tile[kPackK][128 + 1];
   if (MODE == kPackFix && *any == 0) return;
   const int tid = threadIdx.x;
   for (int item = blockIdx.x; item < total_tiles; item += gridDim.x) {
@@ -241,62 +303,13 @@ split_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *__
       }
     } else {
       // B tile (nt, kb): columns nt*bn.., k kb*64..; transposed through shared
-      // memory 64 columns at a time so both the read and the write coalesce.
+      // memory 128 columns at a time (64 for bn = 64) so both the read and the
+      // write coalesce, with eight 16-byte loads per thread in flight.
       const int b = local - pr.mt * pr.kt;
-      const int nt = b / pr.kt, kb = b % pr.kt;
-      const int bn = pr.bn;
-      const int64_t base = pr.b_row0 + (int64_t)b * PARTS * bn;
-      const bool vec = aligned16(pr.B) && (pr.p & 3) == 0;
-      for (int c0 = 0; c0 < bn; c0 += 64) {
-        float4 vs[kBIter];
-#pragma unroll
-        for (int it = 0; it < kBIter; it++) {
-          const int q = tid + it * 256;
-          const int kk = q / 16, c4 = q % 16;
-          const int64_t k = (int64_t)kb * kPackK + kk;
-          const int64_t j = (int64_t)nt * bn + c0 + 4 * c4;
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (k < pr.m) {
-            const float *src = pr.B + k * pr.p + j;
-            if (vec && j + 4 <= pr.p) {
-              v = __ldcs(reinterpret_cast<const float4 *>(src));
-            } else {
-              if (j < pr.p) v.x = src[0];
-              if (j + 1 < pr.p) v.y = src[1];
-              if (j + 2 < pr.p) v.z = src[2];
-              if (j + 3 < pr.p) v.w = src[3];
-            }
-          }
-          vs[it] = v;
-        }
-#pragma unroll
-        for (int it = 0; it < kBIter; it++) {
-          const int q = tid + it * 256;
-          const int kk = q / 16, c4 = q % 16;
-          tile[kk][4 * c4 + 0] = vs[it].x;
-          tile[kk][4 * c4 + 1] = vs[it].y;
-          tile[kk][4 * c4 + 2] = vs[it].z;
-          tile[kk][4 * c4 + 3] = vs[it].w;
-        }
-        __syncthreads();
-        for (int q = tid; q < 64 * kQuads; q += 256) {
-          const int c = q / kQuads, kq = q % kQuads;
-          const int64_t j = (int64_t)nt * bn + c0 + c;
-          const int s = (MODE != kPackUnscaled && j < pr.p) ? scale_exponent(pr.tB[j]) : 0;
-          const float4 x = make_float4(tile[4 * kq][c], tile[4 * kq + 1][c], tile[4 * kq + 2][c],
-                                       tile[4 * kq + 3][c]);
-          if (MODE == kPackUnscaled) {
-            // the 16 threads of a half warp hold one column's 64 values
-            const uint32_t mx = half_warp_max(max4_bits(x));
-            if (kq == 0 && j < pr.p) pr.pB[(int64_t)kb * pr.p + j] = mx;
-          }
-          uint2 part[PARTS];
-          split4<PARTS>(x, s, part);
-#pragma unroll
-          for (int h = 0; h < PARTS; h++) pack[(base + h * bn + c0 + c) * kQuads + kq] = part[h];
-        }
-        __syncthreads();
-      }
+      if (pr.bn % 128 == 0)
+        pack_b_tile<PARTS, MODE, 128>(pr, b, pack, tile, tid);
+      else
+        pack_b_tile<PARTS, MODE, 64>(pr, b, pack, tile, tid);
     }
   }
 }
