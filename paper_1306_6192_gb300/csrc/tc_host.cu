@@ -121,20 +121,24 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
   }
   if (ntab == 0) return MM_OK;
   if (rows > 0x7fffffffLL) return MM_EINVAL;
+  // Layout: packs | the words that start at zero (scale words, per-problem
+  // scale flags and one "any flagged" word per group, tail-split counters: one
+  // memset clears them) | partial maxima | table | item maps | partial tiles
   const size_t pack_bytes = (size_t)rows * kPackRowBytes;
   const size_t scal_off = (pack_bytes + 255) & ~(size_t)255;
-  const size_t part_off = (scal_off + (size_t)scal * 4 + 255) & ~(size_t)255;
+  const size_t flag_off = scal_off + (size_t)scal * 4;
+  const size_t tcnt_off = flag_off + (ntab + 3) * sizeof(int);
+  const size_t zero_end = tcnt_off + tail_cnts * sizeof(int);
+  const size_t part_off = (zero_end + 255) & ~(size_t)255;
   const size_t tab_off = (part_off + (size_t)part * 4 + 255) & ~(size_t)255;
   // item -> problem maps (work units, pack tiles, reduction and verify items)
   // of each group with more than one problem
   size_t map_ints = 0;
   for (auto &G : groups)
     if (G.tab.size() > 1) map_ints += (size_t)(G.units + G.packs + G.reds + G.vers);
-  map_ints += ntab + 3;  // per-problem scale flags, one "any flagged" word per group
   const size_t map_off = (tab_off + ntab * sizeof(SplitProb) + 255) & ~(size_t)255;
   const size_t tpart_off = (map_off + map_ints * sizeof(int) + 255) & ~(size_t)255;
-  const size_t tcnt_off = tpart_off + tail_parts;  // tail_parts is a multiple of 256
-  const size_t need = tcnt_off + tail_cnts * sizeof(int);
+  const size_t need = tpart_off + tail_parts;
   cudaError_t e = ws.reserve(need, s);
   if (e != cudaSuccess) return note_cuda(e);
   uint8_t *base = static_cast<uint8_t *>(ws.ptr);
@@ -157,15 +161,11 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
   SplitProb *d_tab = reinterpret_cast<SplitProb *>(base + tab_off);
   e = ws.stage.copy_to_device(d_tab, all.data(), all.size() * sizeof(SplitProb), s);
   if (e != cudaSuccess) return note_cuda(e);
-  e = cudaMemsetAsync(base + scal_off, 0, (size_t)scal * 4, s);
-  if (e == cudaSuccess)  // flags and "any" words
-    e = cudaMemsetAsync(base + map_off, 0, (ntab + 3) * sizeof(int), s);
-  if (e == cudaSuccess && tail_cnts > 0)
-    e = cudaMemsetAsync(base + tcnt_off, 0, tail_cnts * sizeof(int), s);
+  e = cudaMemsetAsync(base + scal_off, 0, zero_end - scal_off, s);
   if (e != cudaSuccess) return note_cuda(e);
   size_t off = 0;
-  int *flags_all = reinterpret_cast<int *>(base + map_off);
-  int *maps = flags_all + ntab + 3;
+  int *flags_all = reinterpret_cast<int *>(base + flag_off);
+  int *maps = reinterpret_cast<int *>(base + map_off);
   for (int gi = 0; gi < 3; gi++) {
     Group &G = groups[gi];
     if (G.tab.empty()) continue;
