@@ -31,7 +31,14 @@ struct SimtShape {
   static constexpr int APAD = SWZ ? 0 : W;
   static constexpr int VA = BM * BK / W / NT;     // vectors of A per thread and K slice
   static constexpr int VB = BK * BN / W / NT;     // vectors of B per thread and K slice
-  static_assert(TM == 2 * W && TN == 2 * W, "fragment = two 16-byte vectors");
+  // a thread's fragment: FA 16-byte vectors of A (rows BM / FA apart) and FB of
+  // B (columns BN / FB apart) per K index
+  static constexpr int FA = TM / W, FB = TN / W;
+  // FP32 tiles of up to 64 outputs per thread fit two blocks per SM (at most
+  // 128 registers per thread); larger ones and FP64 take one
+  static constexpr int MIN_BLOCKS = (sizeof(T) == 4 && TM * TN <= 64) ? 2 : 1;
+  static_assert(TM % W == 0 && TN % W == 0, "fragments of whole 16-byte vectors");
+  static_assert(NT == 256, "launched with 256 threads");
   static_assert(VA >= 1 && VB >= 1 && VA * W * NT == BM * BK && VB * W * NT == BK * BN,
                 "whole vectors per thread");
 };
@@ -144,11 +151,14 @@ __device__ __forceinline__ void simt_tile(const T *__restrict__ A, const T *__re
 #pragma unroll
     for (int k = 0; k < BK; k++) {
       T af[TM], bf[TN];
-      *reinterpret_cast<V *>(&af[0]) = *reinterpret_cast<const V *>(&As[cur][k][acol(k, ty * W)]);
-      *reinterpret_cast<V *>(&af[W]) =
-          *reinterpret_cast<const V *>(&As[cur][k][acol(k, BM / 2 + ty * W)]);
-      *reinterpret_cast<V *>(&bf[0]) = *reinterpret_cast<const V *>(&Bs[cur][k][tx * W]);
-      *reinterpret_cast<V *>(&bf[W]) = *reinterpret_cast<const V *>(&Bs[cur][k][BN / 2 + tx * W]);
+#pragma unroll
+      for (int f = 0; f < S::FA; f++)
+        *reinterpret_cast<V *>(&af[f * W]) =
+            *reinterpret_cast<const V *>(&As[cur][k][acol(k, f * (BM / S::FA) + ty * W)]);
+#pragma unroll
+      for (int f = 0; f < S::FB; f++)
+        *reinterpret_cast<V *>(&bf[f * W]) =
+            *reinterpret_cast<const V *>(&Bs[cur][k][f * (BN / S::FB) + tx * W]);
 #pragma unroll
       for (int i = 0; i < TM; i++)
 #pragma unroll
@@ -158,16 +168,16 @@ __device__ __forceinline__ void simt_tile(const T *__restrict__ A, const T *__re
     __syncthreads();
   }
 
-  // store: rows {ty*W + i, BM/2 + ty*W + i}, columns {tx*W + j, BN/2 + tx*W + j}
+  // store: rows hi*(BM/FA) + ty*W + i, columns hj*(BN/FB) + tx*W + j
 #pragma unroll
-  for (int hi = 0; hi < 2; hi++) {
+  for (int hi = 0; hi < S::FA; hi++) {
 #pragma unroll
     for (int i = 0; i < W; i++) {
-      const int64_t row = m0 + hi * (BM / 2) + ty * W + i;
+      const int64_t row = m0 + hi * (BM / S::FA) + ty * W + i;
       if (EDGE && row >= n) continue;
 #pragma unroll
-      for (int hj = 0; hj < 2; hj++) {
-        const int64_t col = n0 + hj * (BN / 2) + tx * W;
+      for (int hj = 0; hj < S::FB; hj++) {
+        const int64_t col = n0 + hj * (BN / S::FB) + tx * W;
         T *dst = C + row * p + col;
         const T *src = &acc[hi * W + i][hj * W];
         if (!EDGE || (VEC && col + W <= p)) {
@@ -200,11 +210,8 @@ __device__ __forceinline__ void simt_tile_any(const T *__restrict__ A, const T *
     simt_tile<T, BM, BN, BK, TM, TN, VEC, true>(A, B, C, n, m, p, tile_m, tile_n, As, Bs);
 }
 
-// FP32: two blocks per SM (at most 128 registers per thread); FP64: as needed.
-template <typename T> struct MinBlocks { static constexpr int value = sizeof(T) == 4 ? 2 : 1; };
-
 template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
-__global__ void __launch_bounds__(256, MinBlocks<T>::value)
+__global__ void __launch_bounds__(256, (SimtShape<T, BM, BN, BK, TM, TN>::MIN_BLOCKS))
 simt_gemm_kernel(const T *__restrict__ A, const T *__restrict__ B, T *__restrict__ C,
                  int64_t n, int64_t m, int64_t p) {
   simt_tile_any<T, BM, BN, BK, TM, TN, VEC>(A, B, C, n, m, p, blockIdx.y, blockIdx.x);
@@ -213,7 +220,7 @@ simt_gemm_kernel(const T *__restrict__ A, const T *__restrict__ B, T *__restrict
 // Grouped form: one block per output tile over all problems of a table; the
 // block finds its problem by binary search over the tile prefix.
 template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
-__global__ void __launch_bounds__(256, MinBlocks<T>::value)
+__global__ void __launch_bounds__(256, (SimtShape<T, BM, BN, BK, TM, TN>::MIN_BLOCKS))
 simt_grouped_kernel(const SimtProb *__restrict__ probs, int nprobs) {
   const int t = blockIdx.x;
   int lo = 0, hi = nprobs - 1;
