@@ -77,30 +77,21 @@ def pin_small_ints_exact(orc):
 
 
 def pin_hand_example(orc):
-    """Worked by hand from the definition.
-
-    3x3 (the size of the paper's walk-through before Listing 2):
-      A = [[1,2,3],[4,5,6],[7,8,9]], B = [[9,8,7],[6,5,4],[3,2,1]]
-      c_11 = 1*9 + 2*6 + 3*3 = 30, c_12 = 1*8 + 2*5 + 3*2 = 24, ...
-      C = [[30,24,18],[84,69,54],[138,114,90]].
-    In Listing 2 the thread with thread_x = 0, thread_y = 1 reads row
-    thread_y of A and column thread_x of B, i.e. it computes C[1][0] = 84.
-    2x3 by 3x2 (non-square, catches a swapped operand or index):
-      A = [[1,0,-2],[3,1,0]], B = [[2,1],[0,-1],[1,4]]
-      C = [[1*2 + 0*0 + (-2)*1, 1*1 + 0*(-1) + (-2)*4], [3*2 + 1*0 + 0*1, 3*1 + 1*(-1) + 0*4]]
-        = [[0, -7], [6, 2]].
-    """
-    A = np.array([[1, 2, 3], [4, 5, 6], [7, 8, 9]], np.float32)
-    B = np.array([[9, 8, 7], [6, 5, 4], [3, 2, 1]], np.float32)
-    C = orc.gemm(A, B)
-    assert np.array_equal(C, np.array([[30, 24, 18], [84, 69, 54], [138, 114, 90]], np.float64))
-    assert C[1, 0] == 84.0
-    A2 = np.array([[1, 0, -2], [3, 1, 0]], np.float32)
-    B2 = np.array([[2, 1], [0, -1], [1, 4]], np.float32)
-    C2, S2 = orc.gemm(A2, B2, with_abs=True)
-    assert np.array_equal(C2, np.array([[0, -7], [6, 2]], np.float64))
-    # |A||B|: [[1*2+0+2*1, 1*1+0+2*4],[3*2+0+0, 3*1+1*1+0]] = [[4, 9], [6, 4]]
-    assert np.array_equal(S2, np.array([[4, 9], [6, 4]], np.float64))
+    """Products worked by hand from the definition (tests/golden/hand_worked.txt):
+    the 3x3 size of the paper's walk-through before Listing 2, where the
+    thread with thread_x = 0, thread_y = 1 reads row thread_y of A and column
+    thread_x of B and so computes the entry in row 1, column 0 (84 here), and
+    a 2x3 by 3x2 product that catches a swapped operand or index.  The
+    normaliser |A||B| is worked by hand too."""
+    import golden
+    cases = golden.hand_worked()
+    assert [c["name"] for c in cases] == ["walkthrough_3x3", "nonsquare_2x3x2"]
+    for c in cases:
+        C, S = orc.gemm(c["A"], c["B"], with_abs=True)
+        assert C.shape == (c["n"], c["p"]), c["name"]
+        assert np.array_equal(C, c["C"]), c["name"]
+        assert np.array_equal(S, c["ABS"]), c["name"]
+    assert cases[0]["C"][1, 0] == 84.0
 
 
 def pin_identity(orc):
