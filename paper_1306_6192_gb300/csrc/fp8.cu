@@ -23,20 +23,13 @@ __device__ __forceinline__ int e4m3_exponent(uint32_t max_bits) {
   return (f > 0.0f && f <= 3.402823466e38f) ? scale_exponent(max_bits) - 7 : 0;
 }
 
-// x * 2^-e rounded once: a multiplication by the exact power of two when
-// 2^-e is a normal float (the same result as ldexpf), ldexpf otherwise.
-__device__ __forceinline__ float scale_down(float x, int e) {
-  if (e >= -127 && e <= 126) return x * __int_as_float((127 - e) << 23);
-  return ldexpf(x, -e);
-}
-
 // Four consecutive values scaled by 2^-e -> four e4m3 bytes (first in the
 // lowest byte).
 __device__ __forceinline__ uint32_t to_e4m3x4(float4 x, int e) {
   const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(
-      make_float2(scale_down(x.x, e), scale_down(x.y, e)), __NV_SATFINITE, __NV_E4M3);
+      make_float2(scale_pow2(x.x, -e), scale_pow2(x.y, -e)), __NV_SATFINITE, __NV_E4M3);
   const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(
-      make_float2(scale_down(x.z, e), scale_down(x.w, e)), __NV_SATFINITE, __NV_E4M3);
+      make_float2(scale_pow2(x.z, -e), scale_pow2(x.w, -e)), __NV_SATFINITE, __NV_E4M3);
   return (uint32_t)lo | ((uint32_t)hi << 16);
 }
 

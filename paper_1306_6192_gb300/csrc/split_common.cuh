@@ -7,6 +7,14 @@
 
 namespace mm {
 
+// x * 2^e rounded once: a multiplication by the exact power of two when 2^e is
+// a normal float (then identical to ldexpf, which is exact to 0 ulp), ldexpf
+// otherwise.
+__device__ __forceinline__ float scale_pow2(float x, int e) {
+  if (e >= -126 && e <= 127) return x * __int_as_float((e + 127) << 23);
+  return ldexpf(x, e);
+}
+
 // Scale exponent of a row of A / column of B from the bit pattern of its
 // largest magnitude: s = floor(log2(max |x|)), so that x * 2^-s has magnitude
 // below 2 for every entry of the row/column.  An all-zero row and a

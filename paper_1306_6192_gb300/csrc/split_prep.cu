@@ -137,13 +137,18 @@ split_scale_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *_
   }
 }
 
-// Splits four values scaled by 2^-s into PARTS groups of four bf16 (two
-// bf16x2 words each): part 0 = RN(y), part q = RN(y - part 0 - ... - part
-// q-1).  Every remainder is exact in FP32 (the difference of a float and its
-// rounding to fewer bits), so y = sum of parts + d, |d| <= 2^(-8*PARTS) |y|.
-template <int PARTS>
+// Splits four values scaled by 2^-s (SCALED; unscaled: s = 0, no multiply)
+// into PARTS groups of four bf16 (two bf16x2 words each): part 0 = RN(y),
+// part q = RN(y - part 0 - ... - part q-1).  Every remainder is exact in FP32
+// (the difference of a float and its rounding to fewer bits), so y = sum of
+// parts + d, |d| <= 2^(-8*PARTS) |y|.
+template <int PARTS, bool SCALED>
 __device__ __forceinline__ void split4(float4 x, int s, uint2 (&out)[PARTS]) {
-  float y[4] = {ldexpf(x.x, -s), ldexpf(x.y, -s), ldexpf(x.z, -s), ldexpf(x.w, -s)};
+  float y[4] = {x.x, x.y, x.z, x.w};
+  if (SCALED) {
+#pragma unroll
+    for (int e = 0; e < 4; e++) y[e] = scale_pow2(y[e], -s);
+  }
 #pragma unroll
   for (int q = 0; q < PARTS; q++) {
     const __nv_bfloat162 a = __floats2bfloat162_rn(y[0], y[1]);
@@ -163,11 +168,28 @@ __device__ __forceinline__ uint32_t max4_bits(float4 x) {
   return umax(umax(abs_bits(x.x), abs_bits(x.y)), umax(abs_bits(x.z), abs_bits(x.w)));
 }
 
-// max over the 16 lanes of a half warp (lanes 0-15 or 16-31)
-__device__ __forceinline__ uint32_t half_warp_max(uint32_t v) {
+// Eight maxima over the 16 lanes of a half warp at once (v[t], t = 0..7, in
+// every lane): each exchange round sends the half of the slots that the
+// partner keeps, so 8 shuffles replace 4 per slot.  Returns, in every lane,
+// the half-warp maximum of slot t = (lane >> 1) & 7 (lanes 2t and 2t + 1 of
+// the half warp hold slot t).  Every lane of the warp must call it.
+__device__ __forceinline__ uint32_t half_warp_max8(const uint32_t (&v)[8]) {
+  const int lane = threadIdx.x & 31;
+  const bool b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+  uint32_t w[4], u[2];
 #pragma unroll
-  for (int o = 8; o > 0; o >>= 1) v = umax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
+  for (int j = 0; j < 4; j++) {  // lanes with bit 3 clear keep slots 0-3
+    const uint32_t send = b3 ? v[j] : v[j + 4], keep = b3 ? v[j + 4] : v[j];
+    w[j] = umax(keep, __shfl_xor_sync(0xffffffffu, send, 8));
+  }
+#pragma unroll
+  for (int j = 0; j < 2; j++) {  // w[j] holds slot j + 4 b3
+    const uint32_t send = b2 ? w[j] : w[j + 2], keep = b2 ? w[j + 2] : w[j];
+    u[j] = umax(keep, __shfl_xor_sync(0xffffffffu, send, 4));
+  }
+  const uint32_t send = b1 ? u[0] : u[1], keep = b1 ? u[1] : u[0];  // u[j]: slot j + 2 b2 + 4 b3
+  const uint32_t t = umax(keep, __shfl_xor_sync(0xffffffffu, send, 2));
+  return umax(t, __shfl_xor_sync(0xffffffffu, t, 1));
 }
 
 // One B pack tile (nt, kb) of split_pack_kernel: bn columns x 64 k,
@@ -213,21 +235,31 @@ __device__ __forceinline__ void pack_b_tile(const SplitProb &pr, int b, uint2 *_
       tile[kk][4 * c4 + 3] = vs[it].w;
     }
     __syncthreads();
-    for (int q = tid; q < CW * kQuads; q += 256) {
+    // column c = tid / 16 + 16 t of this chunk in round t: the 16 threads of
+    // a half warp hold one column's 64 values
+    constexpr int kCols = CW * kQuads / 256;
+    uint32_t mxv[8];
+#pragma unroll
+    for (int t = 0; t < kCols; t++) {
+      const int q = tid + t * 256;
       const int c = q / kQuads, kq = q % kQuads;
       const int64_t j = (int64_t)nt * bn + c0 + c;
       const int s = (MODE != kPackUnscaled && j < pr.p) ? scale_exponent(pr.tB[j]) : 0;
       const float4 x = make_float4(tile[4 * kq][c], tile[4 * kq + 1][c], tile[4 * kq + 2][c],
                                    tile[4 * kq + 3][c]);
-      if (MODE == kPackUnscaled) {
-        // the 16 threads of a half warp hold one column's 64 values
-        const uint32_t mx = half_warp_max(max4_bits(x));
-        if (kq == 0 && j < pr.p) pr.pB[(int64_t)kb * pr.p + j] = mx;
-      }
+      if (MODE == kPackUnscaled) mxv[t] = max4_bits(x);
       uint2 part[PARTS];
-      split4<PARTS>(x, s, part);
+      split4<PARTS, MODE != kPackUnscaled>(x, s, part);
 #pragma unroll
       for (int h = 0; h < PARTS; h++) pack[(base + h * bn + c0 + c) * kQuads + kq] = part[h];
+    }
+    if (MODE == kPackUnscaled) {
+#pragma unroll
+      for (int t = kCols; t < 8; t++) mxv[t] = 0;
+      const uint32_t mx = half_warp_max8(mxv);
+      const int t = (tid >> 1) & 7;
+      const int64_t j = (int64_t)nt * bn + c0 + tid / kQuads + 16 * t;
+      if ((tid & 1) == 0 && t < kCols && j < pr.p) pr.pB[(int64_t)kb * pr.p + j] = mx;
     }
     __syncthreads();
   }
@@ -249,6 +281,7 @@ split_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *__
                   uint2 *__restrict__ pack) {
   constexpr int kQuads = kPackK / 4;  // groups of four bf16 (8 bytes) per pack row
   constexpr int kAIter = kTcBM * kQuads / 256;
+  static_assert(kAIter == 8, "eight A vectors per thread (one reduction slot each)");
   __shared__ float tile[kPackK][128 + 1];
   if (MODE == kPackFix && *any == 0) return;
   const int tid = threadIdx.x;
@@ -285,19 +318,25 @@ split_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *__
         }
         xs[it] = x;
       }
+      if (MODE == kPackUnscaled) {
+        // row r = tid / 16 + 16 it: the 16 threads of a half warp hold one
+        // row's 64 values
+        uint32_t mxv[8];
+#pragma unroll
+        for (int it = 0; it < 8; it++) mxv[it] = max4_bits(xs[it]);
+        const uint32_t mx = half_warp_max8(mxv);
+        const int t = (tid >> 1) & 7;
+        const int64_t i = (int64_t)mt * kTcBM + tid / kQuads + 16 * t;
+        if ((tid & 1) == 0 && i < pr.n) pr.pA[(int64_t)kb * pr.n + i] = mx;
+      }
 #pragma unroll
       for (int it = 0; it < kAIter; it++) {
         const int q = tid + it * 256;
         const int r = q / kQuads, kq = q % kQuads;
         const int64_t i = (int64_t)mt * kTcBM + r;
         const int s = (MODE != kPackUnscaled && i < pr.n) ? scale_exponent(pr.sA[i]) : 0;
-        if (MODE == kPackUnscaled) {
-          // the 16 threads of a half warp hold one row's 64 values
-          const uint32_t mx = half_warp_max(max4_bits(xs[it]));
-          if (kq == 0 && i < pr.n) pr.pA[(int64_t)kb * pr.n + i] = mx;
-        }
         uint2 part[PARTS];
-        split4<PARTS>(xs[it], s, part);
+        split4<PARTS, MODE != kPackUnscaled>(xs[it], s, part);
 #pragma unroll
         for (int h = 0; h < PARTS; h++) pack[(base + h * kTcBM + r) * kQuads + kq] = part[h];
       }

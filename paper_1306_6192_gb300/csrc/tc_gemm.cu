@@ -218,13 +218,6 @@ __device__ __forceinline__ uint32_t make_idesc(int bn) {
          ((uint32_t)(kTcBM >> 4) << 24);
 }
 
-// x * 2^e rounded once: a multiplication by the exact power of two when 2^e is
-// a normal float (then identical to ldexpf), ldexpf otherwise.
-__device__ __forceinline__ float scale_pow2(float x, int e) {
-  if (e >= -126 && e <= 127) return x * __int_as_float((e + 127) << 23);
-  return ldexpf(x, e);
-}
-
 // AND of `v` over the 128 epilogue threads (named barrier 1): every thread
 // arrives, so the four warps leave the tile loop together.
 __device__ __forceinline__ bool epilogue_all(bool v) {
