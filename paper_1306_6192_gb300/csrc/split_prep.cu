@@ -463,8 +463,10 @@ cudaError_t launch_split_pack(TcKind kind, int mode, const SplitProb *d_probs, i
   TraceScope ts(mode == kPackFix ? "split_fix" : "split_pack", s);
   auto *pk = static_cast<uint2 *>(pack_base);
   const bool x6 = kind == kTcSplitBf16x6;
-  // the fix pass: a persistent grid (8 blocks per SM) over the tiles
-  const int grid = mode == kPackFix ? std::min(total_tiles, sm_count() * 8) : total_tiles;
+  // the fix pass: a persistent grid of one wave (4 blocks per SM, the launch
+  // bound) over the tiles, so that its early return when nothing is flagged
+  // costs a single wave of blocks
+  const int grid = mode == kPackFix ? std::min(total_tiles, sm_count() * 4) : total_tiles;
 #define MM_PACK(P, M) \
   split_pack_kernel<P, M><<<grid, 256, 0, s>>>(d_probs, nprobs, map, flags, any, total_tiles, pk)
   if (mode == kPackUnscaled) { if (x6) MM_PACK(3, kPackUnscaled); else MM_PACK(2, kPackUnscaled); }
