@@ -414,9 +414,10 @@ def bench_grouped(mm, stream, steps: int, seed: int = 4, count: int = 4096):
 
 
 def bench_serving(mm, count: int, rate_frac: float, seed: int = 5, streams: int = 2,
-                  max_batch: int = 0, capacity=None):
+                  max_batch: int = 0, capacity=None, f64_mode=None):
     """Poisson replay of `count` requests (dims log-uniform in [64, 4096], 20%
     FP64) through mm_submit/mm_poll with operands resident on the device.
+    f64_mode: the path of the FP64 requests (default MM_MODE_DGEMM).
     The arrival rate is rate_frac x the measured capacity (requests/s of the
     same mix submitted all at once).  Returns p50/p99 latency and rates."""
     import numpy as np
@@ -430,13 +431,14 @@ def bench_serving(mm, count: int, rate_frac: float, seed: int = 5, streams: int 
     src32 = torch.rand(big, device="cuda", generator=gen) * 2 - 1
     src64 = src32.double()
 
+    f64_md = mm.MM_MODE_DGEMM if f64_mode is None else f64_mode
     out_cap = 40 << 30  # the client's outstanding output bytes (backpressure)
     held = [0]
 
     def submit(k):
         n, m, p = (int(v) for v in dims[k])
         if f64[k]:
-            A, B, dt, md = src64[:n * m], src64[:m * p], mm.MM_F64, mm.MM_MODE_DGEMM
+            A, B, dt, md = src64[:n * m], src64[:m * p], mm.MM_F64, f64_md
             C = torch.empty(n * p, device="cuda", dtype=torch.float64)
         else:
             A, B, dt, md = src32[:n * m], src32[:m * p], mm.MM_F32, mm.MM_MODE_SPLIT_BF16X3
@@ -664,6 +666,22 @@ def run_mine(args):
         extra["dgemm_f64_tflops"] = 2.0 * nd ** 3 / (ms_d / 2 * 1e-3) / 1e12
         extra["dgemm_size"] = nd
         extra["dgemm_check"] = gpu_check(mm, nd, nd, nd, A64, B64, C64, mm.MM_F64)
+        # FP64 emulated on the e4m3 tensor cores (Ozaki scheme, default slices)
+        # on full 53-bit FP64 operands of the same size
+        A64 = torch.from_numpy(synth.uniform_pm1_f64(20, (nd, nd))).cuda()
+        B64 = torch.from_numpy(synth.uniform_pm1_f64(21, (nd, nd))).cuda()
+        oz = lambda: mm.check_status(mm.mm_gemm_async(nd, nd, nd, A64, B64, C64, mm.MM_F64,
+                                                      mm.MM_MODE_OZAKI, stream), "ozaki")
+        ms_o, _ = timed(oz, 5, 2, trace=True)
+        extra["ozaki_f64_tflops"] = 2.0 * nd ** 3 / (ms_o / 5 * 1e-3) / 1e12
+        extra["ozaki_over_dgemm"] = extra["ozaki_f64_tflops"] / extra["dgemm_f64_tflops"]
+        extra["ozaki_kernels_ms"] = {}
+        for k in ("ozaki_max", "ozaki_digits", "fp8_tc", "ozaki_sum"):
+            _, cnt, kms = mm.mm_trace_read(k)
+            if cnt:
+                extra["ozaki_kernels_ms"][k] = kms / 5
+        mm.mm_trace_reset()
+        extra["ozaki_check"] = gpu_check(mm, nd, nd, nd, A64, B64, C64, mm.MM_F64)
         del A64, B64, C64
         # FP8 e4m3 at the same size: rate and measured error (reported only)
         ms_8, _ = timed(lambda: step(mm.MM_MODE_FP8), max(2, args.steps // 4), 1, trace=True)
@@ -701,6 +719,10 @@ def run_mine(args):
                               capacity=cap)
             cap = r["capacity_req_s"] if cap is None else cap
             serving[name] = r
+        # the same arrivals with the FP64 requests on the emulated path
+        serving["batched_ozaki_f64"] = bench_serving(mm, args.serve_requests, 0.9, streams=2,
+                                                     max_batch=0, capacity=None,
+                                                     f64_mode=mm.MM_MODE_OZAKI)
         line["serving"] = serving
 
         # end to end: mm_gemm with pinned host operands, copies inside the timing

@@ -27,6 +27,14 @@
  *                         power-of-two scales; accuracy is reported, not
  *                         guaranteed.  Not in the paper.
  *   MM_MODE_AUTO          SPLIT_BF16X3 for MM_F32, DGEMM for MM_F64.
+ *   MM_MODE_OZAKI         FP64 in/out on the e4m3 tensor cores (Ozaki
+ *                         scheme): each row of A / column of B is scaled by a
+ *                         power of two and cut into S 4-bit integer digit
+ *                         slices; the slice products of equal weight are
+ *                         exact in FP32 and are added in FP64.  Accuracy
+ *                         depends on S and on the spread of magnitudes within
+ *                         rows and columns (mm_ozaki_slices).  Not in the
+ *                         paper.
  *
  * Accuracy contract (measured against an FP64 CPU evaluation of the
  * definition): max_ij |c^_ij - c_ij| / (|A|.|B|)_ij <= 1e-6*sqrt(m) for SIMT
@@ -41,8 +49,8 @@
  *   - The caller owns A, B, C.  The library owns its scratch: packed bf16
  *     operand splits, scale exponents, problem tables, tensor memory.
  *   - n, m, p >= 0.  n == 0 or p == 0 is a no-op; m == 0 writes C = 0.
- *   - dtype/mode mismatch (MM_F64 with SIMT/SPLIT/FP8, MM_F32 with DGEMM)
- *     returns MM_EUNSUPPORTED.
+ *   - dtype/mode mismatch (MM_F64 with SIMT/SPLIT/FP8, MM_F32 with DGEMM or
+ *     OZAKI) returns MM_EUNSUPPORTED.
  *   - A sticky CUDA error (the context is lost) returns MM_ECUDA from then on.
  *   - Device-side waits are bounded; a wait that runs out sets a device flag
  *     that the next synchronising call reports as MM_ETIMEOUT.
@@ -83,7 +91,8 @@ typedef enum {
   MM_MODE_SPLIT_BF16X3 = 1,
   MM_MODE_DGEMM = 2,
   MM_MODE_FP8 = 3,
-  MM_MODE_AUTO = 4
+  MM_MODE_AUTO = 4,
+  MM_MODE_OZAKI = 5
 } mm_mode;
 
 typedef struct {
@@ -125,6 +134,27 @@ const char *mm_strerror(mm_status s);
  * when C is written.  C is fully overwritten and must not alias A or B. */
 mm_status mm_gemm(int64_t n, int64_t m, int64_t p, const void *A, const void *B,
                   void *C, mm_dtype dt, mm_mode mode);
+
+/* Digit slices S used by MM_MODE_OZAKI for products queued after the call
+ * (serving requests keep the value current at mm_submit).  2 <= S <= 16,
+ * default 14; the cost grows as S (S + 1) / 2 e4m3 products.
+ * Method (K. Ozaki, T. Ogita, S. Oishi, S. M. Rump, Numer. Algorithms 59,
+ * 2012, error-free splitting of matrix products): with sigma_i =
+ * ilogb(max_r |a_ir|) + 1 and tau_j likewise for column j of B, every entry
+ * is truncated to 4S bits below 2^sigma and cut into S digits of 4 bits
+ * (|d| <= 15, exact in e4m3); level L = t + u of the digit products is one
+ * tensor-core product whose FP32 sums stay exact (K is cut into chunks of
+ * at most (2^24 - 1) / (225 S) columns for that); levels t + u >= S are
+ * dropped.  Each term a_ir b_rj is then off by at most
+ * (S + 2) 2^(sigma_i + tau_j - 4S), zero entries by nothing: relative to
+ * (|A||B|)_ij about 4 (S + 2) 2^(-4S) (S = 14: 9e-16) for rows and columns
+ * without a wide spread of magnitudes, more where a row's largest entry
+ * dwarfs the entries that meet the column's mass (mm_check measures a
+ * result).  Rows of A or columns of B holding a NaN or an infinity give NaN
+ * rows or columns of C.  Scratch: (S digit bytes per entry of A and B, plus
+ * S FP32 level sums per entry of C per K chunk), library-owned.
+ * Returns MM_EINVAL outside 2..16, MM_ENOTINIT before mm_init. */
+mm_status mm_ozaki_slices(int slices);
 
 /* As mm_gemm, but device pointers only and asynchronous: the work is queued on
  * `stream` (a cudaStream_t; NULL = the library stream) and the call returns

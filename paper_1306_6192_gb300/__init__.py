@@ -23,6 +23,7 @@ MM_ESCRATCH = 12
 # element types and modes
 MM_F32, MM_F64 = 0, 1
 MM_MODE_SIMT, MM_MODE_SPLIT_BF16X3, MM_MODE_DGEMM, MM_MODE_FP8, MM_MODE_AUTO = 0, 1, 2, 3, 4
+MM_MODE_OZAKI = 5
 
 _i64 = ctypes.c_int64
 _vp = ctypes.c_void_p
@@ -96,6 +97,8 @@ def lib():
             getattr(L, name).restype = ctypes.c_int
         L.mm_gemm_split_static.argtypes = [_i64, _i64, _i64, _vp, _vp, _vp, _vp]
         L.mm_gemm_split_static.restype = ctypes.c_int
+        L.mm_ozaki_slices.argtypes = [ctypes.c_int]
+        L.mm_ozaki_slices.restype = ctypes.c_int
         for name in ("mm_init", "mm_shutdown", "mm_gemm", "mm_gemm_async", "mm_gemm_grouped",
                      "mm_gemm_grouped_async", "mm_sync", "mm_check", "mm_submit", "mm_poll",
                      "mm_wait", "mm_serve_stats", "mm_tune", "mm_tune_save", "mm_tune_load",
@@ -266,6 +269,11 @@ def mm_tail_plan(tiles, grid, kt, bn, m, products):
     st = lib().mm_tail_plan(tiles, grid, kt, bn, m, float(products), ctypes.byref(a),
                             ctypes.byref(b))
     return st, a.value, b.value
+
+
+def mm_ozaki_slices(slices: int) -> int:
+    """Digit slices S (2..16) of MM_MODE_OZAKI for the products queued next."""
+    return lib().mm_ozaki_slices(int(slices))
 
 
 def mm_trace_enable(on: bool = True) -> int:

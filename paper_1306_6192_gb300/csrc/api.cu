@@ -217,10 +217,11 @@ static mm_mode resolve_mode(mm_dtype dt, mm_mode mode) {
 mm_status validate(int64_t n, int64_t m, int64_t p, mm_dtype dt, mm_mode mode) {
   if (n < 0 || m < 0 || p < 0) return MM_EINVAL;
   if (dt != MM_F32 && dt != MM_F64) return MM_EINVAL;
-  if ((int)mode < 0 || (int)mode > (int)MM_MODE_AUTO) return MM_EINVAL;
+  if ((int)mode < 0 || (int)mode > (int)MM_MODE_OZAKI) return MM_EINVAL;
   const mm_mode md = resolve_mode(dt, mode);
-  if (dt == MM_F64 && md != MM_MODE_DGEMM) return MM_EUNSUPPORTED;
-  if (dt == MM_F32 && md == MM_MODE_DGEMM) return MM_EUNSUPPORTED;
+  const bool f64_mode = md == MM_MODE_DGEMM || md == MM_MODE_OZAKI;
+  if (dt == MM_F64 && !f64_mode) return MM_EUNSUPPORTED;
+  if (dt == MM_F32 && f64_mode) return MM_EUNSUPPORTED;
   // 32-bit tile bookkeeping of the kernels
   if (n > (int64_t)1 << 31 || m > (int64_t)1 << 31 || p > (int64_t)1 << 31) return MM_EINVAL;
   return MM_OK;
@@ -249,6 +250,9 @@ mm_status enqueue_gemm(int64_t n, int64_t m, int64_t p, const void *A, const voi
       mm_problem q{n, m, p, A, B, C};
       return run_fp8(g_ctx.fp8_ws, &q, 1, s);
     }
+    case MM_MODE_OZAKI:
+      return run_ozaki(g_ctx.ozaki_ws, n, m, p, (const double *)A, (const double *)B, (double *)C,
+                       g_ctx.ozaki_slices, s);
     default: return MM_EINVAL;
   }
 }
@@ -372,6 +376,8 @@ mm_status mm_shutdown(void) {
   g_ctx.stage_ws.release();
   g_ctx.check_ws.release();
   g_ctx.cplx_ws.release();
+  g_ctx.ozaki_ws.release();
+  g_ctx.ozaki_slices = kOzakiDefaultSlices;
   if (g_ctx.d_err) cudaFree(g_ctx.d_err);
   g_ctx.d_err = nullptr;
   trace_destroy();
@@ -389,6 +395,14 @@ mm_status mm_shutdown(void) {
   cudaStreamDestroy(g_ctx.stream);
   g_ctx.stream = nullptr;
   g_ctx.inited = false;
+  return MM_OK;
+}
+
+mm_status mm_ozaki_slices(int slices) {
+  std::lock_guard<std::mutex> lk(g_api_mutex);
+  if (!g_ctx.inited) return MM_ENOTINIT;
+  if (slices < kOzakiMinSlices || slices > kOzakiMaxSlices) return MM_EINVAL;
+  g_ctx.ozaki_slices = slices;
   return MM_OK;
 }
 

@@ -42,6 +42,9 @@ struct TcChoice {
   int tail = 1; // 1: split the last wave's tiles along K where the plan gains
 };
 
+// FP64 emulation (MM_MODE_OZAKI): 4-bit digit slices per operand.
+constexpr int kOzakiMinSlices = 2, kOzakiMaxSlices = 16, kOzakiDefaultSlices = 14;
+
 struct Ctx {
   bool inited = false;
   bool sticky = false;
@@ -56,6 +59,8 @@ struct Ctx {
   Scratch stage_ws;      // device copies of host operands
   Scratch check_ws;      // FP64 check work vectors
   Scratch cplx_ws;       // real/imaginary planes and partial products (mm_cgemm)
+  Scratch ozaki_ws;      // digit packs, level sums and tables of the FP64 emulation
+  int ozaki_slices = kOzakiDefaultSlices;  // digit slices S of MM_MODE_OZAKI
   // host-operand pipeline of mm_gemm: copy streams and per-chunk events
   cudaStream_t h2d = nullptr, d2h = nullptr;
   cudaStream_t tc_streams[2] = {};  // slab GEMMs alternate between these
@@ -109,6 +114,14 @@ TcTail product_tail(int64_t n, int64_t m, int64_t p, TcKind kind, int64_t *tiles
 size_t tail_scratch_bytes(int64_t n, int64_t m, int64_t p, TcKind kind);
 // FP8 path (report-only accuracy).
 mm_status run_fp8(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s);
+// FP64 product by the Ozaki scheme on the e4m3 tensor cores with S digit
+// slices (ozaki.cu); ozaki_chunk(S) = the K columns per chunk that keep every
+// level sum exact in FP32; ozaki_scratch_bytes = an upper bound of the
+// scratch one product needs.
+mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *A,
+                    const double *B, double *C, int S, cudaStream_t s);
+int64_t ozaki_chunk(int S);
+size_t ozaki_scratch_bytes(int64_t n, int64_t m, int64_t p, int S);
 // Grouped dispatch: split / SIMT / DGEMM tables in one launch per path.
 mm_status enqueue_grouped(Scratch &split_ws, Scratch &tab_ws, int count, const mm_problem *probs,
                           mm_dtype dt, mm_mode mode, cudaStream_t s);

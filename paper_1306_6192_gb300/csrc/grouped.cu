@@ -13,6 +13,16 @@ mm_status enqueue_grouped(Scratch &split_ws, Scratch &tab_ws, int count, const m
   if (count == 0) return MM_OK;
   if (mode == MM_MODE_SPLIT_BF16X3) return run_split(split_ws, probs, count, s, nullptr);
   if (mode == MM_MODE_FP8) return run_fp8(g_ctx.fp8_ws, probs, count, s);
+  if (mode == MM_MODE_OZAKI) {  // one emulated product after the other
+    for (int g = 0; g < count; g++) {
+      const mm_problem &q = probs[g];
+      const mm_status st = run_ozaki(g_ctx.ozaki_ws, q.n, q.m, q.p, static_cast<const double *>(q.A),
+                                     static_cast<const double *>(q.B), static_cast<double *>(q.C),
+                                     g_ctx.ozaki_slices, s);
+      if (st != MM_OK) return st;
+    }
+    return MM_OK;
+  }
   const bool f64 = dt == MM_F64;
   const int bm = f64 ? kSimtF64BM : kSimtF32BM, bn = f64 ? kSimtF64BN : kSimtF32BN;
   const int w = f64 ? 2 : 4;

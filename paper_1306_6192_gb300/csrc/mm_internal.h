@@ -78,6 +78,10 @@ struct SplitProb {
   int32_t split_s;         //   is ignored and every tile is one unit)
   float *part;             // partial tiles of the split tiles
   int *cnt;                // parts finished per split tile
+  // pack tiles between consecutive row tiles of A / column tiles of B (0:
+  // kt, the layout above); a larger stride lets a product read a window of
+  // kt K blocks out of a longer pack (the FP64 emulation's level products)
+  int32_t a_kstride, b_kstride;
 };
 
 // Work units of a product with its tail split: whole tiles, then the parts.

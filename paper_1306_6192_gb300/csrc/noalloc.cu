@@ -36,6 +36,7 @@ constexpr size_t kFlagOff = 0;      // int timeout flag
 constexpr size_t kScaleFlagOff = 64;  // int per-operand scale flags
 constexpr size_t kTableOff = 256;   // one SplitProb
 constexpr size_t kScalesOff = 512;  // uint32 per row of A and column of B
+static_assert(sizeof(SplitProb) <= kScalesOff - kTableOff, "table slot");
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocBytes];

@@ -1,0 +1,454 @@
+// FP64 product C = A.B emulated on the e4m3 tensor cores (Ozaki scheme).
+//
+// Method: K. Ozaki, T. Ogita, S. Oishi, S. M. Rump, "Error-free
+// transformations of matrix multiplication by using fast routines of matrix
+// multiplication and its applicability", Numer. Algorithms 59 (2012): split
+// every operand into slices whose pairwise products a low-precision matrix
+// unit computes without rounding, then add the slice products in the working
+// precision.  This library's variant (not in the paper, whose double-precision
+// kernels use FP64 arithmetic directly):
+//
+//   * Row i of A is scaled by 2^-sigma_i, sigma_i = ilogb(max_r |a_ir|) + 1,
+//     so |a_ir| 2^-sigma_i < 1; column j of B by 2^-tau_j likewise.  The
+//     scaled magnitude, truncated to 4S fraction bits, is the integer
+//     F = floor(|a| 2^(4S - sigma)) < 2^(4S), and its 4-bit digits
+//     d_t = (F >> 4(S-1-t)) & 15, t = 0..S-1, carry the sign of a:
+//         a 2^-sigma = sum_t d_t 2^(-4(t+1)) + delta,  |delta| < 2^(-4S).
+//     Every digit (|d| <= 15) is exact in e4m3.
+//   * Level L = 0..S-1 collects the slice products of equal weight:
+//         D_L = sum_{t+u=L} A_t B_u,
+//     one tensor-core product along a K of (L+1) slices: A's slices 0..L
+//     against B's slices L..0.  Each term is at most 225, a level at most
+//     225 S mc, so with K cut into chunks of mc <= (2^24 - 1) / (225 S)
+//     columns (a multiple of 128) every D_L is an integer below 2^24 and
+//     FP32 accumulation (and the tail split's FP32 partial sums) is exact.
+//     Pairs with t + u >= S are dropped.
+//   * c_ij = 2^(sigma_i + tau_j) * sum_L 2^(-4(L+2)) D_L[i][j] (summed over
+//     the chunks too), formed exactly in 128-bit integers and rounded once
+//     to FP64: the double nearest to the kept digit products.
+//
+// Error: a term a_ir b_rj loses at most (S + 2) 2^(sigma_i + tau_j - 4S)
+// (both truncations and the dropped pairs), and zero entries lose nothing,
+// so |c^_ij - c_ij| <= (S + 2) 2^(sigma_i + tau_j - 4S) #{r : a_ir b_rj != 0}
+// plus the final rounding (half an ulp of c^_ij).  Relative to (|A||B|)_ij this is
+// data dependent: ~4 (S + 2) 2^(-4S) for rows and columns without a wide
+// spread of magnitudes (uniform data), much more where a row's largest entry
+// dwarfs the entries that meet the column's mass.
+//
+// Data layout in the library's scratch ("pack region" first, 128-byte rows,
+// as the tensor-core kernel's tensor map requires):
+//   A digits of chunk c: tile (mt, slice t, kb) at rows
+//       a0_c + ((mt*S + t)*kt_c + kb)*128, one row per row of A (128 k);
+//   B digits of chunk c: tile (nt, slot, kb) at rows
+//       b0_c + ((nt*S + slot)*kt_c + kb)*bn, slot = S-1-u for slice u, one
+//       row per column of B, so that B's slices L..0 are contiguous;
+//   then the row/column maxima (bit patterns), zero scale words, the level
+//   sums D (FP32, [chunk][level][n][p]), the problem table and its maps.
+// The level problem (c, L) reads A's K blocks [0, (L+1) kt_c) and B's
+// [(S-1-L) kt_c, S kt_c) of each tile through the table's K stride S kt_c.
+// Rows (columns) holding a NaN or an infinity give NaN rows (columns) of C.
+#include <cuda_fp8.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "ctx.h"
+#include "split_common.cuh"
+
+namespace mm {
+namespace {
+
+constexpr int kRowsPerItem = 8;   // maxima: warps per block, one row of A each
+constexpr int kColStrip = 32;     // maxima: columns of B per strip
+constexpr int kRowChunk = 256;    // maxima: rows of B per strip item
+constexpr int kSeg = 16;          // digits: consecutive k per thread
+
+__device__ __forceinline__ uint64_t abs_bits64(double x) {
+  return (uint64_t)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
+// sigma = ilogb(max) + 1 from the bit pattern of a row's largest magnitude;
+// 0 for an all-zero row; finite = false for a NaN or an infinity.
+__device__ __forceinline__ int slice_exponent(uint64_t max_bits, bool &finite) {
+  const int e_raw = (int)(max_bits >> 52);
+  finite = e_raw != 0x7ff;
+  if (max_bits == 0 || !finite) return 0;
+  if (e_raw == 0) return (63 - __clzll((long long)max_bits)) - 1074 + 1;  // subnormal
+  return e_raw - 1023 + 1;
+}
+
+// Truncated fixed-point magnitude F = floor(|x| 2^(4S - sigma)) (< 2^(4S)
+// for |x| < 2^sigma) and the sign of x.
+__device__ __forceinline__ uint64_t fixed_magnitude(double x, int sigma, int S, bool &neg) {
+  const uint64_t bits = (uint64_t)__double_as_longlong(x);
+  neg = (bits >> 63) != 0;
+  const int e_raw = (int)((bits >> 52) & 0x7ff);
+  const uint64_t frac = bits & 0xfffffffffffffull;
+  uint64_t mant;
+  int ex;
+  if (e_raw == 0) {
+    mant = frac;
+    ex = -1022;
+  } else {
+    mant = frac | (1ull << 52);
+    ex = e_raw - 1023;
+  }
+  const int sh = ex - 52 + 4 * S - sigma;  // |x| = mant 2^(ex - 52)
+  if (mant == 0 || sh <= -64) return 0;
+  return sh >= 0 ? (mant << sh) : (mant >> -sh);
+}
+
+// 16 digits of slice t (one per k) -> 16 e4m3 bytes; zero digits are +0.
+__device__ __forceinline__ uint4 digit_bytes(const uint64_t (&F)[kSeg], uint32_t negmask, int shift) {
+  uint32_t w[4];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    float v[4];
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      const int d = (int)((F[4 * q + e] >> shift) & 15u);
+      v[e] = ((negmask >> (4 * q + e)) & 1u) && d ? -(float)d : (float)d;
+    }
+    const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v[0], v[1]), __NV_SATFINITE, __NV_E4M3);
+    const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v[2], v[3]), __NV_SATFINITE, __NV_E4M3);
+    w[q] = (uint32_t)lo | ((uint32_t)hi << 16);
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Maxima: items [0, ceil(n/8)) take 8 rows of A (a warp per row); the rest
+// strips of 32 columns x 256 rows of B, merged into colmax with atomicMax on
+// the bit patterns (which order like the magnitudes).
+__global__ void __launch_bounds__(256)
+ozaki_max_kernel(const double *__restrict__ A, const double *__restrict__ B, int64_t n, int64_t m,
+                 int64_t p, uint64_t *__restrict__ rowmax, unsigned long long *__restrict__ colmax) {
+  const int64_t items_a = (n + kRowsPerItem - 1) / kRowsPerItem;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if ((int64_t)blockIdx.x < items_a) {
+    const int64_t i = (int64_t)blockIdx.x * kRowsPerItem + warp;
+    if (i >= n) return;
+    const double *row = A + i * m;
+    uint64_t mx = 0;
+    for (int64_t k = lane; k < m; k += 32) {
+      const uint64_t b = abs_bits64(row[k]);
+      mx = b > mx ? b : mx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t other = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = other > mx ? other : mx;
+    }
+    if (lane == 0) rowmax[i] = mx;
+    return;
+  }
+  __shared__ uint64_t part[8][kColStrip];
+  const int64_t b = (int64_t)blockIdx.x - items_a;
+  const int64_t strips = (p + kColStrip - 1) / kColStrip;
+  const int64_t c0 = (b % strips) * kColStrip, r0 = (b / strips) * kRowChunk;
+  const int64_t col = c0 + lane;
+  uint64_t mx = 0;
+  if (col < p)
+    for (int r = warp; r < kRowChunk; r += 8) {
+      const int64_t k = r0 + r;
+      if (k < m) {
+        const uint64_t v = abs_bits64(B[k * p + col]);
+        mx = v > mx ? v : mx;
+      }
+    }
+  part[warp][lane] = mx;
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int w = 1; w < 8; w++) mx = part[w][lane] > mx ? part[w][lane] : mx;
+    if (col < p) atomicMax(&colmax[col], (unsigned long long)mx);
+  }
+}
+
+// A digits of one K chunk [k0, k0 + mc): one block per tile (mt, kb); a
+// thread takes 16 consecutive k of a row (8 threads per 128-k row, 4 rows per
+// warp: both the FP64 reads and the 16-byte digit stores are whole lines).
+__global__ void __launch_bounds__(256)
+ozaki_digits_a_kernel(const double *__restrict__ A, int64_t n, int64_t m, int64_t k0, int64_t mc,
+                      int kt, int S, const uint64_t *__restrict__ rowmax, uint4 *__restrict__ pack,
+                      int64_t a0) {
+  const int mt = blockIdx.x / kt, kb = blockIdx.x % kt;
+#pragma unroll 1
+  for (int q = threadIdx.x; q < kTcBM * (128 / kSeg); q += 256) {
+    const int r = q / (128 / kSeg), sg = q % (128 / kSeg);
+    const int64_t i = (int64_t)mt * kTcBM + r;
+    uint64_t F[kSeg];
+    uint32_t negmask = 0;
+    bool finite = true;
+    const int sigma = i < n ? slice_exponent(rowmax[i], finite) : 0;
+#pragma unroll
+    for (int e = 0; e < kSeg; e++) {
+      const int64_t kk = (int64_t)kb * 128 + sg * kSeg + e;  // within the chunk
+      F[e] = 0;
+      if (i < n && finite && kk < mc) {
+        bool neg;
+        F[e] = fixed_magnitude(A[i * m + k0 + kk], sigma, S, neg);
+        negmask |= (uint32_t)neg << e;
+      }
+    }
+#pragma unroll 1
+    for (int t = 0; t < S; t++) {
+      const int64_t row = a0 + (((int64_t)mt * S + t) * kt + kb) * kTcBM + r;
+      pack[row * (kPackRowBytes / 16) + sg] = digit_bytes(F, negmask, 4 * (S - 1 - t));
+    }
+  }
+}
+
+// B digits of one K chunk: one block per tile (nt, kb); the bn columns are
+// transposed through shared memory 32 at a time (FP64 rows of 32 columns
+// read whole), then a thread takes 16 consecutive k of a column.
+__global__ void __launch_bounds__(256)
+ozaki_digits_b_kernel(const double *__restrict__ B, int64_t m, int64_t p, int64_t k0, int64_t mc,
+                      int kt, int S, int bn, const unsigned long long *__restrict__ colmax,
+                      uint4 *__restrict__ pack, int64_t b0) {
+  __shared__ double tile[128][32 + 1];
+  const int nt = blockIdx.x / kt, kb = blockIdx.x % kt;
+  const int tid = threadIdx.x;
+  for (int c0 = 0; c0 < bn; c0 += 32) {
+    for (int q = tid; q < 128 * 32; q += 256) {
+      const int kk = q / 32, c = q % 32;
+      const int64_t k = (int64_t)kb * 128 + kk, j = (int64_t)nt * bn + c0 + c;
+      tile[kk][c] = (k < mc && j < p) ? B[(k0 + k) * p + j] : 0.0;
+    }
+    __syncthreads();
+    {
+      const int c = tid % 32, sg = tid / 32;  // 32 columns x 8 segments of 16 k
+      const int64_t j = (int64_t)nt * bn + c0 + c;
+      bool finite = true;
+      const int tau = j < p ? slice_exponent(colmax[j], finite) : 0;
+      uint64_t F[kSeg];
+      uint32_t negmask = 0;
+#pragma unroll
+      for (int e = 0; e < kSeg; e++) {
+        F[e] = 0;
+        if (j < p && finite) {
+          bool neg;
+          F[e] = fixed_magnitude(tile[sg * kSeg + e][c], tau, S, neg);
+          negmask |= (uint32_t)neg << e;
+        }
+      }
+#pragma unroll 1
+      for (int u = 0; u < S; u++) {
+        const int64_t row = b0 + (((int64_t)nt * S + (S - 1 - u)) * kt + kb) * bn + c0 + c;
+        pack[row * (kPackRowBytes / 16) + sg] = digit_bytes(F, negmask, 4 * (S - 1 - u));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Adds v 2^s (|v| < 2^31, 0 <= s < 64) to the two's-complement 128-bit
+// integer hi:lo.
+__device__ __forceinline__ void add_shifted(uint64_t &lo, int64_t &hi, int64_t v, int s) {
+  const uint64_t a_lo = (uint64_t)v << s;
+  const int64_t a_hi = s == 0 ? (v < 0 ? -1 : 0) : (v >> (64 - s));  // arithmetic shift
+  const uint64_t r = lo + a_lo;
+  hi += a_hi + (r < lo ? 1 : 0);
+  lo = r;
+}
+
+// The double nearest to hi:lo (ties to even), times 2^k.
+__device__ __forceinline__ double int128_scaled(uint64_t lo, int64_t hi, int k) {
+  const bool neg = hi < 0;
+  uint64_t mlo = lo, mhi = (uint64_t)hi;
+  if (neg) {  // magnitude
+    mlo = ~lo + 1;
+    mhi = ~(uint64_t)hi + (mlo == 0 ? 1 : 0);
+  }
+  double d;
+  if (mhi == 0) {
+    d = __ull2double_rn(mlo);
+  } else {
+    // keep the top 64 bits, with the bits shifted out as a sticky bit far
+    // below the 53-bit rounding position, then round once
+    const int sh = 64 - __clzll((long long)mhi);  // 1..64
+    const uint64_t top = sh == 64 ? mhi : ((mhi << (64 - sh)) | (mlo >> sh));
+    const uint64_t lost = sh == 64 ? mlo : (mlo << (64 - sh));
+    d = __ull2double_rn(top | (lost != 0 ? 1ull : 0ull));
+    k += sh;
+  }
+  return scalbn(neg ? -d : d, k);
+}
+
+// c_ij = 2^(sigma_i + tau_j - 4(S+1)) sum_c sum_L D[c][L][i][j] 2^(4(S-1-L)):
+// the level sums are integers below 2^24, so their weighted sum is formed
+// exactly in 128-bit integers and rounded once to FP64 (then scaled by a
+// power of two, which rounds again only in the subnormal range); NaN where
+// row i of A or column j of B is not finite.
+__global__ void __launch_bounds__(256)
+ozaki_sum_kernel(const float *__restrict__ D, int64_t n, int64_t p, int S, int chunks,
+                 const uint64_t *__restrict__ rowmax, const unsigned long long *__restrict__ colmax,
+                 double *__restrict__ C) {
+  const int64_t np = n * p;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < np;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = x / p, j = x - i * p;
+    bool fa, fb;
+    const int sigma = slice_exponent(rowmax[i], fa);
+    const int tau = slice_exponent(colmax[j], fb);
+    uint64_t lo = 0;
+    int64_t hi = 0;
+    for (int c = 0; c < chunks; c++)
+      for (int L = 0; L < S; L++) {
+        const int v = __float2int_rn(__ldcs(D + ((int64_t)c * S + L) * np + x));
+        add_shifted(lo, hi, v, 4 * (S - 1 - L));
+      }
+    C[x] = (fa && fb) ? int128_scaled(lo, hi, sigma + tau - 4 * (S + 1))
+                      : __longlong_as_double(0x7ff8000000000000ll);
+  }
+}
+
+// Scratch offsets of one call.
+struct OzLayout {
+  int S, chunks, bn, mt, nt;
+  int64_t mc;
+  std::vector<int64_t> k0, kc, kt, a0, b0;
+  int64_t rows = 0;
+  size_t max_off, zero_off, zero_end, d_off, tab_off, map_off, need;
+  int64_t units = 0, packs = 0;
+};
+
+}  // namespace
+
+int64_t ozaki_chunk(int S) {
+  const int64_t mc = ((int64_t)((1 << 24) - 1) / (225 * (int64_t)S)) / 128 * 128;
+  return mc;
+}
+
+mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *A,
+                    const double *B, double *C, int S, cudaStream_t s) {
+  if (S < kOzakiMinSlices || S > kOzakiMaxSlices) return MM_EINVAL;
+  if (n == 0 || p == 0) return MM_OK;
+  if (m == 0) return note_cuda(cudaMemsetAsync(C, 0, (size_t)(n * p) * sizeof(double), s));
+  OzLayout lay;
+  lay.S = S;
+  lay.mc = ozaki_chunk(S);
+  lay.chunks = (int)ceil_div(m, lay.mc);
+  TcChoice ch = tune_choose(n, std::min(m, lay.mc), p);
+  lay.bn = tc_bn(kTcE4m3, ch.bn);
+  lay.mt = (int)ceil_div(n, kTcBM);
+  lay.nt = (int)ceil_div(p, lay.bn);
+  for (int c = 0; c < lay.chunks; c++) {
+    const int64_t k0 = (int64_t)c * lay.mc, kc = std::min(lay.mc, m - k0);
+    const int64_t kt = ceil_div(kc, 128);
+    lay.k0.push_back(k0);
+    lay.kc.push_back(kc);
+    lay.kt.push_back(kt);
+    lay.a0.push_back(lay.rows);
+    lay.rows += (int64_t)lay.mt * S * kt * kTcBM;
+    lay.b0.push_back(lay.rows);
+    lay.rows += (int64_t)lay.nt * S * kt * lay.bn;
+  }
+  if (lay.rows > 0x7fffffffLL) return MM_EINVAL;
+  const int nprobs = lay.chunks * S;
+  std::vector<SplitProb> tab((size_t)nprobs);
+  // level problems, longest K first (the persistent grid takes units in
+  // order, so the short ones fill the last wave)
+  int g = 0;
+  for (int L = S - 1; L >= 0; L--)
+    for (int c = 0; c < lay.chunks; c++, g++) {
+      SplitProb &sp = tab[(size_t)g];
+      std::memset(&sp, 0, sizeof(sp));
+      const int64_t kt = lay.kt[(size_t)c];
+      sp.n = (int32_t)n;
+      sp.p = (int32_t)p;
+      sp.kt = (int32_t)((L + 1) * kt);
+      sp.m = sp.kt * 128;  // padded K of the level: zero digits past the chunk
+      sp.mt = lay.mt;
+      sp.nt = lay.nt;
+      sp.bn = lay.bn;
+      sp.group_m = ch.group_m;
+      sp.a_row0 = lay.a0[(size_t)c];
+      sp.b_row0 = lay.b0[(size_t)c] + (int64_t)(S - 1 - L) * kt * lay.bn;
+      sp.a_kstride = (int32_t)(S * kt);
+      sp.b_kstride = (int32_t)(S * kt);
+      sp.unit_start = (int32_t)lay.units;
+      lay.units += (int64_t)lay.mt * lay.nt;
+      sp.pack_start = (int32_t)lay.packs;
+      lay.packs += (int64_t)(lay.mt + lay.nt) * sp.kt;
+      sp.split_from = lay.mt * lay.nt;
+      sp.split_s = 1;
+      sp.C = reinterpret_cast<float *>((uintptr_t)(((int64_t)c * S + L) * n * p));  // offset
+    }
+  if (lay.units > 0x7fffffffLL || lay.packs > 0x7fffffffLL) return MM_EINVAL;
+  const size_t pack_bytes = (size_t)lay.rows * kPackRowBytes;
+  lay.max_off = (pack_bytes + 255) & ~(size_t)255;  // row maxima (n) + column maxima (p)
+  lay.zero_off = lay.max_off;
+  lay.zero_end = lay.max_off + (size_t)(n + p) * 8 + (size_t)(n + p) * 4;  // + zero scale words
+  lay.d_off = (lay.zero_end + 255) & ~(size_t)255;
+  lay.tab_off = (lay.d_off + (size_t)nprobs * n * p * sizeof(float) + 255) & ~(size_t)255;
+  lay.map_off = (lay.tab_off + (size_t)nprobs * sizeof(SplitProb) + 255) & ~(size_t)255;
+  lay.need = lay.map_off + (size_t)(lay.units + lay.packs) * sizeof(int);
+  cudaError_t e = ws.reserve(lay.need, s);
+  if (e != cudaSuccess) return note_cuda(e);
+  uint8_t *base = static_cast<uint8_t *>(ws.ptr);
+  uint64_t *rowmax = reinterpret_cast<uint64_t *>(base + lay.max_off);
+  unsigned long long *colmax = reinterpret_cast<unsigned long long *>(rowmax + n);
+  uint32_t *zero_words = reinterpret_cast<uint32_t *>(colmax + p);
+  float *D = reinterpret_cast<float *>(base + lay.d_off);
+  for (auto &sp : tab) {
+    sp.C = D + (uintptr_t)sp.C;
+    sp.sA = zero_words;      // scale exponent 0: the digits are not rescaled
+    sp.tB = zero_words + n;
+  }
+  SplitProb *d_tab = reinterpret_cast<SplitProb *>(base + lay.tab_off);
+  e = ws.stage.copy_to_device(d_tab, tab.data(), tab.size() * sizeof(SplitProb), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + lay.zero_off, 0, lay.zero_end - lay.zero_off, s);
+  if (e != cudaSuccess) return note_cuda(e);
+  {
+    TraceScope ts("ozaki_max", s);
+    const int64_t items = ceil_div(n, kRowsPerItem) + ceil_div(p, kColStrip) * ceil_div(m, kRowChunk);
+    if (items > 0x7fffffffLL) return MM_EINVAL;
+    ozaki_max_kernel<<<(unsigned)items, 256, 0, s>>>(A, B, n, m, p, rowmax, colmax);
+    if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
+  }
+  {
+    TraceScope ts("ozaki_digits", s);
+    uint4 *pk = static_cast<uint4 *>(ws.ptr);
+    for (int c = 0; c < lay.chunks; c++) {
+      const int kt = (int)lay.kt[(size_t)c];
+      ozaki_digits_a_kernel<<<(unsigned)(lay.mt * kt), 256, 0, s>>>(
+          A, n, m, lay.k0[(size_t)c], lay.kc[(size_t)c], kt, S, rowmax, pk, lay.a0[(size_t)c]);
+      ozaki_digits_b_kernel<<<(unsigned)(lay.nt * kt), 256, 0, s>>>(
+          B, m, p, lay.k0[(size_t)c], lay.kc[(size_t)c], kt, S, lay.bn, colmax, pk,
+          lay.b0[(size_t)c]);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
+  }
+  int *unit_map = nullptr;
+  if (nprobs > 1) {
+    unit_map = reinterpret_cast<int *>(base + lay.map_off);
+    e = launch_split_maps(d_tab, nprobs, unit_map, unit_map + lay.units, nullptr, nullptr, s);
+    if (e != cudaSuccess) return note_cuda(e);
+  }
+  TcConfig cfg{128, 4, ch.grid};
+  cfg.max_bn = lay.bn;
+  e = launch_tc(kTcE4m3, d_tab, nprobs, (int)lay.units, unit_map, nullptr, ws.ptr, lay.rows, cfg,
+                g_ctx.d_err, s);
+  if (e != cudaSuccess) return note_cuda(e);
+  {
+    TraceScope ts("ozaki_sum", s);
+    const int64_t np = n * p;
+    const int64_t blocks = std::min<int64_t>(ceil_div(np, 256), (int64_t)sm_count() * 16);
+    ozaki_sum_kernel<<<(unsigned)blocks, 256, 0, s>>>(D, n, p, S, lay.chunks, rowmax, colmax, C);
+    if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
+  }
+  return MM_OK;
+}
+
+size_t ozaki_scratch_bytes(int64_t n, int64_t m, int64_t p, int S) {
+  if (n <= 0 || p <= 0 || m <= 0) return 0;
+  const int64_t mc = ozaki_chunk(S);
+  const int64_t chunks = ceil_div(m, mc);
+  const int64_t kt_all = ceil_div(m, 128) + chunks;  // K blocks over all chunks (bound)
+  const int64_t rows = (ceil_div(n, kTcBM) * kTcBM + ceil_div(p, 128) * 256) * S * kt_all;
+  return (size_t)rows * kPackRowBytes + (size_t)chunks * S * n * p * sizeof(float) +
+         (size_t)(n + p) * 12 + ((size_t)1 << 20);
+}
+
+}  // namespace mm

@@ -40,6 +40,7 @@ struct Request {
   mm_problem pr{};
   mm_dtype dt = MM_F32;
   mm_mode mode = MM_MODE_SPLIT_BF16X3;
+  int slices = 0;  // MM_MODE_OZAKI: digit slices at submission
   size_t bytes = 0;
   Clock::time_point t_submit;
   mm_status status = MM_EPENDING;
@@ -56,6 +57,7 @@ double request_ms(const Request &r) {
   if (r.mode == MM_MODE_DGEMM) rate = 1.2e12;          // FP64 FMA
   else if (r.mode == MM_MODE_SIMT) rate = 4.5e13;      // FP32 FMA
   else if (r.mode == MM_MODE_FP8) rate = 1e15;
+  else if (r.mode == MM_MODE_OZAKI) rate = 2.5e15 / (0.5 * r.slices * (r.slices + 1));
   return flops / rate * 1e3;
 }
 
@@ -117,9 +119,10 @@ size_t elem_bytes(mm_dtype dt) { return dt == MM_F64 ? 8 : 4; }
 
 // Device bytes a request holds while admitted: its operands and output plus
 // the scratch of its path (split: bf16 hi/lo packs padded to whole tiles).
-size_t request_bytes(const mm_problem &q, mm_dtype dt, mm_mode mode) {
+size_t request_bytes(const mm_problem &q, mm_dtype dt, mm_mode mode, int slices) {
   const size_t es = elem_bytes(dt);
   size_t b = es * (size_t)(q.n * q.m + q.m * q.p + q.n * q.p);
+  if (mode == MM_MODE_OZAKI) b += ozaki_scratch_bytes(q.n, q.m, q.p, slices);
   if (mode == MM_MODE_SPLIT_BF16X3 || mode == MM_MODE_FP8) {
     const TcKind kind = mode == MM_MODE_FP8 ? kTcE4m3 : split_kind_for(q.m);
     TcChoice c = tune_choose(q.n, q.m, q.p);
@@ -153,7 +156,16 @@ mm_status launch_batch(Slot &sl, std::vector<Request *> &reqs) {
     st = run_split(sl.split_ws, probs.data(), (int)probs.size(), sl.s, nullptr);
   else if (mode == MM_MODE_FP8)
     st = run_fp8(sl.split_ws, probs.data(), (int)probs.size(), sl.s);
-  else
+  else if (mode == MM_MODE_OZAKI) {
+    // one emulated product after the other on the slot's stream
+    st = MM_OK;
+    for (size_t k = 0; k < reqs.size() && st == MM_OK; k++) {
+      const mm_problem &q = reqs[k]->pr;
+      st = run_ozaki(sl.split_ws, q.n, q.m, q.p, static_cast<const double *>(q.A),
+                     static_cast<const double *>(q.B), static_cast<double *>(q.C),
+                     reqs[k]->slices, sl.s);
+    }
+  } else
     st = enqueue_grouped(sl.split_ws, sl.tab_ws, (int)probs.size(), probs.data(), dt, mode, sl.s);
   if (st != MM_OK) return st;
   if (g_srv.check) {
@@ -395,7 +407,8 @@ mm_status mm_submit(const mm_problem *pr, mm_dtype dt, mm_mode mode, uint64_t *i
   r->pr = *pr;
   r->dt = dt;
   r->mode = mode;
-  r->bytes = request_bytes(*pr, dt, mode);
+  r->slices = g_ctx.ozaki_slices;
+  r->bytes = request_bytes(*pr, dt, mode, r->slices);
   std::lock_guard<std::mutex> lk(g_srv.mu);
   if (!g_srv.running) {
     delete r;

@@ -386,8 +386,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
           ++issued;
           const int kb = (ki * BKB) / kPackRowBytes;
           const int x = (ki * BKB) % kPackRowBytes;  // byte offset in the pack row
-          const int64_t arow = pr.a_row0 + ((int64_t)tc.mt * pr.kt + kb) * (L::kParts * kTcBM);
-          const int64_t brow = pr.b_row0 + ((int64_t)tc.nt * pr.kt + kb) * (L::kParts * bn);
+          const int64_t ak = pr.a_kstride > 0 ? pr.a_kstride : pr.kt;
+          const int64_t bk = pr.b_kstride > 0 ? pr.b_kstride : pr.kt;
+          const int64_t arow = pr.a_row0 + ((int64_t)tc.mt * ak + kb) * (L::kParts * kTcBM);
+          const int64_t brow = pr.b_row0 + ((int64_t)tc.nt * bk + kb) * (L::kParts * bn);
           const uint32_t st = sbase + stage * L::kStageBytes;
 #pragma unroll
           for (int part = 0; part < L::kParts; part++)
