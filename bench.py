@@ -524,6 +524,53 @@ def run_grouped_only(args):
     return 0
 
 
+def run_ozaki_only(args):
+    """Only the FP64 product emulated by the Ozaki scheme (MM_MODE_OZAKI) at
+    n = m = p = --dgemm-size on full 53-bit uniform[-1,1) operands (seeds
+    20/21), --ozaki-slices digit slices: rate, per-kernel device time and the
+    library's FP64 check.  Prints one JSON line; also the profiling driver of
+    the emulation's kernels."""
+    import torch
+
+    import paper_1306_6192_gb300 as mm
+    import synth
+    torch.cuda.set_device(0)
+    mm.check_status(mm.mm_init(device=0), "mm_init")
+    mm.check_status(mm.mm_ozaki_slices(args.ozaki_slices), "mm_ozaki_slices")
+    n = args.dgemm_size
+    A = torch.from_numpy(synth.uniform_pm1_f64(20, (n, n))).cuda()
+    B = torch.from_numpy(synth.uniform_pm1_f64(21, (n, n))).cuda()
+    C = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    run = lambda: mm.check_status(mm.mm_gemm_async(n, n, n, A, B, C, mm.MM_F64, mm.MM_MODE_OZAKI,
+                                                   stream), "ozaki")
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    mm.mm_trace_reset()
+    mm.mm_trace_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    mm.mm_trace_enable(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    kernels = {}
+    for k in ("ozaki_max", "ozaki_digits", "split_maps", "fp8_tc", "ozaki_sum"):
+        _, cnt, kms = mm.mm_trace_read(k)
+        if cnt:
+            kernels[k] = kms / args.steps
+    check = gpu_check(mm, n, n, n, A, B, C, mm.MM_F64)
+    mm.mm_shutdown()
+    print(json.dumps({"metric": "FP64 GEMM TFLOP/s (Ozaki scheme)", "value": 2.0 * n ** 3 / (ms * 1e-3) / 1e12,
+                      "unit": "TFLOP/s", "n": n, "slices": args.ozaki_slices, "ms": ms,
+                      "steps": args.steps, "kernels_ms": kernels, "check": check}))
+    return 0
+
+
 def run_serve_sweep(args):
     """Config-5 sweep: the Poisson replay at several fractions of the measured
     capacity, batched (2 streams, up to 256 per launch) against one request
@@ -772,6 +819,9 @@ def main(argv=None):
     ap.add_argument("--grouped-only", action="store_true",
                     help="only the grouped leg (config 4), --steps grouped launches")
     ap.add_argument("--grouped-count", type=int, default=4096)
+    ap.add_argument("--ozaki-only", action="store_true",
+                    help="only the FP64 product emulated by the Ozaki scheme")
+    ap.add_argument("--ozaki-slices", type=int, default=14)
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "mine":
         args.warmup = 3
@@ -781,6 +831,8 @@ def main(argv=None):
         return run_serve_sweep(args)
     if args.grouped_only:
         return run_grouped_only(args)
+    if args.ozaki_only:
+        return run_ozaki_only(args)
     return run_mine(args)
 
 

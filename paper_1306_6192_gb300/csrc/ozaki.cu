@@ -242,13 +242,13 @@ ozaki_digits_b_kernel(const double *__restrict__ B, int64_t m, int64_t p, int64_
   }
 }
 
-// Adds v 2^s (|v| < 2^31, 0 <= s < 64) to the two's-complement 128-bit
-// integer hi:lo.
-__device__ __forceinline__ void add_shifted(uint64_t &lo, int64_t &hi, int64_t v, int s) {
-  const uint64_t a_lo = (uint64_t)v << s;
-  const int64_t a_hi = s == 0 ? (v < 0 ? -1 : 0) : (v >> (64 - s));  // arithmetic shift
-  const uint64_t r = lo + a_lo;
-  hi += a_hi + (r < lo ? 1 : 0);
+// hi:lo <- 16 hi:lo + a for the two's-complement 128-bit integer hi:lo (one
+// Horner step over the levels; the shifts are by constants).
+__device__ __forceinline__ void horner16(uint64_t &lo, int64_t &hi, int64_t a) {
+  const uint64_t h = ((uint64_t)hi << 4) | (lo >> 60);
+  const uint64_t l = lo << 4;
+  const uint64_t r = l + (uint64_t)a;
+  hi = (int64_t)(h + (a < 0 ? ~0ull : 0ull) + (r < l ? 1ull : 0ull));
   lo = r;
 }
 
@@ -279,25 +279,39 @@ __device__ __forceinline__ double int128_scaled(uint64_t lo, int64_t hi, int k) 
 // the level sums are integers below 2^24, so their weighted sum is formed
 // exactly in 128-bit integers and rounded once to FP64 (then scaled by a
 // power of two, which rounds again only in the subnormal range); NaN where
-// row i of A or column j of B is not finite.
+// row i of A or column j of B is not finite.  A thread takes column j of the
+// rows blockIdx.y, blockIdx.y + gridDim.y, ...; the S level values of a chunk
+// are loaded together (at most kOzakiMaxSlices in flight per thread).
 __global__ void __launch_bounds__(256)
 ozaki_sum_kernel(const float *__restrict__ D, int64_t n, int64_t p, int S, int chunks,
                  const uint64_t *__restrict__ rowmax, const unsigned long long *__restrict__ colmax,
                  double *__restrict__ C) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= p) return;
   const int64_t np = n * p;
-  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < np;
-       x += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = x / p, j = x - i * p;
-    bool fa, fb;
+  bool fb;
+  const int tau = slice_exponent(colmax[j], fb);
+  for (int64_t i = blockIdx.y; i < n; i += gridDim.y) {
+    bool fa;
     const int sigma = slice_exponent(rowmax[i], fa);
-    const int tau = slice_exponent(colmax[j], fb);
+    const int64_t x = i * p + j;
+    // level sums over the chunks (exact in int64), then Horner from level 0
+    int64_t lv[kOzakiMaxSlices];
+#pragma unroll
+    for (int L = 0; L < kOzakiMaxSlices; L++) lv[L] = 0;
+    for (int c = 0; c < chunks; c++) {
+      const float *d = D + (int64_t)c * S * np + x;
+      float v[kOzakiMaxSlices];
+#pragma unroll
+      for (int L = 0; L < kOzakiMaxSlices; L++) v[L] = L < S ? __ldcs(d + (int64_t)L * np) : 0.0f;
+#pragma unroll
+      for (int L = 0; L < kOzakiMaxSlices; L++) lv[L] += __float2int_rn(v[L]);
+    }
     uint64_t lo = 0;
     int64_t hi = 0;
-    for (int c = 0; c < chunks; c++)
-      for (int L = 0; L < S; L++) {
-        const int v = __float2int_rn(__ldcs(D + ((int64_t)c * S + L) * np + x));
-        add_shifted(lo, hi, v, 4 * (S - 1 - L));
-      }
+#pragma unroll
+    for (int L = 0; L < kOzakiMaxSlices; L++)
+      if (L < S) horner16(lo, hi, lv[L]);
     C[x] = (fa && fb) ? int128_scaled(lo, hi, sigma + tau - 4 * (S + 1))
                       : __longlong_as_double(0x7ff8000000000000ll);
   }
@@ -433,9 +447,11 @@ mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *
   if (e != cudaSuccess) return note_cuda(e);
   {
     TraceScope ts("ozaki_sum", s);
-    const int64_t np = n * p;
-    const int64_t blocks = std::min<int64_t>(ceil_div(np, 256), (int64_t)sm_count() * 16);
-    ozaki_sum_kernel<<<(unsigned)blocks, 256, 0, s>>>(D, n, p, S, lay.chunks, rowmax, colmax, C);
+    const int64_t gx = ceil_div(p, 256);
+    const int64_t gy = std::max<int64_t>(1, std::min<int64_t>({n, 65535, ceil_div((int64_t)sm_count() * 8, gx)}));
+    if (gx > 0x7fffffffLL) return MM_EINVAL;
+    ozaki_sum_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(D, n, p, S, lay.chunks, rowmax,
+                                                                       colmax, C);
     if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
   }
   return MM_OK;
