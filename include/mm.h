@@ -153,7 +153,9 @@ mm_status mm_gemm(int64_t n, int64_t m, int64_t p, const void *A, const void *B,
  * result).  Rows of A or columns of B holding a NaN or an infinity give NaN
  * rows or columns of C.  Scratch: (S digit bytes per entry of A and B, plus
  * S FP32 level sums per entry of C per K chunk), library-owned.
- * Returns MM_EINVAL outside 2..16, MM_ENOTINIT before mm_init. */
+ * Returns MM_EINVAL outside 2..16, MM_ENOTINIT before mm_init.  An
+ * MM_MODE_OZAKI product whose inner dimension needs more than 1024 K chunks
+ * (m above about 5.4 million at S = 14) returns MM_EINVAL. */
 mm_status mm_ozaki_slices(int slices);
 
 /* As mm_gemm, but device pointers only and asynchronous: the work is queued on

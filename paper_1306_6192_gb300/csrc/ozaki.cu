@@ -63,6 +63,7 @@ constexpr int kRowsPerItem = 8;   // maxima: warps per block, one row of A each
 constexpr int kColStrip = 32;     // maxima: columns of B per strip
 constexpr int kRowChunk = 256;    // maxima: rows of B per strip item
 constexpr int kSeg = 16;          // digits: consecutive k per thread
+constexpr int kOzakiMaxChunks = 1024;  // K chunks (the sum's int64 parts stay exact)
 
 __device__ __forceinline__ uint64_t abs_bits64(double x) {
   return (uint64_t)__double_as_longlong(x) & 0x7fffffffffffffffull;
@@ -242,16 +243,6 @@ ozaki_digits_b_kernel(const double *__restrict__ B, int64_t m, int64_t p, int64_
   }
 }
 
-// hi:lo <- 16 hi:lo + a for the two's-complement 128-bit integer hi:lo (one
-// Horner step over the levels; the shifts are by constants).
-__device__ __forceinline__ void horner16(uint64_t &lo, int64_t &hi, int64_t a) {
-  const uint64_t h = ((uint64_t)hi << 4) | (lo >> 60);
-  const uint64_t l = lo << 4;
-  const uint64_t r = l + (uint64_t)a;
-  hi = (int64_t)(h + (a < 0 ? ~0ull : 0ull) + (r < l ? 1ull : 0ull));
-  lo = r;
-}
-
 // The double nearest to hi:lo (ties to even), times 2^k.
 __device__ __forceinline__ double int128_scaled(uint64_t lo, int64_t hi, int k) {
   const bool neg = hi < 0;
@@ -272,7 +263,11 @@ __device__ __forceinline__ double int128_scaled(uint64_t lo, int64_t hi, int k) 
     d = __ull2double_rn(top | (lost != 0 ? 1ull : 0ull));
     k += sh;
   }
-  return scalbn(neg ? -d : d, k);
+  d = neg ? -d : d;
+  // times 2^k: one multiplication by the power of two when it is a normal
+  // double (correctly rounded, as scalbn), scalbn otherwise
+  if (k >= -1022 && k <= 1023) return d * __longlong_as_double((long long)(k + 1023) << 52);
+  return scalbn(d, k);
 }
 
 // c_ij = 2^(sigma_i + tau_j - 4(S+1)) sum_c sum_L D[c][L][i][j] 2^(4(S-1-L)):
@@ -282,7 +277,7 @@ __device__ __forceinline__ double int128_scaled(uint64_t lo, int64_t hi, int k) 
 // row i of A or column j of B is not finite.  A thread takes column j of the
 // rows blockIdx.y, blockIdx.y + gridDim.y, ...; the S level values of a chunk
 // are loaded together (at most kOzakiMaxSlices in flight per thread).
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 ozaki_sum_kernel(const float *__restrict__ D, int64_t n, int64_t p, int S, int chunks,
                  const uint64_t *__restrict__ rowmax, const unsigned long long *__restrict__ colmax,
                  double *__restrict__ C) {
@@ -295,23 +290,33 @@ ozaki_sum_kernel(const float *__restrict__ D, int64_t n, int64_t p, int S, int c
     bool fa;
     const int sigma = slice_exponent(rowmax[i], fa);
     const int64_t x = i * p + j;
-    // level sums over the chunks (exact in int64), then Horner from level 0
-    int64_t lv[kOzakiMaxSlices];
-#pragma unroll
-    for (int L = 0; L < kOzakiMaxSlices; L++) lv[L] = 0;
+    // Horner by 16 over levels 0..h-1 into X and h..S-1 into Y (int64: each
+    // part at most (2^24 - 1)(16^8 - 1)/15 < 2^52.1 per chunk, below 2^63 over
+    // at most kOzakiMaxChunks = 2^10 chunks), then v = X 16^(S-h) + Y once in
+    // 128 bits
+    const int h = (S + 1) / 2;
+    int64_t X = 0, Y = 0;
     for (int c = 0; c < chunks; c++) {
       const float *d = D + (int64_t)c * S * np + x;
       float v[kOzakiMaxSlices];
 #pragma unroll
       for (int L = 0; L < kOzakiMaxSlices; L++) v[L] = L < S ? __ldcs(d + (int64_t)L * np) : 0.0f;
+      int64_t xc = 0, yc = 0;
 #pragma unroll
-      for (int L = 0; L < kOzakiMaxSlices; L++) lv[L] += __float2int_rn(v[L]);
+      for (int L = 0; L < kOzakiMaxSlices; L++) {
+        const int64_t q = __float2int_rn(v[L]);
+        if (L < h) xc = xc * 16 + q;
+        else if (L < S) yc = yc * 16 + q;
+      }
+      X += xc;
+      Y += yc;
     }
-    uint64_t lo = 0;
-    int64_t hi = 0;
-#pragma unroll
-    for (int L = 0; L < kOzakiMaxSlices; L++)
-      if (L < S) horner16(lo, hi, lv[L]);
+    const int sh = 4 * (S - h);  // 4..32
+    uint64_t lo = (uint64_t)X << sh;
+    int64_t hi = X >> (64 - sh);
+    const uint64_t r = lo + (uint64_t)Y;
+    hi += (Y < 0 ? -1 : 0) + (r < lo ? 1 : 0);
+    lo = r;
     C[x] = (fa && fb) ? int128_scaled(lo, hi, sigma + tau - 4 * (S + 1))
                       : __longlong_as_double(0x7ff8000000000000ll);
   }
@@ -342,6 +347,7 @@ mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *
   OzLayout lay;
   lay.S = S;
   lay.mc = ozaki_chunk(S);
+  if (ceil_div(m, lay.mc) > kOzakiMaxChunks) return MM_EINVAL;
   lay.chunks = (int)ceil_div(m, lay.mc);
   TcChoice ch = tune_choose(n, std::min(m, lay.mc), p);
   lay.bn = tc_bn(kTcE4m3, ch.bn);
@@ -448,7 +454,8 @@ mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *
   {
     TraceScope ts("ozaki_sum", s);
     const int64_t gx = ceil_div(p, 256);
-    const int64_t gy = std::max<int64_t>(1, std::min<int64_t>({n, 65535, ceil_div((int64_t)sm_count() * 8, gx)}));
+    // one wave: four blocks per SM (the launch bound)
+    const int64_t gy = std::max<int64_t>(1, std::min<int64_t>({n, 65535, ceil_div((int64_t)sm_count() * 4, gx)}));
     if (gx > 0x7fffffffLL) return MM_EINVAL;
     ozaki_sum_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(D, n, p, S, lay.chunks, rowmax,
                                                                        colmax, C);
