@@ -43,9 +43,13 @@
 //       b0_c + ((nt*S + slot)*kt_c + kb)*bn, slot = S-1-u for slice u, one
 //       row per column of B, so that B's slices L..0 are contiguous;
 //   then the row/column maxima (bit patterns), zero scale words, the level
-//   sums D (FP32, [chunk][level][n][p]), the problem table and its maps.
+//   sums D (FP32, [chunk][level] planes of n x p, padded so that planes are
+//   not a power of two apart), the problem table and its unit map.
 // The level problem (c, L) reads A's K blocks [0, (L+1) kt_c) and B's
 // [(S-1-L) kt_c, S kt_c) of each tile through the table's K stride S kt_c.
+// The level problems of a chunk share one tile grid; their work units are
+// interleaved tile by tile (unit stride S), longest level first, so that the
+// CTAs running at the same time read the same digit windows from L2.
 // Rows (columns) holding a NaN or an infinity give NaN rows (columns) of C.
 #include <cuda_fp8.h>
 
@@ -270,6 +274,14 @@ __device__ __forceinline__ double int128_scaled(uint64_t lo, int64_t hi, int k) 
   return scalbn(d, k);
 }
 
+// Item map of the interleaved level problems: unit u of chunk c (units
+// [c*S*T, (c+1)*S*T), T tiles) belongs to problem c*S + u % S.
+__global__ void __launch_bounds__(256)
+ozaki_map_kernel(int *__restrict__ map, int64_t units, int64_t per_chunk, int S) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < units) map[u] = (int)((u / per_chunk) * S + (u % per_chunk) % S);
+}
+
 // c_ij = 2^(sigma_i + tau_j - 4(S+1)) sum_c sum_L D[c][L][i][j] 2^(4(S-1-L)):
 // the level sums are integers below 2^24, so their weighted sum is formed
 // exactly in 128-bit integers and rounded once to FP64 (then scaled by a
@@ -278,12 +290,11 @@ __device__ __forceinline__ double int128_scaled(uint64_t lo, int64_t hi, int k) 
 // rows blockIdx.y, blockIdx.y + gridDim.y, ...; the S level values of a chunk
 // are loaded together (at most kOzakiMaxSlices in flight per thread).
 __global__ void __launch_bounds__(256, 4)
-ozaki_sum_kernel(const float *__restrict__ D, int64_t n, int64_t p, int S, int chunks,
+ozaki_sum_kernel(const float *__restrict__ D, int64_t plane, int64_t n, int64_t p, int S, int chunks,
                  const uint64_t *__restrict__ rowmax, const unsigned long long *__restrict__ colmax,
                  double *__restrict__ C) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= p) return;
-  const int64_t np = n * p;
   bool fb;
   const int tau = slice_exponent(colmax[j], fb);
   for (int64_t i = blockIdx.y; i < n; i += gridDim.y) {
@@ -297,10 +308,10 @@ ozaki_sum_kernel(const float *__restrict__ D, int64_t n, int64_t p, int S, int c
     const int h = (S + 1) / 2;
     int64_t X = 0, Y = 0;
     for (int c = 0; c < chunks; c++) {
-      const float *d = D + (int64_t)c * S * np + x;
+      const float *d = D + (int64_t)c * S * plane + x;
       float v[kOzakiMaxSlices];
 #pragma unroll
-      for (int L = 0; L < kOzakiMaxSlices; L++) v[L] = L < S ? __ldcs(d + (int64_t)L * np) : 0.0f;
+      for (int L = 0; L < kOzakiMaxSlices; L++) v[L] = L < S ? __ldcs(d + (int64_t)L * plane) : 0.0f;
       int64_t xc = 0, yc = 0;
 #pragma unroll
       for (int L = 0; L < kOzakiMaxSlices; L++) {
@@ -327,9 +338,9 @@ struct OzLayout {
   int S, chunks, bn, mt, nt;
   int64_t mc;
   std::vector<int64_t> k0, kc, kt, a0, b0;
-  int64_t rows = 0;
+  int64_t rows = 0, plane = 0;
   size_t max_off, zero_off, zero_end, d_off, tab_off, map_off, need;
-  int64_t units = 0, packs = 0;
+  int64_t units = 0;
 };
 
 }  // namespace
@@ -366,15 +377,20 @@ mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *
   }
   if (lay.rows > 0x7fffffffLL) return MM_EINVAL;
   const int nprobs = lay.chunks * S;
+  const int64_t tiles = (int64_t)lay.mt * lay.nt;
+  // level planes of D, padded so that the planes of one entry do not sit a
+  // power of two apart (128-byte aligned)
+  lay.plane = (n * p + 31) / 32 * 32 + 32;
   std::vector<SplitProb> tab((size_t)nprobs);
-  // level problems, longest K first (the persistent grid takes units in
-  // order, so the short ones fill the last wave)
-  int g = 0;
-  for (int L = S - 1; L >= 0; L--)
-    for (int c = 0; c < lay.chunks; c++, g++) {
-      SplitProb &sp = tab[(size_t)g];
+  // problem c*S + k is level L = S-1-k of chunk c; the units of a chunk run
+  // tile by tile, and within a tile the S levels longest first, so CTAs that
+  // run at the same time read the same windows of the digit packs
+  for (int c = 0; c < lay.chunks; c++) {
+    const int64_t kt = lay.kt[(size_t)c];
+    for (int k = 0; k < S; k++) {
+      const int L = S - 1 - k;
+      SplitProb &sp = tab[(size_t)c * S + k];
       std::memset(&sp, 0, sizeof(sp));
-      const int64_t kt = lay.kt[(size_t)c];
       sp.n = (int32_t)n;
       sp.p = (int32_t)p;
       sp.kt = (int32_t)((L + 1) * kt);
@@ -387,23 +403,23 @@ mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *
       sp.b_row0 = lay.b0[(size_t)c] + (int64_t)(S - 1 - L) * kt * lay.bn;
       sp.a_kstride = (int32_t)(S * kt);
       sp.b_kstride = (int32_t)(S * kt);
-      sp.unit_start = (int32_t)lay.units;
-      lay.units += (int64_t)lay.mt * lay.nt;
-      sp.pack_start = (int32_t)lay.packs;
-      lay.packs += (int64_t)(lay.mt + lay.nt) * sp.kt;
-      sp.split_from = lay.mt * lay.nt;
+      sp.unit_start = (int32_t)(lay.units + k);
+      sp.unit_stride = S;
+      sp.split_from = (int32_t)tiles;
       sp.split_s = 1;
-      sp.C = reinterpret_cast<float *>((uintptr_t)(((int64_t)c * S + L) * n * p));  // offset
+      sp.C = reinterpret_cast<float *>((uintptr_t)(((int64_t)c * S + L) * lay.plane));  // offset
     }
-  if (lay.units > 0x7fffffffLL || lay.packs > 0x7fffffffLL) return MM_EINVAL;
+    lay.units += (int64_t)S * tiles;
+  }
+  if (lay.units > 0x7fffffffLL) return MM_EINVAL;
   const size_t pack_bytes = (size_t)lay.rows * kPackRowBytes;
   lay.max_off = (pack_bytes + 255) & ~(size_t)255;  // row maxima (n) + column maxima (p)
   lay.zero_off = lay.max_off;
   lay.zero_end = lay.max_off + (size_t)(n + p) * 8 + (size_t)(n + p) * 4;  // + zero scale words
   lay.d_off = (lay.zero_end + 255) & ~(size_t)255;
-  lay.tab_off = (lay.d_off + (size_t)nprobs * n * p * sizeof(float) + 255) & ~(size_t)255;
+  lay.tab_off = (lay.d_off + (size_t)nprobs * lay.plane * sizeof(float) + 255) & ~(size_t)255;
   lay.map_off = (lay.tab_off + (size_t)nprobs * sizeof(SplitProb) + 255) & ~(size_t)255;
-  lay.need = lay.map_off + (size_t)(lay.units + lay.packs) * sizeof(int);
+  lay.need = lay.map_off + (size_t)lay.units * sizeof(int);
   cudaError_t e = ws.reserve(lay.need, s);
   if (e != cudaSuccess) return note_cuda(e);
   uint8_t *base = static_cast<uint8_t *>(ws.ptr);
@@ -440,11 +456,12 @@ mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
   }
-  int *unit_map = nullptr;
-  if (nprobs > 1) {
-    unit_map = reinterpret_cast<int *>(base + lay.map_off);
-    e = launch_split_maps(d_tab, nprobs, unit_map, unit_map + lay.units, nullptr, nullptr, s);
-    if (e != cudaSuccess) return note_cuda(e);
+  int *unit_map = reinterpret_cast<int *>(base + lay.map_off);
+  {
+    TraceScope ts("ozaki_map", s);
+    ozaki_map_kernel<<<(unsigned)ceil_div(lay.units, 256), 256, 0, s>>>(unit_map, lay.units,
+                                                                          S * tiles, S);
+    if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
   }
   TcConfig cfg{128, 4, ch.grid};
   cfg.max_bn = lay.bn;
@@ -457,8 +474,8 @@ mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *
     // one wave: four blocks per SM (the launch bound)
     const int64_t gy = std::max<int64_t>(1, std::min<int64_t>({n, 65535, ceil_div((int64_t)sm_count() * 4, gx)}));
     if (gx > 0x7fffffffLL) return MM_EINVAL;
-    ozaki_sum_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(D, n, p, S, lay.chunks, rowmax,
-                                                                       colmax, C);
+    ozaki_sum_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(D, lay.plane, n, p, S,
+                                                                       lay.chunks, rowmax, colmax, C);
     if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
   }
   return MM_OK;
@@ -470,8 +487,9 @@ size_t ozaki_scratch_bytes(int64_t n, int64_t m, int64_t p, int S) {
   const int64_t chunks = ceil_div(m, mc);
   const int64_t kt_all = ceil_div(m, 128) + chunks;  // K blocks over all chunks (bound)
   const int64_t rows = (ceil_div(n, kTcBM) * kTcBM + ceil_div(p, 128) * 256) * S * kt_all;
-  return (size_t)rows * kPackRowBytes + (size_t)chunks * S * n * p * sizeof(float) +
-         (size_t)(n + p) * 12 + ((size_t)1 << 20);
+  return (size_t)rows * kPackRowBytes + (size_t)chunks * S * (n * p + 64) * sizeof(float) +
+         (size_t)(n + p) * 12 + (size_t)chunks * S * ceil_div(n, kTcBM) * ceil_div(p, 128) * 4 +
+         ((size_t)1 << 20);
 }
 
 }  // namespace mm
