@@ -82,11 +82,6 @@ struct SplitProb {
   // kt, the layout above); a larger stride lets a product read a window of
   // kt K blocks out of a longer pack (the FP64 emulation's level products)
   int32_t a_kstride, b_kstride;
-  // work units of the table between consecutive units of this product (0 or
-  // 1: its units are contiguous from unit_start; k > 1: unit_start + i*k,
-  // the units of k products with equal tile grids interleaved tile by tile,
-  // with an item map giving each unit's product)
-  int32_t unit_stride;
 };
 
 // Work units of a product with its tail split: whole tiles, then the parts.

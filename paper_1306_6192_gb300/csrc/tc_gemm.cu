@@ -257,7 +257,6 @@ __device__ __forceinline__ UnitCoord decode_unit(const SplitProb *__restrict__ p
       find_problem(probs, nprobs, map, u, [](const SplitProb &q) { return q.unit_start; });
   const SplitProb &pr = probs[g];
   int t = u - pr.unit_start, h = -1;
-  if (pr.unit_stride > 1) t /= pr.unit_stride;
   if (pr.split_s > 1 && t >= pr.split_from) {
     const int v = t - pr.split_from;
     t = pr.split_from + v / pr.split_s;
