@@ -377,6 +377,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
         const uint32_t bytes = (uint32_t)(L::kParts * (kTcBM + bn) * BKB);
         int k0, k1;
         unit_krange<BKB>(pr, tc.h, kiters, k0, k1);
+        // first pack rows of the unit's A and B tiles (K block 0)
+        const int64_t ak = pr.a_kstride > 0 ? pr.a_kstride : pr.kt;
+        const int64_t bk = pr.b_kstride > 0 ? pr.b_kstride : pr.kt;
+        const int64_t abase = pr.a_row0 + (int64_t)tc.mt * ak * (L::kParts * kTcBM);
+        const int64_t bbase = pr.b_row0 + (int64_t)tc.nt * bk * (L::kParts * bn);
         for (int ki = k0; ki < k1; ki++) {
           if (!mbar_wait(empty_bar(stage), phase ^ 1u, err, 1, true, kWaitLimitNs)) {
             ok = false;
@@ -386,10 +391,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
           ++issued;
           const int kb = (ki * BKB) / kPackRowBytes;
           const int x = (ki * BKB) % kPackRowBytes;  // byte offset in the pack row
-          const int64_t ak = pr.a_kstride > 0 ? pr.a_kstride : pr.kt;
-          const int64_t bk = pr.b_kstride > 0 ? pr.b_kstride : pr.kt;
-          const int64_t arow = pr.a_row0 + ((int64_t)tc.mt * ak + kb) * (L::kParts * kTcBM);
-          const int64_t brow = pr.b_row0 + ((int64_t)tc.nt * bk + kb) * (L::kParts * bn);
+          const int64_t arow = abase + (int64_t)kb * (L::kParts * kTcBM);
+          const int64_t brow = bbase + (int64_t)kb * (L::kParts * bn);
           const uint32_t st = sbase + stage * L::kStageBytes;
 #pragma unroll
           for (int part = 0; part < L::kParts; part++)
