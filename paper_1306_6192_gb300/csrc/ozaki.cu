@@ -169,7 +169,8 @@ ozaki_max_kernel(const double *__restrict__ A, const double *__restrict__ B, int
 
 // A digits of one K chunk [k0, k0 + mc): one block per tile (mt, kb); a
 // thread takes 16 consecutive k of a row (8 threads per 128-k row, 4 rows per
-// warp: both the FP64 reads and the 16-byte digit stores are whole lines).
+// warp: a warp's 16 loads read four whole 1 KB row segments, and each digit
+// store instruction writes four whole 128-byte pack rows).
 __global__ void __launch_bounds__(256)
 ozaki_digits_a_kernel(const double *__restrict__ A, int64_t n, int64_t m, int64_t k0, int64_t mc,
                       int kt, int S, const uint64_t *__restrict__ rowmax, uint4 *__restrict__ pack,
