@@ -158,6 +158,17 @@ mm_status mm_gemm(int64_t n, int64_t m, int64_t p, const void *A, const void *B,
  * (m above about 5.4 million at S = 14) returns MM_EINVAL. */
 mm_status mm_ozaki_slices(int slices);
 
+/* Plan of an MM_MODE_OZAKI product, a pure host function (no device, no
+ * mm_init): for A n x m, B m x p and `slices` digit slices, writes the K
+ * columns per chunk (the largest multiple of 128 with
+ * 225 * slices * columns < 2^24, so every level sum stays an exact FP32
+ * integer), the number of chunks (ceil(m / columns); 0 for m = 0) and an
+ * upper bound of the library scratch the product holds (digit packs, FP32
+ * level sums, maxima, table).  Returns MM_EINVAL for negative sizes, slices
+ * outside 2..16, NULL outputs or more than 1024 chunks. */
+mm_status mm_ozaki_plan(int64_t n, int64_t m, int64_t p, int slices, int64_t *chunk_columns,
+                        int *chunks, size_t *scratch_bytes);
+
 /* As mm_gemm, but device pointers only and asynchronous: the work is queued on
  * `stream` (a cudaStream_t; NULL = the library stream) and the call returns
  * after the launches.  Calls that use the split or FP8 path share the

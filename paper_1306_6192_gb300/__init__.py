@@ -99,6 +99,9 @@ def lib():
         L.mm_gemm_split_static.restype = ctypes.c_int
         L.mm_ozaki_slices.argtypes = [ctypes.c_int]
         L.mm_ozaki_slices.restype = ctypes.c_int
+        L.mm_ozaki_plan.argtypes = [_i64, _i64, _i64, ctypes.c_int, ctypes.POINTER(_i64),
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)]
+        L.mm_ozaki_plan.restype = ctypes.c_int
         for name in ("mm_init", "mm_shutdown", "mm_gemm", "mm_gemm_async", "mm_gemm_grouped",
                      "mm_gemm_grouped_async", "mm_sync", "mm_check", "mm_submit", "mm_poll",
                      "mm_wait", "mm_serve_stats", "mm_tune", "mm_tune_save", "mm_tune_load",
@@ -274,6 +277,15 @@ def mm_tail_plan(tiles, grid, kt, bn, m, products):
 def mm_ozaki_slices(slices: int) -> int:
     """Digit slices S (2..16) of MM_MODE_OZAKI for the products queued next."""
     return lib().mm_ozaki_slices(int(slices))
+
+
+def mm_ozaki_plan(n, m, p, slices):
+    """Returns (status, K columns per chunk, chunks, scratch bytes bound) of an
+    MM_MODE_OZAKI product (a pure host function; no GPU needed)."""
+    mc, q, b = _i64(0), ctypes.c_int(0), ctypes.c_size_t(0)
+    st = lib().mm_ozaki_plan(n, m, p, int(slices), ctypes.byref(mc), ctypes.byref(q),
+                             ctypes.byref(b))
+    return st, mc.value, q.value, b.value
 
 
 def mm_trace_enable(on: bool = True) -> int:

@@ -58,13 +58,15 @@
 #include "split_common.cuh"
 
 namespace mm {
+
+constexpr int kOzakiMaxChunks = 1024;  // K chunks (the sum's int64 parts stay exact)
+
 namespace {
 
 constexpr int kRowsPerItem = 8;   // maxima: warps per block, one row of A each
 constexpr int kColStrip = 32;     // maxima: columns of B per strip
 constexpr int kRowChunk = 256;    // maxima: rows of B per strip item
 constexpr int kSeg = 16;          // digits: consecutive k per thread
-constexpr int kOzakiMaxChunks = 1024;  // K chunks (the sum's int64 parts stay exact)
 
 __device__ __forceinline__ uint64_t abs_bits64(double x) {
   return (uint64_t)__double_as_longlong(x) & 0x7fffffffffffffffull;
@@ -487,7 +489,26 @@ size_t ozaki_scratch_bytes(int64_t n, int64_t m, int64_t p, int S) {
   const int64_t rows = (ceil_div(n, kTcBM) * kTcBM + ceil_div(p, 128) * 256) * S * kt_all;
   return (size_t)rows * kPackRowBytes + (size_t)chunks * S * (n * p + 64) * sizeof(float) +
          (size_t)(n + p) * 12 + (size_t)chunks * S * ceil_div(n, kTcBM) * ceil_div(p, 128) * 4 +
-         ((size_t)1 << 20);
+         (size_t)chunks * S * sizeof(SplitProb) + ((size_t)1 << 20);
 }
+
+}  // namespace mm
+
+extern "C" mm_status mm_ozaki_plan(int64_t n, int64_t m, int64_t p, int slices,
+                                   int64_t *chunk_columns, int *chunks, size_t *scratch_bytes) {
+  using namespace mm;
+  if (n < 0 || m < 0 || p < 0 || slices < kOzakiMinSlices || slices > kOzakiMaxSlices ||
+      !chunk_columns || !chunks || !scratch_bytes)
+    return MM_EINVAL;
+  const int64_t mc = ozaki_chunk(slices);
+  const int64_t q = ceil_div(m, mc);
+  if (q > kOzakiMaxChunks) return MM_EINVAL;
+  *chunk_columns = mc;
+  *chunks = (int)q;
+  *scratch_bytes = ozaki_scratch_bytes(n, m, p, slices);
+  return MM_OK;
+}
+
+namespace mm {
 
 }  // namespace mm
