@@ -359,6 +359,91 @@ def bench_paper_workloads(mm, stream, peaks, n: int = 4096, reps: int = 5):
     return out
 
 
+def bench_stress(mm, stream, peaks, reps: int = 10):
+    """Config 3, shape and value stress with FP32 in/out: the rectangular
+    8192x512.512x8192 product (TFLOP/s), the skinny 64x16384.16384x64 one
+    (bandwidth-bound: GB/s of A + B + C against the measured HBM copy rate,
+    64 operand copies taken round-robin so the 512 MB footprint exceeds L2),
+    B = diag(d) at 4096 through the general product, and 4096^3 with entries
+    s 2^e, e real uniform in [-20, 20) (split-precision scaling; FP8 error
+    reported).  Device time per product from CUDA events on the stream; the
+    library's FP64 check for the error.  A failure is recorded, not raised."""
+    import torch
+
+    import synth
+    out = {}
+    hbm = peaks.get("hbm_gbs", 6797.9)
+
+    def per_call_ms(fn, count, warm=2):
+        for k in range(warm):
+            fn(k)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(count):
+            fn(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / count
+
+    def gemm(n, m, p, A, B, C, md):
+        mm.check_status(mm.mm_gemm_async(n, m, p, A, B, C, mm.MM_F32, md, stream), "stress")
+
+    modes = (("simt", mm.MM_MODE_SIMT), ("split", mm.MM_MODE_SPLIT_BF16X3))
+    try:
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(3)
+        # 3a: rectangular, a large C write
+        n, m, p = 8192, 512, 8192
+        A = torch.rand(n, m, device="cuda", generator=gen) * 2 - 1
+        B = torch.rand(m, p, device="cuda", generator=gen) * 2 - 1
+        C = torch.empty(n, p, device="cuda")
+        for name, md in modes:
+            ms = per_call_ms(lambda k: gemm(n, m, p, A, B, C, md), reps)
+            out["rect_8192x512x8192_" + name] = {
+                "ms": ms, "tflops": 2.0 * n * m * p / (ms * 1e-3) / 1e12,
+                "gbs": 4.0 * (n * m + m * p + n * p) / (ms * 1e-3) / 1e9}
+        out["rect_check_split"] = gpu_check(mm, n, m, p, A, B, C, mm.MM_F32)
+        del A, B, C
+        # 3b: skinny, bandwidth-bound
+        n, m, p, copies = 64, 16384, 64, 64
+        As = torch.rand(copies, n, m, device="cuda", generator=gen) * 2 - 1
+        Bs = torch.rand(copies, m, p, device="cuda", generator=gen) * 2 - 1
+        Cs = torch.empty(copies, n, p, device="cuda")
+        nbytes = 4.0 * (n * m + m * p + n * p)
+        for name, md in modes:
+            ms = per_call_ms(lambda k: gemm(n, m, p, As[k % copies], Bs[k % copies],
+                                            Cs[k % copies], md), 4 * copies)
+            gbs = nbytes / (ms * 1e-3) / 1e9
+            out["skinny_64x16384x64_" + name] = {"us": ms * 1e3, "gbs": gbs, "frac_hbm": gbs / hbm}
+        out["skinny_check_split"] = gpu_check(mm, n, m, p, As[0], Bs[0], Cs[0], mm.MM_F32)
+        del As, Bs, Cs
+        # 3c: B = diag(d) through the general product (dense flops counted)
+        n = 4096
+        A = torch.rand(n, n, device="cuda", generator=gen) * 2 - 1
+        Bd = torch.diag(torch.rand(n, device="cuda", generator=gen) * 2 - 1).contiguous()
+        C = torch.empty(n, n, device="cuda")
+        for name, md in modes:
+            ms = per_call_ms(lambda k: gemm(n, n, n, A, Bd, C, md), reps)
+            out["diag_4096_" + name] = {"ms": ms, "dense_tflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e12}
+        del A, Bd, C
+        # 3d/3e: s 2^e entries, e real in [-20, 20)
+        A = torch.from_numpy(synth.pow2_real(30, (n, n))).cuda()
+        B = torch.from_numpy(synth.pow2_real(31, (n, n))).cuda()
+        C = torch.empty(n, n, device="cuda")
+        ms = per_call_ms(lambda k: gemm(n, n, n, A, B, C, mm.MM_MODE_SPLIT_BF16X3), reps)
+        out["pow2_4096_split"] = {"ms": ms, "tflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e12,
+                                  "check": gpu_check(mm, n, n, n, A, B, C, mm.MM_F32)}
+        gemm(n, n, n, A, B, C, mm.MM_MODE_FP8)
+        mm.check_status(mm.mm_sync(stream), "stress fp8")
+        out["pow2_4096_fp8_check"] = gpu_check(mm, n, n, n, A, B, C, mm.MM_F32)
+        del A, B, C
+    except Exception as ex:  # recorded in the JSON line instead of ending the run
+        out["error"] = repr(ex)
+    return out
+
+
 def bench_grouped(mm, stream, steps: int, seed: int = 4, count: int = 4096):
     """Grouped GEMM of `count` products, n, m, p uniform over {32, ..., 1024}
     step 32 (seeded), split path: one grouped launch per step vs one launch
@@ -571,6 +656,21 @@ def run_ozaki_only(args):
     return 0
 
 
+def run_stress_only(args):
+    """Only the config-3 stress shapes (bench_stress).  Prints one JSON line."""
+    import torch
+
+    import paper_1306_6192_gb300 as mm
+    torch.cuda.set_device(0)
+    mm.check_status(mm.mm_init(device=0), "mm_init")
+    stream = torch.cuda.Stream()
+    peaks, _ = _peaks()
+    out = bench_stress(mm, stream, peaks)
+    mm.mm_shutdown()
+    print(json.dumps({"metric": "stress shapes", "stress_shapes": out}))
+    return 0 if "error" not in out else 1
+
+
 def run_serve_sweep(args):
     """Config-5 sweep: the Poisson replay at several fractions of the measured
     capacity, batched (2 streams, up to 256 per launch) against one request
@@ -758,6 +858,7 @@ def run_mine(args):
         extra["square_sizes"] = sizes
         line["paths"] = extra
         line["paper_workloads_4096"] = bench_paper_workloads(mm, stream, peaks)
+        line["stress_shapes"] = bench_stress(mm, stream, peaks)
         line["grouped"] = bench_grouped(mm, stream, max(3, args.steps // 20))
         cap = None
         serving = {}
@@ -822,6 +923,7 @@ def main(argv=None):
     ap.add_argument("--ozaki-only", action="store_true",
                     help="only the FP64 product emulated by the Ozaki scheme")
     ap.add_argument("--ozaki-slices", type=int, default=14)
+    ap.add_argument("--stress-only", action="store_true", help="only the config-3 stress shapes")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "mine":
         args.warmup = 3
@@ -833,6 +935,8 @@ def main(argv=None):
         return run_grouped_only(args)
     if args.ozaki_only:
         return run_ozaki_only(args)
+    if args.stress_only:
+        return run_stress_only(args)
     return run_mine(args)
 
 
