@@ -171,15 +171,16 @@ mm_status mm_ozaki_plan(int64_t n, int64_t m, int64_t p, int slices, int64_t *ch
 
 /* As mm_gemm, but device pointers only and asynchronous: the work is queued on
  * `stream` (a cudaStream_t; NULL = the library stream) and the call returns
- * after the launches.  Calls that use the split or FP8 path share the
- * library's scratch and must be ordered on one stream. */
+ * after the launches.  Calls that use the split, FP8 or Ozaki path share the
+ * library's scratch of that path and must be ordered on one stream. */
 mm_status mm_gemm_async(int64_t n, int64_t m, int64_t p, const void *A,
                         const void *B, void *C, mm_dtype dt, mm_mode mode,
                         void *stream);
 
 /* count independent products in one persistent launch per path (grouped
  * GEMM).  probs is a host array; A/B/C inside it are device pointers.  Tile
- * shapes and raster order come from the autotuner table.  Synchronous. */
+ * shapes and raster order come from the autotuner table.  Synchronous.
+ * MM_MODE_OZAKI products run one after the other (each its own launches). */
 mm_status mm_gemm_grouped(int32_t count, const mm_problem *probs, mm_dtype dt,
                           mm_mode mode);
 mm_status mm_gemm_grouped_async(int32_t count, const mm_problem *probs,
@@ -207,7 +208,9 @@ mm_status mm_check(int64_t n, int64_t m, int64_t p, const void *A,
 /* Queues one request (device pointers; they must stay valid until mm_poll or
  * mm_wait reports a final status).  Admission: the request's operand, output
  * and scratch bytes must fit the HBM budget; a request that can never fit
- * returns MM_EBUDGET immediately.  *id_out receives the request id. */
+ * returns MM_EBUDGET immediately.  Requests are batched by dtype and mode;
+ * a batch of MM_MODE_OZAKI requests runs them one after the other on its
+ * stream.  *id_out receives the request id. */
 mm_status mm_submit(const mm_problem *pr, mm_dtype dt, mm_mode mode,
                     uint64_t *id_out);
 
