@@ -174,17 +174,20 @@ def default() -> Oracle:
 # -- error metric ---------------------------------------------------------------
 
 def rel_errors(c_hat, c_ref, abs_ref):
-    """e = |c_hat - c_ref| / abs_ref elementwise; inf where abs_ref == 0 and
-    c_hat != c_ref, 0 where both are zero."""
+    """e = |c_hat - c_ref| / abs_ref elementwise; where abs_ref == 0 the entry
+    must be exact: 0 if c_hat == c_ref (signed zeros compare equal), inf
+    otherwise.  A NaN on either side, or infinities that do not cancel to a
+    finite difference, give inf: a non-finite entry is never within a
+    tolerance (tests of NaN/inf propagation check those entries directly)."""
     c_hat = np.asarray(c_hat, np.float64)
     c_ref = np.asarray(c_ref, np.float64)
     abs_ref = np.asarray(abs_ref, np.float64)
-    diff = np.abs(c_hat - c_ref)
+    with np.errstate(invalid="ignore"):
+        diff = np.abs(c_hat - c_ref)
     with np.errstate(divide="ignore", invalid="ignore"):
         e = np.where(abs_ref > 0, diff / np.where(abs_ref > 0, abs_ref, 1.0),
                      np.where(diff == 0, 0.0, np.inf))
-    e = np.where(np.isnan(c_hat) & ~np.isnan(c_ref), np.inf, e)
-    return e
+    return np.where(np.isnan(diff), np.inf, e)
 
 
 def rel_errors_complex(c_hat, c_ref, abs_ref):
@@ -215,6 +218,8 @@ def tolerance(m: int, dtype: str) -> float:
 
 
 def normwise_error(c_hat, c_ref) -> float:
+    """max |c_hat - c_ref| / max |c_ref| over all entries (reported, never a
+    gate); the plain max difference when c_ref is all zero, 0 when empty."""
     c_ref = np.asarray(c_ref, np.float64)
     mx = float(np.max(np.abs(c_ref))) if c_ref.size else 0.0
     d = float(np.max(np.abs(np.asarray(c_hat, np.float64) - c_ref))) if c_ref.size else 0.0
