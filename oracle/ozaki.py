@@ -22,7 +22,11 @@ path implements:
   3. K chunks.  The inner dimension is cut into chunks of
      mc = floor(floor((2^24 - 1) / (225 S)) / 128) * 128 columns (the last one
      shorter); with |d| <= 15 a level of S pairs over mc columns stays below
-     2^24.
+     2^24, so each level sum is an integer that FP32 holds exactly (the
+     condition under which the tensor cores' FP32 accumulation of the digit
+     products is error-free).  The chunking leaves the exact result unchanged;
+     the oracle checks that condition on every level sum it forms and raises
+     if a chunk rule ever lets one reach 2^24.
   4. Levels.  For each chunk c and L = 0..S-1,
          D[c][L] = sum_{t+u=L} A_t[:, chunk c] . B_u[chunk c, :]
      exactly (integers; float64 matrix products of integers whose partial
@@ -87,6 +91,8 @@ def level_sums(Ad: np.ndarray, Bd: np.ndarray, slices: int) -> np.ndarray:
         for L in range(slices):
             for t in range(L + 1):
                 D[c, L] += Af[t][:, k0:k1] @ Bf[L - t][k0:k1, :]
+    if D.size and float(np.max(np.abs(D))) >= 2.0 ** 24:
+        raise ArithmeticError("a level sum reached 2^24: not exact in FP32 (K chunk too long)")
     return D
 
 

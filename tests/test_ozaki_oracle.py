@@ -60,6 +60,40 @@ def test_chunk_rule():
         assert mc % 128 == 0 and 225 * S * mc < 2 ** 24 <= 225 * S * (mc + 128)
 
 
+@pytest.mark.parametrize("slices", list(range(ozaki.MIN_SLICES, ozaki.MAX_SLICES + 1)))
+def test_chunk_rule_worst_case_level_sum(slices):
+    """Every level sum the chunk rule admits is exact in FP32: with all digits
+    at their largest magnitude 15 (entries 1 - 2^-53, whose 4S-bit truncation
+    is all ones up to S = 13; the digit arrays are written directly so that
+    every S is covered) over one full chunk, the top level L = S - 1 has S
+    pairs of 15 * 15 per column, 225 S mc < 2^24.  One more 128-column block
+    per chunk would reach 2^24, and the oracle refuses such a level sum."""
+    mc = ozaki.chunk_columns(slices)
+    if 4 * slices <= 53:
+        x = 1.0 - 2.0 ** -53
+        sig = ozaki.scales(np.array([x]))
+        assert sig.tolist() == [0]
+        assert (ozaki.digits(np.full((1, 4), x), sig[:, None], slices) == 15).all()
+    Ad = np.full((slices, 1, mc), 15, np.int64)
+    Bd = np.full((slices, mc, 1), -15, np.int64)
+    D = ozaki.level_sums(Ad, Bd, slices)
+    assert D.shape == (1, slices, 1, 1)
+    for L in range(slices):
+        assert D[0, L, 0, 0] == -225 * (L + 1) * mc
+    assert abs(D).max() < 2 ** 24
+    # a chunk rule one block too long lets the top level reach 2^24
+    wide = mc + 128
+    Aw = np.full((slices, 1, wide), 15, np.int64)
+    Bw = np.full((slices, wide, 1), 15, np.int64)
+    orig = ozaki.chunk_columns
+    try:
+        ozaki.chunk_columns = lambda s: wide
+        with pytest.raises(ArithmeticError):
+            ozaki.level_sums(Aw, Bw, slices)
+    finally:
+        ozaki.chunk_columns = orig
+
+
 @pytest.mark.parametrize("shape,slices", [((7, 33, 5), 2), ((9, 5000, 6), 16), ((4, 1, 3), 14)])
 def test_small_integers_exact(shape, slices):
     n, m, p = shape
@@ -192,3 +226,18 @@ def test_planted_mistakes_are_caught(monkeypatch, name, fake):
         except AssertionError:
             failed += 1
     assert failed >= 1, name
+
+
+_ORIG_CHUNK = ozaki.chunk_columns
+
+
+@pytest.mark.parametrize("fake", [lambda s: _ORIG_CHUNK(s) + 128,
+                                  lambda s: ((2 ** 24 - 1) // (225 * s) + 127) // 128 * 128,
+                                  lambda s: (2 ** 24 // (15 * s)) // 128 * 128])
+def test_planted_chunk_rule_is_caught(monkeypatch, fake):
+    """Planted mistakes in the chunk rule (one block too long, rounded up, the
+    digit bound 15 instead of 15 * 15): the worst-case level sum catches each."""
+    monkeypatch.setattr(ozaki, "chunk_columns", fake)
+    with pytest.raises((AssertionError, ArithmeticError)):
+        for S in range(ozaki.MIN_SLICES, ozaki.MAX_SLICES + 1):
+            test_chunk_rule_worst_case_level_sum(S)
