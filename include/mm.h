@@ -26,19 +26,29 @@
  *   MM_MODE_FP8           FP32 in/out through e4m3 operands with per-tile
  *                         power-of-two scales; accuracy is reported, not
  *                         guaranteed.  Not in the paper.
+ *   MM_MODE_SPLIT_BF16X6  FP32 in/out on the tensor cores, the upper rung
+ *                         of the split ladder: three bf16 parts (hi, mid,
+ *                         lo) per scaled operand and the six products down to
+ *                         2^-16 relative (mid.mid, hi.lo, lo.hi, hi.mid,
+ *                         mid.hi, hi.hi), so every term keeps about FP32
+ *                         precision; about half the rate of SPLIT_BF16X3.
+ *                         SPLIT_BF16X3 itself takes this form for inner
+ *                         dimensions m < 2237, where two parts cannot meet its
+ *                         tolerance.  Not in the paper.
  *   MM_MODE_AUTO          SPLIT_BF16X3 for MM_F32, DGEMM for MM_F64.
  *   MM_MODE_OZAKI         FP64 in/out on the e4m3 tensor cores (Ozaki
  *                         scheme): each row of A / column of B is scaled by a
  *                         power of two and cut into S 4-bit integer digit
  *                         slices; the slice products of equal weight are
- *                         exact in FP32 and are added in FP64.  Accuracy
+ *                         exact in FP32; the levels are added exactly in
+ *                         128-bit integers and rounded once to FP64.  Accuracy
  *                         depends on S and on the spread of magnitudes within
  *                         rows and columns (mm_ozaki_slices).  Not in the
  *                         paper.
  *
  * Accuracy contract (measured against an FP64 CPU evaluation of the
  * definition): max_ij |c^_ij - c_ij| / (|A|.|B|)_ij <= 1e-6*sqrt(m) for SIMT
- * and SPLIT_BF16X3, <= 1e-14*sqrt(m) for DGEMM, for finite inputs whose
+ * SPLIT_BF16X3 and SPLIT_BF16X6, <= 1e-14*sqrt(m) for DGEMM, for finite inputs whose
  * products stay in range.
  *
  * Conventions for every entry point:
@@ -49,8 +59,8 @@
  *   - The caller owns A, B, C.  The library owns its scratch: packed bf16
  *     operand splits, scale exponents, problem tables, tensor memory.
  *   - n, m, p >= 0.  n == 0 or p == 0 is a no-op; m == 0 writes C = 0.
- *   - dtype/mode mismatch (MM_F64 with SIMT/SPLIT/FP8, MM_F32 with DGEMM or
- *     OZAKI) returns MM_EUNSUPPORTED.
+ *   - dtype/mode mismatch (MM_F64 with SIMT/SPLIT_BF16X3/SPLIT_BF16X6/FP8,
+ *     MM_F32 with DGEMM or OZAKI) returns MM_EUNSUPPORTED.
  *   - A sticky CUDA error (the context is lost) returns MM_ECUDA from then on.
  *   - Device-side waits are bounded; a wait that runs out sets a device flag
  *     that the next synchronising call reports as MM_ETIMEOUT.
@@ -92,7 +102,8 @@ typedef enum {
   MM_MODE_DGEMM = 2,
   MM_MODE_FP8 = 3,
   MM_MODE_AUTO = 4,
-  MM_MODE_OZAKI = 5
+  MM_MODE_OZAKI = 5,
+  MM_MODE_SPLIT_BF16X6 = 6
 } mm_mode;
 
 typedef struct {
@@ -207,8 +218,10 @@ mm_status mm_check(int64_t n, int64_t m, int64_t p, const void *A,
 
 /* Queues one request (device pointers; they must stay valid until mm_poll or
  * mm_wait reports a final status).  Admission: the request's operand, output
- * and scratch bytes must fit the HBM budget; a request that can never fit
- * returns MM_EBUDGET immediately.  Requests are batched by dtype and mode;
+ * and scratch bytes, with those of the requests already admitted and the
+ * buffers the serving streams keep, must fit the HBM budget (idle streams
+ * give their buffers back when that makes the request fit); a request that
+ * can never fit returns MM_EBUDGET immediately.  Requests are batched by dtype and mode;
  * a batch of MM_MODE_OZAKI requests runs them one after the other on its
  * stream.  *id_out receives the request id. */
 mm_status mm_submit(const mm_problem *pr, mm_dtype dt, mm_mode mode,
@@ -228,7 +241,9 @@ mm_status mm_wait(uint64_t id, double timeout_s, mm_status *result,
                   double *err_out, double *latency_ms_out);
 
 /* Serving counters: completed requests, batches launched, requests waiting,
- * resident bytes admitted now.  Any pointer may be NULL. */
+ * and the device bytes counted against the HBM budget now (operands, outputs
+ * and scratch of the admitted requests, plus what the serving streams'
+ * buffers keep from earlier, larger batches).  Any pointer may be NULL. */
 mm_status mm_serve_stats(int64_t *completed, int64_t *batches,
                          int64_t *waiting, int64_t *resident_bytes);
 
@@ -341,7 +356,7 @@ mm_status mm_diag_async(int64_t n, int64_t p, const void *X, const void *d, void
  * with MM_ESCRATCH (2048^3 fits, 3072^3 does not).
  * A (n x m), B (m x p), C (n x p): device pointers, FP32, row-major and dense
  * as in mm_gemm.  stream: a cudaStream_t (NULL: the legacy default stream);
- * the call returns when C is written.  Same kernels and tile choices as
+ * the call synchronises that stream and returns when C is written.  Same kernels and tile choices as
  * mm_gemm's split path, without its tail split (mm_tune_query_tail): where
  * mm_gemm splits tiles along K the two results differ only in the rounding
  * of that one extra addition, within the split path's tolerance; elsewhere

@@ -24,6 +24,7 @@ MM_ESCRATCH = 12
 MM_F32, MM_F64 = 0, 1
 MM_MODE_SIMT, MM_MODE_SPLIT_BF16X3, MM_MODE_DGEMM, MM_MODE_FP8, MM_MODE_AUTO = 0, 1, 2, 3, 4
 MM_MODE_OZAKI = 5
+MM_MODE_SPLIT_BF16X6 = 6
 
 _i64 = ctypes.c_int64
 _vp = ctypes.c_void_p

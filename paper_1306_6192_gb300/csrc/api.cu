@@ -42,6 +42,9 @@ int sm_count() { return g_ctx.sms > 0 ? g_ctx.sms : 148; }
 // ---------------------------------------------------------------- scratch
 cudaError_t Scratch::reserve(size_t need, cudaStream_t s) {
   if (need <= bytes) return cudaSuccess;
+  // grow by at least a quarter of the old size, so that a run of slightly
+  // larger requests does not pay a synchronisation and a reallocation each
+  const size_t old = bytes;
   if (ptr) {
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
@@ -49,7 +52,7 @@ cudaError_t Scratch::reserve(size_t need, cudaStream_t s) {
     ptr = nullptr;
     bytes = 0;
   }
-  size_t want = std::max(need, bytes + bytes / 4);
+  size_t want = std::max(need, old + old / 4);
   want = (want + (1u << 20) - 1) & ~(size_t)((1u << 20) - 1);
   cudaError_t e = cudaMalloc(&ptr, want);
   if (e != cudaSuccess) {
@@ -217,7 +220,7 @@ static mm_mode resolve_mode(mm_dtype dt, mm_mode mode) {
 mm_status validate(int64_t n, int64_t m, int64_t p, mm_dtype dt, mm_mode mode) {
   if (n < 0 || m < 0 || p < 0) return MM_EINVAL;
   if (dt != MM_F32 && dt != MM_F64) return MM_EINVAL;
-  if ((int)mode < 0 || (int)mode > (int)MM_MODE_OZAKI) return MM_EINVAL;
+  if ((int)mode < 0 || (int)mode > (int)MM_MODE_SPLIT_BF16X6) return MM_EINVAL;
   const mm_mode md = resolve_mode(dt, mode);
   const bool f64_mode = md == MM_MODE_DGEMM || md == MM_MODE_OZAKI;
   if (dt == MM_F64 && !f64_mode) return MM_EUNSUPPORTED;
@@ -245,6 +248,10 @@ mm_status enqueue_gemm(int64_t n, int64_t m, int64_t p, const void *A, const voi
     case MM_MODE_SPLIT_BF16X3: {
       mm_problem q{n, m, p, A, B, C};
       return run_split(g_ctx.split_ws, &q, 1, s, nullptr);  // two or three parts by m
+    }
+    case MM_MODE_SPLIT_BF16X6: {
+      mm_problem q{n, m, p, A, B, C};
+      return run_split(g_ctx.split_ws, &q, 1, s, nullptr, true);  // three parts
     }
     case MM_MODE_FP8: {
       mm_problem q{n, m, p, A, B, C};

@@ -85,6 +85,10 @@ mm_status note_cuda(cudaError_t e);
 // where their worst-case per-product error 3 * 2^-16 is within the stated
 // tolerance 1e-6 sqrt(m), three parts (six products) below that.
 TcKind split_kind_for(int64_t m);
+// The kind a split-path mode runs with for inner dimension m.
+inline TcKind split_kind_of(mm_mode mode, int64_t m) {
+  return mode == MM_MODE_SPLIT_BF16X6 ? kTcSplitBf16x6 : split_kind_for(m);
+}
 
 // N tile used for a kind: the tensor-core kernel loads B in 128-row boxes, so
 // parts * bn must be a multiple of 128; with one or three parts that rules
@@ -99,8 +103,9 @@ inline int tc_bn(TcKind kind, int bn) {
 // Split path over a table of problems (single GEMM = table of one); each
 // problem takes the kind split_kind_for(m).  `force` overrides the tuned tile
 // choice (autotuner and tests).
+// `six` selects the three-part kind (six products) for every problem.
 mm_status run_split(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s,
-                    const TcChoice *force);
+                    const TcChoice *force, bool six = false);
 // Split path for one product whose rows of A (and of C) are processed in
 // `chunks` slabs: slab c waits for event in_ready[c + 1] (B: in_ready[0])
 // before its prep and records out_ready[c] when its part of C is written.

@@ -12,6 +12,7 @@ mm_status enqueue_grouped(Scratch &split_ws, Scratch &tab_ws, int count, const m
                           mm_dtype dt, mm_mode mode, cudaStream_t s) {
   if (count == 0) return MM_OK;
   if (mode == MM_MODE_SPLIT_BF16X3) return run_split(split_ws, probs, count, s, nullptr);
+  if (mode == MM_MODE_SPLIT_BF16X6) return run_split(split_ws, probs, count, s, nullptr, true);
   if (mode == MM_MODE_FP8) return run_fp8(g_ctx.fp8_ws, probs, count, s);
   if (mode == MM_MODE_OZAKI) {  // one emulated product after the other
     for (int g = 0; g < count; g++) {

@@ -21,6 +21,8 @@
 //   - The first call on a device looks up the array's device address there
 //     (cudaGetSymbolAddress, with that device current); make that first call
 //     before any stream capture.
+//   - Every call waits for its stream before it returns: it reads the device
+//     timeout flag back to report MM_ETIMEOUT.
 //   - The split path's other kernels are reused unchanged; nothing here
 //     depends on mm_init.
 // There is no counterpart in the paper.
@@ -158,8 +160,10 @@ mm_status mm_gemm_split_static(int64_t n, int64_t m, int64_t p, const float *A, 
     e = launch_split_pack(kind, kPackFix, d_tab, 1, (int)packs, nullptr, d_sflag, d_sflag + 1,
                           pack, s);
   if (e == cudaSuccess) {
-    TcConfig cfg = kind == kTcSplitBf16x3 ? TcConfig{2 * ch.bk, ch.stages, sms, ch.bn}
-                                          : TcConfig{64, 3, sms, ch.bn};
+    // the tuned grid (0: one CTA per SM of this device, counted at set-up)
+    const int grid = ch.grid > 0 ? ch.grid : sms;
+    TcConfig cfg = kind == kTcSplitBf16x3 ? TcConfig{2 * ch.bk, ch.stages, grid, ch.bn}
+                                          : TcConfig{64, 3, grid, ch.bn};
     e = launch_tc(kind, d_tab, 1, (int)tiles, nullptr, d_sflag, pack, rows, cfg, d_flag, s);
   }
   if (e != cudaSuccess) {

@@ -2,7 +2,10 @@
 //
 // Requests (mm_submit) queue in arrival order.  A scheduler thread admits
 // them in that order while the bytes they hold on the device (operands,
-// output and the library scratch they need) fit the HBM budget, groups the
+// output and the library scratch they need), together with what the streams'
+// buffers keep beyond the batches they run, fit the HBM budget (buffers of
+// idle streams are released when the next request fits only without them),
+// groups the
 // admitted-but-unlaunched ones by path (split FP32, DGEMM FP64, SIMT, FP8)
 // into grouped launches of at most max_batch requests and about kBatchMs of
 // estimated device time (every request of a batch completes when the batch
@@ -41,7 +44,8 @@ struct Request {
   mm_dtype dt = MM_F32;
   mm_mode mode = MM_MODE_SPLIT_BF16X3;
   int slices = 0;  // MM_MODE_OZAKI: digit slices at submission
-  size_t bytes = 0;
+  size_t bytes = 0;    // operands, output and the scratch estimate below
+  size_t scratch = 0;  // library scratch the request needs while it runs
   Clock::time_point t_submit;
   mm_status status = MM_EPENDING;
   double err = -1.0;
@@ -57,6 +61,7 @@ double request_ms(const Request &r) {
   if (r.mode == MM_MODE_DGEMM) rate = 1.2e12;          // FP64 FMA
   else if (r.mode == MM_MODE_SIMT) rate = 4.5e13;      // FP32 FMA
   else if (r.mode == MM_MODE_FP8) rate = 1e15;
+  else if (r.mode == MM_MODE_SPLIT_BF16X6) rate = 1.5e14;
   else if (r.mode == MM_MODE_OZAKI) rate = 2.5e15 / (0.5 * r.slices * (r.slices + 1));
   return flops / rate * 1e3;
 }
@@ -71,6 +76,23 @@ struct Slot {
   int64_t x_len = 0;           // entries of the check vector on the device
   bool busy = false;
   std::vector<Request *> batch;
+  size_t batch_scratch = 0;    // scratch estimates of the batch in flight
+  // Device bytes the slot's buffers hold now (they grow to the largest batch
+  // the slot has run and are kept for the next one).
+  size_t held() const {
+    return split_ws.bytes + tab_ws.bytes + check_ws.bytes + x_ws.bytes + idx_ws.bytes +
+           err_ws.bytes;
+  }
+  void release_buffers() {
+    cudaStreamSynchronize(s);
+    split_ws.release();
+    tab_ws.release();
+    check_ws.release();
+    x_ws.release();
+    idx_ws.release();
+    err_ws.release();
+    x_len = 0;
+  }
 };
 
 struct Server {
@@ -117,14 +139,14 @@ uint64_t splitmix(uint64_t seed, uint64_t i) {
 
 size_t elem_bytes(mm_dtype dt) { return dt == MM_F64 ? 8 : 4; }
 
-// Device bytes a request holds while admitted: its operands and output plus
-// the scratch of its path (split: bf16 hi/lo packs padded to whole tiles).
-size_t request_bytes(const mm_problem &q, mm_dtype dt, mm_mode mode, int slices) {
-  const size_t es = elem_bytes(dt);
-  size_t b = es * (size_t)(q.n * q.m + q.m * q.p + q.n * q.p);
+// Library scratch a request needs while it runs (split: bf16 hi/lo packs
+// padded to whole tiles, scale words, tail-split partial tiles; FP64
+// emulation: digit packs and level sums).
+size_t request_scratch(const mm_problem &q, mm_mode mode, int slices) {
+  size_t b = 0;
   if (mode == MM_MODE_OZAKI) b += ozaki_scratch_bytes(q.n, q.m, q.p, slices);
-  if (mode == MM_MODE_SPLIT_BF16X3 || mode == MM_MODE_FP8) {
-    const TcKind kind = mode == MM_MODE_FP8 ? kTcE4m3 : split_kind_for(q.m);
+  if (mode == MM_MODE_SPLIT_BF16X3 || mode == MM_MODE_SPLIT_BF16X6 || mode == MM_MODE_FP8) {
+    const TcKind kind = mode == MM_MODE_FP8 ? kTcE4m3 : split_kind_of(mode, q.m);
     TcChoice c = tune_choose(q.n, q.m, q.p);
     c.bn = tc_bn(kind, c.bn);
     const size_t kb = (size_t)ceil_div(q.m, pack_k(kind));  // pack rows per matrix row
@@ -134,6 +156,38 @@ size_t request_bytes(const mm_problem &q, mm_dtype dt, mm_mode mode, int slices)
     b += tail_scratch_bytes(q.n, q.m, q.p, kind);  // partial tiles of a tail split
   }
   return b;
+}
+
+// Device bytes of a request's operands and output (the caller's memory).
+size_t request_operand_bytes(const mm_problem &q, mm_dtype dt) {
+  return elem_bytes(dt) * (size_t)(q.n * q.m + q.m * q.p + q.n * q.p);
+}
+
+// Bytes the slots' buffers hold beyond the scratch estimates of the batches
+// they run: what a slot kept from an earlier, larger batch (or an idle slot's
+// buffers).  Counted against the budget with the admitted requests.
+size_t slots_extra() {
+  size_t x = 0;
+  for (const Slot &sl : g_srv.slots) {
+    const size_t h = sl.held();
+    x += h > sl.batch_scratch ? h - sl.batch_scratch : 0;
+  }
+  return x;
+}
+
+// Whether the request at the head of the queue fits the budget now; if it
+// fits only without the buffers that idle slots keep, those are released.
+bool head_fits() {
+  const size_t need = g_srv.pending.front()->bytes;
+  if (g_srv.resident + slots_extra() + need <= g_srv.budget) return true;
+  if (g_srv.resident + need > g_srv.budget) return false;
+  bool freed = false;
+  for (Slot &sl : g_srv.slots)
+    if (!sl.busy && sl.held() > 0) {
+      sl.release_buffers();
+      freed = true;
+    }
+  return freed && g_srv.resident + slots_extra() + need <= g_srv.budget;
 }
 
 void finish(Request *r, mm_status st, double err) {
@@ -152,8 +206,9 @@ mm_status launch_batch(Slot &sl, std::vector<Request *> &reqs) {
   const mm_dtype dt = reqs[0]->dt;
   const mm_mode mode = reqs[0]->mode;
   mm_status st;
-  if (mode == MM_MODE_SPLIT_BF16X3)
-    st = run_split(sl.split_ws, probs.data(), (int)probs.size(), sl.s, nullptr);
+  if (mode == MM_MODE_SPLIT_BF16X3 || mode == MM_MODE_SPLIT_BF16X6)
+    st = run_split(sl.split_ws, probs.data(), (int)probs.size(), sl.s, nullptr,
+                   mode == MM_MODE_SPLIT_BF16X6);
   else if (mode == MM_MODE_FP8)
     st = run_fp8(sl.split_ws, probs.data(), (int)probs.size(), sl.s);
   else if (mode == MM_MODE_OZAKI) {
@@ -256,12 +311,12 @@ void scheduler() {
         g_srv.completed++;
       }
       sl.batch.clear();
+      sl.batch_scratch = 0;
       sl.busy = false;
       g_srv.cv_done.notify_all();
     }
     // 2. admission in arrival order while the budget allows
-    while (!g_srv.pending.empty() &&
-           g_srv.resident + g_srv.pending.front()->bytes <= g_srv.budget) {
+    while (!g_srv.pending.empty() && head_fits()) {
       Request *r = g_srv.pending.front();
       g_srv.pending.pop_front();
       g_srv.resident += r->bytes;
@@ -301,6 +356,8 @@ void scheduler() {
         g_srv.cv_done.notify_all();
         continue;
       }
+      sl.batch_scratch = 0;
+      for (const Request *r : take) sl.batch_scratch += r->scratch;
       sl.batch = std::move(take);
       sl.busy = true;
       g_srv.batches++;
@@ -314,8 +371,7 @@ void scheduler() {
       g_srv.cv_work.wait_for(lk, std::chrono::microseconds(20));
     else
       g_srv.cv_work.wait(lk, [] {
-        return g_srv.stop || (!g_srv.pending.empty() &&
-                              g_srv.resident + g_srv.pending.front()->bytes <= g_srv.budget) ||
+        return g_srv.stop || (!g_srv.pending.empty() && head_fits()) ||
                !g_srv.admitted.empty();
       });
   }
@@ -367,13 +423,7 @@ void serve_stop() {
   g_srv.th.join();
   std::lock_guard<std::mutex> lk(g_srv.mu);
   for (Slot &sl : g_srv.slots) {
-    cudaStreamSynchronize(sl.s);
-    sl.split_ws.release();
-    sl.tab_ws.release();
-    sl.check_ws.release();
-    sl.x_ws.release();
-    sl.idx_ws.release();
-    sl.err_ws.release();
+    sl.release_buffers();
     if (sl.h_err) cudaFreeHost(sl.h_err);
     if (sl.h_idx) cudaFreeHost(sl.h_idx);
     cudaEventDestroy(sl.ev);
@@ -408,7 +458,8 @@ mm_status mm_submit(const mm_problem *pr, mm_dtype dt, mm_mode mode, uint64_t *i
   r->dt = dt;
   r->mode = mode;
   r->slices = g_ctx.ozaki_slices;
-  r->bytes = request_bytes(*pr, dt, mode, r->slices);
+  r->scratch = request_scratch(*pr, mode, r->slices);
+  r->bytes = request_operand_bytes(*pr, dt) + r->scratch;
   std::lock_guard<std::mutex> lk(g_srv.mu);
   if (!g_srv.running) {
     delete r;
@@ -469,7 +520,7 @@ mm_status mm_serve_stats(int64_t *completed, int64_t *batches, int64_t *waiting,
   if (completed) *completed = g_srv.completed;
   if (batches) *batches = g_srv.batches;
   if (waiting) *waiting = (int64_t)(g_srv.pending.size() + g_srv.admitted.size());
-  if (resident_bytes) *resident_bytes = (int64_t)g_srv.resident;
+  if (resident_bytes) *resident_bytes = (int64_t)(g_srv.resident + slots_extra());
   return MM_OK;
 }
 

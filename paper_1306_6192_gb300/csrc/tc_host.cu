@@ -41,7 +41,7 @@ TcTail plan_tail(SplitProb &sp, TcKind kind, const TcChoice &ch) {
 }
 
 mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s,
-                        const TcChoice *force, bool fp8) {
+                        const TcChoice *force, bool fp8, bool six) {
   Group groups[3] = {{kTcSplitBf16x3}, {kTcSplitBf16x6}, {kTcE4m3}};
   int64_t rows = 0, scal = 0, part = 0;
   size_t tail_parts = 0, tail_cnts = 0;  // partial tiles and counters of tail splits
@@ -53,7 +53,7 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
       if (e != cudaSuccess) return note_cuda(e);
       continue;
     }
-    const TcKind kind = fp8 ? kTcE4m3 : split_kind_for(q.m);
+    const TcKind kind = fp8 ? kTcE4m3 : (six ? kTcSplitBf16x6 : split_kind_for(q.m));
     Group &G = groups[kind == kTcSplitBf16x3 ? 0 : (kind == kTcSplitBf16x6 ? 1 : 2)];
     TcChoice ch = force ? *force : tune_choose(q.n, q.m, q.p);
     ch.bn = tc_bn(kind, ch.bn);
@@ -318,12 +318,12 @@ mm_status run_split_chunked(Scratch &ws, int64_t n, int64_t m, int64_t p, const 
 }
 
 mm_status run_split(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s,
-                    const TcChoice *force) {
-  return run_tc_groups(ws, probs, count, s, force, false);
+                    const TcChoice *force, bool six) {
+  return run_tc_groups(ws, probs, count, s, force, false, six);
 }
 
 mm_status run_fp8(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s) {
-  return run_tc_groups(ws, probs, count, s, nullptr, true);
+  return run_tc_groups(ws, probs, count, s, nullptr, true, false);
 }
 
 }  // namespace mm

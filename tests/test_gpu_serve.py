@@ -2,6 +2,8 @@
 is the same alone and in the mix; over-budget requests are rejected; a
 request that cannot finish in time reports a timeout without losing it;
 shutdown cancels what was not launched."""
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -147,3 +149,48 @@ def test_submit_validation(server):
     assert mm.mm_submit(2, 2, 2, h, x, x, mm.MM_F32, mm.MM_MODE_SIMT)[0] == mm.MM_EINVAL
     assert mm.mm_submit(-2, 2, 2, x, x, x, mm.MM_F32, mm.MM_MODE_SIMT)[0] == mm.MM_EINVAL
     assert mm.mm_submit(2, 2, 2, x, x, x, mm.MM_F64, mm.MM_MODE_SIMT)[0] == mm.MM_EUNSUPPORTED
+
+
+def test_budget_counts_buffers_the_streams_keep(server):
+    """A stream keeps the scratch of its largest batch for the next one.  Those
+    bytes count against the budget, and an idle stream gives them back when
+    the next request fits only without them: the reported total never exceeds
+    the budget, and a request of nearly the whole budget still runs after a
+    large split product left its buffers behind."""
+    budget = 512 << 20
+    mm = server(n_streams=1, hbm_budget_bytes=budget)
+    n = 2048
+    A = torch.rand(n, n, device="cuda") * 2 - 1
+    B = torch.rand(n, n, device="cuda") * 2 - 1
+    C = torch.empty(n, n, device="cuda")
+    st, rid = mm.mm_submit(n, n, n, A, B, C, mm.MM_F32, mm.MM_MODE_SPLIT_BF16X3)
+    assert st == mm.MM_OK
+    st, res, _, _ = mm.mm_wait(rid, 60.0)
+    assert st == mm.MM_OK and res == mm.MM_OK
+    _, _, _, _, held = mm.mm_serve_stats()
+    assert 0 < held <= budget, held  # the split packs of 2048^3, kept by the stream
+    # SIMT requests carry no scratch estimate: operands and output alone, here
+    # budget - 16 MiB, which fits only once the stream's buffers are gone
+    x = int(((budget - (16 << 20)) / 12) ** 0.5)
+    assert 12 * x * x + held > budget
+    A2 = torch.rand(x, x, device="cuda") * 2 - 1
+    B2 = torch.rand(x, x, device="cuda") * 2 - 1
+    C2 = torch.empty(x, x, device="cuda")
+    st, rid = mm.mm_submit(x, x, x, A2, B2, C2, mm.MM_F32, mm.MM_MODE_SIMT)
+    assert st == mm.MM_OK
+    peak = 0
+    for _ in range(2000):
+        st, res, _, _ = mm.mm_poll(rid)
+        _, _, _, _, r = mm.mm_serve_stats()
+        peak = max(peak, r)
+        if st == mm.MM_OK:
+            break
+        time.sleep(0.005)
+    else:
+        st, res, _, _ = mm.mm_wait(rid, 120.0)
+    assert st == mm.MM_OK and res == mm.MM_OK
+    assert peak <= budget, peak
+    I, J = synth.sample_indices(77, x, x, 64)
+    hi, lo, ab = oracle.default().entries(A2.cpu().numpy(), B2.cpu().numpy(), I, J)
+    got = C2.cpu().numpy()[I, J].astype(np.float64)
+    assert oracle.rel_errors(got, hi + lo, ab).max() <= oracle.tolerance(x, "f32")

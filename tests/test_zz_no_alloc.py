@@ -56,6 +56,55 @@ def test_static_entry_matches_mm_gemm_twice(mmlib):
         assert oracle.rel_errors(cs, ref, absref).max() <= oracle.tolerance(m, "f32")
 
 
+def test_static_entry_rescaled_rows_then_uniform(mmlib):
+    """Rows of A at 2^-120 and 2^100 make the verify pass flag A and the fix
+    pass re-pack it with its scales; the next call, on plain uniform data,
+    must start from cleared flags in the shared array."""
+    mm = mmlib
+    fn = _static_entry(mm)
+    s = torch.cuda.current_stream()
+    n, m, p = 300, 700, 260
+    A = synth.uniform_pm1(9301, (n, m))
+    A = (A.astype(np.float64) * np.ldexp(1.0, synth.row_scale_exponents(9302, n))[:, None]
+         ).astype(np.float32)
+    B = synth.uniform_pm1(9303, (m, p))
+    A2 = synth.uniform_pm1(9304, (n, m))
+    orc = oracle.default()
+    for a in (A, A2):
+        dA, dB = dev(a), dev(B)
+        C = torch.full((n, p), float("nan"), device="cuda")
+        st = fn(n, m, p, dA.data_ptr(), dB.data_ptr(), C.data_ptr(), s.cuda_stream)
+        assert st == mm.MM_OK, mm.mm_strerror(st)
+        ref, absref = orc.gemm(a, B, with_abs=True)
+        e = oracle.rel_errors(C.cpu().numpy(), ref, absref)
+        assert e.max() <= oracle.tolerance(m, "f32"), e.max()
+
+
+def test_static_entry_bitwise_where_no_tail_split(mmlib):
+    """Where mm_gemm does not split its last wave along K, both entry points
+    run the same kernels with the same tiles, so the bits agree."""
+    mm = mmlib
+    fn = _static_entry(mm)
+    s = torch.cuda.current_stream()
+    checked = 0
+    for seed, (n, m, p) in enumerate(((1000, 1500, 900), (256, 4096, 256), (129, 65, 300))):
+        st, tiles, split_from, split_s = mm.mm_tune_query_tail(n, m, p)
+        assert st == mm.MM_OK
+        if split_s > 1:
+            continue
+        A = synth.uniform_pm1(9400 + seed, (n, m))
+        B = synth.uniform_pm1(9500 + seed, (m, p))
+        dA, dB = dev(A), dev(B)
+        C1 = torch.full((n, p), float("nan"), device="cuda")
+        C2 = torch.full((n, p), float("nan"), device="cuda")
+        st = fn(n, m, p, dA.data_ptr(), dB.data_ptr(), C1.data_ptr(), s.cuda_stream)
+        assert st == mm.MM_OK, mm.mm_strerror(st)
+        assert mm.mm_gemm(n, m, p, dA, dB, C2, mm.MM_F32, mm.MM_MODE_SPLIT_BF16X3) == 0
+        assert torch.equal(C1.view(torch.int32), C2.view(torch.int32)), (n, m, p)
+        checked += 1
+    assert checked >= 1
+
+
 def test_static_entry_rejects_oversize(mmlib):
     mm = mmlib
     fn = _static_entry(mm)
