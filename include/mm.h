@@ -274,6 +274,25 @@ mm_status mm_tune_query(int64_t n, int64_t m, int64_t p, int *bn, int *bk,
 mm_status mm_tune_query_tail(int64_t n, int64_t m, int64_t p, int *tiles,
                              int *split_from, int *split_s);
 
+/* Fused split-K plan of the split path for one product n x m x p (mm_gemm /
+ * mm_gemm_async on MM_MODE_SPLIT_BF16X3): a product with fewer 128 x 128
+ * output tiles than half the SMs runs as ONE launch that reads A and B
+ * directly, splits each 64-wide K block into bf16 parts in shared memory
+ * (power-of-two scales per row of A and column of B within a block, only for
+ * blocks holding an entry outside [2^-40, 2^40]), multiplies on the tensor
+ * cores and adds the blocks' FP32 partial products in registers; the inner
+ * dimension of each tile is cut into *slices slices, one CTA each, in
+ * *clusters thread-block clusters of *cluster_size CTAs that add their
+ * partial tiles through distributed shared memory (and, for *clusters > 1,
+ * through library scratch, the cluster finishing last adding the others in
+ * order).  The result does not depend on timing.  *slices = 0: the product
+ * takes the packed path (mm_tune_query_tail).  Grouped calls and serving
+ * batches always take the packed path, so a product's bits there equal a
+ * grouped call of that product alone; against mm_gemm they agree within the
+ * split path's tolerance.  Needs mm_init; any pointer may be NULL. */
+mm_status mm_tune_query_splitk(int64_t n, int64_t m, int64_t p, int *tiles, int *slices,
+                               int *clusters, int *cluster_size);
+
 /* The tail-split planner itself, a pure host function (no device, no
  * mm_init): for a product of `tiles` output tiles of 128 x bn, kt pack rows
  * of K (64 bf16 or 128 e4m3 values each), inner dimension m and `products`
@@ -292,7 +311,7 @@ mm_status mm_tail_plan(int64_t tiles, int grid, int kt, int bn, int64_t m,
 /* When enabled, every kernel the library launches is bracketed by CUDA events
  * on its stream; mm_trace_read returns the launch count and summed device
  * time (ms) of the kernel named `kernel` ("simt_f32", "dgemm_f64",
- * "split_scale", "split_pack", "split_tc", "fp8_tc", "check_f64") since the
+ * "split_scale", "split_pack", "split_tc", "fused_tc", "fp8_tc", "check_f64") since the
  * last reset.  Reading synchronises the recorded events. */
 mm_status mm_trace_enable(int on);
 mm_status mm_trace_reset(void);

@@ -81,6 +81,7 @@ def lib():
         L.mm_tune_load.argtypes = [ctypes.c_char_p]
         L.mm_tune_query.argtypes = [_i64, _i64, _i64] + [ctypes.POINTER(ctypes.c_int)] * 4
         L.mm_tune_query_tail.argtypes = [_i64, _i64, _i64] + [ctypes.POINTER(ctypes.c_int)] * 3
+        L.mm_tune_query_splitk.argtypes = [_i64, _i64, _i64] + [ctypes.POINTER(ctypes.c_int)] * 4
         L.mm_tail_plan.argtypes = [_i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64,
                                    ctypes.c_double] + [ctypes.POINTER(ctypes.c_int)] * 2
         L.mm_trace_enable.argtypes = [ctypes.c_int]
@@ -106,7 +107,8 @@ def lib():
         for name in ("mm_init", "mm_shutdown", "mm_gemm", "mm_gemm_async", "mm_gemm_grouped",
                      "mm_gemm_grouped_async", "mm_sync", "mm_check", "mm_submit", "mm_poll",
                      "mm_wait", "mm_serve_stats", "mm_tune", "mm_tune_save", "mm_tune_load",
-                     "mm_tune_query", "mm_tune_query_tail", "mm_tail_plan", "mm_trace_enable",
+                     "mm_tune_query", "mm_tune_query_tail", "mm_tune_query_splitk",
+                     "mm_tail_plan", "mm_trace_enable",
                      "mm_trace_reset", "mm_trace_read"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -263,6 +265,14 @@ def mm_tune_query_tail(n, m, p):
     split for one n x m x p product."""
     v = [ctypes.c_int(0) for _ in range(3)]
     st = lib().mm_tune_query_tail(n, m, p, *[ctypes.byref(x) for x in v])
+    return (st,) + tuple(x.value for x in v)
+
+
+def mm_tune_query_splitk(n, m, p):
+    """Returns (status, tiles, slices, clusters, cluster_size) of the fused
+    split-K plan of one n x m x p split product (slices = 0: packed path)."""
+    v = [ctypes.c_int(0) for _ in range(4)]
+    st = lib().mm_tune_query_splitk(n, m, p, *[ctypes.byref(x) for x in v])
     return (st,) + tuple(x.value for x in v)
 
 

@@ -245,13 +245,18 @@ mm_status enqueue_gemm(int64_t n, int64_t m, int64_t p, const void *A, const voi
     case MM_MODE_DGEMM:
       return note_cuda(
           launch_simt_f64(n, m, p, (const double *)A, (const double *)B, (double *)C, s));
-    case MM_MODE_SPLIT_BF16X3: {
-      mm_problem q{n, m, p, A, B, C};
-      return run_split(g_ctx.split_ws, &q, 1, s, nullptr);  // two or three parts by m
-    }
+    case MM_MODE_SPLIT_BF16X3:
     case MM_MODE_SPLIT_BF16X6: {
+      // two or three parts by m (x3), three parts (x6); products with few
+      // output tiles run as one fused split-K launch
+      const TcKind kind = split_kind_of(md, m);
+      const FusedPlan fpl = fused_plan(n, m, p, kind);
+      if (fpl.S > 0 && fused_operands_ok(static_cast<const float *>(A),
+                                         static_cast<const float *>(B), m, p))
+        return run_fused(g_ctx.fused_ws, n, m, p, static_cast<const float *>(A),
+                         static_cast<const float *>(B), static_cast<float *>(C), kind, fpl, s);
       mm_problem q{n, m, p, A, B, C};
-      return run_split(g_ctx.split_ws, &q, 1, s, nullptr, true);  // three parts
+      return run_split(g_ctx.split_ws, &q, 1, s, nullptr, md == MM_MODE_SPLIT_BF16X6);
     }
     case MM_MODE_FP8: {
       mm_problem q{n, m, p, A, B, C};
@@ -272,6 +277,7 @@ mm_status check_device_flag(cudaStream_t s) {
   if (e != cudaSuccess) return note_cuda(e);
   if (flag != 0) {
     cudaMemset(g_ctx.d_err, 0, sizeof(int));
+    g_ctx.fused_zero_ptr = nullptr;  // an aborted fused launch may leave counters set
     return MM_ETIMEOUT;
   }
   return MM_OK;
@@ -384,6 +390,9 @@ mm_status mm_shutdown(void) {
   g_ctx.check_ws.release();
   g_ctx.cplx_ws.release();
   g_ctx.ozaki_ws.release();
+  g_ctx.fused_ws.release();
+  g_ctx.fused_zero_ptr = nullptr;
+  g_ctx.fused_zeroed = 0;
   g_ctx.ozaki_slices = kOzakiDefaultSlices;
   if (g_ctx.d_err) cudaFree(g_ctx.d_err);
   g_ctx.d_err = nullptr;

@@ -60,6 +60,9 @@ struct Ctx {
   Scratch check_ws;      // FP64 check work vectors
   Scratch cplx_ws;       // real/imaginary planes and partial products (mm_cgemm)
   Scratch ozaki_ws;      // digit packs, level sums and tables of the FP64 emulation
+  Scratch fused_ws;      // counters and cluster partial tiles of the fused split-K path
+  void *fused_zero_ptr = nullptr;  // fused_ws buffer whose leading counters are zero
+  size_t fused_zeroed = 0;         //   and how many bytes of them
   int ozaki_slices = kOzakiDefaultSlices;  // digit slices S of MM_MODE_OZAKI
   // host-operand pipeline of mm_gemm: copy streams and per-chunk events
   cudaStream_t h2d = nullptr, d2h = nullptr;
@@ -117,6 +120,16 @@ mm_status run_split_chunked(Scratch &ws, int64_t n, int64_t m, int64_t p, const 
 // scratch bytes of its partial tiles and counters.
 TcTail product_tail(int64_t n, int64_t m, int64_t p, TcKind kind, int64_t *tiles_out);
 size_t tail_scratch_bytes(int64_t n, int64_t m, int64_t p, TcKind kind);
+// Fused split-K path (tc_fused.cu) for products with fewer 128 x 128 tiles
+// than half the SMs: S slices per tile in Q clusters of cs CTAs; S = 0 when
+// the product takes the packed path.  The plan depends on the product's shape
+// (and the device's cluster capacity) only.
+struct FusedPlan {
+  int S, Q, cs;
+};
+FusedPlan fused_plan(int64_t n, int64_t m, int64_t p, TcKind kind);
+mm_status run_fused(Scratch &ws, int64_t n, int64_t m, int64_t p, const float *A, const float *B,
+                    float *C, TcKind kind, const FusedPlan &plan, cudaStream_t s);
 // FP8 path (report-only accuracy).
 mm_status run_fp8(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s);
 // FP64 product by the Ozaki scheme on the e4m3 tensor cores with S digit

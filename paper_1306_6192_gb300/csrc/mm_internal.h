@@ -90,6 +90,23 @@ __host__ __device__ inline int64_t split_units(const SplitProb &sp) {
   return sp.split_s > 1 ? sp.split_from + (tiles - sp.split_from) * sp.split_s : tiles;
 }
 
+// One product of the fused split-K path (tc_fused.cu): output tiles of
+// 128 x 128 in row-major tile order, each tile's K blocks of 64 cut into S
+// slices [h*kb/S, (h+1)*kb/S), one CTA per slice, S = Q * CS with CS the
+// launch's cluster size.  With Q > 1 the clusters of a tile meet through
+// `slots` (tiles * Q partial tiles of 128 x 128 floats) and `cnt` (tiles * CS
+// counters, zero between launches).
+struct FusedProb {
+  const float *A;
+  const float *B;
+  float *C;
+  int32_t n, m, p;
+  int32_t mt, nt, kb;      // ceil(n/128), ceil(p/128), ceil(m/64)
+  int32_t S, Q;            // slices per tile, clusters per tile
+  float *slots;
+  int *cnt;
+};
+
 // One product of the grouped SIMT path (f32 or f64 elements).
 struct SimtProb {
   const void *A;
@@ -170,6 +187,15 @@ cudaError_t launch_tc(TcKind kind, const SplitProb *d_probs, int nprobs,
                       int total_units, const int *unit_map, const int *flags,
                       void *pack_base, int64_t pack_rows, const TcConfig &cfg,
                       int *d_err, cudaStream_t s);
+
+// Fused split-K launch of one product (tiles * S CTAs in clusters of cs =
+// S / Q); six: three bf16 parts.  The operands are read by TMA, so A and B
+// must be 16-byte aligned with m and p multiples of 4 (fused_operands_ok).
+bool fused_operands_ok(const float *A, const float *B, int64_t m, int64_t p);
+cudaError_t launch_fused(bool six, const FusedProb &pr, int cs, int *d_err, cudaStream_t s);
+// Most CTAs of the fused kernel resident at once with clusters of cs CTAs
+// (cs = 1, 2, 4, 8), measured once per device and kind.
+int fused_capacity(bool six, int cs);
 
 // FP64 check (Freivalds + sampled entries): writes 2 doubles to d_out.
 cudaError_t launch_check(bool f64, int64_t n, int64_t m, int64_t p,

@@ -386,3 +386,96 @@ extern "C" mm_status mm_tail_plan(int64_t tiles, int grid, int kt, int bn, int64
   *split_s = t.split_s > 1 ? t.split_s : 1;
   return MM_OK;
 }
+
+// ------------------------------------------------------ fused split-K path
+namespace mm {
+
+FusedPlan fused_plan(int64_t n, int64_t m, int64_t p, TcKind kind) {
+  FusedPlan best{0, 0, 0};
+  if (kind == kTcE4m3 || n <= 0 || m <= 0 || p <= 0) return best;
+  const int64_t tiles = ceil_div(n, kTcBM) * ceil_div(p, 128);
+  const int64_t kb = ceil_div(m, 64);
+  // products that fill at least half of the SMs with whole tiles keep the
+  // packed path (their operands are converted once, not once per tile)
+  if (2 * tiles > sm_count()) return best;
+  const bool six = kind == kTcSplitBf16x6;
+  // cost in units of one K block of one CTA (its conversion dominates): the
+  // blocks of the longest slice, the cluster's exchange through distributed
+  // shared memory, and the clusters' meeting in global memory, whose last
+  // cluster reads Q partial tiles
+  double best_cost = 1e300;
+  for (int cs : {8, 4, 2, 1}) {
+    const int cap = fused_capacity(six, cs);
+    if (cap <= 0) continue;
+    for (int64_t q = 1;; q++) {
+      const int64_t S = q * cs;
+      if (S > kb || tiles * S > cap) break;
+      const double cost = (double)ceil_div(kb, S) + (cs > 1 ? 0.3 : 0.0) +
+                          (q > 1 ? 0.5 + 0.1 * (double)q : 0.0);
+      if (cost < best_cost - 1e-9 || (cost < best_cost + 1e-9 && S < best.S)) {
+        best_cost = cost;
+        best = FusedPlan{(int)S, (int)q, cs};
+      }
+    }
+  }
+  // a slice of more than four K blocks is slower here than on the packed
+  // path, whose operands are split once and streamed by TMA
+  if (best.S > 0 && ceil_div(kb, best.S) > 4) best = FusedPlan{0, 0, 0};
+  return best;
+}
+
+mm_status run_fused(Scratch &ws, int64_t n, int64_t m, int64_t p, const float *A, const float *B,
+                    float *C, TcKind kind, const FusedPlan &plan, cudaStream_t s) {
+  FusedProb fp;
+  std::memset(&fp, 0, sizeof(fp));
+  fp.A = A;
+  fp.B = B;
+  fp.C = C;
+  fp.n = (int32_t)n;
+  fp.m = (int32_t)m;
+  fp.p = (int32_t)p;
+  fp.mt = (int32_t)ceil_div(n, kTcBM);
+  fp.nt = (int32_t)ceil_div(p, 128);
+  fp.kb = (int32_t)ceil_div(m, 64);
+  fp.S = plan.S;
+  fp.Q = plan.Q;
+  const int64_t tiles = (int64_t)fp.mt * fp.nt;
+  cudaError_t e = cudaSuccess;
+  if (plan.Q > 1) {
+    // counters first (kept at zero between launches: the last cluster of a
+    // chunk resets its counter), then the clusters' partial tiles
+    const size_t cnt_bytes = ((size_t)tiles * plan.cs * sizeof(int) + 255) & ~(size_t)255;
+    const size_t need = cnt_bytes + (size_t)tiles * plan.Q * kTcBM * 128 * sizeof(float);
+    e = ws.reserve(need, s);
+    if (e != cudaSuccess) return note_cuda(e);
+    if (ws.ptr != g_ctx.fused_zero_ptr || cnt_bytes > g_ctx.fused_zeroed) {
+      e = cudaMemsetAsync(ws.ptr, 0, cnt_bytes, s);
+      if (e != cudaSuccess) return note_cuda(e);
+      g_ctx.fused_zero_ptr = ws.ptr;
+      g_ctx.fused_zeroed = cnt_bytes;
+    }
+    fp.cnt = static_cast<int *>(ws.ptr);
+    fp.slots = reinterpret_cast<float *>(static_cast<uint8_t *>(ws.ptr) + cnt_bytes);
+  }
+  e = launch_fused(kind == kTcSplitBf16x6, fp, plan.cs, g_ctx.d_err, s);
+  return note_cuda(e);
+}
+
+}  // namespace mm
+
+extern "C" mm_status mm_tune_query_splitk(int64_t n, int64_t m, int64_t p, int *tiles,
+                                          int *slices, int *clusters, int *cluster_size) {
+  if (!g_ctx.inited) return MM_ENOTINIT;
+  if (n < 0 || m < 0 || p < 0) return MM_EINVAL;
+  FusedPlan f{0, 0, 0};
+  int64_t t = 0;
+  if (n > 0 && m > 0 && p > 0) {
+    f = fused_plan(n, m, p, split_kind_for(m));
+    t = f.S > 0 ? ceil_div(n, kTcBM) * ceil_div(p, 128) : 0;
+  }
+  if (tiles) *tiles = (int)t;
+  if (slices) *slices = f.S;
+  if (clusters) *clusters = f.Q;
+  if (cluster_size) *cluster_size = f.cs;
+  return MM_OK;
+}

@@ -32,6 +32,28 @@ def run_gemm(mm, A, B, mode, f64=False, out_fill=float("nan")):
     return dC.cpu().numpy()
 
 
+def run_packed(mm, A, B, mode):
+    """C = A.B as a grouped call of this one product: the packed split path
+    (pack, verify, fix, persistent tcgen05 kernel with its tail split), which
+    grouped calls and serving batches use for every product.  mm_gemm runs
+    products with few output tiles on the fused split-K kernel instead."""
+    n, m = A.shape
+    p = B.shape[1]
+    dA, dB = dev(A), dev(B)
+    dC = torch.full((n, p), float("nan"), device="cuda")
+    st = mm.mm_gemm_grouped([(n, m, p, dA, dB, dC)], mm.MM_F32, mode)
+    assert st == mm.MM_OK, mm.mm_strerror(st)
+    return dC.cpu().numpy()
+
+
+def fused_slices(mm, n, m, p):
+    """Slices of the fused split-K plan of an n x m x p split product (0: the
+    product takes the packed path)."""
+    st, _, slices, _, _ = mm.mm_tune_query_splitk(n, m, p)
+    assert st == mm.MM_OK
+    return slices
+
+
 def full_errors(C, A, B, orc=None):
     orc = orc or oracle.default()
     ref, absref = orc.gemm(A, B, with_abs=True)

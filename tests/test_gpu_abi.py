@@ -7,6 +7,7 @@ import pytest
 import torch
 
 import oracle
+from gpu_util import fused_slices
 import synth
 from gpu_util import assert_full, dev
 
@@ -84,7 +85,7 @@ def test_host_operands_pipelined(mmlib, shape):
     assert mm.mm_gemm(n, m, p, dev(A), dev(B), Cd, mm.MM_F32, mm.MM_MODE_SPLIT_BF16X3) == 0
     st, _, _, split_s = mm.mm_tune_query_tail(n, m, p)
     assert st == 0
-    if split_s == 1:
+    if split_s == 1 and fused_slices(mm, n, m, p) == 0:
         assert torch.equal(Cp, Cd.cpu())
     else:
         absref = np.abs(A.astype(np.float64)) @ np.abs(B.astype(np.float64))
@@ -95,8 +96,12 @@ def test_host_operands_pipelined(mmlib, shape):
 
 
 def test_async_on_torch_stream_and_trace(mmlib):
+    """Queued calls on a caller stream and the launch tracer: a product with
+    enough tiles for the packed path launches its four kernels per call; one
+    with few tiles launches the fused split-K kernel once per call."""
     mm = mmlib
-    n, m, p = 512, 384, 640
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    n, m, p = 128 * n_sm, 384, 640
     A = synth.uniform_pm1(711, (n, m))
     B = synth.uniform_pm1(712, (m, p))
     dA, dB = dev(A), dev(B)
@@ -114,9 +119,22 @@ def test_async_on_torch_stream_and_trace(mmlib):
     assert st == 0 and k == 3 and ms > 0
     st, k, _ = mm.mm_trace_read("split_pack")
     assert k == 3
-    mm.mm_trace_enable(False)
     mm.mm_trace_reset()
     assert_full(C.cpu().numpy(), A, B, "f32")
+    n2, m2, p2 = 512, 384, 640
+    assert fused_slices(mm, n2, m2, p2) > 0
+    C2 = torch.full((n2, p2), float("nan"), device="cuda")
+    before = mm.mm_launch_count()
+    for _ in range(3):
+        assert mm.mm_gemm_async(n2, m2, p2, dA[:n2], dB, C2, mm.MM_F32, mm.MM_MODE_SPLIT_BF16X3,
+                                s) == 0
+    assert mm.mm_sync(s) == 0
+    assert mm.mm_launch_count() - before == 3
+    st, k, ms = mm.mm_trace_read("fused_tc")
+    assert st == 0 and k == 3 and ms > 0
+    mm.mm_trace_enable(False)
+    mm.mm_trace_reset()
+    assert_full(C2.cpu().numpy(), A[:n2], B, "f32")
 
 
 def test_tune_table_roundtrip(mmlib, tmp_path):

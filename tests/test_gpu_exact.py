@@ -120,8 +120,12 @@ def test_grouped_mixed_scaling(mmlib):
     for (n, m, p, dA, dB, C), (A, B) in zip(probs, host):
         assert_full(C.cpu().numpy(), A, B, "f32")
         C1 = torch.full_like(C, float("nan"))
-        assert mmlib.mm_gemm(n, m, p, dA, dB, C1, mmlib.MM_F32, mmlib.MM_MODE_SPLIT_BF16X3) == 0
+        assert mmlib.mm_gemm_grouped([(n, m, p, dA, dB, C1)], mmlib.MM_F32,
+                                     mmlib.MM_MODE_SPLIT_BF16X3) == 0
         assert torch.equal(C, C1)
+        C2 = torch.full_like(C, float("nan"))
+        assert mmlib.mm_gemm(n, m, p, dA, dB, C2, mmlib.MM_F32, mmlib.MM_MODE_SPLIT_BF16X3) == 0
+        assert_full(C2.cpu().numpy(), A, B, "f32")
 
 
 @pytest.mark.parametrize("mode", MODES)

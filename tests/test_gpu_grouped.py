@@ -40,14 +40,22 @@ def test_grouped_uneven(mmlib, mode):
 
 
 def test_grouped_matches_single(mmlib):
-    """Each grouped result equals the same product run alone (same tiles)."""
+    """Each grouped result equals the same product run alone as a grouped call
+    of one (same tiles, same tail split), and mm_gemm's result (the fused
+    split-K kernel for products with few tiles) within the tolerance."""
     probs, host = _problems(12, 9)
     assert mmlib.mm_gemm_grouped(probs, mmlib.MM_F32, mmlib.MM_MODE_SPLIT_BF16X3) == 0
-    for (n, m, p, A, B, C) in probs:
+    for (n, m, p, A, B, C), (Ah, Bh) in zip(probs, host):
         C1 = torch.full_like(C, float("nan"))
-        assert mmlib.mm_gemm(n, m, p, A, B, C1, mmlib.MM_F32, mmlib.MM_MODE_SPLIT_BF16X3) == 0
+        assert mmlib.mm_gemm_grouped([(n, m, p, A, B, C1)], mmlib.MM_F32,
+                                     mmlib.MM_MODE_SPLIT_BF16X3) == 0
         bn_g = mmlib.mm_tune_query(n, m, p)[1]
         assert torch.equal(C, C1), (n, m, p, bn_g)
+        C2 = torch.full_like(C, float("nan"))
+        assert mmlib.mm_gemm(n, m, p, A, B, C2, mmlib.MM_F32, mmlib.MM_MODE_SPLIT_BF16X3) == 0
+        absref = np.abs(Ah.astype(np.float64)) @ np.abs(Bh.astype(np.float64))
+        e = oracle.rel_errors(C2.cpu().numpy(), C1.cpu().numpy(), absref).max()
+        assert e <= oracle.tolerance(m, "f32"), (n, m, p, e)
 
 
 def test_grouped_config4_sample(mmlib):

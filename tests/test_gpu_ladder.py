@@ -23,20 +23,27 @@ def test_x6_matches_oracle(mmlib, shape):
     assert_full(C, A, B, "f32")
 
 
-def test_x6_more_accurate_than_x3(mmlib):
-    """At m = 4096 the two-part split carries up to 3 2^-16 of each term; the
-    three-part one keeps every term to about 2^-24, so its error on the same
-    inputs is far smaller (and near the SIMT kernel's)."""
+def test_x6_more_accurate_than_x3_where_the_split_dominates(mmlib):
+    """With one non-zero term per output (B holds one entry per column) the
+    two-part split leaves up to 3 2^-16 of the term, the three-part split about
+    2^-24.  On dense uniform data at the same m = 4096 both errors come from
+    the tensor cores' FP32 accumulation of thousands of products and are of the
+    same size (measured on GB300: 4.7e-7 and 6.1e-7 of |A||B|), both far within
+    the tolerance."""
     n, m, p = 256, 4096, 256
     A = synth.uniform_pm1(63, (n, m))
+    Bs = np.zeros((m, p), np.float32)
+    Bs[(np.arange(p) * 13) % m, np.arange(p)] = synth.uniform_pm1(64, p)
+    e3, _ = full_errors(run_gemm(mmlib, A, Bs, mmlib.MM_MODE_SPLIT_BF16X3), A, Bs)
+    e6, _ = full_errors(run_gemm(mmlib, A, Bs, mmlib.MM_MODE_SPLIT_BF16X6), A, Bs)
+    tol = oracle.tolerance(m, "f32")
+    assert e3.max() <= tol and e6.max() <= tol
+    assert e6.max() * 64 < e3.max(), (e6.max(), e3.max())
     B = synth.uniform_pm1(64, (m, p))
     e3, _ = full_errors(run_gemm(mmlib, A, B, mmlib.MM_MODE_SPLIT_BF16X3), A, B)
     e6, _ = full_errors(run_gemm(mmlib, A, B, mmlib.MM_MODE_SPLIT_BF16X6), A, B)
-    es, _ = full_errors(run_gemm(mmlib, A, B, mmlib.MM_MODE_SIMT), A, B)
-    tol = oracle.tolerance(m, "f32")
     assert e3.max() <= tol and e6.max() <= tol
-    assert e6.max() * 8 < e3.max(), (e6.max(), e3.max())
-    assert e6.max() < 4 * es.max(), (e6.max(), es.max())
+    assert e6.max() <= 4 * e3.max(), (e6.max(), e3.max())
 
 
 def test_x6_small_integers_exact(mmlib):

@@ -63,12 +63,20 @@ def test_alone_equals_in_the_mix(server):
         lat.append(ms)
     st, done, batches, waiting, resident = mm.mm_serve_stats()
     assert done == 60 and waiting == 0 and resident == 0 and batches >= 2
-    # every result again, alone, through mm_gemm: identical bits
+    # every result again, alone (a grouped call of that product only, the
+    # path serving batches take): identical bits; and through mm_gemm, which
+    # runs products with few tiles on the fused split-K kernel: within the
+    # tolerance
     for (n, m, p, A, B, C, f64) in reqs:
         C1 = torch.full_like(C, float("nan"))
         dt = mm.MM_F64 if f64 else mm.MM_F32
-        assert mm.mm_gemm(n, m, p, A, B, C1, dt, mm.MM_MODE_AUTO) == 0
+        assert mm.mm_gemm_grouped([(n, m, p, A, B, C1)], dt, mm.MM_MODE_AUTO) == 0
         assert torch.equal(C, C1), (n, m, p, f64)
+        C2 = torch.full_like(C, float("nan"))
+        assert mm.mm_gemm(n, m, p, A, B, C2, dt, mm.MM_MODE_AUTO) == 0
+        absref = (A.abs().double() @ B.abs().double()).cpu().numpy()
+        e = oracle.rel_errors(C2.cpu().numpy(), C1.cpu().numpy(), absref).max()
+        assert e <= oracle.tolerance(m, "f64" if f64 else "f32"), (n, m, p, f64, e)
     # and a sample of them against the oracle
     for k in range(0, 60, 6):
         n, m, p, A, B, C, f64 = reqs[k]

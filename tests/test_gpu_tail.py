@@ -14,7 +14,7 @@ import pytest
 import torch
 
 import synth
-from gpu_util import assert_full, dev, run_gemm, sampled_check
+from gpu_util import assert_full, dev, run_gemm, run_packed, sampled_check
 
 pytestmark = pytest.mark.gpu
 
@@ -55,7 +55,7 @@ def test_tail_small_integers_bit_exact(mmlib, shape):
     n, m, p = shape
     A = synth.small_ints(2101, (n, m))
     B = synth.small_ints(2102, (m, p))
-    C = run_gemm(mmlib, A, B, mmlib.MM_MODE_SPLIT_BF16X3)
+    C = run_packed(mmlib, A, B, mmlib.MM_MODE_SPLIT_BF16X3)
     exact = A.astype(np.float64) @ B.astype(np.float64)  # exact: |c| < 2^53
     assert np.array_equal(C.astype(np.float64), exact)
 
@@ -65,7 +65,7 @@ def test_tail_uniform_full_oracle(mmlib, shape):
     n, m, p = shape
     A = synth.uniform_pm1(2201, (n, m))
     B = synth.uniform_pm1(2202, (m, p))
-    C = run_gemm(mmlib, A, B, mmlib.MM_MODE_SPLIT_BF16X3)
+    C = run_packed(mmlib, A, B, mmlib.MM_MODE_SPLIT_BF16X3)
     assert_full(C, A, B, "f32")
 
 
@@ -73,7 +73,7 @@ def test_tail_uniform_mixed_sampled(mmlib):
     n, m, p = MIXED
     A = synth.uniform_pm1(2301, (n, m))
     B = synth.uniform_pm1(2302, (m, p))
-    C = run_gemm(mmlib, A, B, mmlib.MM_MODE_SPLIT_BF16X3)
+    C = run_packed(mmlib, A, B, mmlib.MM_MODE_SPLIT_BF16X3)
     sampled_check(C, A, B, "f32")
 
 
@@ -90,7 +90,7 @@ def test_tail_deterministic_and_batch_invariant(mmlib):
     outs = []
     for _ in range(2):
         C = torch.full((n, p), float("nan"), device="cuda")
-        assert mm.mm_gemm(n, m, p, dA, dB, C, mm.MM_F32, mm.MM_MODE_SPLIT_BF16X3) == 0
+        assert mm.mm_gemm_grouped([(n, m, p, dA, dB, C)], mm.MM_F32, mm.MM_MODE_SPLIT_BF16X3) == 0
         outs.append(C.cpu().numpy())
     assert np.array_equal(outs[0], outs[1])
     for other in ((64, m, 64), (300, 700, 200)):  # same split kind / another kind
@@ -113,11 +113,11 @@ def test_tail_three_part_kind(mmlib):
     assert s > 1 and 0 < f < tiles
     A = synth.small_ints(2501, (n, m))
     B = synth.small_ints(2502, (m, p))
-    C = run_gemm(mmlib, A, B, mmlib.MM_MODE_SPLIT_BF16X3)
+    C = run_packed(mmlib, A, B, mmlib.MM_MODE_SPLIT_BF16X3)
     assert np.array_equal(C.astype(np.float64), A.astype(np.float64) @ B.astype(np.float64))
     A = synth.uniform_pm1(2503, (n, m))
     B = synth.uniform_pm1(2504, (m, p))
-    C = run_gemm(mmlib, A, B, mmlib.MM_MODE_SPLIT_BF16X3)
+    C = run_packed(mmlib, A, B, mmlib.MM_MODE_SPLIT_BF16X3)
     sampled_check(C, A, B, "f32")
 
 
@@ -145,6 +145,6 @@ def test_tail_with_scaled_operands(mmlib):
     eb = synth.row_scale_exponents(2702, p, choices=(-45, 45))
     A = (synth.uniform_pm1(2703, (n, m)).astype(np.float64) * np.ldexp(1.0, ea)[:, None]).astype(np.float32)
     B = (synth.uniform_pm1(2704, (m, p)).astype(np.float64) * np.ldexp(1.0, eb)[None, :]).astype(np.float32)
-    C = run_gemm(mmlib, A, B, mmlib.MM_MODE_SPLIT_BF16X3)
+    C = run_packed(mmlib, A, B, mmlib.MM_MODE_SPLIT_BF16X3)
     assert np.all(np.isfinite(C))
     assert_full(C, A, B, "f32")

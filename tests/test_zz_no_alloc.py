@@ -17,7 +17,7 @@ import torch
 
 import oracle
 import synth
-from gpu_util import dev
+from gpu_util import dev, fused_slices
 
 pytestmark = pytest.mark.gpu
 
@@ -81,16 +81,17 @@ def test_static_entry_rescaled_rows_then_uniform(mmlib):
 
 
 def test_static_entry_bitwise_where_no_tail_split(mmlib):
-    """Where mm_gemm does not split its last wave along K, both entry points
-    run the same kernels with the same tiles, so the bits agree."""
+    """Where mm_gemm neither splits its last wave along K nor runs the product
+    on the fused split-K kernel, both entry points run the same kernels with
+    the same tiles, so the bits agree."""
     mm = mmlib
     fn = _static_entry(mm)
     s = torch.cuda.current_stream()
     checked = 0
-    for seed, (n, m, p) in enumerate(((1000, 1500, 900), (256, 4096, 256), (129, 65, 300))):
+    for seed, (n, m, p) in enumerate(((2432, 512, 2048), (2560, 2300, 1024), (1000, 1500, 900))):
         st, tiles, split_from, split_s = mm.mm_tune_query_tail(n, m, p)
         assert st == mm.MM_OK
-        if split_s > 1:
+        if split_s > 1 or fused_slices(mm, n, m, p) > 0:
             continue
         A = synth.uniform_pm1(9400 + seed, (n, m))
         B = synth.uniform_pm1(9500 + seed, (m, p))
