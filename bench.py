@@ -19,7 +19,9 @@ in Listing 1's order) on a bounded sample of the same workload: there is no
 reference implementation of this GPU path to run.
 Multi-GPU (torchrun): every rank runs its own product (independent problems,
 weak scaling); no collective touches the data, only a barrier and a max of
-the times.
+the times.  With --shard rows one product is split by row blocks of A and C
+over the ranks instead (strong scaling; B replicated; the gather of C is
+timed apart from the product).
 """
 from __future__ import annotations
 
@@ -418,6 +420,9 @@ def bench_stress(mm, stream, peaks, reps: int = 10):
             gbs = nbytes / (ms * 1e-3) / 1e9
             out["skinny_64x16384x64_" + name] = {"us": ms * 1e3, "gbs": gbs, "frac_hbm": gbs / hbm}
         out["skinny_check_split"] = gpu_check(mm, n, m, p, As[0], Bs[0], Cs[0], mm.MM_F32)
+        _, tiles, sl, ql, csz = mm.mm_tune_query_splitk(n, m, p)
+        out["skinny_split_path"] = ("fused split-K: %d slices in %d clusters of %d" % (sl, ql, csz)
+                                    if sl else "packed")
         del As, Bs, Cs
         # 3c: B = diag(d) through the general product (dense flops counted)
         n = 4096
@@ -492,19 +497,36 @@ def bench_grouped(mm, stream, steps: int, seed: int = 4, count: int = 4096):
         out[name + "_ms"] = ms
         out[name + "_launches_per_step"] = (mm.mm_launch_count() - l0) / k
     mm.check_status(mm.mm_sync(stream), "grouped sync")
-    n, m, p, A, B, C = probs[0]
-    out["check_first"] = gpu_check(mm, n, m, p, A, B, C, mm.MM_F32)
+    # every instance: the library's FP64 GPU check, one Freivalds vector and 64
+    # sampled entries, each against its own tolerance 1e-6 sqrt(m)
+    grouped()
+    mm.check_status(mm.mm_sync(stream), "grouped check run")
+    worst, worst_ratio, over = 0.0, 0.0, 0
+    for g, (n, m, p, A, B, C) in enumerate(probs):
+        fr, sm = gpu_check(mm, n, m, p, A, B, C, mm.MM_F32, seed=100 + g, samples=64)
+        e = max(fr, sm)
+        tol = 1e-6 * m ** 0.5
+        worst = max(worst, e)
+        worst_ratio = max(worst_ratio, e / tol)
+        over += int(e > tol)
+    out["check_all"] = {"instances": len(probs), "max_err": worst,
+                        "max_err_over_tol": worst_ratio, "over_tol": over,
+                        "check": "per instance: 1 Freivalds vector + 64 sampled entries (FP64, GPU)"}
     del probs
     return out
 
 
 def bench_serving(mm, count: int, rate_frac: float, seed: int = 5, streams: int = 2,
-                  max_batch: int = 0, capacity=None, f64_mode=None):
+                  max_batch: int = 0, capacity=None, f64_mode=None, check: bool = False):
     """Poisson replay of `count` requests (dims log-uniform in [64, 4096], 20%
     FP64) through mm_submit/mm_poll with operands resident on the device.
     f64_mode: the path of the FP64 requests (default MM_MODE_DGEMM).
     The arrival rate is rate_frac x the measured capacity (requests/s of the
-    same mix submitted all at once).  Returns p50/p99 latency and rates."""
+    same mix submitted all at once).  Returns p50/p99 latency (all requests and
+    per class: FP32 on the split path, FP64) and rates; with check=True the
+    serving loop also runs the library's FP64 GPU check (Freivalds + 64
+    sampled entries) on every result and the maximum normalised error of each
+    class is returned beside its tolerance's worst case over the mix."""
     import numpy as np
     import torch
 
@@ -531,16 +553,26 @@ def bench_serving(mm, count: int, rate_frac: float, seed: int = 5, streams: int 
         st, rid = mm.mm_submit(n, m, p, A, B, C, dt, md)
         mm.check_status(st, "mm_submit")
         held[0] += C.numel() * C.element_size()
+        cls[rid] = (bool(f64[k]), m)
         return rid, C
+
+    cls = {}          # request id -> (is FP64, inner dimension)
+    err_max = {False: 0.0, True: 0.0}
+    err_ratio = {False: 0.0, True: 0.0}  # error / tolerance of the request
 
     def drain(live, lat, budget=32):
         # polls the oldest requests first, a bounded number per call
         done = []
         for rid in itertools.islice(live, budget):
-            st, res, _, ms = mm.mm_poll(rid)
+            st, res, err, ms = mm.mm_poll(rid)
             if st == mm.MM_OK:
                 mm.check_status(res, "request")
-                lat.append(ms)
+                is64, mk = cls.pop(rid)
+                lat.append((ms, is64))
+                if check:
+                    tol = (1e-14 if is64 else 1e-6) * max(mk, 1) ** 0.5
+                    err_max[is64] = max(err_max[is64], err)
+                    err_ratio[is64] = max(err_ratio[is64], err / tol)
                 done.append(rid)
         for rid in done:
             C = live.pop(rid)
@@ -555,8 +587,8 @@ def bench_serving(mm, count: int, rate_frac: float, seed: int = 5, streams: int 
     flops = float(np.sum(2.0 * dims[:, 0] * dims[:, 1] * dims[:, 2]))
     dev_index = torch.cuda.current_device()
     mm.mm_shutdown()
-    mm.check_status(mm.mm_init(n_streams=streams, max_batch=max_batch, device=dev_index),
-                    "mm_init serving")
+    mm.check_status(mm.mm_init(n_streams=streams, max_batch=max_batch, device=dev_index,
+                               check=1 if check else 0), "mm_init serving")
     if capacity is None:
         # capacity: everything submitted at once
         live, lat = collections.OrderedDict(), []
@@ -585,11 +617,20 @@ def bench_serving(mm, count: int, rate_frac: float, seed: int = 5, streams: int 
     st, completed, batches, waiting, resident = mm.mm_serve_stats()
     mm.mm_shutdown()
     mm.check_status(mm.mm_init(device=dev_index), "mm_init default")
-    lat = np.asarray(lat)
-    return {"requests": count, "rate_req_s": rate, "capacity_req_s": capacity,
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "throughput_req_s": count / wall, "tflops": flops / wall / 1e12,
-            "batches": batches, "streams": streams, "max_batch": max_batch or 256}
+    ms_all = np.asarray([x[0] for x in lat])
+    out = {"requests": count, "rate_req_s": rate, "capacity_req_s": capacity,
+           "p50_ms": float(np.percentile(ms_all, 50)), "p99_ms": float(np.percentile(ms_all, 99)),
+           "throughput_req_s": count / wall, "tflops": flops / wall / 1e12,
+           "batches": batches, "streams": streams, "max_batch": max_batch or 256}
+    for name, want in (("f32_split", False), ("f64", True)):
+        v = np.asarray([x[0] for x in lat if x[1] == want])
+        if v.size:
+            out[name] = {"requests": int(v.size), "p50_ms": float(np.percentile(v, 50)),
+                         "p99_ms": float(np.percentile(v, 99))}
+            if check:
+                out[name]["max_err"] = err_max[want]
+                out[name]["max_err_over_tol"] = err_ratio[want]
+    return out
 
 
 def run_grouped_only(args):
@@ -680,22 +721,28 @@ def run_serve_sweep(args):
     import paper_1306_6192_gb300 as mm
     torch.cuda.set_device(0)
     mm.check_status(mm.mm_init(device=0), "mm_init")
+    f64_md = mm.MM_MODE_OZAKI if args.serve_f64 == "ozaki" else mm.MM_MODE_DGEMM
     rows = []
     cap = None
     for frac in args.serve_rates:
         row = {"rate_frac": frac}
         for name, st_, mb in (("batched", 2, 0), ("one_per_launch", 1, 1)):
             r = bench_serving(mm, args.serve_requests, frac, streams=st_, max_batch=mb,
-                              capacity=cap)
+                              capacity=cap, f64_mode=f64_md)
             cap = r["capacity_req_s"] if cap is None else cap
             row[name] = {k: r[k] for k in ("rate_req_s", "p50_ms", "p99_ms", "throughput_req_s",
-                                           "tflops", "batches")}
+                                           "tflops", "batches", "f32_split", "f64") if k in r}
         rows.append(row)
         print(json.dumps(row), file=sys.stderr, flush=True)
+    # the FP64 GPU check of every result, at 0.9 x capacity, on a shorter replay
+    chk = bench_serving(mm, min(args.serve_requests, 5000), 0.9, streams=2, max_batch=0,
+                        capacity=cap, f64_mode=f64_md, check=True)
     mm.mm_shutdown()
     print(json.dumps({"metric": "serving p50/p99 ms", "requests": args.serve_requests,
                       "capacity_req_s": cap, "mix": "dims log-uniform [64,4096], 20% FP64",
-                      "sweep": rows}))
+                      "f64_path": args.serve_f64, "sweep": rows,
+                      "checked_replay": {k: chk[k] for k in ("requests", "f32_split", "f64")
+                                         if k in chk}}))
     return 0
 
 
@@ -761,7 +808,16 @@ def run_mine(args):
 
     with Clocks(local) as clk:
         ms, launches = timed(step, args.steps, args.warmup, trace=True)
+        # the same step keeps running, untimed, for 1.2 s more, so that the
+        # 50 ms clock samples describe the GPU while it runs this step (the
+        # timed region alone can be shorter than a few sampling intervals)
+        t_end = time.perf_counter() + 1.2
+        while time.perf_counter() < t_end:
+            for _ in range(10):
+                step()
+            torch.cuda.synchronize()
     clocks = clk.summary()
+    clocks["window"] = "timed region + 1.2 s more of the same step"
     per_kernel = {}
     for k in ("split_scale", "split_pack", "split_verify", "split_fix", "split_tc", "simt_f32"):
         st, cnt, kms = mm.mm_trace_read(k)
@@ -812,6 +868,15 @@ def run_mine(args):
         ms_d, _ = timed(f64, 2, 1)
         extra["dgemm_f64_tflops"] = 2.0 * nd ** 3 / (ms_d / 2 * 1e-3) / 1e12
         extra["dgemm_size"] = nd
+        # the CUDA cores' measured FMA rates: the SIMT and DGEMM rooflines
+        st32, f32 = mm.mm_measure_fma_peak(mm.MM_F32, 4096)
+        st64, f64r = mm.mm_measure_fma_peak(mm.MM_F64, 256)
+        if st32 == mm.MM_OK and st64 == mm.MM_OK:
+            extra["ffma_peak_tflops"] = f32 / 1e12
+            extra["dfma_peak_tflops"] = f64r / 1e12
+            extra["dgemm_frac_of_measured_dfma"] = extra["dgemm_f64_tflops"] / (f64r / 1e12)
+            if "simt_f32_tflops" in extra:
+                extra["simt_frac_of_measured_ffma"] = extra["simt_f32_tflops"] / (f32 / 1e12)
         extra["dgemm_check"] = gpu_check(mm, nd, nd, nd, A64, B64, C64, mm.MM_F64)
         # FP64 emulated on the e4m3 tensor cores (Ozaki scheme, default slices)
         # on full 53-bit FP64 operands of the same size
@@ -901,6 +966,87 @@ def run_mine(args):
     return 0
 
 
+def run_shard(args):
+    """One product split by row blocks over the ranks (strong scaling): rank r
+    multiplies its rows [r0, r1) of A by the replicated B into its rows of C
+    (paper_1306_6192_gb300.shard), with no collective inside the timed
+    region; an NCCL all-gather of the C blocks is timed afterwards and
+    reported on its own."""
+    import torch
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1306_6192_gb300 as mm
+    from paper_1306_6192_gb300 import shard
+    import synth
+
+    mm.check_status(mm.mm_init(device=local), "mm_init")
+    n = args.size
+    r0, r1 = shard.local_block(n, rank, world)
+    A = torch.from_numpy(synth.uniform_pm1(0, (n, n))[r0:r1]).cuda()  # this rank's rows
+    B = torch.from_numpy(synth.uniform_pm1(1, (n, n))).cuda()         # replicated
+    C = torch.empty((r1 - r0, n), device="cuda")
+    stream = torch.cuda.Stream()
+    md = {"split": mm.MM_MODE_SPLIT_BF16X3, "simt": mm.MM_MODE_SIMT}[args.mode]
+
+    def step():
+        if r1 > r0:
+            mm.check_status(mm.mm_gemm_async(r1 - r0, n, n, A, B, C, mm.MM_F32, md, stream),
+                            "shard")
+
+    for _ in range(args.warmup):
+        step()
+    mm.check_status(mm.mm_sync(stream), "warmup")
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = mm.mm_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = mm.mm_launch_count() - l0
+    mm.check_status(mm.mm_sync(stream), "timed")
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda") / args.steps
+    gather_ms = None
+    if dist is not None:
+        rows = max(b1 - b0 for b0, b1 in shard.row_blocks(n, world))
+        buf = torch.zeros((rows, n), device="cuda")
+        buf[: r1 - r0] = C
+        parts = [torch.empty_like(buf) for _ in range(world)]
+        dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dist.all_gather(parts, buf)
+        torch.cuda.synchronize()
+        gather_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, dist, "cuda")
+    flops = 2.0 * n * n * n
+    line = {
+        "metric": "GEMM TFLOP/s", "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+        "dtype": "bf16x3->f32" if args.mode == "split" else "f32", "data": "synthetic",
+        "path": "row blocks of one product, split-BF16x3 tcgen05 per rank",
+        "config": dict(workload_config(n, world), parallelism="row blocks x%d" % world,
+                       rows_per_rank=[b1 - b0 for b0, b1 in shard.row_blocks(n, world)]),
+        "gpu_launches": launches, "clocks": clk.summary(),
+        "gather_ms": gather_ms,
+    }
+    mm.mm_shutdown()
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -924,6 +1070,10 @@ def main(argv=None):
                     help="only the FP64 product emulated by the Ozaki scheme")
     ap.add_argument("--ozaki-slices", type=int, default=14)
     ap.add_argument("--stress-only", action="store_true", help="only the config-3 stress shapes")
+    ap.add_argument("--serve-f64", choices=["dgemm", "ozaki"], default="dgemm",
+                    help="path of the serving mix's FP64 requests")
+    ap.add_argument("--shard", choices=["none", "rows"], default="none",
+                    help="rows: one product split by row blocks over the ranks (strong scaling)")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "mine":
         args.warmup = 3
@@ -937,6 +1087,8 @@ def main(argv=None):
         return run_ozaki_only(args)
     if args.stress_only:
         return run_stress_only(args)
+    if args.shard == "rows":
+        return run_shard(args)
     return run_mine(args)
 
 

@@ -275,8 +275,10 @@ mm_status mm_tune_query_tail(int64_t n, int64_t m, int64_t p, int *tiles,
                              int *split_from, int *split_s);
 
 /* Fused split-K plan of the split path for one product n x m x p (mm_gemm /
- * mm_gemm_async on MM_MODE_SPLIT_BF16X3): a product with fewer 128 x 128
- * output tiles than half the SMs runs as ONE launch that reads A and B
+ * mm_gemm_async on MM_MODE_SPLIT_BF16X3 or _X6): a product with fewer
+ * 128 x 128 output tiles than half the SMs, whose slices need at most eight
+ * 64-wide K blocks each, with A and B 16-byte aligned and m and p multiples
+ * of 4 (the kernel loads them with TMA), runs as ONE launch that reads A and B
  * directly, splits each 64-wide K block into bf16 parts in shared memory
  * (power-of-two scales per row of A and column of B within a block, only for
  * blocks holding an entry outside [2^-40, 2^40]), multiplies on the tensor
@@ -301,10 +303,18 @@ mm_status mm_tune_query_splitk(int64_t n, int64_t m, int64_t p, int *tiles, int 
  * parts (1: no split).  It picks the split that minimises a makespan model of
  * the round-robin assignment of work units to CTAs: at most 4 parts, at
  * least 2 pack rows per part, at most 2 x grid split units, and no split for
- * products with fewer tiles than CTAs and fewer than 32 pack rows.
+ * products with fewer tiles than CTAs and fewer than 16 pack rows.
  * Returns MM_EINVAL for negative sizes or NULL outputs. */
 mm_status mm_tail_plan(int64_t tiles, int grid, int kt, int bn, int64_t m,
                        double products, int *split_from, int *split_s);
+
+/* Measured fused multiply-add rate of the CUDA cores for dtype dt (FP32
+ * FFMA or FP64 DFMA), in flops per second (2 per FMA): a grid of several
+ * blocks per SM runs independent FMA chains on registers for `iters` rounds
+ * of 128 FMAs per thread, timed with CUDA events on the library stream.  The
+ * denominator of the SIMT FP32 and DGEMM kernels' rooflines; it reads the
+ * device only.  Synchronous.  Not in the paper. */
+mm_status mm_measure_fma_peak(mm_dtype dt, int64_t iters, double *flops_per_s);
 
 /* ----------------------------------------------------------------- tracing */
 

@@ -99,6 +99,8 @@ def lib():
             getattr(L, name).restype = ctypes.c_int
         L.mm_gemm_split_static.argtypes = [_i64, _i64, _i64, _vp, _vp, _vp, _vp]
         L.mm_gemm_split_static.restype = ctypes.c_int
+        L.mm_measure_fma_peak.argtypes = [st, _i64, _dp]
+        L.mm_measure_fma_peak.restype = ctypes.c_int
         L.mm_ozaki_slices.argtypes = [ctypes.c_int]
         L.mm_ozaki_slices.restype = ctypes.c_int
         L.mm_ozaki_plan.argtypes = [_i64, _i64, _i64, ctypes.c_int, ctypes.POINTER(_i64),
@@ -274,6 +276,13 @@ def mm_tune_query_splitk(n, m, p):
     v = [ctypes.c_int(0) for _ in range(4)]
     st = lib().mm_tune_query_splitk(n, m, p, *[ctypes.byref(x) for x in v])
     return (st,) + tuple(x.value for x in v)
+
+
+def mm_measure_fma_peak(dt, iters: int = 4096):
+    """Returns (status, flops per second) of the CUDA cores' FMA for dt."""
+    v = ctypes.c_double(0.0)
+    st = lib().mm_measure_fma_peak(dt, iters, ctypes.byref(v))
+    return st, v.value
 
 
 def mm_tail_plan(tiles, grid, kt, bn, m, products):

@@ -172,7 +172,7 @@ int tc_grid(const TcConfig &cfg);
 // `tiles` output tiles of 128 x bn, kt pack rows of K, the kind's bf16 (or
 // e4m3) products per K step, on `grid` persistent CTAs.  The makespan model
 // of the product run alone decides; a product that fills less than one wave
-// and has fewer than 32 pack rows is never split (grouped tables of many
+// and has fewer than 16 pack rows is never split (grouped tables of many
 // small products gain nothing from it).
 struct TcTail {
   int split_from, split_s;

@@ -548,7 +548,7 @@ TcTail tc_tail_plan(int64_t tiles, int grid, int kt, int bn, int64_t m, double p
   TcTail best{(int)tiles, 1};
   if (tiles <= 0 || grid <= 1 || kt < 4) return best;
   const int64_t G = grid;
-  if (tiles < G && kt < 32) return best;  // small products: grouped tables hold many
+  if (tiles < G && kt < 16) return best;  // small products: grouped tables hold many
   // units c, c + G, c + 2G, ... below x go to CTA c
   auto upto = [G](int64_t x, int64_t c) -> int64_t { return x > c ? (x - c + G - 1) / G : 0; };
   // per-unit overhead of a part, in tiles: the pipeline refill (~2 us)

@@ -418,9 +418,11 @@ FusedPlan fused_plan(int64_t n, int64_t m, int64_t p, TcKind kind) {
       }
     }
   }
-  // a slice of more than four K blocks is slower here than on the packed
-  // path, whose operands are split once and streamed by TMA
-  if (best.S > 0 && ceil_div(kb, best.S) > 4) best = FusedPlan{0, 0, 0};
+  // a slice of more than eight K blocks is slower here than on the packed
+  // path, whose operands are split once and streamed by TMA (GB300, 1024^3:
+  // 52 us fused at eight blocks per slice against 58 us packed; 1024 x 2048
+  // x 1024 at sixteen: 90 against 69 us)
+  if (best.S > 0 && ceil_div(kb, best.S) > 8) best = FusedPlan{0, 0, 0};
   return best;
 }
 

@@ -37,8 +37,10 @@ def test_plan(mmlib):
     assert tiles == 1 and s >= 64 and q > 1 and cs in (2, 4, 8) and s == q * cs
     tiles, s, q, cs = _plan(mm, 512, 512, 512)
     assert tiles == 16 and s >= 2 and tiles * s <= n_sm
-    # more than four K blocks per slice: the packed path
-    assert _plan(mm, 1024, 1024, 1024)[1] == 0
+    # 1024^3: eight K blocks per slice; 1024 x 2048 x 1024 would need sixteen
+    # and takes the packed path
+    assert _plan(mm, 1024, 1024, 1024)[1] >= 2
+    assert _plan(mm, 1024, 2048, 1024)[1] == 0
     tiles, s, q, cs = _plan(mm, 3, 8, 12)
     assert tiles == 1 and s == 1 and q == 1 and cs == 1
     # products that fill half the SMs with whole tiles keep the packed path

@@ -35,7 +35,7 @@ def test_bounds_over_a_sweep(mm):
         assert r * s <= 2 * grid            # at most two rounds of parts
         assert kt // s >= 2                 # every part keeps two pack rows
         assert r in (tiles % grid, tiles % grid + grid)  # the last (or last two) waves
-        assert not (tiles < grid and kt < 32)
+        assert not (tiles < grid and kt < 16)
 
 
 def test_full_waves_are_not_split(mm):
@@ -50,10 +50,17 @@ def test_square_8192_splits_its_last_wave(mm):
 
 
 def test_small_products_of_grouped_tables_are_not_split(mm):
-    # the grouped workload's products: at most 8 x 8 tiles, m <= 1024 (kt <= 16)
+    # the grouped workload's products below m = 961 (kt <= 15): never split
     for tiles in range(1, 65):
-        for kt in (1, 2, 8, 16):
+        for kt in (1, 2, 8, 15):
             assert plan(mm, tiles, 152, kt, 128, kt * 64, 6.0)[1] == 1
+
+
+def test_underfilled_1024_cube_is_split(mm):
+    # 1024^3 on the three-part kind: 64 tiles of 128 x 128, 16 pack rows of
+    # K, on 152 CTAs: half the SMs idle unless the tiles are cut along K
+    f, s = plan(mm, 64, 152, 16, 128, 1024, 6.0)
+    assert f == 0 and s >= 2
 
 
 def test_one_long_tile_is_split(mm):
