@@ -808,16 +808,8 @@ def run_mine(args):
 
     with Clocks(local) as clk:
         ms, launches = timed(step, args.steps, args.warmup, trace=True)
-        # the same step keeps running, untimed, for 1.2 s more, so that the
-        # 50 ms clock samples describe the GPU while it runs this step (the
-        # timed region alone can be shorter than a few sampling intervals)
-        t_end = time.perf_counter() + 1.2
-        while time.perf_counter() < t_end:
-            for _ in range(10):
-                step()
-            torch.cuda.synchronize()
     clocks = clk.summary()
-    clocks["window"] = "timed region + 1.2 s more of the same step"
+    clocks["window"] = "the timed region"
     per_kernel = {}
     for k in ("split_scale", "split_pack", "split_verify", "split_fix", "split_tc", "simt_f32"):
         st, cnt, kms = mm.mm_trace_read(k)
@@ -859,6 +851,12 @@ def run_mine(args):
             ms_s, _ = timed(lambda: step(mm.MM_MODE_SIMT), max(2, args.steps // 4), 1)
             extra["simt_f32_tflops"] = flops / (ms_s / max(2, args.steps // 4) * 1e-3) / 1e12
             extra["split_over_simt"] = value / world / extra["simt_f32_tflops"]
+            # the CUDA cores' measured FFMA rate right after (the same clock):
+            # the SIMT kernel's roofline
+            st32, f32 = mm.mm_measure_fma_peak(mm.MM_F32, 4096)
+            if st32 == mm.MM_OK and f32 > 0:
+                extra["ffma_peak_tflops"] = f32 / 1e12
+                extra["simt_frac_of_measured_ffma"] = extra["simt_f32_tflops"] / (f32 / 1e12)
         nd = args.dgemm_size
         A64 = A[:nd, :nd].double().contiguous()
         B64 = B[:nd, :nd].double().contiguous()
@@ -868,15 +866,12 @@ def run_mine(args):
         ms_d, _ = timed(f64, 2, 1)
         extra["dgemm_f64_tflops"] = 2.0 * nd ** 3 / (ms_d / 2 * 1e-3) / 1e12
         extra["dgemm_size"] = nd
-        # the CUDA cores' measured FMA rates: the SIMT and DGEMM rooflines
-        st32, f32 = mm.mm_measure_fma_peak(mm.MM_F32, 4096)
+        # the CUDA cores' measured DFMA rate right after the DGEMM timing (at
+        # the same clock): the DGEMM roofline
         st64, f64r = mm.mm_measure_fma_peak(mm.MM_F64, 256)
-        if st32 == mm.MM_OK and st64 == mm.MM_OK:
-            extra["ffma_peak_tflops"] = f32 / 1e12
+        if st64 == mm.MM_OK and f64r > 0:
             extra["dfma_peak_tflops"] = f64r / 1e12
             extra["dgemm_frac_of_measured_dfma"] = extra["dgemm_f64_tflops"] / (f64r / 1e12)
-            if "simt_f32_tflops" in extra:
-                extra["simt_frac_of_measured_ffma"] = extra["simt_f32_tflops"] / (f32 / 1e12)
         extra["dgemm_check"] = gpu_check(mm, nd, nd, nd, A64, B64, C64, mm.MM_F64)
         # FP64 emulated on the e4m3 tensor cores (Ozaki scheme, default slices)
         # on full 53-bit FP64 operands of the same size
@@ -952,6 +947,18 @@ def run_mine(args):
         line["e2e"] = {"value": flops / t_e2e / 1e12, "unit": "TFLOP/s",
                        "h2d_bytes_per_step": 2 * n * n * 4, "d2h_bytes_per_step": n * n * 4}
         del Ah, Bh, Ch
+
+    # the headline step again, untimed, for 1.5 s with the clocks sampled: the
+    # timed region alone can be shorter than a few 50 ms sampling intervals.
+    # Run last, so that the power-capped clock of a sustained run does not
+    # carry over into the other legs.
+    with Clocks(local) as clk2:
+        t_end = time.perf_counter() + 1.5
+        while time.perf_counter() < t_end:
+            for _ in range(10):
+                step()
+            torch.cuda.synchronize()
+    line["clocks_steady"] = dict(clk2.summary(), window="1.5 s of the headline step, after the other legs")
 
     if rank == 0 and not args.no_cpu_baseline and not args.quick:
         rate, cores, rows, t = oracle_sample_rate(n)

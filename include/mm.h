@@ -23,8 +23,12 @@
  *                         unscaled exactly.  Not in the paper.
  *   MM_MODE_DGEMM         FP64 in/out, FP64 FMA.  The paper's Table 2
  *                         "double" column computes this product in double.
- *   MM_MODE_FP8           FP32 in/out through e4m3 operands with per-tile
- *                         power-of-two scales; accuracy is reported, not
+ *   MM_MODE_FP8           FP32 in/out through e4m3 operands: each row of A
+ *                         and column of B is cut into K blocks of 128 values,
+ *                         each block scaled by its own power of two (largest
+ *                         magnitude to [128, 256)); every block's product is
+ *                         accumulated on the tensor cores, unscaled exactly
+ *                         and added in FP32.  Accuracy is reported, not
  *                         guaranteed.  Not in the paper.
  *   MM_MODE_SPLIT_BF16X6  FP32 in/out on the tensor cores, the upper rung
  *                         of the split ladder: three bf16 parts (hi, mid,
@@ -311,7 +315,7 @@ mm_status mm_tail_plan(int64_t tiles, int grid, int kt, int bn, int64_t m,
 /* Measured fused multiply-add rate of the CUDA cores for dtype dt (FP32
  * FFMA or FP64 DFMA), in flops per second (2 per FMA): a grid of several
  * blocks per SM runs independent FMA chains on registers for `iters` rounds
- * of 128 FMAs per thread, timed with CUDA events on the library stream.  The
+ * of 192 FMAs per thread, timed with CUDA events on the library stream.  The
  * denominator of the SIMT FP32 and DGEMM kernels' rooflines; it reads the
  * device only.  Synchronous.  Not in the paper. */
 mm_status mm_measure_fma_peak(mm_dtype dt, int64_t iters, double *flops_per_s);
@@ -321,7 +325,8 @@ mm_status mm_measure_fma_peak(mm_dtype dt, int64_t iters, double *flops_per_s);
 /* When enabled, every kernel the library launches is bracketed by CUDA events
  * on its stream; mm_trace_read returns the launch count and summed device
  * time (ms) of the kernel named `kernel` ("simt_f32", "dgemm_f64",
- * "split_scale", "split_pack", "split_tc", "fused_tc", "fp8_tc", "check_f64") since the
+ * "split_pack", "split_verify", "split_fix", "split_tc", "fused_tc", "fp8_pack", "fp8_tc",
+ * "check_f64", "ozaki_max", "ozaki_digits", "ozaki_sum") since the
  * last reset.  Reading synchronises the recorded events. */
 mm_status mm_trace_enable(int on);
 mm_status mm_trace_reset(void);

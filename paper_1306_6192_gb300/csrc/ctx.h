@@ -1,5 +1,5 @@
 // Library context and host-side helpers shared by api.cu, grouped.cu,
-// tune.cu, serve.cu and fp8.cu.
+// tune.cu, serve.cu, fp8_blk.cu, tc_fused.cu, ozaki.cu and noalloc.cu.
 #pragma once
 
 #include "mm_internal.h"
@@ -130,8 +130,11 @@ struct FusedPlan {
 FusedPlan fused_plan(int64_t n, int64_t m, int64_t p, TcKind kind);
 mm_status run_fused(Scratch &ws, int64_t n, int64_t m, int64_t p, const float *A, const float *B,
                     float *C, TcKind kind, const FusedPlan &plan, cudaStream_t s);
-// FP8 path (report-only accuracy).
+// FP8 path (report-only accuracy): e4m3 operands with a power-of-two scale
+// per 128-value K block of each row of A and column of B (fp8_blk.cu).
 mm_status run_fp8(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s);
+mm_status run_fp8_blocks(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s);
+size_t fp8_blocks_scratch_bytes(int64_t n, int64_t m, int64_t p);
 // FP64 product by the Ozaki scheme on the e4m3 tensor cores with S digit
 // slices (ozaki.cu); ozaki_chunk(S) = the K columns per chunk that keep every
 // level sum exact in FP32; ozaki_scratch_bytes = an upper bound of the

@@ -71,8 +71,6 @@ struct SplitProb {
   int32_t bn, group_m;     // N tile (64, 128 or 256), raster band height
   int32_t unit_start;      // prefix over problems of tensor-core work units
   int32_t pack_start;      // prefix of pack tiles: mt*kt + nt*kt
-  int32_t red_start;       // prefix of scale-reduction items
-  int32_t red_a;           // reduction items for A rows: ceil(n/8)
   int32_t ver_start;       // prefix of verify items: ceil((n + p) / 32) each
   int32_t split_from;      // tail split (split_s <= 1: none; then split_from
   int32_t split_s;         //   is ignored and every tile is one unit)
@@ -125,16 +123,15 @@ cudaError_t launch_simt_f64(int64_t n, int64_t m, int64_t p, const double *A,
 cudaError_t launch_simt_grouped(bool f64, const SimtProb *d_probs, int nprobs,
                                 int total_tiles, bool all_vec, cudaStream_t s);
 
-// Prep: per-row/column max-abs reduction, then the split (hi/lo bf16) or
-// e4m3 conversion into the packs.
+// Prep of the packed split path: the split (hi/lo bf16) into the packs with
+// the row/column maxima, their verification and the re-pack of operands out
+// of range.
 // `map` arguments: item -> problem index arrays written by
 // launch_split_maps for tables of several problems, or nullptr.
 cudaError_t launch_split_maps(const SplitProb *d_probs, int nprobs, int *unit_map,
-                              int *pack_map, int *red_map, int *ver_map, cudaStream_t s);
+                              int *pack_map, int *ver_map, cudaStream_t s);
 // Verify items of a product: 32 rows/columns each.
 __host__ __device__ inline int64_t verify_items(int64_t n, int64_t p) { return (n + p + 31) / 32; }
-cudaError_t launch_split_scale(const SplitProb *d_probs, int nprobs,
-                               int total_items, const int *map, cudaStream_t s);
 // Pack modes (split kinds) and the per-problem flags they use.
 constexpr int kPackUnscaled = 1, kPackFix = 2;
 constexpr int kFlagScaleA = 1, kFlagScaleB = 2;
@@ -154,10 +151,6 @@ cudaError_t launch_split_pack(TcKind kind, int mode, const SplitProb *d_probs, i
 cudaError_t launch_split_verify(const SplitProb *d_probs, int nprobs, int64_t total_items,
                                 const int *map, int *flags, int *any, int max_kt, cudaStream_t s,
                                 bool write_cols = true);
-cudaError_t launch_fp8_pack(const SplitProb *d_probs, int nprobs,
-                            int total_tiles, const int *map, void *pack_base,
-                            cudaStream_t s);
-
 // Tensor-core mainloop + epilogue over all work units of all problems.
 struct TcConfig {
   int bkb;      // bytes of K per pipeline stage and pack row: 64 or 128

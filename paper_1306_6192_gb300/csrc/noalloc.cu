@@ -131,11 +131,8 @@ mm_status mm_gemm_split_static(int64_t n, int64_t m, int64_t p, const float *A, 
   sp.pB = sp.pA + (int64_t)sp.kt * n;
   sp.unit_start = 0;  // no tail split: split_s = 0 from the memset
   sp.pack_start = 0;
-  sp.red_start = 0;
-  sp.red_a = (int32_t)ceil_div(n, 8);
   const int64_t tiles = (int64_t)sp.mt * sp.nt;
   const int64_t packs = (int64_t)sp.mt * sp.kt + (int64_t)sp.nt * sp.kt;
-  const int64_t reds = sp.red_a + ceil_div(p, 32) * ceil_div(m, 256);
   SplitProb *d_tab = reinterpret_cast<SplitProb *>(base + kTableOff);
   int *d_flag = reinterpret_cast<int *>(base + kFlagOff);
   // The array keeps the previous call's contents: the timeout and scale flags
@@ -146,7 +143,6 @@ mm_status mm_gemm_split_static(int64_t n, int64_t m, int64_t p, const float *A, 
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_tab, &sp, sizeof(sp), cudaMemcpyHostToDevice, s);
   int *d_sflag = reinterpret_cast<int *>(base + kScaleFlagOff);
-  (void)reds;
   // same passes as mm_gemm's split path: unscaled pack with the maxima,
   // verification, re-pack of operands out of range
   if (e == cudaSuccess)

@@ -12,7 +12,7 @@ namespace mm {
 namespace {
 
 constexpr int kPeakThreads = 256;
-constexpr int kChains = 8;  // independent FMA chains per thread
+constexpr int kChains = 12;  // independent FMA chains per thread
 
 template <typename T>
 __global__ void __launch_bounds__(kPeakThreads)

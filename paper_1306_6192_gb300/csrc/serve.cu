@@ -145,8 +145,9 @@ size_t elem_bytes(mm_dtype dt) { return dt == MM_F64 ? 8 : 4; }
 size_t request_scratch(const mm_problem &q, mm_mode mode, int slices) {
   size_t b = 0;
   if (mode == MM_MODE_OZAKI) b += ozaki_scratch_bytes(q.n, q.m, q.p, slices);
-  if (mode == MM_MODE_SPLIT_BF16X3 || mode == MM_MODE_SPLIT_BF16X6 || mode == MM_MODE_FP8) {
-    const TcKind kind = mode == MM_MODE_FP8 ? kTcE4m3 : split_kind_of(mode, q.m);
+  if (mode == MM_MODE_FP8) b += fp8_blocks_scratch_bytes(q.n, q.m, q.p);
+  if (mode == MM_MODE_SPLIT_BF16X3 || mode == MM_MODE_SPLIT_BF16X6) {
+    const TcKind kind = split_kind_of(mode, q.m);
     TcChoice c = tune_choose(q.n, q.m, q.p);
     c.bn = tc_bn(kind, c.bn);
     const size_t kb = (size_t)ceil_div(q.m, pack_k(kind));  // pack rows per matrix row

@@ -11,12 +11,6 @@
 // the paper, whose kernels compute in the input type directly.
 //
 // Kernels:
-//   split_scale_kernel  max |a_ir| per row of A (a warp per row) and
-//                       max |b_rj| per column of B (strips of 32 columns x
-//                       256 rows, atomicMax on the float bit pattern, which
-//                       orders like the value for non-negative floats); used
-//                       by the e4m3 path, whose conversion needs the scales
-//                       first.
 //   split_pack_kernel   one block per 128 x 64 tile of A or bn x 64 tile of
 //                       B^T: scale, split, write the bf16 parts (hi, lo - or
 //                       hi, mid, lo for the three-part split) of the pack
@@ -39,9 +33,6 @@
 namespace mm {
 namespace {
 
-constexpr int kRowsPerScaleItem = 8;    // warps per block, one row each
-constexpr int kColStrip = 32;
-constexpr int kRowChunk = 256;
 
 __device__ __forceinline__ uint32_t abs_bits(float x) { return __float_as_uint(x) & 0x7fffffffu; }
 
@@ -49,92 +40,6 @@ __device__ __forceinline__ uint32_t umax(uint32_t a, uint32_t b) { return a > b 
 
 __device__ __forceinline__ bool aligned16(const void *p) {
   return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
-}
-
-__global__ void __launch_bounds__(256)
-split_scale_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *__restrict__ map) {
-  const int item = blockIdx.x;
-  const int g =
-      find_problem(probs, nprobs, map, item, [](const SplitProb &q) { return q.red_start; });
-  const SplitProb &pr = probs[g];
-  const int local = item - pr.red_start;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (local < pr.red_a) {
-    // a warp per row of A; 16-byte loads when every row start is aligned
-    const int64_t i = (int64_t)local * kRowsPerScaleItem + warp;
-    if (i >= pr.n) return;
-    const float *row = pr.A + i * pr.m;
-    uint32_t mx = 0;
-    if (aligned16(pr.A) && (pr.m & 3) == 0) {
-      const float4 *r4 = reinterpret_cast<const float4 *>(row);
-      const int64_t m4 = pr.m >> 2;
-#pragma unroll 4
-      for (int64_t k = lane; k < m4; k += 32) {
-        const float4 v = r4[k];
-        mx = umax(mx, umax(umax(abs_bits(v.x), abs_bits(v.y)), umax(abs_bits(v.z), abs_bits(v.w))));
-      }
-    } else {
-#pragma unroll 4
-      for (int64_t k = lane; k < pr.m; k += 32) mx = umax(mx, abs_bits(row[k]));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = umax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) pr.sA[i] = mx;
-  } else {
-    // a strip of 32 columns x 256 rows of B; the block's maxima are merged
-    // into the column words with atomicMax
-    __shared__ uint32_t part[32][kColStrip + 1];
-    const int b = local - pr.red_a;
-    const int strips = (pr.p + kColStrip - 1) / kColStrip;
-    const int strip = b % strips, chunk = b / strips;
-    const int64_t c0 = (int64_t)strip * kColStrip;
-    const int64_t r0 = (int64_t)chunk * kRowChunk;
-    const int tid = threadIdx.x;
-    if (aligned16(pr.B) && (pr.p & 3) == 0 && c0 + kColStrip <= pr.p) {
-      // 8 threads x 4 columns cover a 128-byte row segment; 32 row groups
-      const int cq = tid & 7, grp = tid >> 3;
-      uint32_t m0 = 0, m1 = 0, m2 = 0, m3 = 0;
-#pragma unroll 4
-      for (int r = grp; r < kRowChunk; r += 32) {
-        const int64_t k = r0 + r;
-        if (k < pr.m) {
-          const float4 v = *reinterpret_cast<const float4 *>(pr.B + k * pr.p + c0 + 4 * cq);
-          m0 = umax(m0, abs_bits(v.x));
-          m1 = umax(m1, abs_bits(v.y));
-          m2 = umax(m2, abs_bits(v.z));
-          m3 = umax(m3, abs_bits(v.w));
-        }
-      }
-      part[grp][4 * cq + 0] = m0;
-      part[grp][4 * cq + 1] = m1;
-      part[grp][4 * cq + 2] = m2;
-      part[grp][4 * cq + 3] = m3;
-      __syncthreads();
-      if (warp == 0) {
-        uint32_t mx = 0;
-#pragma unroll 8
-        for (int w = 0; w < 32; w++) mx = umax(mx, part[w][lane]);
-        atomicMax(&pr.tB[c0 + lane], mx);
-      }
-    } else {
-      const int64_t col = c0 + lane;
-      uint32_t mx = 0;
-      if (col < pr.p) {
-#pragma unroll 8
-        for (int r = warp; r < kRowChunk; r += 8) {
-          const int64_t k = r0 + r;
-          if (k < pr.m) mx = umax(mx, abs_bits(pr.B[k * pr.p + col]));
-        }
-      }
-      part[warp][lane] = mx;
-      __syncthreads();
-      if (warp == 0) {
-#pragma unroll
-        for (int w = 1; w < 8; w++) mx = umax(mx, part[w][lane]);
-        if (col < pr.p) atomicMax(&pr.tB[col], mx);
-      }
-    }
-  }
 }
 
 // Splits four values scaled by 2^-s (SCALED; unscaled: s = 0, no multiply)
@@ -420,19 +325,14 @@ split_verify_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *
 // tiles, pack tiles and scale-reduction items.
 __global__ void __launch_bounds__(256)
 split_maps_kernel(const SplitProb *__restrict__ probs, int *__restrict__ unit_map,
-                  int *__restrict__ pack_map, int *__restrict__ red_map,
-                  int *__restrict__ ver_map) {
+                  int *__restrict__ pack_map, int *__restrict__ ver_map) {
   const int g = blockIdx.x;
   const SplitProb &pr = probs[g];
   const int units = (int)split_units(pr);
   const int packs = pr.mt * pr.kt + pr.nt * pr.kt;
-  const int reds = pr.red_a + ((pr.p + kColStrip - 1) / kColStrip) *
-                                  ((pr.m + kRowChunk - 1) / kRowChunk);
   for (int i = threadIdx.x; i < units; i += blockDim.x) unit_map[pr.unit_start + i] = g;
   for (int i = threadIdx.x; i < packs; i += blockDim.x) pack_map[pr.pack_start + i] = g;
-  if (red_map)  // only tables that run split_scale_kernel (the e4m3 path)
-    for (int i = threadIdx.x; i < reds; i += blockDim.x) red_map[pr.red_start + i] = g;
-  if (ver_map) {  // only tables that run split_verify_kernel (the split kinds)
+  if (ver_map) {  // only tables that run split_verify_kernel
     const int vers = (int)verify_items(pr.n, pr.p);
     for (int i = threadIdx.x; i < vers; i += blockDim.x) ver_map[pr.ver_start + i] = g;
   }
@@ -441,18 +341,10 @@ split_maps_kernel(const SplitProb *__restrict__ probs, int *__restrict__ unit_ma
 }  // namespace
 
 cudaError_t launch_split_maps(const SplitProb *d_probs, int nprobs, int *unit_map, int *pack_map,
-                              int *red_map, int *ver_map, cudaStream_t s) {
+                              int *ver_map, cudaStream_t s) {
   if (nprobs <= 0) return cudaSuccess;
   TraceScope ts("split_maps", s);
-  split_maps_kernel<<<nprobs, 256, 0, s>>>(d_probs, unit_map, pack_map, red_map, ver_map);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_split_scale(const SplitProb *d_probs, int nprobs, int total_items,
-                               const int *map, cudaStream_t s) {
-  if (total_items <= 0) return cudaSuccess;
-  TraceScope ts("split_scale", s);
-  split_scale_kernel<<<total_items, 256, 0, s>>>(d_probs, nprobs, map);
+  split_maps_kernel<<<nprobs, 256, 0, s>>>(d_probs, unit_map, pack_map, ver_map);
   return cudaGetLastError();
 }
 

@@ -6,11 +6,11 @@
 //     C_ij ~= 2^(s_i + t_j) * sum_r (Ah Bh + Ah Bl + Al Bh)_irj
 // accumulated in FP32 in tensor memory; the lo.lo product (below 2^-16
 // relative) is dropped.
-// E4M3 kind: one e4m3 x e4m3 product per K step of the packs written by
-// fp8.cu, with the power-of-two row/column scales of that path, or of the
-// digit packs of the FP64 emulation (ozaki.cu), whose level products read
-// windows of a longer pack through a per-problem K stride (a_kstride,
-// b_kstride) and keep their integer sums exact in FP32.
+// E4M3 kind: one e4m3 x e4m3 product per K step of the digit packs of the
+// FP64 emulation (ozaki.cu), whose level products read windows of a longer
+// pack through a per-problem K stride (a_kstride, b_kstride) and keep their
+// integer sums exact in FP32.  (The FP32 FP8 mode has its own kernel with
+// per-block scales, fp8_blk.cu.)
 // The definition of the product is the paper's (Section "Implementacje
 // algorytmow", Cauchy product); the split-precision method, the FP8 variant
 // and everything below are this library's GB300 design, not the paper's (its

@@ -1,6 +1,7 @@
-// Host side of the tensor-core paths (split-BF16x3 / x6 and e4m3): builds the
-// problem tables, lays out the scratch (pack rows, scale words, tables) and
-// queues prep + tensor-core kernels, one launch per kernel and kind.
+// Host side of the packed split path (split-BF16x3 / x6): builds the problem
+// tables, lays out the scratch (pack rows, scale words, tables) and queues
+// prep + tensor-core kernels, one launch per kernel and kind; and the fused
+// split-K path's plan and launch.
 #include <cmath>
 #include <cstring>
 
@@ -19,8 +20,8 @@ struct Group {
   TcKind kind;
   TcConfig cfg{0, 0, 0};
   std::vector<SplitProb> tab;
-  int64_t units = 0, packs = 0, reds = 0;  // tensor-core work units, pack tiles, reductions
-  int64_t vers = 0;                         // verify items (split kinds)
+  int64_t units = 0, packs = 0;  // tensor-core work units, pack tiles
+  int64_t vers = 0;               // verify items
   int max_kt = 0;                           // longest K (pack rows) of the table
 };
 
@@ -41,8 +42,8 @@ TcTail plan_tail(SplitProb &sp, TcKind kind, const TcChoice &ch) {
 }
 
 mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s,
-                        const TcChoice *force, bool fp8, bool six) {
-  Group groups[3] = {{kTcSplitBf16x3}, {kTcSplitBf16x6}, {kTcE4m3}};
+                        const TcChoice *force, bool six) {
+  Group groups[2] = {{kTcSplitBf16x3}, {kTcSplitBf16x6}};
   int64_t rows = 0, scal = 0, part = 0;
   size_t tail_parts = 0, tail_cnts = 0;  // partial tiles and counters of tail splits
   for (int g = 0; g < count; g++) {
@@ -53,14 +54,13 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
       if (e != cudaSuccess) return note_cuda(e);
       continue;
     }
-    const TcKind kind = fp8 ? kTcE4m3 : (six ? kTcSplitBf16x6 : split_kind_for(q.m));
-    Group &G = groups[kind == kTcSplitBf16x3 ? 0 : (kind == kTcSplitBf16x6 ? 1 : 2)];
+    const TcKind kind = six ? kTcSplitBf16x6 : split_kind_for(q.m);
+    Group &G = groups[kind == kTcSplitBf16x3 ? 0 : 1];
     TcChoice ch = force ? *force : tune_choose(q.n, q.m, q.p);
     ch.bn = tc_bn(kind, ch.bn);
     if (G.tab.empty()) {
       if (kind == kTcSplitBf16x3) G.cfg = TcConfig{2 * ch.bk, ch.stages, ch.grid};
-      else if (kind == kTcSplitBf16x6) G.cfg = TcConfig{64, 3, ch.grid};
-      else G.cfg = TcConfig{128, 4, ch.grid};
+      else G.cfg = TcConfig{64, 3, ch.grid};
     }
     const int parts = pack_parts(kind);
     SplitProb sp;
@@ -84,15 +84,14 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
     scal += q.n;
     sp.tB = reinterpret_cast<uint32_t *>((uintptr_t)scal);
     scal += q.p;
-    if (kind != kTcE4m3) {  // partial maxima of the unscaled pack
-      sp.pA = reinterpret_cast<uint32_t *>((uintptr_t)part);
-      part += (int64_t)sp.kt * q.n;
-      sp.pB = reinterpret_cast<uint32_t *>((uintptr_t)part);
-      part += (int64_t)sp.kt * q.p;
-      sp.ver_start = (int32_t)G.vers;
-      G.vers += verify_items(q.n, q.p);
-      G.max_kt = std::max(G.max_kt, sp.kt);
-    }
+    // partial maxima of the unscaled pack
+    sp.pA = reinterpret_cast<uint32_t *>((uintptr_t)part);
+    part += (int64_t)sp.kt * q.n;
+    sp.pB = reinterpret_cast<uint32_t *>((uintptr_t)part);
+    part += (int64_t)sp.kt * q.p;
+    sp.ver_start = (int32_t)G.vers;
+    G.vers += verify_items(q.n, q.p);
+    G.max_kt = std::max(G.max_kt, sp.kt);
     const TcTail tail = plan_tail(sp, kind, ch);
     if (tail.split_s > 1) {  // offsets, fixed below
       sp.part = reinterpret_cast<float *>((uintptr_t)tail_parts);
@@ -105,17 +104,11 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
     G.cfg.max_bn = G.tab.empty() ? sp.bn : std::max(G.cfg.max_bn, sp.bn);
     sp.pack_start = (int32_t)G.packs;
     G.packs += (int64_t)sp.mt * sp.kt + (int64_t)sp.nt * sp.kt;
-    if (kind == kTcE4m3) {  // the e4m3 path reduces its maxima in a separate pass
-      sp.red_start = (int32_t)G.reds;
-      sp.red_a = (int32_t)ceil_div(q.n, 8);
-      G.reds += sp.red_a + ceil_div(q.p, 32) * ceil_div(q.m, 256);
-    }
     G.tab.push_back(sp);
   }
   size_t ntab = 0;
   for (auto &G : groups) {
-    if (G.units > 0x7fffffffLL || G.packs > 0x7fffffffLL || G.reds > 0x7fffffffLL ||
-        G.vers > 0x7fffffffLL)
+    if (G.units > 0x7fffffffLL || G.packs > 0x7fffffffLL || G.vers > 0x7fffffffLL)
       return MM_EINVAL;
     ntab += G.tab.size();
   }
@@ -131,11 +124,11 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
   const size_t zero_end = tcnt_off + tail_cnts * sizeof(int);
   const size_t part_off = (zero_end + 255) & ~(size_t)255;
   const size_t tab_off = (part_off + (size_t)part * 4 + 255) & ~(size_t)255;
-  // item -> problem maps (work units, pack tiles, reduction and verify items)
-  // of each group with more than one problem
+  // item -> problem maps (work units, pack tiles and verify items) of each
+  // group with more than one problem
   size_t map_ints = 0;
   for (auto &G : groups)
-    if (G.tab.size() > 1) map_ints += (size_t)(G.units + G.packs + G.reds + G.vers);
+    if (G.tab.size() > 1) map_ints += (size_t)(G.units + G.packs + G.vers);
   const size_t map_off = (tab_off + ntab * sizeof(SplitProb) + 255) & ~(size_t)255;
   const size_t tpart_off = (map_off + map_ints * sizeof(int) + 255) & ~(size_t)255;
   const size_t need = tpart_off + tail_parts;
@@ -148,10 +141,8 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
     for (auto &sp : G.tab) {
       sp.sA = reinterpret_cast<uint32_t *>(base + scal_off) + (uintptr_t)sp.sA;
       sp.tB = reinterpret_cast<uint32_t *>(base + scal_off) + (uintptr_t)sp.tB;
-      if (G.kind != kTcE4m3) {
-        sp.pA = reinterpret_cast<uint32_t *>(base + part_off) + (uintptr_t)sp.pA;
-        sp.pB = reinterpret_cast<uint32_t *>(base + part_off) + (uintptr_t)sp.pB;
-      }
+      sp.pA = reinterpret_cast<uint32_t *>(base + part_off) + (uintptr_t)sp.pA;
+      sp.pB = reinterpret_cast<uint32_t *>(base + part_off) + (uintptr_t)sp.pB;
       if (sp.split_s > 1) {
         sp.part = reinterpret_cast<float *>(base + tpart_off + (uintptr_t)sp.part);
         sp.cnt = reinterpret_cast<int *>(base + tcnt_off) + (uintptr_t)sp.cnt;
@@ -166,7 +157,7 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
   size_t off = 0;
   int *flags_all = reinterpret_cast<int *>(base + flag_off);
   int *maps = reinterpret_cast<int *>(base + map_off);
-  for (int gi = 0; gi < 3; gi++) {
+  for (int gi = 0; gi < 2; gi++) {
     Group &G = groups[gi];
     if (G.tab.empty()) continue;
     const SplitProb *dt = d_tab + off;
@@ -174,37 +165,25 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
     int *any = flags_all + ntab + gi;
     const int np = (int)G.tab.size();
     off += G.tab.size();
-    int *tile_map = nullptr, *pack_map = nullptr, *red_map = nullptr, *ver_map = nullptr;
+    int *tile_map = nullptr, *pack_map = nullptr, *ver_map = nullptr;
     if (np > 1) {
       tile_map = maps;
       pack_map = tile_map + G.units;
-      red_map = G.reds > 0 ? pack_map + G.packs : nullptr;
-      ver_map = G.vers > 0 ? pack_map + G.packs + G.reds : nullptr;
-      maps = pack_map + G.packs + G.reds + G.vers;
-      e = launch_split_maps(dt, np, tile_map, pack_map, red_map, ver_map, s);
+      ver_map = pack_map + G.packs;
+      maps = ver_map + G.vers;
+      e = launch_split_maps(dt, np, tile_map, pack_map, ver_map, s);
       if (e != cudaSuccess) return note_cuda(e);
     }
-    if (G.kind == kTcE4m3) {
-      // e4m3 needs its scales before the conversion: reduce, then pack
-      e = launch_split_scale(dt, np, (int)G.reds, red_map, s);
-      if (e == cudaSuccess) e = launch_fp8_pack(dt, np, (int)G.packs, pack_map, base, s);
-      if (e == cudaSuccess)
-        e = launch_tc(G.kind, dt, np, (int)G.units, tile_map, nullptr, base, rows, G.cfg,
-                      g_ctx.d_err, s);
-    } else {
-      // split: one unscaled pass that also reduces the maxima, then the
-      // operands out of range are re-packed with their scales
-      e = launch_split_pack(G.kind, kPackUnscaled, dt, np, (int)G.packs, pack_map, nullptr,
-                            nullptr, base, s);
-      if (e == cudaSuccess)
-        e = launch_split_verify(dt, np, G.vers, ver_map, flags, any, G.max_kt, s);
-      if (e == cudaSuccess)
-        e = launch_split_pack(G.kind, kPackFix, dt, np, (int)G.packs, pack_map, flags, any, base,
-                              s);
-      if (e == cudaSuccess)
-        e = launch_tc(G.kind, dt, np, (int)G.units, tile_map, flags, base, rows, G.cfg,
-                      g_ctx.d_err, s);
-    }
+    // one unscaled pass that also reduces the maxima, then the operands out
+    // of range are re-packed with their scales
+    e = launch_split_pack(G.kind, kPackUnscaled, dt, np, (int)G.packs, pack_map, nullptr, nullptr,
+                          base, s);
+    if (e == cudaSuccess) e = launch_split_verify(dt, np, G.vers, ver_map, flags, any, G.max_kt, s);
+    if (e == cudaSuccess)
+      e = launch_split_pack(G.kind, kPackFix, dt, np, (int)G.packs, pack_map, flags, any, base, s);
+    if (e == cudaSuccess)
+      e = launch_tc(G.kind, dt, np, (int)G.units, tile_map, flags, base, rows, G.cfg, g_ctx.d_err,
+                    s);
     if (e != cudaSuccess) return note_cuda(e);
   }
   return MM_OK;
@@ -251,7 +230,6 @@ mm_status run_split_chunked(Scratch &ws, int64_t n, int64_t m, int64_t p, const 
     // partial maxima: B's columns first (kt * p), then each slab's rows
     sp.pA = reinterpret_cast<uint32_t *>((uintptr_t)((int64_t)kt * p + (int64_t)kt * r0));
     sp.pB = reinterpret_cast<uint32_t *>((uintptr_t)0);
-    sp.red_a = (int32_t)ceil_div(r1 - r0, 8);
     // slabs are not tail-split: each slab's last wave is filled by the next
     // slab's GEMM on the other tensor-core stream
     sp.split_s = 1;
@@ -319,11 +297,11 @@ mm_status run_split_chunked(Scratch &ws, int64_t n, int64_t m, int64_t p, const 
 
 mm_status run_split(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s,
                     const TcChoice *force, bool six) {
-  return run_tc_groups(ws, probs, count, s, force, false, six);
+  return run_tc_groups(ws, probs, count, s, force, six);
 }
 
 mm_status run_fp8(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s) {
-  return run_tc_groups(ws, probs, count, s, nullptr, true, false);
+  return run_fp8_blocks(ws, probs, count, s);
 }
 
 }  // namespace mm

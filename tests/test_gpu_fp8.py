@@ -60,3 +60,53 @@ def test_fp8_grouped(mmlib):
     for (n, m, p, _, _, C, A, B) in probs:
         exact = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float32)
         assert np.array_equal(C.cpu().numpy(), exact)
+
+
+def test_fp8_block_scales_keep_small_blocks(mmlib):
+    """Scales per 128-value K block: a row whose first block holds values near
+    2^30 and whose other blocks hold values near 1 keeps the small blocks'
+    significance (one scale per row would push them below the e4m3 range and
+    lose them).  Here the small blocks carry most of |A||B| for the columns of
+    B that are zero on the first block, so one scale per row would give an
+    error near 1 there; per block it is that of 4-bit operands."""
+    n, m, p = 130, 640, 70
+    A = synth.uniform_pm1(831, (n, m)).astype(np.float64)
+    A[:, :128] *= 2.0 ** 30
+    B = synth.uniform_pm1(832, (m, p)).astype(np.float64)
+    B[:128, : p // 2] = 0.0  # half of the columns never meet the large block
+    A = A.astype(np.float32)
+    B = B.astype(np.float32)
+    C = run_gemm(mmlib, A, B, mmlib.MM_MODE_FP8)
+    ref, absref = oracle.default().gemm(A, B, with_abs=True)
+    e = oracle.rel_errors(C, ref, absref)
+    assert np.isfinite(C).all()
+    assert e.max() < 0.05, e.max()
+    assert e[:, : p // 2].max() < 0.05
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (5, 129, 3), (257, 300, 130), (128, 128, 128)])
+def test_fp8_ragged_shapes(mmlib, shape):
+    """Edges of the 128 x 128 tiles and of the 128-value K blocks (zero
+    padding), against the oracle within the e4m3 sanity bound."""
+    n, m, p = shape
+    A = synth.uniform_pm1(841, (n, m))
+    B = synth.uniform_pm1(842, (m, p))
+    C = run_gemm(mmlib, A, B, mmlib.MM_MODE_FP8)
+    ref, absref = oracle.default().gemm(A, B, with_abs=True)
+    assert oracle.rel_errors(C, ref, absref).max() < 0.05
+
+
+def test_fp8_grouped_equals_single(mmlib):
+    """A grouped call runs the same kernels with the same per-block scales:
+    each product's bits equal its single call."""
+    probs, host = [], []
+    for g, (n, m, p) in enumerate([(100, 300, 96), (260, 1000, 140), (7, 129, 500)]):
+        A = synth.uniform_pm1(850 + 2 * g, (n, m))
+        B = synth.uniform_pm1(851 + 2 * g, (m, p))
+        probs.append((n, m, p, dev(A), dev(B), torch.full((n, p), float("nan"), device="cuda")))
+        host.append((A, B))
+    assert mmlib.mm_gemm_grouped(probs, mmlib.MM_F32, mmlib.MM_MODE_FP8) == 0
+    for (n, m, p, dA, dB, C), (A, B) in zip(probs, host):
+        C1 = torch.full_like(C, float("nan"))
+        assert mmlib.mm_gemm(n, m, p, dA, dB, C1, mmlib.MM_F32, mmlib.MM_MODE_FP8) == 0
+        assert torch.equal(C, C1), (n, m, p)
