@@ -173,6 +173,26 @@ mm_status mm_gemm(int64_t n, int64_t m, int64_t p, const void *A, const void *B,
  * (m above about 5.4 million at S = 14) returns MM_EINVAL. */
 mm_status mm_ozaki_slices(int slices);
 
+/* Accuracy gate of MM_MODE_OZAKI products queued after the call (serving
+ * requests keep the setting current at mm_submit); on (1) by default.  With
+ * the gate, each product also computes P = (|A| 2^-sigma).(|B| 2^-tau) in FP32
+ * on the split path (a lower bound of sum_r |a_ir||b_rj| 2^-(sigma_i + tau_j)
+ * after a 2^-10 margin) and checks every entry against the method's bound:
+ * entry (i, j) of the emulation is off by at most m (S + 2) 2^(sigma_i + tau_j
+ * - 4S), so it meets 1e-14 sqrt(m) of (|A||B|)_ij wherever P_ij >= sqrt(m)
+ * (S + 2) 2^-4S 1e14 / (0.98 - m 2^-23) (room for the FP32 rounding of P and
+ * the final rounding; every product falls back where m 2^-23 > 0.48).
+ * If any entry with finite row and column misses it (a row whose largest
+ * entry dwarfs the ones that meet a column, e.g. magnitudes spread over many
+ * binades), the FP64 FMA product (MM_MODE_DGEMM's kernel) recomputes all of C
+ * on the device, so the result meets the FP64 tolerance for any finite input;
+ * the decision is data-dependent and made on the device (no host round
+ * trip).  Off (0): the emulation's result is returned as it is (bit for bit
+ * the method of mm_ozaki_slices).  When it passes, a 4096^3 product at
+ * S = 14 takes about 15% longer with the gate (5.1 ms without, 5.9 ms
+ * with).  Returns MM_EINVAL for other values, MM_ENOTINIT before mm_init. */
+mm_status mm_ozaki_gate(int on);
+
 /* Plan of an MM_MODE_OZAKI product, a pure host function (no device, no
  * mm_init): for A n x m, B m x p and `slices` digit slices, writes the K
  * columns per chunk (the largest multiple of 128 with

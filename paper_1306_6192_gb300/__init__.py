@@ -102,6 +102,8 @@ def lib():
         L.mm_measure_fma_peak.argtypes = [st, _i64, _dp]
         L.mm_measure_fma_peak.restype = ctypes.c_int
         L.mm_ozaki_slices.argtypes = [ctypes.c_int]
+        L.mm_ozaki_gate.argtypes = [ctypes.c_int]
+        L.mm_ozaki_gate.restype = ctypes.c_int
         L.mm_ozaki_slices.restype = ctypes.c_int
         L.mm_ozaki_plan.argtypes = [_i64, _i64, _i64, ctypes.c_int, ctypes.POINTER(_i64),
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)]
@@ -297,6 +299,11 @@ def mm_tail_plan(tiles, grid, kt, bn, m, products):
 def mm_ozaki_slices(slices: int) -> int:
     """Digit slices S (2..16) of MM_MODE_OZAKI for the products queued next."""
     return lib().mm_ozaki_slices(int(slices))
+
+
+def mm_ozaki_gate(on: int) -> int:
+    """Turns the accuracy gate of MM_MODE_OZAKI products on (1) or off (0)."""
+    return lib().mm_ozaki_gate(on)
 
 
 def mm_ozaki_plan(n, m, p, slices):

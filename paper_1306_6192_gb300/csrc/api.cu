@@ -263,8 +263,8 @@ mm_status enqueue_gemm(int64_t n, int64_t m, int64_t p, const void *A, const voi
       return run_fp8(g_ctx.fp8_ws, &q, 1, s);
     }
     case MM_MODE_OZAKI:
-      return run_ozaki(g_ctx.ozaki_ws, n, m, p, (const double *)A, (const double *)B, (double *)C,
-                       g_ctx.ozaki_slices, s);
+      return run_ozaki(g_ctx.ozaki_ws, g_ctx.split_ws, n, m, p, (const double *)A,
+                       (const double *)B, (double *)C, g_ctx.ozaki_slices, g_ctx.ozaki_gate != 0, s);
     default: return MM_EINVAL;
   }
 }
@@ -394,6 +394,7 @@ mm_status mm_shutdown(void) {
   g_ctx.fused_zero_ptr = nullptr;
   g_ctx.fused_zeroed = 0;
   g_ctx.ozaki_slices = kOzakiDefaultSlices;
+  g_ctx.ozaki_gate = 1;
   if (g_ctx.d_err) cudaFree(g_ctx.d_err);
   g_ctx.d_err = nullptr;
   trace_destroy();
@@ -419,6 +420,14 @@ mm_status mm_ozaki_slices(int slices) {
   if (!g_ctx.inited) return MM_ENOTINIT;
   if (slices < kOzakiMinSlices || slices > kOzakiMaxSlices) return MM_EINVAL;
   g_ctx.ozaki_slices = slices;
+  return MM_OK;
+}
+
+mm_status mm_ozaki_gate(int on) {
+  std::lock_guard<std::mutex> lk(g_api_mutex);
+  if (!g_ctx.inited) return MM_ENOTINIT;
+  if (on != 0 && on != 1) return MM_EINVAL;
+  g_ctx.ozaki_gate = on;
   return MM_OK;
 }
 

@@ -64,6 +64,7 @@ struct Ctx {
   void *fused_zero_ptr = nullptr;  // fused_ws buffer whose leading counters are zero
   size_t fused_zeroed = 0;         //   and how many bytes of them
   int ozaki_slices = kOzakiDefaultSlices;  // digit slices S of MM_MODE_OZAKI
+  int ozaki_gate = 1;                      // accuracy gate of MM_MODE_OZAKI on
   // host-operand pipeline of mm_gemm: copy streams and per-chunk events
   cudaStream_t h2d = nullptr, d2h = nullptr;
   cudaStream_t tc_streams[2] = {};  // slab GEMMs alternate between these
@@ -139,8 +140,12 @@ size_t fp8_blocks_scratch_bytes(int64_t n, int64_t m, int64_t p);
 // slices (ozaki.cu); ozaki_chunk(S) = the K columns per chunk that keep every
 // level sum exact in FP32; ozaki_scratch_bytes = an upper bound of the
 // scratch one product needs.
-mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *A,
-                    const double *B, double *C, int S, cudaStream_t s);
+// gate: check every entry against the method's error bound and recompute C
+// with the FP64 FMA product where any entry could miss 1e-14 sqrt(m); its FP32
+// product of the scaled magnitudes runs on the split path in gate_ws.
+mm_status run_ozaki(Scratch &ws, Scratch &gate_ws, int64_t n, int64_t m, int64_t p,
+                    const double *A, const double *B, double *C, int S, bool gate,
+                    cudaStream_t s);
 int64_t ozaki_chunk(int S);
 size_t ozaki_scratch_bytes(int64_t n, int64_t m, int64_t p, int S);
 // Grouped dispatch: split / SIMT / DGEMM tables in one launch per path.

@@ -118,8 +118,11 @@ struct SimtProb {
 // ------------------------------------------------------------ launchers
 cudaError_t launch_simt_f32(int64_t n, int64_t m, int64_t p, const float *A,
                             const float *B, float *C, cudaStream_t s);
+// run_if: a device word; when given, the product runs only if it is non-zero
+// when the kernel starts (the FP64 emulation's fallback).
 cudaError_t launch_simt_f64(int64_t n, int64_t m, int64_t p, const double *A,
-                            const double *B, double *C, cudaStream_t s);
+                            const double *B, double *C, cudaStream_t s,
+                            const int *run_if = nullptr);
 cudaError_t launch_simt_grouped(bool f64, const SimtProb *d_probs, int nprobs,
                                 int total_tiles, bool all_vec, cudaStream_t s);
 

@@ -33,7 +33,10 @@
 // plus the final rounding (half an ulp of c^_ij).  Relative to (|A||B|)_ij this is
 // data dependent: ~4 (S + 2) 2^(-4S) for rows and columns without a wide
 // spread of magnitudes (uniform data), much more where a row's largest entry
-// dwarfs the entries that meet the column's mass.
+// dwarfs the entries that meet the column's mass.  The accuracy gate (on by
+// default) bounds P_ij = (|A||B|)_ij 2^-(sigma_i + tau_j) from below with an
+// FP32 product on the split path and, where any entry's bound could exceed
+// 1e-14 sqrt(m) (|A||B|)_ij, recomputes C with the FP64 FMA kernel.
 //
 // Data layout in the library's scratch ("pack region" first, 128-byte rows,
 // as the tensor-core kernel's tensor map requires):
@@ -333,13 +336,65 @@ ozaki_sum_kernel(const float *__restrict__ D, int64_t plane, int64_t n, int64_t 
   }
 }
 
+// Accuracy gate.  Every term a_ir b_rj of the emulated product is off by at
+// most (S + 2) 2^(sigma_i + tau_j - 4S), so entry (i, j) is off by at most
+// m (S + 2) 2^(sigma_i + tau_j - 4S); the product meets e_ij <= 1e-14 sqrt(m)
+// wherever P_ij = sum_r |a_ir| 2^-sigma_i |b_rj| 2^-tau_j is at least
+// sqrt(m) (S + 2) 2^-4S 1e14.  P is computed in FP32 on the split path from
+// |A| 2^-sigma and |B| 2^-tau: entries in [0, 1), so no cancellation.  Each
+// term is off by a few 2^-16 relative (the kernel lowers P by 2^-10) and the
+// FP32 accumulation by at most m 2^-23 relative (the host divides the
+// threshold by 0.98 - m 2^-23; the 2% also covers the final rounding to a
+// double, 2^-53 relative, below 1.2% of 1e-14).  Where m 2^-23 reaches 1/2
+// the threshold is infinite and every product falls back.  Entries whose
+// FP32 copies underflow only lower P (a fallback, never a miss).  An entry
+// that misses the bound sets a flag; the FP64 FMA product then recomputes C.
+__global__ void __launch_bounds__(256)
+ozaki_gate_abs_kernel(const double *__restrict__ X, int64_t rows, int64_t cols,
+                      const uint64_t *__restrict__ rmax, const unsigned long long *__restrict__ cmax,
+                      float *__restrict__ out) {
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+    const double *src = X + r * cols;
+    float *dst = out + r * cols;
+    bool frow = true;
+    const int srow = rmax ? slice_exponent(rmax[r], frow) : 0;
+    for (int64_t c = threadIdx.x; c < cols; c += blockDim.x) {
+      bool f = frow;
+      const int sc = cmax ? slice_exponent(cmax[c], f) : srow;
+      dst[c] = f ? (float)ldexp(fabs(src[c]), -sc) : 0.0f;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256)
+ozaki_gate_check_kernel(const float *__restrict__ P, int64_t n, int64_t p,
+                        const uint64_t *__restrict__ rowmax,
+                        const unsigned long long *__restrict__ colmax, float thr, int *flag) {
+  bool fail = false;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    bool fi;
+    slice_exponent(rowmax[i], fi);
+    if (!fi) continue;  // a row with a NaN or an infinity gives NaN by design
+    for (int64_t j = threadIdx.x; j < p; j += blockDim.x) {
+      bool fj;
+      slice_exponent(colmax[j], fj);
+      if (!fj) continue;
+      const float v = P[i * p + j];
+      // all-zero rows or columns give exact zeros; any other entry must meet
+      // the bound (P == 0 there may be an underflow of the FP32 copy)
+      if (rowmax[i] != 0 && colmax[j] != 0 && !(v * (1.0f - 0x1p-10f) >= thr)) fail = true;
+    }
+  }
+  if (__syncthreads_or(fail) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
 // Scratch offsets of one call.
 struct OzLayout {
   int S, chunks, bn, mt, nt;
   int64_t mc;
   std::vector<int64_t> k0, kc, kt, a0, b0;
   int64_t rows = 0, plane = 0;
-  size_t max_off, zero_off, zero_end, d_off, tab_off, map_off, need;
+  size_t max_off, zero_off, zero_end, d_off, tab_off, map_off, gate_off, need;
   int64_t units = 0;
 };
 
@@ -350,8 +405,9 @@ int64_t ozaki_chunk(int S) {
   return mc;
 }
 
-mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *A,
-                    const double *B, double *C, int S, cudaStream_t s) {
+mm_status run_ozaki(Scratch &ws, Scratch &gate_ws, int64_t n, int64_t m, int64_t p,
+                    const double *A, const double *B, double *C, int S, bool gate,
+                    cudaStream_t s) {
   if (S < kOzakiMinSlices || S > kOzakiMaxSlices) return MM_EINVAL;
   if (n == 0 || p == 0) return MM_OK;
   if (m == 0) return note_cuda(cudaMemsetAsync(C, 0, (size_t)(n * p) * sizeof(double), s));
@@ -419,7 +475,9 @@ mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *
   lay.d_off = (lay.zero_end + 255) & ~(size_t)255;
   lay.tab_off = (lay.d_off + (size_t)nprobs * lay.plane * sizeof(float) + 255) & ~(size_t)255;
   lay.map_off = (lay.tab_off + (size_t)nprobs * sizeof(SplitProb) + 255) & ~(size_t)255;
-  lay.need = lay.map_off + (size_t)lay.units * sizeof(int);
+  // gate: |A| 2^-sigma, |B| 2^-tau, P (FP32) and the fallback flag
+  lay.gate_off = (lay.map_off + (size_t)lay.units * sizeof(int) + 255) & ~(size_t)255;
+  lay.need = lay.gate_off + (size_t)(n * m + m * p + n * p) * sizeof(float) + 256;
   cudaError_t e = ws.reserve(lay.need, s);
   if (e != cudaSuccess) return note_cuda(e);
   uint8_t *base = static_cast<uint8_t *>(ws.ptr);
@@ -478,7 +536,33 @@ mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *
                                                                        lay.chunks, rowmax, colmax, C);
     if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
   }
-  return MM_OK;
+  if (!gate) return MM_OK;
+  float *ah = reinterpret_cast<float *>(base + lay.gate_off);
+  float *bh = ah + n * m;
+  float *P = bh + m * p;
+  int *flag = reinterpret_cast<int *>(P + n * p);
+  {
+    TraceScope ts("ozaki_gate", s);
+    if ((e = cudaMemsetAsync(flag, 0, sizeof(int), s)) != cudaSuccess) return note_cuda(e);
+    const unsigned ga = (unsigned)std::min<int64_t>(n, 65535), gb = (unsigned)std::min<int64_t>(m, 65535);
+    ozaki_gate_abs_kernel<<<ga, 256, 0, s>>>(A, n, m, rowmax, nullptr, ah);
+    ozaki_gate_abs_kernel<<<gb, 256, 0, s>>>(B, m, p, nullptr, colmax, bh);
+    if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
+  }
+  const mm_problem q{n, m, p, ah, bh, P};
+  mm_status st = run_split(gate_ws, &q, 1, s, nullptr);
+  if (st != MM_OK) return st;
+  {
+    TraceScope ts("ozaki_gate", s);
+    const double room = 0.98 - (double)m * 0x1p-23;
+    const double thr = room < 0.5 ? (double)INFINITY
+                                  : std::sqrt((double)m) * (S + 2) * std::ldexp(1.0, -4 * S) * 1e14 / room;
+    const unsigned gc = (unsigned)std::min<int64_t>(n, (int64_t)sm_count() * 8);
+    ozaki_gate_check_kernel<<<gc, 256, 0, s>>>(P, n, p, rowmax, colmax, (float)thr, flag);
+    if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
+  }
+  // the FP64 FMA product replaces C where the flag is set
+  return note_cuda(launch_simt_f64(n, m, p, A, B, C, s, flag));
 }
 
 size_t ozaki_scratch_bytes(int64_t n, int64_t m, int64_t p, int S) {
@@ -487,9 +571,14 @@ size_t ozaki_scratch_bytes(int64_t n, int64_t m, int64_t p, int S) {
   const int64_t chunks = ceil_div(m, mc);
   const int64_t kt_all = ceil_div(m, 128) + chunks;  // K blocks over all chunks (bound)
   const int64_t rows = (ceil_div(n, kTcBM) * kTcBM + ceil_div(p, 128) * 256) * S * kt_all;
+  // digit packs, level sums, maxima, table and map; the accuracy gate's FP32
+  // copies and product, and the split packs of that product (bf16 hi/lo)
+  const size_t gate = (size_t)(n * m + m * p + n * p) * sizeof(float) +
+                      (size_t)(ceil_div(n, kTcBM) * kTcBM + ceil_div(p, 128) * 256) *
+                          ceil_div(m, 64) * kPackRowBytes * 2;
   return (size_t)rows * kPackRowBytes + (size_t)chunks * S * (n * p + 64) * sizeof(float) +
          (size_t)(n + p) * 12 + (size_t)chunks * S * ceil_div(n, kTcBM) * ceil_div(p, 128) * 4 +
-         (size_t)chunks * S * sizeof(SplitProb) + ((size_t)1 << 20);
+         (size_t)chunks * S * sizeof(SplitProb) + gate + ((size_t)1 << 20);
 }
 
 }  // namespace mm

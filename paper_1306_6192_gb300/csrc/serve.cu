@@ -44,6 +44,7 @@ struct Request {
   mm_dtype dt = MM_F32;
   mm_mode mode = MM_MODE_SPLIT_BF16X3;
   int slices = 0;  // MM_MODE_OZAKI: digit slices at submission
+  bool gate = true;  // MM_MODE_OZAKI: accuracy gate at submission
   size_t bytes = 0;    // operands, output and the scratch estimate below
   size_t scratch = 0;  // library scratch the request needs while it runs
   Clock::time_point t_submit;
@@ -217,9 +218,11 @@ mm_status launch_batch(Slot &sl, std::vector<Request *> &reqs) {
     st = MM_OK;
     for (size_t k = 0; k < reqs.size() && st == MM_OK; k++) {
       const mm_problem &q = reqs[k]->pr;
-      st = run_ozaki(sl.split_ws, q.n, q.m, q.p, static_cast<const double *>(q.A),
+      // the slot's table scratch (unused by this batch) holds the gate's
+      // split packs
+      st = run_ozaki(sl.split_ws, sl.tab_ws, q.n, q.m, q.p, static_cast<const double *>(q.A),
                      static_cast<const double *>(q.B), static_cast<double *>(q.C),
-                     reqs[k]->slices, sl.s);
+                     reqs[k]->slices, reqs[k]->gate, sl.s);
     }
   } else
     st = enqueue_grouped(sl.split_ws, sl.tab_ws, (int)probs.size(), probs.data(), dt, mode, sl.s);
@@ -459,6 +462,7 @@ mm_status mm_submit(const mm_problem *pr, mm_dtype dt, mm_mode mode, uint64_t *i
   r->dt = dt;
   r->mode = mode;
   r->slices = g_ctx.ozaki_slices;
+  r->gate = g_ctx.ozaki_gate != 0;
   r->scratch = request_scratch(*pr, mode, r->slices);
   r->bytes = request_operand_bytes(*pr, dt) + r->scratch;
   std::lock_guard<std::mutex> lk(g_srv.mu);

@@ -213,7 +213,9 @@ __device__ __forceinline__ void simt_tile_any(const T *__restrict__ A, const T *
 template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
 __global__ void __launch_bounds__(256, (SimtShape<T, BM, BN, BK, TM, TN>::MIN_BLOCKS))
 simt_gemm_kernel(const T *__restrict__ A, const T *__restrict__ B, T *__restrict__ C,
-                 int64_t n, int64_t m, int64_t p) {
+                 int64_t n, int64_t m, int64_t p, const int *__restrict__ run_if) {
+  // run_if: a device word; when given, the product runs only where it is set
+  if (run_if != nullptr && *reinterpret_cast<const volatile int *>(run_if) == 0) return;
   simt_tile_any<T, BM, BN, BK, TM, TN, VEC>(A, B, C, n, m, p, blockIdx.y, blockIdx.x);
 }
 
@@ -239,7 +241,7 @@ inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 
 
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 cudaError_t launch_simt(int64_t n, int64_t m, int64_t p, const T *A, const T *B, T *C,
-                        cudaStream_t s, const char *name) {
+                        cudaStream_t s, const char *name, const int *run_if = nullptr) {
   constexpr int W = 16 / (int)sizeof(T);
   const int64_t gy = ceil_div(n, BM), gx = ceil_div(p, BN);
   if (gy > 65535 || gx > 2147483647LL) return cudaErrorInvalidValue;
@@ -247,9 +249,9 @@ cudaError_t launch_simt(int64_t n, int64_t m, int64_t p, const T *A, const T *B,
   const bool vec = aligned16(A) && aligned16(B) && aligned16(C) && m % W == 0 && p % W == 0;
   TraceScope ts(name, s);
   if (vec)
-    simt_gemm_kernel<T, BM, BN, BK, TM, TN, true><<<grid, 256, 0, s>>>(A, B, C, n, m, p);
+    simt_gemm_kernel<T, BM, BN, BK, TM, TN, true><<<grid, 256, 0, s>>>(A, B, C, n, m, p, run_if);
   else
-    simt_gemm_kernel<T, BM, BN, BK, TM, TN, false><<<grid, 256, 0, s>>>(A, B, C, n, m, p);
+    simt_gemm_kernel<T, BM, BN, BK, TM, TN, false><<<grid, 256, 0, s>>>(A, B, C, n, m, p, run_if);
   return cudaGetLastError();
 }
 
@@ -262,9 +264,9 @@ cudaError_t launch_simt_f32(int64_t n, int64_t m, int64_t p, const float *A, con
 }
 
 cudaError_t launch_simt_f64(int64_t n, int64_t m, int64_t p, const double *A, const double *B,
-                            double *C, cudaStream_t s) {
+                            double *C, cudaStream_t s, const int *run_if) {
   return launch_simt<double, kSimtF64BM, kSimtF64BN, kSimtF64BK, 4, 4>(n, m, p, A, B, C, s,
-                                                                       "dgemm_f64");
+                                                                       "dgemm_f64", run_if);
 }
 
 cudaError_t launch_simt_grouped(bool f64, const SimtProb *d_probs, int nprobs, int total_tiles,

@@ -1,14 +1,19 @@
 """MM_MODE_OZAKI (FP64 emulated by the Ozaki scheme on the e4m3 tensor cores)
-through the C ABI: equal bit for bit to the Ozaki oracle (oracle/ozaki.py) on
-the same seeded inputs, at sizes that span several tiles, ragged edges and
-several K chunks, for several slice counts; exact on integers; within the FP64
-tolerance of the exact product at 4096^3 (sampled entries against Dot2 plus
-Freivalds); grouped, served and host-operand calls give the same bits as a
-single device call; edge cases and argument checks."""
+through the C ABI: with the accuracy gate off, equal bit for bit to the Ozaki
+oracle (oracle/ozaki.py) on the same seeded inputs, at sizes that span several
+tiles, ragged edges and several K chunks, for several slice counts; exact on
+integers; within the FP64 tolerance of the exact product at 4096^3 (sampled
+entries against Dot2 plus Freivalds); grouped, served and host-operand calls
+give the same bits as a single device call; edge cases and argument checks.
+With the gate on: products the method's error bound clears keep the
+emulation's bits, and products it does not (magnitudes spread over many
+binades, where the emulation itself misses the FP64 tolerance) are the FP64
+FMA product's bits and meet the tolerance."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
 from gpu_util import dev, sampled_check
 from oracle import ozaki
@@ -18,11 +23,15 @@ pytestmark = pytest.mark.gpu
 
 @pytest.fixture
 def mm(mmlib):
+    """The library with the accuracy gate off (the bare method, comparable bit
+    for bit with the oracle); slices and gate restored afterwards."""
+    assert mmlib.mm_ozaki_gate(0) == mmlib.MM_OK
     yield mmlib
     assert mmlib.mm_ozaki_slices(ozaki.DEFAULT_SLICES) == mmlib.MM_OK
+    assert mmlib.mm_ozaki_gate(1) == mmlib.MM_OK
 
 
-def _run(mm, A, B, S=None, host=False):
+def _run(mm, A, B, S=None, host=False, mode=None):
     if S is not None:
         assert mm.mm_ozaki_slices(S) == mm.MM_OK
     n, m = A.shape
@@ -34,7 +43,7 @@ def _run(mm, A, B, S=None, host=False):
     else:
         dA, dB = dev(A, torch.float64), dev(B, torch.float64)
         dC = torch.full((n, p), float("nan"), dtype=torch.float64, device="cuda")
-    st = mm.mm_gemm(n, m, p, dA, dB, dC, mm.MM_F64, mm.MM_MODE_OZAKI)
+    st = mm.mm_gemm(n, m, p, dA, dB, dC, mm.MM_F64, mm.MM_MODE_OZAKI if mode is None else mode)
     assert st == mm.MM_OK, mm.mm_strerror(st)
     return dC.cpu().numpy()
 
@@ -115,6 +124,8 @@ def test_edges(mm):
 def test_arguments(mm):
     assert mm.mm_ozaki_slices(1) == mm.MM_EINVAL
     assert mm.mm_ozaki_slices(17) == mm.MM_EINVAL
+    assert mm.mm_ozaki_gate(2) == mm.MM_EINVAL
+    assert mm.mm_ozaki_gate(-1) == mm.MM_EINVAL
     for S in (2, 16):
         assert mm.mm_ozaki_slices(S) == mm.MM_OK
     a = torch.zeros((8, 8), device="cuda")
@@ -144,6 +155,7 @@ def test_served_requests_match_single_calls(mmlib):
     assert mm.mm_init(device=0) == mm.MM_OK
     try:
         assert mm.mm_ozaki_slices(10) == mm.MM_OK
+        assert mm.mm_ozaki_gate(0) == mm.MM_OK  # re-initialised: the gate is on again
         reqs = []
         for k, (n, m, p) in enumerate([(300, 200, 100), (128, 700, 256), (65, 65, 65)]):
             A = synth.uniform_pm1_f64(4600 + k, (n, m))
@@ -160,3 +172,54 @@ def test_served_requests_match_single_calls(mmlib):
     finally:
         mm.mm_shutdown()
         assert mm.mm_init(device=0) == mm.MM_OK
+
+
+def _exact(A, B):
+    """Every entry of A.B by Dot2 (the oracle's compensated dot product) and
+    the |A||B| normaliser."""
+    n, p = A.shape[0], B.shape[1]
+    I, J = np.meshgrid(np.arange(n), np.arange(p), indexing="ij")
+    hi, lo, ab = oracle.default().entries(A, B, I.ravel(), J.ravel(), "dot2")
+    return (hi + lo).reshape(n, p), ab.reshape(n, p)
+
+
+def test_gate_keeps_emulation_where_the_bound_holds(mmlib):
+    """Uniform entries: at S = 14 the bound clears every entry, so the gated
+    product is the emulation's, bit for bit; at S = 8 it clears none at
+    m = 1000 (the bound needs m of about 860,000 there), so the gated product
+    is the FP64 FMA product's."""
+    mm = mmlib
+    assert mm.mm_ozaki_gate(1) == mm.MM_OK
+    try:
+        A = synth.uniform_pm1_f64(7100, (257, 1000))
+        B = synth.uniform_pm1_f64(7101, (1000, 300))
+        _same(_run(mm, A, B, 14), ozaki.gemm(A, B, 14))
+        _same(_run(mm, A, B, 8), _run(mm, A, B, mode=mm.MM_MODE_DGEMM))
+    finally:
+        assert mm.mm_ozaki_slices(ozaki.DEFAULT_SLICES) == mm.MM_OK
+
+
+def test_gate_falls_back_where_the_emulation_misses(mmlib):
+    """Entries spread over 2^-40 .. 2^40: the oracle's emulation at S = 14
+    misses the FP64 tolerance on a share of the entries; the gated product is
+    the FP64 FMA product, bit for bit, and meets the tolerance everywhere,
+    including a row of NaN (NaN by design) and an all-zero row (zeros)."""
+    mm = mmlib
+    assert mm.mm_ozaki_gate(1) == mm.MM_OK
+    try:
+        A = _wide(7000, (129, 300))
+        B = _wide(7002, (300, 70))
+        A[4, :] = 0.0
+        A[9, 17] = np.nan
+        exact, ab = _exact(A, B)
+        tol = oracle.tolerance(300, "f64")
+        fin = np.isfinite(exact)
+        emul = oracle.rel_errors(ozaki.gemm(A, B, 14)[fin], exact[fin], ab[fin])
+        assert emul.max() > tol  # the bare method is not enough here
+        C = _run(mm, A, B, 14)
+        _same(C, _run(mm, A, B, mode=mm.MM_MODE_DGEMM))
+        e = oracle.rel_errors(C[fin], exact[fin], ab[fin])
+        assert e.max() <= tol, "max e %g > %g" % (e.max(), tol)
+        assert np.all(np.isnan(C[9])) and np.all(C[4] == 0)
+    finally:
+        assert mm.mm_ozaki_slices(ozaki.DEFAULT_SLICES) == mm.MM_OK

@@ -2,7 +2,7 @@
 (mm_ozaki_plan, no GPU): its K chunk rule must be the one the oracle restates
 independently (oracle/ozaki.py), its chunk count ceil(m / columns), its
 argument checks as documented, and its scratch bound must cover the digit
-packs and level sums the method stores."""
+packs and level sums the method stores, and the accuracy gate's buffers."""
 import math
 
 import pytest
@@ -42,8 +42,11 @@ def test_scratch_bound_covers_digits_and_level_sums(mm, n, m, p, S):
     assert st == mm.MM_OK
     digits = S * (math.ceil(n / 128) * 128 + math.ceil(p / 128) * 128) * m
     levels = q * S * n * p * 4
-    assert b >= digits + levels
-    assert b <= 2 * (digits + levels) + (4 << 20)
+    # the accuracy gate: FP32 copies of the scaled |A|, |B| and their product,
+    # and that product's bf16 hi/lo packs
+    gate = (n * m + m * p + n * p) * 4 + 2 * (n + p) * m * 2
+    assert b >= digits + levels + gate
+    assert b <= 2 * (digits + levels + gate) + (4 << 20)
 
 
 def test_arguments(mm):
