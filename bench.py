@@ -497,6 +497,18 @@ def bench_grouped(mm, stream, steps: int, seed: int = 4, count: int = 4096):
         out[name + "_ms"] = ms
         out[name + "_launches_per_step"] = (mm.mm_launch_count() - l0) / k
     mm.check_status(mm.mm_sync(stream), "grouped sync")
+    # device time of each kernel of one grouped step (the library's tracer)
+    mm.mm_trace_reset()
+    mm.mm_trace_enable(True)
+    grouped()
+    mm.check_status(mm.mm_sync(stream), "grouped traced run")
+    mm.mm_trace_enable(False)
+    out["grouped_kernels_ms"] = {}
+    for kname in ("split_maps", "split_pack", "split_verify", "split_fix", "split_tc"):
+        _, cnt, kms = mm.mm_trace_read(kname)
+        if cnt:
+            out["grouped_kernels_ms"][kname] = kms
+    mm.mm_trace_reset()
     # every instance: the library's FP64 GPU check, one Freivalds vector and 64
     # sampled entries, each against its own tolerance 1e-6 sqrt(m)
     grouped()
@@ -650,6 +662,63 @@ def run_grouped_only(args):
     return 0
 
 
+# the emulation's kernels as the library's tracer names them: maxima, digit
+# slices, level products, exact sum; then the accuracy gate (its own kernels,
+# its split-path product, and the FP64 FMA kernel that returns at once unless
+# the gate failed)
+OZAKI_TRACE = ("ozaki_max", "ozaki_digits", "split_maps", "fp8_tc", "ozaki_sum", "ozaki_gate",
+               "split_pack", "split_verify", "split_fix", "split_tc", "dgemm_f64")
+
+
+def run_fp8_only(args):
+    """Only the FP8 e4m3 product (per-block scales) at n = m = p = --size on
+    uniform[-1,1) operands (seeds 0/1): step rate, per-kernel device time and
+    the library's FP64 check of the result.  Prints one JSON line; also the
+    profiling driver of the FP8 kernels."""
+    import torch
+
+    import paper_1306_6192_gb300 as mm
+    import synth
+    torch.cuda.set_device(0)
+    mm.check_status(mm.mm_init(device=0), "mm_init")
+    n = args.size
+    A = torch.from_numpy(synth.uniform_pm1(0, (n, n))).cuda()
+    B = torch.from_numpy(synth.uniform_pm1(1, (n, n))).cuda()
+    C = torch.empty((n, n), device="cuda")
+    stream = torch.cuda.Stream()
+    run = lambda: mm.check_status(mm.mm_gemm_async(n, n, n, A, B, C, mm.MM_F32, mm.MM_MODE_FP8,
+                                                   stream), "fp8")
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    mm.mm_trace_reset()
+    mm.mm_trace_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    mm.mm_trace_enable(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    kernels = {}
+    for k in ("fp8_pack", "fp8_tc"):
+        _, cnt, kms = mm.mm_trace_read(k)
+        if cnt:
+            kernels[k] = kms / cnt
+    check = gpu_check(mm, n, n, n, A, B, C, mm.MM_F32)
+    mm.mm_shutdown()
+    flops = 2.0 * n ** 3
+    out = {"metric": "FP8 e4m3 GEMM TFLOP/s (per-block scales)", "value": flops / (ms * 1e-3) / 1e12,
+           "unit": "TFLOP/s", "n": n, "ms": ms, "steps": args.steps, "kernels_ms": kernels,
+           "check": check}
+    if "fp8_tc" in kernels:
+        out["tc_tflops"] = flops / (kernels["fp8_tc"] * 1e-3) / 1e12
+    print(json.dumps(out))
+    return 0
+
+
 def run_ozaki_only(args):
     """Only the FP64 product emulated by the Ozaki scheme (MM_MODE_OZAKI) at
     n = m = p = --dgemm-size on full 53-bit uniform[-1,1) operands (seeds
@@ -685,7 +754,7 @@ def run_ozaki_only(args):
     mm.mm_trace_enable(False)
     ms = e0.elapsed_time(e1) / args.steps
     kernels = {}
-    for k in ("ozaki_max", "ozaki_digits", "split_maps", "fp8_tc", "ozaki_sum"):
+    for k in OZAKI_TRACE:
         _, cnt, kms = mm.mm_trace_read(k)
         if cnt:
             kernels[k] = kms / args.steps
@@ -883,7 +952,7 @@ def run_mine(args):
         extra["ozaki_f64_tflops"] = 2.0 * nd ** 3 / (ms_o / 5 * 1e-3) / 1e12
         extra["ozaki_over_dgemm"] = extra["ozaki_f64_tflops"] / extra["dgemm_f64_tflops"]
         extra["ozaki_kernels_ms"] = {}
-        for k in ("ozaki_max", "ozaki_digits", "fp8_tc", "ozaki_sum"):
+        for k in OZAKI_TRACE:
             _, cnt, kms = mm.mm_trace_read(k)
             if cnt:
                 extra["ozaki_kernels_ms"][k] = kms / 5
@@ -1076,6 +1145,8 @@ def main(argv=None):
     ap.add_argument("--ozaki-only", action="store_true",
                     help="only the FP64 product emulated by the Ozaki scheme")
     ap.add_argument("--ozaki-slices", type=int, default=14)
+    ap.add_argument("--fp8-only", action="store_true",
+                    help="only the FP8 e4m3 product at --size")
     ap.add_argument("--stress-only", action="store_true", help="only the config-3 stress shapes")
     ap.add_argument("--serve-f64", choices=["dgemm", "ozaki"], default="dgemm",
                     help="path of the serving mix's FP64 requests")
@@ -1094,6 +1165,8 @@ def main(argv=None):
         return run_ozaki_only(args)
     if args.stress_only:
         return run_stress_only(args)
+    if args.fp8_only:
+        return run_fp8_only(args)
     if args.shard == "rows":
         return run_shard(args)
     return run_mine(args)

@@ -174,23 +174,24 @@ mm_status mm_gemm(int64_t n, int64_t m, int64_t p, const void *A, const void *B,
 mm_status mm_ozaki_slices(int slices);
 
 /* Accuracy gate of MM_MODE_OZAKI products queued after the call (serving
- * requests keep the setting current at mm_submit); on (1) by default.  With
- * the gate, each product also computes P = (|A| 2^-sigma).(|B| 2^-tau) in FP32
- * on the split path (a lower bound of sum_r |a_ir||b_rj| 2^-(sigma_i + tau_j)
- * after a 2^-10 margin) and checks every entry against the method's bound:
- * entry (i, j) of the emulation is off by at most m (S + 2) 2^(sigma_i + tau_j
- * - 4S), so it meets 1e-14 sqrt(m) of (|A||B|)_ij wherever P_ij >= sqrt(m)
- * (S + 2) 2^-4S 1e14 / (0.98 - m 2^-23) (room for the FP32 rounding of P and
- * the final rounding; every product falls back where m 2^-23 > 0.48).
- * If any entry with finite row and column misses it (a row whose largest
- * entry dwarfs the ones that meet a column, e.g. magnitudes spread over many
- * binades), the FP64 FMA product (MM_MODE_DGEMM's kernel) recomputes all of C
- * on the device, so the result meets the FP64 tolerance for any finite input;
- * the decision is data-dependent and made on the device (no host round
- * trip).  Off (0): the emulation's result is returned as it is (bit for bit
- * the method of mm_ozaki_slices).  When it passes, a 4096^3 product at
- * S = 14 takes about 15% longer with the gate (5.1 ms without, 5.9 ms
- * with).  Returns MM_EINVAL for other values, MM_ENOTINIT before mm_init. */
+ * requests keep the setting current at mm_submit); on (1) by default.  Entry
+ * (i, j) of the emulation is off by at most m (S + 2) 2^(sigma_i + tau_j - 4S)
+ * (scales 2^sigma_i of row i of A, 2^tau_j of column j of B), so it meets
+ * 1e-14 sqrt(m) of (|A||B|)_ij wherever P_ij = sum_r |a_ir| 2^-sigma_i
+ * |b_rj| 2^-tau_j >= sqrt(m) (S + 2) 2^-4S 1e14.  With the gate, each product
+ * also packs one more e4m3 slice per operand (16 |x| 2^-sigma truncated
+ * toward zero onto the e4m3 grid) and multiplies the two on the tensor cores,
+ * a lower bound of 256 P, and checks every entry against the threshold
+ * divided by 0.98 - m 2^-23 (room for the FP32 accumulation and the final
+ * rounding; every product falls back where m 2^-23 > 0.48).  If any entry
+ * with a finite, non-zero row and column misses it (magnitudes spread over
+ * many binades, entries below the e4m3 grid), the FP64 FMA product
+ * (MM_MODE_DGEMM's kernel) recomputes all of C on the device, so the result
+ * meets the FP64 tolerance for any finite input; the decision is
+ * data-dependent and made on the device (no host round trip).  Off (0): the
+ * emulation's result is returned as it is (bit for bit the method of
+ * mm_ozaki_slices; the gate never changes the emulation's own bits).
+ * Returns MM_EINVAL for other values, MM_ENOTINIT before mm_init. */
 mm_status mm_ozaki_gate(int on);
 
 /* Plan of an MM_MODE_OZAKI product, a pure host function (no device, no
@@ -345,9 +346,10 @@ mm_status mm_measure_fma_peak(mm_dtype dt, int64_t iters, double *flops_per_s);
 /* When enabled, every kernel the library launches is bracketed by CUDA events
  * on its stream; mm_trace_read returns the launch count and summed device
  * time (ms) of the kernel named `kernel` ("simt_f32", "dgemm_f64",
- * "split_pack", "split_verify", "split_fix", "split_tc", "fused_tc", "fp8_pack", "fp8_tc",
- * "check_f64", "ozaki_max", "ozaki_digits", "ozaki_sum") since the
- * last reset.  Reading synchronises the recorded events. */
+ * "split_maps", "split_pack", "split_verify", "split_fix", "split_tc", "fused_tc",
+ * "fp8_pack", "fp8_tc", "check_f64", "ozaki_max", "ozaki_map", "ozaki_digits",
+ * "ozaki_sum", "ozaki_gate", "add", "diag", "cplx_planes", "cplx_combine") since
+ * the last reset.  Reading synchronises the recorded events. */
 mm_status mm_trace_enable(int on);
 mm_status mm_trace_reset(void);
 mm_status mm_trace_read(const char *kernel, int64_t *launches, double *total_ms);

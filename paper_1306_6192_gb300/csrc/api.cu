@@ -263,8 +263,8 @@ mm_status enqueue_gemm(int64_t n, int64_t m, int64_t p, const void *A, const voi
       return run_fp8(g_ctx.fp8_ws, &q, 1, s);
     }
     case MM_MODE_OZAKI:
-      return run_ozaki(g_ctx.ozaki_ws, g_ctx.split_ws, n, m, p, (const double *)A,
-                       (const double *)B, (double *)C, g_ctx.ozaki_slices, g_ctx.ozaki_gate != 0, s);
+      return run_ozaki(g_ctx.ozaki_ws, n, m, p, (const double *)A, (const double *)B, (double *)C,
+                       g_ctx.ozaki_slices, g_ctx.ozaki_gate != 0, s);
     default: return MM_EINVAL;
   }
 }

@@ -141,11 +141,9 @@ size_t fp8_blocks_scratch_bytes(int64_t n, int64_t m, int64_t p);
 // level sum exact in FP32; ozaki_scratch_bytes = an upper bound of the
 // scratch one product needs.
 // gate: check every entry against the method's error bound and recompute C
-// with the FP64 FMA product where any entry could miss 1e-14 sqrt(m); its FP32
-// product of the scaled magnitudes runs on the split path in gate_ws.
-mm_status run_ozaki(Scratch &ws, Scratch &gate_ws, int64_t n, int64_t m, int64_t p,
-                    const double *A, const double *B, double *C, int S, bool gate,
-                    cudaStream_t s);
+// with the FP64 FMA product where any entry could miss 1e-14 sqrt(m).
+mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *A,
+                    const double *B, double *C, int S, bool gate, cudaStream_t s);
 int64_t ozaki_chunk(int S);
 size_t ozaki_scratch_bytes(int64_t n, int64_t m, int64_t p, int S);
 // Grouped dispatch: split / SIMT / DGEMM tables in one launch per path.

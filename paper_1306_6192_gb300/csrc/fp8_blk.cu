@@ -254,11 +254,11 @@ fp8blk_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__
     }
     for (int s = 0; s < kEStages; s++) {
       mbar_init(efull_bar(s), 1);
-      mbar_init(eempty_bar(s), kWorkers);
+      mbar_init(eempty_bar(s), kWorkers / 32);  // one arrival per worker warp
     }
     for (int a = 0; a < kAccs; a++) {
       mbar_init(accf_bar(a), 1);
-      mbar_init(acce_bar(a), kWorkers);
+      mbar_init(acce_bar(a), kWorkers / 32);
     }
     mbar_init(drain_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -377,9 +377,10 @@ fp8blk_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__
       int g, mt, nt;
       blk_unit(probs, nprobs, unit_map, u, g, mt, nt);
       const SplitProb &pr = probs[g];
-      float sum[kWCols];
+      // column pairs, packed for the paired FP32 instructions
+      uint64_t sum[kWCols / 2];
 #pragma unroll
-      for (int c = 0; c < kWCols; c++) sum[c] = 0.0f;
+      for (int c = 0; c < kWCols / 2; c++) sum[c] = 0ull;
       for (int kb = 0; kb < pr.kt; kb++) {
         bool w = mbar_wait(efull_bar(es), ephase, err, 23, true, kWaitNs) &&
                  mbar_wait(accf_bar(acc), aphase, err, 23, true, kWaitNs);
@@ -392,7 +393,9 @@ fp8blk_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__
         tc_fence_after();
         const float *fx = reinterpret_cast<const float *>(smem + Lay::kEOff + es * Lay::kESlot);
         const float fr = fx[row];
-        const float *fc = fx + 128 + ch * kWCols;
+        const uint64_t fr2 = pack_f32x2(__float_as_uint(fr), __float_as_uint(fr));
+        // this warp's columns' factors, two per 8-byte word
+        const uint64_t *fc2 = reinterpret_cast<const uint64_t *>(fx + 128 + ch * kWCols);
         uint32_t v[kWCols];
         const uint32_t ta = tmem_base + tlane + (uint32_t)(acc * kBN + ch * kWCols);
 #pragma unroll
@@ -400,12 +403,18 @@ fp8blk_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__
           tmem_ld_32x32b_x16(ta + c0, *reinterpret_cast<uint32_t(*)[16]>(&v[c0]));
         tmem_ld_wait();
         // v 2^(e_j) 2^(e_i): both factors are powers of two, so each product
-        // is exact and one rounding (the addition) remains
+        // is exact and one rounding (the addition) remains; two columns per
+        // instruction (mul.rn / fma.rn on FP32 pairs: each half rounds as the
+        // scalar instruction would)
 #pragma unroll
-        for (int c = 0; c < kWCols; c++) sum[c] = fmaf(__uint_as_float(v[c]) * fc[c], fr, sum[c]);
+        for (int c = 0; c < kWCols / 2; c++)
+          sum[c] = fma_f32x2(mul_f32x2(pack_f32x2(v[2 * c], v[2 * c + 1]), fc2[c]), fr2, sum[c]);
         tc_fence_before();
-        mbar_arrive(acce_bar(acc));
-        mbar_arrive(eempty_bar(es));
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(acce_bar(acc));
+          mbar_arrive(eempty_bar(es));
+        }
         if (++acc == kAccs) {
           acc = 0;
           aphase ^= 1u;
@@ -420,16 +429,19 @@ fp8blk_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__
       const int64_t i = (int64_t)mt * kTcBM + row;
       const int64_t j0 = (int64_t)nt * kBN + ch * kWCols;
       if (i < pr.n) {
+        float out[kWCols];
+#pragma unroll
+        for (int c = 0; c < kWCols / 2; c++) unpack_f32x2(sum[c], out[2 * c], out[2 * c + 1]);
         float *dst = pr.C + i * pr.p + j0;
         if (al16(pr.C) && (pr.p & 3) == 0 && j0 + kWCols <= pr.p) {
 #pragma unroll
           for (int c = 0; c < kWCols; c += 4)
             __stcs(reinterpret_cast<float4 *>(dst + c),
-                   make_float4(sum[c], sum[c + 1], sum[c + 2], sum[c + 3]));
+                   make_float4(out[c], out[c + 1], out[c + 2], out[c + 3]));
         } else {
 #pragma unroll
           for (int c = 0; c < kWCols; c++)
-            if (j0 + c < pr.p) __stcs(dst + c, sum[c]);
+            if (j0 + c < pr.p) __stcs(dst + c, out[c]);
         }
       }
     }

@@ -17,8 +17,7 @@ mm_status enqueue_grouped(Scratch &split_ws, Scratch &tab_ws, int count, const m
   if (mode == MM_MODE_OZAKI) {  // one emulated product after the other
     for (int g = 0; g < count; g++) {
       const mm_problem &q = probs[g];
-      const mm_status st = run_ozaki(g_ctx.ozaki_ws, split_ws, q.n, q.m, q.p,
-                                     static_cast<const double *>(q.A),
+      const mm_status st = run_ozaki(g_ctx.ozaki_ws, q.n, q.m, q.p, static_cast<const double *>(q.A),
                                      static_cast<const double *>(q.B), static_cast<double *>(q.C),
                                      g_ctx.ozaki_slices, g_ctx.ozaki_gate != 0, s);
       if (st != MM_OK) return st;

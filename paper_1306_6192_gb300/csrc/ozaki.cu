@@ -34,22 +34,27 @@
 // data dependent: ~4 (S + 2) 2^(-4S) for rows and columns without a wide
 // spread of magnitudes (uniform data), much more where a row's largest entry
 // dwarfs the entries that meet the column's mass.  The accuracy gate (on by
-// default) bounds P_ij = (|A||B|)_ij 2^-(sigma_i + tau_j) from below with an
-// FP32 product on the split path and, where any entry's bound could exceed
-// 1e-14 sqrt(m) (|A||B|)_ij, recomputes C with the FP64 FMA kernel.
+// default) bounds P_ij = (|A||B|)_ij 2^-(sigma_i + tau_j) from below with one
+// more e4m3 slice per operand (the scaled magnitudes truncated onto the e4m3
+// grid) and one more tensor-core product per K chunk, and where any entry's
+// bound could exceed 1e-14 sqrt(m) (|A||B|)_ij, recomputes C with the FP64
+// FMA kernel.
 //
 // Data layout in the library's scratch ("pack region" first, 128-byte rows,
 // as the tensor-core kernel's tensor map requires):
 //   A digits of chunk c: tile (mt, slice t, kb) at rows
-//       a0_c + ((mt*S + t)*kt_c + kb)*128, one row per row of A (128 k);
+//       a0_c + ((mt*SS + t)*kt_c + kb)*128, one row per row of A (128 k);
 //   B digits of chunk c: tile (nt, slot, kb) at rows
-//       b0_c + ((nt*S + slot)*kt_c + kb)*bn, slot = S-1-u for slice u, one
+//       b0_c + ((nt*SS + slot)*kt_c + kb)*bn, slot = S-1-u for slice u, one
 //       row per column of B, so that B's slices L..0 are contiguous;
+//   SS = S, or S + 1 with the gate, whose slice is t = slot = S;
 //   then the row/column maxima (bit patterns), zero scale words, the level
 //   sums D (FP32, [chunk][level] planes of n x p, padded so that planes are
-//   not a power of two apart), the problem table and its unit map.
+//   not a power of two apart) followed by the gate's planes [chunk], the
+//   problem table, its unit map and the gate's flag.
 // The level problem (c, L) reads A's K blocks [0, (L+1) kt_c) and B's
-// [(S-1-L) kt_c, S kt_c) of each tile through the table's K stride S kt_c.
+// [(S-1-L) kt_c, S kt_c) of each tile through the table's K stride SS kt_c;
+// the gate's problem c reads [S kt_c, (S+1) kt_c) of both.
 // Rows (columns) holding a NaN or an infinity give NaN rows (columns) of C.
 #include <cuda_fp8.h>
 
@@ -124,6 +129,36 @@ __device__ __forceinline__ uint4 digit_bytes(const uint64_t (&F)[kSeg], uint32_t
   return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
+// The accuracy gate's slice: 16 |x| 2^-sigma truncated toward zero onto the
+// e4m3 grid (4 significant bits at 2^-6 and above, multiples of 2^-9 below;
+// 0 under 2^-9), so the value is exact in e4m3 and never above 16 |x| 2^-sigma.
+// Formed from the truncated fixed-point magnitude F = floor(|x| 2^(4S-sigma))
+// in integer and FP32 arithmetic (16 |x| 2^-sigma >= F 2^(4-4S)): F's top four
+// bits times a power of two.
+__device__ __forceinline__ float gate_value(uint64_t F, int S) {
+  if (F == 0) return 0.0f;
+  const int b = 64 - __clzll((long long)F);  // bit length, 1..4S
+  const int sh = b > 4 ? b - 4 : 0;
+  const float top = (float)(uint32_t)(F >> sh);  // 1..15, exact
+  // 2^(sh + 4 - 4S) >= 2^(4 - 64): a normal float
+  const float v = top * __int_as_float((sh + 4 - 4 * S + 127) << 23);
+  return v >= 0x1p-6f ? v : floorf(v * 512.0f) * 0x1p-9f;
+}
+
+// 16 gate values -> 16 e4m3 bytes (exact conversions).
+__device__ __forceinline__ uint4 gate_bytes(const float (&g)[kSeg]) {
+  uint32_t w[4];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const __nv_fp8x2_storage_t lo =
+        __nv_cvt_float2_to_fp8x2(make_float2(g[4 * q], g[4 * q + 1]), __NV_SATFINITE, __NV_E4M3);
+    const __nv_fp8x2_storage_t hi =
+        __nv_cvt_float2_to_fp8x2(make_float2(g[4 * q + 2], g[4 * q + 3]), __NV_SATFINITE, __NV_E4M3);
+    w[q] = (uint32_t)lo | ((uint32_t)hi << 16);
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
 // Maxima: items [0, ceil(n/8)) take 8 rows of A (a warp per row); the rest
 // strips of 32 columns x 256 rows of B, merged into colmax with atomicMax on
 // the bit patterns (which order like the magnitudes).
@@ -175,17 +210,19 @@ ozaki_max_kernel(const double *__restrict__ A, const double *__restrict__ B, int
 // A digits of one K chunk [k0, k0 + mc): one block per tile (mt, kb); a
 // thread takes 16 consecutive k of a row (8 threads per 128-k row, 4 rows per
 // warp: a warp's 16 loads read four whole 1 KB row segments, and each digit
-// store instruction writes four whole 128-byte pack rows).
+// store instruction writes four whole 128-byte pack rows).  SS = S slices per
+// tile, or S + 1 with the accuracy gate's slice (gate_value) after them.
 __global__ void __launch_bounds__(256)
 ozaki_digits_a_kernel(const double *__restrict__ A, int64_t n, int64_t m, int64_t k0, int64_t mc,
-                      int kt, int S, const uint64_t *__restrict__ rowmax, uint4 *__restrict__ pack,
-                      int64_t a0) {
+                      int kt, int S, int SS, const uint64_t *__restrict__ rowmax,
+                      uint4 *__restrict__ pack, int64_t a0) {
   const int mt = blockIdx.x / kt, kb = blockIdx.x % kt;
 #pragma unroll 1
   for (int q = threadIdx.x; q < kTcBM * (128 / kSeg); q += 256) {
     const int r = q / (128 / kSeg), sg = q % (128 / kSeg);
     const int64_t i = (int64_t)mt * kTcBM + r;
     uint64_t F[kSeg];
+    float G[kSeg];
     uint32_t negmask = 0;
     bool finite = true;
     const int sigma = i < n ? slice_exponent(rowmax[i], finite) : 0;
@@ -193,16 +230,22 @@ ozaki_digits_a_kernel(const double *__restrict__ A, int64_t n, int64_t m, int64_
     for (int e = 0; e < kSeg; e++) {
       const int64_t kk = (int64_t)kb * 128 + sg * kSeg + e;  // within the chunk
       F[e] = 0;
+      G[e] = 0.0f;
       if (i < n && finite && kk < mc) {
         bool neg;
         F[e] = fixed_magnitude(A[i * m + k0 + kk], sigma, S, neg);
         negmask |= (uint32_t)neg << e;
+        if (SS > S) G[e] = gate_value(F[e], S);
       }
     }
 #pragma unroll 1
     for (int t = 0; t < S; t++) {
-      const int64_t row = a0 + (((int64_t)mt * S + t) * kt + kb) * kTcBM + r;
+      const int64_t row = a0 + (((int64_t)mt * SS + t) * kt + kb) * kTcBM + r;
       pack[row * (kPackRowBytes / 16) + sg] = digit_bytes(F, negmask, 4 * (S - 1 - t));
+    }
+    if (SS > S) {
+      const int64_t row = a0 + (((int64_t)mt * SS + S) * kt + kb) * kTcBM + r;
+      pack[row * (kPackRowBytes / 16) + sg] = gate_bytes(G);
     }
   }
 }
@@ -212,7 +255,7 @@ ozaki_digits_a_kernel(const double *__restrict__ A, int64_t n, int64_t m, int64_
 // read whole), then a thread takes 16 consecutive k of a column.
 __global__ void __launch_bounds__(256)
 ozaki_digits_b_kernel(const double *__restrict__ B, int64_t m, int64_t p, int64_t k0, int64_t mc,
-                      int kt, int S, int bn, const unsigned long long *__restrict__ colmax,
+                      int kt, int S, int SS, int bn, const unsigned long long *__restrict__ colmax,
                       uint4 *__restrict__ pack, int64_t b0) {
   __shared__ double tile[128][32 + 1];
   const int nt = blockIdx.x / kt, kb = blockIdx.x % kt;
@@ -230,20 +273,27 @@ ozaki_digits_b_kernel(const double *__restrict__ B, int64_t m, int64_t p, int64_
       bool finite = true;
       const int tau = j < p ? slice_exponent(colmax[j], finite) : 0;
       uint64_t F[kSeg];
+      float G[kSeg];
       uint32_t negmask = 0;
 #pragma unroll
       for (int e = 0; e < kSeg; e++) {
         F[e] = 0;
+        G[e] = 0.0f;
         if (j < p && finite) {
           bool neg;
           F[e] = fixed_magnitude(tile[sg * kSeg + e][c], tau, S, neg);
           negmask |= (uint32_t)neg << e;
+          if (SS > S) G[e] = gate_value(F[e], S);
         }
       }
 #pragma unroll 1
       for (int u = 0; u < S; u++) {
-        const int64_t row = b0 + (((int64_t)nt * S + (S - 1 - u)) * kt + kb) * bn + c0 + c;
+        const int64_t row = b0 + (((int64_t)nt * SS + (S - 1 - u)) * kt + kb) * bn + c0 + c;
         pack[row * (kPackRowBytes / 16) + sg] = digit_bytes(F, negmask, 4 * (S - 1 - u));
+      }
+      if (SS > S) {
+        const int64_t row = b0 + (((int64_t)nt * SS + S) * kt + kb) * bn + c0 + c;
+        pack[row * (kPackRowBytes / 16) + sg] = gate_bytes(G);
       }
     }
     __syncthreads();
@@ -340,49 +390,38 @@ ozaki_sum_kernel(const float *__restrict__ D, int64_t plane, int64_t n, int64_t 
 // most (S + 2) 2^(sigma_i + tau_j - 4S), so entry (i, j) is off by at most
 // m (S + 2) 2^(sigma_i + tau_j - 4S); the product meets e_ij <= 1e-14 sqrt(m)
 // wherever P_ij = sum_r |a_ir| 2^-sigma_i |b_rj| 2^-tau_j is at least
-// sqrt(m) (S + 2) 2^-4S 1e14.  P is computed in FP32 on the split path from
-// |A| 2^-sigma and |B| 2^-tau: entries in [0, 1), so no cancellation.  Each
-// term is off by a few 2^-16 relative (the kernel lowers P by 2^-10) and the
-// FP32 accumulation by at most m 2^-23 relative (the host divides the
-// threshold by 0.98 - m 2^-23; the 2% also covers the final rounding to a
-// double, 2^-53 relative, below 1.2% of 1e-14).  Where m 2^-23 reaches 1/2
-// the threshold is infinite and every product falls back.  Entries whose
-// FP32 copies underflow only lower P (a fallback, never a miss).  An entry
-// that misses the bound sets a flag; the FP64 FMA product then recomputes C.
+// sqrt(m) (S + 2) 2^-4S 1e14.  A lower bound of 256 P comes from the
+// emulation's own machinery: one more slice per operand holds gate_value
+// (16 |x| 2^-sigma truncated toward zero onto the e4m3 grid), and one more
+// tensor-core product per K chunk multiplies the two (products exact in
+// FP32; the FP32 accumulation of nonnegative terms is off by at most m 2^-23
+// relative, which the host's threshold absorbs: it divides by 0.98 - m 2^-23,
+// the 2% also covering the final rounding to a double, 2^-53 relative, below
+// 1.2% of 1e-14; where m 2^-23 reaches 1/2 the threshold is infinite and
+// every product falls back).  Truncation only lowers the bound, so entries
+// whose magnitudes fall below the e4m3 grid cause a fallback, never a miss.
+// The check kernel adds the chunks' planes in FP32 (at most 1024 nonnegative
+// terms), lowers the sum by 2^-10 (more than that addition's rounding) and
+// sets a flag where any entry with a finite, non-zero row and column misses
+// the threshold; the FP64 FMA product then recomputes C.
 __global__ void __launch_bounds__(256)
-ozaki_gate_abs_kernel(const double *__restrict__ X, int64_t rows, int64_t cols,
-                      const uint64_t *__restrict__ rmax, const unsigned long long *__restrict__ cmax,
-                      float *__restrict__ out) {
-  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
-    const double *src = X + r * cols;
-    float *dst = out + r * cols;
-    bool frow = true;
-    const int srow = rmax ? slice_exponent(rmax[r], frow) : 0;
-    for (int64_t c = threadIdx.x; c < cols; c += blockDim.x) {
-      bool f = frow;
-      const int sc = cmax ? slice_exponent(cmax[c], f) : srow;
-      dst[c] = f ? (float)ldexp(fabs(src[c]), -sc) : 0.0f;
-    }
-  }
-}
-
-__global__ void __launch_bounds__(256)
-ozaki_gate_check_kernel(const float *__restrict__ P, int64_t n, int64_t p,
-                        const uint64_t *__restrict__ rowmax,
-                        const unsigned long long *__restrict__ colmax, float thr, int *flag) {
+ozaki_gate_check_kernel(const float *__restrict__ G, int64_t plane, int chunks, int64_t n,
+                        int64_t p, const uint64_t *__restrict__ rowmax,
+                        const unsigned long long *__restrict__ colmax, float thr256, int *flag) {
   bool fail = false;
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
     bool fi;
     slice_exponent(rowmax[i], fi);
-    if (!fi) continue;  // a row with a NaN or an infinity gives NaN by design
+    // a row with a NaN or an infinity gives NaN by design; an all-zero row
+    // gives exact zeros
+    if (!fi || rowmax[i] == 0) continue;
     for (int64_t j = threadIdx.x; j < p; j += blockDim.x) {
       bool fj;
       slice_exponent(colmax[j], fj);
-      if (!fj) continue;
-      const float v = P[i * p + j];
-      // all-zero rows or columns give exact zeros; any other entry must meet
-      // the bound (P == 0 there may be an underflow of the FP32 copy)
-      if (rowmax[i] != 0 && colmax[j] != 0 && !(v * (1.0f - 0x1p-10f) >= thr)) fail = true;
+      if (!fj || colmax[j] == 0) continue;
+      float v = 0.0f;
+      for (int c = 0; c < chunks; c++) v += __ldcs(G + (int64_t)c * plane + i * p + j);
+      if (!(v * (1.0f - 0x1p-10f) >= thr256)) fail = true;
     }
   }
   if (__syncthreads_or(fail) && threadIdx.x == 0) atomicOr(flag, 1);
@@ -390,11 +429,11 @@ ozaki_gate_check_kernel(const float *__restrict__ P, int64_t n, int64_t p,
 
 // Scratch offsets of one call.
 struct OzLayout {
-  int S, chunks, bn, mt, nt;
+  int S, SS, chunks, bn, mt, nt;
   int64_t mc;
   std::vector<int64_t> k0, kc, kt, a0, b0;
   int64_t rows = 0, plane = 0;
-  size_t max_off, zero_off, zero_end, d_off, tab_off, map_off, gate_off, need;
+  size_t max_off, zero_off, zero_end, d_off, tab_off, map_off, flag_off, need;
   int64_t units = 0;
 };
 
@@ -405,14 +444,14 @@ int64_t ozaki_chunk(int S) {
   return mc;
 }
 
-mm_status run_ozaki(Scratch &ws, Scratch &gate_ws, int64_t n, int64_t m, int64_t p,
-                    const double *A, const double *B, double *C, int S, bool gate,
-                    cudaStream_t s) {
+mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *A,
+                    const double *B, double *C, int S, bool gate, cudaStream_t s) {
   if (S < kOzakiMinSlices || S > kOzakiMaxSlices) return MM_EINVAL;
   if (n == 0 || p == 0) return MM_OK;
   if (m == 0) return note_cuda(cudaMemsetAsync(C, 0, (size_t)(n * p) * sizeof(double), s));
   OzLayout lay;
   lay.S = S;
+  lay.SS = S + (gate ? 1 : 0);  // slices per tile in the packs (the gate's last)
   lay.mc = ozaki_chunk(S);
   if (ceil_div(m, lay.mc) > kOzakiMaxChunks) return MM_EINVAL;
   lay.chunks = (int)ceil_div(m, lay.mc);
@@ -427,12 +466,13 @@ mm_status run_ozaki(Scratch &ws, Scratch &gate_ws, int64_t n, int64_t m, int64_t
     lay.kc.push_back(kc);
     lay.kt.push_back(kt);
     lay.a0.push_back(lay.rows);
-    lay.rows += (int64_t)lay.mt * S * kt * kTcBM;
+    lay.rows += (int64_t)lay.mt * lay.SS * kt * kTcBM;
     lay.b0.push_back(lay.rows);
-    lay.rows += (int64_t)lay.nt * S * kt * lay.bn;
+    lay.rows += (int64_t)lay.nt * lay.SS * kt * lay.bn;
   }
   if (lay.rows > 0x7fffffffLL) return MM_EINVAL;
-  const int nprobs = lay.chunks * S;
+  // S level problems per chunk, then the gate's product per chunk
+  const int nprobs = lay.chunks * lay.SS;
   const int64_t tiles = (int64_t)lay.mt * lay.nt;
   // level planes of D, padded so that the planes of one entry do not sit a
   // power of two apart (128-byte aligned)
@@ -459,14 +499,38 @@ mm_status run_ozaki(Scratch &ws, Scratch &gate_ws, int64_t n, int64_t m, int64_t
       sp.group_m = ch.group_m;
       sp.a_row0 = lay.a0[(size_t)c];
       sp.b_row0 = lay.b0[(size_t)c] + (int64_t)(S - 1 - L) * kt * lay.bn;
-      sp.a_kstride = (int32_t)(S * kt);
-      sp.b_kstride = (int32_t)(S * kt);
+      sp.a_kstride = (int32_t)(lay.SS * kt);
+      sp.b_kstride = (int32_t)(lay.SS * kt);
       sp.unit_start = (int32_t)lay.units;
       lay.units += tiles;
       sp.split_from = (int32_t)tiles;
       sp.split_s = 1;
       sp.C = reinterpret_cast<float *>((uintptr_t)(((int64_t)c * S + L) * lay.plane));  // offset
     }
+  // the gate's products (one slice against one slice: as short as level 0,
+  // so they run last), planes after the level planes
+  for (int c = 0; gate && c < lay.chunks; c++, g++) {
+    SplitProb &sp = tab[(size_t)g];
+    std::memset(&sp, 0, sizeof(sp));
+    const int64_t kt = lay.kt[(size_t)c];
+    sp.n = (int32_t)n;
+    sp.p = (int32_t)p;
+    sp.kt = (int32_t)kt;
+    sp.m = sp.kt * 128;
+    sp.mt = lay.mt;
+    sp.nt = lay.nt;
+    sp.bn = lay.bn;
+    sp.group_m = ch.group_m;
+    sp.a_row0 = lay.a0[(size_t)c] + (int64_t)S * kt * kTcBM;
+    sp.b_row0 = lay.b0[(size_t)c] + (int64_t)S * kt * lay.bn;
+    sp.a_kstride = (int32_t)(lay.SS * kt);
+    sp.b_kstride = (int32_t)(lay.SS * kt);
+    sp.unit_start = (int32_t)lay.units;
+    lay.units += tiles;
+    sp.split_from = (int32_t)tiles;
+    sp.split_s = 1;
+    sp.C = reinterpret_cast<float *>((uintptr_t)(((int64_t)lay.chunks * S + c) * lay.plane));
+  }
   if (lay.units > 0x7fffffffLL) return MM_EINVAL;
   const size_t pack_bytes = (size_t)lay.rows * kPackRowBytes;
   lay.max_off = (pack_bytes + 255) & ~(size_t)255;  // row maxima (n) + column maxima (p)
@@ -475,9 +539,9 @@ mm_status run_ozaki(Scratch &ws, Scratch &gate_ws, int64_t n, int64_t m, int64_t
   lay.d_off = (lay.zero_end + 255) & ~(size_t)255;
   lay.tab_off = (lay.d_off + (size_t)nprobs * lay.plane * sizeof(float) + 255) & ~(size_t)255;
   lay.map_off = (lay.tab_off + (size_t)nprobs * sizeof(SplitProb) + 255) & ~(size_t)255;
-  // gate: |A| 2^-sigma, |B| 2^-tau, P (FP32) and the fallback flag
-  lay.gate_off = (lay.map_off + (size_t)lay.units * sizeof(int) + 255) & ~(size_t)255;
-  lay.need = lay.gate_off + (size_t)(n * m + m * p + n * p) * sizeof(float) + 256;
+  // the gate's fallback flag
+  lay.flag_off = (lay.map_off + (size_t)lay.units * sizeof(int) + 255) & ~(size_t)255;
+  lay.need = lay.flag_off + 256;
   cudaError_t e = ws.reserve(lay.need, s);
   if (e != cudaSuccess) return note_cuda(e);
   uint8_t *base = static_cast<uint8_t *>(ws.ptr);
@@ -507,9 +571,10 @@ mm_status run_ozaki(Scratch &ws, Scratch &gate_ws, int64_t n, int64_t m, int64_t
     for (int c = 0; c < lay.chunks; c++) {
       const int kt = (int)lay.kt[(size_t)c];
       ozaki_digits_a_kernel<<<(unsigned)(lay.mt * kt), 256, 0, s>>>(
-          A, n, m, lay.k0[(size_t)c], lay.kc[(size_t)c], kt, S, rowmax, pk, lay.a0[(size_t)c]);
+          A, n, m, lay.k0[(size_t)c], lay.kc[(size_t)c], kt, S, lay.SS, rowmax, pk,
+          lay.a0[(size_t)c]);
       ozaki_digits_b_kernel<<<(unsigned)(lay.nt * kt), 256, 0, s>>>(
-          B, m, p, lay.k0[(size_t)c], lay.kc[(size_t)c], kt, S, lay.bn, colmax, pk,
+          B, m, p, lay.k0[(size_t)c], lay.kc[(size_t)c], kt, S, lay.SS, lay.bn, colmax, pk,
           lay.b0[(size_t)c]);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
@@ -537,28 +602,19 @@ mm_status run_ozaki(Scratch &ws, Scratch &gate_ws, int64_t n, int64_t m, int64_t
     if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
   }
   if (!gate) return MM_OK;
-  float *ah = reinterpret_cast<float *>(base + lay.gate_off);
-  float *bh = ah + n * m;
-  float *P = bh + m * p;
-  int *flag = reinterpret_cast<int *>(P + n * p);
+  int *flag = reinterpret_cast<int *>(base + lay.flag_off);
   {
     TraceScope ts("ozaki_gate", s);
     if ((e = cudaMemsetAsync(flag, 0, sizeof(int), s)) != cudaSuccess) return note_cuda(e);
-    const unsigned ga = (unsigned)std::min<int64_t>(n, 65535), gb = (unsigned)std::min<int64_t>(m, 65535);
-    ozaki_gate_abs_kernel<<<ga, 256, 0, s>>>(A, n, m, rowmax, nullptr, ah);
-    ozaki_gate_abs_kernel<<<gb, 256, 0, s>>>(B, m, p, nullptr, colmax, bh);
-    if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
-  }
-  const mm_problem q{n, m, p, ah, bh, P};
-  mm_status st = run_split(gate_ws, &q, 1, s, nullptr);
-  if (st != MM_OK) return st;
-  {
-    TraceScope ts("ozaki_gate", s);
     const double room = 0.98 - (double)m * 0x1p-23;
-    const double thr = room < 0.5 ? (double)INFINITY
-                                  : std::sqrt((double)m) * (S + 2) * std::ldexp(1.0, -4 * S) * 1e14 / room;
+    const double thr256 = room < 0.5 ? (double)INFINITY
+                                     : 256.0 * std::sqrt((double)m) * (S + 2) *
+                                           std::ldexp(1.0, -4 * S) * 1e14 / room;
+    float thr = (float)thr256;  // rounded up to a float
+    if ((double)thr < thr256) thr = std::nextafter(thr, (float)INFINITY);
     const unsigned gc = (unsigned)std::min<int64_t>(n, (int64_t)sm_count() * 8);
-    ozaki_gate_check_kernel<<<gc, 256, 0, s>>>(P, n, p, rowmax, colmax, (float)thr, flag);
+    ozaki_gate_check_kernel<<<gc, 256, 0, s>>>(D + (int64_t)lay.chunks * S * lay.plane, lay.plane,
+                                                lay.chunks, n, p, rowmax, colmax, thr, flag);
     if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
   }
   // the FP64 FMA product replaces C where the flag is set
@@ -570,15 +626,14 @@ size_t ozaki_scratch_bytes(int64_t n, int64_t m, int64_t p, int S) {
   const int64_t mc = ozaki_chunk(S);
   const int64_t chunks = ceil_div(m, mc);
   const int64_t kt_all = ceil_div(m, 128) + chunks;  // K blocks over all chunks (bound)
-  const int64_t rows = (ceil_div(n, kTcBM) * kTcBM + ceil_div(p, 128) * 256) * S * kt_all;
-  // digit packs, level sums, maxima, table and map; the accuracy gate's FP32
-  // copies and product, and the split packs of that product (bf16 hi/lo)
-  const size_t gate = (size_t)(n * m + m * p + n * p) * sizeof(float) +
-                      (size_t)(ceil_div(n, kTcBM) * kTcBM + ceil_div(p, 128) * 256) *
-                          ceil_div(m, 64) * kPackRowBytes * 2;
-  return (size_t)rows * kPackRowBytes + (size_t)chunks * S * (n * p + 64) * sizeof(float) +
-         (size_t)(n + p) * 12 + (size_t)chunks * S * ceil_div(n, kTcBM) * ceil_div(p, 128) * 4 +
-         (size_t)chunks * S * sizeof(SplitProb) + gate + ((size_t)1 << 20);
+  // S digit slices per operand and the accuracy gate's slice (counted whether
+  // or not the gate is on), their level sums and the gate's planes, maxima,
+  // table and map
+  const int64_t SS = S + 1;
+  const int64_t rows = (ceil_div(n, kTcBM) * kTcBM + ceil_div(p, 128) * 256) * SS * kt_all;
+  return (size_t)rows * kPackRowBytes + (size_t)chunks * SS * (n * p + 64) * sizeof(float) +
+         (size_t)(n + p) * 12 + (size_t)chunks * SS * ceil_div(n, kTcBM) * ceil_div(p, 128) * 4 +
+         (size_t)chunks * SS * sizeof(SplitProb) + ((size_t)1 << 20);
 }
 
 }  // namespace mm

@@ -218,9 +218,7 @@ mm_status launch_batch(Slot &sl, std::vector<Request *> &reqs) {
     st = MM_OK;
     for (size_t k = 0; k < reqs.size() && st == MM_OK; k++) {
       const mm_problem &q = reqs[k]->pr;
-      // the slot's table scratch (unused by this batch) holds the gate's
-      // split packs
-      st = run_ozaki(sl.split_ws, sl.tab_ws, q.n, q.m, q.p, static_cast<const double *>(q.A),
+      st = run_ozaki(sl.split_ws, q.n, q.m, q.p, static_cast<const double *>(q.A),
                      static_cast<const double *>(q.B), static_cast<double *>(q.C),
                      reqs[k]->slices, reqs[k]->gate, sl.s);
     }

@@ -8,15 +8,17 @@
 //   * Work units are (output tile, K slice): the inner dimension of each tile
 //     is cut into S slices (S = Q * CS), one CTA per slice, CS CTAs of the
 //     same tile forming one thread-block cluster.
-//   * Converter warps read the FP32 operands straight from global memory (no
-//     pack pass), one K block of 64 at a time, split them into bf16 parts
-//     (x3: hi, lo; x6: hi, mid, lo - the split of Henry, Tang & Heinecke,
-//     ARITH 2019) and write them into shared memory in the 128-byte-swizzled
-//     K-major layout that tcgen05 reads (B transposed on the way).
+//   * TMA copies the FP32 operands straight from the caller's matrices (no
+//     pack pass) into two shared-memory staging buffers, one K block of 64 at
+//     a time (zero fill past the edges); eight worker warps split each block
+//     into bf16 parts (x3: hi, lo; x6: hi, mid, lo - the split of Henry, Tang
+//     & Heinecke, ARITH 2019) and write them into shared memory in the
+//     128-byte-swizzled K-major layout that tcgen05 reads (B transposed on
+//     the way).
 //   * One thread issues the tcgen05 MMAs of the block (hi.hi + hi.lo + lo.hi,
 //     or the six products of the three-part split) into one of two tensor-
-//     memory accumulators; the epilogue warps load the block's FP32 partial
-//     product (tcgen05.ld) and add it into registers, so every block of 64
+//     memory accumulators; the same worker warps load the block's FP32
+//     partial product (tcgen05.ld) and add it into registers, so every block of 64
 //     terms is accumulated on the tensor cores and the blocks are summed with
 //     round-to-nearest FP32 additions.
 //   * Scaling: a block whose non-zero entries all lie in [2^-40, 2^40] is

@@ -192,5 +192,33 @@ __device__ __forceinline__ uint32_t make_idesc(int bn) {
          ((uint32_t)(kTcBM >> 4) << 24);
 }
 
+// Paired FP32 arithmetic (two independent lanes in one 64-bit register, the
+// low half first): each half is rounded to nearest exactly as the scalar
+// mul.rn.f32 / fma.rn.f32 would round it.
+__device__ __forceinline__ uint64_t pack_f32x2(uint32_t lo, uint32_t hi) {
+  uint64_t d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "r"(lo), "r"(hi));
+  return d;
+}
+
+__device__ __forceinline__ void unpack_f32x2(uint64_t d, float &lo, float &hi) {
+  uint32_t a, b;
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(a), "=r"(b) : "l"(d));
+  lo = __uint_as_float(a);
+  hi = __uint_as_float(b);
+}
+
+__device__ __forceinline__ uint64_t mul_f32x2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+__device__ __forceinline__ uint64_t fma_f32x2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 }  // namespace tcx
 }  // namespace mm

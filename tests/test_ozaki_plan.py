@@ -2,7 +2,8 @@
 (mm_ozaki_plan, no GPU): its K chunk rule must be the one the oracle restates
 independently (oracle/ozaki.py), its chunk count ceil(m / columns), its
 argument checks as documented, and its scratch bound must cover the digit
-packs and level sums the method stores, and the accuracy gate's buffers."""
+packs and level sums the method stores, with the accuracy gate's slice and
+planes."""
 import math
 
 import pytest
@@ -40,13 +41,12 @@ def test_chunk_count(mm, m):
 def test_scratch_bound_covers_digits_and_level_sums(mm, n, m, p, S):
     st, mc, q, b = mm.mm_ozaki_plan(n, m, p, S)
     assert st == mm.MM_OK
-    digits = S * (math.ceil(n / 128) * 128 + math.ceil(p / 128) * 128) * m
-    levels = q * S * n * p * 4
-    # the accuracy gate: FP32 copies of the scaled |A|, |B| and their product,
-    # and that product's bf16 hi/lo packs
-    gate = (n * m + m * p + n * p) * 4 + 2 * (n + p) * m * 2
-    assert b >= digits + levels + gate
-    assert b <= 2 * (digits + levels + gate) + (4 << 20)
+    # S digit slices per operand plus the accuracy gate's slice, S level sums
+    # per K chunk plus the gate's plane
+    digits = (S + 1) * (math.ceil(n / 128) * 128 + math.ceil(p / 128) * 128) * m
+    levels = q * (S + 1) * n * p * 4
+    assert b >= digits + levels
+    assert b <= 2 * (digits + levels) + (4 << 20)
 
 
 def test_arguments(mm):
