@@ -178,11 +178,24 @@ TcTail tc_tail_plan(int64_t tiles, int grid, int kt, int bn, int64_t m, double p
 size_t tc_tail_bytes(const TcTail &t, int64_t tiles, int bn);
 size_t tc_tail_part_bytes(const TcTail &t, int64_t tiles, int bn);
 // flags: per-problem kFlagScaleA / kFlagScaleB (nullptr: both operands were
-// packed scaled).
+// packed scaled).  order: the work units of each CTA (tc_unit_order, on the
+// device), or nullptr for units c, c + grid, c + 2 grid, ... on CTA c.
 cudaError_t launch_tc(TcKind kind, const SplitProb *d_probs, int nprobs,
                       int total_units, const int *unit_map, const int *flags,
                       void *pack_base, int64_t pack_rows, const TcConfig &cfg,
-                      int *d_err, cudaStream_t s);
+                      int *d_err, cudaStream_t s, const int *order = nullptr);
+// CTAs of a tensor-core launch of total_units work units.
+int tc_launch_grid(const TcConfig &cfg, int64_t total_units);
+// Work units per CTA for a table whose units differ in length (a grouped
+// table, the FP64 emulation's levels): each unit, in index order, goes to the
+// CTA the cost model (K pack rows of the unit, plus one for its fixed cost)
+// expects to be free first, the lowest-numbered CTA on a tie.  The CTAs then
+// work on neighbouring units at any time, so the operand tiles that
+// neighbouring units share are still in L2 when the second one reads them, and
+// they finish together; with units of equal length the schedule is the
+// round-robin one.  out: grid + 1 offsets into the list that follows, then the
+// units of CTA 0, of CTA 1, ... (each ascending).  Host only.
+void tc_unit_order(const SplitProb *tab, int nprobs, int grid, std::vector<int> &out);
 
 // Fused split-K launch of one product (tiles * S CTAs in clusters of cs =
 // S / Q); six: three bf16 parts.  The operands are read by TMA, so A and B

@@ -51,7 +51,8 @@
 //   then the row/column maxima (bit patterns), zero scale words, the level
 //   sums D (FP32, [chunk][level] planes of n x p, padded so that planes are
 //   not a power of two apart) followed by the gate's planes [chunk], the
-//   problem table, its unit map and the gate's flag.
+//   problem table with the work units of each CTA, the unit map and the
+//   gate's flag.
 // The level problem (c, L) reads A's K blocks [0, (L+1) kt_c) and B's
 // [(S-1-L) kt_c, S kt_c) of each tile through the table's K stride SS kt_c;
 // the gate's problem c reads [S kt_c, (S+1) kt_c) of both.
@@ -538,7 +539,13 @@ mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *
   lay.zero_end = lay.max_off + (size_t)(n + p) * 8 + (size_t)(n + p) * 4;  // + zero scale words
   lay.d_off = (lay.zero_end + 255) & ~(size_t)255;
   lay.tab_off = (lay.d_off + (size_t)nprobs * lay.plane * sizeof(float) + 255) & ~(size_t)255;
-  lay.map_off = (lay.tab_off + (size_t)nprobs * sizeof(SplitProb) + 255) & ~(size_t)255;
+  // the table, then the work units of each CTA (the levels differ in length)
+  TcConfig cfg{128, 4, ch.grid};
+  cfg.max_bn = lay.bn;
+  std::vector<int> order;
+  tc_unit_order(tab.data(), nprobs, tc_launch_grid(cfg, lay.units), order);
+  const size_t tab_bytes = ((size_t)nprobs * sizeof(SplitProb) + 15) & ~(size_t)15;
+  lay.map_off = (lay.tab_off + tab_bytes + order.size() * sizeof(int) + 255) & ~(size_t)255;
   // the gate's fallback flag
   lay.flag_off = (lay.map_off + (size_t)lay.units * sizeof(int) + 255) & ~(size_t)255;
   lay.need = lay.flag_off + 256;
@@ -555,7 +562,13 @@ mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *
     sp.tB = zero_words + n;
   }
   SplitProb *d_tab = reinterpret_cast<SplitProb *>(base + lay.tab_off);
-  e = ws.stage.copy_to_device(d_tab, tab.data(), tab.size() * sizeof(SplitProb), s);
+  const int *d_order = reinterpret_cast<const int *>(base + lay.tab_off + tab_bytes);
+  {
+    std::vector<uint8_t> blob(tab_bytes + order.size() * sizeof(int), 0);
+    std::memcpy(blob.data(), tab.data(), tab.size() * sizeof(SplitProb));
+    std::memcpy(blob.data() + tab_bytes, order.data(), order.size() * sizeof(int));
+    e = ws.stage.copy_to_device(d_tab, blob.data(), blob.size(), s);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(base + lay.zero_off, 0, lay.zero_end - lay.zero_off, s);
   if (e != cudaSuccess) return note_cuda(e);
   {
@@ -586,10 +599,8 @@ mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *
                                                                           tiles);
     if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
   }
-  TcConfig cfg{128, 4, ch.grid};
-  cfg.max_bn = lay.bn;
   e = launch_tc(kTcE4m3, d_tab, nprobs, (int)lay.units, unit_map, nullptr, ws.ptr, lay.rows, cfg,
-                g_ctx.d_err, s);
+                g_ctx.d_err, s, d_order);
   if (e != cudaSuccess) return note_cuda(e);
   {
     TraceScope ts("ozaki_sum", s);
@@ -628,12 +639,13 @@ size_t ozaki_scratch_bytes(int64_t n, int64_t m, int64_t p, int S) {
   const int64_t kt_all = ceil_div(m, 128) + chunks;  // K blocks over all chunks (bound)
   // S digit slices per operand and the accuracy gate's slice (counted whether
   // or not the gate is on), their level sums and the gate's planes, maxima,
-  // table and map
+  // table, the CTAs' unit lists and the unit map
   const int64_t SS = S + 1;
   const int64_t rows = (ceil_div(n, kTcBM) * kTcBM + ceil_div(p, 128) * 256) * SS * kt_all;
   return (size_t)rows * kPackRowBytes + (size_t)chunks * SS * (n * p + 64) * sizeof(float) +
          (size_t)(n + p) * 12 + (size_t)chunks * SS * ceil_div(n, kTcBM) * ceil_div(p, 128) * 4 +
-         (size_t)chunks * SS * sizeof(SplitProb) + ((size_t)1 << 20);
+         (size_t)chunks * SS * sizeof(SplitProb) +
+         (size_t)chunks * SS * ceil_div(n, kTcBM) * ceil_div(p, 128) * 4 + ((size_t)1 << 20);
 }
 
 }  // namespace mm

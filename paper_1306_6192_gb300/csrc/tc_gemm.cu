@@ -50,6 +50,10 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+#include <utility>
+#include <vector>
+
 #include "tc_ptx.cuh"
 
 namespace mm {
@@ -165,7 +169,7 @@ template <int BKB, int STAGES, int KIND, int MAXBN>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__restrict__ probs,
                int nprobs, const int *__restrict__ unit_map, const int *__restrict__ flags,
-               int total_units, int *err) {
+               int total_units, const int *__restrict__ order, int *err) {
   using L = TcLayout<BKB, STAGES, KIND, MAXBN>;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -183,6 +187,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
   float *stage_buf = reinterpret_cast<float *>(smem + L::kStageOffset);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // this CTA's work units, the same sequence for every role: the host's list
+  // (grid + 1 offsets, then the units), or units c, c + grid, ...
+  const int *ulist = order ? order + gridDim.x + 1 : nullptr;
+  const int i_first = order ? order[blockIdx.x] : (int)blockIdx.x;
+  const int i_end = order ? order[blockIdx.x + 1] : total_units;
+  const int i_step = order ? 1 : (int)gridDim.x;
 
   if (warp == 0) {
     tmem_alloc(smem_u32(tmem_holder), kTmemCols);
@@ -215,7 +225,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
       uint32_t phase = 0;
       uint32_t issued = 0;  // stage loads armed so far
       bool ok = true;
-      for (int u = blockIdx.x; u < total_units && ok; u += gridDim.x) {
+      for (int ui = i_first; ui < i_end && ok; ui += i_step) {
+        const int u = ulist ? ulist[ui] : ui;
         const UnitCoord tc = decode_unit(probs, nprobs, unit_map, u);
         const SplitProb &pr = probs[tc.g];
         const int bn = pr.bn;
@@ -272,7 +283,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
       int acc = 0;
       uint32_t acc_phase = 0;
       bool ok = true, issued = false;
-      for (int u = blockIdx.x; u < total_units && ok; u += gridDim.x) {
+      for (int ui = i_first; ui < i_end && ok; ui += i_step) {
+        const int u = ulist ? ulist[ui] : ui;
         const UnitCoord tc = decode_unit(probs, nprobs, unit_map, u);
         const SplitProb &pr = probs[tc.g];
         const int kiters = (int)(((int64_t)pr.m * L::kElemBytes + BKB - 1) / BKB);
@@ -351,7 +363,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
     int acc = 0;
     uint32_t acc_phase = 0;
     const int et = threadIdx.x - 64;  // 0..127 over the epilogue warps
-    for (int u = blockIdx.x; u < total_units; u += gridDim.x) {
+    for (int ui = i_first; ui < i_end; ui += i_step) {
+      const int u = ulist ? ulist[ui] : ui;
       const UnitCoord tc = decode_unit(probs, nprobs, unit_map, u);
       const SplitProb &pr = probs[tc.g];
       // column exponents of this tile, once per tile, while the MMAs run
@@ -519,7 +532,7 @@ cudaError_t encode_pack_map(CUtensorMap *map, void *base, int64_t rows, int bkb)
 template <int BKB, int STAGES, int KIND, int MAXBN>
 cudaError_t launch_tc_t(const SplitProb *d_probs, int nprobs, const int *unit_map,
                         const int *flags, int total_units, void *pack_base, int64_t pack_rows,
-                        int grid, int *d_err, cudaStream_t s) {
+                        int grid, int *d_err, cudaStream_t s, const int *order) {
   using L = TcLayout<BKB, STAGES, KIND, MAXBN>;
   static_assert(L::kSmemBytes <= 232448, "shared memory budget");
   // one CTA per SM: the kernel allocates all 512 TMEM columns
@@ -536,13 +549,57 @@ cudaError_t launch_tc_t(const SplitProb *d_probs, int nprobs, const int *unit_ma
   if (e != cudaSuccess) return e;
   TraceScope ts(KIND == kTcE4m3 ? "fp8_tc" : "split_tc", s);
   tc_gemm_kernel<BKB, STAGES, KIND, MAXBN><<<grid, kThreads, L::kSmemBytes, s>>>(
-      map, d_probs, nprobs, unit_map, flags, total_units, d_err);
+      map, d_probs, nprobs, unit_map, flags, total_units, order, d_err);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 int tc_grid(const TcConfig &cfg) { return cfg.grid > 0 ? cfg.grid : sm_count(); }
+
+int tc_launch_grid(const TcConfig &cfg, int64_t total_units) {
+  const int g = tc_grid(cfg);
+  return total_units < g ? (int)std::max<int64_t>(total_units, 1) : g;
+}
+
+void tc_unit_order(const SplitProb *tab, int nprobs, int grid, std::vector<int> &out) {
+  int64_t total = 0;
+  for (int g = 0; g < nprobs; g++) total += split_units(tab[g]);
+  out.assign((size_t)grid + 1 + (size_t)total, 0);
+  if (grid <= 0) return;
+  // (expected free time, CTA): a binary heap on the earliest time, lowest CTA
+  std::vector<std::pair<int64_t, int>> heap;
+  heap.reserve((size_t)grid);
+  for (int c = 0; c < grid; c++) heap.emplace_back(0, c);
+  auto later = [](const std::pair<int64_t, int> &a, const std::pair<int64_t, int> &b) {
+    return a.first != b.first ? a.first > b.first : a.second > b.second;
+  };
+  std::make_heap(heap.begin(), heap.end(), later);
+  std::vector<int> owner((size_t)total);
+  std::vector<int> count((size_t)grid, 0);
+  for (int g = 0; g < nprobs; g++) {
+    const SplitProb &pr = tab[g];
+    const int64_t units = split_units(pr);
+    for (int64_t t = 0; t < units; t++) {
+      int64_t rows = pr.kt;  // K pack rows of the unit
+      if (pr.split_s > 1 && t >= pr.split_from) {
+        const int64_t h = (t - pr.split_from) % pr.split_s;
+        rows = (h + 1) * pr.kt / pr.split_s - h * pr.kt / pr.split_s;
+      }
+      std::pop_heap(heap.begin(), heap.end(), later);
+      auto &slot = heap.back();
+      owner[(size_t)(pr.unit_start + t)] = slot.second;
+      count[(size_t)slot.second]++;
+      slot.first += rows + 1;
+      std::push_heap(heap.begin(), heap.end(), later);
+    }
+  }
+  int *off = out.data();
+  for (int c = 0; c < grid; c++) off[c + 1] = off[c] + count[(size_t)c];
+  std::vector<int> fill(off, off + grid);
+  int *list = off + grid + 1;
+  for (int64_t u = 0; u < total; u++) list[fill[(size_t)owner[(size_t)u]]++] = (int)u;
+}
 
 TcTail tc_tail_plan(int64_t tiles, int grid, int kt, int bn, int64_t m, double products) {
   TcTail best{(int)tiles, 1};
@@ -598,13 +655,12 @@ size_t tc_tail_bytes(const TcTail &t, int64_t tiles, int bn) {
 
 cudaError_t launch_tc(TcKind kind, const SplitProb *d_probs, int nprobs, int total_units,
                       const int *unit_map, const int *flags, void *pack_base, int64_t pack_rows,
-                      const TcConfig &cfg, int *d_err, cudaStream_t s) {
+                      const TcConfig &cfg, int *d_err, cudaStream_t s, const int *order) {
   if (total_units <= 0) return cudaSuccess;
   if (pack_rows <= 0 || pack_rows > 0x7fffffffLL) return cudaErrorInvalidValue;
-  int grid = tc_grid(cfg);
-  if (grid > total_units) grid = total_units;
+  const int grid = tc_launch_grid(cfg, total_units);
   const int *mp = unit_map;
-#define MM_TC_ARGS d_probs, nprobs, mp, flags, total_units, pack_base, pack_rows, grid, d_err, s
+#define MM_TC_ARGS d_probs, nprobs, mp, flags, total_units, pack_base, pack_rows, grid, d_err, s, order
   cudaError_t e = cudaErrorInvalidValue;
   const bool narrow = cfg.max_bn <= 128;  // every N tile of the table fits 128
   if (kind == kTcE4m3) e = launch_tc_t<128, 4, kTcE4m3, 256>(MM_TC_ARGS);

@@ -129,7 +129,18 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
   size_t map_ints = 0;
   for (auto &G : groups)
     if (G.tab.size() > 1) map_ints += (size_t)(G.units + G.packs + G.vers);
-  const size_t map_off = (tab_off + ntab * sizeof(SplitProb) + 255) & ~(size_t)255;
+  // the work units of each CTA for groups of several problems (their units
+  // differ in length), written with the table in one copy
+  std::vector<int> orders[2];
+  size_t order_ints = 0;
+  for (int gi = 0; gi < 2; gi++) {
+    Group &G = groups[gi];
+    if (G.tab.size() <= 1) continue;
+    tc_unit_order(G.tab.data(), (int)G.tab.size(), tc_launch_grid(G.cfg, G.units), orders[gi]);
+    order_ints += orders[gi].size();
+  }
+  const size_t tab_bytes = (ntab * sizeof(SplitProb) + 15) & ~(size_t)15;
+  const size_t map_off = (tab_off + tab_bytes + order_ints * sizeof(int) + 255) & ~(size_t)255;
   const size_t tpart_off = (map_off + map_ints * sizeof(int) + 255) & ~(size_t)255;
   const size_t need = tpart_off + tail_parts;
   cudaError_t e = ws.reserve(need, s);
@@ -150,7 +161,20 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
       all.push_back(sp);
     }
   SplitProb *d_tab = reinterpret_cast<SplitProb *>(base + tab_off);
-  e = ws.stage.copy_to_device(d_tab, all.data(), all.size() * sizeof(SplitProb), s);
+  int *d_orders = reinterpret_cast<int *>(base + tab_off + tab_bytes);
+  if (order_ints == 0) {
+    e = ws.stage.copy_to_device(d_tab, all.data(), all.size() * sizeof(SplitProb), s);
+  } else {
+    std::vector<uint8_t> blob(tab_bytes + order_ints * sizeof(int), 0);
+    std::memcpy(blob.data(), all.data(), all.size() * sizeof(SplitProb));
+    size_t at = tab_bytes;
+    for (auto &o : orders) {
+      if (o.empty()) continue;
+      std::memcpy(blob.data() + at, o.data(), o.size() * sizeof(int));
+      at += o.size() * sizeof(int);
+    }
+    e = ws.stage.copy_to_device(d_tab, blob.data(), blob.size(), s);
+  }
   if (e != cudaSuccess) return note_cuda(e);
   e = cudaMemsetAsync(base + scal_off, 0, zero_end - scal_off, s);
   if (e != cudaSuccess) return note_cuda(e);
@@ -166,6 +190,11 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
     const int np = (int)G.tab.size();
     off += G.tab.size();
     int *tile_map = nullptr, *pack_map = nullptr, *ver_map = nullptr;
+    const int *order = nullptr;
+    if (!orders[gi].empty()) {
+      order = d_orders;
+      d_orders += orders[gi].size();
+    }
     if (np > 1) {
       tile_map = maps;
       pack_map = tile_map + G.units;
@@ -183,7 +212,7 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
       e = launch_split_pack(G.kind, kPackFix, dt, np, (int)G.packs, pack_map, flags, any, base, s);
     if (e == cudaSuccess)
       e = launch_tc(G.kind, dt, np, (int)G.units, tile_map, flags, base, rows, G.cfg, g_ctx.d_err,
-                    s);
+                    s, order);
     if (e != cudaSuccess) return note_cuda(e);
   }
   return MM_OK;
