@@ -347,7 +347,7 @@ mm_status mm_measure_fma_peak(mm_dtype dt, int64_t iters, double *flops_per_s);
  * on its stream; mm_trace_read returns the launch count and summed device
  * time (ms) of the kernel named `kernel` ("simt_f32", "dgemm_f64",
  * "split_maps", "split_pack", "split_verify", "split_fix", "split_tc", "fused_tc",
- * "fp8_pack", "fp8_tc", "check_f64", "ozaki_max", "ozaki_map", "ozaki_digits",
+ * "fp8_pack", "fp8_tc", "fp8_blk", "check_f64", "ozaki_max", "ozaki_map", "ozaki_digits",
  * "ozaki_sum", "ozaki_gate", "add", "diag", "cplx_planes", "cplx_combine") since
  * the last reset.  Reading synchronises the recorded events. */
 mm_status mm_trace_enable(int on);

@@ -8,12 +8,22 @@
 // the significance of blocks whose values are far below the row's largest.
 //
 // Kernels:
-//   fp8blk_pack_kernel  one block per pack tile (128 rows of A, or 128
+//   fp8blk_pack_kernel  one block per pack tile (128 rows of A, or 256
 //                       columns of B, by one K block): the block's row /
-//                       column maxima, the exponents (int32 per row or
-//                       column and K block, padded to whole tiles), and the
-//                       e4m3 pack rows (the layout of mm_internal.h, bn = 128).
-//   fp8blk_gemm_kernel  persistent, warp-specialised: a TMA producer (pack
+//                       column maxima, the factors 2^e (per row or column
+//                       and K block, padded to whole tiles), block 0's maxima
+//                       as the row / column scale words, and the e4m3 pack
+//                       rows (the layout of mm_internal.h, bn = 256).
+//   fp8blk_flag_kernel  per row tile of A and 128-column sub-tile of B: 1
+//                       when every row (column) has the same exponent in all
+//                       K blocks.
+//   tc_gemm_kernel      (tc_gemm.cu, e4m3, 128 x 256 tiles) the tiles whose
+//                       row tile and both column sub-tiles are flagged: all
+//                       K blocks accumulated in tensor memory, one factor per
+//                       row and column applied in the epilogue; it skips the
+//                       other tiles.
+//   fp8blk_gemm_kernel  the other tiles, as 128 x 128 sub-tiles; persistent,
+//                       warp-specialised: a TMA producer (pack
 //                       tiles of each K block into a shared-memory ring, and
 //                       the block's exponents into a second ring), one thread
 //                       issuing four tcgen05.mma kind::f8f6f4 per K block
@@ -22,7 +32,10 @@
 //                       block's FP32 partial product (tcgen05.ld), multiply it
 //                       by 2^(e_i + e_j) exactly and add it into registers,
 //                       then store the tile.  The K blocks are added in order
-//                       with round-to-nearest FP32 additions.
+//                       with round-to-nearest FP32 additions.  A tile whose
+//                       rows and columns keep one exponent along K (flagged
+//                       by fp8blk_flag_kernel) accumulates all its blocks in
+//                       one accumulator instead and is unscaled once.
 // The error of the result against the FP64 oracle is measured and reported;
 // there is no tolerance for it.  The product is the paper's (Section
 // "Implementacje algorytmow"); the FP8 path is this library's, not the
@@ -41,7 +54,8 @@ namespace {
 using namespace tcx;
 
 constexpr int kBK = 128;              // e4m3 values per K block (one pack row)
-constexpr int kBN = 128;              // N tile
+constexpr int kBN = 128;              // N tile of the blockwise kernel
+constexpr int kPackBN = 256;          // columns of B per pack tile (two kBN sub-tiles)
 constexpr int kStages = 6;            // operand ring
 constexpr int kEStages = 8;           // scale-factor ring
 constexpr int kAccs = 4;              // 128-column accumulators in 512 columns
@@ -72,6 +86,19 @@ __device__ __forceinline__ int blk_exponent(uint32_t max_bits) {
   return (f > 0.0f && f <= 3.402823466e38f) ? scale_exponent(max_bits) - 7 : 0;
 }
 
+// Exponent of a block: its own, or the whole row's (column's) when the
+// block's largest magnitude lies within one binade of the row's (an all-zero
+// block too), so that the blocks of rows without a wide spread of magnitudes
+// share one factor and their tiles can be accumulated along K in tensor
+// memory; a block two or more binades below keeps its own.  Rows with a NaN
+// or an infinity keep the blocks' own exponents.
+__device__ __forceinline__ int pick_exponent(uint32_t blk_max, uint32_t whole_max) {
+  const int eb = blk_exponent(blk_max);
+  if (!(__uint_as_float(whole_max) <= 3.402823466e38f)) return eb;
+  const int ew = blk_exponent(whole_max);
+  return (blk_max == 0 || eb >= ew - 1) ? ew : eb;
+}
+
 __device__ __forceinline__ uint32_t to_e4m3x4(float4 x, int e) {
   const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(
       make_float2(scale_pow2(x.x, -e), scale_pow2(x.y, -e)), __NV_SATFINITE, __NV_E4M3);
@@ -93,6 +120,83 @@ __device__ __forceinline__ float *fac_a(const SplitProb &pr) { return reinterpre
 __device__ __forceinline__ float *fac_b(const SplitProb &pr) { return reinterpret_cast<float *>(pr.pB); }
 
 __device__ __forceinline__ float pow2f(int e) { return scale_pow2(1.0f, e); }
+
+// Whole-row maxima of A and whole-column maxima of B (bit patterns of |x|,
+// which order like the magnitudes) into the problem's sA / tB (zeroed before
+// the launch).  Items of a problem, from the prefix `split_from` of its entry
+// in the blockwise table: ceil(n / 8) items of 8 rows of A (a warp per row,
+// 16-byte loads where the row allows), then strips of 128 columns x 256 rows
+// of B (four columns per lane), merged with atomicMax.
+constexpr int kMaxRows = 8, kMaxStrip = 128, kMaxChunk = 256;
+
+__host__ __device__ inline int64_t max_items(int64_t n, int64_t m, int64_t p) {
+  return (n + kMaxRows - 1) / kMaxRows +
+         ((p + kMaxStrip - 1) / kMaxStrip) * ((m + kMaxChunk - 1) / kMaxChunk);
+}
+
+__device__ __forceinline__ uint32_t absmax4(float4 v) {
+  return max(max(__float_as_uint(v.x) & 0x7fffffffu, __float_as_uint(v.y) & 0x7fffffffu),
+             max(__float_as_uint(v.z) & 0x7fffffffu, __float_as_uint(v.w) & 0x7fffffffu));
+}
+
+__global__ void __launch_bounds__(256)
+fp8blk_max_kernel(const SplitProb *__restrict__ probs, int nprobs) {
+  const int item = blockIdx.x;
+  const int g =
+      find_problem(probs, nprobs, nullptr, item, [](const SplitProb &q) { return q.split_from; });
+  const SplitProb &pr = probs[g];
+  const int64_t local = item - pr.split_from;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t items_a = (pr.n + kMaxRows - 1) / kMaxRows;
+  if (local < items_a) {
+    const int64_t i = local * kMaxRows + warp;
+    if (i >= pr.n) return;
+    const float *row = pr.A + i * pr.m;
+    uint32_t mx = 0;
+    if ((reinterpret_cast<uintptr_t>(pr.A) & 15u) == 0 && (pr.m & 3) == 0) {
+      const float4 *r4 = reinterpret_cast<const float4 *>(row);
+      for (int64_t k = lane; k < pr.m / 4; k += 32) mx = max(mx, absmax4(__ldg(r4 + k)));
+    } else {
+      for (int64_t k = lane; k < pr.m; k += 32) mx = max(mx, __float_as_uint(row[k]) & 0x7fffffffu);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) pr.sA[i] = mx;
+    return;
+  }
+  __shared__ uint32_t part[8][kMaxStrip];
+  const int64_t b = local - items_a;
+  const int64_t strips = (pr.p + kMaxStrip - 1) / kMaxStrip;
+  const int64_t c0 = (b % strips) * kMaxStrip + 4 * lane, r0 = (b / strips) * kMaxChunk;
+  const bool vec = (reinterpret_cast<uintptr_t>(pr.B) & 15u) == 0 && (pr.p & 3) == 0;
+  uint32_t mx[4] = {0, 0, 0, 0};
+  for (int r = warp; r < kMaxChunk; r += 8) {
+    const int64_t k = r0 + r;
+    if (k >= pr.m) break;
+    const float *src = pr.B + k * pr.p + c0;
+    if (vec && c0 + 4 <= pr.p) {
+      const float4 v = __ldg(reinterpret_cast<const float4 *>(src));
+      mx[0] = max(mx[0], __float_as_uint(v.x) & 0x7fffffffu);
+      mx[1] = max(mx[1], __float_as_uint(v.y) & 0x7fffffffu);
+      mx[2] = max(mx[2], __float_as_uint(v.z) & 0x7fffffffu);
+      mx[3] = max(mx[3], __float_as_uint(v.w) & 0x7fffffffu);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; e++)
+        if (c0 + e < pr.p) mx[e] = max(mx[e], __float_as_uint(src[e]) & 0x7fffffffu);
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 4; e++) part[warp][4 * lane + e] = mx[e];
+  __syncthreads();
+  if (threadIdx.x < kMaxStrip) {
+    uint32_t v = 0;
+#pragma unroll
+    for (int w = 0; w < 8; w++) v = max(v, part[w][threadIdx.x]);
+    const int64_t col = (b % strips) * kMaxStrip + threadIdx.x;
+    if (col < pr.p) atomicMax(&pr.tB[col], v);
+  }
+}
 
 __global__ void __launch_bounds__(256)
 fp8blk_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *__restrict__ map,
@@ -138,25 +242,25 @@ fp8blk_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *_
       uint32_t mx = max(max(absb(xs[it].x), absb(xs[it].y)), max(absb(xs[it].z), absb(xs[it].w)));
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      const int e = blk_exponent(mx);
+      const int e = pick_exponent(mx, pr.sA[(int64_t)mt * kTcBM + r]);
       if (lane == 0) fac_a(pr)[(int64_t)kb * pr.mt * kTcBM + (int64_t)mt * kTcBM + r] = pow2f(e);
       pack[(base + r) * kQuads + lane] = to_e4m3x4(xs[it], e);
     }
   } else {
-    // B tile (nt, kb): 128 columns x 128 k, transposed through shared memory
+    // B tile (nt, kb): 256 columns x 128 k, transposed through shared memory
     // 64 columns at a time; one exponent per column of the block
     const int b = local - pr.mt * pr.kt;
     const int nt = b / pr.kt, kb = b % pr.kt;
-    const int64_t base = pr.b_row0 + (int64_t)b * kBN;
+    const int64_t base = pr.b_row0 + (int64_t)b * kPackBN;
     const bool vec = al16(pr.B) && (pr.p & 3) == 0;
-    for (int c0 = 0; c0 < kBN; c0 += 64) {
+    for (int c0 = 0; c0 < kPackBN; c0 += 64) {
       float4 vs[8];
 #pragma unroll
       for (int it = 0; it < 8; it++) {
         const int q = tid + it * 256;  // 128 k rows x 16 vectors of 4 columns
         const int kk = q / 16, c4 = q % 16;
         const int64_t k = (int64_t)kb * kBK + kk;
-        const int64_t j = (int64_t)nt * kBN + c0 + 4 * c4;
+        const int64_t j = (int64_t)nt * kPackBN + c0 + 4 * c4;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (k < pr.m) {
           const float *src = pr.B + k * pr.p + j;
@@ -185,9 +289,9 @@ fp8blk_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *_
         uint32_t mx = 0;
 #pragma unroll 8
         for (int kk = 0; kk < kBK; kk++) mx = max(mx, absb(tile[kk][tid]));
-        const int e = blk_exponent(mx);
+        const int e = pick_exponent(mx, pr.tB[(int64_t)nt * kPackBN + c0 + tid]);
         colexp[tid] = e;
-        fac_b(pr)[(int64_t)kb * pr.nt * kBN + (int64_t)nt * kBN + c0 + tid] = pow2f(e);
+        fac_b(pr)[(int64_t)kb * pr.nt * kPackBN + (int64_t)nt * kPackBN + c0 + tid] = pow2f(e);
       }
       __syncthreads();
       for (int q = tid; q < 64 * (kBK / 16); q += 256) {
@@ -208,6 +312,45 @@ fp8blk_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *_
   }
 }
 
+
+// Tiles whose exponents do not change along K.  For row tile mt of A (items
+// [0, mt) of a problem) or column tile nt of B (items [mt, mt + nt)), flag 1
+// when every row (column) of the tile has the same exponent in all its K
+// blocks.  A product tile whose row tile and column tile are both flagged
+// takes the uniform form of the tensor-core kernel: all its K blocks are
+// accumulated in tensor memory and the factor 2^(e_i + e_j), the same for
+// every block, is applied once; elsewhere each block is unscaled on its own.
+// flags: the problem's `cnt` array, mt + nt words; item prefix `ver_start`.
+__global__ void __launch_bounds__(128)
+fp8blk_flag_kernel(const SplitProb *__restrict__ probs, int nprobs) {
+  const int item = blockIdx.x;
+  const int g =
+      find_problem(probs, nprobs, nullptr, item, [](const SplitProb &q) { return q.ver_start; });
+  const SplitProb &pr = probs[g];
+  const int local = item - pr.ver_start;
+  const bool is_a = local < pr.mt;
+  const int tile = is_a ? local : local - pr.mt;
+  const int64_t width = (int64_t)(is_a ? pr.mt : pr.nt) * 128;  // padded rows per K block
+  const float *f = (is_a ? fac_a(pr) : fac_b(pr)) + (int64_t)tile * 128 + threadIdx.x;
+  const float f0 = f[0];
+  // a row (column) with a NaN or an infinity keeps its blocks' own factors
+  const uint32_t whole = (is_a ? pr.sA : pr.tB)[(int64_t)tile * 128 + threadIdx.x];
+  bool same = __uint_as_float(whole) <= 3.402823466e38f;
+  for (int kb = 1; kb < pr.kt; kb++) same &= f[(int64_t)kb * width] == f0;
+  same = __syncthreads_and(same);
+  if (threadIdx.x == 0) pr.cnt[local] = same ? 1 : 0;
+}
+
+__device__ __forceinline__ bool tile_uniform(const SplitProb &pr, int mt, int nt) {
+  return pr.cnt[mt] != 0 && pr.cnt[pr.mt + nt] != 0;
+}
+
+// The 128 x 256 tile that holds sub-tile (mt, nt) is uniform: the tensor-core
+// kernel of tc_gemm.cu computes it (one factor per row and column), so this
+// kernel skips it in every role.
+__device__ __forceinline__ bool pair_uniform(const SplitProb &pr, int mt, int nt) {
+  return pr.cnt[mt] != 0 && pr.cnt[pr.mt + (nt & ~1)] != 0 && pr.cnt[pr.mt + (nt | 1)] != 0;
+}
 
 // Tile t of problem g in bands of group_m row tiles (as the split path).
 __device__ __forceinline__ void blk_unit(const SplitProb *__restrict__ probs, int nprobs,
@@ -280,8 +423,11 @@ fp8blk_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__
         int g, mt, nt;
         blk_unit(probs, nprobs, unit_map, u, g, mt, nt);
         const SplitProb &pr = probs[g];
+        if (pair_uniform(pr, mt, nt)) continue;
         const int64_t abase = pr.a_row0 + (int64_t)mt * pr.kt * kTcBM;
-        const int64_t bbase = pr.b_row0 + (int64_t)nt * pr.kt * kBN;
+        // sub-tile nt of 128 columns: half nt & 1 of pack tile nt >> 1
+        const int64_t bbase = pr.b_row0 + (int64_t)(nt >> 1) * pr.kt * kPackBN + (nt & 1) * kBN;
+        const bool uni = tile_uniform(pr, mt, nt);
         for (int kb = 0; kb < pr.kt; kb++) {
           if (!mbar_wait(empty_bar(stage), phase ^ 1u, err, 21, true, kWaitNs)) {
             ok = false;
@@ -291,12 +437,13 @@ fp8blk_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__
           ++issued;
           const uint32_t st = sbase + (uint32_t)(stage * Lay::kStage);
           tma_load_2d(st, &tmap, 0, (int)(abase + (int64_t)kb * kTcBM), full_bar(stage));
-          tma_load_2d(st + Lay::kA, &tmap, 0, (int)(bbase + (int64_t)kb * kBN), full_bar(stage));
+          tma_load_2d(st + Lay::kA, &tmap, 0, (int)(bbase + (int64_t)kb * kPackBN), full_bar(stage));
           if (++stage == kStages) {
             stage = 0;
             phase ^= 1u;
           }
-          // the block's row and column exponents
+          // the block's row and column factors (a uniform tile: block 0's only)
+          if (uni && kb > 0) continue;
           if (!mbar_wait(eempty_bar(es), ephase ^ 1u, err, 21, true, kWaitNs)) {
             ok = false;
             break;
@@ -330,9 +477,14 @@ fp8blk_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__
       for (int u = blockIdx.x; u < total_units && ok; u += gridDim.x) {
         int g, mt, nt;
         blk_unit(probs, nprobs, unit_map, u, g, mt, nt);
+        if (pair_uniform(probs[g], mt, nt)) continue;
         const int kt = probs[g].kt;
+        // a uniform tile accumulates all its K blocks in one accumulator;
+        // otherwise each block takes an accumulator of its own
+        const bool uni = tile_uniform(probs[g], mt, nt);
         for (int kb = 0; kb < kt; kb++) {
-          if (!mbar_wait(acce_bar(acc), aphase ^ 1u, err, 22, true, kWaitNs) ||
+          const bool fresh = !uni || kb == 0;  // the block starts an accumulator
+          if ((fresh && !mbar_wait(acce_bar(acc), aphase ^ 1u, err, 22, true, kWaitNs)) ||
               !mbar_wait(full_bar(stage), phase, err, 22, true, kWaitNs)) {
             ok = false;
             break;
@@ -344,18 +496,20 @@ fp8blk_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__
 #pragma unroll
           for (int kk = 0; kk < kBK / 32; kk++) {  // 32 e4m3 = 32 bytes per MMA
             const uint64_t adv = (uint64_t)(kk * 32) >> 4;
-            tc_mma_f8(d_tmem, a0 + adv, b0 + adv, idesc, kk != 0 ? 1u : 0u);
+            tc_mma_f8(d_tmem, a0 + adv, b0 + adv, idesc, (kk != 0 || !fresh) ? 1u : 0u);
           }
           any = true;
           tc_commit(empty_bar(stage));
-          tc_commit(accf_bar(acc));
           if (++stage == kStages) {
             stage = 0;
             phase ^= 1u;
           }
-          if (++acc == kAccs) {
-            acc = 0;
-            aphase ^= 1u;
+          if (!uni || kb == kt - 1) {  // the accumulator is complete
+            tc_commit(accf_bar(acc));
+            if (++acc == kAccs) {
+              acc = 0;
+              aphase ^= 1u;
+            }
           }
         }
       }
@@ -377,11 +531,14 @@ fp8blk_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__
       int g, mt, nt;
       blk_unit(probs, nprobs, unit_map, u, g, mt, nt);
       const SplitProb &pr = probs[g];
+      if (pair_uniform(pr, mt, nt)) continue;
       // column pairs, packed for the paired FP32 instructions
       uint64_t sum[kWCols / 2];
 #pragma unroll
       for (int c = 0; c < kWCols / 2; c++) sum[c] = 0ull;
-      for (int kb = 0; kb < pr.kt; kb++) {
+      // a uniform tile's accumulator holds all its K blocks (one factor slot)
+      const int nacc = tile_uniform(pr, mt, nt) ? 1 : pr.kt;
+      for (int kb = 0; kb < nacc; kb++) {
         bool w = mbar_wait(efull_bar(es), ephase, err, 23, true, kWaitNs) &&
                  mbar_wait(accf_bar(acc), aphase, err, 23, true, kWaitNs);
         // agreement within the warp (tcgen05.ld is warp-collective); warps
@@ -487,15 +644,114 @@ cudaError_t blk_pack_map(CUtensorMap *map, void *base, int64_t rows) {
 
 }  // namespace
 
-size_t fp8_blocks_scratch_bytes(int64_t n, int64_t m, int64_t p) {
-  if (n <= 0 || m <= 0 || p <= 0) return 0;
-  const int64_t mt = ceil_div(n, kTcBM), nt = ceil_div(p, kBN), kt = ceil_div(m, kBK);
-  return (size_t)(mt * kTcBM + nt * kBN) * kt * (kPackRowBytes + 4) + sizeof(SplitProb) + 1024;
+namespace {
+
+mm_status fp8_blocks_launch(Scratch &ws, std::vector<SplitProb> &blk, std::vector<SplitProb> &tc,
+                            int64_t rows, int64_t exps, int64_t maxw, int64_t blk_units,
+                            int64_t tc_units, int64_t packs, int64_t flag_items,
+                            int64_t max_items_all, cudaStream_t s) {
+  if (rows > 0x7fffffffLL || blk_units > 0x7fffffffLL || packs > 0x7fffffffLL ||
+      flag_items > 0x7fffffffLL)
+    return MM_EINVAL;
+  const int np = (int)blk.size();
+  // layout: packs | factors (FP32) | maxima words | tile flags | both tables
+  // (one copy) | unit maps and the pack map
+  const size_t pack_bytes = (size_t)rows * kPackRowBytes;
+  const size_t exp_off = (pack_bytes + 255) & ~(size_t)255;
+  const size_t max_off = (exp_off + (size_t)exps * 4 + 255) & ~(size_t)255;
+  const size_t flag_off = (max_off + (size_t)maxw * 4 + 255) & ~(size_t)255;
+  const size_t tab_off = (flag_off + (size_t)flag_items * 4 + 255) & ~(size_t)255;
+  const size_t tab_bytes = (size_t)np * sizeof(SplitProb);
+  const size_t map_off = (tab_off + 2 * tab_bytes + 255) & ~(size_t)255;
+  const size_t map_ints = np > 1 ? (size_t)(blk_units + tc_units + packs) : 0;
+  cudaError_t e = ws.reserve(map_off + map_ints * sizeof(int), s);
+  if (e != cudaSuccess) return note_cuda(e);
+  uint8_t *base = static_cast<uint8_t *>(ws.ptr);
+  for (int g = 0; g < np; g++) {
+    for (SplitProb *sp : {&blk[(size_t)g], &tc[(size_t)g]}) {
+      sp->pA = reinterpret_cast<uint32_t *>(base + exp_off) + (uintptr_t)sp->pA;
+      sp->pB = reinterpret_cast<uint32_t *>(base + exp_off) + (uintptr_t)sp->pB;
+      sp->sA = reinterpret_cast<uint32_t *>(base + max_off) + (uintptr_t)sp->sA;
+      sp->tB = reinterpret_cast<uint32_t *>(base + max_off) + (uintptr_t)sp->tB;
+    }
+    blk[(size_t)g].cnt = reinterpret_cast<int *>(base + flag_off) + (uintptr_t)blk[(size_t)g].cnt;
+    tc[(size_t)g].cnt = blk[(size_t)g].cnt;  // the tensor-core kernel reads the same flags
+  }
+  SplitProb *d_blk = reinterpret_cast<SplitProb *>(base + tab_off);
+  SplitProb *d_tc = d_blk + np;
+  {
+    std::vector<uint8_t> blob(2 * tab_bytes);
+    std::memcpy(blob.data(), blk.data(), tab_bytes);
+    std::memcpy(blob.data() + tab_bytes, tc.data(), tab_bytes);
+    e = ws.stage.copy_to_device(d_blk, blob.data(), blob.size(), s);
+  }
+  // whole-row and whole-column maxima first (zeroed: columns merge by atomicMax)
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + max_off, 0, (size_t)maxw * 4, s);
+  if (e != cudaSuccess) return note_cuda(e);
+  {
+    TraceScope ts("fp8_max", s);
+    fp8blk_max_kernel<<<(unsigned)max_items_all, 256, 0, s>>>(d_blk, np);
+    if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
+  }
+  int *blk_map = nullptr, *tc_map = nullptr, *pack_map = nullptr;
+  if (np > 1) {
+    blk_map = reinterpret_cast<int *>(base + map_off);
+    tc_map = blk_map + blk_units;
+    pack_map = tc_map + tc_units;
+    e = launch_split_maps(d_blk, np, blk_map, nullptr, nullptr, s);
+    if (e == cudaSuccess) e = launch_split_maps(d_tc, np, tc_map, pack_map, nullptr, s);
+    if (e != cudaSuccess) return note_cuda(e);
+  }
+  {
+    TraceScope ts("fp8_pack", s);
+    fp8blk_pack_kernel<<<(unsigned)packs, 256, 0, s>>>(d_tc, np, pack_map,
+                                                       static_cast<uint32_t *>(ws.ptr));
+    if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
+    fp8blk_flag_kernel<<<(unsigned)flag_items, 128, 0, s>>>(d_blk, np);
+    if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
+  }
+  // the uniform 128 x 256 tiles: one factor per row and column
+  TcConfig cfg{128, 4, 0};
+  cfg.max_bn = kPackBN;
+  e = launch_tc(kTcE4m3, d_tc, np, (int)tc_units, tc_map, nullptr, ws.ptr, rows, cfg, g_ctx.d_err,
+                s, nullptr, 1);
+  if (e != cudaSuccess) return note_cuda(e);
+  // the other tiles, K block by K block
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(fp8blk_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    Lay::kSmem);
+  });
+  if (attr_err != cudaSuccess) return note_cuda(attr_err);
+  CUtensorMap map;
+  if ((e = blk_pack_map(&map, ws.ptr, rows)) != cudaSuccess) return note_cuda(e);
+  const int grid = (int)std::min<int64_t>(blk_units, sm_count());
+  TraceScope ts("fp8_blk", s);
+  fp8blk_gemm_kernel<<<grid, kThreads, Lay::kSmem, s>>>(map, d_blk, np, blk_map, (int)blk_units,
+                                                        g_ctx.d_err);
+  return note_cuda(cudaGetLastError());
 }
 
+}  // namespace
+
+size_t fp8_blocks_scratch_bytes(int64_t n, int64_t m, int64_t p) {
+  if (n <= 0 || m <= 0 || p <= 0) return 0;
+  const int64_t mt = ceil_div(n, kTcBM), nt = ceil_div(p, kPackBN), kt = ceil_div(m, kBK);
+  // packs and factors, maxima, tile flags, two tables, unit maps
+  return (size_t)(mt * kTcBM + nt * kPackBN) * kt * (kPackRowBytes + 4) +
+         (size_t)(mt * kTcBM + nt * kPackBN) * 4 + (size_t)(mt + 2 * nt) * 4 +
+         2 * sizeof(SplitProb) + (size_t)mt * nt * 12 + 4096;
+}
+
+// Two tables over the same packs: `blk` for the blockwise kernel (N sub-tiles
+// of 128 columns: nt = 2 x the pack tiles of B) and `tc` for the tensor-core
+// kernel of split_prep/tc_gemm (128 x 256 tiles, one factor per row and
+// column from the maxima words).  The pack kernel runs over `tc`.
 mm_status run_fp8_blocks(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s) {
-  std::vector<SplitProb> tab;
-  int64_t rows = 0, exps = 0, units = 0, packs = 0;
+  std::vector<SplitProb> blk, tc;
+  int64_t rows = 0, exps = 0, maxw = 0, blk_units = 0, tc_units = 0, packs = 0, flag_items = 0,
+          max_items_all = 0;
   for (int g = 0; g < count; g++) {
     const mm_problem &q = probs[g];
     if (q.n == 0 || q.p == 0) continue;
@@ -512,72 +768,48 @@ mm_status run_fp8_blocks(Scratch &ws, const mm_problem *probs, int count, cudaSt
     sp.n = (int32_t)q.n;
     sp.m = (int32_t)q.m;
     sp.p = (int32_t)q.p;
-    sp.bn = kBN;
     sp.group_m = 16;
     sp.mt = (int32_t)ceil_div(q.n, kTcBM);
-    sp.nt = (int32_t)ceil_div(q.p, kBN);
+    const int32_t ntp = (int32_t)ceil_div(q.p, kPackBN);  // pack tiles of B
     sp.kt = (int32_t)ceil_div(q.m, kBK);
     sp.a_row0 = rows;
     rows += (int64_t)sp.mt * sp.kt * kTcBM;
     sp.b_row0 = rows;
-    rows += (int64_t)sp.nt * sp.kt * kBN;
+    rows += (int64_t)ntp * sp.kt * kPackBN;
     sp.pA = reinterpret_cast<uint32_t *>((uintptr_t)exps);  // offsets, fixed below
     exps += (int64_t)sp.kt * sp.mt * kTcBM;
     sp.pB = reinterpret_cast<uint32_t *>((uintptr_t)exps);
-    exps += (int64_t)sp.kt * sp.nt * kBN;
-    sp.unit_start = (int32_t)units;
-    units += (int64_t)sp.mt * sp.nt;
+    exps += (int64_t)sp.kt * ntp * kPackBN;
+    sp.sA = reinterpret_cast<uint32_t *>((uintptr_t)maxw);
+    maxw += (int64_t)sp.mt * kTcBM;
+    sp.tB = reinterpret_cast<uint32_t *>((uintptr_t)maxw);
+    maxw += (int64_t)ntp * kPackBN;
     sp.pack_start = (int32_t)packs;
-    packs += (int64_t)sp.mt * sp.kt + (int64_t)sp.nt * sp.kt;
-    sp.split_s = 1;
-    tab.push_back(sp);
+    packs += (int64_t)sp.mt * sp.kt + (int64_t)ntp * sp.kt;
+    SplitProb b = sp, t = sp;
+    b.bn = kBN;
+    b.nt = 2 * ntp;
+    b.unit_start = (int32_t)blk_units;
+    blk_units += (int64_t)b.mt * b.nt;
+    b.ver_start = (int32_t)flag_items;  // uniform-exponent flags of its tiles
+    b.cnt = reinterpret_cast<int *>((uintptr_t)flag_items);  // offset, fixed below
+    flag_items += (int64_t)b.mt + b.nt;
+    b.split_s = 1;
+    b.split_from = (int32_t)max_items_all;  // prefix of its maxima items
+    max_items_all += max_items(q.n, q.m, q.p);
+    t.bn = kPackBN;
+    t.nt = ntp;
+    t.unit_start = (int32_t)tc_units;
+    tc_units += (int64_t)t.mt * t.nt;
+    t.split_from = t.mt * t.nt;
+    t.split_s = 1;
+    blk.push_back(b);
+    tc.push_back(t);
   }
-  if (tab.empty()) return MM_OK;
-  if (rows > 0x7fffffffLL || units > 0x7fffffffLL || packs > 0x7fffffffLL) return MM_EINVAL;
-  // layout: packs | exponents (int32) | table | item maps
-  const size_t pack_bytes = (size_t)rows * kPackRowBytes;
-  const size_t exp_off = (pack_bytes + 255) & ~(size_t)255;
-  const size_t tab_off = (exp_off + (size_t)exps * 4 + 255) & ~(size_t)255;
-  const size_t map_off = (tab_off + tab.size() * sizeof(SplitProb) + 255) & ~(size_t)255;
-  const size_t map_ints = tab.size() > 1 ? (size_t)(units + packs) : 0;
-  cudaError_t e = ws.reserve(map_off + map_ints * sizeof(int), s);
-  if (e != cudaSuccess) return note_cuda(e);
-  uint8_t *base = static_cast<uint8_t *>(ws.ptr);
-  for (auto &sp : tab) {
-    sp.pA = reinterpret_cast<uint32_t *>(base + exp_off) + (uintptr_t)sp.pA;
-    sp.pB = reinterpret_cast<uint32_t *>(base + exp_off) + (uintptr_t)sp.pB;
-  }
-  SplitProb *d_tab = reinterpret_cast<SplitProb *>(base + tab_off);
-  e = ws.stage.copy_to_device(d_tab, tab.data(), tab.size() * sizeof(SplitProb), s);
-  if (e != cudaSuccess) return note_cuda(e);
-  const int np = (int)tab.size();
-  int *unit_map = nullptr, *pack_map = nullptr;
-  if (np > 1) {
-    unit_map = reinterpret_cast<int *>(base + map_off);
-    pack_map = unit_map + units;
-    e = launch_split_maps(d_tab, np, unit_map, pack_map, nullptr, s);
-    if (e != cudaSuccess) return note_cuda(e);
-  }
-  {
-    TraceScope ts("fp8_pack", s);
-    fp8blk_pack_kernel<<<(unsigned)packs, 256, 0, s>>>(d_tab, np, pack_map,
-                                                       static_cast<uint32_t *>(ws.ptr));
-    if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
-  }
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(fp8blk_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    Lay::kSmem);
-  });
-  if (attr_err != cudaSuccess) return note_cuda(attr_err);
-  CUtensorMap map;
-  if ((e = blk_pack_map(&map, ws.ptr, rows)) != cudaSuccess) return note_cuda(e);
-  const int grid = (int)std::min<int64_t>(units, sm_count());
-  TraceScope ts("fp8_tc", s);
-  fp8blk_gemm_kernel<<<grid, kThreads, Lay::kSmem, s>>>(map, d_tab, np, unit_map, (int)units,
-                                                        g_ctx.d_err);
-  return note_cuda(cudaGetLastError());
+  if (blk.empty()) return MM_OK;
+  if (max_items_all > 0x7fffffffLL) return MM_EINVAL;
+  return fp8_blocks_launch(ws, blk, tc, rows, exps, maxw, blk_units, tc_units, packs, flag_items,
+                           max_items_all, s);
 }
 
 }  // namespace mm

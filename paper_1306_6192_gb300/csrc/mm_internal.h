@@ -180,10 +180,13 @@ size_t tc_tail_part_bytes(const TcTail &t, int64_t tiles, int bn);
 // flags: per-problem kFlagScaleA / kFlagScaleB (nullptr: both operands were
 // packed scaled).  order: the work units of each CTA (tc_unit_order, on the
 // device), or nullptr for units c, c + grid, c + 2 grid, ... on CTA c.
+// uniform_only (FP8 with per-block factors): only the tiles whose rows and
+// columns keep one exponent along K (flags in each problem's cnt) run.
 cudaError_t launch_tc(TcKind kind, const SplitProb *d_probs, int nprobs,
                       int total_units, const int *unit_map, const int *flags,
                       void *pack_base, int64_t pack_rows, const TcConfig &cfg,
-                      int *d_err, cudaStream_t s, const int *order = nullptr);
+                      int *d_err, cudaStream_t s, const int *order = nullptr,
+                      int uniform_only = 0);
 // CTAs of a tensor-core launch of total_units work units.
 int tc_launch_grid(const TcConfig &cfg, int64_t total_units);
 // Work units per CTA for a table whose units differ in length (a grouped

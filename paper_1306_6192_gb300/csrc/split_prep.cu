@@ -330,8 +330,10 @@ split_maps_kernel(const SplitProb *__restrict__ probs, int *__restrict__ unit_ma
   const SplitProb &pr = probs[g];
   const int units = (int)split_units(pr);
   const int packs = pr.mt * pr.kt + pr.nt * pr.kt;
-  for (int i = threadIdx.x; i < units; i += blockDim.x) unit_map[pr.unit_start + i] = g;
-  for (int i = threadIdx.x; i < packs; i += blockDim.x) pack_map[pr.pack_start + i] = g;
+  if (unit_map)
+    for (int i = threadIdx.x; i < units; i += blockDim.x) unit_map[pr.unit_start + i] = g;
+  if (pack_map)
+    for (int i = threadIdx.x; i < packs; i += blockDim.x) pack_map[pr.pack_start + i] = g;
   if (ver_map) {  // only tables that run split_verify_kernel
     const int vers = (int)verify_items(pr.n, pr.p);
     for (int i = threadIdx.x; i < vers; i += blockDim.x) ver_map[pr.ver_start + i] = g;

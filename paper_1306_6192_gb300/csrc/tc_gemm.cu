@@ -120,6 +120,17 @@ __device__ __forceinline__ UnitCoord decode_unit(const SplitProb *__restrict__ p
   return UnitCoord{g, first + in % rows, in / rows, t, h};
 }
 
+// FP8 tables with per-block factors: tile (mt, nt) of 128 x 256 keeps one
+// exponent per row and column along K when its row tile and both of its
+// 128-column halves are flagged (pr.cnt: mt row-tile flags, then the flags of
+// the 128-column sub-tiles).  With uniform_only, the other tiles are skipped
+// by every role (the blockwise kernel computes them).
+__device__ __forceinline__ bool skip_unit(const SplitProb &pr, int uniform_only, int mt, int nt) {
+  if (!uniform_only) return false;
+  const int *f = pr.cnt;
+  return !(f[mt] != 0 && f[pr.mt + 2 * nt] != 0 && f[pr.mt + 2 * nt + 1] != 0);
+}
+
 // Pipeline stages [k0, k1) of a unit: all kiters of a whole tile; for part h
 // the stages of pack rows [h*kt/S, (h+1)*kt/S), so the split points do not
 // depend on the stage depth BKB.
@@ -169,7 +180,7 @@ template <int BKB, int STAGES, int KIND, int MAXBN>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__restrict__ probs,
                int nprobs, const int *__restrict__ unit_map, const int *__restrict__ flags,
-               int total_units, const int *__restrict__ order, int *err) {
+               int total_units, const int *__restrict__ order, int uniform_only, int *err) {
   using L = TcLayout<BKB, STAGES, KIND, MAXBN>;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -229,6 +240,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
         const int u = ulist ? ulist[ui] : ui;
         const UnitCoord tc = decode_unit(probs, nprobs, unit_map, u);
         const SplitProb &pr = probs[tc.g];
+        if (skip_unit(pr, uniform_only, tc.mt, tc.nt)) continue;
         const int bn = pr.bn;
         const int kiters = (int)(((int64_t)pr.m * L::kElemBytes + BKB - 1) / BKB);
         const uint32_t bytes = (uint32_t)(L::kParts * (kTcBM + bn) * BKB);
@@ -287,6 +299,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
         const int u = ulist ? ulist[ui] : ui;
         const UnitCoord tc = decode_unit(probs, nprobs, unit_map, u);
         const SplitProb &pr = probs[tc.g];
+        if (skip_unit(pr, uniform_only, tc.mt, tc.nt)) continue;
         const int kiters = (int)(((int64_t)pr.m * L::kElemBytes + BKB - 1) / BKB);
         int k0, k1;
         unit_krange<BKB>(pr, tc.h, kiters, k0, k1);
@@ -367,6 +380,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
       const int u = ulist ? ulist[ui] : ui;
       const UnitCoord tc = decode_unit(probs, nprobs, unit_map, u);
       const SplitProb &pr = probs[tc.g];
+      if (skip_unit(pr, uniform_only, tc.mt, tc.nt)) continue;
       // column exponents of this tile, once per tile, while the MMAs run
       // operands packed without scaling (flags) take exponent 0
       const int fl = flags ? flags[tc.g] : (kFlagScaleA | kFlagScaleB);
@@ -532,7 +546,8 @@ cudaError_t encode_pack_map(CUtensorMap *map, void *base, int64_t rows, int bkb)
 template <int BKB, int STAGES, int KIND, int MAXBN>
 cudaError_t launch_tc_t(const SplitProb *d_probs, int nprobs, const int *unit_map,
                         const int *flags, int total_units, void *pack_base, int64_t pack_rows,
-                        int grid, int *d_err, cudaStream_t s, const int *order) {
+                        int grid, int *d_err, cudaStream_t s, const int *order,
+                        int uniform_only) {
   using L = TcLayout<BKB, STAGES, KIND, MAXBN>;
   static_assert(L::kSmemBytes <= 232448, "shared memory budget");
   // one CTA per SM: the kernel allocates all 512 TMEM columns
@@ -549,7 +564,7 @@ cudaError_t launch_tc_t(const SplitProb *d_probs, int nprobs, const int *unit_ma
   if (e != cudaSuccess) return e;
   TraceScope ts(KIND == kTcE4m3 ? "fp8_tc" : "split_tc", s);
   tc_gemm_kernel<BKB, STAGES, KIND, MAXBN><<<grid, kThreads, L::kSmemBytes, s>>>(
-      map, d_probs, nprobs, unit_map, flags, total_units, order, d_err);
+      map, d_probs, nprobs, unit_map, flags, total_units, order, uniform_only, d_err);
   return cudaGetLastError();
 }
 
@@ -655,12 +670,15 @@ size_t tc_tail_bytes(const TcTail &t, int64_t tiles, int bn) {
 
 cudaError_t launch_tc(TcKind kind, const SplitProb *d_probs, int nprobs, int total_units,
                       const int *unit_map, const int *flags, void *pack_base, int64_t pack_rows,
-                      const TcConfig &cfg, int *d_err, cudaStream_t s, const int *order) {
+                      const TcConfig &cfg, int *d_err, cudaStream_t s, const int *order,
+                      int uniform_only) {
   if (total_units <= 0) return cudaSuccess;
   if (pack_rows <= 0 || pack_rows > 0x7fffffffLL) return cudaErrorInvalidValue;
   const int grid = tc_launch_grid(cfg, total_units);
   const int *mp = unit_map;
-#define MM_TC_ARGS d_probs, nprobs, mp, flags, total_units, pack_base, pack_rows, grid, d_err, s, order
+#define MM_TC_ARGS \
+  d_probs, nprobs, mp, flags, total_units, pack_base, pack_rows, grid, d_err, s, order, \
+      uniform_only
   cudaError_t e = cudaErrorInvalidValue;
   const bool narrow = cfg.max_bn <= 128;  // every N tile of the table fits 128
   if (kind == kTcE4m3) e = launch_tc_t<128, 4, kTcE4m3, 256>(MM_TC_ARGS);

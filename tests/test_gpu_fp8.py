@@ -110,3 +110,25 @@ def test_fp8_grouped_equals_single(mmlib):
         C1 = torch.full_like(C, float("nan"))
         assert mmlib.mm_gemm(n, m, p, dA, dB, C1, mmlib.MM_F32, mmlib.MM_MODE_FP8) == 0
         assert torch.equal(C, C1), (n, m, p)
+
+
+def test_fp8_uniform_and_blockwise_tiles_in_one_product(mmlib):
+    """Tiles whose rows and columns keep one exponent along K accumulate all K
+    blocks in tensor memory and are unscaled once; the others unscale each K
+    block.  One product with both kinds (row tile 0 of A has one K block
+    scaled by 2^12, so its tiles take the blockwise form): every tile within
+    the e4m3 sanity bound of the oracle, and the blockwise tiles' rows equal
+    to a product of those rows alone (the same decision per tile)."""
+    n, m, p = 256, 512, 256
+    A = synth.uniform_pm1(861, (n, m)).astype(np.float64)
+    A[:128, 128:256] *= 2.0 ** 12
+    A = A.astype(np.float32)
+    B = synth.uniform_pm1(862, (m, p))
+    C = run_gemm(mmlib, A, B, mmlib.MM_MODE_FP8)
+    ref, absref = oracle.default().gemm(A, B, with_abs=True)
+    e = oracle.rel_errors(C, ref, absref)
+    assert e[:128].max() < 0.05 and e[128:].max() < 0.05, (e[:128].max(), e[128:].max())
+    C0 = run_gemm(mmlib, np.ascontiguousarray(A[:128]), B, mmlib.MM_MODE_FP8)
+    assert np.array_equal(C0, C[:128])
+    C1 = run_gemm(mmlib, np.ascontiguousarray(A[128:]), B, mmlib.MM_MODE_FP8)
+    assert np.array_equal(C1, C[128:])
