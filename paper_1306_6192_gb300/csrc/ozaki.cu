@@ -213,9 +213,10 @@ ozaki_max_kernel(const double *__restrict__ A, const double *__restrict__ B, int
 // warp: a warp's 16 loads read four whole 1 KB row segments, and each digit
 // store instruction writes four whole 128-byte pack rows).  SS = S slices per
 // tile, or S + 1 with the accuracy gate's slice (gate_value) after them.
+template <int S>
 __global__ void __launch_bounds__(256)
 ozaki_digits_a_kernel(const double *__restrict__ A, int64_t n, int64_t m, int64_t k0, int64_t mc,
-                      int kt, int S, int SS, const uint64_t *__restrict__ rowmax,
+                      int kt, int SS, const uint64_t *__restrict__ rowmax,
                       uint4 *__restrict__ pack, int64_t a0) {
   const int mt = blockIdx.x / kt, kb = blockIdx.x % kt;
 #pragma unroll 1
@@ -239,7 +240,7 @@ ozaki_digits_a_kernel(const double *__restrict__ A, int64_t n, int64_t m, int64_
         if (SS > S) G[e] = gate_value(F[e], S);
       }
     }
-#pragma unroll 1
+#pragma unroll
     for (int t = 0; t < S; t++) {
       const int64_t row = a0 + (((int64_t)mt * SS + t) * kt + kb) * kTcBM + r;
       pack[row * (kPackRowBytes / 16) + sg] = digit_bytes(F, negmask, 4 * (S - 1 - t));
@@ -254,9 +255,10 @@ ozaki_digits_a_kernel(const double *__restrict__ A, int64_t n, int64_t m, int64_
 // B digits of one K chunk: one block per tile (nt, kb); the bn columns are
 // transposed through shared memory 32 at a time (FP64 rows of 32 columns
 // read whole), then a thread takes 16 consecutive k of a column.
+template <int S>
 __global__ void __launch_bounds__(256)
 ozaki_digits_b_kernel(const double *__restrict__ B, int64_t m, int64_t p, int64_t k0, int64_t mc,
-                      int kt, int S, int SS, int bn, const unsigned long long *__restrict__ colmax,
+                      int kt, int SS, int bn, const unsigned long long *__restrict__ colmax,
                       uint4 *__restrict__ pack, int64_t b0) {
   __shared__ double tile[128][32 + 1];
   const int nt = blockIdx.x / kt, kb = blockIdx.x % kt;
@@ -287,7 +289,7 @@ ozaki_digits_b_kernel(const double *__restrict__ B, int64_t m, int64_t p, int64_
           if (SS > S) G[e] = gate_value(F[e], S);
         }
       }
-#pragma unroll 1
+#pragma unroll
       for (int u = 0; u < S; u++) {
         const int64_t row = b0 + (((int64_t)nt * SS + (S - 1 - u)) * kt + kb) * bn + c0 + c;
         pack[row * (kPackRowBytes / 16) + sg] = digit_bytes(F, negmask, 4 * (S - 1 - u));
@@ -336,55 +338,137 @@ ozaki_map_kernel(int *__restrict__ map, int64_t units, int64_t tiles) {
   if (u < units) map[u] = (int)(u / tiles);
 }
 
+// Both digit kernels of one K chunk, instantiated per S (the slice loops
+// unroll with constant shifts).
+cudaError_t launch_ozaki_digits(int S, int64_t blocks_a, int64_t blocks_b, cudaStream_t s,
+                                const double *A, const double *B, int64_t n, int64_t m,
+                                int64_t p, int64_t k0, int64_t mc, int kt, int SS, int bn,
+                                const uint64_t *rowmax, const unsigned long long *colmax,
+                                uint4 *pack, int64_t a0, int64_t b0) {
+  if (blocks_a > 0x7fffffffLL || blocks_b > 0x7fffffffLL) return cudaErrorInvalidValue;
+  switch (S) {
+#define MM_OZ_DIG(V)                                                                            \
+  case V:                                                                                       \
+    ozaki_digits_a_kernel<V><<<(unsigned)blocks_a, 256, 0, s>>>(A, n, m, k0, mc, kt, SS, rowmax, \
+                                                                pack, a0);                      \
+    ozaki_digits_b_kernel<V><<<(unsigned)blocks_b, 256, 0, s>>>(B, m, p, k0, mc, kt, SS, bn,    \
+                                                                colmax, pack, b0);              \
+    break;
+    MM_OZ_DIG(2) MM_OZ_DIG(3) MM_OZ_DIG(4) MM_OZ_DIG(5) MM_OZ_DIG(6) MM_OZ_DIG(7) MM_OZ_DIG(8)
+    MM_OZ_DIG(9) MM_OZ_DIG(10) MM_OZ_DIG(11) MM_OZ_DIG(12) MM_OZ_DIG(13) MM_OZ_DIG(14)
+    MM_OZ_DIG(15) MM_OZ_DIG(16)
+#undef MM_OZ_DIG
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// The double nearest to M 2^k (M > 0 a 128-bit integer; ties to even) in
+// integer arithmetic: the top 53 bits of M, rounded on the bits below them,
+// and the exponent placed directly.  Returns false where the result is not a
+// normal double (the caller then takes int128_scaled).
+__device__ __forceinline__ bool round_to_double(unsigned __int128 M, int k, uint64_t &bits) {
+  const uint64_t mh = (uint64_t)(M >> 64), ml = (uint64_t)M;
+  const int L = mh ? 128 - __clzll((long long)mh) : 64 - __clzll((long long)ml);  // bit length
+  int e = L - 1 + k;
+  uint64_t top;
+  if (L <= 53) {
+    top = ml << (53 - L);  // exact
+  } else {
+    const int sh = L - 53;  // 1..75
+    top = (uint64_t)(M >> sh);
+    const unsigned __int128 rem = M - ((unsigned __int128)top << sh);
+    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+    if (rem > half || (rem == half && (top & 1u))) {
+      if (++top == (1ull << 53)) {
+        top >>= 1;
+        e++;
+      }
+    }
+  }
+  if (e < -1022 || e > 1023) return false;
+  bits = ((uint64_t)(e + 1023) << 52) | (top & ((1ull << 52) - 1));
+  return true;
+}
+
 // c_ij = 2^(sigma_i + tau_j - 4(S+1)) sum_c sum_L D[c][L][i][j] 2^(4(S-1-L)):
 // the level sums are integers below 2^24, so their weighted sum is formed
 // exactly in 128-bit integers and rounded once to FP64 (then scaled by a
 // power of two, which rounds again only in the subnormal range); NaN where
 // row i of A or column j of B is not finite.  A thread takes column j of the
 // rows blockIdx.y, blockIdx.y + gridDim.y, ...; the S level values of a chunk
-// are loaded together (at most kOzakiMaxSlices in flight per thread).
+// are loaded together.  One instantiation per S, so the level loop unrolls
+// without predicates.
+template <int S>
 __global__ void __launch_bounds__(256, 4)
-ozaki_sum_kernel(const float *__restrict__ D, int64_t plane, int64_t n, int64_t p, int S, int chunks,
+ozaki_sum_kernel(const float *__restrict__ D, int64_t plane, int64_t n, int64_t p, int chunks,
                  const uint64_t *__restrict__ rowmax, const unsigned long long *__restrict__ colmax,
                  double *__restrict__ C) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= p) return;
   bool fb;
   const int tau = slice_exponent(colmax[j], fb);
+  // Horner by 16 over levels 0..h-1 into X and h..S-1 into Y (int64: each
+  // part at most (2^24 - 1)(16^8 - 1)/15 < 2^52.1 per chunk, below 2^63 over
+  // at most kOzakiMaxChunks = 2^10 chunks), then v = X 16^(S-h) + Y once in
+  // 128 bits
+  constexpr int h = (S + 1) / 2;
   for (int64_t i = blockIdx.y; i < n; i += gridDim.y) {
     bool fa;
     const int sigma = slice_exponent(rowmax[i], fa);
     const int64_t x = i * p + j;
-    // Horner by 16 over levels 0..h-1 into X and h..S-1 into Y (int64: each
-    // part at most (2^24 - 1)(16^8 - 1)/15 < 2^52.1 per chunk, below 2^63 over
-    // at most kOzakiMaxChunks = 2^10 chunks), then v = X 16^(S-h) + Y once in
-    // 128 bits
-    const int h = (S + 1) / 2;
     int64_t X = 0, Y = 0;
     for (int c = 0; c < chunks; c++) {
       const float *d = D + (int64_t)c * S * plane + x;
-      float v[kOzakiMaxSlices];
+      float v[S];
 #pragma unroll
-      for (int L = 0; L < kOzakiMaxSlices; L++) v[L] = L < S ? __ldcs(d + (int64_t)L * plane) : 0.0f;
+      for (int L = 0; L < S; L++) v[L] = __ldcs(d + (int64_t)L * plane);
       int64_t xc = 0, yc = 0;
 #pragma unroll
-      for (int L = 0; L < kOzakiMaxSlices; L++) {
+      for (int L = 0; L < S; L++) {
         const int64_t q = __float2int_rn(v[L]);
         if (L < h) xc = xc * 16 + q;
-        else if (L < S) yc = yc * 16 + q;
+        else yc = yc * 16 + q;
       }
       X += xc;
       Y += yc;
     }
-    const int sh = 4 * (S - h);  // 4..32
+    constexpr int sh = 4 * (S - h);  // 4..32
     uint64_t lo = (uint64_t)X << sh;
     int64_t hi = X >> (64 - sh);
     const uint64_t r = lo + (uint64_t)Y;
     hi += (Y < 0 ? -1 : 0) + (r < lo ? 1 : 0);
     lo = r;
-    C[x] = (fa && fb) ? int128_scaled(lo, hi, sigma + tau - 4 * (S + 1))
-                      : __longlong_as_double(0x7ff8000000000000ll);
+    const int k = sigma + tau - 4 * (S + 1);
+    double out;
+    if (!(fa && fb)) {
+      out = __longlong_as_double(0x7ff8000000000000ll);
+    } else {
+      const bool neg = hi < 0;
+      unsigned __int128 M = ((unsigned __int128)(uint64_t)hi << 64) | lo;
+      if (neg) M = ~M + 1;
+      uint64_t bits;
+      if (M == 0) out = 0.0;
+      else if (round_to_double(M, k, bits)) out = __longlong_as_double((long long)(bits | ((uint64_t)neg << 63)));
+      else out = int128_scaled(lo, hi, k);
+    }
+    C[x] = out;
   }
+}
+
+cudaError_t launch_ozaki_sum(int S, dim3 grid, cudaStream_t s, const float *D, int64_t plane,
+                             int64_t n, int64_t p, int chunks, const uint64_t *rowmax,
+                             const unsigned long long *colmax, double *C) {
+  switch (S) {
+#define MM_OZ_SUM(V) \
+  case V: ozaki_sum_kernel<V><<<grid, 256, 0, s>>>(D, plane, n, p, chunks, rowmax, colmax, C); break;
+    MM_OZ_SUM(2) MM_OZ_SUM(3) MM_OZ_SUM(4) MM_OZ_SUM(5) MM_OZ_SUM(6) MM_OZ_SUM(7) MM_OZ_SUM(8)
+    MM_OZ_SUM(9) MM_OZ_SUM(10) MM_OZ_SUM(11) MM_OZ_SUM(12) MM_OZ_SUM(13) MM_OZ_SUM(14)
+    MM_OZ_SUM(15) MM_OZ_SUM(16)
+#undef MM_OZ_SUM
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 // Accuracy gate.  Every term a_ir b_rj of the emulated product is off by at
@@ -583,12 +667,10 @@ mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *
     uint4 *pk = static_cast<uint4 *>(ws.ptr);
     for (int c = 0; c < lay.chunks; c++) {
       const int kt = (int)lay.kt[(size_t)c];
-      ozaki_digits_a_kernel<<<(unsigned)(lay.mt * kt), 256, 0, s>>>(
-          A, n, m, lay.k0[(size_t)c], lay.kc[(size_t)c], kt, S, lay.SS, rowmax, pk,
-          lay.a0[(size_t)c]);
-      ozaki_digits_b_kernel<<<(unsigned)(lay.nt * kt), 256, 0, s>>>(
-          B, m, p, lay.k0[(size_t)c], lay.kc[(size_t)c], kt, S, lay.SS, lay.bn, colmax, pk,
-          lay.b0[(size_t)c]);
+      e = launch_ozaki_digits(S, lay.mt * kt, lay.nt * kt, s, A, B, n, m, p, lay.k0[(size_t)c],
+                              lay.kc[(size_t)c], kt, lay.SS, lay.bn, rowmax, colmax, pk,
+                              lay.a0[(size_t)c], lay.b0[(size_t)c]);
+      if (e != cudaSuccess) return note_cuda(e);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
   }
@@ -608,8 +690,9 @@ mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *
     // one wave: four blocks per SM (the launch bound)
     const int64_t gy = std::max<int64_t>(1, std::min<int64_t>({n, 65535, ceil_div((int64_t)sm_count() * 4, gx)}));
     if (gx > 0x7fffffffLL) return MM_EINVAL;
-    ozaki_sum_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(D, lay.plane, n, p, S,
-                                                                       lay.chunks, rowmax, colmax, C);
+    e = launch_ozaki_sum(S, dim3((unsigned)gx, (unsigned)gy), s, D, lay.plane, n, p, lay.chunks,
+                         rowmax, colmax, C);
+    if (e != cudaSuccess) return note_cuda(e);
     if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
   }
   if (!gate) return MM_OK;
