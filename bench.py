@@ -1151,7 +1151,7 @@ def main(argv=None):
     ap.add_argument("--grouped-count", type=int, default=4096)
     ap.add_argument("--ozaki-only", action="store_true",
                     help="only the FP64 product emulated by the Ozaki scheme")
-    ap.add_argument("--ozaki-slices", type=int, default=14)
+    ap.add_argument("--ozaki-slices", type=int, default=12)
     ap.add_argument("--fp8-only", action="store_true",
                     help="only the FP8 e4m3 product at --size")
     ap.add_argument("--stress-only", action="store_true", help="only the config-3 stress shapes")

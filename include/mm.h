@@ -42,8 +42,9 @@
  *   MM_MODE_AUTO          SPLIT_BF16X3 for MM_F32, DGEMM for MM_F64.
  *   MM_MODE_OZAKI         FP64 in/out on the e4m3 tensor cores (Ozaki
  *                         scheme): each row of A / column of B is scaled by a
- *                         power of two and cut into S 4-bit integer digit
- *                         slices; the slice products of equal weight are
+ *                         power of two and cut into S balanced base-32
+ *                         integer digit slices (|d| <= 16); the slice
+ *                         products of equal weight are
  *                         exact in FP32; the levels are added exactly in
  *                         128-bit integers and rounded once to FP64.  Accuracy
  *                         depends on S and on the spread of magnitudes within
@@ -151,34 +152,36 @@ mm_status mm_gemm(int64_t n, int64_t m, int64_t p, const void *A, const void *B,
                   void *C, mm_dtype dt, mm_mode mode);
 
 /* Digit slices S used by MM_MODE_OZAKI for products queued after the call
- * (serving requests keep the value current at mm_submit).  2 <= S <= 16,
- * default 14; the cost grows as S (S + 1) / 2 e4m3 products.
+ * (serving requests keep the value current at mm_submit).  2 <= S <= 12,
+ * default 12; the cost grows as S (S + 1) / 2 e4m3 products.
  * Method (K. Ozaki, T. Ogita, S. Oishi, S. M. Rump, Numer. Algorithms 59,
  * 2012, error-free splitting of matrix products): with sigma_i =
- * ilogb(max_r |a_ir|) + 1 and tau_j likewise for column j of B, every entry
- * is truncated to 4S bits below 2^sigma and cut into S digits of 4 bits
- * (|d| <= 15, exact in e4m3); level L = t + u of the digit products is one
- * tensor-core product whose FP32 sums stay exact (K is cut into chunks of
- * at most (2^24 - 1) / (225 S) columns for that); levels t + u >= S are
- * dropped.  Each term a_ir b_rj is then off by at most
- * (S + 2) 2^(sigma_i + tau_j - 4S), zero entries by nothing: relative to
- * (|A||B|)_ij about 4 (S + 2) 2^(-4S) (S = 14: 9e-16) for rows and columns
+ * ilogb(max_r |a_ir|) + 2 and tau_j likewise for column j of B, every entry
+ * is truncated to 5S bits below 2^sigma and written as S balanced base-32
+ * digits (d_0 in [0, 16], the others in [-16, 15], signed by the entry;
+ * exact in e4m3); level L = t + u of the digit products is one tensor-core
+ * product whose FP32 sums stay exact (K is cut into chunks of at most
+ * (2^24 - 1) / (256 S) columns for that); levels t + u >= S are dropped.
+ * Each term a_ir b_rj is then off by at most
+ * (S + 2) 2^(sigma_i + tau_j - 5S - 1), zero entries by nothing: relative to
+ * (|A||B|)_ij about 8 (S + 2) 2^(-5S) (S = 12: 1e-16) for rows and columns
  * without a wide spread of magnitudes, more where a row's largest entry
- * dwarfs the entries that meet the column's mass (mm_check measures a
- * result).  Rows of A or columns of B holding a NaN or an infinity give NaN
- * rows or columns of C.  Scratch: (S digit bytes per entry of A and B, plus
- * S FP32 level sums per entry of C per K chunk), library-owned.
- * Returns MM_EINVAL outside 2..16, MM_ENOTINIT before mm_init.  An
- * MM_MODE_OZAKI product whose inner dimension needs more than 1024 K chunks
- * (m above about 5.4 million at S = 14) returns MM_EINVAL. */
+ * dwarfs the entries that meet the column's mass (the accuracy gate below
+ * guards the FP64 tolerance).  Rows of A or columns of B holding a NaN or an
+ * infinity give NaN rows or columns of C.  Scratch: (S + 1 digit bytes per
+ * entry of A and B, plus S + 1 FP32 level sums per entry of C per K chunk),
+ * library-owned.  Returns MM_EINVAL outside 2..12, MM_ENOTINIT before
+ * mm_init.  An MM_MODE_OZAKI product whose inner dimension needs more than
+ * 1024 K chunks (m above about 5.5 million at S = 12) returns MM_EINVAL. */
 mm_status mm_ozaki_slices(int slices);
 
 /* Accuracy gate of MM_MODE_OZAKI products queued after the call (serving
  * requests keep the setting current at mm_submit); on (1) by default.  Entry
- * (i, j) of the emulation is off by at most m (S + 2) 2^(sigma_i + tau_j - 4S)
+ * (i, j) of the emulation is off by at most
+ * m (S + 2) 2^(sigma_i + tau_j - 5S - 1)
  * (scales 2^sigma_i of row i of A, 2^tau_j of column j of B), so it meets
  * 1e-14 sqrt(m) of (|A||B|)_ij wherever P_ij = sum_r |a_ir| 2^-sigma_i
- * |b_rj| 2^-tau_j >= sqrt(m) (S + 2) 2^-4S 1e14.  With the gate, each product
+ * |b_rj| 2^-tau_j >= sqrt(m) (S + 2) 2^(-5S-1) 1e14.  With the gate, each product
  * also packs one more e4m3 slice per operand (16 |x| 2^-sigma truncated
  * toward zero onto the e4m3 grid) and multiplies the two on the tensor cores,
  * a lower bound of 256 P, and checks every entry against the threshold
@@ -197,11 +200,11 @@ mm_status mm_ozaki_gate(int on);
 /* Plan of an MM_MODE_OZAKI product, a pure host function (no device, no
  * mm_init): for A n x m, B m x p and `slices` digit slices, writes the K
  * columns per chunk (the largest multiple of 128 with
- * 225 * slices * columns < 2^24, so every level sum stays an exact FP32
+ * 256 * slices * columns < 2^24, so every level sum stays an exact FP32
  * integer), the number of chunks (ceil(m / columns); 0 for m = 0) and an
  * upper bound of the library scratch the product holds (digit packs, FP32
  * level sums, maxima, table).  Returns MM_EINVAL for negative sizes, slices
- * outside 2..16, NULL outputs or more than 1024 chunks. */
+ * outside 2..12, NULL outputs or more than 1024 chunks. */
 mm_status mm_ozaki_plan(int64_t n, int64_t m, int64_t p, int slices, int64_t *chunk_columns,
                         int *chunks, size_t *scratch_bytes);
 

@@ -297,7 +297,7 @@ def mm_tail_plan(tiles, grid, kt, bn, m, products):
 
 
 def mm_ozaki_slices(slices: int) -> int:
-    """Digit slices S (2..16) of MM_MODE_OZAKI for the products queued next."""
+    """Digit slices S (2..12) of MM_MODE_OZAKI for the products queued next."""
     return lib().mm_ozaki_slices(int(slices))
 
 

@@ -43,7 +43,7 @@ struct TcChoice {
 };
 
 // FP64 emulation (MM_MODE_OZAKI): 4-bit digit slices per operand.
-constexpr int kOzakiMinSlices = 2, kOzakiMaxSlices = 16, kOzakiDefaultSlices = 14;
+constexpr int kOzakiMinSlices = 2, kOzakiMaxSlices = 12, kOzakiDefaultSlices = 12;
 
 struct Ctx {
   bool inited = false;

@@ -8,30 +8,36 @@
 // precision.  This library's variant (not in the paper, whose double-precision
 // kernels use FP64 arithmetic directly):
 //
-//   * Row i of A is scaled by 2^-sigma_i, sigma_i = ilogb(max_r |a_ir|) + 1,
-//     so |a_ir| 2^-sigma_i < 1; column j of B by 2^-tau_j likewise.  The
-//     scaled magnitude, truncated to 4S fraction bits, is the integer
-//     F = floor(|a| 2^(4S - sigma)) < 2^(4S), and its 4-bit digits
-//     d_t = (F >> 4(S-1-t)) & 15, t = 0..S-1, carry the sign of a:
-//         a 2^-sigma = sum_t d_t 2^(-4(t+1)) + delta,  |delta| < 2^(-4S).
-//     Every digit (|d| <= 15) is exact in e4m3.
+//   * Row i of A is scaled by 2^-sigma_i, sigma_i = ilogb(max_r |a_ir|) + 2,
+//     so |a_ir| 2^-sigma_i < 1/2; column j of B by 2^-tau_j likewise.  The
+//     scaled magnitude, truncated to 5S fraction bits, is the integer
+//     F = floor(|a| 2^(5S - sigma)) < 2^(5S - 1) (S <= 12: 59 bits), written
+//     in balanced base 32: G = F + 16 (32^S - 1) / 31 (16 added to every
+//     base-32 position), then d_t = g_t - 16 with g_t = (G >> 5(S-1-t)) & 31
+//     for t >= 1 and g_0 = G >> 5(S-1) unmasked, so d_t lies in [-16, 15]
+//     (t >= 1), d_0 in [0, 16], and sum_t d_t 32^(S-1-t) = F.  With the sign
+//     of a on every digit:
+//         a 2^-sigma = sum_t d_t 32^-(t+1) + delta,  |delta| < 2^(-5S).
+//     Every digit (|d| <= 16) is exact in e4m3; five bits per slice instead
+//     of four cut the slices (and the S(S+1)/2 level products) for the same
+//     precision.
 //   * Level L = 0..S-1 collects the slice products of equal weight:
 //         D_L = sum_{t+u=L} A_t B_u,
 //     one tensor-core product along a K of (L+1) slices: A's slices 0..L
-//     against B's slices L..0.  Each term is at most 225, a level at most
-//     225 S mc, so with K cut into chunks of mc <= (2^24 - 1) / (225 S)
+//     against B's slices L..0.  Each term is at most 256, a level at most
+//     256 S mc, so with K cut into chunks of mc <= (2^24 - 1) / (256 S)
 //     columns (a multiple of 128) every D_L is an integer below 2^24 and
 //     FP32 accumulation (and the tail split's FP32 partial sums) is exact.
 //     Pairs with t + u >= S are dropped.
-//   * c_ij = 2^(sigma_i + tau_j) * sum_L 2^(-4(L+2)) D_L[i][j] (summed over
+//   * c_ij = 2^(sigma_i + tau_j) * sum_L 32^-(L+2) D_L[i][j] (summed over
 //     the chunks too), formed exactly in 128-bit integers and rounded once
 //     to FP64: the double nearest to the kept digit products.
 //
-// Error: a term a_ir b_rj loses at most (S + 2) 2^(sigma_i + tau_j - 4S)
+// Error: a term a_ir b_rj loses at most (S + 2) 2^(sigma_i + tau_j - 5S - 1)
 // (both truncations and the dropped pairs), and zero entries lose nothing,
-// so |c^_ij - c_ij| <= (S + 2) 2^(sigma_i + tau_j - 4S) #{r : a_ir b_rj != 0}
+// so |c^_ij - c_ij| <= (S + 2) 2^(sigma_i + tau_j - 5S - 1) #{r : a_ir b_rj != 0}
 // plus the final rounding (half an ulp of c^_ij).  Relative to (|A||B|)_ij this is
-// data dependent: ~4 (S + 2) 2^(-4S) for rows and columns without a wide
+// data dependent: ~8 (S + 2) 2^(-5S) for rows and columns without a wide
 // spread of magnitudes (uniform data), much more where a row's largest entry
 // dwarfs the entries that meet the column's mass.  The accuracy gate (on by
 // default) bounds P_ij = (|A||B|)_ij 2^-(sigma_i + tau_j) from below with one
@@ -81,18 +87,18 @@ __device__ __forceinline__ uint64_t abs_bits64(double x) {
   return (uint64_t)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
 
-// sigma = ilogb(max) + 1 from the bit pattern of a row's largest magnitude;
+// sigma = ilogb(max) + 2 from the bit pattern of a row's largest magnitude;
 // 0 for an all-zero row; finite = false for a NaN or an infinity.
 __device__ __forceinline__ int slice_exponent(uint64_t max_bits, bool &finite) {
   const int e_raw = (int)(max_bits >> 52);
   finite = e_raw != 0x7ff;
   if (max_bits == 0 || !finite) return 0;
-  if (e_raw == 0) return (63 - __clzll((long long)max_bits)) - 1074 + 1;  // subnormal
-  return e_raw - 1023 + 1;
+  if (e_raw == 0) return (63 - __clzll((long long)max_bits)) - 1074 + 2;  // subnormal
+  return e_raw - 1023 + 2;
 }
 
-// Truncated fixed-point magnitude F = floor(|x| 2^(4S - sigma)) (< 2^(4S)
-// for |x| < 2^sigma) and the sign of x.
+// Truncated fixed-point magnitude F = floor(|x| 2^(5S - sigma)) (< 2^(5S-1)
+// for |x| < 2^(sigma-1)) and the sign of x.
 __device__ __forceinline__ uint64_t fixed_magnitude(double x, int sigma, int S, bool &neg) {
   const uint64_t bits = (uint64_t)__double_as_longlong(x);
   neg = (bits >> 63) != 0;
@@ -107,20 +113,35 @@ __device__ __forceinline__ uint64_t fixed_magnitude(double x, int sigma, int S, 
     mant = frac | (1ull << 52);
     ex = e_raw - 1023;
   }
-  const int sh = ex - 52 + 4 * S - sigma;  // |x| = mant 2^(ex - 52)
+  const int sh = ex - 52 + 5 * S - sigma;  // |x| = mant 2^(ex - 52)
   if (mant == 0 || sh <= -64) return 0;
   return sh >= 0 ? (mant << sh) : (mant >> -sh);
 }
 
-// 16 digits of slice t (one per k) -> 16 e4m3 bytes; zero digits are +0.
-__device__ __forceinline__ uint4 digit_bytes(const uint64_t (&F)[kSeg], uint32_t negmask, int shift) {
+// G = F + 16 (32^S - 1) / 31: 16 added to every base-32 position of F, so
+// that g_t - 16 are the balanced digits (below 2^60 for S <= 12).
+template <int S>
+__device__ __forceinline__ uint64_t balanced_offset() {
+  static_assert(S >= 2 && S <= 12, "slices");
+  uint64_t o = 0;
+#pragma unroll
+  for (int t = 0; t < S; t++) o = (o << 5) | 16u;
+  return o;
+}
+
+// 16 digits of slice t (one per k) from G -> 16 e4m3 bytes: d = g_t - 16
+// (g_t = (G >> shift) & 31, the top slice unmasked), with the sign of x;
+// zero digits are +0.
+__device__ __forceinline__ uint4 digit_bytes(const uint64_t (&G)[kSeg], uint32_t negmask, int shift,
+                                             bool top) {
   uint32_t w[4];
 #pragma unroll
   for (int q = 0; q < 4; q++) {
     float v[4];
 #pragma unroll
     for (int e = 0; e < 4; e++) {
-      const int d = (int)((F[4 * q + e] >> shift) & 15u);
+      const uint64_t g = G[4 * q + e] >> shift;
+      const int d = (int)(top ? g : (g & 31u)) - 16;
       v[e] = ((negmask >> (4 * q + e)) & 1u) && d ? -(float)d : (float)d;
     }
     const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v[0], v[1]), __NV_SATFINITE, __NV_E4M3);
@@ -133,16 +154,16 @@ __device__ __forceinline__ uint4 digit_bytes(const uint64_t (&F)[kSeg], uint32_t
 // The accuracy gate's slice: 16 |x| 2^-sigma truncated toward zero onto the
 // e4m3 grid (4 significant bits at 2^-6 and above, multiples of 2^-9 below;
 // 0 under 2^-9), so the value is exact in e4m3 and never above 16 |x| 2^-sigma.
-// Formed from the truncated fixed-point magnitude F = floor(|x| 2^(4S-sigma))
-// in integer and FP32 arithmetic (16 |x| 2^-sigma >= F 2^(4-4S)): F's top four
-// bits times a power of two.
+// Formed from the truncated fixed-point magnitude F = floor(|x| 2^(5S-sigma))
+// in integer and FP32 arithmetic (16 |x| 2^-sigma >= F 2^(4-5S)): F's top four
+// bits times a power of two (below 8, since |x| 2^-sigma < 1/2).
 __device__ __forceinline__ float gate_value(uint64_t F, int S) {
   if (F == 0) return 0.0f;
-  const int b = 64 - __clzll((long long)F);  // bit length, 1..4S
+  const int b = 64 - __clzll((long long)F);  // bit length, 1..5S-1
   const int sh = b > 4 ? b - 4 : 0;
   const float top = (float)(uint32_t)(F >> sh);  // 1..15, exact
-  // 2^(sh + 4 - 4S) >= 2^(4 - 64): a normal float
-  const float v = top * __int_as_float((sh + 4 - 4 * S + 127) << 23);
+  // 2^(sh + 4 - 5S) >= 2^(4 - 60): a normal float
+  const float v = top * __int_as_float((sh + 4 - 5 * S + 127) << 23);
   return v >= 0x1p-6f ? v : floorf(v * 512.0f) * 0x1p-9f;
 }
 
@@ -224,7 +245,7 @@ ozaki_digits_a_kernel(const double *__restrict__ A, int64_t n, int64_t m, int64_
     const int r = q / (128 / kSeg), sg = q % (128 / kSeg);
     const int64_t i = (int64_t)mt * kTcBM + r;
     uint64_t F[kSeg];
-    float G[kSeg];
+    float Gv[kSeg];
     uint32_t negmask = 0;
     bool finite = true;
     const int sigma = i < n ? slice_exponent(rowmax[i], finite) : 0;
@@ -232,22 +253,23 @@ ozaki_digits_a_kernel(const double *__restrict__ A, int64_t n, int64_t m, int64_
     for (int e = 0; e < kSeg; e++) {
       const int64_t kk = (int64_t)kb * 128 + sg * kSeg + e;  // within the chunk
       F[e] = 0;
-      G[e] = 0.0f;
+      Gv[e] = 0.0f;
       if (i < n && finite && kk < mc) {
         bool neg;
         F[e] = fixed_magnitude(A[i * m + k0 + kk], sigma, S, neg);
         negmask |= (uint32_t)neg << e;
-        if (SS > S) G[e] = gate_value(F[e], S);
+        if (SS > S) Gv[e] = gate_value(F[e], S);
       }
+      F[e] += balanced_offset<S>();  // padding and zeros: all digits 0
     }
 #pragma unroll
     for (int t = 0; t < S; t++) {
       const int64_t row = a0 + (((int64_t)mt * SS + t) * kt + kb) * kTcBM + r;
-      pack[row * (kPackRowBytes / 16) + sg] = digit_bytes(F, negmask, 4 * (S - 1 - t));
+      pack[row * (kPackRowBytes / 16) + sg] = digit_bytes(F, negmask, 5 * (S - 1 - t), t == 0);
     }
     if (SS > S) {
       const int64_t row = a0 + (((int64_t)mt * SS + S) * kt + kb) * kTcBM + r;
-      pack[row * (kPackRowBytes / 16) + sg] = gate_bytes(G);
+      pack[row * (kPackRowBytes / 16) + sg] = gate_bytes(Gv);
     }
   }
 }
@@ -276,27 +298,28 @@ ozaki_digits_b_kernel(const double *__restrict__ B, int64_t m, int64_t p, int64_
       bool finite = true;
       const int tau = j < p ? slice_exponent(colmax[j], finite) : 0;
       uint64_t F[kSeg];
-      float G[kSeg];
+      float Gv[kSeg];
       uint32_t negmask = 0;
 #pragma unroll
       for (int e = 0; e < kSeg; e++) {
         F[e] = 0;
-        G[e] = 0.0f;
+        Gv[e] = 0.0f;
         if (j < p && finite) {
           bool neg;
           F[e] = fixed_magnitude(tile[sg * kSeg + e][c], tau, S, neg);
           negmask |= (uint32_t)neg << e;
-          if (SS > S) G[e] = gate_value(F[e], S);
+          if (SS > S) Gv[e] = gate_value(F[e], S);
         }
+        F[e] += balanced_offset<S>();  // padding and zeros: all digits 0
       }
 #pragma unroll
       for (int u = 0; u < S; u++) {
         const int64_t row = b0 + (((int64_t)nt * SS + (S - 1 - u)) * kt + kb) * bn + c0 + c;
-        pack[row * (kPackRowBytes / 16) + sg] = digit_bytes(F, negmask, 4 * (S - 1 - u));
+        pack[row * (kPackRowBytes / 16) + sg] = digit_bytes(F, negmask, 5 * (S - 1 - u), u == 0);
       }
       if (SS > S) {
         const int64_t row = b0 + (((int64_t)nt * SS + S) * kt + kb) * bn + c0 + c;
-        pack[row * (kPackRowBytes / 16) + sg] = gate_bytes(G);
+        pack[row * (kPackRowBytes / 16) + sg] = gate_bytes(Gv);
       }
     }
     __syncthreads();
@@ -355,8 +378,7 @@ cudaError_t launch_ozaki_digits(int S, int64_t blocks_a, int64_t blocks_b, cudaS
                                                                 colmax, pack, b0);              \
     break;
     MM_OZ_DIG(2) MM_OZ_DIG(3) MM_OZ_DIG(4) MM_OZ_DIG(5) MM_OZ_DIG(6) MM_OZ_DIG(7) MM_OZ_DIG(8)
-    MM_OZ_DIG(9) MM_OZ_DIG(10) MM_OZ_DIG(11) MM_OZ_DIG(12) MM_OZ_DIG(13) MM_OZ_DIG(14)
-    MM_OZ_DIG(15) MM_OZ_DIG(16)
+    MM_OZ_DIG(9) MM_OZ_DIG(10) MM_OZ_DIG(11) MM_OZ_DIG(12)
 #undef MM_OZ_DIG
     default: return cudaErrorInvalidValue;
   }
@@ -391,7 +413,7 @@ __device__ __forceinline__ bool round_to_double(unsigned __int128 M, int k, uint
   return true;
 }
 
-// c_ij = 2^(sigma_i + tau_j - 4(S+1)) sum_c sum_L D[c][L][i][j] 2^(4(S-1-L)):
+// c_ij = 2^(sigma_i + tau_j - 5(S+1)) sum_c sum_L D[c][L][i][j] 32^(S-1-L):
 // the level sums are integers below 2^24, so their weighted sum is formed
 // exactly in 128-bit integers and rounded once to FP64 (then scaled by a
 // power of two, which rounds again only in the subnormal range); NaN where
@@ -408,9 +430,9 @@ ozaki_sum_kernel(const float *__restrict__ D, int64_t plane, int64_t n, int64_t 
   if (j >= p) return;
   bool fb;
   const int tau = slice_exponent(colmax[j], fb);
-  // Horner by 16 over levels 0..h-1 into X and h..S-1 into Y (int64: each
-  // part at most (2^24 - 1)(16^8 - 1)/15 < 2^52.1 per chunk, below 2^63 over
-  // at most kOzakiMaxChunks = 2^10 chunks), then v = X 16^(S-h) + Y once in
+  // Horner by 32 over levels 0..h-1 into X and h..S-1 into Y (int64: each
+  // part at most (2^24 - 1)(32^6 - 1)/31 < 2^49.1 per chunk, below 2^63 over
+  // at most kOzakiMaxChunks = 2^10 chunks), then v = X 32^(S-h) + Y once in
   // 128 bits
   constexpr int h = (S + 1) / 2;
   for (int64_t i = blockIdx.y; i < n; i += gridDim.y) {
@@ -427,19 +449,19 @@ ozaki_sum_kernel(const float *__restrict__ D, int64_t plane, int64_t n, int64_t 
 #pragma unroll
       for (int L = 0; L < S; L++) {
         const int64_t q = __float2int_rn(v[L]);
-        if (L < h) xc = xc * 16 + q;
-        else yc = yc * 16 + q;
+        if (L < h) xc = xc * 32 + q;
+        else yc = yc * 32 + q;
       }
       X += xc;
       Y += yc;
     }
-    constexpr int sh = 4 * (S - h);  // 4..32
+    constexpr int sh = 5 * (S - h);  // 5..30
     uint64_t lo = (uint64_t)X << sh;
     int64_t hi = X >> (64 - sh);
     const uint64_t r = lo + (uint64_t)Y;
     hi += (Y < 0 ? -1 : 0) + (r < lo ? 1 : 0);
     lo = r;
-    const int k = sigma + tau - 4 * (S + 1);
+    const int k = sigma + tau - 5 * (S + 1);
     double out;
     if (!(fa && fb)) {
       out = __longlong_as_double(0x7ff8000000000000ll);
@@ -463,8 +485,7 @@ cudaError_t launch_ozaki_sum(int S, dim3 grid, cudaStream_t s, const float *D, i
 #define MM_OZ_SUM(V) \
   case V: ozaki_sum_kernel<V><<<grid, 256, 0, s>>>(D, plane, n, p, chunks, rowmax, colmax, C); break;
     MM_OZ_SUM(2) MM_OZ_SUM(3) MM_OZ_SUM(4) MM_OZ_SUM(5) MM_OZ_SUM(6) MM_OZ_SUM(7) MM_OZ_SUM(8)
-    MM_OZ_SUM(9) MM_OZ_SUM(10) MM_OZ_SUM(11) MM_OZ_SUM(12) MM_OZ_SUM(13) MM_OZ_SUM(14)
-    MM_OZ_SUM(15) MM_OZ_SUM(16)
+    MM_OZ_SUM(9) MM_OZ_SUM(10) MM_OZ_SUM(11) MM_OZ_SUM(12)
 #undef MM_OZ_SUM
     default: return cudaErrorInvalidValue;
   }
@@ -472,10 +493,10 @@ cudaError_t launch_ozaki_sum(int S, dim3 grid, cudaStream_t s, const float *D, i
 }
 
 // Accuracy gate.  Every term a_ir b_rj of the emulated product is off by at
-// most (S + 2) 2^(sigma_i + tau_j - 4S), so entry (i, j) is off by at most
-// m (S + 2) 2^(sigma_i + tau_j - 4S); the product meets e_ij <= 1e-14 sqrt(m)
+// most (S + 2) 2^(sigma_i + tau_j - 5S - 1), so entry (i, j) is off by at most
+// m (S + 2) 2^(sigma_i + tau_j - 5S - 1); the product meets e_ij <= 1e-14 sqrt(m)
 // wherever P_ij = sum_r |a_ir| 2^-sigma_i |b_rj| 2^-tau_j is at least
-// sqrt(m) (S + 2) 2^-4S 1e14.  A lower bound of 256 P comes from the
+// sqrt(m) (S + 2) 2^(-5S-1) 1e14.  A lower bound of 256 P comes from the
 // emulation's own machinery: one more slice per operand holds gate_value
 // (16 |x| 2^-sigma truncated toward zero onto the e4m3 grid), and one more
 // tensor-core product per K chunk multiplies the two (products exact in
@@ -525,7 +546,7 @@ struct OzLayout {
 }  // namespace
 
 int64_t ozaki_chunk(int S) {
-  const int64_t mc = ((int64_t)((1 << 24) - 1) / (225 * (int64_t)S)) / 128 * 128;
+  const int64_t mc = ((int64_t)((1 << 24) - 1) / (256 * (int64_t)S)) / 128 * 128;
   return mc;
 }
 
@@ -703,7 +724,7 @@ mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *
     const double room = 0.98 - (double)m * 0x1p-23;
     const double thr256 = room < 0.5 ? (double)INFINITY
                                      : 256.0 * std::sqrt((double)m) * (S + 2) *
-                                           std::ldexp(1.0, -4 * S) * 1e14 / room;
+                                           std::ldexp(1.0, -5 * S - 1) * 1e14 / room;
     float thr = (float)thr256;  // rounded up to a float
     if ((double)thr < thr256) thr = std::nextafter(thr, (float)INFINITY);
     const unsigned gc = (unsigned)std::min<int64_t>(n, (int64_t)sm_count() * 8);

@@ -27,17 +27,17 @@ def test_chunk_rule_matches_oracle(mm):
         assert q == 1
 
 
-@pytest.mark.parametrize("m", [0, 1, 127, 5248, 5249, 10496, 100000])
+@pytest.mark.parametrize("m", [0, 1, 127, 5376, 5377, 10752, 100000])
 def test_chunk_count(mm, m):
-    st, mc, q, b = mm.mm_ozaki_plan(300, m, 200, 14)
-    assert st == mm.MM_OK and mc == 5248
+    st, mc, q, b = mm.mm_ozaki_plan(300, m, 200, 12)
+    assert st == mm.MM_OK and mc == 5376
     assert q == math.ceil(m / mc)
     if m == 0:
         assert b == 0
 
 
-@pytest.mark.parametrize("n,m,p,S", [(4096, 4096, 4096, 14), (8192, 8192, 8192, 14),
-                                      (300, 517, 260, 2), (129, 4700, 70, 16), (1, 1, 1, 14)])
+@pytest.mark.parametrize("n,m,p,S", [(4096, 4096, 4096, 12), (8192, 8192, 8192, 12),
+                                      (300, 517, 260, 2), (129, 6000, 70, 11), (1, 1, 1, 12)])
 def test_scratch_bound_covers_digits_and_level_sums(mm, n, m, p, S):
     st, mc, q, b = mm.mm_ozaki_plan(n, m, p, S)
     assert st == mm.MM_OK
@@ -51,9 +51,9 @@ def test_scratch_bound_covers_digits_and_level_sums(mm, n, m, p, S):
 
 def test_arguments(mm):
     assert mm.mm_ozaki_plan(4, 4, 4, 1)[0] == mm.MM_EINVAL
-    assert mm.mm_ozaki_plan(4, 4, 4, 17)[0] == mm.MM_EINVAL
-    assert mm.mm_ozaki_plan(-1, 4, 4, 14)[0] == mm.MM_EINVAL
-    assert mm.mm_ozaki_plan(4, -4, 4, 14)[0] == mm.MM_EINVAL
-    mc = ozaki.chunk_columns(14)
-    assert mm.mm_ozaki_plan(4, 1024 * mc, 4, 14)[0] == mm.MM_OK
-    assert mm.mm_ozaki_plan(4, 1024 * mc + 1, 4, 14)[0] == mm.MM_EINVAL
+    assert mm.mm_ozaki_plan(4, 4, 4, 13)[0] == mm.MM_EINVAL
+    assert mm.mm_ozaki_plan(-1, 4, 4, 12)[0] == mm.MM_EINVAL
+    assert mm.mm_ozaki_plan(4, -4, 4, 12)[0] == mm.MM_EINVAL
+    mc = ozaki.chunk_columns(12)
+    assert mm.mm_ozaki_plan(4, 1024 * mc, 4, 12)[0] == mm.MM_OK
+    assert mm.mm_ozaki_plan(4, 1024 * mc + 1, 4, 12)[0] == mm.MM_EINVAL
