@@ -80,6 +80,9 @@ struct SplitProb {
   // kt, the layout above); a larger stride lets a product read a window of
   // kt K blocks out of a longer pack (the FP64 emulation's level products)
   int32_t a_kstride, b_kstride;
+  // 1 + index of C's tensor map in the launch's map array (tiled stores of
+  // the epilogue); 0: C is written with plain stores
+  int32_t c_tma;
 };
 
 // Work units of a product with its tail split: whole tiles, then the parts.
@@ -186,7 +189,11 @@ cudaError_t launch_tc(TcKind kind, const SplitProb *d_probs, int nprobs,
                       int total_units, const int *unit_map, const int *flags,
                       void *pack_base, int64_t pack_rows, const TcConfig &cfg,
                       int *d_err, cudaStream_t s, const int *order = nullptr,
-                      int uniform_only = 0);
+                      int uniform_only = 0, const void *c_maps = nullptr);
+// Tensor map over C for the tensor-core epilogue's tiled stores (128 bytes
+// written to `map`); usable where tc_c_map_ok holds.
+bool tc_c_map_ok(const float *C, int64_t n, int64_t p);
+cudaError_t encode_c_map(void *map, float *C, int64_t n, int64_t p);
 // CTAs of a tensor-core launch of total_units work units.
 int tc_launch_grid(const TcConfig &cfg, int64_t total_units);
 // Work units per CTA for a table whose units differ in length (a grouped

@@ -51,6 +51,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstring>
 #include <utility>
 #include <vector>
 
@@ -172,15 +173,20 @@ struct TcLayout {
   static constexpr int kColExpOffset = kBarOffset + kNumBars * 8 + 16;  // int[kNumAcc][kMaxBN]
   static constexpr int kLastOffset = kColExpOffset + kNumAcc * kMaxBN * 4;  // last-part flag
   // epilogue staging: one 32 x 33 float block per epilogue warp
-  static constexpr int kStageOffset = kLastOffset + 16;
-  static constexpr int kSmemBytes = kStageOffset + 4 * 32 * 33 * 4 + 1024;  // + align slack
+  // epilogue staging, one 5 KB region per epilogue warp (1024-byte aligned):
+  // a dense 32 x 32 FP32 block with a 128-byte swizzle for the tiled stores,
+  // or rows of 33 floats for the plain stores
+  static constexpr int kStageStride = 5120;
+  static constexpr int kStageOffset = (kLastOffset + 16 + 1023) & ~1023;
+  static constexpr int kSmemBytes = kStageOffset + 4 * kStageStride + 1024;  // + align slack
 };
 
 template <int BKB, int STAGES, int KIND, int MAXBN>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__restrict__ probs,
                int nprobs, const int *__restrict__ unit_map, const int *__restrict__ flags,
-               int total_units, const int *__restrict__ order, int uniform_only, int *err) {
+               int total_units, const int *__restrict__ order, int uniform_only,
+               const CUtensorMap *__restrict__ c_maps, int *err) {
   using L = TcLayout<BKB, STAGES, KIND, MAXBN>;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -395,7 +401,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
       const int64_t i = (int64_t)tc.mt * kTcBM + row;
       const bool row_ok = i < pr.n;
       const int si = (row_ok && (fl & kFlagScaleA)) ? kind_exponent<KIND>(pr.sA[i]) : 0;
-      float *buf = stage_buf + q * 32 * 33;  // this warp's 32 x 32 block (row pitch 33)
+      float *buf = stage_buf + q * (L::kStageStride / 4);  // this warp's 32 x 32 block
+      const CUtensorMap *cmap = (c_maps != nullptr && pr.c_tma > 0) ? c_maps + (pr.c_tma - 1)
+                                                                     : nullptr;
       const int64_t row0 = (int64_t)tc.mt * kTcBM + q * 32;  // first row of the warp
       const uint32_t tacc = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * MAXBN);
       // part of a split tile: a partial slot holds bn/4 groups of 4 columns,
@@ -477,10 +485,34 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
         }
         const int64_t j0 = (int64_t)tc.nt * pr.bn + c;
         if (j0 >= pr.p) continue;  // the same for the whole warp
+        const int *ce = cexp + c;
+        if (cmap) {
+          // the block into the dense staging area, 16-byte chunk k of row
+          // `lane` at chunk k ^ (lane & 7) (the 128-byte swizzle of the map;
+          // the writes of one instruction then spread over all banks), and
+          // one tiled store of it; the area is rewritten only after the
+          // previous store has read it
+          if (lane == 0) bulk_wait_read_all();
+          __syncwarp();
+          float4 *rowp = reinterpret_cast<float4 *>(buf + lane * 32);
+#pragma unroll
+          for (int k = 0; k < 8; k++)
+            rowp[k ^ (lane & 7)] =
+                make_float4(scale_pow2(__uint_as_float(v[4 * k]), si + ce[4 * k]),
+                            scale_pow2(__uint_as_float(v[4 * k + 1]), si + ce[4 * k + 1]),
+                            scale_pow2(__uint_as_float(v[4 * k + 2]), si + ce[4 * k + 2]),
+                            scale_pow2(__uint_as_float(v[4 * k + 3]), si + ce[4 * k + 3]));
+          fence_proxy_async_shared();
+          __syncwarp();
+          if (lane == 0 && row0 < pr.n) {  // a block wholly below C is not stored
+            tma_store_2d(cmap, smem_u32(buf), (int)j0, (int)row0);
+            bulk_commit();
+          }
+          continue;
+        }
         // unscale this thread's row of the 32 x 32 block into shared memory,
         // then write the block row by row: each store is 32 consecutive
         // columns of one row, a whole 128-byte line
-        const int *ce = cexp + c;
 #pragma unroll
         for (int e = 0; e < 32; e++)
           buf[lane * 33 + e] = scale_pow2(__uint_as_float(v[e]), si + ce[e]);
@@ -502,6 +534,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
         acc_phase ^= 1u;
       }
     }
+    // the tiled stores have read shared memory and completed
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
   }
 
   tc_fence_before();
@@ -543,11 +578,39 @@ cudaError_t encode_pack_map(CUtensorMap *map, void *base, int64_t rows, int bkb)
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+}  // namespace
+
+// 2-D map over C (n rows of p FP32, row-major) for the epilogue's tiled
+// stores: boxes of 32 x 32 with a 128-byte swizzle.  Needs a 16-byte aligned
+// C and p a multiple of 4.
+bool tc_c_map_ok(const float *C, int64_t n, int64_t p) {
+  return (reinterpret_cast<uintptr_t>(C) & 15u) == 0 && (p & 3) == 0 && n > 0 && p > 0 &&
+         n <= 0x7fffffffLL && p <= 0x7fffffffLL;
+}
+
+cudaError_t encode_c_map(void *map, float *C, int64_t n, int64_t p) {
+  auto enc = get_encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  cuuint64_t dims[2] = {(cuuint64_t)p, (cuuint64_t)n};
+  cuuint64_t strides[1] = {(cuuint64_t)p * 4};
+  cuuint32_t box[2] = {32u, 32u};
+  cuuint32_t estr[2] = {1, 1};
+  CUtensorMap tmp;  // 64-byte aligned; `map` need not be
+  CUresult r = enc(&tmp, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, C, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  std::memcpy(map, &tmp, sizeof(tmp));
+  return cudaSuccess;
+}
+
+namespace {
+
 template <int BKB, int STAGES, int KIND, int MAXBN>
 cudaError_t launch_tc_t(const SplitProb *d_probs, int nprobs, const int *unit_map,
                         const int *flags, int total_units, void *pack_base, int64_t pack_rows,
                         int grid, int *d_err, cudaStream_t s, const int *order,
-                        int uniform_only) {
+                        int uniform_only, const void *c_maps) {
   using L = TcLayout<BKB, STAGES, KIND, MAXBN>;
   static_assert(L::kSmemBytes <= 232448, "shared memory budget");
   // one CTA per SM: the kernel allocates all 512 TMEM columns
@@ -564,7 +627,8 @@ cudaError_t launch_tc_t(const SplitProb *d_probs, int nprobs, const int *unit_ma
   if (e != cudaSuccess) return e;
   TraceScope ts(KIND == kTcE4m3 ? "fp8_tc" : "split_tc", s);
   tc_gemm_kernel<BKB, STAGES, KIND, MAXBN><<<grid, kThreads, L::kSmemBytes, s>>>(
-      map, d_probs, nprobs, unit_map, flags, total_units, order, uniform_only, d_err);
+      map, d_probs, nprobs, unit_map, flags, total_units, order, uniform_only,
+      static_cast<const CUtensorMap *>(c_maps), d_err);
   return cudaGetLastError();
 }
 
@@ -671,14 +735,14 @@ size_t tc_tail_bytes(const TcTail &t, int64_t tiles, int bn) {
 cudaError_t launch_tc(TcKind kind, const SplitProb *d_probs, int nprobs, int total_units,
                       const int *unit_map, const int *flags, void *pack_base, int64_t pack_rows,
                       const TcConfig &cfg, int *d_err, cudaStream_t s, const int *order,
-                      int uniform_only) {
+                      int uniform_only, const void *c_maps) {
   if (total_units <= 0) return cudaSuccess;
   if (pack_rows <= 0 || pack_rows > 0x7fffffffLL) return cudaErrorInvalidValue;
   const int grid = tc_launch_grid(cfg, total_units);
   const int *mp = unit_map;
 #define MM_TC_ARGS \
   d_probs, nprobs, mp, flags, total_units, pack_base, pack_rows, grid, d_err, s, order, \
-      uniform_only
+      uniform_only, c_maps
   cudaError_t e = cudaErrorInvalidValue;
   const bool narrow = cfg.max_bn <= 128;  // every N tile of the table fits 128
   if (kind == kTcE4m3) e = launch_tc_t<128, 4, kTcE4m3, 256>(MM_TC_ARGS);

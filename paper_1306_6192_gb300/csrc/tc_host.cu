@@ -140,7 +140,12 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
     order_ints += orders[gi].size();
   }
   const size_t tab_bytes = (ntab * sizeof(SplitProb) + 15) & ~(size_t)15;
-  const size_t map_off = (tab_off + tab_bytes + order_ints * sizeof(int) + 255) & ~(size_t)255;
+  // tensor maps over the C matrices for the epilogue's tiled stores, for
+  // tables of up to kMaxCMaps products (each map is encoded on the host)
+  constexpr size_t kMaxCMaps = 64, kMapBytes = 128;
+  const size_t cmap_rel = (tab_bytes + order_ints * sizeof(int) + 63) & ~(size_t)63;
+  const size_t cmap_bytes = ntab <= kMaxCMaps ? ntab * kMapBytes : 0;
+  const size_t map_off = (tab_off + cmap_rel + cmap_bytes + 255) & ~(size_t)255;
   const size_t tpart_off = (map_off + map_ints * sizeof(int) + 255) & ~(size_t)255;
   const size_t need = tpart_off + tail_parts;
   cudaError_t e = ws.reserve(need, s);
@@ -162,10 +167,16 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
     }
   SplitProb *d_tab = reinterpret_cast<SplitProb *>(base + tab_off);
   int *d_orders = reinterpret_cast<int *>(base + tab_off + tab_bytes);
-  if (order_ints == 0) {
-    e = ws.stage.copy_to_device(d_tab, all.data(), all.size() * sizeof(SplitProb), s);
-  } else {
-    std::vector<uint8_t> blob(tab_bytes + order_ints * sizeof(int), 0);
+  const void *d_cmaps = cmap_bytes ? static_cast<const void *>(base + tab_off + cmap_rel) : nullptr;
+  {
+    // one copy: the table, the CTAs' unit lists, the C tensor maps
+    std::vector<uint8_t> blob(cmap_rel + cmap_bytes, 0);
+    for (size_t k = 0; cmap_bytes && k < ntab; k++) {
+      SplitProb &sp = all[k];
+      if (tc_c_map_ok(sp.C, sp.n, sp.p) &&
+          encode_c_map(blob.data() + cmap_rel + k * kMapBytes, sp.C, sp.n, sp.p) == cudaSuccess)
+        sp.c_tma = (int32_t)k + 1;
+    }
     std::memcpy(blob.data(), all.data(), all.size() * sizeof(SplitProb));
     size_t at = tab_bytes;
     for (auto &o : orders) {
@@ -212,7 +223,7 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
       e = launch_split_pack(G.kind, kPackFix, dt, np, (int)G.packs, pack_map, flags, any, base, s);
     if (e == cudaSuccess)
       e = launch_tc(G.kind, dt, np, (int)G.units, tile_map, flags, base, rows, G.cfg, g_ctx.d_err,
-                    s, order);
+                    s, order, 0, d_cmaps);
     if (e != cudaSuccess) return note_cuda(e);
   }
   return MM_OK;

@@ -192,6 +192,37 @@ __device__ __forceinline__ uint32_t make_idesc(int bn) {
          ((uint32_t)(kTcBM >> 4) << 24);
 }
 
+// Tiled bulk store of a box from this CTA's shared memory to global memory
+// through a tensor map (elements outside the tensor are not written), in this
+// thread's current bulk group.  x (the inner coordinate) times the element
+// size must be a multiple of 16 bytes and neither coordinate negative; the
+// shared-memory writes it reads must precede fence_proxy_async_shared() by
+// the writing threads and a barrier with the issuing thread.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, uint32_t src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(src), "r"(x), "r"(y)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// This thread's bulk groups have finished reading shared memory.
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// This thread's bulk groups have completed.
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
 // Paired FP32 arithmetic (two independent lanes in one 64-bit register, the
 // low half first): each half is rounded to nearest exactly as the scalar
 // mul.rn.f32 / fma.rn.f32 would round it.
