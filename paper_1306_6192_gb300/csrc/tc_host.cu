@@ -142,7 +142,7 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
   const size_t tab_bytes = (ntab * sizeof(SplitProb) + 15) & ~(size_t)15;
   // tensor maps over the C matrices for the epilogue's tiled stores, for
   // tables of up to kMaxCMaps products (each map is encoded on the host)
-  constexpr size_t kMaxCMaps = 64, kMapBytes = 128;
+  constexpr size_t kMaxCMaps = 8192, kMapBytes = 128;
   const size_t cmap_rel = (tab_bytes + order_ints * sizeof(int) + 63) & ~(size_t)63;
   const size_t cmap_bytes = ntab <= kMaxCMaps ? ntab * kMapBytes : 0;
   const size_t map_off = (tab_off + cmap_rel + cmap_bytes + 255) & ~(size_t)255;
