@@ -26,9 +26,10 @@
 //             and each finished tile to the epilogue ("acc_full").
 //   warps 2-5 epilogue: tcgen05.ld of the accumulator (each warp reads its
 //             32 TMEM lanes = 32 rows), exact power-of-two unscaling, each
-//             32 x 32 block through shared memory so that every global store
-//             is one whole 128-byte line of a row (edge rows and columns
-//             predicated); then "acc_empty".
+//             32 x 32 block through shared memory: one tiled TMA store per
+//             block where the host gave C a tensor map (the store clips the
+//             edges), else whole 128-byte-line stores of each row (edge rows
+//             and columns predicated); then "acc_empty".
 // Two accumulators of 256 TMEM columns each (four of 128 in the 128-wide
 // layouts) let the epilogue of one tile overlap the mainloop of the next.
 // The work units (tiles, or K parts of split tiles) of all problems of a
