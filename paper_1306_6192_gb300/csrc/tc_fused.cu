@@ -332,18 +332,24 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant
         if (wt == 0) flags[0] = scaled ? 1 : 0;
       }
       // B block: warp w takes K rows 8 w .. 8 w + 7, lane l the columns
-      // 4 l .. 4 l + 3: eight consecutive K values of four columns, i.e. one
-      // 16-byte chunk of four rows of the K-major (transposed) B operand
+      // l + 32 c (c = 0..3): eight consecutive K values of a column, i.e. one
+      // 16-byte chunk of a row of the K-major (transposed) B operand; the
+      // rows a warp writes are 32 apart in c and consecutive in l, so each
+      // chunk store spreads over all banks (rows 4 l + c had put 16 lanes on
+      // each bank group)
       {
         const int w = warp, l = lane;
-        const bool cols_in = col0 + 4 * l < pr.p;  // columns past B: as rows past A
-        float4 y[8];
+        bool col_in[4];  // columns past B: as rows past A
+        float y[8][4];
         bool good = true;
 #pragma unroll
+        for (int c = 0; c < 4; c++) col_in[c] = col0 + l + 32 * c < pr.p;
+#pragma unroll
         for (int t = 0; t < 8; t++) {
-          y[t] = cols_in ? reinterpret_cast<const float4 *>(stg_b)[(8 * w + t) * (kFBN / 4) + l]
-                         : make_float4(0.f, 0.f, 0.f, 0.f);
-          good &= in_range4(y[t]);
+#pragma unroll
+          for (int c = 0; c < 4; c++)
+            y[t][c] = col_in[c] ? stg_b[(8 * w + t) * kFBN + l + 32 * c] : 0.0f;
+          good &= in_range4(make_float4(y[t][0], y[t][1], y[t][2], y[t][3]));
         }
         __syncwarp();
         const bool scaled = !work_all(good);  // also: every worker is done with stg_a
@@ -351,49 +357,37 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant
         if (scaled) {
           uint32_t mx[4] = {0, 0, 0, 0};
 #pragma unroll
-          for (int t = 0; t < 8; t++) {
-            mx[0] = max(mx[0], abs_bits(y[t].x));
-            mx[1] = max(mx[1], abs_bits(y[t].y));
-            mx[2] = max(mx[2], abs_bits(y[t].z));
-            mx[3] = max(mx[3], abs_bits(y[t].w));
-          }
+          for (int t = 0; t < 8; t++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) mx[c] = max(mx[c], abs_bits(y[t][c]));
           // column maxima of the eight warps meet in the (consumed) A staging
           uint32_t *part_max = reinterpret_cast<uint32_t *>(smem + a * L::kStgBytes);
 #pragma unroll
-          for (int c = 0; c < 4; c++) part_max[w * 128 + 4 * l + c] = mx[c];
+          for (int c = 0; c < 4; c++) part_max[w * 128 + l + 32 * c] = mx[c];
           work_sync();
 #pragma unroll
           for (int c = 0; c < 4; c++) {
             uint32_t m8 = 0;
 #pragma unroll
-            for (int ww = 0; ww < kFWorkers / 32; ww++) m8 = max(m8, part_max[ww * 128 + 4 * l + c]);
+            for (int ww = 0; ww < kFWorkers / 32; ww++) m8 = max(m8, part_max[ww * 128 + l + 32 * c]);
             sc[c] = scale_exponent(m8);
           }
         }
         if (w == 0) {
 #pragma unroll
-          for (int c = 0; c < 4; c++) sb[4 * l + c] = (int16_t)sc[c];
+          for (int c = 0; c < 4; c++) sb[l + 32 * c] = (int16_t)sc[c];
         }
-        if (cols_in) {
 #pragma unroll
-          for (int c = 0; c < 4; c++) {
-            uint2 lo[PARTS], hi[PARTS];
-            split4f<PARTS>(c == 0 ? make_float4(y[0].x, y[1].x, y[2].x, y[3].x)
-                         : c == 1 ? make_float4(y[0].y, y[1].y, y[2].y, y[3].y)
-                         : c == 2 ? make_float4(y[0].z, y[1].z, y[2].z, y[3].z)
-                                  : make_float4(y[0].w, y[1].w, y[2].w, y[3].w),
-                           scaled, sc[c], lo);
-            split4f<PARTS>(c == 0 ? make_float4(y[4].x, y[5].x, y[6].x, y[7].x)
-                         : c == 1 ? make_float4(y[4].y, y[5].y, y[6].y, y[7].y)
-                         : c == 2 ? make_float4(y[4].z, y[5].z, y[6].z, y[7].z)
-                                  : make_float4(y[4].w, y[5].w, y[6].w, y[7].w),
-                           scaled, sc[c], hi);
-            const int jr = 4 * l + c;  // row of the K-major B operand
+        for (int c = 0; c < 4; c++) {
+          if (!col_in[c]) continue;
+          uint2 lo[PARTS], hi[PARTS];
+          split4f<PARTS>(make_float4(y[0][c], y[1][c], y[2][c], y[3][c]), scaled, sc[c], lo);
+          split4f<PARTS>(make_float4(y[4][c], y[5][c], y[6][c], y[7][c]), scaled, sc[c], hi);
+          const int jr = l + 32 * c;  // row of the K-major B operand
 #pragma unroll
-            for (int pp = 0; pp < PARTS; pp++)
-              *reinterpret_cast<uint4 *>(op_b + pp * L::kPartBytes + swz(jr, 2 * w)) =
-                  make_uint4(lo[pp].x, lo[pp].y, hi[pp].x, hi[pp].y);
-          }
+          for (int pp = 0; pp < PARTS; pp++)
+            *reinterpret_cast<uint4 *>(op_b + pp * L::kPartBytes + swz(jr, 2 * w)) =
+                make_uint4(lo[pp].x, lo[pp].y, hi[pp].x, hi[pp].y);
         }
         if (wt == 0) flags[1] = scaled ? 1 : 0;
       }
