@@ -58,9 +58,46 @@ def test_grouped_matches_single(mmlib):
         assert e <= oracle.tolerance(m, "f32"), (n, m, p, e)
 
 
+def test_grouped_config4_full(mmlib):
+    """The config-4 workload as the bench runs it: 4096 instances, n, m, p
+    uniform over {32, 64, ..., 1024} (seed 4), seeded uniform[-1,1) operands,
+    one grouped call.  Every instance passes the library's FP64 GPU check
+    (one Freivalds vector and 64 sampled entries against 1e-6 sqrt(m)), and 64
+    instances (every 64th) are compared with the CPU oracle in full."""
+    dims = synth.grouped_dims(4, 4096)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(4)
+    probs = []
+    for (n, m, p) in dims:
+        n, m, p = int(n), int(m), int(p)
+        A = torch.rand((n, m), device="cuda", generator=gen) * 2 - 1
+        B = torch.rand((m, p), device="cuda", generator=gen) * 2 - 1
+        probs.append((n, m, p, A, B, torch.full((n, p), float("nan"), device="cuda")))
+    assert mmlib.mm_gemm_grouped(probs, mmlib.MM_F32, mmlib.MM_MODE_SPLIT_BF16X3) == 0
+    chk = torch.Generator(device="cuda")
+    worst = 0.0
+    for g, (n, m, p, A, B, C) in enumerate(probs):
+        chk.manual_seed(100 + g)
+        x = torch.rand(p, device="cuda", dtype=torch.float64, generator=chk) * 2 - 1
+        I = torch.randint(0, n, (64,), device="cuda", generator=chk)
+        J = torch.randint(0, p, (64,), device="cuda", generator=chk)
+        st, fr, sm = mmlib.mm_check(n, m, p, A, B, C, mmlib.MM_F32, x, I, J)
+        assert st == mmlib.MM_OK
+        e = max(fr, sm) / oracle.tolerance(m, "f32")
+        assert e <= 1.0, (g, n, m, p, fr, sm)
+        worst = max(worst, e)
+    orc = oracle.default()
+    for g in range(0, 4096, 64):
+        n, m, p, A, B, C = probs[g]
+        ref, absref = orc.gemm(A.cpu().numpy(), B.cpu().numpy(), with_abs=True)
+        e = oracle.rel_errors(C.cpu().numpy(), ref, absref).max()
+        assert e <= oracle.tolerance(m, "f32"), (g, n, m, p, e)
+
+
 def test_grouped_config4_sample(mmlib):
     """Config-4 shape mix (n, m, p uniform over {32, 64, ..., 1024}): 256 of
-    the instances in one launch, every one checked against the oracle."""
+    the instances (synth operands) in one launch, every 8th compared with the
+    oracle in full."""
     probs, host = _problems(256, 4)
     assert mmlib.mm_gemm_grouped(probs, mmlib.MM_F32, mmlib.MM_MODE_SPLIT_BF16X3) == 0
     orc = oracle.default()

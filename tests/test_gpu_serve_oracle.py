@@ -6,9 +6,12 @@ submitted as fast as the library admits them.  A 1% sample of the requests
 (every 100th, 500 in all) keeps 1024 seeded output entries each, and each of
 those is compared with the oracle's compensated (Dot2) value under the
 elementwise metric e_ij = |c^_ij - c_ij| / (|A||B|)_ij: at most 1e-6 sqrt(m)
-for FP32 requests and 1e-14 sqrt(m) for FP64 requests.  The operands of
-request k are prefixes of two seeded device buffers, as in the serving
-benchmark, so the host holds one copy of each for the oracle."""
+for FP32 requests and 1e-14 sqrt(m) for FP64 requests; sampled requests whose
+C has at most 2^20 entries also keep all of C for a Freivalds check by the
+oracle ((A B) x against A (B x), normalised by |A| (|B| |x|), within 4 times
+the tolerance).  The operands of request k are prefixes of two seeded device
+buffers, as in the serving benchmark, so the host holds one copy of each for
+the oracle."""
 import collections
 import time
 
@@ -24,6 +27,7 @@ pytestmark = pytest.mark.gpu
 COUNT = 50000
 EVERY = 100       # the 1% sample
 ENTRIES = 1024    # sampled output entries per sampled request
+FULL_MAX = 1 << 20  # sampled requests with at most this many outputs keep all of C
 OUT_CAP = 16 << 30  # outstanding output bytes the client holds at most
 
 
@@ -47,7 +51,7 @@ def test_serving_workload_against_oracle(serving):
     src64 = torch.from_numpy(h64).cuda()
 
     live = collections.OrderedDict()  # request id -> (k, C)
-    kept = {}                         # k -> (I, J, sampled entries of C)
+    kept = {}  # k -> (I, J, sampled entries of C, all of C or None)
     held = [0]
 
     def finish(rid):
@@ -58,7 +62,8 @@ def test_serving_workload_against_oracle(serving):
             I, J = synth.sample_indices(1000 + k, n, p, ENTRIES)
             Ct = C.view(n, p)
             kept[k] = (I, J, Ct[torch.from_numpy(I).cuda(), torch.from_numpy(J).cuda()]
-                       .double().cpu().numpy())
+                       .double().cpu().numpy(),
+                       Ct.double().cpu().numpy() if n * p <= FULL_MAX else None)
 
     def drain(budget=64):
         done = []
@@ -93,7 +98,8 @@ def test_serving_workload_against_oracle(serving):
     orc = oracle.default()
     worst = {False: 0.0, True: 0.0}  # max e_ij / tolerance per class
     emax = {False: 0.0, True: 0.0}
-    for k, (I, J, got) in kept.items():
+    fre = {False: 0.0, True: 0.0}  # max Freivalds ratio / tolerance per class
+    for k, (I, J, got, full) in kept.items():
         n, m, p = (int(v) for v in dims[k])
         src = h64 if f64[k] else h32
         A = src[:n * m].reshape(n, m)
@@ -103,7 +109,15 @@ def test_serving_workload_against_oracle(serving):
         tol = oracle.tolerance(m, "f64" if f64[k] else "f32")
         emax[bool(f64[k])] = max(emax[bool(f64[k])], float(e.max()))
         worst[bool(f64[k])] = max(worst[bool(f64[k])], float(e.max()) / tol)
+        if full is not None:
+            x = synth.freivalds_vector(2000 + k, p)
+            y, _ = orc.gemv(full, x)
+            z, za = orc.freivalds_rhs(A, B, x)
+            r = np.abs(y - z) / np.where(za > 0, za, 1.0)
+            fre[bool(f64[k])] = max(fre[bool(f64[k])], float(r.max()) / tol)
     print("\nserving %d requests in %.1f s (%.0f req/s); 1%% sample: FP32 max e %.3g "
-          "(%.3g of tol), FP64 max e %.3g (%.3g of tol)"
-          % (COUNT, wall, COUNT / wall, emax[False], worst[False], emax[True], worst[True]))
+          "(%.3g of tol), FP64 max e %.3g (%.3g of tol); Freivalds / tol FP32 %.3g, FP64 %.3g"
+          % (COUNT, wall, COUNT / wall, emax[False], worst[False], emax[True], worst[True],
+             fre[False], fre[True]))
     assert worst[False] <= 1.0 and worst[True] <= 1.0
+    assert fre[False] <= 4.0 and fre[True] <= 4.0
