@@ -1,10 +1,12 @@
 """Parity at the full workload sizes (square 1024..8192, rectangular, skinny,
 diagonal, wide exponents) on 4096 sampled entries plus two Freivalds trials,
-in the launch configuration the benchmark times."""
+in the launch configuration the benchmark times; the square sizes up to 2048
+also against the oracle's full product."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
 from gpu_util import dev, sampled_check
 
@@ -25,11 +27,17 @@ def _run(mm, A, B, mode, f64=False):
 
 @pytest.mark.parametrize("n", [1024, 2048, 4096, 8192])
 def test_square_f32_paths(mmlib, n):
+    """Sampled entries and Freivalds at every size; at n <= 2048 also every
+    entry against the oracle's full product."""
     A = synth.uniform_pm1(2 * n, (n, n))
     B = synth.uniform_pm1(2 * n + 1, (n, n))
+    full = oracle.default().gemm(A, B, with_abs=True) if n <= 2048 else None
     for mode in (mmlib.MM_MODE_SPLIT_BF16X3, mmlib.MM_MODE_SIMT):
         C = _run(mmlib, A, B, mode)
         sampled_check(C, A, B, "f32")
+        if full is not None:
+            e = oracle.rel_errors(C, *full).max()
+            assert e <= oracle.tolerance(n, "f32"), (mode, e)
 
 
 @pytest.mark.parametrize("n", [1024, 4096, 8192])
@@ -38,6 +46,9 @@ def test_square_dgemm(mmlib, n):
     B = synth.uniform_pm1(2 * n + 1, (n, n))
     C = _run(mmlib, A, B, mmlib.MM_MODE_DGEMM, f64=True)
     sampled_check(C, A, B, "f64")
+    if n <= 2048:
+        e = oracle.rel_errors(C, *oracle.default().gemm(A, B, with_abs=True)).max()
+        assert e <= oracle.tolerance(n, "f64"), e
 
 
 @pytest.mark.parametrize("shape", [(8192, 512, 8192), (64, 16384, 64)], ids=["rect", "skinny"])
