@@ -15,14 +15,19 @@
  *   MM_MODE_SIMT          FP32 in/out, FP32 FMA on the CUDA cores, shared-
  *                         memory tiled with register blocking.  The paper's
  *                         Listing 4 (shared-memory tiling) is its ancestor.
+ *                         Each entry is summed in ascending r by one thread;
+ *                         a product with too few output tiles for the SMs
+ *                         (from its shape alone) is cut along K into slices
+ *                         whose partial sums are then added in slice order.
  *   MM_MODE_SPLIT_BF16X3  FP32 in/out on the tensor cores: every operand is
  *                         scaled per row (A) / per column (B) by a power of
  *                         two and split into bf16 hi + lo parts; the product
  *                         is accumulated in FP32 as hi.hi + hi.lo + lo.hi
  *                         (tcgen05 MMA, accumulator in tensor memory) and
  *                         unscaled exactly.  Not in the paper.
- *   MM_MODE_DGEMM         FP64 in/out, FP64 FMA.  The paper's Table 2
- *                         "double" column computes this product in double.
+ *   MM_MODE_DGEMM         FP64 in/out, FP64 FMA (K slices as for
+ *                         MM_MODE_SIMT).  The paper's Table 2 "double" column
+ *                         computes this product in double.
  *   MM_MODE_FP8           FP32 in/out through e4m3 operands: each row of A
  *                         and column of B is cut into K blocks of 128 values,
  *                         each block scaled by its own power of two (largest
@@ -348,11 +353,12 @@ mm_status mm_measure_fma_peak(mm_dtype dt, int64_t iters, double *flops_per_s);
 
 /* When enabled, every kernel the library launches is bracketed by CUDA events
  * on its stream; mm_trace_read returns the launch count and summed device
- * time (ms) of the kernel named `kernel` ("simt_f32", "dgemm_f64",
- * "split_maps", "split_pack", "split_verify", "split_fix", "split_tc", "fused_tc",
- * "fp8_pack", "fp8_tc", "fp8_blk", "check_f64", "ozaki_max", "ozaki_map", "ozaki_digits",
- * "ozaki_sum", "ozaki_gate", "add", "diag", "cplx_planes", "cplx_combine") since
- * the last reset.  Reading synchronises the recorded events. */
+ * time (ms) of the kernel named `kernel` ("simt_f32", "dgemm_f64", "simt_sum" (the
+ * fixed-order sum of a K-sliced SIMT or FP64 product), "split_maps", "split_pack",
+ * "split_verify", "split_fix", "split_tc", "fused_tc", "fp8_max", "fp8_pack", "fp8_tc",
+ * "fp8_blk", "check_f64", "ozaki_max", "ozaki_map", "ozaki_digits", "ozaki_sum",
+ * "ozaki_gate", "add", "diag", "cplx_planes", "cplx_combine") since the last reset.
+ * Reading synchronises the recorded events. */
 mm_status mm_trace_enable(int on);
 mm_status mm_trace_reset(void);
 mm_status mm_trace_read(const char *kernel, int64_t *launches, double *total_ms);

@@ -241,10 +241,27 @@ mm_status enqueue_gemm(int64_t n, int64_t m, int64_t p, const void *A, const voi
   }
   switch (md) {
     case MM_MODE_SIMT:
-      return note_cuda(launch_simt_f32(n, m, p, (const float *)A, (const float *)B, (float *)C, s));
-    case MM_MODE_DGEMM:
-      return note_cuda(
-          launch_simt_f64(n, m, p, (const double *)A, (const double *)B, (double *)C, s));
+    case MM_MODE_DGEMM: {
+      // products with few output tiles: K slices and a fixed-order sum
+      const bool f64 = md == MM_MODE_DGEMM;
+      const SimtPlan pl = simt_plan(f64, n, m, p);
+      if (pl.S >= 1) {
+        void *part = nullptr;
+        if (pl.S > 1) {
+          cudaError_t e = g_ctx.simt_ws.reserve(simt_scratch_bytes(f64, n, m, p), s);
+          if (e != cudaSuccess) return note_cuda(e);
+          part = g_ctx.simt_ws.ptr;
+        }
+        return note_cuda(f64 ? launch_simt_splitk_f64(n, m, p, (const double *)A, (const double *)B,
+                                                      (double *)C, (double *)part, pl, s)
+                             : launch_simt_splitk_f32(n, m, p, (const float *)A, (const float *)B,
+                                                      (float *)C, (float *)part, pl, s));
+      }
+      return note_cuda(f64 ? launch_simt_f64(n, m, p, (const double *)A, (const double *)B,
+                                             (double *)C, s)
+                           : launch_simt_f32(n, m, p, (const float *)A, (const float *)B,
+                                             (float *)C, s));
+    }
     case MM_MODE_SPLIT_BF16X3:
     case MM_MODE_SPLIT_BF16X6: {
       // two or three parts by m (x3), three parts (x6); products with few
@@ -391,6 +408,7 @@ mm_status mm_shutdown(void) {
   g_ctx.cplx_ws.release();
   g_ctx.ozaki_ws.release();
   g_ctx.fused_ws.release();
+  g_ctx.simt_ws.release();
   g_ctx.fused_zero_ptr = nullptr;
   g_ctx.fused_zeroed = 0;
   g_ctx.ozaki_slices = kOzakiDefaultSlices;

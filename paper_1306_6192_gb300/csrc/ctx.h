@@ -61,6 +61,7 @@ struct Ctx {
   Scratch cplx_ws;       // real/imaginary planes and partial products (mm_cgemm)
   Scratch ozaki_ws;      // digit packs, level sums and tables of the FP64 emulation
   Scratch fused_ws;      // counters and cluster partial tiles of the fused split-K path
+  Scratch simt_ws;       // K-slice partials of under-filled SIMT / FP64 products
   void *fused_zero_ptr = nullptr;  // fused_ws buffer whose leading counters are zero
   size_t fused_zeroed = 0;         //   and how many bytes of them
   int ozaki_slices = kOzakiDefaultSlices;  // digit slices S of MM_MODE_OZAKI

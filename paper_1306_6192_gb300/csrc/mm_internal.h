@@ -128,6 +128,21 @@ cudaError_t launch_simt_f64(int64_t n, int64_t m, int64_t p, const double *A,
                             const int *run_if = nullptr);
 cudaError_t launch_simt_grouped(bool f64, const SimtProb *d_probs, int nprobs,
                                 int total_tiles, bool all_vec, cudaStream_t s);
+// Split-K of a SIMT product with too few output tiles for the SMs: S slices
+// of ks K values on 64 x 64 tiles (S = 0: the one-pass kernel), from the
+// product's shape alone.  With S > 1 the slices' partials go to `part`
+// (S n p elements) and a second kernel adds them into C in a fixed order.
+struct SimtPlan {
+  int S;
+  int64_t ks;
+};
+SimtPlan simt_plan(bool f64, int64_t n, int64_t m, int64_t p);
+size_t simt_scratch_bytes(bool f64, int64_t n, int64_t m, int64_t p);
+cudaError_t launch_simt_splitk_f32(int64_t n, int64_t m, int64_t p, const float *A, const float *B,
+                                   float *C, float *part, const SimtPlan &pl, cudaStream_t s);
+cudaError_t launch_simt_splitk_f64(int64_t n, int64_t m, int64_t p, const double *A,
+                                   const double *B, double *C, double *part, const SimtPlan &pl,
+                                   cudaStream_t s);
 
 // Prep of the packed split path: the split (hi/lo bf16) into the packs with
 // the row/column maxima, their verification and the re-pack of operands out

@@ -9,7 +9,12 @@
 // predicated edges so any n, m, p works (the listing needs multiples of 16).
 //
 // Every output is accumulated by one thread with r ascending, as in the
-// definition of the Cauchy product.
+// definition of the Cauchy product.  Products with too few output tiles to
+// fill the SMs (skinny ones above all) are cut along K into S slices of
+// 64 x 64 tiles: each slice's partial product in that order, then the S
+// partials of each entry added in a fixed order by a second kernel.
+#include <algorithm>
+
 #include "mm_internal.h"
 
 namespace mm {
@@ -72,9 +77,12 @@ __device__ __forceinline__ void load_vec(const T *__restrict__ X, int64_t ld,
 // vector through a pointer advanced by one K slice per step, no bounds checks.
 // EDGE = true: predicated loads and stores for ragged edges and unaligned
 // operands.
+// A has leading dimension lda and K length kb (a K slice of a longer A when
+// kb < lda); B has kb rows.
 template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC, bool EDGE>
 __device__ __forceinline__ void simt_tile(const T *__restrict__ A, const T *__restrict__ B,
-                                          T *__restrict__ C, int64_t n, int64_t m, int64_t p,
+                                          T *__restrict__ C, int64_t n, int64_t lda, int64_t kb,
+                                          int64_t p,
                                           int64_t tile_m, int64_t tile_n,
                                           T (&As)[2][BK][BM + SimtShape<T, BM, BN, BK, TM, TN>::APAD],
                                           T (&Bs)[2][BK][BN]) {
@@ -100,13 +108,13 @@ __device__ __forceinline__ void simt_tile(const T *__restrict__ A, const T *__re
     for (int j = 0; j < TN; j++) acc[i][j] = T(0);
 
   T ra[S::VA][W], rb[S::VB][W];
-  const T *pa = A + (m0 + a_row) * m + (int64_t)a_kv * W;  // interior pointers
+  const T *pa = A + (m0 + a_row) * lda + (int64_t)a_kv * W;  // interior pointers
   const T *pb = B + (int64_t)b_k * p + n0 + (int64_t)b_nv * W;
   auto load_slice = [&](int64_t k0) {
     if (!EDGE) {
 #pragma unroll
       for (int i = 0; i < S::VA; i++)
-        *reinterpret_cast<V *>(ra[i]) = *reinterpret_cast<const V *>(pa + (int64_t)i * ROWS_A * m);
+        *reinterpret_cast<V *>(ra[i]) = *reinterpret_cast<const V *>(pa + (int64_t)i * ROWS_A * lda);
 #pragma unroll
       for (int i = 0; i < S::VB; i++)
         *reinterpret_cast<V *>(rb[i]) = *reinterpret_cast<const V *>(pb + (int64_t)i * KS_B * p);
@@ -115,10 +123,10 @@ __device__ __forceinline__ void simt_tile(const T *__restrict__ A, const T *__re
     } else {
 #pragma unroll
       for (int i = 0; i < S::VA; i++)
-        load_vec<T, VEC>(A, m, n, m, m0 + a_row + i * ROWS_A, k0 + (int64_t)a_kv * W, ra[i]);
+        load_vec<T, VEC>(A, lda, n, kb, m0 + a_row + i * ROWS_A, k0 + (int64_t)a_kv * W, ra[i]);
 #pragma unroll
       for (int i = 0; i < S::VB; i++)
-        load_vec<T, VEC>(B, p, m, p, k0 + b_k + i * KS_B, n0 + (int64_t)b_nv * W, rb[i]);
+        load_vec<T, VEC>(B, p, kb, p, k0 + b_k + i * KS_B, n0 + (int64_t)b_nv * W, rb[i]);
     }
   };
   // column of A's shared tile for row r at K index k: groups of 4 rows XOR
@@ -137,7 +145,7 @@ __device__ __forceinline__ void simt_tile(const T *__restrict__ A, const T *__re
       *reinterpret_cast<V *>(&Bs[buf][b_k + i * KS_B][b_nv * W]) = *reinterpret_cast<V *>(rb[i]);
   };
 
-  const int64_t ktiles = (m + BK - 1) / BK;
+  const int64_t ktiles = (kb + BK - 1) / BK;
   if (ktiles > 0) {
     load_slice(0);
     store_slice(0);
@@ -199,15 +207,15 @@ __device__ __forceinline__ void simt_tile(const T *__restrict__ A, const T *__re
 // Interior tiles of aligned operands take the unchecked form.
 template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
 __device__ __forceinline__ void simt_tile_any(const T *__restrict__ A, const T *__restrict__ B,
-                                              T *__restrict__ C, int64_t n, int64_t m, int64_t p,
-                                              int64_t tile_m, int64_t tile_n) {
+                                              T *__restrict__ C, int64_t n, int64_t lda, int64_t kb,
+                                              int64_t p, int64_t tile_m, int64_t tile_n) {
   __shared__ __align__(16) T As[2][BK][BM + SimtShape<T, BM, BN, BK, TM, TN>::APAD];
   __shared__ __align__(16) T Bs[2][BK][BN];
-  const bool interior = VEC && (tile_m + 1) * BM <= n && (tile_n + 1) * BN <= p && m % BK == 0;
+  const bool interior = VEC && (tile_m + 1) * BM <= n && (tile_n + 1) * BN <= p && kb % BK == 0;
   if (interior)
-    simt_tile<T, BM, BN, BK, TM, TN, VEC, false>(A, B, C, n, m, p, tile_m, tile_n, As, Bs);
+    simt_tile<T, BM, BN, BK, TM, TN, VEC, false>(A, B, C, n, lda, kb, p, tile_m, tile_n, As, Bs);
   else
-    simt_tile<T, BM, BN, BK, TM, TN, VEC, true>(A, B, C, n, m, p, tile_m, tile_n, As, Bs);
+    simt_tile<T, BM, BN, BK, TM, TN, VEC, true>(A, B, C, n, lda, kb, p, tile_m, tile_n, As, Bs);
 }
 
 template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
@@ -216,7 +224,48 @@ simt_gemm_kernel(const T *__restrict__ A, const T *__restrict__ B, T *__restrict
                  int64_t n, int64_t m, int64_t p, const int *__restrict__ run_if) {
   // run_if: a device word; when given, the product runs only where it is set
   if (run_if != nullptr && *reinterpret_cast<const volatile int *>(run_if) == 0) return;
-  simt_tile_any<T, BM, BN, BK, TM, TN, VEC>(A, B, C, n, m, p, blockIdx.y, blockIdx.x);
+  simt_tile_any<T, BM, BN, BK, TM, TN, VEC>(A, B, C, n, m, m, p, blockIdx.y, blockIdx.x);
+}
+
+// K slice blockIdx.z (K values [z ks, min((z + 1) ks, m))) of a product on
+// 64 x 64 tiles, into part + z n p (C's layout).  ks is a multiple of BK, so
+// the slice's first column of A keeps A's 16-byte alignment.
+template <typename T, int BK, bool VEC>
+__global__ void __launch_bounds__(256, (SimtShape<T, 64, 64, BK, 4, 4>::MIN_BLOCKS))
+simt_splitk_kernel(const T *__restrict__ A, const T *__restrict__ B, T *__restrict__ part,
+                   int64_t n, int64_t m, int64_t p, int64_t ks) {
+  const int64_t k0 = (int64_t)blockIdx.z * ks;
+  const int64_t kb = min(ks, m - k0);
+  simt_tile_any<T, 64, 64, BK, 4, 4, VEC>(A + k0, B + k0 * p, part + (int64_t)blockIdx.z * n * p, n,
+                                          m, kb, p, blockIdx.y, blockIdx.x);
+}
+
+// C = sum over s of part[s] for the np entries: slices added in the order
+// 0, 1, ..., S-1 (one thread per entry), or, for many slices, one warp per
+// entry whose lane l adds slices l, l + 32, ... in order and whose lanes are
+// then combined by a fixed butterfly (lane 0's value is stored).
+template <typename T, bool WARP>
+__global__ void __launch_bounds__(256)
+splitk_sum_kernel(const T *__restrict__ part, int S, int64_t np, T *__restrict__ C) {
+  if (!WARP) {
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < np; i += (int64_t)gridDim.x * 256) {
+      T acc = part[i];
+#pragma unroll 8
+      for (int s = 1; s < S; s++) acc += part[(int64_t)s * np + i];
+      C[i] = acc;
+    }
+  } else {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = ((int64_t)blockIdx.x * 256 + threadIdx.x) >> 5; i < np;
+         i += ((int64_t)gridDim.x * 256) >> 5) {
+      T acc = T(0);
+#pragma unroll 4
+      for (int s = lane; s < S; s += 32) acc += part[(int64_t)s * np + i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) C[i] = acc;
+    }
+  }
 }
 
 // Grouped form: one block per output tile over all problems of a table; the
@@ -234,7 +283,7 @@ simt_grouped_kernel(const SimtProb *__restrict__ probs, int nprobs) {
   const int local = t - pr.tile_start;
   simt_tile_any<T, BM, BN, BK, TM, TN, VEC>(
       static_cast<const T *>(pr.A), static_cast<const T *>(pr.B), static_cast<T *>(pr.C),
-      pr.n, pr.m, pr.p, local / pr.tiles_n, local % pr.tiles_n);
+      pr.n, pr.m, pr.m, pr.p, local / pr.tiles_n, local % pr.tiles_n);
 }
 
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
@@ -255,7 +304,76 @@ cudaError_t launch_simt(int64_t n, int64_t m, int64_t p, const T *A, const T *B,
   return cudaGetLastError();
 }
 
+template <typename T, int BK>
+cudaError_t launch_splitk(int64_t n, int64_t m, int64_t p, const T *A, const T *B, T *C, T *part,
+                          const SimtPlan &pl, cudaStream_t s, const char *name) {
+  constexpr int W = 16 / (int)sizeof(T);
+  const int64_t gy = ceil_div(n, 64), gx = ceil_div(p, 64);
+  if (gy > 65535 || gx > 2147483647LL || pl.S < 1 || pl.S > 65535) return cudaErrorInvalidValue;
+  T *out = pl.S > 1 ? part : C;
+  if (pl.S > 1 && part == nullptr) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)pl.S);
+  const bool vec = aligned16(A) && aligned16(B) && aligned16(out) && m % W == 0 && p % W == 0;
+  {
+    TraceScope ts(name, s);
+    if (vec)
+      simt_splitk_kernel<T, BK, true><<<grid, 256, 0, s>>>(A, B, out, n, m, p, pl.ks);
+    else
+      simt_splitk_kernel<T, BK, false><<<grid, 256, 0, s>>>(A, B, out, n, m, p, pl.ks);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || pl.S == 1) return e;
+  TraceScope ts("simt_sum", s);
+  const int64_t np = n * p;
+  if (pl.S > 16) {
+    const int64_t blocks = std::min<int64_t>(ceil_div(np * 32, 256), (int64_t)sm_count() * 8);
+    splitk_sum_kernel<T, true><<<(unsigned)blocks, 256, 0, s>>>(part, pl.S, np, C);
+  } else {
+    const int64_t blocks = std::min<int64_t>(ceil_div(np, 256), (int64_t)sm_count() * 8);
+    splitk_sum_kernel<T, false><<<(unsigned)blocks, 256, 0, s>>>(part, pl.S, np, C);
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+SimtPlan simt_plan(bool f64, int64_t n, int64_t m, int64_t p) {
+  SimtPlan pl{0, 0};
+  if (n <= 0 || m <= 0 || p <= 0) return pl;
+  const int sms = sm_count();
+  const int64_t bm = f64 ? kSimtF64BM : kSimtF32BM, bn = f64 ? kSimtF64BN : kSimtF32BN;
+  // products that fill at least half of the SMs with whole tiles keep the
+  // one-pass kernel
+  if (2 * ceil_div(n, bm) * ceil_div(p, bn) >= sms) return pl;
+  const int64_t tiles = ceil_div(n, 64) * ceil_div(p, 64);
+  const int64_t bk = f64 ? kSimtF64BK : kSimtF32BK;
+  const size_t es = f64 ? 8 : 4;
+  // about two CTAs per SM, slices of at least 128 K values, partials of at
+  // most 256 MiB
+  int64_t S = std::min(ceil_div(2 * (int64_t)sms, tiles), m / 128);
+  S = std::min<int64_t>(S, (int64_t)((size_t(256) << 20) / ((size_t)(n * p) * es)));
+  S = std::max<int64_t>(1, std::min<int64_t>(S, 1024));
+  const int64_t ks = ceil_div(ceil_div(m, S), bk) * bk;
+  pl.S = (int)ceil_div(m, ks);
+  pl.ks = ks;
+  return pl;
+}
+
+size_t simt_scratch_bytes(bool f64, int64_t n, int64_t m, int64_t p) {
+  const SimtPlan pl = simt_plan(f64, n, m, p);
+  return pl.S > 1 ? (size_t)pl.S * (size_t)(n * p) * (f64 ? 8 : 4) : 0;
+}
+
+cudaError_t launch_simt_splitk_f32(int64_t n, int64_t m, int64_t p, const float *A, const float *B,
+                                   float *C, float *part, const SimtPlan &pl, cudaStream_t s) {
+  return launch_splitk<float, kSimtF32BK>(n, m, p, A, B, C, part, pl, s, "simt_f32");
+}
+
+cudaError_t launch_simt_splitk_f64(int64_t n, int64_t m, int64_t p, const double *A,
+                                   const double *B, double *C, double *part, const SimtPlan &pl,
+                                   cudaStream_t s) {
+  return launch_splitk<double, kSimtF64BK>(n, m, p, A, B, C, part, pl, s, "dgemm_f64");
+}
 
 cudaError_t launch_simt_f32(int64_t n, int64_t m, int64_t p, const float *A, const float *B,
                             float *C, cudaStream_t s) {
