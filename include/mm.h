@@ -18,7 +18,7 @@
  *                         Each entry is summed in ascending r by one thread;
  *                         a product with too few output tiles for the SMs
  *                         (from its shape alone) is cut along K into slices
- *                         whose partial sums are then added in slice order.
+ *                         whose partial sums are then added in a fixed order.
  *   MM_MODE_SPLIT_BF16X3  FP32 in/out on the tensor cores: every operand is
  *                         scaled per row (A) / per column (B) by a power of
  *                         two and split into bf16 hi + lo parts; the product

@@ -12,7 +12,8 @@
 // definition of the Cauchy product.  Products with too few output tiles to
 // fill the SMs (skinny ones above all) are cut along K into S slices of
 // 64 x 64 tiles: each slice's partial product in that order, then the S
-// partials of each entry added in a fixed order by a second kernel.
+// partials of each entry added in a fixed grouping and order by a second
+// kernel.
 #include <algorithm>
 
 #include "mm_internal.h"
@@ -240,31 +241,29 @@ simt_splitk_kernel(const T *__restrict__ A, const T *__restrict__ B, T *__restri
                                           m, kb, p, blockIdx.y, blockIdx.x);
 }
 
-// C = sum over s of part[s] for the np entries: slices added in the order
-// 0, 1, ..., S-1 (one thread per entry), or, for many slices, one warp per
-// entry whose lane l adds slices l, l + 32, ... in order and whose lanes are
-// then combined by a fixed butterfly (lane 0's value is stored).
-template <typename T, bool WARP>
+// C = sum over s of part[s] for the np entries, 32 consecutive entries per
+// block (the loads of a slice coalesce): warp g adds slices [g S / G,
+// (g + 1) S / G) in order (G = min(8, S)), then the G partial sums are added
+// in the order g = 0, 1, ..., G - 1.
+template <typename T>
 __global__ void __launch_bounds__(256)
 splitk_sum_kernel(const T *__restrict__ part, int S, int64_t np, T *__restrict__ C) {
-  if (!WARP) {
-    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < np; i += (int64_t)gridDim.x * 256) {
-      T acc = part[i];
+  __shared__ T ps[8][32];
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int G = min(8, S);
+  const int64_t i = (int64_t)blockIdx.x * 32 + lane;
+  if (g < G && i < np) {
+    const int s0 = (int)((int64_t)g * S / G), s1 = (int)((int64_t)(g + 1) * S / G);
+    T acc = part[(int64_t)s0 * np + i];
 #pragma unroll 8
-      for (int s = 1; s < S; s++) acc += part[(int64_t)s * np + i];
-      C[i] = acc;
-    }
-  } else {
-    const int lane = threadIdx.x & 31;
-    for (int64_t i = ((int64_t)blockIdx.x * 256 + threadIdx.x) >> 5; i < np;
-         i += ((int64_t)gridDim.x * 256) >> 5) {
-      T acc = T(0);
-#pragma unroll 4
-      for (int s = lane; s < S; s += 32) acc += part[(int64_t)s * np + i];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) C[i] = acc;
-    }
+    for (int s = s0 + 1; s < s1; s++) acc += part[(int64_t)s * np + i];
+    ps[g][lane] = acc;
+  }
+  __syncthreads();
+  if (g == 0 && i < np) {
+    T acc = ps[0][lane];
+    for (int gg = 1; gg < G; gg++) acc += ps[gg][lane];
+    C[i] = acc;
   }
 }
 
@@ -325,13 +324,8 @@ cudaError_t launch_splitk(int64_t n, int64_t m, int64_t p, const T *A, const T *
   if (e != cudaSuccess || pl.S == 1) return e;
   TraceScope ts("simt_sum", s);
   const int64_t np = n * p;
-  if (pl.S > 16) {
-    const int64_t blocks = std::min<int64_t>(ceil_div(np * 32, 256), (int64_t)sm_count() * 8);
-    splitk_sum_kernel<T, true><<<(unsigned)blocks, 256, 0, s>>>(part, pl.S, np, C);
-  } else {
-    const int64_t blocks = std::min<int64_t>(ceil_div(np, 256), (int64_t)sm_count() * 8);
-    splitk_sum_kernel<T, false><<<(unsigned)blocks, 256, 0, s>>>(part, pl.S, np, C);
-  }
+  if (ceil_div(np, 32) > 2147483647LL) return cudaErrorInvalidValue;
+  splitk_sum_kernel<T><<<(unsigned)ceil_div(np, 32), 256, 0, s>>>(part, pl.S, np, C);
   return cudaGetLastError();
 }
 
