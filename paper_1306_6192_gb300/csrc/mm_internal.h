@@ -129,12 +129,14 @@ cudaError_t launch_simt_f64(int64_t n, int64_t m, int64_t p, const double *A,
 cudaError_t launch_simt_grouped(bool f64, const SimtProb *d_probs, int nprobs,
                                 int total_tiles, bool all_vec, cudaStream_t s);
 // Split-K of a SIMT product with too few output tiles for the SMs: S slices
-// of ks K values on 64 x 64 tiles (S = 0: the one-pass kernel), from the
-// product's shape alone.  With S > 1 the slices' partials go to `part`
-// (S n p elements) and a second kernel adds them into C in a fixed order.
+// of ks K values (S = 0: the one-pass kernel) on 64 x 64 tiles, or 128 x 128
+// (wide: FP32 products at least 128 wide both ways), from the product's shape
+// alone.  With S > 1 the slices' partials go to `part` (S n p elements) and a
+// second kernel adds them into C in a fixed order.
 struct SimtPlan {
   int S;
   int64_t ks;
+  bool wide;
 };
 SimtPlan simt_plan(bool f64, int64_t n, int64_t m, int64_t p);
 size_t simt_scratch_bytes(bool f64, int64_t n, int64_t m, int64_t p);

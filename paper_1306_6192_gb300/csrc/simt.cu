@@ -10,8 +10,9 @@
 //
 // Every output is accumulated by one thread with r ascending, as in the
 // definition of the Cauchy product.  Products with too few output tiles to
-// fill the SMs (skinny ones above all) are cut along K into S slices of
-// 64 x 64 tiles: each slice's partial product in that order, then the S
+// fill the SMs (skinny ones above all) are cut along K into S slices (64 x 64
+// tiles, or 128 x 128 for FP32 products at least 128 wide both ways): each
+// slice's partial product in that order, then the S
 // partials of each entry added in a fixed grouping and order by a second
 // kernel.
 #include <algorithm>
@@ -228,17 +229,17 @@ simt_gemm_kernel(const T *__restrict__ A, const T *__restrict__ B, T *__restrict
   simt_tile_any<T, BM, BN, BK, TM, TN, VEC>(A, B, C, n, m, m, p, blockIdx.y, blockIdx.x);
 }
 
-// K slice blockIdx.z (K values [z ks, min((z + 1) ks, m))) of a product on
-// 64 x 64 tiles, into part + z n p (C's layout).  ks is a multiple of BK, so
-// the slice's first column of A keeps A's 16-byte alignment.
-template <typename T, int BK, bool VEC>
-__global__ void __launch_bounds__(256, (SimtShape<T, 64, 64, BK, 4, 4>::MIN_BLOCKS))
+// K slice blockIdx.z (K values [z ks, min((z + 1) ks, m))) of a product,
+// into part + z n p (C's layout).  ks is a multiple of BK, so the slice's
+// first column of A keeps A's 16-byte alignment.
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
+__global__ void __launch_bounds__(256, (SimtShape<T, BM, BN, BK, TM, TN>::MIN_BLOCKS))
 simt_splitk_kernel(const T *__restrict__ A, const T *__restrict__ B, T *__restrict__ part,
                    int64_t n, int64_t m, int64_t p, int64_t ks) {
   const int64_t k0 = (int64_t)blockIdx.z * ks;
   const int64_t kb = min(ks, m - k0);
-  simt_tile_any<T, 64, 64, BK, 4, 4, VEC>(A + k0, B + k0 * p, part + (int64_t)blockIdx.z * n * p, n,
-                                          m, kb, p, blockIdx.y, blockIdx.x);
+  simt_tile_any<T, BM, BN, BK, TM, TN, VEC>(A + k0, B + k0 * p, part + (int64_t)blockIdx.z * n * p,
+                                            n, m, kb, p, blockIdx.y, blockIdx.x);
 }
 
 // C = sum over s of part[s] for the np entries, 32 consecutive entries per
@@ -303,11 +304,11 @@ cudaError_t launch_simt(int64_t n, int64_t m, int64_t p, const T *A, const T *B,
   return cudaGetLastError();
 }
 
-template <typename T, int BK>
+template <typename T, int BM, int BN, int BK, int TM, int TN>
 cudaError_t launch_splitk(int64_t n, int64_t m, int64_t p, const T *A, const T *B, T *C, T *part,
                           const SimtPlan &pl, cudaStream_t s, const char *name) {
   constexpr int W = 16 / (int)sizeof(T);
-  const int64_t gy = ceil_div(n, 64), gx = ceil_div(p, 64);
+  const int64_t gy = ceil_div(n, BM), gx = ceil_div(p, BN);
   if (gy > 65535 || gx > 2147483647LL || pl.S < 1 || pl.S > 65535) return cudaErrorInvalidValue;
   T *out = pl.S > 1 ? part : C;
   if (pl.S > 1 && part == nullptr) return cudaErrorInvalidValue;
@@ -316,9 +317,9 @@ cudaError_t launch_splitk(int64_t n, int64_t m, int64_t p, const T *A, const T *
   {
     TraceScope ts(name, s);
     if (vec)
-      simt_splitk_kernel<T, BK, true><<<grid, 256, 0, s>>>(A, B, out, n, m, p, pl.ks);
+      simt_splitk_kernel<T, BM, BN, BK, TM, TN, true><<<grid, 256, 0, s>>>(A, B, out, n, m, p, pl.ks);
     else
-      simt_splitk_kernel<T, BK, false><<<grid, 256, 0, s>>>(A, B, out, n, m, p, pl.ks);
+      simt_splitk_kernel<T, BM, BN, BK, TM, TN, false><<<grid, 256, 0, s>>>(A, B, out, n, m, p, pl.ks);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || pl.S == 1) return e;
@@ -332,19 +333,24 @@ cudaError_t launch_splitk(int64_t n, int64_t m, int64_t p, const T *A, const T *
 }  // namespace
 
 SimtPlan simt_plan(bool f64, int64_t n, int64_t m, int64_t p) {
-  SimtPlan pl{0, 0};
+  SimtPlan pl{0, 0, false};
   if (n <= 0 || m <= 0 || p <= 0) return pl;
   const int sms = sm_count();
   const int64_t bm = f64 ? kSimtF64BM : kSimtF32BM, bn = f64 ? kSimtF64BN : kSimtF32BN;
   // products that fill at least half of the SMs with whole tiles keep the
   // one-pass kernel
   if (2 * ceil_div(n, bm) * ceil_div(p, bn) >= sms) return pl;
-  const int64_t tiles = ceil_div(n, 64) * ceil_div(p, 64);
+  // FP32 products at least 128 wide both ways keep the 128 x 128 tiles (8 x 8
+  // outputs a thread: a quarter of the shared-memory reads per FMA of the
+  // 64 x 64 tiles); narrower ones and FP64 take 64 x 64
+  pl.wide = !f64 && n >= 128 && p >= 128;
+  const int64_t tw = pl.wide ? 128 : 64;
+  const int64_t tiles = ceil_div(n, tw) * ceil_div(p, tw);
   const int64_t bk = f64 ? kSimtF64BK : kSimtF32BK;
   const size_t es = f64 ? 8 : 4;
-  // about two CTAs per SM, slices of at least 128 K values, partials of at
-  // most 256 MiB
-  int64_t S = std::min(ceil_div(2 * (int64_t)sms, tiles), m / 128);
+  // at most two CTAs per SM (one wave), slices of at least 128 K values,
+  // partials of at most 256 MiB
+  int64_t S = std::min(2 * (int64_t)sms / tiles, m / 128);
   S = std::min<int64_t>(S, (int64_t)((size_t(256) << 20) / ((size_t)(n * p) * es)));
   S = std::max<int64_t>(1, std::min<int64_t>(S, 1024));
   const int64_t ks = ceil_div(ceil_div(m, S), bk) * bk;
@@ -360,13 +366,17 @@ size_t simt_scratch_bytes(bool f64, int64_t n, int64_t m, int64_t p) {
 
 cudaError_t launch_simt_splitk_f32(int64_t n, int64_t m, int64_t p, const float *A, const float *B,
                                    float *C, float *part, const SimtPlan &pl, cudaStream_t s) {
-  return launch_splitk<float, kSimtF32BK>(n, m, p, A, B, C, part, pl, s, "simt_f32");
+  if (pl.wide)
+    return launch_splitk<float, kSimtF32BM, kSimtF32BN, kSimtF32BK, 8, 8>(n, m, p, A, B, C, part, pl, s,
+                                                                         "simt_f32");
+  return launch_splitk<float, 64, 64, kSimtF32BK, 4, 4>(n, m, p, A, B, C, part, pl, s, "simt_f32");
 }
 
 cudaError_t launch_simt_splitk_f64(int64_t n, int64_t m, int64_t p, const double *A,
                                    const double *B, double *C, double *part, const SimtPlan &pl,
                                    cudaStream_t s) {
-  return launch_splitk<double, kSimtF64BK>(n, m, p, A, B, C, part, pl, s, "dgemm_f64");
+  return launch_splitk<double, kSimtF64BM, kSimtF64BN, kSimtF64BK, 4, 4>(n, m, p, A, B, C, part, pl, s,
+                                                                         "dgemm_f64");
 }
 
 cudaError_t launch_simt_f32(int64_t n, int64_t m, int64_t p, const float *A, const float *B,

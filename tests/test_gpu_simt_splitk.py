@@ -24,7 +24,8 @@ def _launches(mm, fn):
     return mm.mm_launch_count() - l0
 
 
-@pytest.mark.parametrize("shape", [(64, 16384, 64), (70, 4999, 33), (1, 3000, 1), (200, 2048, 150)])
+@pytest.mark.parametrize("shape", [(64, 16384, 64), (70, 4999, 33), (1, 3000, 1), (200, 2048, 150),
+                                   (1024, 1024, 1024)])
 def test_simt_splitk_against_oracle(mmlib, shape):
     """Skinny (the config-3 shape), ragged with K not a multiple of 4 (the
     unaligned loads), one entry, and a product of a few tiles; FP32 and FP64."""
