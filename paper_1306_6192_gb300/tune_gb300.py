@@ -24,9 +24,11 @@ TABLE = os.path.join(HERE, "tune_gb300.txt")
 
 # Single-product shapes: the square sizes, the rectangular and the skinny
 # workload.  Buckets of the grouped range (dims 32..1024) are left to the
-# built-in choice: timed alone, their problems prefer 128-wide tiles (less
-# padding), but a launch of thousands of them runs faster with 256-wide tiles
-# (measured on GB300: 100.7 vs 93.2 TFLOP/s for the 4096-instance mix).
+# built-in choice: their K is below 2237, so they take the three-part split,
+# whose layout is fixed (128-wide tiles, 32 bf16 of K per stage, four stages),
+# and the knobs left (raster band height, grid) were timed on the whole
+# 4096-instance mix on GB300 (band 1 to 16, grid 148 or 152: 97.6 to 99.2
+# TFLOP/s against 98.4 for the built-in choice, within the run-to-run spread).
 SHAPES = ([(s, s, s) for s in (256, 512, 1024, 2048, 4096, 8192)] +
           [(8192, 512, 8192), (64, 16384, 64), (16384, 16384, 16384)])
 
