@@ -236,6 +236,11 @@ template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
 __global__ void __launch_bounds__(256, (SimtShape<T, BM, BN, BK, TM, TN>::MIN_BLOCKS))
 simt_splitk_kernel(const T *__restrict__ A, const T *__restrict__ B, T *__restrict__ part,
                    int64_t n, int64_t m, int64_t p, int64_t ks) {
+  // launched as a programmatic dependent of the previous kernel on the
+  // stream: resident early, it reads nothing before that kernel has finished
+  // and its writes are visible; the sum kernel may then be scheduled
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int64_t k0 = (int64_t)blockIdx.z * ks;
   const int64_t kb = min(ks, m - k0);
   simt_tile_any<T, BM, BN, BK, TM, TN, VEC>(A + k0, B + k0 * p, part + (int64_t)blockIdx.z * n * p,
@@ -250,6 +255,8 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 splitk_sum_kernel(const T *__restrict__ part, int S, int64_t np, T *__restrict__ C) {
   __shared__ T ps[8][32];
+  asm volatile("griddepcontrol.wait;" ::: "memory");  // the slices' partials are written
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int G = min(8, S);
   const int64_t i = (int64_t)blockIdx.x * 32 + lane;
@@ -304,6 +311,25 @@ cudaError_t launch_simt(int64_t n, int64_t m, int64_t p, const T *A, const T *B,
   return cudaGetLastError();
 }
 
+// Launch with programmatic stream serialization: the kernel may start while
+// the stream's previous kernel finishes (it waits for it with
+// griddepcontrol.wait before touching memory), which hides the gap between
+// the launches of small products.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 cudaError_t launch_splitk(int64_t n, int64_t m, int64_t p, const T *A, const T *B, T *C, T *part,
                           const SimtPlan &pl, cudaStream_t s, const char *name) {
@@ -314,20 +340,20 @@ cudaError_t launch_splitk(int64_t n, int64_t m, int64_t p, const T *A, const T *
   if (pl.S > 1 && part == nullptr) return cudaErrorInvalidValue;
   dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)pl.S);
   const bool vec = aligned16(A) && aligned16(B) && aligned16(out) && m % W == 0 && p % W == 0;
+  cudaError_t e;
   {
     TraceScope ts(name, s);
-    if (vec)
-      simt_splitk_kernel<T, BM, BN, BK, TM, TN, true><<<grid, 256, 0, s>>>(A, B, out, n, m, p, pl.ks);
-    else
-      simt_splitk_kernel<T, BM, BN, BK, TM, TN, false><<<grid, 256, 0, s>>>(A, B, out, n, m, p, pl.ks);
+    e = vec ? launch_dependent(simt_splitk_kernel<T, BM, BN, BK, TM, TN, true>, grid, s, A, B, out, n, m,
+                               p, pl.ks)
+            : launch_dependent(simt_splitk_kernel<T, BM, BN, BK, TM, TN, false>, grid, s, A, B, out, n, m,
+                               p, pl.ks);
   }
-  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || pl.S == 1) return e;
   TraceScope ts("simt_sum", s);
   const int64_t np = n * p;
   if (ceil_div(np, 32) > 2147483647LL) return cudaErrorInvalidValue;
-  splitk_sum_kernel<T><<<(unsigned)ceil_div(np, 32), 256, 0, s>>>(part, pl.S, np, C);
-  return cudaGetLastError();
+  return launch_dependent(splitk_sum_kernel<T>, dim3((unsigned)ceil_div(np, 32), 1, 1), s,
+                          static_cast<const T *>(part), pl.S, np, C);
 }
 
 }  // namespace

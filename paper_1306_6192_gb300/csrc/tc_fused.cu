@@ -218,6 +218,11 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t *>(tmem_holder);
+  // launched as a programmatic dependent of the stream's previous kernel:
+  // the set-up above may overlap its end; nothing in global memory is read
+  // or written before it has finished
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
   if (warp < kFMma) {
     // ------------------------------------------------------------ workers
@@ -650,13 +655,15 @@ cudaError_t launch_fused_t(const FusedProb &pr, int cs, int *d_err, cudaStream_t
   cfg.blockDim = dim3(kFThreads, 1, 1);
   cfg.dynamicSmemBytes = L::kSmemBytes;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)cs;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = (unsigned)cs;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = cs > 1 ? 1 : 0;
+  cfg.numAttrs = cs > 1 ? 2 : 1;
   TraceScope ts("fused_tc", s);
   return cudaLaunchKernelEx(&cfg, tc_fused_kernel<PARTS>, map_a, map_b, pr, d_err);
 }
