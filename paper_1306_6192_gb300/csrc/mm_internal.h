@@ -142,9 +142,10 @@ SimtPlan simt_plan(bool f64, int64_t n, int64_t m, int64_t p);
 size_t simt_scratch_bytes(bool f64, int64_t n, int64_t m, int64_t p);
 cudaError_t launch_simt_splitk_f32(int64_t n, int64_t m, int64_t p, const float *A, const float *B,
                                    float *C, float *part, const SimtPlan &pl, cudaStream_t s);
+// run_if: as for launch_simt_f64 (the FP64 emulation's fallback).
 cudaError_t launch_simt_splitk_f64(int64_t n, int64_t m, int64_t p, const double *A,
                                    const double *B, double *C, double *part, const SimtPlan &pl,
-                                   cudaStream_t s);
+                                   cudaStream_t s, const int *run_if = nullptr);
 
 // Prep of the packed split path: the split (hi/lo bf16) into the packs with
 // the row/column maxima, their verification and the re-pack of operands out

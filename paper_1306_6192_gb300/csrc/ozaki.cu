@@ -539,7 +539,7 @@ struct OzLayout {
   int64_t mc;
   std::vector<int64_t> k0, kc, kt, a0, b0;
   int64_t rows = 0, plane = 0;
-  size_t max_off, zero_off, zero_end, d_off, tab_off, map_off, flag_off, need;
+  size_t max_off, zero_off, zero_end, d_off, tab_off, map_off, flag_off, simt_off, need;
   int64_t units = 0;
 };
 
@@ -653,7 +653,9 @@ mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *
   lay.map_off = (lay.tab_off + tab_bytes + order.size() * sizeof(int) + 255) & ~(size_t)255;
   // the gate's fallback flag
   lay.flag_off = (lay.map_off + (size_t)lay.units * sizeof(int) + 255) & ~(size_t)255;
-  lay.need = lay.flag_off + 256;
+  // the fallback's K-slice partials (under-filled products)
+  lay.simt_off = lay.flag_off + 256;
+  lay.need = lay.simt_off + simt_scratch_bytes(true, n, m, p);
   cudaError_t e = ws.reserve(lay.need, s);
   if (e != cudaSuccess) return note_cuda(e);
   uint8_t *base = static_cast<uint8_t *>(ws.ptr);
@@ -732,7 +734,13 @@ mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *
                                                 lay.chunks, n, p, rowmax, colmax, thr, flag);
     if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
   }
-  // the FP64 FMA product replaces C where the flag is set
+  // the FP64 FMA product replaces C where the flag is set: the same kernels
+  // and K slices as MM_MODE_DGEMM, so the bits are that mode's
+  const SimtPlan pl = simt_plan(true, n, m, p);
+  if (pl.S >= 1)
+    return note_cuda(launch_simt_splitk_f64(
+        n, m, p, A, B, C, pl.S > 1 ? reinterpret_cast<double *>(base + lay.simt_off) : nullptr, pl, s,
+        flag));
   return note_cuda(launch_simt_f64(n, m, p, A, B, C, s, flag));
 }
 
@@ -749,7 +757,8 @@ size_t ozaki_scratch_bytes(int64_t n, int64_t m, int64_t p, int S) {
   return (size_t)rows * kPackRowBytes + (size_t)chunks * SS * (n * p + 64) * sizeof(float) +
          (size_t)(n + p) * 12 + (size_t)chunks * SS * ceil_div(n, kTcBM) * ceil_div(p, 128) * 4 +
          (size_t)chunks * SS * sizeof(SplitProb) +
-         (size_t)chunks * SS * ceil_div(n, kTcBM) * ceil_div(p, 128) * 4 + ((size_t)1 << 20);
+         (size_t)chunks * SS * ceil_div(n, kTcBM) * ceil_div(p, 128) * 4 + ((size_t)1 << 20) +
+         simt_scratch_bytes(true, n, m, p);
 }
 
 }  // namespace mm

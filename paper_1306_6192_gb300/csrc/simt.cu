@@ -235,12 +235,14 @@ simt_gemm_kernel(const T *__restrict__ A, const T *__restrict__ B, T *__restrict
 template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
 __global__ void __launch_bounds__(256, (SimtShape<T, BM, BN, BK, TM, TN>::MIN_BLOCKS))
 simt_splitk_kernel(const T *__restrict__ A, const T *__restrict__ B, T *__restrict__ part,
-                   int64_t n, int64_t m, int64_t p, int64_t ks) {
+                   int64_t n, int64_t m, int64_t p, int64_t ks, const int *__restrict__ run_if) {
   // launched as a programmatic dependent of the previous kernel on the
   // stream: resident early, it reads nothing before that kernel has finished
   // and its writes are visible; the sum kernel may then be scheduled
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  // run_if: a device word; when given, the product runs only where it is set
+  if (run_if != nullptr && *reinterpret_cast<const volatile int *>(run_if) == 0) return;
   const int64_t k0 = (int64_t)blockIdx.z * ks;
   const int64_t kb = min(ks, m - k0);
   simt_tile_any<T, BM, BN, BK, TM, TN, VEC>(A + k0, B + k0 * p, part + (int64_t)blockIdx.z * n * p,
@@ -253,10 +255,12 @@ simt_splitk_kernel(const T *__restrict__ A, const T *__restrict__ B, T *__restri
 // in the order g = 0, 1, ..., G - 1.
 template <typename T>
 __global__ void __launch_bounds__(256)
-splitk_sum_kernel(const T *__restrict__ part, int S, int64_t np, T *__restrict__ C) {
+splitk_sum_kernel(const T *__restrict__ part, int S, int64_t np, T *__restrict__ C,
+                  const int *__restrict__ run_if) {
   __shared__ T ps[8][32];
   asm volatile("griddepcontrol.wait;" ::: "memory");  // the slices' partials are written
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  if (run_if != nullptr && *reinterpret_cast<const volatile int *>(run_if) == 0) return;
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int G = min(8, S);
   const int64_t i = (int64_t)blockIdx.x * 32 + lane;
@@ -332,7 +336,8 @@ cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, cudaStream_t s
 
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 cudaError_t launch_splitk(int64_t n, int64_t m, int64_t p, const T *A, const T *B, T *C, T *part,
-                          const SimtPlan &pl, cudaStream_t s, const char *name) {
+                          const SimtPlan &pl, cudaStream_t s, const char *name,
+                          const int *run_if) {
   constexpr int W = 16 / (int)sizeof(T);
   const int64_t gy = ceil_div(n, BM), gx = ceil_div(p, BN);
   if (gy > 65535 || gx > 2147483647LL || pl.S < 1 || pl.S > 65535) return cudaErrorInvalidValue;
@@ -344,16 +349,16 @@ cudaError_t launch_splitk(int64_t n, int64_t m, int64_t p, const T *A, const T *
   {
     TraceScope ts(name, s);
     e = vec ? launch_dependent(simt_splitk_kernel<T, BM, BN, BK, TM, TN, true>, grid, s, A, B, out, n, m,
-                               p, pl.ks)
+                               p, pl.ks, run_if)
             : launch_dependent(simt_splitk_kernel<T, BM, BN, BK, TM, TN, false>, grid, s, A, B, out, n, m,
-                               p, pl.ks);
+                               p, pl.ks, run_if);
   }
   if (e != cudaSuccess || pl.S == 1) return e;
   TraceScope ts("simt_sum", s);
   const int64_t np = n * p;
   if (ceil_div(np, 32) > 2147483647LL) return cudaErrorInvalidValue;
   return launch_dependent(splitk_sum_kernel<T>, dim3((unsigned)ceil_div(np, 32), 1, 1), s,
-                          static_cast<const T *>(part), pl.S, np, C);
+                          static_cast<const T *>(part), pl.S, np, C, run_if);
 }
 
 }  // namespace
@@ -394,15 +399,16 @@ cudaError_t launch_simt_splitk_f32(int64_t n, int64_t m, int64_t p, const float 
                                    float *C, float *part, const SimtPlan &pl, cudaStream_t s) {
   if (pl.wide)
     return launch_splitk<float, kSimtF32BM, kSimtF32BN, kSimtF32BK, 8, 8>(n, m, p, A, B, C, part, pl, s,
-                                                                         "simt_f32");
-  return launch_splitk<float, 64, 64, kSimtF32BK, 4, 4>(n, m, p, A, B, C, part, pl, s, "simt_f32");
+                                                                         "simt_f32", nullptr);
+  return launch_splitk<float, 64, 64, kSimtF32BK, 4, 4>(n, m, p, A, B, C, part, pl, s, "simt_f32",
+                                                        nullptr);
 }
 
 cudaError_t launch_simt_splitk_f64(int64_t n, int64_t m, int64_t p, const double *A,
                                    const double *B, double *C, double *part, const SimtPlan &pl,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, const int *run_if) {
   return launch_splitk<double, kSimtF64BM, kSimtF64BN, kSimtF64BK, 4, 4>(n, m, p, A, B, C, part, pl, s,
-                                                                         "dgemm_f64");
+                                                                         "dgemm_f64", run_if);
 }
 
 cudaError_t launch_simt_f32(int64_t n, int64_t m, int64_t p, const float *A, const float *B,
