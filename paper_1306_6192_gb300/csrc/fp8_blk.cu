@@ -204,6 +204,7 @@ fp8blk_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *_
   constexpr int kQuads = kBK / 4;  // 32-bit words per pack row
   __shared__ float tile[kBK][64 + 1];
   __shared__ int colexp[64];
+  __shared__ uint32_t colmax[4][64];
   const int item = blockIdx.x;
   const int g =
       find_problem(probs, nprobs, map, item, [](const SplitProb &q) { return q.pack_start; });
@@ -285,10 +286,17 @@ fp8blk_pack_kernel(const SplitProb *__restrict__ probs, int nprobs, const int *_
         tile[kk][4 * c4 + 3] = vs[it].w;
       }
       __syncthreads();
-      if (tid < 64) {
+      {
+        // column maxima: four threads a column, 32 K values each
+        const int c = tid & 63, q = tid >> 6;
         uint32_t mx = 0;
 #pragma unroll 8
-        for (int kk = 0; kk < kBK; kk++) mx = max(mx, absb(tile[kk][tid]));
+        for (int kk = 32 * q; kk < 32 * q + 32; kk++) mx = max(mx, absb(tile[kk][c]));
+        colmax[q][c] = mx;
+      }
+      __syncthreads();
+      if (tid < 64) {
+        const uint32_t mx = max(max(colmax[0][tid], colmax[1][tid]), max(colmax[2][tid], colmax[3][tid]));
         const int e = pick_exponent(mx, pr.tB[(int64_t)nt * kPackBN + c0 + tid]);
         colexp[tid] = e;
         fac_b(pr)[(int64_t)kb * pr.nt * kPackBN + (int64_t)nt * kPackBN + c0 + tid] = pow2f(e);
