@@ -368,8 +368,10 @@ def bench_stress(mm, stream, peaks, reps: int = 10):
     64 operand copies taken round-robin so the 512 MB footprint exceeds L2),
     B = diag(d) at 4096 through the general product, and 4096^3 with entries
     s 2^e, e real uniform in [-20, 20) (split-precision scaling; FP8 error
-    reported).  Device time per product from CUDA events on the stream; the
-    library's FP64 check for the error.  A failure is recorded, not raised."""
+    reported).  Device time per product from CUDA events on the stream, the
+    calls queued behind a device-side wait so that their submission does not
+    gate them; the library's FP64 check for the error.  A failure is
+    recorded, not raised."""
     import torch
 
     import synth
@@ -382,6 +384,10 @@ def bench_stress(mm, stream, peaks, reps: int = 10):
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        # the calls are queued behind a ~10 ms device-side wait, so that the
+        # host's submission of short products does not gate the device time
+        with torch.cuda.stream(stream):
+            torch.cuda._sleep(20_000_000)
         e0.record(stream)
         for k in range(count):
             fn(k)
