@@ -216,7 +216,9 @@ mm_status mm_ozaki_plan(int64_t n, int64_t m, int64_t p, int slices, int64_t *ch
 /* As mm_gemm, but device pointers only and asynchronous: the work is queued on
  * `stream` (a cudaStream_t; NULL = the library stream) and the call returns
  * after the launches.  Calls that use the split, FP8 or Ozaki path share the
- * library's scratch of that path and must be ordered on one stream. */
+ * library's scratch of that path and must be ordered on one stream; so must
+ * SIMT and DGEMM calls on products with too few output tiles for the SMs,
+ * whose K slices keep their partial sums in library scratch. */
 mm_status mm_gemm_async(int64_t n, int64_t m, int64_t p, const void *A,
                         const void *B, void *C, mm_dtype dt, mm_mode mode,
                         void *stream);
