@@ -330,6 +330,22 @@ mm_status mm_tune_query_tail(int64_t n, int64_t m, int64_t p, int *tiles,
 mm_status mm_tune_query_splitk(int64_t n, int64_t m, int64_t p, int *tiles, int *slices,
                                int *clusters, int *cluster_size);
 
+/* K-slice plan of a SIMT (dt = MM_F32) or DGEMM (dt = MM_F64) product, a
+ * pure host function (no device, no mm_init): the plan mm_gemm follows on a
+ * device of `sms` SMs (sms <= 0: the initialised device's count, 148 before
+ * mm_init).  A product with fewer whole output tiles (128 x 128 in FP32,
+ * 64 x 64 in FP64) than half the SMs is cut along K into *slices slices of
+ * *slice_k values (the last one shorter), computed on *tile x *tile output
+ * tiles (64, or 128 for FP32 products at least 128 wide both ways); the
+ * slices' partial sums are then added in a fixed order.  The plan keeps one
+ * wave of at most two CTAs per SM, slices of at least 128 values unless K is
+ * shorter, and partials of at most 256 MiB; it depends on the shape (and
+ * sms) only and is the same for (n, m, p) and (p, m, n).  *slices = 0: the
+ * one-pass kernel (*tile its tile, *slice_k 0).  Returns MM_EINVAL for
+ * negative sizes, another dtype or NULL outputs.  Not in the paper. */
+mm_status mm_simt_plan(int64_t n, int64_t m, int64_t p, mm_dtype dt, int sms, int *slices,
+                       int64_t *slice_k, int *tile);
+
 /* The tail-split planner itself, a pure host function (no device, no
  * mm_init): for a product of `tiles` output tiles of 128 x bn, kt pack rows
  * of K (64 bf16 or 128 e4m3 values each), inner dimension m and `products`

@@ -84,6 +84,9 @@ def lib():
         L.mm_tune_query_splitk.argtypes = [_i64, _i64, _i64] + [ctypes.POINTER(ctypes.c_int)] * 4
         L.mm_tail_plan.argtypes = [_i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64,
                                    ctypes.c_double] + [ctypes.POINTER(ctypes.c_int)] * 2
+        L.mm_simt_plan.argtypes = [_i64, _i64, _i64, ctypes.c_int, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_i64),
+                                   ctypes.POINTER(ctypes.c_int)]
         L.mm_trace_enable.argtypes = [ctypes.c_int]
         L.mm_trace_reset.argtypes = []
         L.mm_trace_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(_i64), _dp]
@@ -112,7 +115,7 @@ def lib():
                      "mm_gemm_grouped_async", "mm_sync", "mm_check", "mm_submit", "mm_poll",
                      "mm_wait", "mm_serve_stats", "mm_tune", "mm_tune_save", "mm_tune_load",
                      "mm_tune_query", "mm_tune_query_tail", "mm_tune_query_splitk",
-                     "mm_tail_plan", "mm_trace_enable",
+                     "mm_tail_plan", "mm_simt_plan", "mm_trace_enable",
                      "mm_trace_reset", "mm_trace_read"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -278,6 +281,15 @@ def mm_tune_query_splitk(n, m, p):
     v = [ctypes.c_int(0) for _ in range(4)]
     st = lib().mm_tune_query_splitk(n, m, p, *[ctypes.byref(x) for x in v])
     return (st,) + tuple(x.value for x in v)
+
+
+def mm_simt_plan(n, m, p, dt, sms: int = 0):
+    """Returns (status, slices, slice_k, tile) of the K-slice plan of a SIMT
+    (MM_F32) or DGEMM (MM_F64) product (slices = 0: the one-pass kernel).
+    Needs no device."""
+    s, k, t = ctypes.c_int(0), _i64(0), ctypes.c_int(0)
+    st = lib().mm_simt_plan(n, m, p, dt, sms, ctypes.byref(s), ctypes.byref(k), ctypes.byref(t))
+    return st, s.value, k.value, t.value
 
 
 def mm_measure_fma_peak(dt, iters: int = 4096):

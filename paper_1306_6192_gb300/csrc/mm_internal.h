@@ -139,6 +139,8 @@ struct SimtPlan {
   bool wide;
 };
 SimtPlan simt_plan(bool f64, int64_t n, int64_t m, int64_t p);
+// The same plan for a device of `sms` SMs (host only; mm_simt_plan).
+SimtPlan simt_plan_for(bool f64, int64_t n, int64_t m, int64_t p, int sms);
 size_t simt_scratch_bytes(bool f64, int64_t n, int64_t m, int64_t p);
 cudaError_t launch_simt_splitk_f32(int64_t n, int64_t m, int64_t p, const float *A, const float *B,
                                    float *C, float *part, const SimtPlan &pl, cudaStream_t s);

@@ -363,10 +363,9 @@ cudaError_t launch_splitk(int64_t n, int64_t m, int64_t p, const T *A, const T *
 
 }  // namespace
 
-SimtPlan simt_plan(bool f64, int64_t n, int64_t m, int64_t p) {
+SimtPlan simt_plan_for(bool f64, int64_t n, int64_t m, int64_t p, int sms) {
   SimtPlan pl{0, 0, false};
-  if (n <= 0 || m <= 0 || p <= 0) return pl;
-  const int sms = sm_count();
+  if (n <= 0 || m <= 0 || p <= 0 || sms <= 0) return pl;
   const int64_t bm = f64 ? kSimtF64BM : kSimtF32BM, bn = f64 ? kSimtF64BN : kSimtF32BN;
   // products that fill at least half of the SMs with whole tiles keep the
   // one-pass kernel
@@ -388,6 +387,10 @@ SimtPlan simt_plan(bool f64, int64_t n, int64_t m, int64_t p) {
   pl.S = (int)ceil_div(m, ks);
   pl.ks = ks;
   return pl;
+}
+
+SimtPlan simt_plan(bool f64, int64_t n, int64_t m, int64_t p) {
+  return simt_plan_for(f64, n, m, p, sm_count());
 }
 
 size_t simt_scratch_bytes(bool f64, int64_t n, int64_t m, int64_t p) {
@@ -447,3 +450,16 @@ cudaError_t launch_simt_grouped(bool f64, const SimtProb *d_probs, int nprobs, i
 }
 
 }  // namespace mm
+
+extern "C" mm_status mm_simt_plan(int64_t n, int64_t m, int64_t p, mm_dtype dt, int sms,
+                                  int *slices, int64_t *slice_k, int *tile) {
+  using namespace mm;
+  if (n < 0 || m < 0 || p < 0 || (dt != MM_F32 && dt != MM_F64) || !slices || !slice_k || !tile)
+    return MM_EINVAL;
+  const bool f64 = dt == MM_F64;
+  const SimtPlan pl = simt_plan_for(f64, n, m, p, sms > 0 ? sms : sm_count());
+  *slices = pl.S;
+  *slice_k = pl.S > 0 ? pl.ks : 0;
+  *tile = pl.S > 0 ? (pl.wide ? 128 : 64) : (f64 ? kSimtF64BM : kSimtF32BM);
+  return MM_OK;
+}
