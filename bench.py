@@ -338,6 +338,20 @@ def bench_paper_workloads(mm, stream, peaks, n: int = 4096, reps: int = 5):
     ms = queued_ms(lambda: ok(mm.mm_diag_async(n, n, A, d, C, 0, mm.MM_F32, stream), "diag"))
     out["diag_gbs_queued"] = (2 * 4 * n * n + 4 * n) / (ms * 1e-3) / 1e9
     out["diag_frac_hbm_queued"] = out["diag_gbs_queued"] / hbm
+    # the product with the matrix subtraction C = A.B - D: as two calls (the
+    # product, then mm_add over C and D) and with the subtraction fused into
+    # the product's epilogue (mm_gemm_axpby: D read once as C is stored)
+    F32, X3 = mm.MM_F32, mm.MM_MODE_SPLIT_BF16X3
+
+    def two_calls():
+        ok(mm.mm_gemm_async(n, n, n, A, B, C, F32, X3, stream), "gemm")
+        ok(mm.mm_add_async(n, n, 1.0, C, -1.0, B, C, F32, stream), "add")
+
+    out["gemm_then_add_ms"] = queued_ms(two_calls)
+    out["gemm_axpby_fused_ms"] = queued_ms(
+        lambda: ok(mm.mm_gemm_axpby_async(n, n, n, 1.0, A, B, -1.0, B, C, F32, X3, stream), "axpby"))
+    out["gemm_only_ms"] = queued_ms(lambda: ok(mm.mm_gemm_async(n, n, n, A, B, C, F32, X3, stream),
+                                               "gemm"))
     # the same kernels on 8192^2 operands, where the ~10 us between a synchronous
     # call's first trace event and its kernel weighs less
     del A, B, C
@@ -357,7 +371,8 @@ def bench_paper_workloads(mm, stream, peaks, n: int = 4096, reps: int = 5):
                    "library's event tracer, which includes the launch latency of a synchronous "
                    "call (~10 us); *_queued: 20 asynchronous calls queued on one stream, timed "
                    "by events around all of them; add moves 192 MB (768 MB at 8192^2) and diag "
-                   "128 MB (512 MB) per call")
+                   "128 MB (512 MB) per call; gemm_then_add / gemm_axpby_fused / gemm_only: "
+                   "C = A.B - D at 4096^3 on the split path, queued, per call")
     return out
 
 

@@ -223,6 +223,35 @@ mm_status mm_gemm_async(int64_t n, int64_t m, int64_t p, const void *A,
                         const void *B, void *C, mm_dtype dt, mm_mode mode,
                         void *stream);
 
+/* C = alpha (A.B) + beta D for one product: the paper's second workload, the
+ * elementwise matrix addition/subtraction of the results section, fused into
+ * the epilogue of the product on the SIMT, DGEMM, split and FP64-emulation
+ * paths (the kernel that writes C applies it to each entry as it stores it,
+ * so D is read once and no second pass over C runs; the tensor-core kernels
+ * keep their tiled stores where C and D are 16-byte aligned with p % 4 == 0).
+ * Device pointers only; D is n x p row-major like C, of the same dtype, and
+ * is either C itself (C = alpha (A.B) + beta C) or apart from it (a partial
+ * overlap returns MM_EINVAL).  Each entry x of the product (computed by
+ * `mode` as mm_gemm does) becomes fma(alpha, x, beta d) with one rounding of
+ * beta d first, in the element type (MM_F32: alpha and beta rounded to FP32);
+ * alpha = 1 and beta = +-1 give x +- d correctly rounded, and beta = 0 gives
+ * alpha x without reading D (D may be NULL).  alpha = 0 or m = 0: C = beta D,
+ * and A and B are not read (they may be NULL).  With alpha = 1 and beta = 0
+ * the result is mm_gemm's, bit for bit.  MM_MODE_FP8 runs the same
+ * arithmetic as one elementwise pass after the product instead (its e4m3
+ * tiles' MMAs take about as long as their stores, so the tensor-core kernel
+ * has no slack for it); with D = C the product then goes to library scratch
+ * first.  Returns
+ * what mm_gemm returns, plus MM_EINVAL for a NULL or host D where beta != 0.
+ * mm_gemm_axpby waits for the result; mm_gemm_axpby_async queues it on
+ * `stream` (NULL = the library stream) under mm_gemm_async's scratch rule. */
+mm_status mm_gemm_axpby(int64_t n, int64_t m, int64_t p, double alpha, const void *A,
+                        const void *B, double beta, const void *D, void *C, mm_dtype dt,
+                        mm_mode mode);
+mm_status mm_gemm_axpby_async(int64_t n, int64_t m, int64_t p, double alpha, const void *A,
+                              const void *B, double beta, const void *D, void *C,
+                              mm_dtype dt, mm_mode mode, void *stream);
+
 /* count independent products in one persistent launch per path (grouped
  * GEMM).  probs is a host array; A/B/C inside it are device pointers.  Tile
  * shapes and raster order come from the autotuner table.  Synchronous.

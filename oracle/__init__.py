@@ -89,6 +89,25 @@ class Oracle:
         return (C, absC) if with_abs else C
 
     # -- accurate entries ---------------------------------------------------
+    def axpby(self, alpha, A, B, beta, D, threads: int = 0):
+        """alpha (A.B) + beta D: the product with the matrix addition /
+        subtraction of the paper's results section on top, in FP64, and the
+        normaliser of its entry errors, |alpha| (|A|.|B|) + |beta| |D|.
+        alpha == 0 leaves the product out (A and B are not used) and
+        beta == 0 leaves D out (it may be None), as zero terms."""
+        alpha, beta = float(alpha), float(beta)
+        if alpha != 0.0:
+            ref, ab = self.gemm(A, B, threads=threads, with_abs=True)
+            out, norm = alpha * ref, abs(alpha) * ab
+        else:
+            shape = np.shape(D)  # C has D's shape
+            out, norm = np.zeros(shape), np.zeros(shape)
+        if beta != 0.0:
+            d = np.asarray(D, np.float64)
+            out = out + beta * d
+            norm = norm + abs(beta) * np.abs(d)
+        return out, norm
+
     def entries(self, A, B, I, J, method: str = "dot2"):
         """c_ij for the sampled (I, J) as (hi, lo, |A||B|_ij)."""
         A = _f64(A); B = _f64(B)

@@ -66,6 +66,10 @@ def lib():
         L.mm_shutdown.argtypes = []
         L.mm_gemm.argtypes = [_i64, _i64, _i64, _vp, _vp, _vp, st, st]
         L.mm_gemm_async.argtypes = [_i64, _i64, _i64, _vp, _vp, _vp, st, st, _vp]
+        _dbl = ctypes.c_double
+        L.mm_gemm_axpby.argtypes = [_i64, _i64, _i64, _dbl, _vp, _vp, _dbl, _vp, _vp, st, st]
+        L.mm_gemm_axpby_async.argtypes = [_i64, _i64, _i64, _dbl, _vp, _vp, _dbl, _vp, _vp, st, st,
+                                          _vp]
         L.mm_gemm_grouped.argtypes = [ctypes.c_int32, ctypes.POINTER(mm_problem), st, st]
         L.mm_gemm_grouped_async.argtypes = [ctypes.c_int32, ctypes.POINTER(mm_problem), st, st,
                                             _vp]
@@ -111,7 +115,8 @@ def lib():
         L.mm_ozaki_plan.argtypes = [_i64, _i64, _i64, ctypes.c_int, ctypes.POINTER(_i64),
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)]
         L.mm_ozaki_plan.restype = ctypes.c_int
-        for name in ("mm_init", "mm_shutdown", "mm_gemm", "mm_gemm_async", "mm_gemm_grouped",
+        for name in ("mm_init", "mm_shutdown", "mm_gemm", "mm_gemm_async", "mm_gemm_axpby",
+                     "mm_gemm_axpby_async", "mm_gemm_grouped",
                      "mm_gemm_grouped_async", "mm_sync", "mm_check", "mm_submit", "mm_poll",
                      "mm_wait", "mm_serve_stats", "mm_tune", "mm_tune_save", "mm_tune_load",
                      "mm_tune_query", "mm_tune_query_tail", "mm_tune_query_splitk",
@@ -182,6 +187,18 @@ def mm_gemm(n, m, p, A, B, C, dt, mode) -> int:
 
 def mm_gemm_async(n, m, p, A, B, C, dt, mode, stream=None) -> int:
     return lib().mm_gemm_async(n, m, p, _ptr(A), _ptr(B), _ptr(C), dt, mode, _stream(stream))
+
+
+def mm_gemm_axpby(n, m, p, alpha, A, B, beta, D, C, dt, mode) -> int:
+    """C = alpha (A.B) + beta D with the epilogue fused into the product
+    (device matrices; D may be C itself or None where beta == 0)."""
+    return lib().mm_gemm_axpby(n, m, p, float(alpha), _ptr(A), _ptr(B), float(beta), _ptr(D),
+                               _ptr(C), dt, mode)
+
+
+def mm_gemm_axpby_async(n, m, p, alpha, A, B, beta, D, C, dt, mode, stream=None) -> int:
+    return lib().mm_gemm_axpby_async(n, m, p, float(alpha), _ptr(A), _ptr(B), float(beta),
+                                     _ptr(D), _ptr(C), dt, mode, _stream(stream))
 
 
 def mm_problems(probs):

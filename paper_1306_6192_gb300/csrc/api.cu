@@ -230,12 +230,35 @@ mm_status validate(int64_t n, int64_t m, int64_t p, mm_dtype dt, mm_mode mode) {
   return MM_OK;
 }
 
+// The epilogue C = alpha (A.B) + beta D as a pass of its own after the
+// product, for the paths whose kernels have no slack for it: the product goes
+// to C (or to library scratch where D is C), then one elementwise kernel with
+// the fused form's arithmetic (the same bits).
+template <typename Run>
+static mm_status product_then_epilogue(int64_t n, int64_t p, void *C, mm_dtype dt, const Epi &epi,
+                                       cudaStream_t s, Run run) {
+  const bool two = dt == MM_F32 ? (float)epi.beta != 0.0f : epi.beta != 0.0;
+  void *X = C;
+  if (two && epi.D == C) {
+    cudaError_t e = g_ctx.epi_ws.reserve((size_t)(n * p) * (dt == MM_F64 ? 8 : 4), s);
+    if (e != cudaSuccess) return note_cuda(e);
+    X = g_ctx.epi_ws.ptr;
+  }
+  mm_status st = run(X);
+  if (st != MM_OK) return st;
+  if (two) return enqueue_add(n, p, epi.alpha, X, epi.beta, epi.D, C, dt, s);
+  const bool unit = dt == MM_F32 ? (float)epi.alpha == 1.0f : epi.alpha == 1.0;
+  return unit ? MM_OK : enqueue_scale(n * p, epi.alpha, C, C, dt, s);
+}
+
 // Queues C = A.B (device pointers) on stream s.
 mm_status enqueue_gemm(int64_t n, int64_t m, int64_t p, const void *A, const void *B, void *C,
-                       mm_dtype dt, mm_mode mode, cudaStream_t s) {
+                       mm_dtype dt, mm_mode mode, cudaStream_t s, const Epi *epi) {
   const mm_mode md = resolve_mode(dt, mode);
   if (n == 0 || p == 0) return MM_OK;
   if (m == 0) {
+    // alpha (A.B) = 0: C = beta D
+    if (epi) return enqueue_scale(n * p, epi->beta, epi->D, C, dt, s);
     const size_t es = dt == MM_F64 ? 8 : 4;
     return note_cuda(cudaMemsetAsync(C, 0, (size_t)(n * p) * es, s));
   }
@@ -253,14 +276,15 @@ mm_status enqueue_gemm(int64_t n, int64_t m, int64_t p, const void *A, const voi
           part = g_ctx.simt_ws.ptr;
         }
         return note_cuda(f64 ? launch_simt_splitk_f64(n, m, p, (const double *)A, (const double *)B,
-                                                      (double *)C, (double *)part, pl, s)
+                                                      (double *)C, (double *)part, pl, s, nullptr,
+                                                      epi)
                              : launch_simt_splitk_f32(n, m, p, (const float *)A, (const float *)B,
-                                                      (float *)C, (float *)part, pl, s));
+                                                      (float *)C, (float *)part, pl, s, epi));
       }
       return note_cuda(f64 ? launch_simt_f64(n, m, p, (const double *)A, (const double *)B,
-                                             (double *)C, s)
+                                             (double *)C, s, nullptr, epi)
                            : launch_simt_f32(n, m, p, (const float *)A, (const float *)B,
-                                             (float *)C, s));
+                                             (float *)C, s, epi));
     }
     case MM_MODE_SPLIT_BF16X3:
     case MM_MODE_SPLIT_BF16X6: {
@@ -269,19 +293,25 @@ mm_status enqueue_gemm(int64_t n, int64_t m, int64_t p, const void *A, const voi
       const TcKind kind = split_kind_of(md, m);
       const FusedPlan fpl = fused_plan(n, m, p, kind);
       if (fpl.S > 0 && fused_operands_ok(static_cast<const float *>(A),
-                                         static_cast<const float *>(B), m, p))
+                                         static_cast<const float *>(B), m, p)) {
         return run_fused(g_ctx.fused_ws, n, m, p, static_cast<const float *>(A),
-                         static_cast<const float *>(B), static_cast<float *>(C), kind, fpl, s);
+                         static_cast<const float *>(B), static_cast<float *>(C), kind, fpl, s, epi);
+      }
       mm_problem q{n, m, p, A, B, C};
-      return run_split(g_ctx.split_ws, &q, 1, s, nullptr, md == MM_MODE_SPLIT_BF16X6);
+      return run_split(g_ctx.split_ws, &q, 1, s, nullptr, md == MM_MODE_SPLIT_BF16X6, epi);
     }
     case MM_MODE_FP8: {
-      mm_problem q{n, m, p, A, B, C};
-      return run_fp8(g_ctx.fp8_ws, &q, 1, s);
+      // the e4m3 tiles' MMAs take about as long as their stores, so the
+      // epilogue runs as a pass of its own (measured faster than fused)
+      auto run = [&](void *X) {
+        mm_problem q{n, m, p, A, B, X};
+        return run_fp8(g_ctx.fp8_ws, &q, 1, s);
+      };
+      return epi ? product_then_epilogue(n, p, C, dt, *epi, s, run) : run(C);
     }
     case MM_MODE_OZAKI:
       return run_ozaki(g_ctx.ozaki_ws, n, m, p, (const double *)A, (const double *)B, (double *)C,
-                       g_ctx.ozaki_slices, g_ctx.ozaki_gate != 0, s);
+                       g_ctx.ozaki_slices, g_ctx.ozaki_gate != 0, s, epi);
     default: return MM_EINVAL;
   }
 }
@@ -409,6 +439,7 @@ mm_status mm_shutdown(void) {
   g_ctx.ozaki_ws.release();
   g_ctx.fused_ws.release();
   g_ctx.simt_ws.release();
+  g_ctx.epi_ws.release();
   g_ctx.fused_zero_ptr = nullptr;
   g_ctx.fused_zeroed = 0;
   g_ctx.ozaki_slices = kOzakiDefaultSlices;
@@ -461,6 +492,48 @@ mm_status mm_gemm_async(int64_t n, int64_t m, int64_t p, const void *A, const vo
   cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : g_ctx.stream;
   std::lock_guard<std::mutex> lk(g_api_mutex);
   return enqueue_gemm(n, m, p, A, B, C, dt, mode, s);
+}
+
+// C = alpha (A.B) + beta D on device pointers: checks, then the product with
+// its epilogue, or C = beta D where the product has no terms (alpha = 0 or
+// m = 0: A and B are not read).
+static mm_status enqueue_axpby(int64_t n, int64_t m, int64_t p, double alpha, const void *A,
+                               const void *B, double beta, const void *D, void *C, mm_dtype dt,
+                               mm_mode mode, cudaStream_t s) {
+  mm_status st = validate(n, m, p, dt, mode);
+  if (st != MM_OK) return st;
+  if (n == 0 || p == 0) return MM_OK;
+  const bool terms = m > 0 && alpha != 0.0;
+  if (!C || pointer_kind(C) != 1) return MM_EINVAL;
+  if (terms && (!A || !B || pointer_kind(A) != 1 || pointer_kind(B) != 1)) return MM_EINVAL;
+  if (beta != 0.0) {
+    if (!D || pointer_kind(D) != 1) return MM_EINVAL;
+    // D is C itself or apart from it
+    const size_t bytes = (size_t)(n * p) * (dt == MM_F64 ? 8 : 4);
+    const uintptr_t d0 = reinterpret_cast<uintptr_t>(D), c0 = reinterpret_cast<uintptr_t>(C);
+    if (d0 != c0 && d0 < c0 + bytes && c0 < d0 + bytes) return MM_EINVAL;
+  }
+  const Epi epi{alpha, beta, beta != 0.0 ? D : nullptr};
+  if (!terms) return enqueue_scale(n * p, beta, epi.D, C, dt, s);
+  return enqueue_gemm(n, m, p, A, B, C, dt, mode, s, &epi);
+}
+
+mm_status mm_gemm_axpby_async(int64_t n, int64_t m, int64_t p, double alpha, const void *A,
+                              const void *B, double beta, const void *D, void *C, mm_dtype dt,
+                              mm_mode mode, void *stream) {
+  MM_REQUIRE_INIT();
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : g_ctx.stream;
+  std::lock_guard<std::mutex> lk(g_api_mutex);
+  return enqueue_axpby(n, m, p, alpha, A, B, beta, D, C, dt, mode, s);
+}
+
+mm_status mm_gemm_axpby(int64_t n, int64_t m, int64_t p, double alpha, const void *A,
+                        const void *B, double beta, const void *D, void *C, mm_dtype dt,
+                        mm_mode mode) {
+  MM_REQUIRE_INIT();
+  std::lock_guard<std::mutex> lk(g_api_mutex);
+  const mm_status st = enqueue_axpby(n, m, p, alpha, A, B, beta, D, C, dt, mode, g_ctx.stream);
+  return st != MM_OK ? st : check_device_flag(g_ctx.stream);
 }
 
 mm_status mm_gemm(int64_t n, int64_t m, int64_t p, const void *A, const void *B, void *C,

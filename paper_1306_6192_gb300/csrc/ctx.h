@@ -62,6 +62,7 @@ struct Ctx {
   Scratch ozaki_ws;      // digit packs, level sums and tables of the FP64 emulation
   Scratch fused_ws;      // counters and cluster partial tiles of the fused split-K path
   Scratch simt_ws;       // K-slice partials of under-filled SIMT / FP64 products
+  Scratch epi_ws;        // the product of an in-place epilogue run as a second pass
   void *fused_zero_ptr = nullptr;  // fused_ws buffer whose leading counters are zero
   size_t fused_zeroed = 0;         //   and how many bytes of them
   int ozaki_slices = kOzakiDefaultSlices;  // digit slices S of MM_MODE_OZAKI
@@ -80,8 +81,17 @@ extern std::mutex g_api_mutex;
 
 int pointer_kind(const void *p);
 mm_status validate(int64_t n, int64_t m, int64_t p, mm_dtype dt, mm_mode mode);
+// Queues C = A.B, or with `epi` C = alpha (A.B) + beta D (device pointers).
 mm_status enqueue_gemm(int64_t n, int64_t m, int64_t p, const void *A, const void *B, void *C,
-                       mm_dtype dt, mm_mode mode, cudaStream_t s);
+                       mm_dtype dt, mm_mode mode, cudaStream_t s, const Epi *epi = nullptr);
+// Queues C = beta D for `count` entries (beta == 0: C = 0 without reading D);
+// D may be C.  The epilogue of a product with no terms (alpha = 0 or m = 0).
+mm_status enqueue_scale(int64_t count, double beta, const void *D, void *C, mm_dtype dt,
+                        cudaStream_t s);
+// Queues C = alpha A + beta B for n x p matrices (mm_add's kernels; C may be
+// A or B).
+mm_status enqueue_add(int64_t n, int64_t p, double alpha, const void *A, double beta,
+                      const void *B, void *C, mm_dtype dt, cudaStream_t s);
 mm_status check_device_flag(cudaStream_t s);
 
 mm_status note_cuda(cudaError_t e);
@@ -109,8 +119,9 @@ inline int tc_bn(TcKind kind, int bn) {
 // problem takes the kind split_kind_for(m).  `force` overrides the tuned tile
 // choice (autotuner and tests).
 // `six` selects the three-part kind (six products) for every problem.
+// `epi` (null: C = A.B) is the epilogue of a table of one product.
 mm_status run_split(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s,
-                    const TcChoice *force, bool six = false);
+                    const TcChoice *force, bool six = false, const Epi *epi = nullptr);
 // Split path for one product whose rows of A (and of C) are processed in
 // `chunks` slabs: slab c waits for event in_ready[c + 1] (B: in_ready[0])
 // before its prep and records out_ready[c] when its part of C is written.
@@ -131,7 +142,8 @@ struct FusedPlan {
 };
 FusedPlan fused_plan(int64_t n, int64_t m, int64_t p, TcKind kind);
 mm_status run_fused(Scratch &ws, int64_t n, int64_t m, int64_t p, const float *A, const float *B,
-                    float *C, TcKind kind, const FusedPlan &plan, cudaStream_t s);
+                    float *C, TcKind kind, const FusedPlan &plan, cudaStream_t s,
+                    const Epi *epi = nullptr);
 // FP8 path (report-only accuracy): e4m3 operands with a power-of-two scale
 // per 128-value K block of each row of A and column of B (fp8_blk.cu).
 mm_status run_fp8(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s);
@@ -143,8 +155,10 @@ size_t fp8_blocks_scratch_bytes(int64_t n, int64_t m, int64_t p);
 // scratch one product needs.
 // gate: check every entry against the method's error bound and recompute C
 // with the FP64 FMA product where any entry could miss 1e-14 sqrt(m).
+// epi (null: C = A.B) is applied by the kernels that write C.
 mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *A,
-                    const double *B, double *C, int S, bool gate, cudaStream_t s);
+                    const double *B, double *C, int S, bool gate, cudaStream_t s,
+                    const Epi *epi = nullptr);
 int64_t ozaki_chunk(int S);
 size_t ozaki_scratch_bytes(int64_t n, int64_t m, int64_t p, int S);
 // Grouped dispatch: split / SIMT / DGEMM tables in one launch per path.

@@ -51,6 +51,15 @@ add_kernel(const T *__restrict__ a, const T *__restrict__ b, T *__restrict__ c, 
   }
 }
 
+// c = beta d (c may be d)
+template <typename T>
+__global__ void __launch_bounds__(256)
+scale_kernel(const T *d, T *c, T beta, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    c[i] = beta * d[i];
+}
+
 // The 16-byte kernels below give each block one contiguous run of
 // 256 * kEwUnroll vectors (thread t takes vectors t, t + 256, ...): all loads
 // of a thread are issued before its stores, and consecutive blocks sweep
@@ -225,6 +234,8 @@ mm_status check_add_args(int64_t n, int64_t p, const void *A, const void *B, con
   return MM_EPENDING;  // valid and non-empty: queue the kernel
 }
 
+}  // namespace
+
 mm_status enqueue_add(int64_t n, int64_t p, double alpha, const void *A, double beta,
                       const void *B, void *C, mm_dtype dt, cudaStream_t s) {
   const int64_t count = n * p;
@@ -248,6 +259,28 @@ mm_status enqueue_add(int64_t n, int64_t p, double alpha, const void *A, double 
   }
   return note_cuda(cudaGetLastError());
 }
+
+namespace {
+
+}  // namespace
+
+mm_status enqueue_scale(int64_t count, double beta, const void *D, void *C, mm_dtype dt,
+                        cudaStream_t s) {
+  if (count <= 0) return MM_OK;
+  const size_t es = dt == MM_F64 ? 8 : 4;
+  if (dt == MM_F32 ? (float)beta == 0.0f : beta == 0.0)
+    return note_cuda(cudaMemsetAsync(C, 0, (size_t)count * es, s));
+  TraceScope ts("add", s);
+  if (dt == MM_F32)
+    scale_kernel<float><<<grid_for(count), 256, 0, s>>>(static_cast<const float *>(D),
+                                                        static_cast<float *>(C), (float)beta, count);
+  else
+    scale_kernel<double><<<grid_for(count), 256, 0, s>>>(static_cast<const double *>(D),
+                                                         static_cast<double *>(C), beta, count);
+  return note_cuda(cudaGetLastError());
+}
+
+namespace {
 
 mm_status check_diag_args(int64_t n, int64_t p, const void *X, const void *d, const void *C,
                           int side, mm_dtype dt) {

@@ -37,6 +37,45 @@ inline int pack_k(TcKind k) { return k == kTcE4m3 ? 128 : 64; }
 inline int pack_parts(TcKind k) { return k == kTcE4m3 ? 1 : (k == kTcSplitBf16x3 ? 2 : 3); }
 constexpr int kPackK = 64;  // bf16 elements per pack row
 
+// ------------------------------------------------------------ epilogue
+// C = alpha (A.B) + beta D of one product (mm_gemm_axpby), applied by the
+// kernel that writes C, to the product x of entry (i, j): on = 0 writes x,
+// on = 1 alpha x, on = 2 fma(alpha, x, beta d) with d = D[i p + j] (D is n x p
+// row-major like C; it may be C itself, since each entry of C is read and
+// written by the same thread).  Zero-initialised: off.
+template <typename T>
+struct EpiT {
+  const T *D;
+  T alpha, beta;
+  int on;
+};
+using EpiF = EpiT<float>;
+#ifdef __CUDACC__
+template <typename T>
+__device__ __forceinline__ T epi_apply(const EpiT<T> &e, T x, int64_t idx) {
+  if (e.on == 0) return x;
+  if (e.on == 1) return e.alpha * x;
+  return fma(e.alpha, x, e.beta * e.D[idx]);
+}
+#endif
+// The host request: alpha and beta as given (rounded to T for the kernels),
+// D a device pointer or null where beta == 0.
+struct Epi {
+  double alpha, beta;
+  const void *D;
+  template <typename T>
+  EpiT<T> as() const {
+    EpiT<T> e{static_cast<const T *>(D), (T)alpha, (T)beta, 0};
+    e.on = e.beta != T(0) ? 2 : (e.alpha != T(1) ? 1 : 0);
+    if (e.on != 2) e.D = nullptr;
+    return e;
+  }
+};
+template <typename T>
+inline EpiT<T> epi_of(const Epi *e) {
+  return e ? e->as<T>() : EpiT<T>{nullptr, T(1), T(0), 0};
+}
+
 // ------------------------------------------------------------ device tables
 // One product of a tensor-core path, as the prep and tensor-core kernels see
 // it.  With P = pack_parts(kind) and kt = ceil(m / pack_k(kind)):
@@ -83,6 +122,8 @@ struct SplitProb {
   // 1 + index of C's tensor map in the launch's map array (tiled stores of
   // the epilogue); 0: C is written with plain stores
   int32_t c_tma;
+  // C = alpha (A.B) + beta D (plain stores only; off: C = A.B)
+  EpiF epi;
 };
 
 // Work units of a product with its tail split: whole tiles, then the parts.
@@ -106,6 +147,7 @@ struct FusedProb {
   int32_t S, Q;            // slices per tile, clusters per tile
   float *slots;
   int *cnt;
+  EpiF epi;  // C = alpha (A.B) + beta D (off: C = A.B)
 };
 
 // One product of the grouped SIMT path (f32 or f64 elements).
@@ -119,13 +161,14 @@ struct SimtProb {
 };
 
 // ------------------------------------------------------------ launchers
+// epi (null: C = A.B) as for EpiT, applied where C is written.
 cudaError_t launch_simt_f32(int64_t n, int64_t m, int64_t p, const float *A,
-                            const float *B, float *C, cudaStream_t s);
+                            const float *B, float *C, cudaStream_t s, const Epi *epi = nullptr);
 // run_if: a device word; when given, the product runs only if it is non-zero
 // when the kernel starts (the FP64 emulation's fallback).
 cudaError_t launch_simt_f64(int64_t n, int64_t m, int64_t p, const double *A,
                             const double *B, double *C, cudaStream_t s,
-                            const int *run_if = nullptr);
+                            const int *run_if = nullptr, const Epi *epi = nullptr);
 cudaError_t launch_simt_grouped(bool f64, const SimtProb *d_probs, int nprobs,
                                 int total_tiles, bool all_vec, cudaStream_t s);
 // Split-K of a SIMT product with too few output tiles for the SMs: S slices
@@ -143,11 +186,13 @@ SimtPlan simt_plan(bool f64, int64_t n, int64_t m, int64_t p);
 SimtPlan simt_plan_for(bool f64, int64_t n, int64_t m, int64_t p, int sms);
 size_t simt_scratch_bytes(bool f64, int64_t n, int64_t m, int64_t p);
 cudaError_t launch_simt_splitk_f32(int64_t n, int64_t m, int64_t p, const float *A, const float *B,
-                                   float *C, float *part, const SimtPlan &pl, cudaStream_t s);
+                                   float *C, float *part, const SimtPlan &pl, cudaStream_t s,
+                                   const Epi *epi = nullptr);
 // run_if: as for launch_simt_f64 (the FP64 emulation's fallback).
 cudaError_t launch_simt_splitk_f64(int64_t n, int64_t m, int64_t p, const double *A,
                                    const double *B, double *C, double *part, const SimtPlan &pl,
-                                   cudaStream_t s, const int *run_if = nullptr);
+                                   cudaStream_t s, const int *run_if = nullptr,
+                                   const Epi *epi = nullptr);
 
 // Prep of the packed split path: the split (hi/lo bf16) into the packs with
 // the row/column maxima, their verification and the re-pack of operands out

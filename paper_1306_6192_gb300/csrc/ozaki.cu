@@ -420,12 +420,15 @@ __device__ __forceinline__ bool round_to_double(unsigned __int128 M, int k, uint
 // row i of A or column j of B is not finite.  A thread takes column j of the
 // rows blockIdx.y, blockIdx.y + gridDim.y, ...; the S level values of a chunk
 // are loaded together.  One instantiation per S, so the level loop unrolls
-// without predicates.
+// without predicates.  The epilogue epi is applied to each entry; skip_if
+// (the accuracy gate's flag, when given) set: the FP64 FMA product writes C
+// instead and this kernel writes nothing.
 template <int S>
 __global__ void __launch_bounds__(256, 4)
 ozaki_sum_kernel(const float *__restrict__ D, int64_t plane, int64_t n, int64_t p, int chunks,
                  const uint64_t *__restrict__ rowmax, const unsigned long long *__restrict__ colmax,
-                 double *__restrict__ C) {
+                 double *C, const int *skip_if, EpiT<double> epi) {
+  if (skip_if != nullptr && *reinterpret_cast<const volatile int *>(skip_if) != 0) return;
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= p) return;
   bool fb;
@@ -474,16 +477,19 @@ ozaki_sum_kernel(const float *__restrict__ D, int64_t plane, int64_t n, int64_t 
       else if (round_to_double(M, k, bits)) out = __longlong_as_double((long long)(bits | ((uint64_t)neg << 63)));
       else out = int128_scaled(lo, hi, k);
     }
-    C[x] = out;
+    C[x] = epi_apply(epi, out, x);
   }
 }
 
 cudaError_t launch_ozaki_sum(int S, dim3 grid, cudaStream_t s, const float *D, int64_t plane,
                              int64_t n, int64_t p, int chunks, const uint64_t *rowmax,
-                             const unsigned long long *colmax, double *C) {
+                             const unsigned long long *colmax, double *C, const int *skip_if,
+                             const EpiT<double> &epi) {
   switch (S) {
 #define MM_OZ_SUM(V) \
-  case V: ozaki_sum_kernel<V><<<grid, 256, 0, s>>>(D, plane, n, p, chunks, rowmax, colmax, C); break;
+  case V: \
+    ozaki_sum_kernel<V><<<grid, 256, 0, s>>>(D, plane, n, p, chunks, rowmax, colmax, C, skip_if, epi); \
+    break;
     MM_OZ_SUM(2) MM_OZ_SUM(3) MM_OZ_SUM(4) MM_OZ_SUM(5) MM_OZ_SUM(6) MM_OZ_SUM(7) MM_OZ_SUM(8)
     MM_OZ_SUM(9) MM_OZ_SUM(10) MM_OZ_SUM(11) MM_OZ_SUM(12)
 #undef MM_OZ_SUM
@@ -551,7 +557,7 @@ int64_t ozaki_chunk(int S) {
 }
 
 mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *A,
-                    const double *B, double *C, int S, bool gate, cudaStream_t s) {
+                    const double *B, double *C, int S, bool gate, cudaStream_t s, const Epi *epi) {
   if (S < kOzakiMinSlices || S > kOzakiMaxSlices) return MM_EINVAL;
   if (n == 0 || p == 0) return MM_OK;
   if (m == 0) return note_cuda(cudaMemsetAsync(C, 0, (size_t)(n * p) * sizeof(double), s));
@@ -707,20 +713,11 @@ mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *
   e = launch_tc(kTcE4m3, d_tab, nprobs, (int)lay.units, unit_map, nullptr, ws.ptr, lay.rows, cfg,
                 g_ctx.d_err, s, d_order);
   if (e != cudaSuccess) return note_cuda(e);
-  {
-    TraceScope ts("ozaki_sum", s);
-    const int64_t gx = ceil_div(p, 256);
-    // one wave: four blocks per SM (the launch bound)
-    const int64_t gy = std::max<int64_t>(1, std::min<int64_t>({n, 65535, ceil_div((int64_t)sm_count() * 4, gx)}));
-    if (gx > 0x7fffffffLL) return MM_EINVAL;
-    e = launch_ozaki_sum(S, dim3((unsigned)gx, (unsigned)gy), s, D, lay.plane, n, p, lay.chunks,
-                         rowmax, colmax, C);
-    if (e != cudaSuccess) return note_cuda(e);
-    if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
-  }
-  if (!gate) return MM_OK;
-  int *flag = reinterpret_cast<int *>(base + lay.flag_off);
-  {
+  // the gate reads the level sums only, so it runs before the sum kernel:
+  // where it fails, the sum writes nothing and the FP64 FMA product below
+  // reads the epilogue's D (which may be C) untouched
+  int *flag = gate ? reinterpret_cast<int *>(base + lay.flag_off) : nullptr;
+  if (gate) {
     TraceScope ts("ozaki_gate", s);
     if ((e = cudaMemsetAsync(flag, 0, sizeof(int), s)) != cudaSuccess) return note_cuda(e);
     const double room = 0.98 - (double)m * 0x1p-23;
@@ -734,14 +731,26 @@ mm_status run_ozaki(Scratch &ws, int64_t n, int64_t m, int64_t p, const double *
                                                 lay.chunks, n, p, rowmax, colmax, thr, flag);
     if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
   }
+  {
+    TraceScope ts("ozaki_sum", s);
+    const int64_t gx = ceil_div(p, 256);
+    // one wave: four blocks per SM (the launch bound)
+    const int64_t gy = std::max<int64_t>(1, std::min<int64_t>({n, 65535, ceil_div((int64_t)sm_count() * 4, gx)}));
+    if (gx > 0x7fffffffLL) return MM_EINVAL;
+    e = launch_ozaki_sum(S, dim3((unsigned)gx, (unsigned)gy), s, D, lay.plane, n, p, lay.chunks,
+                         rowmax, colmax, C, flag, epi_of<double>(epi));
+    if (e != cudaSuccess) return note_cuda(e);
+    if ((e = cudaGetLastError()) != cudaSuccess) return note_cuda(e);
+  }
+  if (!gate) return MM_OK;
   // the FP64 FMA product replaces C where the flag is set: the same kernels
   // and K slices as MM_MODE_DGEMM, so the bits are that mode's
   const SimtPlan pl = simt_plan(true, n, m, p);
   if (pl.S >= 1)
     return note_cuda(launch_simt_splitk_f64(
         n, m, p, A, B, C, pl.S > 1 ? reinterpret_cast<double *>(base + lay.simt_off) : nullptr, pl, s,
-        flag));
-  return note_cuda(launch_simt_f64(n, m, p, A, B, C, s, flag));
+        flag, epi));
+  return note_cuda(launch_simt_f64(n, m, p, A, B, C, s, flag, epi));
 }
 
 size_t ozaki_scratch_bytes(int64_t n, int64_t m, int64_t p, int S) {

@@ -80,14 +80,15 @@ __device__ __forceinline__ void load_vec(const T *__restrict__ X, int64_t ld,
 // EDGE = true: predicated loads and stores for ragged edges and unaligned
 // operands.
 // A has leading dimension lda and K length kb (a K slice of a longer A when
-// kb < lda); B has kb rows.
+// kb < lda); B has kb rows.  The stores apply the epilogue epi (C may be the
+// epilogue's D).
 template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC, bool EDGE>
 __device__ __forceinline__ void simt_tile(const T *__restrict__ A, const T *__restrict__ B,
-                                          T *__restrict__ C, int64_t n, int64_t lda, int64_t kb,
+                                          T *C, int64_t n, int64_t lda, int64_t kb,
                                           int64_t p,
                                           int64_t tile_m, int64_t tile_n,
                                           T (&As)[2][BK][BM + SimtShape<T, BM, BN, BK, TM, TN>::APAD],
-                                          T (&Bs)[2][BK][BN]) {
+                                          T (&Bs)[2][BK][BN], const EpiT<T> &epi) {
   using S = SimtShape<T, BM, BN, BK, TM, TN>;
   constexpr int W = S::W;
   using V = typename Vec16<T>::type;
@@ -194,12 +195,12 @@ __device__ __forceinline__ void simt_tile(const T *__restrict__ A, const T *__re
           V t;
           T *tp = reinterpret_cast<T *>(&t);
 #pragma unroll
-          for (int e = 0; e < W; e++) tp[e] = src[e];
+          for (int e = 0; e < W; e++) tp[e] = epi_apply(epi, src[e], row * p + col + e);
           *reinterpret_cast<V *>(dst) = t;
         } else {
 #pragma unroll
           for (int e = 0; e < W; e++)
-            if (col + e < p) dst[e] = src[e];
+            if (col + e < p) dst[e] = epi_apply(epi, src[e], row * p + col + e);
         }
       }
     }
@@ -209,33 +210,38 @@ __device__ __forceinline__ void simt_tile(const T *__restrict__ A, const T *__re
 // Interior tiles of aligned operands take the unchecked form.
 template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
 __device__ __forceinline__ void simt_tile_any(const T *__restrict__ A, const T *__restrict__ B,
-                                              T *__restrict__ C, int64_t n, int64_t lda, int64_t kb,
-                                              int64_t p, int64_t tile_m, int64_t tile_n) {
+                                              T *C, int64_t n, int64_t lda, int64_t kb,
+                                              int64_t p, int64_t tile_m, int64_t tile_n,
+                                              const EpiT<T> &epi) {
   __shared__ __align__(16) T As[2][BK][BM + SimtShape<T, BM, BN, BK, TM, TN>::APAD];
   __shared__ __align__(16) T Bs[2][BK][BN];
   const bool interior = VEC && (tile_m + 1) * BM <= n && (tile_n + 1) * BN <= p && kb % BK == 0;
   if (interior)
-    simt_tile<T, BM, BN, BK, TM, TN, VEC, false>(A, B, C, n, lda, kb, p, tile_m, tile_n, As, Bs);
+    simt_tile<T, BM, BN, BK, TM, TN, VEC, false>(A, B, C, n, lda, kb, p, tile_m, tile_n, As, Bs,
+                                                 epi);
   else
-    simt_tile<T, BM, BN, BK, TM, TN, VEC, true>(A, B, C, n, lda, kb, p, tile_m, tile_n, As, Bs);
+    simt_tile<T, BM, BN, BK, TM, TN, VEC, true>(A, B, C, n, lda, kb, p, tile_m, tile_n, As, Bs,
+                                                epi);
 }
 
 template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
 __global__ void __launch_bounds__(256, (SimtShape<T, BM, BN, BK, TM, TN>::MIN_BLOCKS))
-simt_gemm_kernel(const T *__restrict__ A, const T *__restrict__ B, T *__restrict__ C,
-                 int64_t n, int64_t m, int64_t p, const int *__restrict__ run_if) {
+simt_gemm_kernel(const T *__restrict__ A, const T *__restrict__ B, T *C,
+                 int64_t n, int64_t m, int64_t p, const int *__restrict__ run_if, EpiT<T> epi) {
   // run_if: a device word; when given, the product runs only where it is set
   if (run_if != nullptr && *reinterpret_cast<const volatile int *>(run_if) == 0) return;
-  simt_tile_any<T, BM, BN, BK, TM, TN, VEC>(A, B, C, n, m, m, p, blockIdx.y, blockIdx.x);
+  simt_tile_any<T, BM, BN, BK, TM, TN, VEC>(A, B, C, n, m, m, p, blockIdx.y, blockIdx.x, epi);
 }
 
 // K slice blockIdx.z (K values [z ks, min((z + 1) ks, m))) of a product,
 // into part + z n p (C's layout).  ks is a multiple of BK, so the slice's
-// first column of A keeps A's 16-byte alignment.
+// first column of A keeps A's 16-byte alignment.  epi applies when the one
+// slice writes C itself (S = 1), and is off otherwise.
 template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
 __global__ void __launch_bounds__(256, (SimtShape<T, BM, BN, BK, TM, TN>::MIN_BLOCKS))
-simt_splitk_kernel(const T *__restrict__ A, const T *__restrict__ B, T *__restrict__ part,
-                   int64_t n, int64_t m, int64_t p, int64_t ks, const int *__restrict__ run_if) {
+simt_splitk_kernel(const T *__restrict__ A, const T *__restrict__ B, T *part,
+                   int64_t n, int64_t m, int64_t p, int64_t ks, const int *__restrict__ run_if,
+                   EpiT<T> epi) {
   // launched as a programmatic dependent of the previous kernel on the
   // stream: resident early, it reads nothing before that kernel has finished
   // and its writes are visible; the sum kernel may then be scheduled
@@ -246,17 +252,17 @@ simt_splitk_kernel(const T *__restrict__ A, const T *__restrict__ B, T *__restri
   const int64_t k0 = (int64_t)blockIdx.z * ks;
   const int64_t kb = min(ks, m - k0);
   simt_tile_any<T, BM, BN, BK, TM, TN, VEC>(A + k0, B + k0 * p, part + (int64_t)blockIdx.z * n * p,
-                                            n, m, kb, p, blockIdx.y, blockIdx.x);
+                                            n, m, kb, p, blockIdx.y, blockIdx.x, epi);
 }
 
 // C = sum over s of part[s] for the np entries, 32 consecutive entries per
 // block (the loads of a slice coalesce): warp g adds slices [g S / G,
 // (g + 1) S / G) in order (G = min(8, S)), then the G partial sums are added
-// in the order g = 0, 1, ..., G - 1.
+// in the order g = 0, 1, ..., G - 1; the epilogue epi is applied to the sum.
 template <typename T>
 __global__ void __launch_bounds__(256)
-splitk_sum_kernel(const T *__restrict__ part, int S, int64_t np, T *__restrict__ C,
-                  const int *__restrict__ run_if) {
+splitk_sum_kernel(const T *__restrict__ part, int S, int64_t np, T *C,
+                  const int *__restrict__ run_if, EpiT<T> epi) {
   __shared__ T ps[8][32];
   asm volatile("griddepcontrol.wait;" ::: "memory");  // the slices' partials are written
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -275,7 +281,7 @@ splitk_sum_kernel(const T *__restrict__ part, int S, int64_t np, T *__restrict__
   if (g == 0 && i < np) {
     T acc = ps[0][lane];
     for (int gg = 1; gg < G; gg++) acc += ps[gg][lane];
-    C[i] = acc;
+    C[i] = epi_apply(epi, acc, i);
   }
 }
 
@@ -294,24 +300,26 @@ simt_grouped_kernel(const SimtProb *__restrict__ probs, int nprobs) {
   const int local = t - pr.tile_start;
   simt_tile_any<T, BM, BN, BK, TM, TN, VEC>(
       static_cast<const T *>(pr.A), static_cast<const T *>(pr.B), static_cast<T *>(pr.C),
-      pr.n, pr.m, pr.m, pr.p, local / pr.tiles_n, local % pr.tiles_n);
+      pr.n, pr.m, pr.m, pr.p, local / pr.tiles_n, local % pr.tiles_n,
+      EpiT<T>{nullptr, T(1), T(0), 0});
 }
 
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 cudaError_t launch_simt(int64_t n, int64_t m, int64_t p, const T *A, const T *B, T *C,
-                        cudaStream_t s, const char *name, const int *run_if = nullptr) {
+                        cudaStream_t s, const char *name, const int *run_if, const Epi *epi) {
   constexpr int W = 16 / (int)sizeof(T);
   const int64_t gy = ceil_div(n, BM), gx = ceil_div(p, BN);
   if (gy > 65535 || gx > 2147483647LL) return cudaErrorInvalidValue;
   dim3 grid((unsigned)gx, (unsigned)gy);
   const bool vec = aligned16(A) && aligned16(B) && aligned16(C) && m % W == 0 && p % W == 0;
+  const EpiT<T> e = epi_of<T>(epi);
   TraceScope ts(name, s);
   if (vec)
-    simt_gemm_kernel<T, BM, BN, BK, TM, TN, true><<<grid, 256, 0, s>>>(A, B, C, n, m, p, run_if);
+    simt_gemm_kernel<T, BM, BN, BK, TM, TN, true><<<grid, 256, 0, s>>>(A, B, C, n, m, p, run_if, e);
   else
-    simt_gemm_kernel<T, BM, BN, BK, TM, TN, false><<<grid, 256, 0, s>>>(A, B, C, n, m, p, run_if);
+    simt_gemm_kernel<T, BM, BN, BK, TM, TN, false><<<grid, 256, 0, s>>>(A, B, C, n, m, p, run_if, e);
   return cudaGetLastError();
 }
 
@@ -337,7 +345,7 @@ cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, cudaStream_t s
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 cudaError_t launch_splitk(int64_t n, int64_t m, int64_t p, const T *A, const T *B, T *C, T *part,
                           const SimtPlan &pl, cudaStream_t s, const char *name,
-                          const int *run_if) {
+                          const int *run_if, const Epi *epi) {
   constexpr int W = 16 / (int)sizeof(T);
   const int64_t gy = ceil_div(n, BM), gx = ceil_div(p, BN);
   if (gy > 65535 || gx > 2147483647LL || pl.S < 1 || pl.S > 65535) return cudaErrorInvalidValue;
@@ -345,20 +353,23 @@ cudaError_t launch_splitk(int64_t n, int64_t m, int64_t p, const T *A, const T *
   if (pl.S > 1 && part == nullptr) return cudaErrorInvalidValue;
   dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)pl.S);
   const bool vec = aligned16(A) && aligned16(B) && aligned16(out) && m % W == 0 && p % W == 0;
+  const EpiT<T> ep = epi_of<T>(epi);
+  // the epilogue goes with the kernel that writes C
+  const EpiT<T> slice_ep = pl.S == 1 ? ep : EpiT<T>{nullptr, T(1), T(0), 0};
   cudaError_t e;
   {
     TraceScope ts(name, s);
     e = vec ? launch_dependent(simt_splitk_kernel<T, BM, BN, BK, TM, TN, true>, grid, s, A, B, out, n, m,
-                               p, pl.ks, run_if)
+                               p, pl.ks, run_if, slice_ep)
             : launch_dependent(simt_splitk_kernel<T, BM, BN, BK, TM, TN, false>, grid, s, A, B, out, n, m,
-                               p, pl.ks, run_if);
+                               p, pl.ks, run_if, slice_ep);
   }
   if (e != cudaSuccess || pl.S == 1) return e;
   TraceScope ts("simt_sum", s);
   const int64_t np = n * p;
   if (ceil_div(np, 32) > 2147483647LL) return cudaErrorInvalidValue;
   return launch_dependent(splitk_sum_kernel<T>, dim3((unsigned)ceil_div(np, 32), 1, 1), s,
-                          static_cast<const T *>(part), pl.S, np, C, run_if);
+                          static_cast<const T *>(part), pl.S, np, C, run_if, ep);
 }
 
 }  // namespace
@@ -399,31 +410,32 @@ size_t simt_scratch_bytes(bool f64, int64_t n, int64_t m, int64_t p) {
 }
 
 cudaError_t launch_simt_splitk_f32(int64_t n, int64_t m, int64_t p, const float *A, const float *B,
-                                   float *C, float *part, const SimtPlan &pl, cudaStream_t s) {
+                                   float *C, float *part, const SimtPlan &pl, cudaStream_t s,
+                                   const Epi *epi) {
   if (pl.wide)
     return launch_splitk<float, kSimtF32BM, kSimtF32BN, kSimtF32BK, 8, 8>(n, m, p, A, B, C, part, pl, s,
-                                                                         "simt_f32", nullptr);
+                                                                         "simt_f32", nullptr, epi);
   return launch_splitk<float, 64, 64, kSimtF32BK, 4, 4>(n, m, p, A, B, C, part, pl, s, "simt_f32",
-                                                        nullptr);
+                                                        nullptr, epi);
 }
 
 cudaError_t launch_simt_splitk_f64(int64_t n, int64_t m, int64_t p, const double *A,
                                    const double *B, double *C, double *part, const SimtPlan &pl,
-                                   cudaStream_t s, const int *run_if) {
+                                   cudaStream_t s, const int *run_if, const Epi *epi) {
   return launch_splitk<double, kSimtF64BM, kSimtF64BN, kSimtF64BK, 4, 4>(n, m, p, A, B, C, part, pl, s,
-                                                                         "dgemm_f64", run_if);
+                                                                         "dgemm_f64", run_if, epi);
 }
 
 cudaError_t launch_simt_f32(int64_t n, int64_t m, int64_t p, const float *A, const float *B,
-                            float *C, cudaStream_t s) {
+                            float *C, cudaStream_t s, const Epi *epi) {
   return launch_simt<float, kSimtF32BM, kSimtF32BN, kSimtF32BK, 8, 8>(n, m, p, A, B, C, s,
-                                                                      "simt_f32");
+                                                                      "simt_f32", nullptr, epi);
 }
 
 cudaError_t launch_simt_f64(int64_t n, int64_t m, int64_t p, const double *A, const double *B,
-                            double *C, cudaStream_t s, const int *run_if) {
+                            double *C, cudaStream_t s, const int *run_if, const Epi *epi) {
   return launch_simt<double, kSimtF64BM, kSimtF64BN, kSimtF64BK, 4, 4>(n, m, p, A, B, C, s,
-                                                                       "dgemm_f64", run_if);
+                                                                       "dgemm_f64", run_if, epi);
 }
 
 cudaError_t launch_simt_grouped(bool f64, const SimtProb *d_probs, int nprobs, int total_tiles,

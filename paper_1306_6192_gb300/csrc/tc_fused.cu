@@ -524,9 +524,33 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant
   const int nvalid = rows_valid * cols_valid;  // entries of this CTA's chunk inside C
   if (nvalid > 0 && !failed) {
     if (pr.Q == 1) {
-      for (int e = threadIdx.x; e < nvalid; e += kFThreads) {
-        const int rr = r0 + e / cols_valid, c = e % cols_valid;
-        __stcs(pr.C + (row0 + rr) * pr.p + col0 + c, red[rr * kFRedPitch + c]);
+      if (pr.epi.on == 0) {
+        for (int e = threadIdx.x; e < nvalid; e += kFThreads) {
+          const int rr = r0 + e / cols_valid, c = e % cols_valid;
+          __stcs(pr.C + (row0 + rr) * pr.p + col0 + c, red[rr * kFRedPitch + c]);
+        }
+      } else {
+        // C = alpha (A.B) + beta D, eight entries a thread at a time: their
+        // values of D are loaded before any of them is stored (D may be C)
+        for (int e0 = threadIdx.x; e0 < nvalid; e0 += 8 * kFThreads) {
+          float dv[8];
+          int64_t idx[8];
+#pragma unroll
+          for (int u = 0; u < 8; u++) {
+            const int e = min(e0 + u * kFThreads, nvalid - 1);
+            idx[u] = (row0 + r0 + e / cols_valid) * pr.p + col0 + e % cols_valid;
+            dv[u] = pr.epi.on == 2 ? pr.epi.D[idx[u]] : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; u++) {
+            const int e = e0 + u * kFThreads;
+            if (e < nvalid) {
+              const float x = red[(r0 + e / cols_valid) * kFRedPitch + e % cols_valid];
+              __stcs(pr.C + idx[u], pr.epi.on == 2 ? fmaf(pr.epi.alpha, x, pr.epi.beta * dv[u])
+                                                   : pr.epi.alpha * x);
+            }
+          }
+        }
       }
     } else {
       // clusters of this tile meet in global memory: slot (tile, q), then the
@@ -556,6 +580,15 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant
             src[u] = slot0 + (size_t)(r0 + e / cols_valid) * kFBN + e % cols_valid;
             sum[u] = __ldcg(src[u]);
           }
+          // the epilogue's D for the same entries, in flight with the slots
+          float dv[4];
+          int64_t idx[4];
+#pragma unroll
+          for (int u = 0; u < 4; u++) {
+            const int e = min(e0 + u * kFThreads, nvalid - 1);
+            idx[u] = (row0 + r0 + e / cols_valid) * pr.p + col0 + e % cols_valid;
+            dv[u] = pr.epi.on == 2 ? pr.epi.D[idx[u]] : 0.f;
+          }
           int qq = 1;
           for (; qq + 4 <= pr.Q; qq += 4) {
             float v[4][4];
@@ -576,7 +609,9 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant
           for (int u = 0; u < 4; u++) {
             const int e = e0 + u * kFThreads;
             if (e < nvalid)
-              __stcs(pr.C + (row0 + r0 + e / cols_valid) * pr.p + col0 + e % cols_valid, sum[u]);
+              __stcs(pr.C + idx[u], pr.epi.on == 0 ? sum[u]
+                                    : pr.epi.on == 2 ? fmaf(pr.epi.alpha, sum[u], pr.epi.beta * dv[u])
+                                                     : pr.epi.alpha * sum[u]);
           }
         }
         if (threadIdx.x == 0) *cnt = 0;  // ready for the next launch

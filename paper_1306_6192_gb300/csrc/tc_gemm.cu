@@ -503,6 +503,33 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
                             scale_pow2(__uint_as_float(v[4 * k + 1]), si + ce[4 * k + 1]),
                             scale_pow2(__uint_as_float(v[4 * k + 2]), si + ce[4 * k + 2]),
                             scale_pow2(__uint_as_float(v[4 * k + 3]), si + ce[4 * k + 3]));
+          if (pr.epi.on != 0) {
+            // C = alpha (A.B) + beta D on this thread's row of the block, in
+            // place in the staging area: the row's 32 values of D in eight
+            // 16-byte loads in flight (p % 4 == 0 and a 16-byte aligned D,
+            // so a vector is wholly inside or outside C's columns)
+            const int64_t i = row0 + lane;
+            const float al = pr.epi.alpha, be = pr.epi.beta;
+            if (pr.epi.on == 2) {
+              const float4 *drow = reinterpret_cast<const float4 *>(pr.epi.D + i * pr.p + j0);
+              float4 dq[8];
+#pragma unroll
+              for (int k = 0; k < 8; k++)
+                dq[k] = (i < pr.n && j0 + 4 * k < pr.p) ? drow[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+              for (int k = 0; k < 8; k++) {
+                const float4 x = rowp[k ^ (lane & 7)];
+                rowp[k ^ (lane & 7)] = make_float4(fmaf(al, x.x, be * dq[k].x), fmaf(al, x.y, be * dq[k].y),
+                                                   fmaf(al, x.z, be * dq[k].z), fmaf(al, x.w, be * dq[k].w));
+              }
+            } else {
+#pragma unroll
+              for (int k = 0; k < 8; k++) {
+                const float4 x = rowp[k];
+                rowp[k] = make_float4(al * x.x, al * x.y, al * x.z, al * x.w);
+              }
+            }
+          }
           fence_proxy_async_shared();
           __syncwarp();
           if (lane == 0 && row0 < pr.n) {  // a block wholly below C is not stored
@@ -523,8 +550,28 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap, const SplitProb *__rest
           float *dst = pr.C + row0 * pr.p + j;
           const int64_t left = pr.n - row0;
           const int rows = left < 32 ? (int)left : 32;
+          if (pr.epi.on == 0) {
 #pragma unroll 8
-          for (int r = 0; r < rows; r++, dst += pr.p) __stcs(dst, buf[r * 33 + lane]);
+            for (int r = 0; r < rows; r++, dst += pr.p) __stcs(dst, buf[r * 33 + lane]);
+          } else {
+            // C = alpha (A.B) + beta D, sixteen rows at a time: their values
+            // of D are loaded before any of them is stored (D may be C)
+            const float *dcol = pr.epi.D + row0 * pr.p + j;
+#pragma unroll
+            for (int h = 0; h < 32; h += 16) {
+              float dv[16];
+#pragma unroll
+              for (int r = 0; r < 16; r++)
+                dv[r] = (pr.epi.on == 2 && h + r < rows) ? dcol[(int64_t)(h + r) * pr.p] : 0.f;
+#pragma unroll
+              for (int r = 0; r < 16; r++)
+                if (h + r < rows)
+                  __stcs(dst + (int64_t)(h + r) * pr.p,
+                         pr.epi.on == 2
+                             ? fmaf(pr.epi.alpha, buf[(h + r) * 33 + lane], pr.epi.beta * dv[r])
+                             : pr.epi.alpha * buf[(h + r) * 33 + lane]);
+            }
+          }
         }
         __syncwarp();
       }

@@ -42,7 +42,7 @@ TcTail plan_tail(SplitProb &sp, TcKind kind, const TcChoice &ch) {
 }
 
 mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s,
-                        const TcChoice *force, bool six) {
+                        const TcChoice *force, bool six, const Epi *epi) {
   Group groups[2] = {{kTcSplitBf16x3}, {kTcSplitBf16x6}};
   int64_t rows = 0, scal = 0, part = 0;
   size_t tail_parts = 0, tail_cnts = 0;  // partial tiles and counters of tail splits
@@ -68,6 +68,7 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
     sp.A = static_cast<const float *>(q.A);
     sp.B = static_cast<const float *>(q.B);
     sp.C = static_cast<float *>(q.C);
+    if (epi && count == 1) sp.epi = epi->as<float>();
     sp.n = (int32_t)q.n;
     sp.m = (int32_t)q.m;
     sp.p = (int32_t)q.p;
@@ -173,7 +174,10 @@ mm_status run_tc_groups(Scratch &ws, const mm_problem *probs, int count, cudaStr
     std::vector<uint8_t> blob(cmap_rel + cmap_bytes, 0);
     for (size_t k = 0; cmap_bytes && k < ntab; k++) {
       SplitProb &sp = all[k];
-      if (tc_c_map_ok(sp.C, sp.n, sp.p) &&
+      // the epilogue C = alpha (A.B) + beta D loads D in 16-byte vectors
+      // beside the tiled stores (a D off that alignment: plain stores)
+      const bool d_ok = sp.epi.on != 2 || (reinterpret_cast<uintptr_t>(sp.epi.D) & 15u) == 0;
+      if (d_ok && tc_c_map_ok(sp.C, sp.n, sp.p) &&
           encode_c_map(blob.data() + cmap_rel + k * kMapBytes, sp.C, sp.n, sp.p) == cudaSuccess)
         sp.c_tma = (int32_t)k + 1;
     }
@@ -336,8 +340,8 @@ mm_status run_split_chunked(Scratch &ws, int64_t n, int64_t m, int64_t p, const 
 }
 
 mm_status run_split(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s,
-                    const TcChoice *force, bool six) {
-  return run_tc_groups(ws, probs, count, s, force, six);
+                    const TcChoice *force, bool six, const Epi *epi) {
+  return run_tc_groups(ws, probs, count, s, force, six, epi);
 }
 
 mm_status run_fp8(Scratch &ws, const mm_problem *probs, int count, cudaStream_t s) {
@@ -445,12 +449,14 @@ FusedPlan fused_plan(int64_t n, int64_t m, int64_t p, TcKind kind) {
 }
 
 mm_status run_fused(Scratch &ws, int64_t n, int64_t m, int64_t p, const float *A, const float *B,
-                    float *C, TcKind kind, const FusedPlan &plan, cudaStream_t s) {
+                    float *C, TcKind kind, const FusedPlan &plan, cudaStream_t s,
+                    const Epi *epi) {
   FusedProb fp;
   std::memset(&fp, 0, sizeof(fp));
   fp.A = A;
   fp.B = B;
   fp.C = C;
+  fp.epi = epi_of<float>(epi);
   fp.n = (int32_t)n;
   fp.m = (int32_t)m;
   fp.p = (int32_t)p;

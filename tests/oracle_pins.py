@@ -247,9 +247,42 @@ def pin_complex(orc):
     assert np.array_equal(C.real, Cr) and np.all(C.imag == 0) and np.array_equal(absC, Sr)
 
 
+def pin_axpby(orc):
+    """alpha (A.B) + beta D against exact rationals on tiny inputs (within the
+    FP64 rounding of the product and of the two scalings), exact on small
+    integers, and its special cases: alpha = 1, beta = 0 is the product
+    itself; alpha = 0 is beta D without the product; D = C gives the same
+    as a separate copy of D."""
+    A = synth.uniform_pm1(3100, (3, 5)).astype(np.float64)
+    B = synth.uniform_pm1(3101, (5, 4)).astype(np.float64)
+    D = synth.uniform_pm1(3102, (3, 4)).astype(np.float64)
+    alpha, beta = -0.3, 1.7
+    got, norm = orc.axpby(alpha, A, B, beta, D)
+    C, S = _exact_product(A, B)
+    for i in range(3):
+        for j in range(4):
+            a, b, d = Fraction(alpha), Fraction(beta), Fraction(float(D[i, j]))
+            exact = a * C[i][j] + b * d
+            nrm = abs(a) * S[i][j] + abs(b) * abs(d)
+            assert abs(Fraction(float(got[i, j])) - exact) <= 8 * Fraction(U64) * nrm
+            assert abs(Fraction(float(norm[i, j])) - nrm) <= 8 * Fraction(U64) * nrm
+    Ai = synth.small_ints(3103, (4, 6)).astype(np.float64)
+    Bi = synth.small_ints(3104, (6, 5)).astype(np.float64)
+    Di = synth.small_ints(3105, (4, 5)).astype(np.float64)
+    got, _ = orc.axpby(3, Ai, Bi, -2, Di)
+    want = [[3 * sum(int(Ai[i, r]) * int(Bi[r, j]) for r in range(6)) - 2 * int(Di[i, j])
+             for j in range(5)] for i in range(4)]
+    assert np.array_equal(got, np.array(want, np.float64))
+    ref, ab = orc.gemm(A, B, with_abs=True)
+    got, norm = orc.axpby(1.0, A, B, 0.0, None)
+    assert np.array_equal(got, ref) and np.array_equal(norm, ab)
+    got, norm = orc.axpby(0.0, None, None, -2.0, D)
+    assert np.array_equal(got, -2.0 * D) and np.array_equal(norm, 2.0 * np.abs(D))
+
+
 ALL_PINS = [
     pin_bruteforce_definition, pin_small_ints_exact, pin_hand_example,
     pin_identity, pin_diagonal, pin_transpose, pin_freivalds,
     pin_threads_invariant, pin_empty_dims, pin_dot2_and_long_double,
-    pin_gemv, pin_pow2_exact, pin_complex,
+    pin_gemv, pin_pow2_exact, pin_complex, pin_axpby,
 ]
