@@ -16,6 +16,7 @@
 // partials of each entry added in a fixed grouping and order by a second
 // kernel.
 #include <algorithm>
+#include <type_traits>
 
 #include "mm_internal.h"
 
@@ -80,11 +81,14 @@ __device__ __forceinline__ void load_vec(const T *__restrict__ X, int64_t ld,
 // EDGE = true: predicated loads and stores for ragged edges and unaligned
 // operands.
 // A has leading dimension lda and K length kb (a K slice of a longer A when
-// kb < lda); B has kb rows.  The stores apply the epilogue epi (C may be the
-// epilogue's D).
-template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC, bool EDGE>
+// kb < lda); B has kb rows.  EPI: the stores apply the epilogue epi (C may
+// then be the epilogue's D, so C is not declared unaliased).
+template <typename T, bool EPI>
+using OutPtr = std::conditional_t<EPI, T *, T *__restrict__>;
+
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC, bool EDGE, bool EPI>
 __device__ __forceinline__ void simt_tile(const T *__restrict__ A, const T *__restrict__ B,
-                                          T *C, int64_t n, int64_t lda, int64_t kb,
+                                          OutPtr<T, EPI> C, int64_t n, int64_t lda, int64_t kb,
                                           int64_t p,
                                           int64_t tile_m, int64_t tile_n,
                                           T (&As)[2][BK][BM + SimtShape<T, BM, BN, BK, TM, TN>::APAD],
@@ -195,12 +199,12 @@ __device__ __forceinline__ void simt_tile(const T *__restrict__ A, const T *__re
           V t;
           T *tp = reinterpret_cast<T *>(&t);
 #pragma unroll
-          for (int e = 0; e < W; e++) tp[e] = epi_apply(epi, src[e], row * p + col + e);
+          for (int e = 0; e < W; e++) tp[e] = EPI ? epi_apply(epi, src[e], row * p + col + e) : src[e];
           *reinterpret_cast<V *>(dst) = t;
         } else {
 #pragma unroll
           for (int e = 0; e < W; e++)
-            if (col + e < p) dst[e] = epi_apply(epi, src[e], row * p + col + e);
+            if (col + e < p) dst[e] = EPI ? epi_apply(epi, src[e], row * p + col + e) : src[e];
         }
       }
     }
@@ -208,38 +212,38 @@ __device__ __forceinline__ void simt_tile(const T *__restrict__ A, const T *__re
 }
 
 // Interior tiles of aligned operands take the unchecked form.
-template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC, bool EPI>
 __device__ __forceinline__ void simt_tile_any(const T *__restrict__ A, const T *__restrict__ B,
-                                              T *C, int64_t n, int64_t lda, int64_t kb,
+                                              OutPtr<T, EPI> C, int64_t n, int64_t lda, int64_t kb,
                                               int64_t p, int64_t tile_m, int64_t tile_n,
                                               const EpiT<T> &epi) {
   __shared__ __align__(16) T As[2][BK][BM + SimtShape<T, BM, BN, BK, TM, TN>::APAD];
   __shared__ __align__(16) T Bs[2][BK][BN];
   const bool interior = VEC && (tile_m + 1) * BM <= n && (tile_n + 1) * BN <= p && kb % BK == 0;
   if (interior)
-    simt_tile<T, BM, BN, BK, TM, TN, VEC, false>(A, B, C, n, lda, kb, p, tile_m, tile_n, As, Bs,
+    simt_tile<T, BM, BN, BK, TM, TN, VEC, false, EPI>(A, B, C, n, lda, kb, p, tile_m, tile_n, As, Bs,
                                                  epi);
   else
-    simt_tile<T, BM, BN, BK, TM, TN, VEC, true>(A, B, C, n, lda, kb, p, tile_m, tile_n, As, Bs,
+    simt_tile<T, BM, BN, BK, TM, TN, VEC, true, EPI>(A, B, C, n, lda, kb, p, tile_m, tile_n, As, Bs,
                                                 epi);
 }
 
-template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC, bool EPI>
 __global__ void __launch_bounds__(256, (SimtShape<T, BM, BN, BK, TM, TN>::MIN_BLOCKS))
-simt_gemm_kernel(const T *__restrict__ A, const T *__restrict__ B, T *C,
+simt_gemm_kernel(const T *__restrict__ A, const T *__restrict__ B, OutPtr<T, EPI> C,
                  int64_t n, int64_t m, int64_t p, const int *__restrict__ run_if, EpiT<T> epi) {
   // run_if: a device word; when given, the product runs only where it is set
   if (run_if != nullptr && *reinterpret_cast<const volatile int *>(run_if) == 0) return;
-  simt_tile_any<T, BM, BN, BK, TM, TN, VEC>(A, B, C, n, m, m, p, blockIdx.y, blockIdx.x, epi);
+  simt_tile_any<T, BM, BN, BK, TM, TN, VEC, EPI>(A, B, C, n, m, m, p, blockIdx.y, blockIdx.x, epi);
 }
 
 // K slice blockIdx.z (K values [z ks, min((z + 1) ks, m))) of a product,
 // into part + z n p (C's layout).  ks is a multiple of BK, so the slice's
 // first column of A keeps A's 16-byte alignment.  epi applies when the one
 // slice writes C itself (S = 1), and is off otherwise.
-template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC, bool EPI>
 __global__ void __launch_bounds__(256, (SimtShape<T, BM, BN, BK, TM, TN>::MIN_BLOCKS))
-simt_splitk_kernel(const T *__restrict__ A, const T *__restrict__ B, T *part,
+simt_splitk_kernel(const T *__restrict__ A, const T *__restrict__ B, OutPtr<T, EPI> part,
                    int64_t n, int64_t m, int64_t p, int64_t ks, const int *__restrict__ run_if,
                    EpiT<T> epi) {
   // launched as a programmatic dependent of the previous kernel on the
@@ -251,7 +255,7 @@ simt_splitk_kernel(const T *__restrict__ A, const T *__restrict__ B, T *part,
   if (run_if != nullptr && *reinterpret_cast<const volatile int *>(run_if) == 0) return;
   const int64_t k0 = (int64_t)blockIdx.z * ks;
   const int64_t kb = min(ks, m - k0);
-  simt_tile_any<T, BM, BN, BK, TM, TN, VEC>(A + k0, B + k0 * p, part + (int64_t)blockIdx.z * n * p,
+  simt_tile_any<T, BM, BN, BK, TM, TN, VEC, EPI>(A + k0, B + k0 * p, part + (int64_t)blockIdx.z * n * p,
                                             n, m, kb, p, blockIdx.y, blockIdx.x, epi);
 }
 
@@ -298,7 +302,7 @@ simt_grouped_kernel(const SimtProb *__restrict__ probs, int nprobs) {
   }
   const SimtProb &pr = probs[lo];
   const int local = t - pr.tile_start;
-  simt_tile_any<T, BM, BN, BK, TM, TN, VEC>(
+  simt_tile_any<T, BM, BN, BK, TM, TN, VEC, false>(
       static_cast<const T *>(pr.A), static_cast<const T *>(pr.B), static_cast<T *>(pr.C),
       pr.n, pr.m, pr.m, pr.p, local / pr.tiles_n, local % pr.tiles_n,
       EpiT<T>{nullptr, T(1), T(0), 0});
@@ -316,10 +320,17 @@ cudaError_t launch_simt(int64_t n, int64_t m, int64_t p, const T *A, const T *B,
   const bool vec = aligned16(A) && aligned16(B) && aligned16(C) && m % W == 0 && p % W == 0;
   const EpiT<T> e = epi_of<T>(epi);
   TraceScope ts(name, s);
-  if (vec)
-    simt_gemm_kernel<T, BM, BN, BK, TM, TN, true><<<grid, 256, 0, s>>>(A, B, C, n, m, p, run_if, e);
-  else
-    simt_gemm_kernel<T, BM, BN, BK, TM, TN, false><<<grid, 256, 0, s>>>(A, B, C, n, m, p, run_if, e);
+  if (e.on != 0) {
+    if (vec)
+      simt_gemm_kernel<T, BM, BN, BK, TM, TN, true, true><<<grid, 256, 0, s>>>(A, B, C, n, m, p, run_if, e);
+    else
+      simt_gemm_kernel<T, BM, BN, BK, TM, TN, false, true><<<grid, 256, 0, s>>>(A, B, C, n, m, p, run_if, e);
+  } else {
+    if (vec)
+      simt_gemm_kernel<T, BM, BN, BK, TM, TN, true, false><<<grid, 256, 0, s>>>(A, B, C, n, m, p, run_if, e);
+    else
+      simt_gemm_kernel<T, BM, BN, BK, TM, TN, false, false><<<grid, 256, 0, s>>>(A, B, C, n, m, p, run_if, e);
+  }
   return cudaGetLastError();
 }
 
@@ -359,10 +370,16 @@ cudaError_t launch_splitk(int64_t n, int64_t m, int64_t p, const T *A, const T *
   cudaError_t e;
   {
     TraceScope ts(name, s);
-    e = vec ? launch_dependent(simt_splitk_kernel<T, BM, BN, BK, TM, TN, true>, grid, s, A, B, out, n, m,
-                               p, pl.ks, run_if, slice_ep)
-            : launch_dependent(simt_splitk_kernel<T, BM, BN, BK, TM, TN, false>, grid, s, A, B, out, n, m,
-                               p, pl.ks, run_if, slice_ep);
+    if (slice_ep.on != 0)
+      e = vec ? launch_dependent(simt_splitk_kernel<T, BM, BN, BK, TM, TN, true, true>, grid, s, A, B, out,
+                                 n, m, p, pl.ks, run_if, slice_ep)
+              : launch_dependent(simt_splitk_kernel<T, BM, BN, BK, TM, TN, false, true>, grid, s, A, B, out,
+                                 n, m, p, pl.ks, run_if, slice_ep);
+    else
+      e = vec ? launch_dependent(simt_splitk_kernel<T, BM, BN, BK, TM, TN, true, false>, grid, s, A, B, out,
+                                 n, m, p, pl.ks, run_if, slice_ep)
+              : launch_dependent(simt_splitk_kernel<T, BM, BN, BK, TM, TN, false, false>, grid, s, A, B, out,
+                                 n, m, p, pl.ks, run_if, slice_ep);
   }
   if (e != cudaSuccess || pl.S == 1) return e;
   TraceScope ts("simt_sum", s);
