@@ -806,6 +806,57 @@ def run_stress_only(args):
     return 0 if "error" not in out else 1
 
 
+def run_epilogue_only(args):
+    """Only C = A.B - D at n^3 on the split path (default 4096): the product,
+    the product then mm_add, and the subtraction fused into the product's
+    epilogue (mm_gemm_axpby), 20 queued calls each, plus one synchronous
+    fused call checked against the product minus D.  Prints one JSON line."""
+    import torch
+
+    import paper_1306_6192_gb300 as mm
+    torch.cuda.set_device(0)
+    mm.check_status(mm.mm_init(device=0), "mm_init")
+    stream = torch.cuda.Stream()
+    n = args.epilogue_size
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(3)
+    A = torch.rand((n, n), device="cuda", generator=gen) * 2 - 1
+    B = torch.rand((n, n), device="cuda", generator=gen) * 2 - 1
+    D = torch.rand((n, n), device="cuda", generator=gen) * 2 - 1
+    C = torch.empty((n, n), device="cuda")
+    X = torch.empty((n, n), device="cuda")
+    F32, X3 = mm.MM_F32, mm.MM_MODE_SPLIT_BF16X3
+    ok = mm.check_status
+
+    def queued(fn, k=20):
+        fn()
+        ok(mm.mm_sync(stream), "sync")
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    def two():
+        ok(mm.mm_gemm_async(n, n, n, A, B, C, F32, X3, stream), "gemm")
+        ok(mm.mm_add_async(n, n, 1.0, C, -1.0, D, C, F32, stream), "add")
+
+    out = {"n": n,
+           "gemm_ms": queued(lambda: ok(mm.mm_gemm_async(n, n, n, A, B, C, F32, X3, stream), "g")),
+           "gemm_then_add_ms": queued(two),
+           "fused_ms": queued(lambda: ok(mm.mm_gemm_axpby_async(n, n, n, 1.0, A, B, -1.0, D, C,
+                                                                  F32, X3, stream), "f"))}
+    ok(mm.mm_gemm(n, n, n, A, B, X, F32, X3), "gemm")
+    ok(mm.mm_gemm_axpby(n, n, n, 1.0, A, B, -1.0, D, C, F32, X3), "axpby")
+    out["fused_equals_product_minus_d"] = bool(torch.equal(C, X - D))
+    mm.mm_shutdown()
+    print(json.dumps({"metric": "fused epilogue", "epilogue": out}))
+    return 0 if out["fused_equals_product_minus_d"] else 1
+
+
 def run_serve_sweep(args):
     """Config-5 sweep: the Poisson replay at several fractions of the measured
     capacity, batched (2 streams, up to 256 per launch) against one request
@@ -1176,6 +1227,9 @@ def main(argv=None):
     ap.add_argument("--fp8-only", action="store_true",
                     help="only the FP8 e4m3 product at --size")
     ap.add_argument("--stress-only", action="store_true", help="only the config-3 stress shapes")
+    ap.add_argument("--epilogue-only", action="store_true",
+                    help="only C = A.B - D, fused into the product's epilogue and as two calls")
+    ap.add_argument("--epilogue-size", type=int, default=4096)
     ap.add_argument("--serve-f64", choices=["dgemm", "ozaki"], default="dgemm",
                     help="path of the serving mix's FP64 requests")
     ap.add_argument("--shard", choices=["none", "rows"], default="none",
@@ -1193,6 +1247,8 @@ def main(argv=None):
         return run_ozaki_only(args)
     if args.stress_only:
         return run_stress_only(args)
+    if args.epilogue_only:
+        return run_epilogue_only(args)
     if args.fp8_only:
         return run_fp8_only(args)
     if args.shard == "rows":
