@@ -50,3 +50,16 @@ def test_strerror_without_gpu(built_lib):
     import paper_1306_6192_gb300 as mm
     assert mm.mm_strerror(mm.MM_OK) == "ok"
     assert "budget" in mm.mm_strerror(mm.MM_EBUDGET)
+
+
+def test_calls_before_init_report_it(built_lib):
+    """Entry points that need the device return MM_ENOTINIT before mm_init,
+    without touching CUDA (no GPU here)."""
+    import paper_1306_6192_gb300 as mm
+    if mm.mm_sync(None) != mm.MM_ENOTINIT:
+        pytest.skip("the library was initialised by an earlier test in this process")
+    F32, SPLIT = mm.MM_F32, mm.MM_MODE_SPLIT_BF16X3
+    assert mm.mm_gemm(8, 8, 8, 1, 1, 1, F32, SPLIT) == mm.MM_ENOTINIT
+    assert mm.mm_gemm_axpby(8, 8, 8, 1.0, 1, 1, -1.0, 1, 1, F32, SPLIT) == mm.MM_ENOTINIT
+    assert mm.mm_gemm_axpby_async(8, 8, 8, 1.0, 1, 1, -1.0, 1, 1, F32, SPLIT) == mm.MM_ENOTINIT
+    assert mm.mm_add(8, 8, 1.0, 1, 1.0, 1, 1, F32) == mm.MM_ENOTINIT
