@@ -229,7 +229,9 @@ mm_status mm_gemm_async(int64_t n, int64_t m, int64_t p, const void *A,
  * paths (the kernel that writes C applies it to each entry as it stores it,
  * so D is read once and no second pass over C runs; the tensor-core kernels
  * keep their tiled stores where C and D are 16-byte aligned with p % 4 == 0).
- * Device pointers only; D is n x p row-major like C, of the same dtype, and
+ * mm_gemm_axpby takes device or host pointers (host operands are staged
+ * through library buffers, as mm_gemm does); mm_gemm_axpby_async takes device
+ * pointers only.  D is n x p row-major like C, of the same dtype, and
  * is either C itself (C = alpha (A.B) + beta C) or apart from it (a partial
  * overlap returns MM_EINVAL).  Each entry x of the product (computed by
  * `mode` as mm_gemm does) becomes fma(alpha, x, beta d) with one rounding of
@@ -242,7 +244,8 @@ mm_status mm_gemm_async(int64_t n, int64_t m, int64_t p, const void *A,
  * tiles' MMAs take about as long as their stores, so the tensor-core kernel
  * has no slack for it); with D = C the product then goes to library scratch
  * first.  Returns
- * what mm_gemm returns, plus MM_EINVAL for a NULL or host D where beta != 0.
+ * what mm_gemm returns, plus MM_EINVAL for a NULL D where beta != 0 (and,
+ * from the asynchronous form, for a host D).
  * mm_gemm_axpby waits for the result; mm_gemm_axpby_async queues it on
  * `stream` (NULL = the library stream) under mm_gemm_async's scratch rule. */
 mm_status mm_gemm_axpby(int64_t n, int64_t m, int64_t p, double alpha, const void *A,

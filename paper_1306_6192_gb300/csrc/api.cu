@@ -531,9 +531,53 @@ mm_status mm_gemm_axpby(int64_t n, int64_t m, int64_t p, double alpha, const voi
                         const void *B, double beta, const void *D, void *C, mm_dtype dt,
                         mm_mode mode) {
   MM_REQUIRE_INIT();
+  mm_status st = validate(n, m, p, dt, mode);
+  if (st != MM_OK) return st;
+  if (n == 0 || p == 0) return MM_OK;
+  const bool terms = m > 0 && alpha != 0.0, with_d = beta != 0.0;
+  if (!C || (terms && (!A || !B)) || (with_d && !D)) return MM_EINVAL;
   std::lock_guard<std::mutex> lk(g_api_mutex);
-  const mm_status st = enqueue_axpby(n, m, p, alpha, A, B, beta, D, C, dt, mode, g_ctx.stream);
-  return st != MM_OK ? st : check_device_flag(g_ctx.stream);
+  cudaStream_t s = g_ctx.stream;
+  const bool dev_c = pointer_kind(C) == 1;
+  const bool dev_a = !terms || pointer_kind(A) == 1;
+  const bool dev_b = !terms || pointer_kind(B) == 1;
+  const bool dev_d = !with_d || pointer_kind(D) == 1;
+  if (!(dev_a && dev_b && dev_c && dev_d)) {
+    // Host operands: staged through library buffers on the library stream,
+    // as mm_gemm does; D and C are checked for overlap as host ranges
+    const size_t es = dt == MM_F64 ? 8 : 4;
+    const size_t ba = terms ? (size_t)(n * m) * es : 0, bb = terms ? (size_t)(m * p) * es : 0;
+    const size_t bc = (size_t)(n * p) * es;
+    const bool d_is_c = with_d && D == C;
+    if (with_d && !d_is_c) {
+      const uintptr_t d0 = reinterpret_cast<uintptr_t>(D), c0 = reinterpret_cast<uintptr_t>(C);
+      if (d0 < c0 + bc && c0 < d0 + bc) return MM_EINVAL;
+    }
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t ob = up(ba), oc = ob + up(bb), od = oc + up(bc);
+    const size_t need = od + ((with_d && !d_is_c && !dev_d) ? bc : 0);
+    cudaError_t e = g_ctx.stage_ws.reserve(need, s);
+    if (e != cudaSuccess) return note_cuda(e);
+    uint8_t *base = static_cast<uint8_t *>(g_ctx.stage_ws.ptr);
+    const void *dA = dev_a ? A : base;
+    const void *dB = dev_b ? B : base + ob;
+    void *dC = dev_c ? C : base + oc;
+    const void *dD = !with_d ? nullptr : d_is_c ? dC : dev_d ? D : base + od;
+    if (!dev_a && ba) e = cudaMemcpyAsync(base, A, ba, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !dev_b && bb) e = cudaMemcpyAsync(base + ob, B, bb, cudaMemcpyHostToDevice, s);
+    // C's entries are D's where D is C: bring them in
+    if (e == cudaSuccess && d_is_c && !dev_c) e = cudaMemcpyAsync(dC, C, bc, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && with_d && !d_is_c && !dev_d)
+      e = cudaMemcpyAsync(base + od, D, bc, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return note_cuda(e);
+    st = enqueue_axpby(n, m, p, alpha, dA, dB, beta, dD, dC, dt, mode, s);
+    if (st != MM_OK) return st;
+    if (!dev_c && (e = cudaMemcpyAsync(C, dC, bc, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      return note_cuda(e);
+    return check_device_flag(s);
+  }
+  st = enqueue_axpby(n, m, p, alpha, A, B, beta, D, C, dt, mode, s);
+  return st != MM_OK ? st : check_device_flag(s);
 }
 
 mm_status mm_gemm(int64_t n, int64_t m, int64_t p, const void *A, const void *B, void *C,

@@ -234,7 +234,7 @@ def test_arguments(mmlib):
     host = np.zeros(64, np.float32)
     F32, SPLIT = mm.MM_F32, mm.MM_MODE_SPLIT_BF16X3
     assert mm.mm_gemm_axpby(8, 8, 8, 1.0, x, x, 1.0, None, x, F32, SPLIT) == mm.MM_EINVAL
-    assert mm.mm_gemm_axpby(8, 8, 8, 1.0, x, x, 1.0, host, x, F32, SPLIT) == mm.MM_EINVAL
+    assert mm.mm_gemm_axpby_async(8, 8, 8, 1.0, x, x, 1.0, host, x, F32, SPLIT) == mm.MM_EINVAL
     C = torch.zeros(128, device="cuda")
     # D overlapping C without being C
     assert mm.mm_gemm_axpby(8, 8, 8, 1.0, x, x, 1.0, C[4:], C, F32, SPLIT) == mm.MM_EINVAL
@@ -243,6 +243,33 @@ def test_arguments(mmlib):
                             mm.MM_MODE_DGEMM) == mm.MM_EUNSUPPORTED
     assert mm.mm_gemm_axpby(0, 8, 8, 1.0, None, None, 1.0, None, None, F32, SPLIT) == mm.MM_OK
     assert mm.mm_gemm_axpby(8, 8, 8, 1.0, None, x, 0.0, None, x, F32, SPLIT) == mm.MM_EINVAL
+
+
+@pytest.mark.parametrize("mode", ["SPLIT_BF16X3", "SIMT"])
+def test_host_operands(mmlib, mode):
+    """Host A, B, D and C (staged through library buffers) give the device
+    call's bits, separate and in place (D = C on the host)."""
+    mm = mmlib
+    md = getattr(mm, "MM_MODE_" + mode)
+    n, m, p = 300, 700, 260
+    A = synth.uniform_pm1(7400, (n, m))
+    B = synth.uniform_pm1(7401, (m, p))
+    D = synth.uniform_pm1(7402, (n, p))
+    want = _axpby(mm, n, m, p, 0.5, dev(A), dev(B), -2.0, dev(D), False, md).cpu().numpy()
+    C = np.full((n, p), np.nan, np.float32)
+    assert mm.mm_gemm_axpby(n, m, p, 0.5, A, B, -2.0, D, C, mm.MM_F32, md) == mm.MM_OK
+    _same(C, want)
+    C = D.copy()
+    assert mm.mm_gemm_axpby(n, m, p, 0.5, A, B, -2.0, C, C, mm.MM_F32, md) == mm.MM_OK
+    _same(C, want)
+    # device A and B, host D and C
+    C = np.full((n, p), np.nan, np.float32)
+    assert mm.mm_gemm_axpby(n, m, p, 0.5, dev(A), dev(B), -2.0, D, C, mm.MM_F32, md) == mm.MM_OK
+    _same(C, want)
+    # host D overlapping host C without being C
+    buf = np.zeros(2 * n * p, np.float32)
+    Cv, Dv = buf[:n * p], buf[4:4 + n * p]
+    assert mm.mm_gemm_axpby(n, m, p, 0.5, A, B, -2.0, Dv, Cv, mm.MM_F32, md) == mm.MM_EINVAL
 
 
 def test_async_on_a_stream(mmlib):
