@@ -670,7 +670,12 @@ mm_status fp8_blocks_launch(Scratch &ws, std::vector<SplitProb> &blk, std::vecto
   const size_t flag_off = (max_off + (size_t)maxw * 4 + 255) & ~(size_t)255;
   const size_t tab_off = (flag_off + (size_t)flag_items * 4 + 255) & ~(size_t)255;
   const size_t tab_bytes = (size_t)np * sizeof(SplitProb);
-  const size_t map_off = (tab_off + 2 * tab_bytes + 255) & ~(size_t)255;
+  // tensor maps over the C matrices for the tensor-core kernel's tiled
+  // stores (tables of up to kMaxCMaps products), after the two tables
+  constexpr size_t kMaxCMaps = 8192, kMapBytes = 128;
+  const size_t cmap_rel = (2 * tab_bytes + 63) & ~(size_t)63;
+  const size_t cmap_bytes = (size_t)np <= kMaxCMaps ? (size_t)np * kMapBytes : 0;
+  const size_t map_off = (tab_off + cmap_rel + cmap_bytes + 255) & ~(size_t)255;
   const size_t map_ints = np > 1 ? (size_t)(blk_units + tc_units + packs) : 0;
   cudaError_t e = ws.reserve(map_off + map_ints * sizeof(int), s);
   if (e != cudaSuccess) return note_cuda(e);
@@ -687,8 +692,15 @@ mm_status fp8_blocks_launch(Scratch &ws, std::vector<SplitProb> &blk, std::vecto
   }
   SplitProb *d_blk = reinterpret_cast<SplitProb *>(base + tab_off);
   SplitProb *d_tc = d_blk + np;
+  const void *d_cmaps = cmap_bytes ? static_cast<const void *>(base + tab_off + cmap_rel) : nullptr;
   {
-    std::vector<uint8_t> blob(2 * tab_bytes);
+    std::vector<uint8_t> blob(cmap_rel + cmap_bytes, 0);
+    for (size_t g = 0; cmap_bytes && g < (size_t)np; g++) {
+      SplitProb &t = tc[g];
+      if (tc_c_map_ok(t.C, t.n, t.p) &&
+          encode_c_map(blob.data() + cmap_rel + g * kMapBytes, t.C, t.n, t.p) == cudaSuccess)
+        t.c_tma = (int32_t)g + 1;
+    }
     std::memcpy(blob.data(), blk.data(), tab_bytes);
     std::memcpy(blob.data() + tab_bytes, tc.data(), tab_bytes);
     e = ws.stage.copy_to_device(d_blk, blob.data(), blob.size(), s);
@@ -722,7 +734,7 @@ mm_status fp8_blocks_launch(Scratch &ws, std::vector<SplitProb> &blk, std::vecto
   TcConfig cfg{128, 4, 0};
   cfg.max_bn = kPackBN;
   e = launch_tc(kTcE4m3, d_tc, np, (int)tc_units, tc_map, nullptr, ws.ptr, rows, cfg, g_ctx.d_err,
-                s, nullptr, 1);
+                s, nullptr, 1, d_cmaps);
   if (e != cudaSuccess) return note_cuda(e);
   // the other tiles, K block by K block
   static std::once_flag once;
@@ -749,7 +761,7 @@ size_t fp8_blocks_scratch_bytes(int64_t n, int64_t m, int64_t p) {
   // packs and factors, maxima, tile flags, two tables, unit maps
   return (size_t)(mt * kTcBM + nt * kPackBN) * kt * (kPackRowBytes + 4) +
          (size_t)(mt * kTcBM + nt * kPackBN) * 4 + (size_t)(mt + 2 * nt) * 4 +
-         2 * sizeof(SplitProb) + (size_t)mt * nt * 12 + 4096;
+         2 * sizeof(SplitProb) + 256 + (size_t)mt * nt * 12 + 4096;
 }
 
 // Two tables over the same packs: `blk` for the blockwise kernel (N sub-tiles
